@@ -1,0 +1,167 @@
+"""Oracle for the stealthy-hyperuniform energy, force and FIRE quench (arXiv:2304.09139).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s
+``cpu_baseline`` / reference arm may import this package.  The product path (the CUDA library
+and its Python binding) never imports, links or calls it, and the two share no code.
+
+The arithmetic lives in ``oracle.c`` (IEEE binary128 via libquadmath, one ``sincosq`` per
+(k, particle) pair, index-order sums, OpenMP across k and across particles).  This module only
+builds that file with gcc and marshals numpy arrays through ctypes.  Each wrapper names the
+paper's equation it evaluates.
+
+Parity pins for every function live in ``tests/test_oracle.py``.  The FIRE trajectory is
+"parity unpinned" by design: trajectories are chaotic and the ground state is degenerate, so
+minimised states are judged by S_max only.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into oracle/_oracle.so (gcc, -O2, OpenMP, libquadmath)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lquadmath", "-lm"],
+                       check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class FireParams(ctypes.Structure):
+    _fields_ = [("dt0", ctypes.c_double), ("dt_max", ctypes.c_double), ("alpha_start", ctypes.c_double),
+                ("f_alpha", ctypes.c_double), ("f_inc", ctypes.c_double), ("f_dec", ctypes.c_double),
+                ("n_min", ctypes.c_int), ("max_steps", ctypes.c_int64), ("smax_target", ctypes.c_double)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.POINTER
+            d, i64, i32 = ctypes.c_double, ctypes.c_int64, ctypes.c_int32
+            lib.oracle_chi_to_m.restype = i64
+            lib.oracle_chi_to_m.argtypes = [ctypes.c_int, i64, d]
+            lib.oracle_kset.restype = ctypes.c_int
+            lib.oracle_kset.argtypes = [ctypes.c_int, i64, d, d, d, i64, P(i32), P(i64)]
+            lib.oracle_ntilde.restype = ctypes.c_int
+            lib.oracle_ntilde.argtypes = [ctypes.c_int, i64, P(d), P(d), i64, P(i32), P(d), P(d), ctypes.c_int]
+            lib.oracle_phi_grad.restype = ctypes.c_int
+            lib.oracle_phi_grad.argtypes = [ctypes.c_int, i64, d, P(d), P(d), i64, P(i32), P(d), P(d), P(d),
+                                            P(d), P(d), ctypes.c_int]
+            lib.oracle_fire.restype = ctypes.c_int
+            lib.oracle_fire.argtypes = [ctypes.c_int, i64, d, P(d), P(d), i64, P(i32), P(FireParams), P(i64),
+                                        P(d), P(d), ctypes.c_int]
+            lib.oracle_num_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def chi_to_m(d: int, N: int, chi: float) -> int:
+    """M = round-half-even(chi d (N-1)), the inverse of chi = M / (d (N-1)) (Definitions, Eq. for chi)."""
+    return int(_load().oracle_chi_to_m(d, N, chi))
+
+
+def kset(d: int, N: int, L: float, chi: float = 0.0, K: float = 0.0) -> np.ndarray:
+    """Independent wavevectors n (k = 2 pi n / L) of the half-space, sorted by (|n|^2, lex) (Definitions)."""
+    lib = _load()
+    M = ctypes.c_int64(0)
+    rc = lib.oracle_kset(d, N, L, chi, K, 0, None, ctypes.byref(M))
+    if rc != 0:
+        raise ValueError(f"oracle_kset rejected d={d} N={N} L={L} chi={chi} K={K} (rc={rc})")
+    out = np.zeros((max(M.value, 1), d), dtype=np.int32)
+    rc = lib.oracle_kset(d, N, L, chi, K, M.value, _ip(out), ctypes.byref(M))
+    if rc != 0:
+        raise RuntimeError(f"oracle_kset failed rc={rc}")
+    return out[:M.value].copy()
+
+
+def _pos(s_hi, s_lo, d):
+    s_hi = np.ascontiguousarray(s_hi, dtype=np.float64).reshape(-1, d)
+    s_lo = np.zeros_like(s_hi) if s_lo is None else np.ascontiguousarray(s_lo, dtype=np.float64).reshape(-1, d)
+    return s_hi, s_lo
+
+
+def ntilde(s_hi, s_lo, n, nthreads: int = 0):
+    """(C_k, S_k) with n~(k) = C + iS = sum_j exp(+2 pi i n.s_j) (Eq. ntilde), each as an [M, 2] (hi, lo) array."""
+    n = np.ascontiguousarray(n, dtype=np.int32)
+    d = n.shape[1]
+    s_hi, s_lo = _pos(s_hi, s_lo, d)
+    M = n.shape[0]
+    C = np.zeros((max(M, 1), 2))
+    S = np.zeros((max(M, 1), 2))
+    rc = _load().oracle_ntilde(d, s_hi.shape[0], _dp(s_hi), _dp(s_lo), M, _ip(n), _dp(C), _dp(S), nthreads)
+    if rc != 0:
+        raise RuntimeError(f"oracle_ntilde rc={rc}")
+    return C[:M], S[:M]
+
+
+def phi_grad(s_hi, s_lo, n, L: float, want_force: bool = True, want_cs: bool = False, nthreads: int = 0):
+    """Phi (Eq. energy, constant dropped), S_max (Eq. smax) and F (Eq. force) in binary128.
+
+    Returns a dict with 'phi' and 'smax' as (hi, lo) pairs, 'F' as an [N, d, 2] array (or None), and
+    'C', 'S' as [M, 2] arrays when want_cs.
+    """
+    n = np.ascontiguousarray(n, dtype=np.int32)
+    d = n.shape[1]
+    s_hi, s_lo = _pos(s_hi, s_lo, d)
+    N, M = s_hi.shape[0], n.shape[0]
+    phi = np.zeros(2)
+    smax = np.zeros(2)
+    F = np.zeros((max(N, 1), d, 2)) if want_force else None
+    C = np.zeros((max(M, 1), 2)) if want_cs else None
+    S = np.zeros((max(M, 1), 2)) if want_cs else None
+    rc = _load().oracle_phi_grad(d, N, L, _dp(s_hi), _dp(s_lo), M, _ip(n), _dp(phi), _dp(smax), _dp(F), _dp(C),
+                                 _dp(S), nthreads)
+    if rc != 0:
+        raise RuntimeError(f"oracle_phi_grad rc={rc}")
+    out = {"phi": phi, "smax": smax, "F": None if F is None else F[:N]}
+    if want_cs:
+        out["C"], out["S"] = C[:M], S[:M]
+    return out
+
+
+def fire(s_hi, s_lo, n, L: float, *, dt0: float, dt_max: float, alpha_start: float = 0.1, f_alpha: float = 0.99,
+         f_inc: float = 1.1, f_dec: float = 0.5, n_min: int = 5, max_steps: int = 100000,
+         smax_target: float = 1e-36, nthreads: int = 0):
+    """FIRE quench (Bitzek et al. 2006, the paper's minimiser) in binary128 with the energy guard.
+
+    Returns (status, steps, s_hi, s_lo, smax(hi, lo), phi(hi, lo)); status 0 = converged.
+    """
+    n = np.ascontiguousarray(n, dtype=np.int32)
+    d = n.shape[1]
+    s_hi, s_lo = _pos(s_hi, s_lo, d)
+    s_hi, s_lo = s_hi.copy(), s_lo.copy()
+    p = FireParams(dt0, dt_max, alpha_start, f_alpha, f_inc, f_dec, n_min, max_steps, smax_target)
+    steps = ctypes.c_int64(0)
+    smax = np.zeros(2)
+    phi = np.zeros(2)
+    st = _load().oracle_fire(d, s_hi.shape[0], L, _dp(s_hi), _dp(s_lo), n.shape[0], _ip(n), ctypes.byref(p),
+                             ctypes.byref(steps), _dp(smax), _dp(phi), nthreads)
+    if st < 0:
+        raise RuntimeError(f"oracle_fire rc={st}")
+    return st, steps.value, s_hi, s_lo, smax, phi
