@@ -1,0 +1,144 @@
+/*
+ * ssh.h -- C ABI of the stealthy-hyperuniform collective-coordinate library (arXiv:2304.09139) for B300.
+ *
+ * The library evaluates, for N points in a periodic box of side L in d dimensions,
+ *   n~(k) = C(k) + i S(k) = sum_j exp(i k.r_j)                       (Eq. ntilde; sign +, see below)
+ *   Phi   = sum over the M independent k (half-space, 0 < |k| <= K) of |n~(k)|^2
+ *                                                                     (Eq. energy with eps0 = 1, constant dropped)
+ *   S(k)  = |n~(k)|^2 / N,  S_max = max_k S(k)                       (Eqs. structurefactor, smax)
+ *   F_j   = -grad_j Phi = 2 sum_k k [C(k) sin(k.r_j) - S(k) cos(k.r_j)] (Eq. force)
+ * on the GPU, and minimises Phi with FIRE (Simulations).  k = 2 pi n / L for integer n in the half-space
+ * {first non-zero component of n > 0}; chi = M / (d (N - 1)) (Definitions).  The paper writes exp(-i k.r);
+ * |n~|, Phi, S and F do not depend on that sign, only the sign of S(k) does.
+ *
+ * Conventions for every entry point:
+ *   * Return value: SSH_OK or an error code; no C++ exception crosses this boundary.  On error,
+ *     ssh_last_error() returns a thread-local message describing it.
+ *   * Host arrays are owned by the caller.  The library copies inputs in and writes outputs into caller
+ *     buffers before returning; it never keeps a caller pointer.
+ *   * Device memory and CUDA streams are owned by the library (one stream per context unless the caller
+ *     installs its own with ssh_set_stream).  Calls on one context are not thread-safe.
+ *   * Double-double (dd) values are passed as a (hi, lo) pair of doubles whose exact sum is the value.
+ *   * Positions and forces are row-major [N][d].
+ */
+#ifndef SSH_H_
+#define SSH_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ssh_ctx ssh_ctx; /* opaque, library-owned */
+
+typedef enum {
+  SSH_OK = 0,
+  SSH_EINVAL = 1,    /* an argument is out of range or inconsistent */
+  SSH_ENOMEM = 2,    /* device or host allocation failed */
+  SSH_ECUDA = 3,     /* a CUDA call failed (no device, launch error, ...) */
+  SSH_ENAN = 4,      /* non-finite value in positions or results */
+  SSH_ENOTCONV = 5,  /* the minimiser hit its step cap or stalled above the target */
+  SSH_ETIMEOUT = 6,  /* a bounded device or host wait gave up */
+  SSH_EBUSY = 7,     /* result not ready yet / no capacity now */
+  SSH_ENOTFOUND = 8  /* unknown ticket or handle */
+} ssh_status;
+
+/* Arithmetic of an evaluation.
+ *   SSH_FP64 -- plain binary64 phases, sums and products (the paper's cheap first stage).
+ *   SSH_DD   -- double-double on the FP64 pipe, as the paper describes (~106-bit significands).
+ *   SSH_FX   -- 128-bit fixed point on the integer pipes (Q0.128 positions, exact phase reduction, exact
+ *               sums, 2^-126 resolution): dd-or-better accuracy on the units B300 has most of.
+ */
+typedef enum { SSH_FP64 = 0, SSH_DD = 1, SSH_FX = 2 } ssh_prec;
+
+typedef struct {
+  int device;       /* CUDA device ordinal (default 0) */
+  int reserved[7];  /* zero */
+} ssh_opts;
+
+/* Library version string, e.g. "ssh 0.1 sm_103a". Never NULL. */
+const char* ssh_version(void);
+
+/* Thread-local message for the most recent non-OK status returned on this thread ("" if none). */
+const char* ssh_last_error(void);
+
+/*
+ * Create a context for N points in d dimensions in a periodic box of side L (Definitions).
+ * Exactly one of chi > 0 (M = round-half-even(chi d (N-1)) smallest |k| of the half-space, ties broken
+ * lexicographically) or K > 0 (every half-space k with |k| <= K, complete shells) must be given.
+ * 1 <= d <= 4, N >= 1, L > 0 finite, chi < 1 (the paper's disordered regime is chi < 1/2).
+ * opts may be NULL.  On success *out owns device memory sized for this (d, N, M); free with ssh_destroy.
+ * Errors: SSH_EINVAL (arguments), SSH_ECUDA (no device), SSH_ENOMEM.
+ */
+ssh_status ssh_create(int d, int64_t N, double L, double chi, double K, const ssh_opts* opts, ssh_ctx** out);
+
+/* Release everything a context owns.  NULL is a no-op. */
+void ssh_destroy(ssh_ctx* ctx);
+
+/* Sizes: any pointer may be NULL. */
+ssh_status ssh_get_dims(const ssh_ctx* ctx, int* d, int64_t* N, int64_t* M, double* L);
+
+/* The M wavevector indices n (k = 2 pi n / L) in public order: by |n|^2, then lexicographic.
+ * n: caller buffer of M*d int32 (row-major), or NULL to query M only. */
+ssh_status ssh_get_kset(const ssh_ctx* ctx, int64_t* M, int32_t* n);
+
+/* Host only (no GPU needed): the wavevector set that ssh_create would build for these arguments, in public
+ * order.  n: caller buffer of cap rows of d int32, or NULL to query M.  Errors: SSH_EINVAL for bad
+ * arguments or cap < M (M is still written). */
+ssh_status ssh_kset_build(int d, int64_t N, double L, double chi, double K, int64_t cap, int32_t* n, int64_t* M);
+
+/* Install a caller-owned cudaStream_t (passed as void*) for all later work on ctx; NULL restores the
+ * context's own stream.  The caller keeps ownership and must keep the stream alive. */
+ssh_status ssh_set_stream(ssh_ctx* ctx, void* cuda_stream);
+
+/* Block the host until all work queued on the context's stream has finished. */
+ssh_status ssh_sync(ssh_ctx* ctx);
+
+/* Positions in physical units r (N*d row-major, dd as hi + lo; lo may be NULL for zero).  Values are
+ * wrapped into [0, L) (periodic box).  Errors: SSH_ENAN for a non-finite coordinate. */
+ssh_status ssh_set_positions(ssh_ctx* ctx, const double* r_hi, const double* r_lo);
+
+/* Positions as fractional coordinates s = r / L (N*d row-major, dd, lo may be NULL); exact, no division. */
+ssh_status ssh_set_positions_frac(ssh_ctx* ctx, const double* s_hi, const double* s_lo);
+
+/* Current fractional positions s in [0, 1) as dd (N*d row-major); either pointer may be NULL. */
+ssh_status ssh_get_positions_frac(ssh_ctx* ctx, double* s_hi, double* s_lo);
+
+/*
+ * One evaluation of Phi, S_max and F at the current positions in arithmetic `prec` (Eqs. energy, smax,
+ * force), results copied to the caller: phi[2] and smax[2] as dd (either may be NULL), F_hi / F_lo the
+ * force in physical units (N*d row-major; either may be NULL).  Blocks until the copies are done.
+ * Errors: SSH_EINVAL (no positions set / bad prec), SSH_ECUDA, SSH_ENAN (non-finite result).
+ */
+ssh_status ssh_energy_grad(ssh_ctx* ctx, int prec, double phi[2], double smax[2], double* F_hi, double* F_lo);
+
+/*
+ * The same evaluation with inputs already resident on the device and results left there: it only
+ * enqueues kernels on the context's stream and returns (no host synchronisation).  want_force = 0 skips
+ * the force sum (energy and S_max only).  Read results later with ssh_get_results / ssh_get_ntilde.
+ */
+ssh_status ssh_eval(ssh_ctx* ctx, int prec, int want_force);
+
+/* Copy the results of the last evaluation to the host (synchronises the stream).  Any pointer may be NULL.
+ * The force is present only if the last evaluation computed it. */
+ssh_status ssh_get_results(ssh_ctx* ctx, double phi[2], double smax[2], double* F_hi, double* F_lo);
+
+/* n~(k) = C + i S of the last evaluation, M entries each as dd, in public k order; any pointer may be NULL. */
+ssh_status ssh_get_ntilde(ssh_ctx* ctx, double* C_hi, double* C_lo, double* S_hi, double* S_lo);
+
+/*
+ * Event profiler (tracing).  When enabled, every kernel the context launches is bracketed by a CUDA event
+ * pair on the context's stream; ssh_prof_read synchronises the stream and returns, per kernel id, the
+ * summed device time in milliseconds and the launch count since the last ssh_prof_enable call.
+ * Kernel ids: 0 twiddle tables, 1 collective density n~, 2 density reduction, 3 Phi/S_max finalise,
+ * 4 force coefficients, 5 force, 6 force reduction, 7 minimiser update (FIRE).  n entries are written.
+ */
+ssh_status ssh_prof_enable(ssh_ctx* ctx, int on);
+ssh_status ssh_prof_read(ssh_ctx* ctx, int n, double* ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSH_H_ */

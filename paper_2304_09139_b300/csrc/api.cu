@@ -1,0 +1,323 @@
+// api.cu -- the extern "C" boundary (include/ssh.h): validation, host<->device copies, dispatch.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "ssh_internal.h"
+
+#define SSH_TABLE_QUAL static
+#include "gen/tables.h"
+
+struct ssh_ctx {
+  ssh::Ctx c;
+  double* h_stage = nullptr;  // pinned staging for positions and forces: 2 * d * N doubles
+};
+
+namespace ssh {
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+}  // namespace ssh
+
+using ssh::set_error;
+
+static ssh_status cuda_fail(cudaError_t e, const char* what) {
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return SSH_ECUDA;
+}
+
+#define SSH_CUDA(call, what)                         \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+static void free_buf(ssh::DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+}
+
+extern "C" {
+
+const char* ssh_version(void) { return "ssh 0.1 sm_103a"; }
+
+const char* ssh_last_error(void) { return ssh::g_err.c_str(); }
+
+ssh_status ssh_create(int d, int64_t N, double L, double chi, double K, const ssh_opts* opts, ssh_ctx** out) {
+  if (!out) { set_error("ssh_create: out is NULL"); return SSH_EINVAL; }
+  *out = nullptr;
+  if (d < 1 || d > ssh::kMaxDim) { set_error("ssh_create: d must be 1..4"); return SSH_EINVAL; }
+  if (N < 1 || N > (int64_t)1 << 31) { set_error("ssh_create: N must be in [1, 2^31]"); return SSH_EINVAL; }
+  if (!(L > 0) || !isfinite(L)) { set_error("ssh_create: L must be positive and finite"); return SSH_EINVAL; }
+  if (!isfinite(chi) || !isfinite(K) || chi < 0 || K < 0 || (chi > 0) == (K > 0)) {
+    set_error("ssh_create: give exactly one of chi > 0 or K > 0");
+    return SSH_EINVAL;
+  }
+  if (chi >= 1.0) { set_error("ssh_create: chi must be < 1"); return SSH_EINVAL; }
+  ssh_ctx* h = new (std::nothrow) ssh_ctx();
+  if (!h) { set_error("ssh_create: out of host memory"); return SSH_ENOMEM; }
+  ssh::Ctx& c = h->c;
+  c.d = d;
+  c.N = N;
+  c.L = L;
+  c.device = opts ? opts->device : 0;
+  if (ssh::build_kset(d, N, L, chi, K, &c.ks) != 0) {
+    delete h;
+    set_error("ssh_create: could not build the wavevector set");
+    return SSH_EINVAL;
+  }
+  c.M = c.ks.M;
+  if (c.M > (int64_t)1 << 30) { delete h; set_error("ssh_create: M too large"); return SSH_EINVAL; }
+  c.tl = ssh::build_table_layout(c.ks);
+  c.nt = ssh::build_nt_plan(c.ks, c.tl);
+  c.fp = ssh::build_f_plan(c.ks, c.tl);
+  c.Npad = (N + 31) / 32 * 32;
+  // 4 pi / L as dd
+  dd four_pi = dd_make(2.0 * SSH_DD_2PI[0], 2.0 * SSH_DD_2PI[1]);
+  c.pref = dd_div(four_pi, dd_make(L));
+  cudaError_t e = cudaSetDevice(c.device);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) { delete h; return cuda_fail(e, "ssh_create: device/stream"); }
+  c.own_stream = true;
+  cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, c.device);
+  e = ssh::plan_upload(&c);
+  if (e == cudaSuccess) e = cudaMallocHost(&h->h_stage, sizeof(double) * 2 * (size_t)d * N);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+  if (e != cudaSuccess) {
+    ssh_destroy(h);
+    return e == cudaErrorMemoryAllocation ? (set_error("ssh_create: out of device memory"), SSH_ENOMEM)
+                                          : cuda_fail(e, "ssh_create: set-up");
+  }
+  *out = h;
+  return SSH_OK;
+}
+
+void ssh_destroy(ssh_ctx* h) {
+  if (!h) return;
+  ssh::Ctx& c = h->c;
+  cudaSetDevice(c.device);
+  if (c.stream) cudaStreamSynchronize(c.stream);
+  for (ssh::DevBuf* b : {&c.s_hi, &c.s_lo, &c.rows, &c.slots, &c.blocks, &c.grows, &c.cols, &c.fsplit, &c.tab, &c.part,
+                         &c.C_hi, &c.C_lo, &c.S_hi, &c.S_lo, &c.coef, &c.blk, &c.scal, &c.fpart, &c.F_hi, &c.F_lo})
+    free_buf(*b);
+  if (h->h_stage) cudaFreeHost(h->h_stage);
+  for (ssh::ProfRec& r : c.prof.pending) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
+  for (cudaEvent_t ev : c.prof.pool) cudaEventDestroy(ev);
+  if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
+  delete h;
+}
+
+ssh_status ssh_get_dims(const ssh_ctx* h, int* d, int64_t* N, int64_t* M, double* L) {
+  if (!h) { set_error("ssh_get_dims: NULL context"); return SSH_EINVAL; }
+  if (d) *d = h->c.d;
+  if (N) *N = h->c.N;
+  if (M) *M = h->c.M;
+  if (L) *L = h->c.L;
+  return SSH_OK;
+}
+
+ssh_status ssh_get_kset(const ssh_ctx* h, int64_t* M, int32_t* n) {
+  if (!h) { set_error("ssh_get_kset: NULL context"); return SSH_EINVAL; }
+  if (M) *M = h->c.M;
+  if (n && h->c.M > 0) memcpy(n, h->c.ks.n_pub.data(), sizeof(int32_t) * h->c.ks.n_pub.size());
+  return SSH_OK;
+}
+
+ssh_status ssh_kset_build(int d, int64_t N, double L, double chi, double K, int64_t cap, int32_t* n, int64_t* M) {
+  ssh::KSet ks;
+  if (ssh::build_kset(d, N, L, chi, K, &ks) != 0) { set_error("ssh_kset_build: bad arguments"); return SSH_EINVAL; }
+  if (M) *M = ks.M;
+  if (n) {
+    if (cap < ks.M) { set_error("ssh_kset_build: buffer too small"); return SSH_EINVAL; }
+    if (ks.M > 0) memcpy(n, ks.n_pub.data(), sizeof(int32_t) * ks.n_pub.size());
+  }
+  return SSH_OK;
+}
+
+ssh_status ssh_set_stream(ssh_ctx* h, void* stream) {
+  if (!h) { set_error("ssh_set_stream: NULL context"); return SSH_EINVAL; }
+  ssh::Ctx& c = h->c;
+  cudaSetDevice(c.device);
+  SSH_CUDA(cudaStreamSynchronize(c.stream), "ssh_set_stream: sync old stream");
+  if (stream) {
+    if (c.own_stream) { cudaStreamDestroy(c.stream); c.own_stream = false; }
+    c.stream = (cudaStream_t)stream;
+  } else if (!c.own_stream) {
+    SSH_CUDA(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking), "ssh_set_stream: create");
+    c.own_stream = true;
+  }
+  return SSH_OK;
+}
+
+ssh_status ssh_sync(ssh_ctx* h) {
+  if (!h) { set_error("ssh_sync: NULL context"); return SSH_EINVAL; }
+  cudaSetDevice(h->c.device);
+  SSH_CUDA(cudaStreamSynchronize(h->c.stream), "ssh_sync");
+  return SSH_OK;
+}
+
+// s (fractional, any real) -> [0, 1) as dd, SoA staging [a][j].
+static ssh_status stage_and_upload(ssh_ctx* h, const double* s_hi, const double* s_lo, bool physical) {
+  ssh::Ctx& c = h->c;
+  const int64_t N = c.N;
+  const int d = c.d;
+  double* hs = h->h_stage;
+  double* ls = h->h_stage + (size_t)d * N;
+  dd Ld = dd_make(c.L);
+  for (int64_t j = 0; j < N; j++) {
+    for (int a = 0; a < d; a++) {
+      double hi = s_hi[j * d + a], lo = s_lo ? s_lo[j * d + a] : 0.0;
+      if (!isfinite(hi) || !isfinite(lo)) {
+        set_error("positions contain a non-finite value");
+        return SSH_ENAN;
+      }
+      dd v = two_sum(hi, lo);
+      if (physical) v = dd_div(v, Ld);
+      v = dd_frac(v);
+      hs[a * N + j] = v.hi;
+      ls[a * N + j] = v.lo;
+    }
+  }
+  cudaSetDevice(c.device);
+  SSH_CUDA(cudaMemcpyAsync(c.s_hi.p, hs, sizeof(double) * d * N, cudaMemcpyHostToDevice, c.stream), "upload positions");
+  SSH_CUDA(cudaMemcpyAsync(c.s_lo.p, ls, sizeof(double) * d * N, cudaMemcpyHostToDevice, c.stream), "upload positions");
+  // the staging buffer is reused by the next call: wait for the copies before returning
+  SSH_CUDA(cudaStreamSynchronize(c.stream), "upload positions");
+  c.have_positions = true;
+  c.have_result = false;
+  return SSH_OK;
+}
+
+ssh_status ssh_set_positions(ssh_ctx* h, const double* r_hi, const double* r_lo) {
+  if (!h || !r_hi) { set_error("ssh_set_positions: NULL argument"); return SSH_EINVAL; }
+  return stage_and_upload(h, r_hi, r_lo, true);
+}
+
+ssh_status ssh_set_positions_frac(ssh_ctx* h, const double* s_hi, const double* s_lo) {
+  if (!h || !s_hi) { set_error("ssh_set_positions_frac: NULL argument"); return SSH_EINVAL; }
+  return stage_and_upload(h, s_hi, s_lo, false);
+}
+
+ssh_status ssh_get_positions_frac(ssh_ctx* h, double* s_hi, double* s_lo) {
+  if (!h) { set_error("ssh_get_positions_frac: NULL context"); return SSH_EINVAL; }
+  ssh::Ctx& c = h->c;
+  if (!c.have_positions) { set_error("ssh_get_positions_frac: no positions set"); return SSH_EINVAL; }
+  const int64_t N = c.N;
+  const int d = c.d;
+  double* hs = h->h_stage;
+  double* ls = h->h_stage + (size_t)d * N;
+  cudaSetDevice(c.device);
+  SSH_CUDA(cudaMemcpyAsync(hs, c.s_hi.p, sizeof(double) * d * N, cudaMemcpyDeviceToHost, c.stream), "download positions");
+  SSH_CUDA(cudaMemcpyAsync(ls, c.s_lo.p, sizeof(double) * d * N, cudaMemcpyDeviceToHost, c.stream), "download positions");
+  SSH_CUDA(cudaStreamSynchronize(c.stream), "download positions");
+  for (int64_t j = 0; j < N; j++)
+    for (int a = 0; a < d; a++) {
+      if (s_hi) s_hi[j * d + a] = hs[a * N + j];
+      if (s_lo) s_lo[j * d + a] = ls[a * N + j];
+    }
+  return SSH_OK;
+}
+
+ssh_status ssh_eval(ssh_ctx* h, int prec, int want_force) {
+  if (!h) { set_error("ssh_eval: NULL context"); return SSH_EINVAL; }
+  ssh::Ctx& c = h->c;
+  if (prec < SSH_FP64 || prec > SSH_FX) { set_error("ssh_eval: unknown precision"); return SSH_EINVAL; }
+  if (!c.have_positions) { set_error("ssh_eval: no positions set"); return SSH_EINVAL; }
+  cudaSetDevice(c.device);
+  cudaError_t e = ssh::eval_phi_grad(&c, prec, want_force != 0);
+  if (e != cudaSuccess) return cuda_fail(e, "ssh_eval: launch");
+  c.have_result = true;
+  c.last_prec = prec;
+  c.last_force = want_force != 0;
+  return SSH_OK;
+}
+
+ssh_status ssh_get_results(ssh_ctx* h, double phi[2], double smax[2], double* F_hi, double* F_lo) {
+  if (!h) { set_error("ssh_get_results: NULL context"); return SSH_EINVAL; }
+  ssh::Ctx& c = h->c;
+  if (!c.have_result) { set_error("ssh_get_results: no evaluation yet"); return SSH_EINVAL; }
+  if ((F_hi || F_lo) && !c.last_force) { set_error("ssh_get_results: last evaluation had no force"); return SSH_EINVAL; }
+  cudaSetDevice(c.device);
+  double sc[ssh::kScCount];
+  SSH_CUDA(cudaMemcpyAsync(sc, c.scal.p, sizeof(sc), cudaMemcpyDeviceToHost, c.stream), "download scalars");
+  const int64_t N = c.N;
+  const int d = c.d;
+  double* hs = h->h_stage;
+  double* ls = h->h_stage + (size_t)d * N;
+  if (F_hi || F_lo) {
+    SSH_CUDA(cudaMemcpyAsync(hs, c.F_hi.p, sizeof(double) * d * N, cudaMemcpyDeviceToHost, c.stream), "download force");
+    SSH_CUDA(cudaMemcpyAsync(ls, c.F_lo.p, sizeof(double) * d * N, cudaMemcpyDeviceToHost, c.stream), "download force");
+  }
+  SSH_CUDA(cudaStreamSynchronize(c.stream), "ssh_get_results");
+  if (phi) { phi[0] = sc[ssh::kScPhiHi]; phi[1] = sc[ssh::kScPhiLo]; }
+  if (smax) { smax[0] = sc[ssh::kScSmaxHi]; smax[1] = sc[ssh::kScSmaxLo]; }
+  bool bad = !isfinite(sc[ssh::kScPhiHi]) || !isfinite(sc[ssh::kScSmaxHi]);
+  if (F_hi || F_lo) {
+    for (int64_t j = 0; j < N; j++)
+      for (int a = 0; a < d; a++) {
+        double fh = hs[a * N + j], fl = ls[a * N + j];
+        bad = bad || !isfinite(fh);
+        if (F_hi) F_hi[j * d + a] = fh;
+        if (F_lo) F_lo[j * d + a] = fl;
+      }
+  }
+  if (bad) { set_error("non-finite energy, S_max or force"); return SSH_ENAN; }
+  return SSH_OK;
+}
+
+ssh_status ssh_energy_grad(ssh_ctx* h, int prec, double phi[2], double smax[2], double* F_hi, double* F_lo) {
+  ssh_status s = ssh_eval(h, prec, (F_hi || F_lo) ? 1 : 0);
+  if (s != SSH_OK) return s;
+  return ssh_get_results(h, phi, smax, F_hi, F_lo);
+}
+
+ssh_status ssh_get_ntilde(ssh_ctx* h, double* C_hi, double* C_lo, double* S_hi, double* S_lo) {
+  if (!h) { set_error("ssh_get_ntilde: NULL context"); return SSH_EINVAL; }
+  ssh::Ctx& c = h->c;
+  if (!c.have_result) { set_error("ssh_get_ntilde: no evaluation yet"); return SSH_EINVAL; }
+  const int64_t M = c.M;
+  if (M == 0) return SSH_OK;
+  std::vector<double> buf((size_t)4 * M);
+  cudaSetDevice(c.device);
+  const ssh::DevBuf* src[4] = {&c.C_hi, &c.C_lo, &c.S_hi, &c.S_lo};
+  for (int i = 0; i < 4; i++)
+    SSH_CUDA(cudaMemcpyAsync(buf.data() + (size_t)i * M, src[i]->p, sizeof(double) * M, cudaMemcpyDeviceToHost, c.stream),
+             "download n~");
+  SSH_CUDA(cudaStreamSynchronize(c.stream), "download n~");
+  double* dst[4] = {C_hi, C_lo, S_hi, S_lo};
+  for (int i = 0; i < 4; i++) {
+    if (!dst[i]) continue;
+    for (int64_t k = 0; k < M; k++) dst[i][c.ks.int2pub[k]] = buf[(size_t)i * M + k];
+  }
+  return SSH_OK;
+}
+
+ssh_status ssh_prof_enable(ssh_ctx* h, int on) {
+  if (!h) { set_error("ssh_prof_enable: NULL context"); return SSH_EINVAL; }
+  ssh::Ctx& c = h->c;
+  cudaSetDevice(c.device);
+  cudaError_t e = ssh::prof_collect(&c);
+  if (e != cudaSuccess) return cuda_fail(e, "ssh_prof_enable");
+  c.prof.on = on != 0;
+  for (int i = 0; i < ssh::kKCount; i++) { c.prof.ms[i] = 0; c.prof.launches[i] = 0; }
+  return SSH_OK;
+}
+
+ssh_status ssh_prof_read(ssh_ctx* h, int n, double* ms, int64_t* launches) {
+  if (!h || n < 0) { set_error("ssh_prof_read: bad arguments"); return SSH_EINVAL; }
+  ssh::Ctx& c = h->c;
+  cudaSetDevice(c.device);
+  cudaError_t e = ssh::prof_collect(&c);
+  if (e != cudaSuccess) return cuda_fail(e, "ssh_prof_read");
+  for (int i = 0; i < n && i < ssh::kKCount; i++) {
+    if (ms) ms[i] = c.prof.ms[i];
+    if (launches) launches[i] = c.prof.launches[i];
+  }
+  return SSH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,612 @@
+// kernels.cu -- the Phi + force hot path (Eqs. ntilde, energy, smax, force of arXiv:2304.09139) on sm_103a.
+//
+// One evaluation is seven launches on the context's stream:
+//   k_twiddle     per-particle power tables T[row][j] = e^{2 pi i m s_{j,axis}} for the rows of the
+//                 table layout (prefix components, high and low digit of the last component)
+//   k_ntilde      n~(k) = sum_j e^{2 pi i n.s_j}: a thread owns up to 4 consecutive k of one column; a
+//                 block stages, per chunk of particles, the products G = prod_prefix T * T_hi and the 32
+//                 low-digit rows in shared memory, so each (k, particle) pair costs one complex multiply
+//                 and one accumulate.  Particle splits write partial sums.
+//   k_nt_reduce   fixed-order sum of the partials, |n~|^2, per-block Phi / max partials
+//   k_finalize    Phi, S_max, and the power-of-two scale of (C, S) for the fixed-point force
+//   k_coef        (C_k, S_k) in the arithmetic of the force kernel
+//   k_force       F_j = (4 pi / L) sum_k n [C sin(th) - S cos(th)]: a thread owns a particle and walks the
+//                 columns; along a column the phase advances by one multiply with T_lo[1]; per column the
+//                 sums A = sum w, B = sum A give sum (n_lo + i) w = n_lo A + (len A - B)
+//   k_f_reduce    fixed-order sum over column splits, scaling to physical units
+// Every reduction has a fixed order, so results are bitwise reproducible run to run.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "fx.cuh"
+#include "ssh_internal.h"
+
+#define SSH_TABLE_QUAL __device__
+#include "gen/tables.h"
+
+namespace ssh {
+
+// ------------------------------------------------------------------------------------------------ policies
+
+struct PolF64 {
+  using Tab = double2;  // (cos, sin)
+  using Ph = double2;
+  struct Acc { double re, im; };
+  using Real = double;
+  using RAcc = double;
+  using Coef = double2;  // (C, S)
+  static constexpr int kIdx = SSH_FP64;
+  static __device__ __forceinline__ Ph load(const Tab* p) { return __ldg(p); }
+  static __device__ __forceinline__ Ph one() { return make_double2(1.0, 0.0); }
+  static __device__ __forceinline__ Ph mul(const Ph& a, const Ph& b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+  }
+  static __device__ __forceinline__ void acc_zero(Acc& a) { a.re = 0; a.im = 0; }
+  static __device__ __forceinline__ void acc_add(Acc& a, const Ph& z) { a.re += z.x; a.im += z.y; }
+  static __device__ __forceinline__ void acc_add_acc(Acc& a, const Acc& b) { a.re += b.re; a.im += b.im; }
+  static __device__ __forceinline__ void acc_to_dd(const Acc& a, dd* c, dd* s) { *c = dd_make(a.re); *s = dd_make(a.im); }
+  static __device__ __forceinline__ Real w(const Coef& c, const Ph& z) { return fma(c.x, z.y, -c.y * z.x); }
+  static __device__ __forceinline__ void rzero(RAcc& a) { a = 0; }
+  static __device__ __forceinline__ void radd(RAcc& a, const Real& x) { a += x; }
+  static __device__ __forceinline__ void radd_r(RAcc& a, const RAcc& x) { a += x; }
+  static __device__ __forceinline__ RAcc rmul_int(const RAcc& a, int k) { return a * (double)k; }
+  static __device__ __forceinline__ RAcc rsub(const RAcc& a, const RAcc& b) { return a - b; }
+  static __device__ __forceinline__ dd r_to_dd(const RAcc& a) { return dd_make(a); }
+  static __device__ __forceinline__ Coef make_coef(dd c, dd s, int /*e*/) { return make_double2(c.hi + c.lo, s.hi + s.lo); }
+  static __device__ __forceinline__ Tab phasor(int32_t m, double sh, double sl) {
+    double p = (double)m * sh;
+    double e = fma((double)m, sh, -p);
+    double t = (p - floor(p)) + (e + (double)m * sl);
+    double sv, cv;
+    sincospi(2.0 * t, &sv, &cv);
+    return make_double2(cv, sv);
+  }
+};
+
+struct PolDD {
+  using Tab = ddc;
+  using Ph = ddc;
+  using Acc = ddc;
+  using Real = dd;
+  using RAcc = dd;
+  using Coef = ddc;  // (C, S)
+  static constexpr int kIdx = SSH_DD;
+  static __device__ __forceinline__ Ph load(const Tab* p) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+    double2 a = __ldg(q), b = __ldg(q + 1);
+    return ddc_make(dd_make(a.x, a.y), dd_make(b.x, b.y));
+  }
+  static __device__ __forceinline__ Ph one() { return ddc_make(dd_make(1.0), dd_make(0.0)); }
+  static __device__ __forceinline__ Ph mul(const Ph& a, const Ph& b) { return ddc_mul(a, b); }
+  static __device__ __forceinline__ void acc_zero(Acc& a) { a = ddc_make(dd_make(0.0), dd_make(0.0)); }
+  static __device__ __forceinline__ void acc_add(Acc& a, const Ph& z) { a = ddc_add(a, z); }
+  static __device__ __forceinline__ void acc_add_acc(Acc& a, const Acc& b) { a = ddc_add(a, b); }
+  static __device__ __forceinline__ void acc_to_dd(const Acc& a, dd* c, dd* s) { *c = a.re; *s = a.im; }
+  static __device__ __forceinline__ Real w(const Coef& c, const Ph& z) {
+    return dd_add(dd_mul(c.re, z.im), dd_neg(dd_mul(c.im, z.re)));
+  }
+  static __device__ __forceinline__ void rzero(RAcc& a) { a = dd_make(0.0); }
+  static __device__ __forceinline__ void radd(RAcc& a, const Real& x) { a = dd_add(a, x); }
+  static __device__ __forceinline__ void radd_r(RAcc& a, const RAcc& x) { a = dd_add(a, x); }
+  static __device__ __forceinline__ RAcc rmul_int(const RAcc& a, int k) { return dd_mul_d(a, (double)k); }
+  static __device__ __forceinline__ RAcc rsub(const RAcc& a, const RAcc& b) { return dd_sub(a, b); }
+  static __device__ __forceinline__ dd r_to_dd(const RAcc& a) { return a; }
+  static __device__ __forceinline__ Coef make_coef(dd c, dd s, int /*e*/) { return ddc_make(c, s); }
+  static __device__ __forceinline__ Tab phasor(int32_t m, double sh, double sl) {
+    dd p = two_prod((double)m, sh);  // exact
+    dd t = dd_make(p.hi - floor(p.hi), p.lo);
+    t = dd_add_d(two_sum(t.hi, t.lo), (double)m * sl);
+    return dd_sincos_turns_tab(t, SSH_DD_TAB_A, SSH_DD_TAB_B, SSH_DD_INV_FACT, SSH_DD_2PI);
+  }
+};
+
+struct FxAcc {
+  q160 re, im;
+};
+
+struct PolFX {
+  using Tab = fxc;
+  using Ph = fxc;
+  using Acc = FxAcc;
+  using Real = q128;
+  using RAcc = q160;
+  using Coef = fxc;  // (C, S) * 2^-e in Q2.126
+  static constexpr int kIdx = SSH_FX;
+  static __device__ __forceinline__ Ph load(const Tab* p) {
+    const uint4* q = reinterpret_cast<const uint4*>(p);
+    uint4 a = __ldg(q), b = __ldg(q + 1);
+    fxc z;
+    z.re.w[0] = a.x; z.re.w[1] = a.y; z.re.w[2] = a.z; z.re.w[3] = a.w;
+    z.im.w[0] = b.x; z.im.w[1] = b.y; z.im.w[2] = b.z; z.im.w[3] = b.w;
+    return z;
+  }
+  static __device__ __forceinline__ Ph one() { fxc z; z.re = q126_one(); z.im = q128_zero(); return z; }
+  static __device__ __forceinline__ Ph mul(const Ph& a, const Ph& b) { return fxc_mul(a, b); }
+  static __device__ __forceinline__ void acc_zero(Acc& a) { a.re = q160_zero(); a.im = q160_zero(); }
+  static __device__ __forceinline__ void acc_add(Acc& a, const Ph& z) { q160_add(a.re, z.re); q160_add(a.im, z.im); }
+  static __device__ __forceinline__ void acc_add_acc(Acc& a, const Acc& b) { q160_add160(a.re, b.re); q160_add160(a.im, b.im); }
+  static __device__ __forceinline__ void acc_to_dd(const Acc& a, dd* c, dd* s) {
+    q160_to_dd(a.re, &c->hi, &c->lo);
+    q160_to_dd(a.im, &s->hi, &s->lo);
+  }
+  static __device__ __forceinline__ Real w(const Coef& c, const Ph& z) {
+    return q128_sub(mul126(c.re, z.im), mul126(c.im, z.re));
+  }
+  static __device__ __forceinline__ void rzero(RAcc& a) { a = q160_zero(); }
+  static __device__ __forceinline__ void radd(RAcc& a, const Real& x) { q160_add(a, x); }
+  static __device__ __forceinline__ void radd_r(RAcc& a, const RAcc& x) { q160_add160(a, x); }
+  static __device__ __forceinline__ RAcc rmul_int(const RAcc& a, int k) { return q160_mul_int(a, k); }
+  static __device__ __forceinline__ RAcc rsub(const RAcc& a, const RAcc& b) { return q160_sub160(a, b); }
+  static __device__ __forceinline__ dd r_to_dd(const RAcc& a) { dd r; q160_to_dd(a, &r.hi, &r.lo); return r; }
+  static __device__ __forceinline__ Coef make_coef(dd c, dd s, int e) {
+    fxc z;
+    z.re = q126_from_dd(ldexp(c.hi, -e), ldexp(c.lo, -e));
+    z.im = q126_from_dd(ldexp(s.hi, -e), ldexp(s.lo, -e));
+    return z;
+  }
+  static __device__ __forceinline__ Tab phasor(int32_t m, double sh, double sl) {
+    q128 u = turns_from_dd(sh, sl);
+    unsigned __int128 uu = ((unsigned __int128)u.w[3] << 96) | ((unsigned __int128)u.w[2] << 64) |
+                           ((unsigned __int128)u.w[1] << 32) | (unsigned __int128)u.w[0];
+    unsigned __int128 t = uu * (unsigned __int128)(__int128)m;  // exact phase modulo one turn
+    q128 tq = q128_from_i128((__int128)t);
+    q128 piq;
+#pragma unroll
+    for (int i = 0; i < 4; i++) piq.w[i] = SSH_FX_PI_Q3_125[i];
+    return fx_sincos_turns(tq, SSH_FX_TAB_A, SSH_FX_TAB_B, piq, SSH_FX_INV_FACT);
+  }
+};
+
+template <class T>
+__device__ __forceinline__ void st_tab(T* dst, const T& v) { *dst = v; }
+
+// ------------------------------------------------------------------------------------------------ kernels
+
+template <class P>
+__global__ void k_twiddle(const TabRow* __restrict__ rows, int nrows, const double* __restrict__ s_hi,
+                          const double* __restrict__ s_lo, int64_t N, int64_t Npad, typename P::Tab* __restrict__ tab) {
+  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)nrows * Npad) return;
+  int row = (int)(idx / Npad);
+  int64_t j = idx - (int64_t)row * Npad;
+  typename P::Tab v;
+  if (j < N) {
+    TabRow r = rows[row];
+    v = P::phasor(r.m, s_hi[r.axis * N + j], s_lo[r.axis * N + j]);
+  } else {
+    v = P::one();
+  }
+  tab[idx] = v;
+}
+
+template <class P>
+__global__ void __launch_bounds__(kNtThreads) k_ntilde(const NtSlot* __restrict__ slots, const NtBlock* __restrict__ blocks,
+                                                       const int32_t* __restrict__ g_rows,
+                                                       const typename P::Tab* __restrict__ tab, int64_t ld, int64_t N,
+                                                       int64_t plen, int pchunk, int lo_base, int64_t M,
+                                                       typename P::Acc* __restrict__ part) {
+  using Tab = typename P::Tab;
+  using Ph = typename P::Ph;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Tab* sm = reinterpret_cast<Tab*>(smem_raw);
+  const NtBlock blk = blocks[blockIdx.x];
+  const int64_t j_begin = (int64_t)blockIdx.y * plen;
+  const int64_t j_end = min(N, j_begin + plen);
+  const int nrow = blk.ng + kDigit;
+  const int stride = nrow | 1;
+  const bool active = (int)threadIdx.x < blk.nslots;
+  NtSlot sl;
+  if (active) sl = slots[blk.slot0 + threadIdx.x];
+  else { sl.k0 = 0; sl.cnt = 0; sl.g = 0; sl.r0 = 0; }
+  typename P::Acc acc[kSlotK];
+#pragma unroll
+  for (int i = 0; i < kSlotK; i++) P::acc_zero(acc[i]);
+  for (int64_t j0 = j_begin; j0 < j_end; j0 += pchunk) {
+    const int pc = (int)min((int64_t)pchunk, j_end - j0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < nrow * pc; idx += blockDim.x) {
+      const int row = idx / pc, jj = idx - row * pc;
+      const int64_t j = j0 + jj;
+      Ph v;
+      if (row < blk.ng) {
+        const int32_t* gr = g_rows + (int64_t)(blk.g0 + row) * kMaxDim;
+        v = P::load(tab + (int64_t)gr[kMaxDim - 1] * ld + j);
+#pragma unroll
+        for (int a = 0; a < kMaxDim - 1; a++)
+          if (gr[a] >= 0) v = P::mul(v, P::load(tab + (int64_t)gr[a] * ld + j));
+      } else {
+        v = P::load(tab + (int64_t)(lo_base + row - blk.ng) * ld + j);
+      }
+      sm[jj * stride + row] = v;
+    }
+    __syncthreads();
+    if (active) {
+      for (int jj = 0; jj < pc; jj++) {
+        const Tab* rp = sm + jj * stride;
+        const Ph G = rp[sl.g];
+        const Tab* lp = rp + blk.ng + sl.r0;
+#pragma unroll
+        for (int i = 0; i < kSlotK; i++) {
+          if (i < sl.cnt) P::acc_add(acc[i], P::mul(G, lp[i]));
+        }
+      }
+    }
+  }
+  if (active) {
+#pragma unroll
+    for (int i = 0; i < kSlotK; i++)
+      if (i < sl.cnt) part[(int64_t)blockIdx.y * M + sl.k0 + i] = acc[i];
+  }
+}
+
+struct RedPart {  // per-block partials of the density reduction
+  double phi_hi, phi_lo, a2max_hi, a2max_lo, cmax, pad0, pad1, pad2;
+};
+
+__device__ __forceinline__ void red_combine(RedPart& a, const RedPart& b) {
+  dd s = dd_add(dd_make(a.phi_hi, a.phi_lo), dd_make(b.phi_hi, b.phi_lo));
+  a.phi_hi = s.hi;
+  a.phi_lo = s.lo;
+  if (dd_gt(dd_make(b.a2max_hi, b.a2max_lo), dd_make(a.a2max_hi, a.a2max_lo))) {
+    a.a2max_hi = b.a2max_hi;
+    a.a2max_lo = b.a2max_lo;
+  }
+  a.cmax = fmax(a.cmax, b.cmax);
+}
+
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ void block_reduce(RedPart& v, RedPart* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) {
+      RedPart o = sh[threadIdx.x + s];
+      RedPart m = sh[threadIdx.x];
+      red_combine(m, o);
+      sh[threadIdx.x] = m;
+    }
+    __syncthreads();
+  }
+  v = sh[0];
+}
+
+template <class P>
+__global__ void __launch_bounds__(kRedThreads) k_nt_reduce(const typename P::Acc* __restrict__ part, int psplit, int64_t M,
+                                                           double* C_hi, double* C_lo, double* S_hi, double* S_lo,
+                                                           RedPart* blk) {
+  __shared__ RedPart sh[kRedThreads];
+  int64_t k = (int64_t)blockIdx.x * kRedThreads + threadIdx.x;
+  RedPart v = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (k < M) {
+    typename P::Acc a = part[k];
+    for (int p = 1; p < psplit; p++) P::acc_add_acc(a, part[(int64_t)p * M + k]);
+    dd c, s;
+    P::acc_to_dd(a, &c, &s);
+    C_hi[k] = c.hi;
+    C_lo[k] = c.lo;
+    S_hi[k] = s.hi;
+    S_lo[k] = s.lo;
+    dd a2 = dd_add(dd_sqr(c), dd_sqr(s));
+    v.phi_hi = a2.hi;
+    v.phi_lo = a2.lo;
+    v.a2max_hi = a2.hi;
+    v.a2max_lo = a2.lo;
+    v.cmax = fmax(fabs(c.hi), fabs(s.hi));
+  }
+  block_reduce(v, sh);
+  if (threadIdx.x == 0) blk[blockIdx.x] = v;
+}
+
+// scal[kScPhiHi..] as listed in ssh_internal.h.  Scale exponent e: |C|, |S| < 2^(e-1).
+__global__ void __launch_bounds__(kRedThreads) k_finalize(const RedPart* __restrict__ blk, int nblk, double N, double* scal) {
+  __shared__ RedPart sh[kRedThreads];
+  RedPart v = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int i = threadIdx.x; i < nblk; i += kRedThreads) red_combine(v, blk[i]);
+  block_reduce(v, sh);
+  if (threadIdx.x == 0) {
+    scal[kScPhiHi] = v.phi_hi;
+    scal[kScPhiLo] = v.phi_lo;
+    dd sm = dd_div(dd_make(v.a2max_hi, v.a2max_lo), dd_make(N));
+    scal[kScSmaxHi] = sm.hi;
+    scal[kScSmaxLo] = sm.lo;
+    scal[kScCmax] = v.cmax;
+    scal[kScScaleExp] = v.cmax > 0 ? (double)(ilogb(v.cmax) + 2) : 0.0;
+    scal[kScA2MaxHi] = v.a2max_hi;
+    scal[kScA2MaxLo] = v.a2max_lo;
+  }
+}
+
+template <class P>
+__global__ void k_coef(const double* __restrict__ C_hi, const double* __restrict__ C_lo, const double* __restrict__ S_hi,
+                       const double* __restrict__ S_lo, const double* __restrict__ scal, int64_t M,
+                       typename P::Coef* __restrict__ coef) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= M) return;
+  int e = (int)scal[kScScaleExp];
+  coef[k] = P::make_coef(dd_make(C_hi[k], C_lo[k]), dd_make(S_hi[k], S_lo[k]), e);
+}
+
+__device__ __forceinline__ int floordiv_d(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+template <class P>
+__global__ void __launch_bounds__(kForceThreads) k_force(const FCol* __restrict__ cols, const int32_t* __restrict__ fsplit,
+                                                         const typename P::Coef* __restrict__ coef,
+                                                         const typename P::Tab* __restrict__ tab, int64_t ld, int64_t N,
+                                                         int d, int hi_base, int qmin, int lo_base,
+                                                         typename P::RAcc* __restrict__ fpart) {
+  using Ph = typename P::Ph;
+  using RAcc = typename P::RAcc;
+  const int64_t j = (int64_t)blockIdx.x * kForceThreads + threadIdx.x;
+  const int64_t jj = j < N ? j : N - 1;
+  const int ks = blockIdx.y;
+  const Ph b = P::load(tab + (int64_t)(lo_base + 1) * ld + jj);
+  RAcc F[kMaxDim];
+#pragma unroll
+  for (int a = 0; a < kMaxDim; a++) P::rzero(F[a]);
+  const int c_end = fsplit[ks + 1];
+  for (int c = fsplit[ks]; c < c_end; c++) {
+    const FCol col = cols[c];
+    Ph G = P::one();
+    const bool hasG = d > 1;
+#pragma unroll
+    for (int a = 0; a < kMaxDim - 1; a++) {
+      if (a + 1 < d) {
+        Ph t = P::load(tab + (int64_t)col.rows[a] * ld + jj);
+        G = a > 0 ? P::mul(G, t) : t;
+      }
+    }
+    int q = floordiv_d(col.nlo, kDigit);
+    int r = col.nlo - q * kDigit;
+    Ph th = P::load(tab + (int64_t)(hi_base + q - qmin) * ld + jj);
+    Ph z = hasG ? P::mul(G, th) : th;
+    if (r != 0) z = P::mul(z, P::load(tab + (int64_t)(lo_base + r) * ld + jj));
+    RAcc A, B;
+    P::rzero(A);
+    P::rzero(B);
+    for (int i = 0; i < col.len; i++) {
+      if (i > 0) {
+        if (++r == kDigit) {  // re-anchor at each digit boundary
+          r = 0;
+          q++;
+          th = P::load(tab + (int64_t)(hi_base + q - qmin) * ld + jj);
+          z = hasG ? P::mul(G, th) : th;
+        } else {
+          z = P::mul(z, b);
+        }
+      }
+      const typename P::Coef cf = coef[col.k0 + i];
+      P::radd(A, P::w(cf, z));
+      P::radd_r(B, A);
+    }
+    const RAcc last = P::rsub(P::rmul_int(A, col.nlo + col.len), B);
+#pragma unroll
+    for (int a = 0; a < kMaxDim; a++) {
+      if (a + 1 < d) P::radd_r(F[a], P::rmul_int(A, col.pre[a < kMaxDim - 1 ? a : 0]));
+      else if (a + 1 == d) P::radd_r(F[a], last);
+    }
+  }
+  if (j < N) {
+#pragma unroll
+    for (int a = 0; a < kMaxDim; a++)
+      if (a < d) fpart[((int64_t)ks * d + a) * N + j] = F[a];
+  }
+}
+
+template <class P>
+__global__ void k_f_reduce(const typename P::RAcc* __restrict__ fpart, int ksplit, int64_t N, int d,
+                           const double* __restrict__ scal, dd pref, double* F_hi, double* F_lo) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // over d * N, [a][j]
+  if (i >= (int64_t)d * N) return;
+  typename P::RAcc s = fpart[i];
+  for (int k = 1; k < ksplit; k++) P::radd_r(s, fpart[(int64_t)k * d * N + i]);
+  dd f = dd_mul(P::r_to_dd(s), pref);
+  int e = P::kIdx == SSH_FX ? (int)scal[kScScaleExp] : 0;
+  F_hi[i] = ldexp(f.hi, e);
+  F_lo[i] = ldexp(f.lo, e);
+}
+
+// ------------------------------------------------------------------------------------------------ host side
+
+static size_t tab_bytes(int prec) { return prec == SSH_FP64 ? 16 : 32; }
+
+void setup_launch(Ctx* c) {
+  const int nblocks = (int)c->nt.blocks.size();
+  const int target = c->sm_count * 2;
+  for (int prec = 0; prec < 3; prec++) {
+    Launch& L = c->launch[prec];
+    int stride = (c->nt.max_ng + kDigit) | 1;
+    L.nt_stride = stride;
+    size_t budget = 96 * 1024;
+    int pchunk = (int)(budget / ((size_t)stride * tab_bytes(prec)));
+    pchunk = std::max(8, std::min(64, pchunk & ~7));
+    L.nt_pchunk = pchunk;
+    L.nt_smem = (size_t)pchunk * stride * tab_bytes(prec);
+    int ps = nblocks > 0 ? (target + nblocks - 1) / nblocks : 1;
+    int64_t max_ps = std::max<int64_t>(1, c->N / pchunk);
+    L.nt_psplit = (int)std::max<int64_t>(1, std::min<int64_t>(ps, max_ps));
+    int pblocks = (int)((c->N + kForceThreads - 1) / kForceThreads);
+    int kspl = (target + pblocks - 1) / pblocks;
+    kspl = std::max(1, std::min(kspl, (int)c->fp.cols.size()));
+    L.f_ksplit = kspl;
+  }
+}
+
+template <class P>
+static cudaError_t run_prec(Ctx* c, bool want_force) {
+  const int prec = P::kIdx;
+  const Launch& L = c->launch[prec];
+  cudaStream_t st = c->stream;
+  const int nrows = (int)c->tl.rows.size();
+  auto* tab = reinterpret_cast<typename P::Tab*>(c->tab.p);
+  {
+    int64_t total = (int64_t)nrows * c->Npad;
+    int thr = 128;
+    int64_t grid = (total + thr - 1) / thr;
+    prof_begin(c, kKTwiddle);
+    k_twiddle<P><<<(unsigned)grid, thr, 0, st>>>(reinterpret_cast<const TabRow*>(c->rows.p), nrows,
+                                                  (const double*)c->s_hi.p, (const double*)c->s_lo.p, c->N, c->Npad, tab);
+    prof_end(c);
+  }
+  if (c->M > 0) {
+    const int nb = (int)c->nt.blocks.size();
+    int64_t plen = (c->N + L.nt_psplit - 1) / L.nt_psplit;
+    plen = (plen + L.nt_pchunk - 1) / L.nt_pchunk * L.nt_pchunk;
+    int psplit = (int)((c->N + plen - 1) / plen);
+    cudaFuncSetAttribute(k_ntilde<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.nt_smem);
+    dim3 grid(nb, psplit);
+    prof_begin(c, kKNtilde);
+    k_ntilde<P><<<grid, kNtThreads, L.nt_smem, st>>>(
+        reinterpret_cast<const NtSlot*>(c->slots.p), reinterpret_cast<const NtBlock*>(c->blocks.p),
+        (const int32_t*)c->grows.p, tab, c->Npad, c->N, plen, L.nt_pchunk, c->tl.lo_base, c->M,
+        reinterpret_cast<typename P::Acc*>(c->part.p));
+    prof_end(c);
+    int rb = (int)((c->M + kRedThreads - 1) / kRedThreads);
+    prof_begin(c, kKNtReduce);
+    k_nt_reduce<P><<<rb, kRedThreads, 0, st>>>(reinterpret_cast<const typename P::Acc*>(c->part.p), psplit, c->M,
+                                               (double*)c->C_hi.p, (double*)c->C_lo.p, (double*)c->S_hi.p,
+                                               (double*)c->S_lo.p, reinterpret_cast<RedPart*>(c->blk.p));
+    prof_end(c);
+    prof_begin(c, kKFinalize);
+    k_finalize<<<1, kRedThreads, 0, st>>>(reinterpret_cast<const RedPart*>(c->blk.p), rb, (double)c->N,
+                                          (double*)c->scal.p);
+    prof_end(c);
+  } else {
+    cudaMemsetAsync(c->scal.p, 0, sizeof(double) * kScCount, st);
+  }
+  if (want_force) {
+    if (c->M > 0) {
+      int thr = 256;
+      prof_begin(c, kKCoef);
+      k_coef<P><<<(unsigned)((c->M + thr - 1) / thr), thr, 0, st>>>(
+          (const double*)c->C_hi.p, (const double*)c->C_lo.p, (const double*)c->S_hi.p, (const double*)c->S_lo.p,
+          (const double*)c->scal.p, c->M, reinterpret_cast<typename P::Coef*>(c->coef.p));
+      prof_end(c);
+      dim3 grid((unsigned)((c->N + kForceThreads - 1) / kForceThreads), L.f_ksplit);
+      const int32_t* fs = (const int32_t*)c->fsplit.p;  // one column split serves every precision
+      prof_begin(c, kKForce);
+      k_force<P><<<grid, kForceThreads, 0, st>>>(reinterpret_cast<const FCol*>(c->cols.p), fs,
+                                                  reinterpret_cast<const typename P::Coef*>(c->coef.p), tab, c->Npad,
+                                                  c->N, c->d, c->tl.hi_base, c->tl.qmin, c->tl.lo_base,
+                                                  reinterpret_cast<typename P::RAcc*>(c->fpart.p));
+      prof_end(c);
+      int64_t tot = (int64_t)c->d * c->N;
+      prof_begin(c, kKFReduce);
+      k_f_reduce<P><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
+          reinterpret_cast<const typename P::RAcc*>(c->fpart.p), L.f_ksplit, c->N, c->d, (const double*)c->scal.p,
+          c->pref, (double*)c->F_hi.p, (double*)c->F_lo.p);
+      prof_end(c);
+    } else {
+      cudaMemsetAsync(c->F_hi.p, 0, sizeof(double) * c->d * c->N, st);
+      cudaMemsetAsync(c->F_lo.p, 0, sizeof(double) * c->d * c->N, st);
+    }
+  }
+  return cudaGetLastError();
+}
+
+static cudaError_t dev_alloc(DevBuf* b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  b->bytes = bytes;
+  return cudaMalloc(&b->p, bytes);
+}
+
+template <class T>
+static cudaError_t upload(DevBuf* b, const std::vector<T>& v, cudaStream_t st) {
+  cudaError_t e = dev_alloc(b, sizeof(T) * v.size());
+  if (e != cudaSuccess || v.empty()) return e;
+  return cudaMemcpyAsync(b->p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st);
+}
+
+cudaError_t plan_upload(Ctx* c) {
+  cudaStream_t st = c->stream;
+  cudaError_t e;
+  setup_launch(c);
+  // column split for the force kernel: equal numbers of wavevectors per split (same for every precision;
+  // sized for the largest split count)
+  int ks = 1;
+  for (int p = 0; p < 3; p++) ks = std::max(ks, c->launch[p].f_ksplit);
+  for (int p = 0; p < 3; p++) c->launch[p].f_ksplit = ks;
+  c->f_split.assign(ks + 1, 0);
+  {
+    int ncol = (int)c->fp.cols.size();
+    int64_t per = (c->M + ks - 1) / std::max(1, ks);
+    int ci = 0;
+    for (int s = 1; s < ks; s++) {
+      int64_t target = per * s;
+      while (ci < ncol && c->fp.cols[ci].k0 < target) ci++;
+      c->f_split[s] = ci;
+    }
+    c->f_split[ks] = ncol;
+  }
+  if ((e = upload(&c->rows, c->tl.rows, st)) != cudaSuccess) return e;
+  if ((e = upload(&c->slots, c->nt.slots, st)) != cudaSuccess) return e;
+  if ((e = upload(&c->blocks, c->nt.blocks, st)) != cudaSuccess) return e;
+  if ((e = upload(&c->grows, c->nt.g_rows, st)) != cudaSuccess) return e;
+  if ((e = upload(&c->cols, c->fp.cols, st)) != cudaSuccess) return e;
+  if ((e = upload(&c->fsplit, c->f_split, st)) != cudaSuccess) return e;
+  size_t nd = (size_t)c->d * c->N;
+  if ((e = dev_alloc(&c->s_hi, nd * 8)) != cudaSuccess) return e;
+  if ((e = dev_alloc(&c->s_lo, nd * 8)) != cudaSuccess) return e;
+  if ((e = dev_alloc(&c->tab, (size_t)c->tl.rows.size() * c->Npad * kTabBytes)) != cudaSuccess) return e;
+  int max_ps = 1;
+  for (int p = 0; p < 3; p++) max_ps = std::max(max_ps, c->launch[p].nt_psplit);
+  if ((e = dev_alloc(&c->part, (size_t)max_ps * c->M * kAccBytes)) != cudaSuccess) return e;
+  for (DevBuf* b : {&c->C_hi, &c->C_lo, &c->S_hi, &c->S_lo})
+    if ((e = dev_alloc(b, (size_t)c->M * 8)) != cudaSuccess) return e;
+  if ((e = dev_alloc(&c->coef, (size_t)c->M * kTabBytes)) != cudaSuccess) return e;
+  c->n_red_blocks = (int)((c->M + kRedThreads - 1) / kRedThreads);
+  if ((e = dev_alloc(&c->blk, (size_t)std::max(1, c->n_red_blocks) * sizeof(RedPart))) != cudaSuccess) return e;
+  if ((e = dev_alloc(&c->scal, sizeof(double) * kScCount)) != cudaSuccess) return e;
+  if ((e = dev_alloc(&c->fpart, (size_t)ks * nd * kRAccBytes)) != cudaSuccess) return e;
+  if ((e = dev_alloc(&c->F_hi, nd * 8)) != cudaSuccess) return e;
+  if ((e = dev_alloc(&c->F_lo, nd * 8)) != cudaSuccess) return e;
+  cudaMemsetAsync(c->scal.p, 0, sizeof(double) * kScCount, st);
+  return cudaGetLastError();
+}
+
+void prof_begin(Ctx* c, int id) {
+  if (!c->prof.on) return;
+  ProfRec r;
+  r.id = id;
+  if (!c->prof.pool.empty()) { r.e0 = c->prof.pool.back(); c->prof.pool.pop_back(); }
+  else cudaEventCreate(&r.e0);
+  if (!c->prof.pool.empty()) { r.e1 = c->prof.pool.back(); c->prof.pool.pop_back(); }
+  else cudaEventCreate(&r.e1);
+  cudaEventRecord(r.e0, c->stream);
+  c->prof.pending.push_back(r);
+}
+
+void prof_end(Ctx* c) {
+  if (!c->prof.on || c->prof.pending.empty()) return;
+  cudaEventRecord(c->prof.pending.back().e1, c->stream);
+}
+
+cudaError_t prof_collect(Ctx* c) {
+  if (c->prof.pending.empty()) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return e;
+  for (ProfRec& r : c->prof.pending) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) {
+      c->prof.ms[r.id] += ms;
+      c->prof.launches[r.id] += 1;
+    }
+    c->prof.pool.push_back(r.e0);
+    c->prof.pool.push_back(r.e1);
+  }
+  c->prof.pending.clear();
+  return cudaSuccess;
+}
+
+cudaError_t eval_phi_grad(Ctx* c, int prec, bool want_force) {
+  switch (prec) {
+    case SSH_FP64: return run_prec<PolF64>(c, want_force);
+    case SSH_DD: return run_prec<PolDD>(c, want_force);
+    case SSH_FX: return run_prec<PolFX>(c, want_force);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace ssh

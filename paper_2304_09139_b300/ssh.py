@@ -1,0 +1,201 @@
+"""Python binding of the C ABI in include/ssh.h (ctypes, argument marshalling only).
+
+Every step of the computation runs in the CUDA library libssh.so next to this file.  There is no
+fallback: if the library is missing or cannot be loaded, every call raises.  Build it with
+``python -m paper_2304_09139_b300._build`` (or ``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+FP64, DD, FX = 0, 1, 2
+PREC_NAMES = {FP64: "fp64", DD: "dd", FX: "fx"}
+KERNELS = ["twiddle", "ntilde", "nt_reduce", "finalize", "coef", "force", "f_reduce", "fire"]
+
+_STATUS = {0: "SSH_OK", 1: "SSH_EINVAL", 2: "SSH_ENOMEM", 3: "SSH_ECUDA", 4: "SSH_ENAN", 5: "SSH_ENOTCONV",
+           6: "SSH_ETIMEOUT", 7: "SSH_EBUSY", 8: "SSH_ENOTFOUND"}
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libssh.so")
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SshError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+P = ctypes.POINTER
+c_d, c_i64, c_i32, c_int, c_vp = ctypes.c_double, ctypes.c_int64, ctypes.c_int32, ctypes.c_int, ctypes.c_void_p
+
+
+def _sig(lib, name, res, args):
+    f = getattr(lib, name)
+    f.restype = res
+    f.argtypes = args
+
+
+def load():
+    """Load libssh.so (raises OSError if it is missing: there is no CPU fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise OSError(f"CUDA library not built: {LIB_PATH} is missing "
+                              "(run python -m paper_2304_09139_b300._build)")
+            lib = ctypes.CDLL(LIB_PATH)
+            _sig(lib, "ssh_version", ctypes.c_char_p, [])
+            _sig(lib, "ssh_last_error", ctypes.c_char_p, [])
+            _sig(lib, "ssh_create", c_int, [c_int, c_i64, c_d, c_d, c_d, c_vp, P(c_vp)])
+            _sig(lib, "ssh_destroy", None, [c_vp])
+            _sig(lib, "ssh_get_dims", c_int, [c_vp, P(c_int), P(c_i64), P(c_i64), P(c_d)])
+            _sig(lib, "ssh_get_kset", c_int, [c_vp, P(c_i64), P(c_i32)])
+            _sig(lib, "ssh_kset_build", c_int, [c_int, c_i64, c_d, c_d, c_d, c_i64, P(c_i32), P(c_i64)])
+            _sig(lib, "ssh_set_stream", c_int, [c_vp, c_vp])
+            _sig(lib, "ssh_sync", c_int, [c_vp])
+            _sig(lib, "ssh_set_positions", c_int, [c_vp, P(c_d), P(c_d)])
+            _sig(lib, "ssh_set_positions_frac", c_int, [c_vp, P(c_d), P(c_d)])
+            _sig(lib, "ssh_get_positions_frac", c_int, [c_vp, P(c_d), P(c_d)])
+            _sig(lib, "ssh_energy_grad", c_int, [c_vp, c_int, P(c_d), P(c_d), P(c_d), P(c_d)])
+            _sig(lib, "ssh_eval", c_int, [c_vp, c_int, c_int])
+            _sig(lib, "ssh_get_results", c_int, [c_vp, P(c_d), P(c_d), P(c_d), P(c_d)])
+            _sig(lib, "ssh_get_ntilde", c_int, [c_vp, P(c_d), P(c_d), P(c_d), P(c_d)])
+            _sig(lib, "ssh_prof_enable", c_int, [c_vp, c_int])
+            _sig(lib, "ssh_prof_read", c_int, [c_vp, c_int, P(c_d), P(c_i64)])
+            _lib = lib
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise SshError(status, load().ssh_last_error().decode(errors="replace"))
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(P(c_d))
+
+
+def version() -> str:
+    return load().ssh_version().decode()
+
+
+def kset_build(d: int, N: int, L: float, chi: float = 0.0, K: float = 0.0) -> np.ndarray:
+    """Host-only wavevector set (public order) with the library's own rules; no GPU needed."""
+    lib = load()
+    M = c_i64(0)
+    _check(lib.ssh_kset_build(d, N, L, chi, K, 0, None, ctypes.byref(M)))
+    out = np.zeros((max(M.value, 1), d), dtype=np.int32)
+    _check(lib.ssh_kset_build(d, N, L, chi, K, M.value, out.ctypes.data_as(P(c_i32)), ctypes.byref(M)))
+    return out[:M.value].copy()
+
+
+def _rows(a, N, d):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(N, d)
+    return a
+
+
+class Context:
+    """One configuration (d, N, L, chi | K) resident on the GPU.  Wraps ssh_create / ssh_destroy."""
+
+    def __init__(self, d: int, N: int, L: float, chi: float = 0.0, K: float = 0.0, device: int = 0):
+        lib = load()
+        self._lib = lib
+        self._h = c_vp()
+        opts = (c_int * 8)(device, 0, 0, 0, 0, 0, 0, 0)
+        _check(lib.ssh_create(d, N, L, chi, K, ctypes.cast(opts, c_vp), ctypes.byref(self._h)))
+        dd_, NN, MM, LL = c_int(), c_i64(), c_i64(), c_d()
+        _check(lib.ssh_get_dims(self._h, ctypes.byref(dd_), ctypes.byref(NN), ctypes.byref(MM), ctypes.byref(LL)))
+        self.d, self.N, self.M, self.L = dd_.value, NN.value, MM.value, LL.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            self._lib.ssh_destroy(self._h)
+            self._h = c_vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def kset(self) -> np.ndarray:
+        out = np.zeros((max(self.M, 1), self.d), dtype=np.int32)
+        M = c_i64(0)
+        _check(self._lib.ssh_get_kset(self._h, ctypes.byref(M), out.ctypes.data_as(P(c_i32))))
+        return out[:self.M].copy()
+
+    def set_stream(self, stream_ptr: int | None):
+        _check(self._lib.ssh_set_stream(self._h, c_vp(stream_ptr) if stream_ptr else None))
+
+    def sync(self):
+        _check(self._lib.ssh_sync(self._h))
+
+    def set_positions_frac(self, s_hi, s_lo=None):
+        s_hi = _rows(s_hi, self.N, self.d)
+        s_lo = _rows(s_lo, self.N, self.d)
+        _check(self._lib.ssh_set_positions_frac(self._h, _dp(s_hi), _dp(s_lo)))
+
+    def set_positions(self, r_hi, r_lo=None):
+        r_hi = _rows(r_hi, self.N, self.d)
+        r_lo = _rows(r_lo, self.N, self.d)
+        _check(self._lib.ssh_set_positions(self._h, _dp(r_hi), _dp(r_lo)))
+
+    def positions_frac(self):
+        hi = np.zeros((self.N, self.d))
+        lo = np.zeros((self.N, self.d))
+        _check(self._lib.ssh_get_positions_frac(self._h, _dp(hi), _dp(lo)))
+        return hi, lo
+
+    def eval(self, prec: int, want_force: bool = True):
+        _check(self._lib.ssh_eval(self._h, prec, 1 if want_force else 0))
+
+    def results(self, want_force: bool = True):
+        phi = np.zeros(2)
+        smax = np.zeros(2)
+        Fh = np.zeros((self.N, self.d)) if want_force else None
+        Fl = np.zeros((self.N, self.d)) if want_force else None
+        _check(self._lib.ssh_get_results(self._h, _dp(phi), _dp(smax), _dp(Fh), _dp(Fl)))
+        return {"phi": phi, "smax": smax, "F_hi": Fh, "F_lo": Fl}
+
+    def energy_grad(self, prec: int, want_force: bool = True):
+        """Phi, S_max (dd pairs) and F (physical units, hi and lo [N, d]) through ssh_energy_grad."""
+        phi = np.zeros(2)
+        smax = np.zeros(2)
+        Fh = np.zeros((self.N, self.d)) if want_force else None
+        Fl = np.zeros((self.N, self.d)) if want_force else None
+        _check(self._lib.ssh_energy_grad(self._h, prec, _dp(phi), _dp(smax), _dp(Fh), _dp(Fl)))
+        return {"phi": phi, "smax": smax, "F_hi": Fh, "F_lo": Fl}
+
+    def prof_enable(self, on: bool = True):
+        _check(self._lib.ssh_prof_enable(self._h, 1 if on else 0))
+
+    def prof_read(self):
+        """{kernel name: (total ms, launches)} since the last prof_enable."""
+        ms = np.zeros(16)
+        n = np.zeros(16, dtype=np.int64)
+        _check(self._lib.ssh_prof_read(self._h, 16, _dp(ms), n.ctypes.data_as(P(c_i64))))
+        return {KERNELS[i]: (float(ms[i]), int(n[i])) for i in range(len(KERNELS)) if n[i] > 0}
+
+    def ntilde(self):
+        """(C, S) of the last evaluation, each an [M, 2] (hi, lo) array in public order."""
+        ch, cl, sh, sl = (np.zeros(self.M) for _ in range(4))
+        _check(self._lib.ssh_get_ntilde(self._h, _dp(ch), _dp(cl), _dp(sh), _dp(sl)))
+        return np.stack([ch, cl], 1), np.stack([sh, sl], 1)

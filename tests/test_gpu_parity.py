@@ -1,0 +1,180 @@
+"""GPU parity: n~(k), Phi, S_max and F from the CUDA library against the binary128 oracle.
+
+Eqs. ntilde, energy, structurefactor/smax and force of arXiv:2304.09139.  Every comparison is element by
+element on the same seeded inputs, with normwise bounds (near a ground state n~ ~ 0, so relative error of
+Phi alone is ill-conditioned):
+  |dC_k|, |dS_k| <= tol N
+  |dPhi|         <= tol * 4 max(Phi, M N)
+  |dS_max|       <= tol * 4 (2 sqrt(N S_max) + 1)
+  |dF_{j,a}|     <= tol * (4 pi / L) sum_k |n_a| (|C_k| + |S_k| + sqrt N)
+with tol = 1e-28 for the double-double and fixed-point arithmetics and 1e-13 for plain FP64.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2304_09139_b300 import ssh, synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = {ssh.FP64: 1e-13, ssh.DD: 1e-28, ssh.FX: 1e-28}
+PRECS = [ssh.FP64, ssh.DD, ssh.FX]
+NTHREADS = os.cpu_count() or 8
+
+
+def ddv(x):
+    return x[..., 0] + x[..., 1]
+
+
+def ddiff(a, b):
+    """a - b for dd pairs, accurate when a ~ b: (hi - hi) is exact by Sterbenz, then the lo words."""
+    return (a[..., 0] - b[..., 0]) + (a[..., 1] - b[..., 1])
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2304_09139_b300 import _build
+    _build.build()
+    ssh.load()
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return True
+
+
+def check_parity(ctx, s_hi, s_lo, L, prec, ref, n, label=""):
+    tol = TOL[prec]
+    N, d = s_hi.shape
+    M = len(n)
+    r = ctx.energy_grad(prec)
+    C, S = ctx.ntilde()
+    # n~
+    assert np.all(np.abs(ddiff(C, ref["C"])) <= tol * N), (label, np.abs(ddiff(C, ref["C"])).max())
+    assert np.all(np.abs(ddiff(S, ref["S"])) <= tol * N), (label, np.abs(ddiff(S, ref["S"])).max())
+    # Phi, S_max
+    phi_ref = ddv(ref["phi"])
+    assert abs(ddiff(r["phi"], ref["phi"])) <= tol * 4 * max(phi_ref, M * N), (label, r["phi"], ref["phi"])
+    sm = ddv(ref["smax"])
+    assert abs(ddiff(r["smax"], ref["smax"])) <= tol * 4 * (2 * math.sqrt(N * sm) + 1), (label, r["smax"], ref["smax"])
+    # F (physical units)
+    Cabs = np.abs(ddv(ref["C"])) + np.abs(ddv(ref["S"])) + math.sqrt(N)
+    scale = tol * 4 * math.pi / L * (np.abs(n).astype(np.float64) * Cabs[:, None]).sum(0)  # [d]
+    F = np.stack([r["F_hi"], r["F_lo"]], -1)
+    err = np.abs(ddiff(F, ref["F"]))
+    assert np.all(err <= scale[None, :]), (label, (err / scale[None, :]).max())
+    return r
+
+
+CASES = [
+    # (label, d, N, L, chi, K, seed)
+    ("small_d2", 2, 100, 1.0, 0.30, 0.0, 1),
+    ("ragged_d2", 2, 333, 333 ** 0.5, 0.45, 0.0, 7),
+    ("d1", 1, 257, 257.0, 0.45, 0.0, 8),
+    ("d3", 3, 300, 300 ** (1 / 3), 0.40, 0.0, 9),
+    ("d3_kmode", 3, 150, 4.0, 0.0, 2 * math.pi * 3.3 / 4.0, 10),
+    ("d4", 4, 120, 120 ** 0.25, 0.3, 0.0, 11),
+    ("wide_d2", 2, 2000, 2000 ** 0.5, 0.45, 0.0, 12),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_parity_against_oracle(built, oracle_mod, case):
+    label, d, N, L, chi, K, seed = case
+    s = synth.positions(seed, N, d)
+    # a few coordinates at the edges of the cell and a non-zero low word
+    s[0, 0] = 0.0
+    s[-1, -1] = 1.0 - 2.0 ** -53
+    s_lo = np.zeros_like(s)
+    s_lo[1::3, 0] = 2.0 ** -60
+    ctx = ssh.Context(d, N, L, chi=chi, K=K)
+    n = ctx.kset()
+    assert np.array_equal(n, oracle_mod.kset(d, N, L, chi=chi, K=K))
+    ref = oracle_mod.phi_grad(s, s_lo, n, L, want_cs=True, nthreads=NTHREADS)
+    ctx.set_positions_frac(s, s_lo)
+    for prec in PRECS:
+        check_parity(ctx, s, s_lo, L, prec, ref, n, label=f"{label}/{ssh.PREC_NAMES[prec]}")
+    ctx.close()
+
+
+def test_parity_medium_d2_full(built, oracle_mod):
+    """The d=2, N=10^4, chi=0.45 workload at full size: every output against the oracle."""
+    cfg = synth.MEDIUM_D2
+    s = synth.positions(cfg.seed, cfg.N, cfg.d)
+    ctx = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi)
+    n = ctx.kset()
+    ref = oracle_mod.phi_grad(s, None, n, cfg.L, want_cs=True, nthreads=NTHREADS)
+    ctx.set_positions_frac(s)
+    for prec in PRECS:
+        check_parity(ctx, s, None, cfg.L, prec, ref, n, label=f"medium/{ssh.PREC_NAMES[prec]}")
+
+
+def test_lattice_closed_form_on_gpu(built):
+    """N = q^d lattice points: n~(k) = 0 unless every n_a = 0 (mod q), where it is N (geometric sums)."""
+    from fractions import Fraction
+    q, d = 16, 2   # s = m / 16 is exact in binary
+    g = np.stack(np.meshgrid(np.arange(q) / q, np.arange(q) / q, indexing="ij"), -1).reshape(-1, d)
+    N = len(g)
+    ctx = ssh.Context(d, N, 1.0, K=2 * math.pi * 20.5)
+    n = ctx.kset()
+    ctx.set_positions_frac(g)
+    mult = np.all(n % q == 0, axis=1)
+    for prec in PRECS:
+        ctx.energy_grad(prec)
+        C, S = ctx.ntilde()
+        tol = TOL[prec] * N
+        assert np.all(np.abs(ddv(C[~mult])) <= tol) and np.all(np.abs(ddv(S[~mult])) <= tol)
+        assert np.all(np.abs(ddv(C[mult]) - N) <= tol) and np.all(np.abs(ddv(S[mult])) <= tol)
+
+
+def test_single_particle_on_gpu(built):
+    """N = 1: |n~|^2 = 1 for every k, Phi = M, F = 0."""
+    ctx = ssh.Context(3, 1, 2.0, K=2 * math.pi * 4 / 2.0)
+    ctx.set_positions_frac(np.array([[0.1234, 0.5678, 0.9012]]))
+    for prec in PRECS:
+        r = ctx.energy_grad(prec)
+        assert abs(ddv(r["phi"]) - ctx.M) <= TOL[prec] * 4 * ctx.M
+        assert np.all(np.abs(r["F_hi"]) <= TOL[prec] * 1e3)
+
+
+def test_repeat_is_bitwise_identical(built):
+    """Fixed-order reductions: two evaluations of the same positions agree bit for bit."""
+    cfg = synth.MEDIUM_D2
+    s = synth.positions(cfg.seed, cfg.N, cfg.d)
+    ctx = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi)
+    ctx.set_positions_frac(s)
+    for prec in PRECS:
+        a = ctx.energy_grad(prec)
+        Ca, Sa = ctx.ntilde()
+        b = ctx.energy_grad(prec)
+        Cb, Sb = ctx.ntilde()
+        assert np.array_equal(a["phi"], b["phi"]) and np.array_equal(a["F_hi"], b["F_hi"])
+        assert np.array_equal(a["F_lo"], b["F_lo"]) and np.array_equal(Ca, Cb) and np.array_equal(Sa, Sb)
+
+
+def test_physical_positions_match_fractional(built):
+    """ssh_set_positions (r in [0, L), divided by L in dd) agrees with the exact fractional entry."""
+    d, N, L = 2, 500, 500 ** 0.5
+    s = synth.positions(77, N, d)
+    ctx = ssh.Context(d, N, L, chi=0.3)
+    ctx.set_positions_frac(s)
+    a = ctx.energy_grad(ssh.FX)
+    from fractions import Fraction
+    r_hi = s * L
+    r_lo = np.array([float(Fraction(x) * Fraction(L) - Fraction(y)) for x, y in zip(s.ravel(), r_hi.ravel())]).reshape(s.shape)
+    ctx.set_positions(r_hi, r_lo)
+    b = ctx.energy_grad(ssh.FX)
+    assert abs(ddiff(a["phi"], b["phi"])) <= 1e-26 * ctx.M * N
+
+
+def test_bad_inputs_raise(built):
+    ctx = ssh.Context(2, 10, 1.0, chi=0.3)
+    with pytest.raises(ssh.SshError):
+        ctx.energy_grad(ssh.FX)        # no positions yet
+    s = synth.positions(1, 10, 2)
+    s[3, 1] = float("nan")
+    with pytest.raises(ssh.SshError) as e:
+        ctx.set_positions_frac(s)
+    assert e.value.status == 4
+    with pytest.raises(ssh.SshError):
+        ctx.eval(7)
