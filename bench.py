@@ -1,0 +1,315 @@
+"""Throughput of the hot path: one FIRE step = Phi + force (+ minimiser update) on one configuration.
+
+Metric: (k, particle) pairs per second per Phi+grad, pairs = M * N (one of the two sums of
+Eqs. ntilde / force, counted as the paper does: "2 calculations -- each with MN terms").
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fx|dd|fp64] [--impl ours|reference]
+
+Default workload: d = 2, N = 10^4 uniform random points (SplitMix64 seed 2) in a periodic square at unit
+density (L = 100), chi = 0.45, so M = 8999.  Inputs are resident in HBM when the timed region starts;
+L2 (126 MB) is flushed between timed steps by writing a 256 MiB buffer, outside the step's events.
+Under torchrun every rank runs its own replica (independent configuration, seed 2 + rank): the path
+shards by configuration with no collective; value = pairs of all ranks / max over ranks of the time.
+
+--impl reference times the binary128 oracle (the only reference this method has) on the host cores,
+each step a bounded sample of the same workload: the first M/8 wavevectors, all N particles, both sums.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+# Algorithmic integer multiply-add (IMAD pipe) instructions per (k, particle) pair in the fixed-point
+# kernels: one truncated 128x128 product is 20 32-bit multiply-adds; the density kernel does one complex
+# product per pair (4 products), the force kernel one complex product (phase recurrence) plus the two
+# products of C sin - S cos.
+FX_IMAD_PER_PAIR = {"ntilde": 80, "force": 120}
+# Algorithmic FP64 instructions per pair on the double-double path (dd_mul = 8, dd_add = 20 flops as
+# written in dd.cuh): density = complex dd multiply (4 mul + 2 add = 72) + complex accumulate (2 add = 40);
+# force = complex multiply (72) + w = C sin - S cos (2 mul + 1 add = 36) + A += w, B += A (40).
+DD_FP64_PER_PAIR = {"ntilde": 112, "force": 148}
+F64_FP64_PER_PAIR = {"ntilde": 6, "force": 8}
+# Peaks derived from unit counts and the maximum SM clock (148 SMs, 2032 MHz): 64 IMAD lanes per SM per
+# clock; 2 FP64 FMA lanes per SM per clock (1.2 TFLOP/s).
+SM_COUNT, SM_MAX_MHZ = 148, 2032.0
+IMAD_PEAK = 64 * SM_COUNT * SM_MAX_MHZ * 1e6
+FP64_PEAK = 2 * SM_COUNT * SM_MAX_MHZ * 1e6
+
+WORKLOAD = dict(d=2, N=10_000, L=100.0, chi=0.45, seed=2)
+
+# DRAM bytes (read + write) per launch from one ncu capture of this workload (profiles/), valid only while
+# the kernel sources hash to the value recorded with them; otherwise the traffic is reported as null.
+NCU_TRAFFIC = {("fx", "force"): ("4b684e8da53d", 35_851_520 + 2_560),
+               ("fx", "ntilde"): ("4b684e8da53d", 36_560_896 + 2_560)}
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "fx.cuh", "dd.cuh"):
+        with open(os.path.join(ROOT, "paper_2304_09139_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--prec", default="fx", choices=["fx", "dd", "fp64"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_sample(N, d, L, chi, seed, frac_k=8, nthreads=0):
+    """One bounded oracle Phi+grad sample: the first M/frac_k wavevectors, all particles, both sums."""
+    import oracle
+    from paper_2304_09139_b300 import synth
+    oracle.build()
+    n = oracle.kset(d, N, L, chi=chi)
+    Ms = max(1, len(n) // frac_k)
+    s = synth.positions(seed, N, d)
+    t = time.perf_counter()
+    oracle.phi_grad(s, None, n[:Ms], L, nthreads=nthreads)
+    dt = time.perf_counter() - t
+    return Ms * N / dt, Ms, oracle.num_threads() if nthreads == 0 else nthreads
+
+
+def run_reference(args):
+    rank, world, local = dist_info()
+    if rank != 0:
+        return 0
+    w = WORKLOAD
+    times, pairs = [], None
+    for i in range(args.warmup + args.steps):
+        rate, Ms, cores = cpu_sample(w["N"], w["d"], w["L"], w["chi"], w["seed"])
+        if i >= args.warmup:
+            times.append(Ms * w["N"] / rate)
+            pairs = Ms * w["N"]
+    tot = sum(times)
+    value = pairs * len(times) / tot
+    sample = f"first {Ms} of M wavevectors x all {w['N']} particles, both sums, per step"
+    line = {"impl": "reference", "metric": "dd (k,particle) pairs/s per Phi+grad", "value": value,
+            "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": tot / len(times) * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "binary128", "data": "synthetic",
+            "config": {"workload": f"d=2 N={w['N']} L={w['L']} chi={w['chi']} uniform random seed {w['seed']}"},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_2304_09139_b300 import _build, ssh, synth
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+    dev = local
+    torch.cuda.set_device(dev)
+    _build.build()
+    prec = {"fx": ssh.FX, "dd": ssh.DD, "fp64": ssh.FP64}[args.prec]
+    w = WORKLOAD
+    ctx = ssh.Context(w["d"], w["N"], w["L"], chi=w["chi"], device=dev)
+    stream = torch.cuda.Stream(dev)          # a real (non-legacy) stream shared by torch and the library
+    ctx.set_stream(stream.cuda_stream)
+    torch.cuda.set_stream(stream)
+    s = synth.positions(w["seed"] + rank, w["N"], w["d"])
+    ctx.set_positions_frac(s)
+    pairs = ctx.M * ctx.N
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
+
+    def step():
+        ctx.eval(prec, True)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    ctx.prof_enable(True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with Clocks(dev) as clk:
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        t_wall = time.perf_counter()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        t_wall = time.perf_counter() - t_wall
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(step_ms)
+    prof = ctx.prof_read()
+    ctx.prof_enable(False)
+    if dist:
+        t = torch.tensor([tot_ms], device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = pairs * world * args.steps / (tot_ms / 1e3)
+    launches = sum(n for _, n in prof.values())
+
+    # roofline of the dominant kernel (largest share of device time in the timed region)
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_n) = dom
+    per_launch_s = dom_ms / 1e3 / dom_n
+    if prec == ssh.FX:
+        per_pair, peak, unit, bound, what = FX_IMAD_PER_PAIR, IMAD_PEAK, "IMAD/s", "alu", "IMAD"
+    elif prec == ssh.DD:
+        per_pair, peak, unit, bound, what = DD_FP64_PER_PAIR, FP64_PEAK, "FP64 instr/s", "fp64", "FP64"
+    else:
+        per_pair, peak, unit, bound, what = F64_FP64_PER_PAIR, FP64_PEAK, "FP64 instr/s", "fp64", "FP64"
+    roof = None
+    if dom_name in per_pair:
+        achieved = per_pair[dom_name] * pairs / per_launch_s
+        roof = {"bound": bound, "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None,
+                "traffic_unit": "bytes per launch (dram read + write, ncu)",
+                "peak_source": f"unit counts x max clock: {'64 IMAD' if what == 'IMAD' else '2 FP64 FMA'} "
+                               f"lanes/SM/clk x 148 SMs x 2032 MHz",
+                "per_kernel_ms": {k: v[0] / v[1] for k, v in prof.items()}}
+        tr = NCU_TRAFFIC.get((args.prec, dom_name))
+        if tr and tr[0] == kernel_source_hash():
+            roof["traffic"] = tr[1]
+
+    # end to end through the public API with host buffers (positions in, Phi / S_max / F out)
+    e2e_steps = max(3, args.steps // 2)
+    s2 = synth.positions(w["seed"] + 1000 + rank, w["N"], w["d"])
+    ctx.set_positions_frac(s2)
+    ctx.energy_grad(prec)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        ctx.set_positions_frac(s2 if i % 2 == 0 else s)
+        ctx.energy_grad(prec)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    h2d = 2 * 8 * w["d"] * w["N"]
+    d2h = 2 * 8 * w["d"] * w["N"] + 16 * 8
+
+    variants = {}
+    if not args.no_variants and rank == 0:
+        for name, p in (("dd", ssh.DD), ("fp64", ssh.FP64), ("fx", ssh.FX)):
+            if p == prec:
+                continue
+            ctx.eval(p)
+            ctx.sync()
+            t0 = time.perf_counter()
+            reps = 3
+            for _ in range(reps):
+                ctx.eval(p)
+            ctx.sync()
+            variants[name] = pairs / ((time.perf_counter() - t0) / reps)
+
+    line = {"metric": "dd (k,particle) pairs/s per Phi+grad", "value": value, "unit": "pairs/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fx": "q2.126 fixed point (4 x int32 limbs)", "dd": "double-double (2 x f64)",
+                      "fp64": "f64"}[args.prec],
+            "data": "synthetic",
+            "config": {"workload": f"d={w['d']} N={w['N']} L={w['L']} chi={w['chi']} M={ctx.M}, uniform random "
+                                   f"(SplitMix64 seed {w['seed']}+rank), one Phi+force evaluation per step",
+                       "l2": "flushed between timed steps (256 MiB write, outside the step events)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof, "gpu_launches": launches, "wall_s": t_wall,
+            "e2e": {"value": pairs / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "clocks": clk.summary(), "variants_pairs_per_s": variants}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, Ms, cores = cpu_sample(w["N"], w["d"], w["L"], w["chi"], w["seed"])
+        line["cpu_baseline"] = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                                "sample": f"one oracle Phi+grad over the first {Ms} of {ctx.M} wavevectors x all "
+                                          f"{w['N']} particles (binary128, OpenMP)"}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
