@@ -137,6 +137,28 @@ ssh_status ssh_get_ntilde(ssh_ctx* ctx, double* C_hi, double* C_lo, double* S_hi
 ssh_status ssh_prof_enable(ssh_ctx* ctx, int on);
 ssh_status ssh_prof_read(ssh_ctx* ctx, int n, double* ms, int64_t* launches);
 
+/*
+ * Allocation-free collective density, for callers that cannot allocate device memory: code running inside
+ * another framework's memory pool or arena, inside a CUDA-graph stream capture, or in a loop that forbids
+ * allocation after start-up.  The paper has no counterpart; it is a service of this library.
+ *
+ * Computes C_k + i S_k = sum_j exp(2 pi i n_k.s_j) for k = 0..M-1 in 128-bit fixed point, like SSH_FX,
+ * with every pointer a DEVICE pointer owned by the caller: s_hi, s_lo fractional positions [N][d]
+ * row-major (s_lo may be NULL), n the wavevector indices [M][d] int32, outputs C_hi, C_lo, S_hi, S_lo [M]
+ * (dd), all in the order of n.  Work is enqueued on `stream` (a cudaStream_t, NULL = legacy default
+ * stream) and the call returns without synchronising.
+ *
+ * Memory: it calls no cudaMalloc / cudaFree.  Its working memory is one fixed 8 MiB device array per
+ * device, present for the life of the process; calls need N*d*16 (rounded up to 256) + M*40 bytes of it
+ * and larger ones are rejected with SSH_EINVAL.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream capture.  Every call on a device
+ * shares the array: calls whose kernels may overlap on the GPU (other streams, other host threads) race
+ * and must be serialised by the caller.
+ * Errors: SSH_EINVAL (arguments, size), SSH_ECUDA (no current device, launch failure).
+ */
+ssh_status ssh_ntilde_noalloc(int d, int64_t N, int64_t M, const double* s_hi, const double* s_lo, const int32_t* n,
+                              double* C_hi, double* C_lo, double* S_hi, double* S_lo, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,6 +68,8 @@ def load():
             _sig(lib, "ssh_get_ntilde", c_int, [c_vp, P(c_d), P(c_d), P(c_d), P(c_d)])
             _sig(lib, "ssh_prof_enable", c_int, [c_vp, c_int])
             _sig(lib, "ssh_prof_read", c_int, [c_vp, c_int, P(c_d), P(c_i64)])
+            _sig(lib, "ssh_ntilde_noalloc", c_int, [c_int, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
+                                                   c_vp])
             _lib = lib
     return _lib
 
@@ -93,6 +95,13 @@ def kset_build(d: int, N: int, L: float, chi: float = 0.0, K: float = 0.0) -> np
     out = np.zeros((max(M.value, 1), d), dtype=np.int32)
     _check(lib.ssh_kset_build(d, N, L, chi, K, M.value, out.ctypes.data_as(P(c_i32)), ctypes.byref(M)))
     return out[:M.value].copy()
+
+
+def ntilde_noalloc(d: int, N: int, M: int, s_hi_ptr: int, s_lo_ptr: int | None, n_ptr: int, C_hi_ptr: int,
+                   C_lo_ptr: int, S_hi_ptr: int, S_lo_ptr: int, stream_ptr: int | None = None):
+    """ssh_ntilde_noalloc with raw device pointers (allocation-free n~(k); enqueued, not synchronised)."""
+    _check(load().ssh_ntilde_noalloc(d, N, M, s_hi_ptr, s_lo_ptr, n_ptr, C_hi_ptr, C_lo_ptr, S_hi_ptr, S_lo_ptr,
+                                     stream_ptr))
 
 
 def _rows(a, N, d):
