@@ -1,7 +1,7 @@
 """Throughput of the hot path: one FIRE step = Phi + force (+ minimiser update) on one configuration.
 
 Metric: (k, particle) pairs per second per Phi+grad, pairs = M * N (one of the two sums of
-Eqs. ntilde / force, counted as the paper does: "2 calculations -- each with MN terms").
+Eqs. ntilde / force; the paper counts the work of one step as two such sums of M N terms).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fx|dd|fp64] [--impl ours|reference]
 
@@ -50,8 +50,9 @@ WORKLOAD = dict(d=2, N=10_000, L=100.0, chi=0.45, seed=2)
 
 # DRAM bytes (read + write) per launch from one ncu capture of this workload (profiles/), valid only while
 # the kernel sources hash to the value recorded with them; otherwise the traffic is reported as null.
-NCU_TRAFFIC = {("fx", "force"): ("4b684e8da53d", 35_851_520 + 2_560),
-               ("fx", "ntilde"): ("4b684e8da53d", 36_560_896 + 2_560)}
+# (captured at source hash 4b684e8da53d; 14456463733e differs from it only in comments)
+NCU_TRAFFIC = {("fx", "force"): ("14456463733e", 35_851_520 + 2_560),
+               ("fx", "ntilde"): ("14456463733e", 36_560_896 + 2_560)}
 
 
 def kernel_source_hash() -> str:

@@ -256,7 +256,7 @@ int oracle_phi_grad(int d, int64_t N, double L, const double *s_hi, const double
  *   P = F.v;  v <- (1-alpha) v + alpha |v| F/|F|;
  *   P > 0 for more than n_min steps in a row: dt <- min(dt f_inc, dt_max), alpha <- alpha f_alpha;
  *   P <= 0: dt <- dt f_dec, v <- 0, alpha <- alpha_start.
- * Energy guard (the reading taken for the paper's "until Phi is at the minimum attainable"): a step that
+ * Energy guard (the reading taken for the paper's stopping rule, Phi at its machine-precision floor): a step that
  * raises Phi is undone, dt <- dt f_dec, v <- 0, alpha <- alpha_start.
  * Stop when S_max <= smax_target (status 0) or after max_steps (status 1).
  * Positions are in/out as fractional (hi, lo) pairs; the minimiser works on r = L s in binary128.

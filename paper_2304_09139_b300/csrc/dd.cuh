@@ -1,6 +1,6 @@
 // dd.cuh -- double-double ("double-word") arithmetic for host and device.
 //
-// The paper evaluates the energy and force "with tunable precision using double-doubles" (Simulations);
+// The paper evaluates the energy and force in double-double arithmetic (Simulations);
 // a dd value is an unevaluated sum hi + lo of two doubles with |lo| <= ulp(hi)/2, about 106 significant
 // bits.  The building blocks follow the published algorithms:
 //   two_sum        Knuth's TwoSum, 6 flops, exact: a + b = s + e

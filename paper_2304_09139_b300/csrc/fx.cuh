@@ -1,8 +1,8 @@
 // fx.cuh -- 128-bit fixed-point arithmetic on the integer pipes, the B300 form of "dd precision".
 //
 // On this GPU the FP64 pipe issues about 1.6 FMA per clock per SM while the integer multiply-add pipe
-// issues 64 and the ALU pipes 128, so the double-double sums of the paper (Simulations: "tunable precision
-// using double-doubles") are carried in the integer units instead:
+// issues 64 and the ALU pipes 128, so the sums the paper carries in double-double arithmetic (Simulations)
+// are carried in the integer units instead:
 //   * positions are unsigned Q0.128 fractions of the box (s = u / 2^128), so the phase of k = 2 pi n / L,
 //     t = n.s mod 1, is an exact integer product that wraps modulo 2^128 -- argument reduction is free;
 //   * phasors, tables and scaled densities are signed two's-complement Q2.126 (value = X / 2^126,
