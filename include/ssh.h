@@ -128,6 +128,58 @@ ssh_status ssh_get_results(ssh_ctx* ctx, double phi[2], double smax[2], double* 
 ssh_status ssh_get_ntilde(ssh_ctx* ctx, double* C_hi, double* C_lo, double* S_hi, double* S_lo);
 
 /*
+ * Minimisation (Simulations: FIRE of Bitzek et al. 2006 on Phi, with the paper's stopping rule read as
+ * "S_max at or below a target").  Parameters; zero fields take the defaults that ssh_min_defaults writes.
+ *   dt0, dt_max            time steps in physical units (defaults dt_max = 1/sqrt(2 N max|k|^2), dt0 = dt_max/10)
+ *   alpha_start, f_alpha, f_inc, f_dec, n_min   FIRE constants (defaults 0.1, 0.99, 1.1, 0.5, 5)
+ *   n_stages, stage_prec   precision ladder, e.g. {SSH_FP64, SSH_DD} (default {SSH_FP64, SSH_FX}); a stage
+ *                          ends when S_max <= stage_floor[s] or S_max has not halved in stall_window[s]
+ *                          steps; the last stage ends only at the target, the step cap or a stall
+ *   max_steps, smax_target step cap (default 200000) and convergence target (default 1e-36)
+ *   chunk                  steps between host checks of the device status word (default 64)
+ *   max_seconds            wall-time limit, 0 = none
+ */
+typedef struct {
+  double dt0, dt_max, alpha_start, f_alpha, f_inc, f_dec;
+  int n_min;
+  int n_stages;
+  int stage_prec[3];
+  int pad0;
+  double stage_floor[3];
+  int64_t stall_window[3];
+  int64_t max_steps;
+  double smax_target;
+  int64_t chunk;
+  double max_seconds;
+} ssh_min_params;
+
+typedef struct {
+  int status;              /* SSH_OK (converged), SSH_ENOTCONV, SSH_ENAN, SSH_ETIMEOUT */
+  int final_prec;          /* precision of the last stage run */
+  int stages_used;
+  int pad0;
+  int64_t steps;           /* FIRE steps including rejected ones */
+  int64_t stage_steps[3];
+  int64_t rejected;        /* steps undone by the energy guard */
+  double smax[2], phi[2];  /* accepted S_max and Phi (dd) in the final precision */
+  double dt;               /* final time step */
+  double wall_s, stage_wall_s[3];
+} ssh_min_result;
+
+/* Fill p with the defaults for this context (see ssh_min_params). */
+ssh_status ssh_min_defaults(const ssh_ctx* ctx, ssh_min_params* p);
+
+/*
+ * Minimise Phi from the current positions with FIRE on the device (velocity update, step acceptance,
+ * convergence test and precision switch all run in kernels; the host only replays a CUDA graph of steps
+ * and reads a status word between chunks).  An energy guard undoes any step that raises Phi (dt halves,
+ * v = 0).  On return the context holds the accepted positions (ssh_get_positions_frac).  p may be NULL
+ * (defaults); res may be NULL.  Returns SSH_OK when S_max <= smax_target, SSH_ENOTCONV on the step cap or
+ * a stall of the last stage, SSH_ENAN, SSH_ETIMEOUT (max_seconds), SSH_EINVAL, SSH_ECUDA.
+ */
+ssh_status ssh_minimize(ssh_ctx* ctx, const ssh_min_params* p, ssh_min_result* res);
+
+/*
  * Event profiler (tracing).  When enabled, every kernel the context launches is bracketed by a CUDA event
  * pair on the context's stream; ssh_prof_read synchronises the stream and returns, per kernel id, the
  * summed device time in milliseconds and the launch count since the last ssh_prof_enable call.

@@ -3,6 +3,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -79,6 +80,7 @@ ssh_status ssh_create(int d, int64_t N, double L, double chi, double K, const ss
   // 4 pi / L as dd
   dd four_pi = dd_make(2.0 * SSH_DD_2PI[0], 2.0 * SSH_DD_2PI[1]);
   c.pref = dd_div(four_pi, dd_make(L));
+  c.inv_L = dd_div(dd_make(1.0), dd_make(L));
   cudaError_t e = cudaSetDevice(c.device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) { delete h; return cuda_fail(e, "ssh_create: device/stream"); }
@@ -101,6 +103,7 @@ void ssh_destroy(ssh_ctx* h) {
   ssh::Ctx& c = h->c;
   cudaSetDevice(c.device);
   if (c.stream) cudaStreamSynchronize(c.stream);
+  ssh::fire_free(&c);
   for (ssh::DevBuf* b : {&c.s_hi, &c.s_lo, &c.rows, &c.slots, &c.blocks, &c.grows, &c.cols, &c.fsplit, &c.tab, &c.part,
                          &c.C_hi, &c.C_lo, &c.S_hi, &c.S_lo, &c.coef, &c.blk, &c.scal, &c.fpart, &c.F_hi, &c.F_lo})
     free_buf(*b);
@@ -294,6 +297,71 @@ ssh_status ssh_get_ntilde(ssh_ctx* h, double* C_hi, double* C_lo, double* S_hi, 
     for (int64_t k = 0; k < M; k++) dst[i][c.ks.int2pub[k]] = buf[(size_t)i * M + k];
   }
   return SSH_OK;
+}
+
+ssh_status ssh_min_defaults(const ssh_ctx* h, ssh_min_params* p) {
+  if (!h || !p) { set_error("ssh_min_defaults: NULL argument"); return SSH_EINVAL; }
+  const ssh::Ctx& c = h->c;
+  memset(p, 0, sizeof *p);
+  double k2 = c.ks.k2max > 0 ? c.ks.k2max : 1.0;
+  p->dt_max = 1.0 / sqrt(2.0 * (double)c.N * k2);
+  p->dt0 = p->dt_max / 10.0;
+  p->alpha_start = 0.1;
+  p->f_alpha = 0.99;
+  p->f_inc = 1.1;
+  p->f_dec = 0.5;
+  p->n_min = 5;
+  p->n_stages = 2;
+  p->stage_prec[0] = SSH_FP64;
+  p->stage_prec[1] = SSH_FX;
+  p->stage_prec[2] = SSH_FX;
+  p->stage_floor[0] = 1e-24;
+  p->stall_window[0] = 200;
+  p->stall_window[1] = 5000;
+  p->stall_window[2] = 5000;
+  p->max_steps = 200000;
+  p->smax_target = 1e-36;
+  p->chunk = 64;
+  p->max_seconds = 0;
+  return SSH_OK;
+}
+
+ssh_status ssh_minimize(ssh_ctx* h, const ssh_min_params* pin, ssh_min_result* res) {
+  if (!h) { set_error("ssh_minimize: NULL context"); return SSH_EINVAL; }
+  ssh::Ctx& c = h->c;
+  if (!c.have_positions) { set_error("ssh_minimize: no positions set"); return SSH_EINVAL; }
+  ssh_min_params d;
+  ssh_min_defaults(h, &d);
+  ssh_min_params p = pin ? *pin : d;
+  // zero fields take defaults
+  if (p.dt_max <= 0) p.dt_max = d.dt_max;
+  if (p.dt0 <= 0) p.dt0 = std::min(d.dt0, p.dt_max);
+  if (p.alpha_start <= 0) p.alpha_start = d.alpha_start;
+  if (p.f_alpha <= 0) p.f_alpha = d.f_alpha;
+  if (p.f_inc <= 0) p.f_inc = d.f_inc;
+  if (p.f_dec <= 0) p.f_dec = d.f_dec;
+  if (p.n_min <= 0) p.n_min = d.n_min;
+  if (p.n_stages <= 0) {
+    p.n_stages = d.n_stages;
+    for (int i = 0; i < 3; i++) { p.stage_prec[i] = d.stage_prec[i]; p.stage_floor[i] = d.stage_floor[i]; }
+  }
+  for (int i = 0; i < 3; i++)
+    if (p.stall_window[i] <= 0) p.stall_window[i] = d.stall_window[i];
+  if (p.max_steps <= 0) p.max_steps = d.max_steps;
+  if (p.smax_target <= 0) p.smax_target = d.smax_target;
+  if (p.chunk <= 0) p.chunk = d.chunk;
+  if (p.n_stages > 3 || !(p.dt0 > 0) || !(p.dt_max >= p.dt0) || !(p.f_dec < 1) || !(p.f_inc >= 1) ||
+      !(p.alpha_start < 1) || !(p.f_alpha <= 1)) {
+    set_error("ssh_minimize: inconsistent parameters");
+    return SSH_EINVAL;
+  }
+  for (int i = 0; i < p.n_stages; i++)
+    if (p.stage_prec[i] < SSH_FP64 || p.stage_prec[i] > SSH_FX) {
+      set_error("ssh_minimize: unknown stage precision");
+      return SSH_EINVAL;
+    }
+  cudaSetDevice(c.device);
+  return ssh::minimize(&c, &p, res);
 }
 
 ssh_status ssh_prof_enable(ssh_ctx* h, int on) {

@@ -107,19 +107,25 @@ SSH_HD dd dd_div(dd x, dd y) {
 
 SSH_HD double dd_to_d(dd x) { return x.hi + x.lo; }
 
-// x - floor(x) for a normalised dd, result in [0, 1) (up to the lo word's rounding).
+// x - floor(x) for a normalised dd: a value in [0, 1).  The integer part is removed with TwoSum, which is
+// exact even when x.hi is a small negative number (there hi - floor(hi) = hi + 1 would round).  The result
+// may have hi = 1.0 with lo < 0 (a value just below one).
 SSH_HD dd dd_frac(dd x) {
   double fh = floor(x.hi);
-  dd r = x;
-  r.hi -= fh;  // exact: x.hi and fh share the exponent range
-  if (r.hi == 0.0) {
-    double fl = floor(r.lo);
-    r.lo -= fl;
-  }
-  r = fast_two_sum(r.hi, r.lo);
-  if (r.hi < 0.0) r = dd_add_d(r, 1.0);
-  if (r.hi >= 1.0) r = dd_add_d(r, -1.0);
+  dd r = two_sum(x.hi, -fh);  // exact
+  r = dd_add_d(r, x.lo);
+  if (r.hi < 0.0 || (r.hi == 0.0 && r.lo < 0.0)) r = dd_add_d(r, 1.0);
+  if (r.hi > 1.0 || (r.hi == 1.0 && r.lo >= 0.0)) r = dd_add_d(r, -1.0);
   return r;
+}
+
+// frac(m (sh + sl)) in turns for an integer m: m * sh is split exactly with TwoProd, its integer part is
+// removed exactly, and m * sl (below 2^-53 |m sh|) is added.  The phase of k = 2 pi n / L at fractional
+// position s is the sum of these over the axes.
+SSH_HD dd dd_turns_times(int m, double sh, double sl) {
+  dd p = two_prod((double)m, sh);
+  dd t = dd_frac(p);
+  return dd_add_d(t, (double)m * sl);
 }
 
 SSH_HD int dd_lt(dd a, dd b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }

@@ -221,9 +221,12 @@ __device__ __forceinline__ q128 q128_from_i128(__int128 v) {
 
 // Fractional position (hi + lo, any real; only the value mod 1 matters) as an unsigned Q0.128 turn.
 __device__ __forceinline__ q128 turns_from_dd(double hi, double lo) {
-  hi = hi - floor(hi);
-  // hi * 2^128 can exceed the signed range: scale by 2^127, then double in unsigned (wrapping) arithmetic
-  unsigned __int128 v = (unsigned __int128)d2i128_scaled(hi, 127) * 2u + (unsigned __int128)d2i128_scaled(lo, 128);
+  // remove the integer part exactly (hi - floor(hi) can round for small negative hi): f + e = hi - floor(hi)
+  dd f = two_sum(hi, -floor(hi));
+  if (f.hi >= 1.0) f.hi -= 1.0;  // f.hi = 1 exactly when e < 0; one turn is zero modulo 2^128
+  // f.hi * 2^128 can exceed the signed range: scale by 2^127, then double in unsigned (wrapping) arithmetic
+  unsigned __int128 v = (unsigned __int128)d2i128_scaled(f.hi, 127) * 2u + (unsigned __int128)d2i128_scaled(f.lo, 128) +
+                        (unsigned __int128)d2i128_scaled(lo, 128);
   return q128_from_i128((__int128)v);
 }
 

@@ -95,9 +95,7 @@ struct PolDD {
   static __device__ __forceinline__ dd r_to_dd(const RAcc& a) { return a; }
   static __device__ __forceinline__ Coef make_coef(dd c, dd s, int /*e*/) { return ddc_make(c, s); }
   static __device__ __forceinline__ Tab phasor(int32_t m, double sh, double sl) {
-    dd p = two_prod((double)m, sh);  // exact
-    dd t = dd_make(p.hi - floor(p.hi), p.lo);
-    t = dd_add_d(two_sum(t.hi, t.lo), (double)m * sl);
+    dd t = dd_turns_times(m, sh, sl);
     return dd_sincos_turns_tab(t, SSH_DD_TAB_A, SSH_DD_TAB_B, SSH_DD_INV_FACT, SSH_DD_2PI);
   }
 };
@@ -165,8 +163,9 @@ __device__ __forceinline__ void st_tab(T* dst, const T& v) { *dst = v; }
 // ------------------------------------------------------------------------------------------------ kernels
 
 template <class P>
-__global__ void k_twiddle(const TabRow* __restrict__ rows, int nrows, const double* __restrict__ s_hi,
+__global__ void k_twiddle(const int* __restrict__ run, const TabRow* __restrict__ rows, int nrows, const double* __restrict__ s_hi,
                           const double* __restrict__ s_lo, int64_t N, int64_t Npad, typename P::Tab* __restrict__ tab) {
+  if (run && *run) return;  // a finished minimisation turns captured launches into no-ops
   int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)nrows * Npad) return;
   int row = (int)(idx / Npad);
@@ -182,11 +181,12 @@ __global__ void k_twiddle(const TabRow* __restrict__ rows, int nrows, const doub
 }
 
 template <class P>
-__global__ void __launch_bounds__(kNtThreads) k_ntilde(const NtSlot* __restrict__ slots, const NtBlock* __restrict__ blocks,
+__global__ void __launch_bounds__(kNtThreads) k_ntilde(const int* __restrict__ run, const NtSlot* __restrict__ slots, const NtBlock* __restrict__ blocks,
                                                        const int32_t* __restrict__ g_rows,
                                                        const typename P::Tab* __restrict__ tab, int64_t ld, int64_t N,
                                                        int64_t plen, int pchunk, int lo_base, int64_t M,
                                                        typename P::Acc* __restrict__ part) {
+  if (run && *run) return;  // a finished minimisation turns captured launches into no-ops
   using Tab = typename P::Tab;
   using Ph = typename P::Ph;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -274,9 +274,10 @@ __device__ __forceinline__ void block_reduce(RedPart& v, RedPart* sh) {
 }
 
 template <class P>
-__global__ void __launch_bounds__(kRedThreads) k_nt_reduce(const typename P::Acc* __restrict__ part, int psplit, int64_t M,
+__global__ void __launch_bounds__(kRedThreads) k_nt_reduce(const int* __restrict__ run, const typename P::Acc* __restrict__ part, int psplit, int64_t M,
                                                            double* C_hi, double* C_lo, double* S_hi, double* S_lo,
                                                            RedPart* blk) {
+  if (run && *run) return;  // a finished minimisation turns captured launches into no-ops
   __shared__ RedPart sh[kRedThreads];
   int64_t k = (int64_t)blockIdx.x * kRedThreads + threadIdx.x;
   RedPart v = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -301,7 +302,8 @@ __global__ void __launch_bounds__(kRedThreads) k_nt_reduce(const typename P::Acc
 }
 
 // scal[kScPhiHi..] as listed in ssh_internal.h.  Scale exponent e: |C|, |S| < 2^(e-1).
-__global__ void __launch_bounds__(kRedThreads) k_finalize(const RedPart* __restrict__ blk, int nblk, double N, double* scal) {
+__global__ void __launch_bounds__(kRedThreads) k_finalize(const int* __restrict__ run, const RedPart* __restrict__ blk, int nblk, double N, double* scal) {
+  if (run && *run) return;  // a finished minimisation turns captured launches into no-ops
   __shared__ RedPart sh[kRedThreads];
   RedPart v = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int i = threadIdx.x; i < nblk; i += kRedThreads) red_combine(v, blk[i]);
@@ -320,9 +322,10 @@ __global__ void __launch_bounds__(kRedThreads) k_finalize(const RedPart* __restr
 }
 
 template <class P>
-__global__ void k_coef(const double* __restrict__ C_hi, const double* __restrict__ C_lo, const double* __restrict__ S_hi,
+__global__ void k_coef(const int* __restrict__ run, const double* __restrict__ C_hi, const double* __restrict__ C_lo, const double* __restrict__ S_hi,
                        const double* __restrict__ S_lo, const double* __restrict__ scal, int64_t M,
                        typename P::Coef* __restrict__ coef) {
+  if (run && *run) return;  // a finished minimisation turns captured launches into no-ops
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= M) return;
   int e = (int)scal[kScScaleExp];
@@ -332,11 +335,12 @@ __global__ void k_coef(const double* __restrict__ C_hi, const double* __restrict
 __device__ __forceinline__ int floordiv_d(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
 template <class P>
-__global__ void __launch_bounds__(kForceThreads) k_force(const FCol* __restrict__ cols, const int32_t* __restrict__ fsplit,
+__global__ void __launch_bounds__(kForceThreads) k_force(const int* __restrict__ run, const FCol* __restrict__ cols, const int32_t* __restrict__ fsplit,
                                                          const typename P::Coef* __restrict__ coef,
                                                          const typename P::Tab* __restrict__ tab, int64_t ld, int64_t N,
                                                          int d, int hi_base, int qmin, int lo_base,
                                                          typename P::RAcc* __restrict__ fpart) {
+  if (run && *run) return;  // a finished minimisation turns captured launches into no-ops
   using Ph = typename P::Ph;
   using RAcc = typename P::RAcc;
   const int64_t j = (int64_t)blockIdx.x * kForceThreads + threadIdx.x;
@@ -396,8 +400,9 @@ __global__ void __launch_bounds__(kForceThreads) k_force(const FCol* __restrict_
 }
 
 template <class P>
-__global__ void k_f_reduce(const typename P::RAcc* __restrict__ fpart, int ksplit, int64_t N, int d,
+__global__ void k_f_reduce(const int* __restrict__ run, const typename P::RAcc* __restrict__ fpart, int ksplit, int64_t N, int d,
                            const double* __restrict__ scal, dd pref, double* F_hi, double* F_lo) {
+  if (run && *run) return;  // a finished minimisation turns captured launches into no-ops
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // over d * N, [a][j]
   if (i >= (int64_t)d * N) return;
   typename P::RAcc s = fpart[i];
@@ -446,7 +451,7 @@ static cudaError_t run_prec(Ctx* c, bool want_force) {
     int thr = 128;
     int64_t grid = (total + thr - 1) / thr;
     prof_begin(c, kKTwiddle);
-    k_twiddle<P><<<(unsigned)grid, thr, 0, st>>>(reinterpret_cast<const TabRow*>(c->rows.p), nrows,
+    k_twiddle<P><<<(unsigned)grid, thr, 0, st>>>(c->run_flag, reinterpret_cast<const TabRow*>(c->rows.p), nrows,
                                                   (const double*)c->s_hi.p, (const double*)c->s_lo.p, c->N, c->Npad, tab);
     prof_end(c);
   }
@@ -455,22 +460,21 @@ static cudaError_t run_prec(Ctx* c, bool want_force) {
     int64_t plen = (c->N + L.nt_psplit - 1) / L.nt_psplit;
     plen = (plen + L.nt_pchunk - 1) / L.nt_pchunk * L.nt_pchunk;
     int psplit = (int)((c->N + plen - 1) / plen);
-    cudaFuncSetAttribute(k_ntilde<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.nt_smem);
     dim3 grid(nb, psplit);
     prof_begin(c, kKNtilde);
     k_ntilde<P><<<grid, kNtThreads, L.nt_smem, st>>>(
-        reinterpret_cast<const NtSlot*>(c->slots.p), reinterpret_cast<const NtBlock*>(c->blocks.p),
+        c->run_flag,        reinterpret_cast<const NtSlot*>(c->slots.p), reinterpret_cast<const NtBlock*>(c->blocks.p),
         (const int32_t*)c->grows.p, tab, c->Npad, c->N, plen, L.nt_pchunk, c->tl.lo_base, c->M,
         reinterpret_cast<typename P::Acc*>(c->part.p));
     prof_end(c);
     int rb = (int)((c->M + kRedThreads - 1) / kRedThreads);
     prof_begin(c, kKNtReduce);
-    k_nt_reduce<P><<<rb, kRedThreads, 0, st>>>(reinterpret_cast<const typename P::Acc*>(c->part.p), psplit, c->M,
+    k_nt_reduce<P><<<rb, kRedThreads, 0, st>>>(c->run_flag, reinterpret_cast<const typename P::Acc*>(c->part.p), psplit, c->M,
                                                (double*)c->C_hi.p, (double*)c->C_lo.p, (double*)c->S_hi.p,
                                                (double*)c->S_lo.p, reinterpret_cast<RedPart*>(c->blk.p));
     prof_end(c);
     prof_begin(c, kKFinalize);
-    k_finalize<<<1, kRedThreads, 0, st>>>(reinterpret_cast<const RedPart*>(c->blk.p), rb, (double)c->N,
+    k_finalize<<<1, kRedThreads, 0, st>>>(c->run_flag, reinterpret_cast<const RedPart*>(c->blk.p), rb, (double)c->N,
                                           (double*)c->scal.p);
     prof_end(c);
   } else {
@@ -481,13 +485,13 @@ static cudaError_t run_prec(Ctx* c, bool want_force) {
       int thr = 256;
       prof_begin(c, kKCoef);
       k_coef<P><<<(unsigned)((c->M + thr - 1) / thr), thr, 0, st>>>(
-          (const double*)c->C_hi.p, (const double*)c->C_lo.p, (const double*)c->S_hi.p, (const double*)c->S_lo.p,
+          c->run_flag,          (const double*)c->C_hi.p, (const double*)c->C_lo.p, (const double*)c->S_hi.p, (const double*)c->S_lo.p,
           (const double*)c->scal.p, c->M, reinterpret_cast<typename P::Coef*>(c->coef.p));
       prof_end(c);
       dim3 grid((unsigned)((c->N + kForceThreads - 1) / kForceThreads), L.f_ksplit);
       const int32_t* fs = (const int32_t*)c->fsplit.p;  // one column split serves every precision
       prof_begin(c, kKForce);
-      k_force<P><<<grid, kForceThreads, 0, st>>>(reinterpret_cast<const FCol*>(c->cols.p), fs,
+      k_force<P><<<grid, kForceThreads, 0, st>>>(c->run_flag, reinterpret_cast<const FCol*>(c->cols.p), fs,
                                                   reinterpret_cast<const typename P::Coef*>(c->coef.p), tab, c->Npad,
                                                   c->N, c->d, c->tl.hi_base, c->tl.qmin, c->tl.lo_base,
                                                   reinterpret_cast<typename P::RAcc*>(c->fpart.p));
@@ -495,7 +499,7 @@ static cudaError_t run_prec(Ctx* c, bool want_force) {
       int64_t tot = (int64_t)c->d * c->N;
       prof_begin(c, kKFReduce);
       k_f_reduce<P><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
-          reinterpret_cast<const typename P::RAcc*>(c->fpart.p), L.f_ksplit, c->N, c->d, (const double*)c->scal.p,
+          c->run_flag,          reinterpret_cast<const typename P::RAcc*>(c->fpart.p), L.f_ksplit, c->N, c->d, (const double*)c->scal.p,
           c->pref, (double*)c->F_hi.p, (double*)c->F_lo.p);
       prof_end(c);
     } else {
@@ -563,6 +567,10 @@ cudaError_t plan_upload(Ctx* c) {
   if ((e = dev_alloc(&c->F_hi, nd * 8)) != cudaSuccess) return e;
   if ((e = dev_alloc(&c->F_lo, nd * 8)) != cudaSuccess) return e;
   cudaMemsetAsync(c->scal.p, 0, sizeof(double) * kScCount, st);
+  // dynamic shared memory above 48 KB is opted into once here, never inside a stream capture
+  cudaFuncSetAttribute(k_ntilde<PolF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->launch[SSH_FP64].nt_smem);
+  cudaFuncSetAttribute(k_ntilde<PolDD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->launch[SSH_DD].nt_smem);
+  cudaFuncSetAttribute(k_ntilde<PolFX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->launch[SSH_FX].nt_smem);
   return cudaGetLastError();
 }
 

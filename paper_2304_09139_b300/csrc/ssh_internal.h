@@ -18,6 +18,8 @@ constexpr size_t kAccBytes = 40;    // one complex partial sum
 constexpr size_t kRAccBytes = 20;   // one real partial sum
 constexpr int kForceThreads = 128;
 
+struct FireBufs;  // fire.cu
+
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -79,6 +81,9 @@ struct Ctx {
   int last_prec = -1;
   bool last_force = false;
   Prof prof;
+  const int* run_flag = nullptr;  // device status word: kernels return at once when it is non-zero
+  dd inv_L;                       // 1 / L
+  FireBufs* fire = nullptr;       // minimiser state, allocated on first ssh_minimize
 };
 
 // record an event pair around a launch when profiling is on
@@ -95,5 +100,9 @@ cudaError_t eval_phi_grad(Ctx* c, int prec, bool want_force);
 void setup_launch(Ctx* c);
 
 void set_error(const std::string& msg);
+
+// fire.cu
+ssh_status minimize(Ctx* c, const ssh_min_params* p, ssh_min_result* res);
+void fire_free(Ctx* c);
 
 }  // namespace ssh

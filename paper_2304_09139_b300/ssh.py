@@ -25,6 +25,29 @@ _lock = threading.Lock()
 _lib = None
 
 
+class MinParams(ctypes.Structure):
+    """ssh_min_params (include/ssh.h); zero fields take the library defaults."""
+    _fields_ = [("dt0", ctypes.c_double), ("dt_max", ctypes.c_double), ("alpha_start", ctypes.c_double),
+                ("f_alpha", ctypes.c_double), ("f_inc", ctypes.c_double), ("f_dec", ctypes.c_double),
+                ("n_min", ctypes.c_int), ("n_stages", ctypes.c_int), ("stage_prec", ctypes.c_int * 3),
+                ("pad0", ctypes.c_int), ("stage_floor", ctypes.c_double * 3), ("stall_window", ctypes.c_int64 * 3),
+                ("max_steps", ctypes.c_int64), ("smax_target", ctypes.c_double), ("chunk", ctypes.c_int64),
+                ("max_seconds", ctypes.c_double)]
+
+
+class MinResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("final_prec", ctypes.c_int), ("stages_used", ctypes.c_int),
+                ("pad0", ctypes.c_int), ("steps", ctypes.c_int64), ("stage_steps", ctypes.c_int64 * 3),
+                ("rejected", ctypes.c_int64), ("smax", ctypes.c_double * 2), ("phi", ctypes.c_double * 2),
+                ("dt", ctypes.c_double), ("wall_s", ctypes.c_double), ("stage_wall_s", ctypes.c_double * 3)]
+
+    def as_dict(self):
+        return {"status": self.status, "final_prec": self.final_prec, "stages_used": self.stages_used,
+                "steps": self.steps, "stage_steps": list(self.stage_steps), "rejected": self.rejected,
+                "smax": list(self.smax), "phi": list(self.phi), "dt": self.dt, "wall_s": self.wall_s,
+                "stage_wall_s": list(self.stage_wall_s)}
+
+
 class SshError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{_STATUS.get(status, status)}: {message}")
@@ -70,6 +93,8 @@ def load():
             _sig(lib, "ssh_prof_read", c_int, [c_vp, c_int, P(c_d), P(c_i64)])
             _sig(lib, "ssh_ntilde_noalloc", c_int, [c_int, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
                                                    c_vp])
+            _sig(lib, "ssh_min_defaults", c_int, [c_vp, P(MinParams)])
+            _sig(lib, "ssh_minimize", c_int, [c_vp, P(MinParams), P(MinResult)])
             _lib = lib
     return _lib
 
@@ -202,6 +227,33 @@ class Context:
         n = np.zeros(16, dtype=np.int64)
         _check(self._lib.ssh_prof_read(self._h, 16, _dp(ms), n.ctypes.data_as(P(c_i64))))
         return {KERNELS[i]: (float(ms[i]), int(n[i])) for i in range(len(KERNELS)) if n[i] > 0}
+
+    def min_defaults(self) -> MinParams:
+        p = MinParams()
+        _check(self._lib.ssh_min_defaults(self._h, ctypes.byref(p)))
+        return p
+
+    def minimize(self, params: MinParams | None = None, stages=None, check: bool = False, **kw) -> dict:
+        """Run ssh_minimize.  `stages` is a list of precisions (e.g. [FP64, DD]); keyword arguments set
+        ssh_min_params fields.  Returns the result as a dict (its 'status' is the ssh_status code); with
+        check=True a non-OK status raises."""
+        p = params if params is not None else self.min_defaults()
+        if stages is not None:
+            p.n_stages = len(stages)
+            for i, st in enumerate(stages):
+                p.stage_prec[i] = st
+        for k, v in kw.items():
+            if k in ("stage_floor", "stall_window"):
+                arr = getattr(p, k)
+                for i, x in enumerate(v):
+                    arr[i] = x
+            else:
+                setattr(p, k, v)
+        r = MinResult()
+        st = self._lib.ssh_minimize(self._h, ctypes.byref(p), ctypes.byref(r))
+        if check:
+            _check(st)
+        return r.as_dict()
 
     def ntilde(self):
         """(C, S) of the last evaluation, each an [M, 2] (hi, lo) array in public order."""

@@ -1,0 +1,101 @@
+"""The device-resident FIRE quench (Simulations: FIRE to the minimum) against the oracle.
+
+Minimised states are judged by S_max only (the ground state is degenerate and trajectories are chaotic,
+so no trajectory is compared): for chi < 1/2 a quench from a random start must reach S_max <= 1e-36, and
+the binary128 oracle, evaluated once at the returned positions, must confirm it.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2304_09139_b300 import ssh, synth
+
+pytestmark = pytest.mark.gpu
+NTHREADS = os.cpu_count() or 8
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2304_09139_b300 import _build
+    _build.build()
+    import torch
+    assert torch.cuda.is_available()
+    return True
+
+
+def oracle_smax(oracle_mod, ctx, s_hi, s_lo):
+    r = oracle_mod.phi_grad(s_hi, s_lo, ctx.kset(), ctx.L, want_force=False, nthreads=NTHREADS)
+    return r["smax"][0] + r["smax"][1], r["phi"][0] + r["phi"][1]
+
+
+STAGINGS = {
+    "fp64_then_fx": [ssh.FP64, ssh.FX],
+    "fp64_then_dd": [ssh.FP64, ssh.DD],
+    "all_fx": [ssh.FX],
+    "all_dd": [ssh.DD],
+}
+
+
+@pytest.mark.parametrize("name", list(STAGINGS))
+def test_small_d2_quench_converges(built, oracle_mod, name):
+    cfg = synth.SMALL_D2
+    ctx = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi)
+    ctx.set_positions_frac(synth.positions(cfg.seed, cfg.N, cfg.d))
+    r = ctx.minimize(stages=STAGINGS[name], max_steps=20000)
+    assert r["status"] == 0, r
+    assert r["smax"][0] <= 1e-36
+    hi, lo = ctx.positions_frac()
+    assert np.all((hi >= 0) & (hi < 1))
+    sm, phi = oracle_smax(oracle_mod, ctx, hi, lo)
+    assert sm <= 1.01e-36, (sm, r)
+    assert phi <= ctx.M * cfg.N * 1.01e-36
+
+
+def test_medium_d2_staged_quench(built, oracle_mod):
+    """The d=2, N=10^4, chi=0.45 workload: FP64 descent, then fixed-point polish, to S_max <= 1e-36."""
+    cfg = synth.MEDIUM_D2
+    ctx = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi)
+    ctx.set_positions_frac(synth.positions(cfg.seed, cfg.N, cfg.d))
+    r = ctx.minimize(stages=[ssh.FP64, ssh.FX], max_steps=60000, max_seconds=240)
+    assert r["status"] == 0, r
+    hi, lo = ctx.positions_frac()
+    sm, _ = oracle_smax(oracle_mod, ctx, hi, lo)   # one oracle evaluation of S_max (~9e7 pairs)
+    assert sm <= 1.01e-36, (sm, r)
+
+
+def test_d3_and_d1_quench(built, oracle_mod):
+    for (d, N, chi, seed) in [(3, 200, 0.40, 31), (1, 150, 0.30, 32)]:
+        L = float(N) ** (1.0 / d)
+        ctx = ssh.Context(d, N, L, chi=chi)
+        ctx.set_positions_frac(synth.positions(seed, N, d))
+        r = ctx.minimize(max_steps=40000)
+        assert r["status"] == 0, (d, r)
+        hi, lo = ctx.positions_frac()
+        sm, _ = oracle_smax(oracle_mod, ctx, hi, lo)
+        assert sm <= 1.01e-36, (d, sm, r)
+
+
+def test_step_cap_and_bad_parameters(built):
+    cfg = synth.SMALL_D2
+    ctx = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi)
+    ctx.set_positions_frac(synth.positions(cfg.seed, cfg.N, cfg.d))
+    r = ctx.minimize(max_steps=5)
+    assert r["status"] == 5 and r["steps"] == 5      # SSH_ENOTCONV at the cap
+    with pytest.raises(ssh.SshError):
+        ctx.minimize(check=True, dt0=1.0, dt_max=0.5)  # dt0 > dt_max
+    with pytest.raises(ssh.SshError):
+        ctx.minimize(check=True, stages=[7])
+
+
+def test_energy_guard_never_accepts_an_uphill_step(built):
+    """With an oversized time step most moves raise Phi; the guard must undo them (rejected > 0) and the
+    accepted energy can only go down."""
+    cfg = synth.SMALL_D2
+    ctx = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi)
+    ctx.set_positions_frac(synth.positions(cfg.seed, cfg.N, cfg.d))
+    e0 = ctx.energy_grad(ssh.FX)["phi"][0]
+    d = ctx.min_defaults()
+    r = ctx.minimize(stages=[ssh.FX], dt0=50 * d.dt_max, dt_max=100 * d.dt_max, max_steps=200)
+    assert r["rejected"] > 0
+    assert r["phi"][0] <= e0

@@ -75,18 +75,27 @@ CASES = [
     ("d3_kmode", 3, 150, 4.0, 0.0, 2 * math.pi * 3.3 / 4.0, 10),
     ("d4", 4, 120, 120 ** 0.25, 0.3, 0.0, 11),
     ("wide_d2", 2, 2000, 2000 ** 0.5, 0.45, 0.0, 12),
+    # positions with full-mantissa bits and low words on every axis (as after minimiser moves); synthetic
+    # draws are multiples of 2^-53, which makes every phase reduction exact and hides rounding in it
+    ("fullbits_d2", 2, 700, 700 ** 0.5, 0.45, 0.0, -13),
+    ("fullbits_d3", 3, 400, 400 ** (1 / 3), 0.40, 0.0, -14),
 ]
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_parity_against_oracle(built, oracle_mod, case):
     label, d, N, L, chi, K, seed = case
-    s = synth.positions(seed, N, d)
+    s = synth.positions(abs(seed), N, d)
     # a few coordinates at the edges of the cell and a non-zero low word
     s[0, 0] = 0.0
     s[-1, -1] = 1.0 - 2.0 ** -53
     s_lo = np.zeros_like(s)
     s_lo[1::3, 0] = 2.0 ** -60
+    if seed < 0:
+        u = synth.uniform01(abs(seed) + 100, N * d).reshape(N, d)
+        s = np.sqrt(s) * 0.999999937 + 1e-9 * u          # arbitrary low mantissa bits
+        s[: N // 8] *= 0.01                                # many coordinates below 1/64
+        s_lo = (u - 0.5) * 2.0 ** -53 * s
     ctx = ssh.Context(d, N, L, chi=chi, K=K)
     n = ctx.kset()
     assert np.array_equal(n, oracle_mod.kset(d, N, L, chi=chi, K=K))
