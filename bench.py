@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-minimize", action="store_true")
+    ap.add_argument("--minimize-dd", action="store_true", help="also time FP64->dd and all-dd quenches")
+    ap.add_argument("--minimize-seconds", type=float, default=150.0)
     return ap.parse_args()
 
 
@@ -148,6 +151,27 @@ def cpu_sample(N, d, L, chi, seed, frac_k=8, nthreads=0):
     return Ms * N / dt, Ms, oracle.num_threads() if nthreads == 0 else nthreads
 
 
+def minimize_block(ssh, synth, w, dev, stream, with_dd=False, max_seconds=150):
+    """Time full quenches of the workload from its random start to S_max <= 1e-36 (configs per hour):
+    staged FP64 -> fixed point (the library default) and all fixed point; with --minimize-dd also FP64 -> dd
+    and all-dd, the paper's arithmetic (about a minute and several minutes)."""
+    out = {}
+    runs = [("fp64_then_fx", [ssh.FP64, ssh.FX]), ("all_fx", [ssh.FX])]
+    if with_dd:
+        runs += [("fp64_then_dd", [ssh.FP64, ssh.DD]), ("all_dd", [ssh.DD])]
+    for name, stages in runs:
+        c = ssh.Context(w["d"], w["N"], w["L"], chi=w["chi"], device=dev)
+        c.set_stream(stream.cuda_stream)
+        c.set_positions_frac(synth.positions(w["seed"], w["N"], w["d"]))
+        r = c.minimize(stages=stages, max_steps=100000, max_seconds=max_seconds)
+        out[name] = {"converged": r["status"] == 0, "status": r["status"], "wall_s": r["wall_s"],
+                     "steps": r["steps"], "stage_steps": r["stage_steps"][:len(stages)],
+                     "stage_wall_s": r["stage_wall_s"][:len(stages)], "smax": r["smax"][0],
+                     "configs_per_hour": 3600.0 / r["wall_s"] if r["status"] == 0 else 0.0}
+        c.close()
+    return out
+
+
 def run_reference(args):
     rank, world, local = dist_info()
     if rank != 0:
@@ -200,8 +224,19 @@ def main():
     pairs = ctx.M * ctx.N
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
 
+    # A step is one device FIRE step: twiddle tables, n~, reductions, Phi / S_max, force, the FIRE update,
+    # the energy-guard acceptance and the convergence test.  The target is set out of reach so that no
+    # timed step turns into a no-op.
+    fp = ctx.min_defaults()
+    fp.n_stages = 1
+    fp.stage_prec[0] = prec
+    fp.smax_target = 1e-300
+    fp.max_steps = 1 << 40
+    fp.stall_window[0] = 1 << 40
+    ctx.fire_begin(fp)
+
     def step():
-        ctx.eval(prec, True)
+        ctx.fire_steps(prec, 1)
 
     for _ in range(args.warmup):
         step()
@@ -233,7 +268,9 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         tot_ms = float(t.item())
     value = pairs * world * args.steps / (tot_ms / 1e3)
-    launches = sum(n for _, n in prof.values())
+    # every profiled id is one kernel, except "fire": its two event pairs per step cover 3 + 2 kernels
+    launches = sum(n for k, n in ((k, v[1]) for k, v in prof.items()) if k != "fire") + \
+        5 * prof.get("fire", (0, 0))[1] // 2
 
     # roofline of the dominant kernel (largest share of device time in the timed region)
     dom = max(prof.items(), key=lambda kv: kv[1][0])
@@ -293,12 +330,19 @@ def main():
                       "fp64": "f64"}[args.prec],
             "data": "synthetic",
             "config": {"workload": f"d={w['d']} N={w['N']} L={w['L']} chi={w['chi']} M={ctx.M}, uniform random "
-                                   f"(SplitMix64 seed {w['seed']}+rank), one Phi+force evaluation per step",
+                                   f"(SplitMix64 seed {w['seed']}+rank), one device FIRE step (Phi + force + "
+                                   f"update + acceptance) per step",
                        "l2": "flushed between timed steps (256 MiB write, outside the step events)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "gpu_launches": launches, "wall_s": t_wall,
             "e2e": {"value": pairs / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": clk.summary(), "variants_pairs_per_s": variants}
+    if rank == 0 and not args.no_minimize:
+        line["minimize"] = minimize_block(ssh, synth, w, dev, stream, with_dd=args.minimize_dd,
+                                          max_seconds=args.minimize_seconds)
+        conv = line["minimize"].get("fp64_then_fx", {})
+        if conv.get("converged"):
+            line["configs_per_hour"] = 3600.0 / conv["wall_s"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, Ms, cores = cpu_sample(w["N"], w["d"], w["L"], w["chi"], w["seed"])
         line["cpu_baseline"] = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle",

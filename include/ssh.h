@@ -180,11 +180,27 @@ ssh_status ssh_min_defaults(const ssh_ctx* ctx, ssh_min_params* p);
 ssh_status ssh_minimize(ssh_ctx* ctx, const ssh_min_params* p, ssh_min_result* res);
 
 /*
+ * Stepper: the same device FIRE step as ssh_minimize, driven one step at a time.
+ *   ssh_fire_begin  v = 0, and Phi, S_max and F at the current positions in p->stage_prec[0] (p as for
+ *                   ssh_minimize; stage floors are ignored, the step cap and target still stop the run)
+ *   ssh_fire_steps  enqueue exactly nsteps steps in precision prec on the context's stream and return
+ *                   without synchronising; steps after the run has stopped do nothing.  Steps replay a
+ *                   captured CUDA graph, except while the profiler is on: then each kernel is launched
+ *                   directly so that it carries its own event pair
+ *   ssh_fire_state  synchronise and report steps, rejected steps, S_max, Phi and dt of the accepted state;
+ *                   *running = 1 while the device status word says the run continues
+ */
+ssh_status ssh_fire_begin(ssh_ctx* ctx, const ssh_min_params* p);
+ssh_status ssh_fire_steps(ssh_ctx* ctx, int prec, int64_t nsteps);
+ssh_status ssh_fire_state(ssh_ctx* ctx, ssh_min_result* res, int* running);
+
+/*
  * Event profiler (tracing).  When enabled, every kernel the context launches is bracketed by a CUDA event
  * pair on the context's stream; ssh_prof_read synchronises the stream and returns, per kernel id, the
  * summed device time in milliseconds and the launch count since the last ssh_prof_enable call.
  * Kernel ids: 0 twiddle tables, 1 collective density n~, 2 density reduction, 3 Phi/S_max finalise,
- * 4 force coefficients, 5 force, 6 force reduction, 7 minimiser update (FIRE).  n entries are written.
+ * 4 force coefficients, 5 force, 6 force reduction, 7 minimiser kernels of a FIRE step (two event pairs
+ * per step: update, acceptance).  n entries are written.
  */
 ssh_status ssh_prof_enable(ssh_ctx* ctx, int on);
 ssh_status ssh_prof_read(ssh_ctx* ctx, int n, double* ms, int64_t* launches);

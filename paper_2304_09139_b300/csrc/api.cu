@@ -326,10 +326,7 @@ ssh_status ssh_min_defaults(const ssh_ctx* h, ssh_min_params* p) {
   return SSH_OK;
 }
 
-ssh_status ssh_minimize(ssh_ctx* h, const ssh_min_params* pin, ssh_min_result* res) {
-  if (!h) { set_error("ssh_minimize: NULL context"); return SSH_EINVAL; }
-  ssh::Ctx& c = h->c;
-  if (!c.have_positions) { set_error("ssh_minimize: no positions set"); return SSH_EINVAL; }
+static ssh_status complete_params(const ssh_ctx* h, const ssh_min_params* pin, ssh_min_params* out) {
   ssh_min_params d;
   ssh_min_defaults(h, &d);
   ssh_min_params p = pin ? *pin : d;
@@ -360,8 +357,45 @@ ssh_status ssh_minimize(ssh_ctx* h, const ssh_min_params* pin, ssh_min_result* r
       set_error("ssh_minimize: unknown stage precision");
       return SSH_EINVAL;
     }
+  *out = p;
+  return SSH_OK;
+}
+
+ssh_status ssh_minimize(ssh_ctx* h, const ssh_min_params* pin, ssh_min_result* res) {
+  if (!h) { set_error("ssh_minimize: NULL context"); return SSH_EINVAL; }
+  ssh::Ctx& c = h->c;
+  if (!c.have_positions) { set_error("ssh_minimize: no positions set"); return SSH_EINVAL; }
+  ssh_min_params p;
+  ssh_status st = complete_params(h, pin, &p);
+  if (st != SSH_OK) return st;
   cudaSetDevice(c.device);
   return ssh::minimize(&c, &p, res);
+}
+
+ssh_status ssh_fire_begin(ssh_ctx* h, const ssh_min_params* pin) {
+  if (!h) { set_error("ssh_fire_begin: NULL context"); return SSH_EINVAL; }
+  ssh::Ctx& c = h->c;
+  if (!c.have_positions) { set_error("ssh_fire_begin: no positions set"); return SSH_EINVAL; }
+  ssh_min_params p;
+  ssh_status st = complete_params(h, pin, &p);
+  if (st != SSH_OK) return st;
+  cudaSetDevice(c.device);
+  return ssh::fire_begin(&c, &p);
+}
+
+ssh_status ssh_fire_steps(ssh_ctx* h, int prec, int64_t nsteps) {
+  if (!h || prec < SSH_FP64 || prec > SSH_FX || nsteps < 0) { set_error("ssh_fire_steps: bad arguments"); return SSH_EINVAL; }
+  cudaSetDevice(h->c.device);
+  return ssh::fire_steps(&h->c, prec, nsteps);
+}
+
+ssh_status ssh_fire_state(ssh_ctx* h, ssh_min_result* res, int* running) {
+  if (!h) { set_error("ssh_fire_state: NULL context"); return SSH_EINVAL; }
+  cudaSetDevice(h->c.device);
+  int st = 0;
+  ssh_status s = ssh::fire_state(&h->c, res, &st);
+  if (running) *running = st == 0;
+  return s;
 }
 
 ssh_status ssh_prof_enable(ssh_ctx* h, int on) {

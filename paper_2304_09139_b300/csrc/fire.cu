@@ -206,8 +206,10 @@ __global__ void k_fire_stage_init(FireState* fs, const double* __restrict__ scal
 struct FireBufs {
   DevBuf v_hi, v_lo, bs_hi, bs_lo, bF_hi, bF_lo, part, fs;
   FireState* h_fs = nullptr;  // pinned
-  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};   // kFireGraphSteps steps
+  cudaGraphExec_t graph1[3] = {nullptr, nullptr, nullptr};  // one step
   int nb = 0;
+  bool begun = false;
 };
 
 static cudaError_t fire_alloc(Ctx* c) {
@@ -235,8 +237,10 @@ void fire_free(Ctx* c) {
   for (DevBuf* b : {&f->v_hi, &f->v_lo, &f->bs_hi, &f->bs_lo, &f->bF_hi, &f->bF_lo, &f->part, &f->fs})
     if (b->p) cudaFree(b->p);
   if (f->h_fs) cudaFreeHost(f->h_fs);
-  for (int p = 0; p < 3; p++)
+  for (int p = 0; p < 3; p++) {
     if (f->graph[p]) cudaGraphExecDestroy(f->graph[p]);
+    if (f->graph1[p]) cudaGraphExecDestroy(f->graph1[p]);
+  }
   delete f;
   c->fire = nullptr;
 }
@@ -247,6 +251,7 @@ static cudaError_t fire_step(Ctx* c, int prec) {
   cudaStream_t st = c->stream;
   const int64_t nd = (int64_t)c->d * c->N;
   FireState* fs = (FireState*)f->fs.p;
+  prof_begin(c, kKFire);
   k_fire_dots<<<f->nb, kFireThreads, 0, st>>>(fs, nd, (const double*)c->F_hi.p, (const double*)f->v_hi.p,
                                               (double*)f->part.p);
   k_fire_ctrl<<<1, 1, 0, st>>>(fs, (const double*)f->part.p, f->nb);
@@ -255,33 +260,115 @@ static cudaError_t fire_step(Ctx* c, int prec) {
                                  (double*)f->v_lo.p, (const double*)c->F_hi.p, (const double*)c->F_lo.p,
                                  (double*)f->bs_hi.p, (double*)f->bs_lo.p, (double*)f->bF_hi.p, (double*)f->bF_lo.p,
                                  c->inv_L);
+  prof_end(c);
   c->run_flag = &fs->status;
   cudaError_t e = eval_phi_grad(c, prec, true);
   c->run_flag = nullptr;
   if (e != cudaSuccess) return e;
+  prof_begin(c, kKFire);
   k_fire_accept<<<1, 1, 0, st>>>(fs, (const double*)c->scal.p);
   k_fire_restore<<<g, 256, 0, st>>>(fs, nd, (double*)c->s_hi.p, (double*)c->s_lo.p, (double*)f->v_hi.p,
                                     (double*)f->v_lo.p, (double*)c->F_hi.p, (double*)c->F_lo.p,
                                     (const double*)f->bs_hi.p, (const double*)f->bs_lo.p,
                                     (const double*)f->bF_hi.p, (const double*)f->bF_lo.p);
+  prof_end(c);
   return cudaGetLastError();
 }
 
-static cudaError_t fire_graph(Ctx* c, int prec, cudaGraphExec_t* out) {
+static cudaError_t fire_graph(Ctx* c, int prec, cudaGraphExec_t* out, int steps = kFireGraphSteps) {
   FireBufs* f = c->fire;
-  if (f->graph[prec]) { *out = f->graph[prec]; return cudaSuccess; }
+  cudaGraphExec_t* slot = steps == 1 ? &f->graph1[prec] : &f->graph[prec];
+  if (*slot) { *out = *slot; return cudaSuccess; }
   bool prof = c->prof.on;
   c->prof.on = false;  // no profiler events inside a capture
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
-  for (int s = 0; s < kFireGraphSteps && e == cudaSuccess; s++) e = fire_step(c, prec);
+  for (int s = 0; s < steps && e == cudaSuccess; s++) e = fire_step(c, prec);
   cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
   c->prof.on = prof;
   if (e == cudaSuccess) e = e2;
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&f->graph[prec], graph, 0);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(slot, graph, 0);
   if (graph) cudaGraphDestroy(graph);
-  if (e == cudaSuccess) *out = f->graph[prec];
+  if (e == cudaSuccess) *out = *slot;
   return e;
+}
+
+static FireState params_to_state(const ssh_min_params* p) {
+  FireState prm;
+  memset(&prm, 0, sizeof prm);
+  prm.dt = p->dt0;
+  prm.alpha = p->alpha_start;
+  prm.dt_max = p->dt_max;
+  prm.alpha_start = p->alpha_start;
+  prm.f_alpha = p->f_alpha;
+  prm.f_inc = p->f_inc;
+  prm.f_dec = p->f_dec;
+  prm.n_min = p->n_min;
+  prm.max_steps = p->max_steps;
+  prm.target = p->smax_target;
+  prm.stage_floor = 0.0;
+  prm.stall_window = p->stall_window[0];
+  return prm;
+}
+
+// Stepper: state from the current positions in the first stage's precision (v = 0).
+ssh_status fire_begin(Ctx* c, const ssh_min_params* p) {
+  cudaError_t e = fire_alloc(c);
+  if (e != cudaSuccess) { set_error(std::string("ssh_fire_begin: allocation: ") + cudaGetErrorString(e)); return SSH_ENOMEM; }
+  FireBufs* f = c->fire;
+  cudaStream_t st = c->stream;
+  const int64_t nd = (int64_t)c->d * c->N;
+  cudaMemsetAsync(f->v_hi.p, 0, nd * 8, st);
+  cudaMemsetAsync(f->v_lo.p, 0, nd * 8, st);
+  e = eval_phi_grad(c, p->stage_prec[0], true);
+  if (e == cudaSuccess) {
+    k_fire_stage_init<<<1, 1, 0, st>>>((FireState*)f->fs.p, (const double*)c->scal.p, 1, params_to_state(p));
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) { set_error(std::string("ssh_fire_begin: ") + cudaGetErrorString(e)); return SSH_ECUDA; }
+  f->begun = true;
+  return SSH_OK;
+}
+
+// Enqueue exactly nsteps FIRE steps in precision prec (no host synchronisation).
+ssh_status fire_steps(Ctx* c, int prec, int64_t nsteps) {
+  if (!c->fire || !c->fire->begun) { set_error("ssh_fire_steps: call ssh_fire_begin first"); return SSH_EINVAL; }
+  cudaGraphExec_t g8 = nullptr, g1 = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (c->prof.on) {  // profiling: direct launches, so every kernel of the step carries its own events
+    for (int64_t i = 0; e == cudaSuccess && i < nsteps; i++) e = fire_step(c, prec);
+    if (e != cudaSuccess) { set_error(std::string("ssh_fire_steps: ") + cudaGetErrorString(e)); return SSH_ECUDA; }
+    return SSH_OK;
+  }
+  if (nsteps >= kFireGraphSteps) e = fire_graph(c, prec, &g8);
+  if (e == cudaSuccess && nsteps % kFireGraphSteps) e = fire_graph(c, prec, &g1, 1);
+  for (int64_t i = 0; e == cudaSuccess && i + kFireGraphSteps <= nsteps; i += kFireGraphSteps) e = cudaGraphLaunch(g8, c->stream);
+  for (int64_t i = 0; e == cudaSuccess && i < nsteps % kFireGraphSteps; i++) e = cudaGraphLaunch(g1, c->stream);
+  if (e != cudaSuccess) { set_error(std::string("ssh_fire_steps: ") + cudaGetErrorString(e)); return SSH_ECUDA; }
+  return SSH_OK;
+}
+
+// Read the stepper state (synchronises the stream).  Returns the device status word in *dev_status.
+ssh_status fire_state(Ctx* c, ssh_min_result* r, int* dev_status) {
+  if (!c->fire || !c->fire->begun) { set_error("ssh_fire_state: call ssh_fire_begin first"); return SSH_EINVAL; }
+  FireBufs* f = c->fire;
+  cudaError_t e = cudaMemcpyAsync(f->h_fs, f->fs.p, sizeof(FireState), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) { set_error(std::string("ssh_fire_state: ") + cudaGetErrorString(e)); return SSH_ECUDA; }
+  const FireState& h = *f->h_fs;
+  if (r) {
+    memset(r, 0, sizeof *r);
+    r->steps = h.step;
+    r->rejected = h.rejected;
+    r->smax[0] = h.smax_hi;
+    r->smax[1] = h.smax_lo;
+    r->phi[0] = h.phi_hi;
+    r->phi[1] = h.phi_lo;
+    r->dt = h.dt;
+    r->status = h.status == kFsConverged ? SSH_OK : h.status == kFsNan ? SSH_ENAN : SSH_ENOTCONV;
+  }
+  if (dev_status) *dev_status = h.status;
+  return SSH_OK;
 }
 
 ssh_status minimize(Ctx* c, const ssh_min_params* p, ssh_min_result* res) {

@@ -104,5 +104,8 @@ void set_error(const std::string& msg);
 // fire.cu
 ssh_status minimize(Ctx* c, const ssh_min_params* p, ssh_min_result* res);
 void fire_free(Ctx* c);
+ssh_status fire_begin(Ctx* c, const ssh_min_params* p);
+ssh_status fire_steps(Ctx* c, int prec, int64_t nsteps);
+ssh_status fire_state(Ctx* c, ssh_min_result* r, int* dev_status);
 
 }  // namespace ssh

@@ -95,6 +95,9 @@ def load():
                                                    c_vp])
             _sig(lib, "ssh_min_defaults", c_int, [c_vp, P(MinParams)])
             _sig(lib, "ssh_minimize", c_int, [c_vp, P(MinParams), P(MinResult)])
+            _sig(lib, "ssh_fire_begin", c_int, [c_vp, P(MinParams)])
+            _sig(lib, "ssh_fire_steps", c_int, [c_vp, c_int, c_i64])
+            _sig(lib, "ssh_fire_state", c_int, [c_vp, P(MinResult), P(c_int)])
             _lib = lib
     return _lib
 
@@ -254,6 +257,23 @@ class Context:
         if check:
             _check(st)
         return r.as_dict()
+
+    def fire_begin(self, params: MinParams | None = None, **kw):
+        p = params if params is not None else self.min_defaults()
+        for k, v in kw.items():
+            setattr(p, k, v)
+        _check(self._lib.ssh_fire_begin(self._h, ctypes.byref(p)))
+
+    def fire_steps(self, prec: int, nsteps: int):
+        _check(self._lib.ssh_fire_steps(self._h, prec, nsteps))
+
+    def fire_state(self) -> dict:
+        r = MinResult()
+        run = c_int(0)
+        _check(self._lib.ssh_fire_state(self._h, ctypes.byref(r), ctypes.byref(run)))
+        d = r.as_dict()
+        d["running"] = bool(run.value)
+        return d
 
     def ntilde(self):
         """(C, S) of the last evaluation, each an [M, 2] (hi, lo) array in public order."""

@@ -99,3 +99,30 @@ def test_energy_guard_never_accepts_an_uphill_step(built):
     r = ctx.minimize(stages=[ssh.FX], dt0=50 * d.dt_max, dt_max=100 * d.dt_max, max_steps=200)
     assert r["rejected"] > 0
     assert r["phi"][0] <= e0
+
+
+def test_stepper_counts_steps_and_stops_at_convergence(built):
+    """ssh_fire_begin / ssh_fire_steps / ssh_fire_state: exactly the requested steps run (graph replay of 8
+    plus single steps), and steps enqueued after convergence do nothing."""
+    cfg = synth.SMALL_D2
+    ctx = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi)
+    ctx.set_positions_frac(synth.positions(cfg.seed, cfg.N, cfg.d))
+    p = ctx.min_defaults()
+    p.n_stages = 1
+    p.stage_prec[0] = ssh.FX
+    ctx.fire_begin(p)
+    ctx.fire_steps(ssh.FX, 11)
+    st = ctx.fire_state()
+    assert st["steps"] == 11 and st["running"]
+    ctx.prof_enable(True)           # direct launches while profiling
+    ctx.fire_steps(ssh.FX, 3)
+    pr = ctx.prof_read()
+    ctx.prof_enable(False)
+    assert ctx.fire_state()["steps"] == 14
+    assert pr["fire"][1] == 6 and pr["ntilde"][1] == 3 and pr["force"][1] == 3
+    ctx.fire_steps(ssh.FX, 4000)
+    st = ctx.fire_state()
+    assert not st["running"] and st["status"] == 0 and st["smax"][0] <= 1e-36
+    n_conv = st["steps"]
+    ctx.fire_steps(ssh.FX, 16)
+    assert ctx.fire_state()["steps"] == n_conv
