@@ -104,6 +104,11 @@ void ssh_destroy(ssh_ctx* h) {
   cudaSetDevice(c.device);
   if (c.stream) cudaStreamSynchronize(c.stream);
   ssh::fire_free(&c);
+  if (c.eng) {
+    ssh::engine_free(c.eng);
+    delete c.eng;
+    c.eng = nullptr;
+  }
   for (ssh::DevBuf* b : {&c.s_hi, &c.s_lo, &c.rows, &c.slots, &c.blocks, &c.grows, &c.cols, &c.fsplit, &c.tab, &c.part,
                          &c.C_hi, &c.C_lo, &c.S_hi, &c.S_lo, &c.coef, &c.blk, &c.scal, &c.fpart, &c.F_hi, &c.F_lo})
     free_buf(*b);
@@ -402,7 +407,7 @@ ssh_status ssh_prof_enable(ssh_ctx* h, int on) {
   if (!h) { set_error("ssh_prof_enable: NULL context"); return SSH_EINVAL; }
   ssh::Ctx& c = h->c;
   cudaSetDevice(c.device);
-  cudaError_t e = ssh::prof_collect(&c);
+  cudaError_t e = ssh::prof_collect(&c.prof, c.stream);
   if (e != cudaSuccess) return cuda_fail(e, "ssh_prof_enable");
   c.prof.on = on != 0;
   for (int i = 0; i < ssh::kKCount; i++) { c.prof.ms[i] = 0; c.prof.launches[i] = 0; }
@@ -413,7 +418,7 @@ ssh_status ssh_prof_read(ssh_ctx* h, int n, double* ms, int64_t* launches) {
   if (!h || n < 0) { set_error("ssh_prof_read: bad arguments"); return SSH_EINVAL; }
   ssh::Ctx& c = h->c;
   cudaSetDevice(c.device);
-  cudaError_t e = ssh::prof_collect(&c);
+  cudaError_t e = ssh::prof_collect(&c.prof, c.stream);
   if (e != cudaSuccess) return cuda_fail(e, "ssh_prof_read");
   for (int i = 0; i < n && i < ssh::kKCount; i++) {
     if (ms) ms[i] = c.prof.ms[i];

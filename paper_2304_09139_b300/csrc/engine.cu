@@ -1,0 +1,194 @@
+// engine.cu -- descriptors and work lists for a set of configurations evaluated together.
+//
+// A member keeps its own device buffers (Ctx).  The engine uploads one CfgDev per member, the member lists
+// of each precision, and the work items of the twiddle kernel and of the two persistent hot kernels.  Items
+// of the hot kernels are ordered by estimated cost, largest first, so that the dynamic queue ends with small
+// items (longest-processing-time order).  A member's launch shape (particle splits, column splits, staging
+// chunk) depends on that member alone, so its arithmetic, and its result, is the same in every batch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <numeric>
+
+#include "ssh_internal.h"
+
+namespace ssh {
+
+CfgDev make_cfgdev(const Ctx* c, bool fire_mode) {
+  CfgDev g;
+  memset(&g, 0, sizeof g);
+  g.d = c->d;
+  g.nrows = (int)c->tl.rows.size();
+  g.lo_base = c->tl.lo_base;
+  g.hi_base = c->tl.hi_base;
+  g.qmin = c->tl.qmin;
+  g.ksplit = c->launch[0].f_ksplit;
+  g.nblk = c->n_red_blocks;
+  g.N = c->N;
+  g.M = c->M;
+  g.Npad = c->Npad;
+  for (int p = 0; p < 3; p++) {
+    const Launch& L = c->launch[p];
+    int64_t plen = (c->N + L.nt_psplit - 1) / L.nt_psplit;
+    plen = (plen + L.nt_pchunk - 1) / L.nt_pchunk * L.nt_pchunk;
+    g.plen[p] = plen;
+    g.psplit[p] = (int)((c->N + plen - 1) / plen);
+    g.pchunk[p] = L.nt_pchunk;
+  }
+  g.s_hi = (double*)c->s_hi.p;
+  g.s_lo = (double*)c->s_lo.p;
+  g.rows = (const TabRow*)c->rows.p;
+  g.slots = (const NtSlot*)c->slots.p;
+  g.blocks = (const NtBlock*)c->blocks.p;
+  g.g_rows = (const int32_t*)c->grows.p;
+  g.cols = (const FCol*)c->cols.p;
+  g.fsplit = (const int32_t*)c->fsplit.p;
+  g.tab = c->tab.p;
+  g.part = c->part.p;
+  g.C_hi = (double*)c->C_hi.p;
+  g.C_lo = (double*)c->C_lo.p;
+  g.S_hi = (double*)c->S_hi.p;
+  g.S_lo = (double*)c->S_lo.p;
+  g.coef = c->coef.p;
+  g.blk = c->blk.p;
+  g.scal = (double*)c->scal.p;
+  g.fpart = c->fpart.p;
+  g.F_hi = (double*)c->F_hi.p;
+  g.F_lo = (double*)c->F_lo.p;
+  g.pref = c->pref;
+  g.inv_L = c->inv_L;
+  if (c->fire) fire_fill_cfgdev(c, &g);
+  if (!fire_mode) g.run = nullptr;
+  return g;
+}
+
+void engine_free(Engine* e) {
+  for (DevBuf* b : {&e->d_cfgs, &e->d_lists, &e->d_tw, &e->d_nt, &e->d_f, &e->d_counters}) {
+    if (b->p) cudaFree(b->p);
+    b->p = nullptr;
+    b->bytes = 0;
+  }
+}
+
+static cudaError_t up(DevBuf* b, const void* src, size_t bytes, cudaStream_t st) {
+  if (b->p && b->bytes < bytes) {
+    cudaFree(b->p);
+    b->p = nullptr;
+  }
+  if (!b->p) {
+    b->bytes = std::max<size_t>(bytes, 16);
+    cudaError_t e = cudaMalloc(&b->p, b->bytes);
+    if (e != cudaSuccess) return e;
+  }
+  if (bytes == 0) return cudaSuccess;
+  return cudaMemcpyAsync(b->p, src, bytes, cudaMemcpyHostToDevice, st);
+}
+
+cudaError_t engine_build(Engine* e, const std::vector<Ctx*>& members, const std::vector<int>& prec_of, bool fire_mode,
+                         cudaStream_t st) {
+  e->members = members;
+  e->prec_of = prec_of;
+  e->fire_mode = fire_mode;
+  const int n = (int)members.size();
+  if (n > 0) {
+    e->device = members[0]->device;
+    e->sm_count = members[0]->sm_count;
+  }
+  e->host_cfgs.resize(n);
+  for (int i = 0; i < n; i++) e->host_cfgs[i] = make_cfgdev(members[i], fire_mode);
+  // member lists: one per precision, then all members
+  std::vector<int> lists[3];
+  for (int i = 0; i < n; i++)
+    for (int p = 0; p < 3; p++)
+      if (prec_of[i] == p || prec_of[i] < 0) lists[p].push_back(i);
+  e->h_lists.clear();
+  int off[4];
+  for (int p = 0; p < 3; p++) {
+    off[p] = (int)e->h_lists.size();
+    e->h_lists.insert(e->h_lists.end(), lists[p].begin(), lists[p].end());
+  }
+  off[3] = (int)e->h_lists.size();
+  for (int i = 0; i < n; i++) e->h_lists.push_back(i);
+  // work items per precision
+  e->h_tw.clear();
+  e->h_nt.clear();
+  e->h_f.clear();
+  int tw_off[3], nt_off[3], f_off[3], tw_n[3], nt_n[3], f_n[3];
+  for (int p = 0; p < 3; p++) {
+    tw_off[p] = (int)e->h_tw.size();
+    nt_off[p] = (int)e->h_nt.size();
+    f_off[p] = (int)e->h_f.size();
+    std::vector<std::pair<double, NtItem>> nt;
+    std::vector<std::pair<double, FItem>> fi;
+    for (int i : lists[p]) {
+      const Ctx* c = members[i];
+      const CfgDev& g = e->host_cfgs[i];
+      const int64_t total = (int64_t)g.nrows * g.Npad;
+      for (int64_t s = 0; s < total; s += kTwThreads) e->h_tw.push_back({i, 0, s});
+      for (int b = 0; b < (int)c->nt.blocks.size(); b++)
+        for (int ps = 0; ps < g.psplit[p]; ps++) {
+          const int64_t j0 = ps * g.plen[p], j1 = std::min(c->N, j0 + g.plen[p]);
+          nt.push_back({(double)c->nt.blocks[b].nslots * (double)(j1 - j0), {i, b, ps, 0}});
+        }
+      const int pblocks = (int)((c->N + kForceThreads - 1) / kForceThreads);
+      for (int ks = 0; ks < g.ksplit; ks++) {
+        const int c0 = c->f_split[ks], c1 = c->f_split[ks + 1];
+        const int64_t k0 = c0 < (int)c->fp.cols.size() ? c->fp.cols[c0].k0 : c->M;
+        const int64_t k1 = c1 < (int)c->fp.cols.size() ? c->fp.cols[c1].k0 : c->M;
+        for (int pb = 0; pb < pblocks; pb++) fi.push_back({(double)(k1 - k0 + (c1 - c0)), {i, pb, ks, 0}});
+      }
+    }
+    // largest first; ties keep their construction order (stable), so the list is deterministic
+    std::stable_sort(nt.begin(), nt.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    std::stable_sort(fi.begin(), fi.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+    for (auto& x : nt) e->h_nt.push_back(x.second);
+    for (auto& x : fi) e->h_f.push_back(x.second);
+    tw_n[p] = (int)e->h_tw.size() - tw_off[p];
+    nt_n[p] = (int)e->h_nt.size() - nt_off[p];
+    f_n[p] = (int)e->h_f.size() - f_off[p];
+  }
+  cudaError_t err;
+  if ((err = up(&e->d_cfgs, e->host_cfgs.data(), sizeof(CfgDev) * n, st)) != cudaSuccess) return err;
+  if ((err = up(&e->d_lists, e->h_lists.data(), sizeof(int) * e->h_lists.size(), st)) != cudaSuccess) return err;
+  if ((err = up(&e->d_tw, e->h_tw.data(), sizeof(TwItem) * e->h_tw.size(), st)) != cudaSuccess) return err;
+  if ((err = up(&e->d_nt, e->h_nt.data(), sizeof(NtItem) * e->h_nt.size(), st)) != cudaSuccess) return err;
+  if ((err = up(&e->d_f, e->h_f.data(), sizeof(FItem) * e->h_f.size(), st)) != cudaSuccess) return err;
+  if (!e->d_counters.p) {
+    if ((err = up(&e->d_counters, nullptr, 0, st)) != cudaSuccess) return err;
+  }
+  const CfgDev* dc = (const CfgDev*)e->d_cfgs.p;
+  const int* dl = (const int*)e->d_lists.p;
+  for (int p = 0; p < 3; p++) {
+    EngineView& v = e->view[p];
+    v = EngineView();
+    v.cfgs = dc;
+    v.list = dl + off[p];
+    v.nlist = (int)lists[p].size();
+    v.tw = (const TwItem*)e->d_tw.p + tw_off[p];
+    v.ntw = tw_n[p];
+    v.nt = (const NtItem*)e->d_nt.p + nt_off[p];
+    v.nnt = nt_n[p];
+    v.fi = (const FItem*)e->d_f.p + f_off[p];
+    v.nfi = f_n[p];
+    v.counters = (int*)e->d_counters.p;
+    v.sm_count = e->sm_count;
+    for (int i : lists[p]) {
+      const Ctx* c = members[i];
+      v.nt_smem = std::max(v.nt_smem, c->launch[p].nt_smem);
+      v.maxM = std::max(v.maxM, c->M);
+      v.maxND = std::max(v.maxND, (int64_t)c->d * c->N);
+      v.maxblk = std::max(v.maxblk, c->n_red_blocks);
+    }
+  }
+  e->all = dl + off[3];
+  e->nall = n;
+  e->maxND_all = 0;
+  e->max_nb_fire = 0;
+  for (int i = 0; i < n; i++) {
+    e->maxND_all = std::max(e->maxND_all, (int64_t)members[i]->d * members[i]->N);
+    e->max_nb_fire = std::max(e->max_nb_fire, e->host_cfgs[i].nb_fire);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ssh

@@ -1,4 +1,5 @@
-// fire.cu -- the paper's minimiser (Simulations: FIRE, Bitzek et al. 2006) kept on the device.
+// fire.cu -- the paper's minimiser (Simulations: FIRE, Bitzek et al. 2006) kept on the device, for one
+// configuration or for every member of a batch at once.
 //
 // One step, for the force F and energy Phi at the accepted positions and the velocity v of the last step:
 //   k_fire_dots     P = F.v, |F|^2, |v|^2 (per-block partials, fixed order)
@@ -6,14 +7,14 @@
 //                   dt <- min(dt f_inc, dt_max), a <- a f_alpha;  P <= 0 -> v <- 0, dt <- dt f_dec, a <- a_start
 //   k_fire_move     semi-implicit Euler with unit mass: v <- v + dt F, r <- r + dt v (dd, wrapped into the box);
 //                   the accepted positions and force are kept for a possible undo
-//   (Phi + force at the new positions: the seven evaluation kernels)
+//   (Phi + force at the new positions: the evaluation kernels of each member's current precision)
 //   k_fire_accept   energy guard: Phi_new > Phi -> reject (dt <- dt f_dec, v <- 0, a <- a_start) and undo;
 //                   convergence S_max <= target; step cap; the precision stage ends when S_max falls below the
 //                   stage floor or has not halved in stall_window steps
 //   k_fire_restore  the undo of a rejected step
-// Every kernel first reads the device status word and returns when the run has ended, so a captured chunk
-// of steps costs nothing after convergence.  The host replays a CUDA graph of kFireGraphSteps steps per
-// precision and reads the status word between chunks; the status word is the only per-chunk copy.
+// Every kernel first reads its member's device status word and skips the member when its run has ended, so a
+// captured chunk of steps costs nothing for converged members.  The host replays a CUDA graph of
+// kFireGraphSteps steps and reads the status words between chunks; they are the only per-chunk copy.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -27,34 +28,21 @@
 
 namespace ssh {
 
-enum { kFsRunning = 0, kFsConverged = 1, kFsNan = 2, kFsStageDone = 3, kFsMaxSteps = 4 };
 constexpr int kFireThreads = 256;
 constexpr int kFireGraphSteps = 8;
 
-struct FireState {
-  int status;
-  int rejected_now;
-  int zero_v;
-  int pad0;
-  double dt, alpha, cv, cf;
-  long long n_pos, step, stage_step, rejected;
-  double phi_hi, phi_lo, smax_hi, smax_lo;
-  double best_smax;
-  long long best_step;
-  // parameters
-  double dt_max, alpha_start, f_alpha, f_inc, f_dec;
-  long long n_min, stall_window, max_steps;
-  double target, stage_floor;
-};
+__device__ __forceinline__ FireState* fstate(const CfgDev& c) { return reinterpret_cast<FireState*>(c.fs); }
 
-__global__ void __launch_bounds__(kFireThreads) k_fire_dots(const FireState* __restrict__ fs, int64_t nd,
-                                                            const double* __restrict__ F, const double* __restrict__ v,
-                                                            double* __restrict__ part) {
-  if (fs->status) return;
+// grid (blocks per member, members)
+__global__ void __launch_bounds__(kFireThreads) k_fire_dots(const CfgDev* __restrict__ cfgs, const int* __restrict__ all) {
+  const CfgDev& c = cfgs[all[blockIdx.y]];
+  const FireState* fs = fstate(c);
+  if (fs->status || (int)blockIdx.x >= c.nb_fire) return;
   __shared__ double sh[3][kFireThreads];
+  const int64_t nd = (int64_t)c.d * c.N;
   double p = 0, f2 = 0, v2 = 0;
-  for (int64_t i = (int64_t)blockIdx.x * kFireThreads + threadIdx.x; i < nd; i += (int64_t)gridDim.x * kFireThreads) {
-    double f = F[i], w = v[i];
+  for (int64_t i = (int64_t)blockIdx.x * kFireThreads + threadIdx.x; i < nd; i += (int64_t)c.nb_fire * kFireThreads) {
+    double f = c.F_hi[i], w = c.v_hi[i];
     p = fma(f, w, p);
     f2 = fma(f, f, f2);
     v2 = fma(w, w, v2);
@@ -69,16 +57,21 @@ __global__ void __launch_bounds__(kFireThreads) k_fire_dots(const FireState* __r
     __syncthreads();
   }
   if (threadIdx.x == 0)
-    for (int q = 0; q < 3; q++) part[q * gridDim.x + blockIdx.x] = sh[q][0];
+    for (int q = 0; q < 3; q++) c.fdots[q * c.nb_fire + blockIdx.x] = sh[q][0];
 }
 
-__global__ void k_fire_ctrl(FireState* fs, const double* __restrict__ part, int nb) {
+// one thread per member
+__global__ void k_fire_ctrl(const CfgDev* __restrict__ cfgs, const int* __restrict__ all, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const CfgDev& c = cfgs[all[i]];
+  FireState* fs = fstate(c);
   if (fs->status) return;
   double P = 0, f2 = 0, v2 = 0;
-  for (int b = 0; b < nb; b++) {  // fixed order
-    P += part[b];
-    f2 += part[nb + b];
-    v2 += part[2 * nb + b];
+  for (int b = 0; b < c.nb_fire; b++) {  // fixed order
+    P += c.fdots[b];
+    f2 += c.fdots[c.nb_fire + b];
+    v2 += c.fdots[2 * c.nb_fire + b];
   }
   if (P > 0) {
     fs->zero_v = 0;
@@ -99,31 +92,37 @@ __global__ void k_fire_ctrl(FireState* fs, const double* __restrict__ part, int 
   }
 }
 
-__global__ void k_fire_move(const FireState* __restrict__ fs, int64_t nd, double* s_hi, double* s_lo, double* v_hi,
-                            double* v_lo, const double* __restrict__ F_hi, const double* __restrict__ F_lo,
-                            double* bs_hi, double* bs_lo, double* bF_hi, double* bF_lo, dd inv_L) {
+// grid (coordinate blocks, members)
+__global__ void k_fire_move(const CfgDev* __restrict__ cfgs, const int* __restrict__ all) {
+  const CfgDev& c = cfgs[all[blockIdx.y]];
+  const FireState* fs = fstate(c);
   if (fs->status) return;
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nd) return;
-  dd F = dd_make(F_hi[i], F_lo[i]);
-  dd v = fs->zero_v ? dd_make(0.0) : dd_add(dd_mul_d(dd_make(v_hi[i], v_lo[i]), fs->cv), dd_mul_d(F, fs->cf));
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)c.d * c.N) return;
+  dd F = dd_make(c.F_hi[i], c.F_lo[i]);
+  dd v = fs->zero_v ? dd_make(0.0) : dd_add(dd_mul_d(dd_make(c.v_hi[i], c.v_lo[i]), fs->cv), dd_mul_d(F, fs->cf));
   v = dd_add(v, dd_mul_d(F, fs->dt));
-  v_hi[i] = v.hi;
-  v_lo[i] = v.lo;
-  dd s = dd_make(s_hi[i], s_lo[i]);
-  bs_hi[i] = s.hi;
-  bs_lo[i] = s.lo;
-  bF_hi[i] = F.hi;
-  bF_lo[i] = F.lo;
-  s = dd_frac(dd_add(s, dd_mul(dd_mul_d(v, fs->dt), inv_L)));
-  s_hi[i] = s.hi;
-  s_lo[i] = s.lo;
+  c.v_hi[i] = v.hi;
+  c.v_lo[i] = v.lo;
+  dd s = dd_make(c.s_hi[i], c.s_lo[i]);
+  c.bs_hi[i] = s.hi;
+  c.bs_lo[i] = s.lo;
+  c.bF_hi[i] = F.hi;
+  c.bF_lo[i] = F.lo;
+  s = dd_frac(dd_add(s, dd_mul(dd_mul_d(v, fs->dt), c.inv_L)));
+  c.s_hi[i] = s.hi;
+  c.s_lo[i] = s.lo;
 }
 
-__global__ void k_fire_accept(FireState* fs, const double* __restrict__ scal) {
+// one thread per member
+__global__ void k_fire_accept(const CfgDev* __restrict__ cfgs, const int* __restrict__ all, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const CfgDev& c = cfgs[all[i]];
+  FireState* fs = fstate(c);
   if (fs->status) return;
-  dd phi = dd_make(scal[kScPhiHi], scal[kScPhiLo]);
-  dd smx = dd_make(scal[kScSmaxHi], scal[kScSmaxLo]);
+  dd phi = dd_make(c.scal[kScPhiHi], c.scal[kScPhiLo]);
+  dd smx = dd_make(c.scal[kScSmaxHi], c.scal[kScSmaxLo]);
   fs->step++;
   fs->stage_step++;
   if (!isfinite(phi.hi) || !isfinite(smx.hi)) {
@@ -160,26 +159,31 @@ __global__ void k_fire_accept(FireState* fs, const double* __restrict__ scal) {
 }
 
 // Undo of a rejected step.  Runs whatever the status, so the state the host reads is the accepted one; a
-// repeated undo restores the same saved copy again.
-__global__ void k_fire_restore(const FireState* __restrict__ fs, int64_t nd, double* s_hi, double* s_lo, double* v_hi,
-                               double* v_lo, double* F_hi, double* F_lo, const double* __restrict__ bs_hi,
-                               const double* __restrict__ bs_lo, const double* __restrict__ bF_hi,
-                               const double* __restrict__ bF_lo) {
-  if (!fs->rejected_now) return;
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nd) return;
-  s_hi[i] = bs_hi[i];
-  s_lo[i] = bs_lo[i];
-  F_hi[i] = bF_hi[i];
-  F_lo[i] = bF_lo[i];
-  v_hi[i] = 0.0;
-  v_lo[i] = 0.0;
+// repeated undo restores the same saved copy again.  Grid (coordinate blocks, members).
+__global__ void k_fire_restore(const CfgDev* __restrict__ cfgs, const int* __restrict__ all) {
+  const CfgDev& c = cfgs[all[blockIdx.y]];
+  if (!fstate(c)->rejected_now) return;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)c.d * c.N) return;
+  c.s_hi[i] = c.bs_hi[i];
+  c.s_lo[i] = c.bs_lo[i];
+  c.F_hi[i] = c.bF_hi[i];
+  c.F_lo[i] = c.bF_lo[i];
+  c.v_hi[i] = 0.0;
+  c.v_lo[i] = 0.0;
 }
 
-// New stage: the accepted energy, S_max and force are those of this precision at the current positions.
-__global__ void k_fire_stage_init(FireState* fs, const double* __restrict__ scal, int first, FireState params) {
-  if (first) {
-    *fs = params;
+// New stage for members idx[0..n): the accepted energy, S_max and force are those of the stage's precision at the
+// current positions (already in scal / F).  first[t]: a new run (parameters and counters; v is zeroed apart).
+__global__ void k_fire_stage_init(const CfgDev* __restrict__ cfgs, const int* __restrict__ idx, int n,
+                                  const FireState* __restrict__ params, const int* __restrict__ first) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const CfgDev& c = cfgs[idx[t]];
+  FireState* fs = fstate(c);
+  const FireState& prm = params[t];
+  if (first[t]) {
+    *fs = prm;
     fs->step = 0;
     fs->rejected = 0;
     fs->n_pos = 0;
@@ -187,113 +191,105 @@ __global__ void k_fire_stage_init(FireState* fs, const double* __restrict__ scal
   fs->status = kFsRunning;
   fs->rejected_now = 0;
   fs->stage_step = 0;
-  fs->phi_hi = scal[kScPhiHi];
-  fs->phi_lo = scal[kScPhiLo];
-  fs->smax_hi = scal[kScSmaxHi];
-  fs->smax_lo = scal[kScSmaxLo];
+  fs->stage = prm.stage;
+  fs->phi_hi = c.scal[kScPhiHi];
+  fs->phi_lo = c.scal[kScPhiLo];
+  fs->smax_hi = c.scal[kScSmaxHi];
+  fs->smax_lo = c.scal[kScSmaxLo];
   fs->best_smax = fs->smax_hi + fs->smax_lo;
   fs->best_step = 0;
-  fs->stage_floor = params.stage_floor;
-  fs->stall_window = params.stall_window;
+  fs->stage_floor = prm.stage_floor;
+  fs->stall_window = prm.stall_window;
   double sm = fs->best_smax;
   if (!isfinite(sm) || !isfinite(fs->phi_hi)) fs->status = kFsNan;
   else if (sm <= fs->target) fs->status = kFsConverged;
   else if (fs->stage_floor > 0 && sm <= fs->stage_floor) fs->status = kFsStageDone;
 }
 
+// v = 0 for the members idx[t] with first[t]; grid (coordinate blocks, n)
+__global__ void k_fire_zero_v(const CfgDev* __restrict__ cfgs, const int* __restrict__ idx, const int* __restrict__ first) {
+  if (!first[blockIdx.y]) return;
+  const CfgDev& c = cfgs[idx[blockIdx.y]];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)c.d * c.N) return;
+  c.v_hi[i] = 0.0;
+  c.v_lo[i] = 0.0;
+}
+
 // ------------------------------------------------------------------------------------------------ host
 
 struct FireBufs {
   DevBuf v_hi, v_lo, bs_hi, bs_lo, bF_hi, bF_lo, part, fs;
-  FireState* h_fs = nullptr;  // pinned
+  DevBuf init_idx, init_prm, init_first;  // arguments of k_fire_stage_init (single context)
+  FireState* h_fs = nullptr;               // pinned
+  Engine* eng[3] = {nullptr, nullptr, nullptr};             // this context alone, minimising in precision p
   cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};   // kFireGraphSteps steps
   cudaGraphExec_t graph1[3] = {nullptr, nullptr, nullptr};  // one step
   int nb = 0;
   bool begun = false;
 };
 
-static cudaError_t fire_alloc(Ctx* c) {
+cudaError_t fire_alloc(Ctx* c) {
   if (c->fire) return cudaSuccess;
   FireBufs* f = new FireBufs();
   size_t nd = (size_t)c->d * c->N;
   cudaError_t e = cudaSuccess;
   for (DevBuf* b : {&f->v_hi, &f->v_lo, &f->bs_hi, &f->bs_lo, &f->bF_hi, &f->bF_lo}) {
-    b->bytes = nd * 8;
+    b->bytes = std::max<size_t>(nd * 8, 16);
     if (e == cudaSuccess) e = cudaMalloc(&b->p, b->bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->p, 0, b->bytes, c->stream);
   }
-  f->nb = (int)std::min<int64_t>(256, ((int64_t)nd + kFireThreads - 1) / kFireThreads);
+  f->nb = (int)std::max<int64_t>(1, std::min<int64_t>(256, ((int64_t)nd + kFireThreads - 1) / kFireThreads));
   f->part.bytes = sizeof(double) * 3 * f->nb;
   if (e == cudaSuccess) e = cudaMalloc(&f->part.p, f->part.bytes);
   f->fs.bytes = sizeof(FireState);
   if (e == cudaSuccess) e = cudaMalloc(&f->fs.p, f->fs.bytes);
+  if (e == cudaSuccess) e = cudaMemsetAsync(f->fs.p, 0, f->fs.bytes, c->stream);
+  for (DevBuf* b : {&f->init_idx, &f->init_prm, &f->init_first}) {
+    b->bytes = sizeof(FireState);
+    if (e == cudaSuccess) e = cudaMalloc(&b->p, b->bytes);
+  }
   if (e == cudaSuccess) e = cudaMallocHost(&f->h_fs, sizeof(FireState));
   c->fire = f;
+  // the context's own engine now carries the minimiser pointers too (still without a status word)
+  if (e == cudaSuccess) e = engine_build(c->eng, {c}, {-1}, false, c->stream);
   return e;
+}
+
+void fire_fill_cfgdev(const Ctx* c, CfgDev* g) {
+  const FireBufs* f = c->fire;
+  g->fs = f->fs.p;
+  g->v_hi = (double*)f->v_hi.p;
+  g->v_lo = (double*)f->v_lo.p;
+  g->bs_hi = (double*)f->bs_hi.p;
+  g->bs_lo = (double*)f->bs_lo.p;
+  g->bF_hi = (double*)f->bF_hi.p;
+  g->bF_lo = (double*)f->bF_lo.p;
+  g->fdots = (double*)f->part.p;
+  g->nb_fire = f->nb;
+  g->run = &reinterpret_cast<FireState*>(f->fs.p)->status;
 }
 
 void fire_free(Ctx* c) {
   FireBufs* f = c->fire;
   if (!f) return;
-  for (DevBuf* b : {&f->v_hi, &f->v_lo, &f->bs_hi, &f->bs_lo, &f->bF_hi, &f->bF_lo, &f->part, &f->fs})
+  for (DevBuf* b : {&f->v_hi, &f->v_lo, &f->bs_hi, &f->bs_lo, &f->bF_hi, &f->bF_lo, &f->part, &f->fs, &f->init_idx,
+                    &f->init_prm, &f->init_first})
     if (b->p) cudaFree(b->p);
   if (f->h_fs) cudaFreeHost(f->h_fs);
   for (int p = 0; p < 3; p++) {
     if (f->graph[p]) cudaGraphExecDestroy(f->graph[p]);
     if (f->graph1[p]) cudaGraphExecDestroy(f->graph1[p]);
+    if (f->eng[p]) {
+      engine_free(f->eng[p]);
+      delete f->eng[p];
+    }
   }
   delete f;
   c->fire = nullptr;
 }
 
-// One FIRE step as stream work (captured into a graph by the caller).
-static cudaError_t fire_step(Ctx* c, int prec) {
-  FireBufs* f = c->fire;
-  cudaStream_t st = c->stream;
-  const int64_t nd = (int64_t)c->d * c->N;
-  FireState* fs = (FireState*)f->fs.p;
-  prof_begin(c, kKFire);
-  k_fire_dots<<<f->nb, kFireThreads, 0, st>>>(fs, nd, (const double*)c->F_hi.p, (const double*)f->v_hi.p,
-                                              (double*)f->part.p);
-  k_fire_ctrl<<<1, 1, 0, st>>>(fs, (const double*)f->part.p, f->nb);
-  const unsigned g = (unsigned)((nd + 255) / 256);
-  k_fire_move<<<g, 256, 0, st>>>(fs, nd, (double*)c->s_hi.p, (double*)c->s_lo.p, (double*)f->v_hi.p,
-                                 (double*)f->v_lo.p, (const double*)c->F_hi.p, (const double*)c->F_lo.p,
-                                 (double*)f->bs_hi.p, (double*)f->bs_lo.p, (double*)f->bF_hi.p, (double*)f->bF_lo.p,
-                                 c->inv_L);
-  prof_end(c);
-  c->run_flag = &fs->status;
-  cudaError_t e = eval_phi_grad(c, prec, true);
-  c->run_flag = nullptr;
-  if (e != cudaSuccess) return e;
-  prof_begin(c, kKFire);
-  k_fire_accept<<<1, 1, 0, st>>>(fs, (const double*)c->scal.p);
-  k_fire_restore<<<g, 256, 0, st>>>(fs, nd, (double*)c->s_hi.p, (double*)c->s_lo.p, (double*)f->v_hi.p,
-                                    (double*)f->v_lo.p, (double*)c->F_hi.p, (double*)c->F_lo.p,
-                                    (const double*)f->bs_hi.p, (const double*)f->bs_lo.p,
-                                    (const double*)f->bF_hi.p, (const double*)f->bF_lo.p);
-  prof_end(c);
-  return cudaGetLastError();
-}
-
-static cudaError_t fire_graph(Ctx* c, int prec, cudaGraphExec_t* out, int steps = kFireGraphSteps) {
-  FireBufs* f = c->fire;
-  cudaGraphExec_t* slot = steps == 1 ? &f->graph1[prec] : &f->graph[prec];
-  if (*slot) { *out = *slot; return cudaSuccess; }
-  bool prof = c->prof.on;
-  c->prof.on = false;  // no profiler events inside a capture
-  cudaGraph_t graph = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
-  for (int s = 0; s < steps && e == cudaSuccess; s++) e = fire_step(c, prec);
-  cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
-  c->prof.on = prof;
-  if (e == cudaSuccess) e = e2;
-  if (e == cudaSuccess) e = cudaGraphInstantiate(slot, graph, 0);
-  if (graph) cudaGraphDestroy(graph);
-  if (e == cudaSuccess) *out = *slot;
-  return e;
-}
-
-static FireState params_to_state(const ssh_min_params* p) {
+FireState fire_params(const ssh_min_params* p) {
   FireState prm;
   memset(&prm, 0, sizeof prm);
   prm.dt = p->dt0;
@@ -311,35 +307,131 @@ static FireState params_to_state(const ssh_min_params* p) {
   return prm;
 }
 
-// Stepper: state from the current positions in the first stage's precision (v = 0).
+// One FIRE step of every member of e as stream work.
+cudaError_t fire_step_engine(const Engine* e, cudaStream_t st, Prof* prof) {
+  if (e->nall == 0) return cudaSuccess;
+  const CfgDev* cfgs = e->view[0].cfgs;
+  const unsigned gm = (unsigned)std::max<int64_t>(1, (e->maxND_all + 255) / 256);
+  const unsigned gt = (unsigned)((e->nall + 127) / 128);
+  prof_begin(prof, st, kKFire);
+  k_fire_dots<<<dim3((unsigned)std::max(1, e->max_nb_fire), (unsigned)e->nall), kFireThreads, 0, st>>>(cfgs, e->all);
+  k_fire_ctrl<<<gt, 128, 0, st>>>(cfgs, e->all, e->nall);
+  k_fire_move<<<dim3(gm, (unsigned)e->nall), 256, 0, st>>>(cfgs, e->all);
+  prof_end(prof, st);
+  for (int p = 0; p < 3; p++) {
+    if (e->view[p].nlist == 0) continue;
+    cudaError_t err = engine_eval(e, p, true, st, prof);
+    if (err != cudaSuccess) return err;
+  }
+  prof_begin(prof, st, kKFire);
+  k_fire_accept<<<gt, 128, 0, st>>>(cfgs, e->all, e->nall);
+  k_fire_restore<<<dim3(gm, (unsigned)e->nall), 256, 0, st>>>(cfgs, e->all);
+  prof_end(prof, st);
+  return cudaGetLastError();
+}
+
+static cudaError_t stage_init_launch(const CfgDev* cfgs, int64_t maxND, const int* d_idx, int n, const FireState* d_prm,
+                                     const int* d_first, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_fire_zero_v<<<dim3((unsigned)std::max<int64_t>(1, (maxND + 255) / 256), (unsigned)n), 256, 0, st>>>(cfgs, d_idx,
+                                                                                                       d_first);
+  k_fire_stage_init<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(cfgs, d_idx, n, d_prm, d_first);
+  return cudaGetLastError();
+}
+
+cudaError_t fire_stage_init_engine(const Engine* e, const std::vector<int>& idx, const std::vector<FireState>& params,
+                                   const std::vector<int>& first, cudaStream_t st) {
+  const int n = (int)idx.size();
+  if (n == 0) return cudaSuccess;
+  // small, short-lived argument arrays (batch and server set-up, never inside a capture)
+  void *di = nullptr, *dp = nullptr, *df = nullptr;
+  cudaError_t err = cudaMalloc(&di, sizeof(int) * n);
+  if (err == cudaSuccess) err = cudaMalloc(&dp, sizeof(FireState) * n);
+  if (err == cudaSuccess) err = cudaMalloc(&df, sizeof(int) * n);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(di, idx.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(dp, params.data(), sizeof(FireState) * n, cudaMemcpyHostToDevice, st);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(df, first.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st);
+  if (err == cudaSuccess)
+    err = stage_init_launch(e->view[0].cfgs, e->maxND_all, (const int*)di, n, (const FireState*)dp, (const int*)df, st);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(st);  // the host vectors and the arrays are released below
+  cudaFree(di);
+  cudaFree(dp);
+  cudaFree(df);
+  return err;
+}
+
+// ---- single context
+
+static cudaError_t fire_engine(Ctx* c, int prec, Engine** out) {
+  FireBufs* f = c->fire;
+  if (!f->eng[prec]) {
+    f->eng[prec] = new Engine();
+    cudaError_t e = engine_build(f->eng[prec], {c}, {prec}, true, c->stream);
+    if (e != cudaSuccess) return e;
+  }
+  *out = f->eng[prec];
+  return cudaSuccess;
+}
+
+static cudaError_t fire_graph(Ctx* c, int prec, cudaGraphExec_t* out, int steps = kFireGraphSteps) {
+  FireBufs* f = c->fire;
+  cudaGraphExec_t* slot = steps == 1 ? &f->graph1[prec] : &f->graph[prec];
+  if (*slot) { *out = *slot; return cudaSuccess; }
+  Engine* E = nullptr;
+  cudaError_t e = fire_engine(c, prec, &E);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+  for (int s = 0; s < steps && e == cudaSuccess; s++) e = fire_step_engine(E, c->stream, nullptr);
+  cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(slot, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e == cudaSuccess) *out = *slot;
+  return e;
+}
+
+// Start (first = 1) or continue a run in precision prec: Phi, S_max and F at the current positions, then the
+// stage initialisation.
+static cudaError_t single_stage_start(Ctx* c, int prec, const FireState& prm, int first) {
+  FireBufs* f = c->fire;
+  cudaStream_t st = c->stream;
+  cudaError_t e = engine_eval(c->eng, prec, true, st, nullptr);  // no status word: always evaluates
+  Engine* E = nullptr;
+  if (e == cudaSuccess) e = fire_engine(c, prec, &E);
+  int idx = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f->init_idx.p, &idx, sizeof(int), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f->init_prm.p, &prm, sizeof(FireState), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f->init_first.p, &first, sizeof(int), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = stage_init_launch(E->view[0].cfgs, E->maxND_all, (const int*)f->init_idx.p, 1, (const FireState*)f->init_prm.p,
+                          (const int*)f->init_first.p, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host arguments above live on this stack frame
+  return e;
+}
+
 ssh_status fire_begin(Ctx* c, const ssh_min_params* p) {
   cudaError_t e = fire_alloc(c);
   if (e != cudaSuccess) { set_error(std::string("ssh_fire_begin: allocation: ") + cudaGetErrorString(e)); return SSH_ENOMEM; }
-  FireBufs* f = c->fire;
-  cudaStream_t st = c->stream;
-  const int64_t nd = (int64_t)c->d * c->N;
-  cudaMemsetAsync(f->v_hi.p, 0, nd * 8, st);
-  cudaMemsetAsync(f->v_lo.p, 0, nd * 8, st);
-  e = eval_phi_grad(c, p->stage_prec[0], true);
-  if (e == cudaSuccess) {
-    k_fire_stage_init<<<1, 1, 0, st>>>((FireState*)f->fs.p, (const double*)c->scal.p, 1, params_to_state(p));
-    e = cudaGetLastError();
-  }
+  FireState prm = fire_params(p);
+  prm.stage = 0;
+  e = single_stage_start(c, p->stage_prec[0], prm, 1);
   if (e != cudaSuccess) { set_error(std::string("ssh_fire_begin: ") + cudaGetErrorString(e)); return SSH_ECUDA; }
-  f->begun = true;
+  c->fire->begun = true;
   return SSH_OK;
 }
 
-// Enqueue exactly nsteps FIRE steps in precision prec (no host synchronisation).
 ssh_status fire_steps(Ctx* c, int prec, int64_t nsteps) {
   if (!c->fire || !c->fire->begun) { set_error("ssh_fire_steps: call ssh_fire_begin first"); return SSH_EINVAL; }
-  cudaGraphExec_t g8 = nullptr, g1 = nullptr;
   cudaError_t e = cudaSuccess;
   if (c->prof.on) {  // profiling: direct launches, so every kernel of the step carries its own events
-    for (int64_t i = 0; e == cudaSuccess && i < nsteps; i++) e = fire_step(c, prec);
+    Engine* E = nullptr;
+    e = fire_engine(c, prec, &E);
+    for (int64_t i = 0; e == cudaSuccess && i < nsteps; i++) e = fire_step_engine(E, c->stream, &c->prof);
     if (e != cudaSuccess) { set_error(std::string("ssh_fire_steps: ") + cudaGetErrorString(e)); return SSH_ECUDA; }
     return SSH_OK;
   }
+  cudaGraphExec_t g8 = nullptr, g1 = nullptr;
   if (nsteps >= kFireGraphSteps) e = fire_graph(c, prec, &g8);
   if (e == cudaSuccess && nsteps % kFireGraphSteps) e = fire_graph(c, prec, &g1, 1);
   for (int64_t i = 0; e == cudaSuccess && i + kFireGraphSteps <= nsteps; i += kFireGraphSteps) e = cudaGraphLaunch(g8, c->stream);
@@ -348,7 +440,6 @@ ssh_status fire_steps(Ctx* c, int prec, int64_t nsteps) {
   return SSH_OK;
 }
 
-// Read the stepper state (synchronises the stream).  Returns the device status word in *dev_status.
 ssh_status fire_state(Ctx* c, ssh_min_result* r, int* dev_status) {
   if (!c->fire || !c->fire->begun) { set_error("ssh_fire_state: call ssh_fire_begin first"); return SSH_EINVAL; }
   FireBufs* f = c->fire;
@@ -380,43 +471,24 @@ ssh_status minimize(Ctx* c, const ssh_min_params* p, ssh_min_result* res) {
   }
   FireBufs* f = c->fire;
   cudaStream_t st = c->stream;
-  const int64_t nd = (int64_t)c->d * c->N;
-  cudaMemsetAsync(f->v_hi.p, 0, nd * 8, st);
-  cudaMemsetAsync(f->v_lo.p, 0, nd * 8, st);
-  FireState prm;
-  memset(&prm, 0, sizeof prm);
-  prm.dt = p->dt0;
-  prm.alpha = p->alpha_start;
-  prm.dt_max = p->dt_max;
-  prm.alpha_start = p->alpha_start;
-  prm.f_alpha = p->f_alpha;
-  prm.f_inc = p->f_inc;
-  prm.f_dec = p->f_dec;
-  prm.n_min = p->n_min;
-  prm.max_steps = p->max_steps;
-  prm.target = p->smax_target;
+  FireState prm = fire_params(p);
   ssh_min_result r;
   memset(&r, 0, sizeof r);
   r.status = SSH_ENOTCONV;
   int final_status = kFsStageDone;
-  FireState* fs = (FireState*)f->fs.p;
   const int64_t chunk_graphs = std::max<int64_t>(1, p->chunk / kFireGraphSteps);
   // the device stops at max_steps; the host gives up a little after that in case the status never changes
   const int64_t max_chunks = p->max_steps / (chunk_graphs * kFireGraphSteps) + 4;
   for (int s = 0; s < p->n_stages; s++) {
     const int prec = p->stage_prec[s];
     auto ts = std::chrono::steady_clock::now();
+    prm.stage = s;
     prm.stage_floor = s + 1 < p->n_stages ? p->stage_floor[s] : 0.0;
     prm.stall_window = p->stall_window[s];
-    // Phi and F of this precision at the current positions
-    e = eval_phi_grad(c, prec, true);
-    if (e == cudaSuccess) {
-      k_fire_stage_init<<<1, 1, 0, st>>>(fs, (const double*)c->scal.p, s == 0, prm);
-      e = cudaGetLastError();
-    }
+    e = single_stage_start(c, prec, prm, s == 0);
     cudaGraphExec_t g = nullptr;
     if (e == cudaSuccess) e = fire_graph(c, prec, &g);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(f->h_fs, fs, sizeof(FireState), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f->h_fs, f->fs.p, sizeof(FireState), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
       set_error(std::string("ssh_minimize: ") + cudaGetErrorString(e));
@@ -427,7 +499,7 @@ ssh_status minimize(Ctx* c, const ssh_min_params* p, ssh_min_result* res) {
     int64_t chunks = 0;
     while (status == kFsRunning) {
       for (int64_t q = 0; q < chunk_graphs && e == cudaSuccess; q++) e = cudaGraphLaunch(g, st);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(f->h_fs, fs, sizeof(FireState), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(f->h_fs, f->fs.p, sizeof(FireState), cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
       if (e != cudaSuccess) {
         set_error(std::string("ssh_minimize: ") + cudaGetErrorString(e));

@@ -1,6 +1,8 @@
 // kernels.cu -- the Phi + force hot path (Eqs. ntilde, energy, smax, force of arXiv:2304.09139) on sm_103a.
 //
-// One evaluation is seven launches on the context's stream:
+// One evaluation is seven launches; every kernel serves any number of configurations (a batch), each described
+// by a CfgDev.  The two hot kernels are persistent: their CTAs pull (configuration, tile) items from a queue
+// sorted largest-first.  The light kernels take the configuration from blockIdx.y.
 //   k_twiddle     per-particle power tables T[row][j] = e^{2 pi i m s_{j,axis}} for the rows of the
 //                 table layout (prefix components, high and low digit of the last component)
 //   k_ntilde      n~(k) = sum_j e^{2 pi i n.s_j}: a thread owns up to 4 consecutive k of one column; a
@@ -157,87 +159,102 @@ struct PolFX {
   }
 };
 
-template <class T>
-__device__ __forceinline__ void st_tab(T* dst, const T& v) { *dst = v; }
+
+__device__ __forceinline__ bool stopped(const CfgDev& c) { return c.run && *c.run; }
 
 // ------------------------------------------------------------------------------------------------ kernels
 
 template <class P>
-__global__ void k_twiddle(const int* __restrict__ run, const TabRow* __restrict__ rows, int nrows, const double* __restrict__ s_hi,
-                          const double* __restrict__ s_lo, int64_t N, int64_t Npad, typename P::Tab* __restrict__ tab) {
-  if (run && *run) return;  // a finished minimisation turns captured launches into no-ops
-  int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)nrows * Npad) return;
-  int row = (int)(idx / Npad);
-  int64_t j = idx - (int64_t)row * Npad;
+__global__ void __launch_bounds__(kTwThreads) k_twiddle(const CfgDev* __restrict__ cfgs, const TwItem* __restrict__ items) {
+  const TwItem it = items[blockIdx.x];
+  const CfgDev& c = cfgs[it.cfg];
+  if (stopped(c)) return;  // a finished minimisation turns these launches into no-ops
+  const int64_t idx = it.start + threadIdx.x;
+  if (idx >= (int64_t)c.nrows * c.Npad) return;
+  const int row = (int)(idx / c.Npad);
+  const int64_t j = idx - (int64_t)row * c.Npad;
   typename P::Tab v;
-  if (j < N) {
-    TabRow r = rows[row];
-    v = P::phasor(r.m, s_hi[r.axis * N + j], s_lo[r.axis * N + j]);
+  if (j < c.N) {
+    const TabRow r = c.rows[row];
+    v = P::phasor(r.m, c.s_hi[r.axis * c.N + j], c.s_lo[r.axis * c.N + j]);
   } else {
     v = P::one();
   }
-  tab[idx] = v;
+  reinterpret_cast<typename P::Tab*>(c.tab)[idx] = v;
 }
 
+// Persistent: each CTA takes (configuration, k-block, particle split) items until the queue is empty.
 template <class P>
-__global__ void __launch_bounds__(kNtThreads) k_ntilde(const int* __restrict__ run, const NtSlot* __restrict__ slots, const NtBlock* __restrict__ blocks,
-                                                       const int32_t* __restrict__ g_rows,
-                                                       const typename P::Tab* __restrict__ tab, int64_t ld, int64_t N,
-                                                       int64_t plen, int pchunk, int lo_base, int64_t M,
-                                                       typename P::Acc* __restrict__ part) {
-  if (run && *run) return;  // a finished minimisation turns captured launches into no-ops
+__global__ void __launch_bounds__(kNtThreads) k_ntilde(const CfgDev* __restrict__ cfgs, const NtItem* __restrict__ items,
+                                                       int n_items, int* __restrict__ queue) {
   using Tab = typename P::Tab;
   using Ph = typename P::Ph;
+  constexpr int prec = P::kIdx;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_item;
   Tab* sm = reinterpret_cast<Tab*>(smem_raw);
-  const NtBlock blk = blocks[blockIdx.x];
-  const int64_t j_begin = (int64_t)blockIdx.y * plen;
-  const int64_t j_end = min(N, j_begin + plen);
-  const int nrow = blk.ng + kDigit;
-  const int stride = nrow | 1;
-  const bool active = (int)threadIdx.x < blk.nslots;
-  NtSlot sl;
-  if (active) sl = slots[blk.slot0 + threadIdx.x];
-  else { sl.k0 = 0; sl.cnt = 0; sl.g = 0; sl.r0 = 0; }
-  typename P::Acc acc[kSlotK];
-#pragma unroll
-  for (int i = 0; i < kSlotK; i++) P::acc_zero(acc[i]);
-  for (int64_t j0 = j_begin; j0 < j_end; j0 += pchunk) {
-    const int pc = (int)min((int64_t)pchunk, j_end - j0);
+  for (;;) {
+    __syncthreads();  // the previous item is finished with shared memory and s_item
+    if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < nrow * pc; idx += blockDim.x) {
-      const int row = idx / pc, jj = idx - row * pc;
-      const int64_t j = j0 + jj;
-      Ph v;
-      if (row < blk.ng) {
-        const int32_t* gr = g_rows + (int64_t)(blk.g0 + row) * kMaxDim;
-        v = P::load(tab + (int64_t)gr[kMaxDim - 1] * ld + j);
+    const int ii = s_item;
+    if (ii >= n_items) return;
+    const NtItem it = items[ii];
+    const CfgDev& c = cfgs[it.cfg];
+    if (stopped(c)) continue;
+    const Tab* __restrict__ tab = reinterpret_cast<const Tab*>(c.tab);
+    const int64_t ld = c.Npad;
+    const NtBlock blk = c.blocks[it.blk];
+    const int64_t plen = c.plen[prec];
+    const int pchunk = c.pchunk[prec];
+    const int64_t j_begin = (int64_t)it.ps * plen;
+    const int64_t j_end = min(c.N, j_begin + plen);
+    const int nrow = blk.ng + kDigit;
+    const int stride = nrow | 1;
+    const bool active = (int)threadIdx.x < blk.nslots;
+    NtSlot sl;
+    if (active) sl = c.slots[blk.slot0 + threadIdx.x];
+    else { sl.k0 = 0; sl.cnt = 0; sl.g = 0; sl.r0 = 0; }
+    typename P::Acc acc[kSlotK];
 #pragma unroll
-        for (int a = 0; a < kMaxDim - 1; a++)
-          if (gr[a] >= 0) v = P::mul(v, P::load(tab + (int64_t)gr[a] * ld + j));
-      } else {
-        v = P::load(tab + (int64_t)(lo_base + row - blk.ng) * ld + j);
+    for (int i = 0; i < kSlotK; i++) P::acc_zero(acc[i]);
+    for (int64_t j0 = j_begin; j0 < j_end; j0 += pchunk) {
+      const int pc = (int)min((int64_t)pchunk, j_end - j0);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < nrow * pc; idx += blockDim.x) {
+        const int row = idx / pc, jj = idx - row * pc;
+        const int64_t j = j0 + jj;
+        Ph v;
+        if (row < blk.ng) {
+          const int32_t* gr = c.g_rows + (int64_t)(blk.g0 + row) * kMaxDim;
+          v = P::load(tab + (int64_t)gr[kMaxDim - 1] * ld + j);
+#pragma unroll
+          for (int a = 0; a < kMaxDim - 1; a++)
+            if (gr[a] >= 0) v = P::mul(v, P::load(tab + (int64_t)gr[a] * ld + j));
+        } else {
+          v = P::load(tab + (int64_t)(c.lo_base + row - blk.ng) * ld + j);
+        }
+        sm[jj * stride + row] = v;
       }
-      sm[jj * stride + row] = v;
-    }
-    __syncthreads();
-    if (active) {
-      for (int jj = 0; jj < pc; jj++) {
-        const Tab* rp = sm + jj * stride;
-        const Ph G = rp[sl.g];
-        const Tab* lp = rp + blk.ng + sl.r0;
+      __syncthreads();
+      if (active) {
+        for (int jj = 0; jj < pc; jj++) {
+          const Tab* rp = sm + jj * stride;
+          const Ph G = rp[sl.g];
+          const Tab* lp = rp + blk.ng + sl.r0;
 #pragma unroll
-        for (int i = 0; i < kSlotK; i++) {
-          if (i < sl.cnt) P::acc_add(acc[i], P::mul(G, lp[i]));
+          for (int i = 0; i < kSlotK; i++) {
+            if (i < sl.cnt) P::acc_add(acc[i], P::mul(G, lp[i]));
+          }
         }
       }
     }
-  }
-  if (active) {
+    if (active) {
+      typename P::Acc* part = reinterpret_cast<typename P::Acc*>(c.part) + (int64_t)it.ps * c.M;
 #pragma unroll
-    for (int i = 0; i < kSlotK; i++)
-      if (i < sl.cnt) part[(int64_t)blockIdx.y * M + sl.k0 + i] = acc[i];
+      for (int i = 0; i < kSlotK; i++)
+        if (i < sl.cnt) part[sl.k0 + i] = acc[i];
+    }
   }
 }
 
@@ -273,45 +290,50 @@ __device__ __forceinline__ void block_reduce(RedPart& v, RedPart* sh) {
   v = sh[0];
 }
 
+// grid (k blocks, configurations of this precision)
 template <class P>
-__global__ void __launch_bounds__(kRedThreads) k_nt_reduce(const int* __restrict__ run, const typename P::Acc* __restrict__ part, int psplit, int64_t M,
-                                                           double* C_hi, double* C_lo, double* S_hi, double* S_lo,
-                                                           RedPart* blk) {
-  if (run && *run) return;  // a finished minimisation turns captured launches into no-ops
+__global__ void __launch_bounds__(kRedThreads) k_nt_reduce(const CfgDev* __restrict__ cfgs, const int* __restrict__ list) {
+  const CfgDev& c = cfgs[list[blockIdx.y]];
+  if (stopped(c) || (int)blockIdx.x >= c.nblk) return;  // uniform per block
   __shared__ RedPart sh[kRedThreads];
-  int64_t k = (int64_t)blockIdx.x * kRedThreads + threadIdx.x;
+  const int64_t k = (int64_t)blockIdx.x * kRedThreads + threadIdx.x;
+  const int64_t M = c.M;
+  const typename P::Acc* part = reinterpret_cast<const typename P::Acc*>(c.part);
   RedPart v = {0, 0, 0, 0, 0, 0, 0, 0};
   if (k < M) {
     typename P::Acc a = part[k];
-    for (int p = 1; p < psplit; p++) P::acc_add_acc(a, part[(int64_t)p * M + k]);
-    dd c, s;
-    P::acc_to_dd(a, &c, &s);
-    C_hi[k] = c.hi;
-    C_lo[k] = c.lo;
-    S_hi[k] = s.hi;
-    S_lo[k] = s.lo;
-    dd a2 = dd_add(dd_sqr(c), dd_sqr(s));
+    for (int p = 1; p < c.psplit[P::kIdx]; p++) P::acc_add_acc(a, part[(int64_t)p * M + k]);
+    dd cc, ss;
+    P::acc_to_dd(a, &cc, &ss);
+    c.C_hi[k] = cc.hi;
+    c.C_lo[k] = cc.lo;
+    c.S_hi[k] = ss.hi;
+    c.S_lo[k] = ss.lo;
+    dd a2 = dd_add(dd_sqr(cc), dd_sqr(ss));
     v.phi_hi = a2.hi;
     v.phi_lo = a2.lo;
     v.a2max_hi = a2.hi;
     v.a2max_lo = a2.lo;
-    v.cmax = fmax(fabs(c.hi), fabs(s.hi));
+    v.cmax = fmax(fabs(cc.hi), fabs(ss.hi));
   }
   block_reduce(v, sh);
-  if (threadIdx.x == 0) blk[blockIdx.x] = v;
+  if (threadIdx.x == 0) reinterpret_cast<RedPart*>(c.blk)[blockIdx.x] = v;
 }
 
-// scal[kScPhiHi..] as listed in ssh_internal.h.  Scale exponent e: |C|, |S| < 2^(e-1).
-__global__ void __launch_bounds__(kRedThreads) k_finalize(const int* __restrict__ run, const RedPart* __restrict__ blk, int nblk, double N, double* scal) {
-  if (run && *run) return;  // a finished minimisation turns captured launches into no-ops
+// scal[kScPhiHi..] as listed in ssh_internal.h.  Scale exponent e: |C|, |S| < 2^(e-1).  Grid (1, configs).
+__global__ void __launch_bounds__(kRedThreads) k_finalize(const CfgDev* __restrict__ cfgs, const int* __restrict__ list) {
+  const CfgDev& c = cfgs[list[blockIdx.y]];
+  if (stopped(c)) return;
   __shared__ RedPart sh[kRedThreads];
+  const RedPart* blk = reinterpret_cast<const RedPart*>(c.blk);
   RedPart v = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int i = threadIdx.x; i < nblk; i += kRedThreads) red_combine(v, blk[i]);
+  for (int i = threadIdx.x; i < c.nblk; i += kRedThreads) red_combine(v, blk[i]);
   block_reduce(v, sh);
   if (threadIdx.x == 0) {
+    double* scal = c.scal;
     scal[kScPhiHi] = v.phi_hi;
     scal[kScPhiLo] = v.phi_lo;
-    dd sm = dd_div(dd_make(v.a2max_hi, v.a2max_lo), dd_make(N));
+    dd sm = c.N > 0 ? dd_div(dd_make(v.a2max_hi, v.a2max_lo), dd_make((double)c.N)) : dd_make(0.0);
     scal[kScSmaxHi] = sm.hi;
     scal[kScSmaxLo] = sm.lo;
     scal[kScCmax] = v.cmax;
@@ -322,101 +344,118 @@ __global__ void __launch_bounds__(kRedThreads) k_finalize(const int* __restrict_
 }
 
 template <class P>
-__global__ void k_coef(const int* __restrict__ run, const double* __restrict__ C_hi, const double* __restrict__ C_lo, const double* __restrict__ S_hi,
-                       const double* __restrict__ S_lo, const double* __restrict__ scal, int64_t M,
-                       typename P::Coef* __restrict__ coef) {
-  if (run && *run) return;  // a finished minimisation turns captured launches into no-ops
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= M) return;
-  int e = (int)scal[kScScaleExp];
-  coef[k] = P::make_coef(dd_make(C_hi[k], C_lo[k]), dd_make(S_hi[k], S_lo[k]), e);
+__global__ void k_coef(const CfgDev* __restrict__ cfgs, const int* __restrict__ list) {
+  const CfgDev& c = cfgs[list[blockIdx.y]];
+  if (stopped(c)) return;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= c.M) return;
+  const int e = (int)c.scal[kScScaleExp];
+  reinterpret_cast<typename P::Coef*>(c.coef)[k] =
+      P::make_coef(dd_make(c.C_hi[k], c.C_lo[k]), dd_make(c.S_hi[k], c.S_lo[k]), e);
 }
 
 __device__ __forceinline__ int floordiv_d(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
+// Persistent: each CTA takes (configuration, particle block, column split) items until the queue is empty.
 template <class P>
-__global__ void __launch_bounds__(kForceThreads) k_force(const int* __restrict__ run, const FCol* __restrict__ cols, const int32_t* __restrict__ fsplit,
-                                                         const typename P::Coef* __restrict__ coef,
-                                                         const typename P::Tab* __restrict__ tab, int64_t ld, int64_t N,
-                                                         int d, int hi_base, int qmin, int lo_base,
-                                                         typename P::RAcc* __restrict__ fpart) {
-  if (run && *run) return;  // a finished minimisation turns captured launches into no-ops
+__global__ void __launch_bounds__(kForceThreads) k_force(const CfgDev* __restrict__ cfgs, const FItem* __restrict__ items,
+                                                         int n_items, int* __restrict__ queue) {
   using Ph = typename P::Ph;
   using RAcc = typename P::RAcc;
-  const int64_t j = (int64_t)blockIdx.x * kForceThreads + threadIdx.x;
-  const int64_t jj = j < N ? j : N - 1;
-  const int ks = blockIdx.y;
-  const Ph b = P::load(tab + (int64_t)(lo_base + 1) * ld + jj);
-  RAcc F[kMaxDim];
+  __shared__ int s_item;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
+    __syncthreads();
+    const int ii = s_item;
+    if (ii >= n_items) return;
+    const FItem it = items[ii];
+    const CfgDev& c = cfgs[it.cfg];
+    if (stopped(c)) continue;
+    const typename P::Tab* __restrict__ tab = reinterpret_cast<const typename P::Tab*>(c.tab);
+    const typename P::Coef* __restrict__ coef = reinterpret_cast<const typename P::Coef*>(c.coef);
+    const int64_t ld = c.Npad, N = c.N;
+    const int d = c.d;
+    const int64_t j = (int64_t)it.pb * kForceThreads + threadIdx.x;
+    const int64_t jj = j < N ? j : N - 1;
+    const Ph b = P::load(tab + (int64_t)(c.lo_base + 1) * ld + jj);
+    RAcc F[kMaxDim];
 #pragma unroll
-  for (int a = 0; a < kMaxDim; a++) P::rzero(F[a]);
-  const int c_end = fsplit[ks + 1];
-  for (int c = fsplit[ks]; c < c_end; c++) {
-    const FCol col = cols[c];
-    Ph G = P::one();
-    const bool hasG = d > 1;
+    for (int a = 0; a < kMaxDim; a++) P::rzero(F[a]);
+    const int c_end = c.fsplit[it.ks + 1];
+    for (int ci = c.fsplit[it.ks]; ci < c_end; ci++) {
+      const FCol col = c.cols[ci];
+      Ph G = P::one();
+      const bool hasG = d > 1;
 #pragma unroll
-    for (int a = 0; a < kMaxDim - 1; a++) {
-      if (a + 1 < d) {
-        Ph t = P::load(tab + (int64_t)col.rows[a] * ld + jj);
-        G = a > 0 ? P::mul(G, t) : t;
-      }
-    }
-    int q = floordiv_d(col.nlo, kDigit);
-    int r = col.nlo - q * kDigit;
-    Ph th = P::load(tab + (int64_t)(hi_base + q - qmin) * ld + jj);
-    Ph z = hasG ? P::mul(G, th) : th;
-    if (r != 0) z = P::mul(z, P::load(tab + (int64_t)(lo_base + r) * ld + jj));
-    RAcc A, B;
-    P::rzero(A);
-    P::rzero(B);
-    for (int i = 0; i < col.len; i++) {
-      if (i > 0) {
-        if (++r == kDigit) {  // re-anchor at each digit boundary
-          r = 0;
-          q++;
-          th = P::load(tab + (int64_t)(hi_base + q - qmin) * ld + jj);
-          z = hasG ? P::mul(G, th) : th;
-        } else {
-          z = P::mul(z, b);
+      for (int a = 0; a < kMaxDim - 1; a++) {
+        if (a + 1 < d) {
+          Ph t = P::load(tab + (int64_t)col.rows[a] * ld + jj);
+          G = a > 0 ? P::mul(G, t) : t;
         }
       }
-      const typename P::Coef cf = coef[col.k0 + i];
-      P::radd(A, P::w(cf, z));
-      P::radd_r(B, A);
-    }
-    const RAcc last = P::rsub(P::rmul_int(A, col.nlo + col.len), B);
+      int q = floordiv_d(col.nlo, kDigit);
+      int r = col.nlo - q * kDigit;
+      Ph th = P::load(tab + (int64_t)(c.hi_base + q - c.qmin) * ld + jj);
+      Ph z = hasG ? P::mul(G, th) : th;
+      if (r != 0) z = P::mul(z, P::load(tab + (int64_t)(c.lo_base + r) * ld + jj));
+      RAcc A, B;
+      P::rzero(A);
+      P::rzero(B);
+      for (int i = 0; i < col.len; i++) {
+        if (i > 0) {
+          if (++r == kDigit) {  // re-anchor at each digit boundary
+            r = 0;
+            q++;
+            th = P::load(tab + (int64_t)(c.hi_base + q - c.qmin) * ld + jj);
+            z = hasG ? P::mul(G, th) : th;
+          } else {
+            z = P::mul(z, b);
+          }
+        }
+        const typename P::Coef cf = coef[col.k0 + i];
+        P::radd(A, P::w(cf, z));
+        P::radd_r(B, A);
+      }
+      const RAcc last = P::rsub(P::rmul_int(A, col.nlo + col.len), B);
 #pragma unroll
-    for (int a = 0; a < kMaxDim; a++) {
-      if (a + 1 < d) P::radd_r(F[a], P::rmul_int(A, col.pre[a < kMaxDim - 1 ? a : 0]));
-      else if (a + 1 == d) P::radd_r(F[a], last);
+      for (int a = 0; a < kMaxDim; a++) {
+        if (a + 1 < d) P::radd_r(F[a], P::rmul_int(A, col.pre[a < kMaxDim - 1 ? a : 0]));
+        else if (a + 1 == d) P::radd_r(F[a], last);
+      }
     }
-  }
-  if (j < N) {
+    if (j < N) {
+      RAcc* fpart = reinterpret_cast<RAcc*>(c.fpart);
 #pragma unroll
-    for (int a = 0; a < kMaxDim; a++)
-      if (a < d) fpart[((int64_t)ks * d + a) * N + j] = F[a];
+      for (int a = 0; a < kMaxDim; a++)
+        if (a < d) fpart[((int64_t)it.ks * d + a) * N + j] = F[a];
+    }
   }
 }
 
+// grid (coordinate blocks, configurations of this precision)
 template <class P>
-__global__ void k_f_reduce(const int* __restrict__ run, const typename P::RAcc* __restrict__ fpart, int ksplit, int64_t N, int d,
-                           const double* __restrict__ scal, dd pref, double* F_hi, double* F_lo) {
-  if (run && *run) return;  // a finished minimisation turns captured launches into no-ops
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // over d * N, [a][j]
-  if (i >= (int64_t)d * N) return;
+__global__ void k_f_reduce(const CfgDev* __restrict__ cfgs, const int* __restrict__ list) {
+  const CfgDev& c = cfgs[list[blockIdx.y]];
+  if (stopped(c)) return;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // over d * N, [a][j]
+  const int64_t nd = (int64_t)c.d * c.N;
+  if (i >= nd) return;
+  const typename P::RAcc* fpart = reinterpret_cast<const typename P::RAcc*>(c.fpart);
   typename P::RAcc s = fpart[i];
-  for (int k = 1; k < ksplit; k++) P::radd_r(s, fpart[(int64_t)k * d * N + i]);
-  dd f = dd_mul(P::r_to_dd(s), pref);
-  int e = P::kIdx == SSH_FX ? (int)scal[kScScaleExp] : 0;
-  F_hi[i] = ldexp(f.hi, e);
-  F_lo[i] = ldexp(f.lo, e);
+  for (int k = 1; k < c.ksplit; k++) P::radd_r(s, fpart[(int64_t)k * nd + i]);
+  dd f = dd_mul(P::r_to_dd(s), c.pref);
+  const int e = P::kIdx == SSH_FX ? (int)c.scal[kScScaleExp] : 0;
+  c.F_hi[i] = ldexp(f.hi, e);
+  c.F_lo[i] = ldexp(f.lo, e);
 }
 
 // ------------------------------------------------------------------------------------------------ host side
 
 static size_t tab_bytes(int prec) { return prec == SSH_FP64 ? 16 : 32; }
 
+// Launch shape of one configuration (depends on that configuration only, so its arithmetic -- and therefore
+// its result -- is the same alone and in any batch).
 void setup_launch(Ctx* c) {
   const int nblocks = (int)c->nt.blocks.size();
   const int target = c->sm_count * 2;
@@ -440,75 +479,100 @@ void setup_launch(Ctx* c) {
 }
 
 template <class P>
-static cudaError_t run_prec(Ctx* c, bool want_force) {
-  const int prec = P::kIdx;
-  const Launch& L = c->launch[prec];
-  cudaStream_t st = c->stream;
-  const int nrows = (int)c->tl.rows.size();
-  auto* tab = reinterpret_cast<typename P::Tab*>(c->tab.p);
-  {
-    int64_t total = (int64_t)nrows * c->Npad;
-    int thr = 128;
-    int64_t grid = (total + thr - 1) / thr;
-    prof_begin(c, kKTwiddle);
-    k_twiddle<P><<<(unsigned)grid, thr, 0, st>>>(c->run_flag, reinterpret_cast<const TabRow*>(c->rows.p), nrows,
-                                                  (const double*)c->s_hi.p, (const double*)c->s_lo.p, c->N, c->Npad, tab);
-    prof_end(c);
+static cudaError_t launch_prec(const EngineView& v, bool want_force, cudaStream_t st, Prof* prof) {
+  if (v.nlist == 0) return cudaSuccess;
+  if (v.ntw > 0) {
+    prof_begin(prof, st, kKTwiddle);
+    k_twiddle<P><<<(unsigned)v.ntw, kTwThreads, 0, st>>>(v.cfgs, v.tw);
+    prof_end(prof, st);
   }
-  if (c->M > 0) {
-    const int nb = (int)c->nt.blocks.size();
-    int64_t plen = (c->N + L.nt_psplit - 1) / L.nt_psplit;
-    plen = (plen + L.nt_pchunk - 1) / L.nt_pchunk * L.nt_pchunk;
-    int psplit = (int)((c->N + plen - 1) / plen);
-    dim3 grid(nb, psplit);
-    prof_begin(c, kKNtilde);
-    k_ntilde<P><<<grid, kNtThreads, L.nt_smem, st>>>(
-        c->run_flag,        reinterpret_cast<const NtSlot*>(c->slots.p), reinterpret_cast<const NtBlock*>(c->blocks.p),
-        (const int32_t*)c->grows.p, tab, c->Npad, c->N, plen, L.nt_pchunk, c->tl.lo_base, c->M,
-        reinterpret_cast<typename P::Acc*>(c->part.p));
-    prof_end(c);
-    int rb = (int)((c->M + kRedThreads - 1) / kRedThreads);
-    prof_begin(c, kKNtReduce);
-    k_nt_reduce<P><<<rb, kRedThreads, 0, st>>>(c->run_flag, reinterpret_cast<const typename P::Acc*>(c->part.p), psplit, c->M,
-                                               (double*)c->C_hi.p, (double*)c->C_lo.p, (double*)c->S_hi.p,
-                                               (double*)c->S_lo.p, reinterpret_cast<RedPart*>(c->blk.p));
-    prof_end(c);
-    prof_begin(c, kKFinalize);
-    k_finalize<<<1, kRedThreads, 0, st>>>(c->run_flag, reinterpret_cast<const RedPart*>(c->blk.p), rb, (double)c->N,
-                                          (double*)c->scal.p);
-    prof_end(c);
-  } else {
-    cudaMemsetAsync(c->scal.p, 0, sizeof(double) * kScCount, st);
+  if (v.nnt > 0) {
+    cudaMemsetAsync(v.counters, 0, sizeof(int), st);
+    const int grid = std::min(v.nnt, 2 * v.sm_count);
+    prof_begin(prof, st, kKNtilde);
+    k_ntilde<P><<<grid, kNtThreads, v.nt_smem, st>>>(v.cfgs, v.nt, v.nnt, v.counters);
+    prof_end(prof, st);
   }
+  const dim3 gr((unsigned)std::max(1, v.maxblk), (unsigned)v.nlist);
+  prof_begin(prof, st, kKNtReduce);
+  k_nt_reduce<P><<<gr, kRedThreads, 0, st>>>(v.cfgs, v.list);
+  prof_end(prof, st);
+  prof_begin(prof, st, kKFinalize);
+  k_finalize<<<dim3(1, (unsigned)v.nlist), kRedThreads, 0, st>>>(v.cfgs, v.list);
+  prof_end(prof, st);
   if (want_force) {
-    if (c->M > 0) {
-      int thr = 256;
-      prof_begin(c, kKCoef);
-      k_coef<P><<<(unsigned)((c->M + thr - 1) / thr), thr, 0, st>>>(
-          c->run_flag,          (const double*)c->C_hi.p, (const double*)c->C_lo.p, (const double*)c->S_hi.p, (const double*)c->S_lo.p,
-          (const double*)c->scal.p, c->M, reinterpret_cast<typename P::Coef*>(c->coef.p));
-      prof_end(c);
-      dim3 grid((unsigned)((c->N + kForceThreads - 1) / kForceThreads), L.f_ksplit);
-      const int32_t* fs = (const int32_t*)c->fsplit.p;  // one column split serves every precision
-      prof_begin(c, kKForce);
-      k_force<P><<<grid, kForceThreads, 0, st>>>(c->run_flag, reinterpret_cast<const FCol*>(c->cols.p), fs,
-                                                  reinterpret_cast<const typename P::Coef*>(c->coef.p), tab, c->Npad,
-                                                  c->N, c->d, c->tl.hi_base, c->tl.qmin, c->tl.lo_base,
-                                                  reinterpret_cast<typename P::RAcc*>(c->fpart.p));
-      prof_end(c);
-      int64_t tot = (int64_t)c->d * c->N;
-      prof_begin(c, kKFReduce);
-      k_f_reduce<P><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(
-          c->run_flag,          reinterpret_cast<const typename P::RAcc*>(c->fpart.p), L.f_ksplit, c->N, c->d, (const double*)c->scal.p,
-          c->pref, (double*)c->F_hi.p, (double*)c->F_lo.p);
-      prof_end(c);
-    } else {
-      cudaMemsetAsync(c->F_hi.p, 0, sizeof(double) * c->d * c->N, st);
-      cudaMemsetAsync(c->F_lo.p, 0, sizeof(double) * c->d * c->N, st);
+    const dim3 gc((unsigned)std::max<int64_t>(1, (v.maxM + 255) / 256), (unsigned)v.nlist);
+    prof_begin(prof, st, kKCoef);
+    k_coef<P><<<gc, 256, 0, st>>>(v.cfgs, v.list);
+    prof_end(prof, st);
+    if (v.nfi > 0) {
+      cudaMemsetAsync(v.counters + 1, 0, sizeof(int), st);
+      const int grid = std::min(v.nfi, 5 * v.sm_count);
+      prof_begin(prof, st, kKForce);
+      k_force<P><<<grid, kForceThreads, 0, st>>>(v.cfgs, v.fi, v.nfi, v.counters + 1);
+      prof_end(prof, st);
     }
+    const dim3 gf((unsigned)std::max<int64_t>(1, (v.maxND + 255) / 256), (unsigned)v.nlist);
+    prof_begin(prof, st, kKFReduce);
+    k_f_reduce<P><<<gf, 256, 0, st>>>(v.cfgs, v.list);
+    prof_end(prof, st);
   }
   return cudaGetLastError();
 }
+
+cudaError_t engine_eval(const Engine* e, int prec, bool want_force, cudaStream_t st, Prof* prof) {
+  switch (prec) {
+    case SSH_FP64: return launch_prec<PolF64>(e->view[prec], want_force, st, prof);
+    case SSH_DD: return launch_prec<PolDD>(e->view[prec], want_force, st, prof);
+    case SSH_FX: return launch_prec<PolFX>(e->view[prec], want_force, st, prof);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// dynamic shared memory above 48 KB is opted into once, never inside a stream capture
+void kernels_set_attributes(size_t smem_max) {
+  cudaFuncSetAttribute(k_ntilde<PolF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+  cudaFuncSetAttribute(k_ntilde<PolDD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+  cudaFuncSetAttribute(k_ntilde<PolFX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+}
+
+// ------------------------------------------------------------------------------------------------ profiler
+
+void prof_begin(Prof* p, cudaStream_t st, int id) {
+  if (!p || !p->on) return;
+  ProfRec r;
+  r.id = id;
+  if (!p->pool.empty()) { r.e0 = p->pool.back(); p->pool.pop_back(); }
+  else cudaEventCreate(&r.e0);
+  if (!p->pool.empty()) { r.e1 = p->pool.back(); p->pool.pop_back(); }
+  else cudaEventCreate(&r.e1);
+  cudaEventRecord(r.e0, st);
+  p->pending.push_back(r);
+}
+
+void prof_end(Prof* p, cudaStream_t st) {
+  if (!p || !p->on || p->pending.empty()) return;
+  cudaEventRecord(p->pending.back().e1, st);
+}
+
+cudaError_t prof_collect(Prof* p, cudaStream_t st) {
+  if (p->pending.empty()) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  for (ProfRec& r : p->pending) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) {
+      p->ms[r.id] += ms;
+      p->launches[r.id] += 1;
+    }
+    p->pool.push_back(r.e0);
+    p->pool.push_back(r.e1);
+  }
+  p->pending.clear();
+  return cudaSuccess;
+}
+
+// ------------------------------------------------------------------------------------------------ buffers
 
 static cudaError_t dev_alloc(DevBuf* b, size_t bytes) {
   if (bytes == 0) bytes = 16;
@@ -518,17 +582,17 @@ static cudaError_t dev_alloc(DevBuf* b, size_t bytes) {
 
 template <class T>
 static cudaError_t upload(DevBuf* b, const std::vector<T>& v, cudaStream_t st) {
-  cudaError_t e = dev_alloc(b, sizeof(T) * v.size());
+  cudaError_t e = dev_alloc(b, sizeof(T) * std::max<size_t>(1, v.size()));
   if (e != cudaSuccess || v.empty()) return e;
   return cudaMemcpyAsync(b->p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st);
 }
 
+// Plans and buffers of one configuration, then its own single-member engine.
 cudaError_t plan_upload(Ctx* c) {
   cudaStream_t st = c->stream;
   cudaError_t e;
   setup_launch(c);
-  // column split for the force kernel: equal numbers of wavevectors per split (same for every precision;
-  // sized for the largest split count)
+  // column split for the force kernel: equal numbers of wavevectors per split, the same for every precision
   int ks = 1;
   for (int p = 0; p < 3; p++) ks = std::max(ks, c->launch[p].f_ksplit);
   for (int p = 0; p < 3; p++) c->launch[p].f_ksplit = ks;
@@ -567,54 +631,18 @@ cudaError_t plan_upload(Ctx* c) {
   if ((e = dev_alloc(&c->F_hi, nd * 8)) != cudaSuccess) return e;
   if ((e = dev_alloc(&c->F_lo, nd * 8)) != cudaSuccess) return e;
   cudaMemsetAsync(c->scal.p, 0, sizeof(double) * kScCount, st);
-  // dynamic shared memory above 48 KB is opted into once here, never inside a stream capture
-  cudaFuncSetAttribute(k_ntilde<PolF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->launch[SSH_FP64].nt_smem);
-  cudaFuncSetAttribute(k_ntilde<PolDD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->launch[SSH_DD].nt_smem);
-  cudaFuncSetAttribute(k_ntilde<PolFX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->launch[SSH_FX].nt_smem);
+  cudaMemsetAsync(c->F_hi.p, 0, nd * 8, st);
+  cudaMemsetAsync(c->F_lo.p, 0, nd * 8, st);
+  size_t smem_max = 0;
+  for (int p = 0; p < 3; p++) smem_max = std::max(smem_max, c->launch[p].nt_smem);
+  kernels_set_attributes(std::max<size_t>(smem_max, 96 * 1024));
+  c->eng = new Engine();
+  if ((e = engine_build(c->eng, {c}, {-1}, false, st)) != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
-void prof_begin(Ctx* c, int id) {
-  if (!c->prof.on) return;
-  ProfRec r;
-  r.id = id;
-  if (!c->prof.pool.empty()) { r.e0 = c->prof.pool.back(); c->prof.pool.pop_back(); }
-  else cudaEventCreate(&r.e0);
-  if (!c->prof.pool.empty()) { r.e1 = c->prof.pool.back(); c->prof.pool.pop_back(); }
-  else cudaEventCreate(&r.e1);
-  cudaEventRecord(r.e0, c->stream);
-  c->prof.pending.push_back(r);
-}
-
-void prof_end(Ctx* c) {
-  if (!c->prof.on || c->prof.pending.empty()) return;
-  cudaEventRecord(c->prof.pending.back().e1, c->stream);
-}
-
-cudaError_t prof_collect(Ctx* c) {
-  if (c->prof.pending.empty()) return cudaSuccess;
-  cudaError_t e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) return e;
-  for (ProfRec& r : c->prof.pending) {
-    float ms = 0;
-    if (cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) {
-      c->prof.ms[r.id] += ms;
-      c->prof.launches[r.id] += 1;
-    }
-    c->prof.pool.push_back(r.e0);
-    c->prof.pool.push_back(r.e1);
-  }
-  c->prof.pending.clear();
-  return cudaSuccess;
-}
-
 cudaError_t eval_phi_grad(Ctx* c, int prec, bool want_force) {
-  switch (prec) {
-    case SSH_FP64: return run_prec<PolF64>(c, want_force);
-    case SSH_DD: return run_prec<PolDD>(c, want_force);
-    case SSH_FX: return run_prec<PolFX>(c, want_force);
-    default: return cudaErrorInvalidValue;
-  }
+  return engine_eval(c->eng, prec, want_force, c->stream, &c->prof);
 }
 
 }  // namespace ssh

@@ -49,6 +49,108 @@ struct Prof {
   int64_t launches[kKCount] = {0};
 };
 
+// ---- device-side view of one configuration: every pointer and size a kernel needs.  A single context is
+// a batch of one; a batch concatenates the descriptors of its members.
+struct CfgDev {
+  int d, nrows, lo_base, hi_base, qmin, ksplit, nblk, nb_fire;
+  int psplit[3], pchunk[3];
+  int64_t N, M, Npad;
+  int64_t plen[3];
+  double* s_hi;
+  double* s_lo;
+  const TabRow* rows;
+  const NtSlot* slots;
+  const NtBlock* blocks;
+  const int32_t* g_rows;
+  const FCol* cols;
+  const int32_t* fsplit;
+  void* tab;
+  void* part;
+  double *C_hi, *C_lo, *S_hi, *S_lo;
+  void* coef;
+  void* blk;
+  double* scal;
+  void* fpart;
+  double *F_hi, *F_lo;
+  dd pref, inv_L;
+  // minimiser state (null when the context has not minimised yet)
+  void* fs;
+  double *v_hi, *v_lo, *bs_hi, *bs_lo, *bF_hi, *bF_lo, *fdots;
+  const int* run;  // status word that turns this configuration's kernels into no-ops when non-zero, or null
+};
+
+// work items of the persistent kernels and of the twiddle kernel
+struct TwItem {
+  int32_t cfg, pad;
+  int64_t start;  // first table entry of a 128-entry block
+};
+struct NtItem {
+  int32_t cfg, blk, ps, pad;  // k-block, particle split
+};
+struct FItem {
+  int32_t cfg, pb, ks, pad;   // particle block, column split
+};
+constexpr int kTwThreads = 128;
+
+// launch view of an engine (device pointers, counts, grid extents) for one precision
+struct EngineView {
+  const CfgDev* cfgs = nullptr;
+  const int* list = nullptr;  // configurations evaluated in this precision
+  int nlist = 0;
+  const TwItem* tw = nullptr;
+  int ntw = 0;
+  const NtItem* nt = nullptr;
+  int nnt = 0;
+  const FItem* fi = nullptr;
+  int nfi = 0;
+  size_t nt_smem = 0;
+  int64_t maxM = 0, maxND = 0;
+  int maxblk = 0;
+  int* counters = nullptr;  // two ints: density queue, force queue
+  int sm_count = 148;
+};
+
+struct Ctx;
+
+// minimiser state of one configuration (device memory)
+enum { kFsRunning = 0, kFsConverged = 1, kFsNan = 2, kFsStageDone = 3, kFsMaxSteps = 4 };
+struct FireState {
+  int status;
+  int rejected_now;
+  int zero_v;
+  int stage;
+  double dt, alpha, cv, cf;
+  long long n_pos, step, stage_step, rejected;
+  double phi_hi, phi_lo, smax_hi, smax_lo;
+  double best_smax;
+  long long best_step;
+  // parameters
+  double dt_max, alpha_start, f_alpha, f_inc, f_dec;
+  long long n_min, stall_window, max_steps;
+  double target, stage_floor;
+};
+
+// A set of configurations evaluated together.  Members keep their own buffers (Ctx); the engine holds their
+// descriptors, the per-precision member lists and the work lists, all in device memory.
+struct Engine {
+  int device = 0;
+  int sm_count = 148;
+  std::vector<Ctx*> members;
+  std::vector<int> prec_of;  // current precision per member; -1 = listed under every precision
+  bool fire_mode = false;
+  std::vector<CfgDev> host_cfgs;
+  DevBuf d_cfgs, d_lists, d_all, d_tw, d_nt, d_f, d_counters;
+  EngineView view[3];
+  std::vector<int> h_lists;
+  std::vector<TwItem> h_tw;
+  std::vector<NtItem> h_nt;
+  std::vector<FItem> h_f;
+  const int* all = nullptr;  // every member, for the minimiser kernels
+  int nall = 0;
+  int64_t maxND_all = 0;
+  int max_nb_fire = 0;
+};
+
 struct Ctx {
   int d = 0;
   int64_t N = 0, M = 0, Npad = 0;
@@ -81,15 +183,32 @@ struct Ctx {
   int last_prec = -1;
   bool last_force = false;
   Prof prof;
-  const int* run_flag = nullptr;  // device status word: kernels return at once when it is non-zero
   dd inv_L;                       // 1 / L
   FireBufs* fire = nullptr;       // minimiser state, allocated on first ssh_minimize
+  Engine* eng = nullptr;          // this context alone (plain evaluations)
 };
 
 // record an event pair around a launch when profiling is on
-void prof_begin(Ctx* c, int id);
-void prof_end(Ctx* c);
-cudaError_t prof_collect(Ctx* c);
+void prof_begin(Prof* p, cudaStream_t st, int id);
+void prof_end(Prof* p, cudaStream_t st);
+cudaError_t prof_collect(Prof* p, cudaStream_t st);
+
+// engine.cu
+CfgDev make_cfgdev(const Ctx* c, bool fire_mode);
+cudaError_t engine_build(Engine* e, const std::vector<Ctx*>& members, const std::vector<int>& prec_of, bool fire_mode,
+                         cudaStream_t st);
+void engine_free(Engine* e);
+cudaError_t engine_eval(const Engine* e, int prec, bool want_force, cudaStream_t st, Prof* prof);
+void kernels_set_attributes(size_t smem_max);
+
+// fire.cu (minimiser kernels over the members of an engine)
+void fire_fill_cfgdev(const Ctx* c, CfgDev* g);
+cudaError_t fire_alloc(Ctx* c);
+cudaError_t fire_step_engine(const Engine* e, cudaStream_t st, Prof* prof);
+FireState fire_params(const ssh_min_params* p);
+// (re)start the members idx of e: v = 0 when first, accepted Phi / S_max from their scal, stage parameters
+cudaError_t fire_stage_init_engine(const Engine* e, const std::vector<int>& idx, const std::vector<FireState>& params,
+                                   const std::vector<int>& first, cudaStream_t st);
 
 // device scalar block written by k_finalize (doubles)
 enum { kScPhiHi = 0, kScPhiLo, kScSmaxHi, kScSmaxLo, kScCmax, kScScaleExp, kScA2MaxHi, kScA2MaxLo, kScCount = 16 };
