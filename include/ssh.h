@@ -195,6 +195,90 @@ ssh_status ssh_fire_steps(ssh_ctx* ctx, int prec, int64_t nsteps);
 ssh_status ssh_fire_state(ssh_ctx* ctx, ssh_min_result* res, int* running);
 
 /*
+ * Batch: many independent configurations of any sizes resident on one GPU, evaluated and minimised through the
+ * same persistent launches (work queues of (configuration, tile) items, largest first) and graph-captured steps.
+ * Every member keeps its own launch shape, so its arithmetic -- and its result -- is the same alone and in any
+ * batch.  Members are numbered 0, 1, ... in the order they were added.
+ */
+typedef struct ssh_batch ssh_batch;
+ssh_status ssh_batch_create(const ssh_opts* opts, ssh_batch** out);
+void ssh_batch_destroy(ssh_batch* batch);
+/* Add a configuration (as ssh_create) with fractional positions s (N*d row-major dd, s_lo may be NULL). */
+ssh_status ssh_batch_add(ssh_batch* batch, int d, int64_t N, double L, double chi, double K, const double* s_hi,
+                         const double* s_lo, int* slot);
+/* Number of members and the total (k, particle) pairs sum_i M_i N_i of one evaluation. */
+ssh_status ssh_batch_size(const ssh_batch* batch, int* n, int64_t* pairs);
+/* The context of member `slot` (owned by the batch; valid until ssh_batch_destroy), for ssh_get_results,
+ * ssh_get_ntilde, ssh_get_positions_frac. */
+ssh_status ssh_batch_member(ssh_batch* batch, int slot, ssh_ctx** ctx);
+/* Phi, S_max and F (want_force) of every member in one batched evaluation; synchronises. */
+ssh_status ssh_batch_eval(ssh_batch* batch, int prec, int want_force);
+/* Minimise every member to completion (p as for ssh_minimize; zero fields take each member's defaults).  Steps
+ * are replayed in chunks of chunk_steps (0 = 32) between host checks; max_seconds 0 = no limit.  results: array
+ * of n, may be NULL.  Returns SSH_OK if every member converged, else the first failing status. */
+ssh_status ssh_batch_minimize(ssh_batch* batch, const ssh_min_params* p, int64_t chunk_steps, double max_seconds,
+                              ssh_min_result* results);
+/* Stepper for timing: begin every member's run (as ssh_fire_begin), then enqueue exactly nsteps batched steps
+ * without synchronising (members whose run ended are skipped; stages do not advance). */
+ssh_status ssh_batch_begin(ssh_batch* batch, const ssh_min_params* p);
+ssh_status ssh_batch_steps(ssh_batch* batch, int64_t nsteps);
+/* Event profiler of the batch's launches (see ssh_prof_enable); while on, steps are launched directly. */
+ssh_status ssh_batch_prof_enable(ssh_batch* batch, int on);
+ssh_status ssh_batch_prof_read(ssh_batch* batch, int n, double* ms, int64_t* launches);
+
+/*
+ * Server: ensemble requests minimised with continuous batching.  A worker thread keeps a batch of running
+ * configurations resident in HBM; queued requests are admitted first come first served while a slot is free
+ * and the request's device footprint (plans, tables, partial sums, positions, forces, minimiser state) fits the
+ * HBM budget, so requests that arrive while others run join the running batch and their steps share the same
+ * launches.  Finished members are retired between chunks and their memory is released.  Thread-safe.
+ */
+typedef struct ssh_server ssh_server;
+typedef struct {
+  int device;               /* CUDA device */
+  int max_slots;            /* members running at once (default 256) */
+  int64_t hbm_budget_bytes; /* device bytes for running members (default 64 GiB) */
+  int64_t chunk_steps;      /* steps between admissions / retirements (default 32) */
+  int reserved[4];
+} ssh_server_opts;
+typedef struct {
+  int d;
+  int want_positions;       /* 1: keep the final positions for ssh_result_positions */
+  int64_t N;
+  double L, chi, K;         /* as ssh_create */
+  const double* s_hi;       /* initial fractional positions, N*d row-major (copied at submission) */
+  const double* s_lo;       /* may be NULL */
+  const ssh_min_params* params;  /* NULL = defaults */
+} ssh_request;
+typedef struct {
+  int status;               /* SSH_OK converged, SSH_ENOTCONV, SSH_ENAN, or the admission error */
+  int final_prec;
+  int has_positions;
+  int pad0;
+  int64_t steps, rejected;
+  double smax[2], phi[2];
+  double t_submit, t_admit, t_done;  /* seconds since the server started */
+} ssh_result;
+typedef struct {
+  int64_t submitted, completed, converged, running, queued, hbm_used_bytes;
+} ssh_server_stats;
+ssh_status ssh_server_create(const ssh_server_opts* opts, ssh_server** out);
+/* Stops the worker (running members are abandoned) and frees everything. */
+void ssh_server_destroy(ssh_server* server);
+/* Queue a request; *ticket identifies it.  Errors: SSH_EINVAL (bad request, larger than the budget). */
+ssh_status ssh_submit(ssh_server* server, const ssh_request* req, uint64_t* ticket);
+/* SSH_OK with the result when finished, SSH_EBUSY while queued or running, SSH_ENOTFOUND for unknown or
+ * cancelled tickets, SSH_ECUDA if the worker stopped on a device error. */
+ssh_status ssh_poll(ssh_server* server, uint64_t ticket, ssh_result* out);
+/* Final fractional positions (N*d row-major dd) of a finished request submitted with want_positions. */
+ssh_status ssh_result_positions(ssh_server* server, uint64_t ticket, double* s_hi, double* s_lo);
+/* Forget a finished request's result. */
+ssh_status ssh_release(ssh_server* server, uint64_t ticket);
+/* Cancel a request that is still queued (SSH_EBUSY once admitted). */
+ssh_status ssh_cancel(ssh_server* server, uint64_t ticket);
+ssh_status ssh_server_get_stats(ssh_server* server, ssh_server_stats* out);
+
+/*
  * Event profiler (tracing).  When enabled, every kernel the context launches is bracketed by a CUDA event
  * pair on the context's stream; ssh_prof_read synchronises the stream and returns, per kernel id, the
  * summed device time in milliseconds and the launch count since the last ssh_prof_enable call.

@@ -13,10 +13,6 @@
 #define SSH_TABLE_QUAL static
 #include "gen/tables.h"
 
-struct ssh_ctx {
-  ssh::Ctx c;
-  double* h_stage = nullptr;  // pinned staging for positions and forces: 2 * d * N doubles
-};
 
 namespace ssh {
 static thread_local std::string g_err;
@@ -331,7 +327,9 @@ ssh_status ssh_min_defaults(const ssh_ctx* h, ssh_min_params* p) {
   return SSH_OK;
 }
 
-static ssh_status complete_params(const ssh_ctx* h, const ssh_min_params* pin, ssh_min_params* out) {
+}  // extern "C"
+
+ssh_status ssh::complete_params(const ssh_ctx* h, const ssh_min_params* pin, ssh_min_params* out) {
   ssh_min_params d;
   ssh_min_defaults(h, &d);
   ssh_min_params p = pin ? *pin : d;
@@ -366,12 +364,14 @@ static ssh_status complete_params(const ssh_ctx* h, const ssh_min_params* pin, s
   return SSH_OK;
 }
 
+extern "C" {
+
 ssh_status ssh_minimize(ssh_ctx* h, const ssh_min_params* pin, ssh_min_result* res) {
   if (!h) { set_error("ssh_minimize: NULL context"); return SSH_EINVAL; }
   ssh::Ctx& c = h->c;
   if (!c.have_positions) { set_error("ssh_minimize: no positions set"); return SSH_EINVAL; }
   ssh_min_params p;
-  ssh_status st = complete_params(h, pin, &p);
+  ssh_status st = ssh::complete_params(h, pin, &p);
   if (st != SSH_OK) return st;
   cudaSetDevice(c.device);
   return ssh::minimize(&c, &p, res);
@@ -382,7 +382,7 @@ ssh_status ssh_fire_begin(ssh_ctx* h, const ssh_min_params* pin) {
   ssh::Ctx& c = h->c;
   if (!c.have_positions) { set_error("ssh_fire_begin: no positions set"); return SSH_EINVAL; }
   ssh_min_params p;
-  ssh_status st = complete_params(h, pin, &p);
+  ssh_status st = ssh::complete_params(h, pin, &p);
   if (st != SSH_OK) return st;
   cudaSetDevice(c.device);
   return ssh::fire_begin(&c, &p);

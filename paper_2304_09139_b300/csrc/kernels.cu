@@ -641,6 +641,21 @@ cudaError_t plan_upload(Ctx* c) {
   return cudaGetLastError();
 }
 
+size_t device_footprint(const Ctx& c) {
+  const size_t nd = (size_t)c.d * c.N;
+  int max_ps = 1;
+  for (int p = 0; p < 3; p++) max_ps = std::max(max_ps, c.launch[p].nt_psplit);
+  size_t b = 0;
+  b += (size_t)c.tl.rows.size() * c.Npad * kTabBytes;         // power tables
+  b += (size_t)max_ps * c.M * kAccBytes;                       // density partials
+  b += (size_t)c.M * (4 * 8 + kTabBytes);                      // C, S, coefficients
+  b += (size_t)c.launch[0].f_ksplit * nd * kRAccBytes;         // force partials
+  b += nd * 8 * (4 + 6);                                       // positions, force, velocity, undo copies
+  b += c.nt.slots.size() * sizeof(NtSlot) + c.nt.g_rows.size() * 4 + c.fp.cols.size() * sizeof(FCol);
+  b += c.tl.rows.size() * sizeof(TabRow) + 64 * 1024;          // small buffers and allocation granularity
+  return b;
+}
+
 cudaError_t eval_phi_grad(Ctx* c, int prec, bool want_force) {
   return engine_eval(c->eng, prec, want_force, c->stream, &c->prof);
 }

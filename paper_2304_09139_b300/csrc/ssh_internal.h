@@ -227,4 +227,16 @@ ssh_status fire_begin(Ctx* c, const ssh_min_params* p);
 ssh_status fire_steps(Ctx* c, int prec, int64_t nsteps);
 ssh_status fire_state(Ctx* c, ssh_min_result* r, int* dev_status);
 
+// zero fields of pin take the context's defaults; validates the result
+ssh_status complete_params(const ssh_ctx* h, const ssh_min_params* pin, ssh_min_params* out);
+
+// device bytes a configuration occupies once created and minimised (plans, tables, partial sums, state)
+size_t device_footprint(const Ctx& c);
+
 }  // namespace ssh
+
+// the public handle: one configuration plus its pinned host staging
+struct ssh_ctx {
+  ssh::Ctx c;
+  double* h_stage = nullptr;  // pinned staging for positions and forces: 2 * d * N doubles
+};

@@ -48,6 +48,35 @@ class MinResult(ctypes.Structure):
                 "stage_wall_s": list(self.stage_wall_s)}
 
 
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("max_slots", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_int64),
+                ("chunk_steps", ctypes.c_int64), ("reserved", ctypes.c_int * 4)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("want_positions", ctypes.c_int), ("N", ctypes.c_int64),
+                ("L", ctypes.c_double), ("chi", ctypes.c_double), ("K", ctypes.c_double),
+                ("s_hi", ctypes.POINTER(ctypes.c_double)), ("s_lo", ctypes.POINTER(ctypes.c_double)),
+                ("params", ctypes.POINTER(MinParams))]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("final_prec", ctypes.c_int), ("has_positions", ctypes.c_int),
+                ("pad0", ctypes.c_int), ("steps", ctypes.c_int64), ("rejected", ctypes.c_int64),
+                ("smax", ctypes.c_double * 2), ("phi", ctypes.c_double * 2), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"status": self.status, "final_prec": self.final_prec, "has_positions": bool(self.has_positions),
+                "steps": self.steps, "rejected": self.rejected, "smax": list(self.smax), "phi": list(self.phi),
+                "t_submit": self.t_submit, "t_admit": self.t_admit, "t_done": self.t_done}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "converged", "running", "queued",
+                                              "hbm_used_bytes")]
+
+
 class SshError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{_STATUS.get(status, status)}: {message}")
@@ -98,6 +127,25 @@ def load():
             _sig(lib, "ssh_fire_begin", c_int, [c_vp, P(MinParams)])
             _sig(lib, "ssh_fire_steps", c_int, [c_vp, c_int, c_i64])
             _sig(lib, "ssh_fire_state", c_int, [c_vp, P(MinResult), P(c_int)])
+            _sig(lib, "ssh_batch_create", c_int, [c_vp, P(c_vp)])
+            _sig(lib, "ssh_batch_destroy", None, [c_vp])
+            _sig(lib, "ssh_batch_add", c_int, [c_vp, c_int, c_i64, c_d, c_d, c_d, P(c_d), P(c_d), P(c_int)])
+            _sig(lib, "ssh_batch_size", c_int, [c_vp, P(c_int), P(c_i64)])
+            _sig(lib, "ssh_batch_member", c_int, [c_vp, c_int, P(c_vp)])
+            _sig(lib, "ssh_batch_eval", c_int, [c_vp, c_int, c_int])
+            _sig(lib, "ssh_batch_minimize", c_int, [c_vp, P(MinParams), c_i64, c_d, P(MinResult)])
+            _sig(lib, "ssh_batch_begin", c_int, [c_vp, P(MinParams)])
+            _sig(lib, "ssh_batch_steps", c_int, [c_vp, c_i64])
+            _sig(lib, "ssh_batch_prof_enable", c_int, [c_vp, c_int])
+            _sig(lib, "ssh_batch_prof_read", c_int, [c_vp, c_int, P(c_d), P(c_i64)])
+            _sig(lib, "ssh_server_create", c_int, [P(ServerOpts), P(c_vp)])
+            _sig(lib, "ssh_server_destroy", None, [c_vp])
+            _sig(lib, "ssh_submit", c_int, [c_vp, P(Request), P(ctypes.c_uint64)])
+            _sig(lib, "ssh_poll", c_int, [c_vp, ctypes.c_uint64, P(Result)])
+            _sig(lib, "ssh_result_positions", c_int, [c_vp, ctypes.c_uint64, P(c_d), P(c_d)])
+            _sig(lib, "ssh_release", c_int, [c_vp, ctypes.c_uint64])
+            _sig(lib, "ssh_cancel", c_int, [c_vp, ctypes.c_uint64])
+            _sig(lib, "ssh_server_get_stats", c_int, [c_vp, P(ServerStats)])
             _lib = lib
     return _lib
 
@@ -142,12 +190,16 @@ def _rows(a, N, d):
 class Context:
     """One configuration (d, N, L, chi | K) resident on the GPU.  Wraps ssh_create / ssh_destroy."""
 
-    def __init__(self, d: int, N: int, L: float, chi: float = 0.0, K: float = 0.0, device: int = 0):
+    def __init__(self, d: int, N: int, L: float, chi: float = 0.0, K: float = 0.0, device: int = 0, _handle=None):
         lib = load()
         self._lib = lib
+        self._owned = _handle is None
         self._h = c_vp()
-        opts = (c_int * 8)(device, 0, 0, 0, 0, 0, 0, 0)
-        _check(lib.ssh_create(d, N, L, chi, K, ctypes.cast(opts, c_vp), ctypes.byref(self._h)))
+        if _handle is None:
+            opts = (c_int * 8)(device, 0, 0, 0, 0, 0, 0, 0)
+            _check(lib.ssh_create(d, N, L, chi, K, ctypes.cast(opts, c_vp), ctypes.byref(self._h)))
+        else:
+            self._h = _handle
         dd_, NN, MM, LL = c_int(), c_i64(), c_i64(), c_d()
         _check(lib.ssh_get_dims(self._h, ctypes.byref(dd_), ctypes.byref(NN), ctypes.byref(MM), ctypes.byref(LL)))
         self.d, self.N, self.M, self.L = dd_.value, NN.value, MM.value, LL.value
@@ -157,9 +209,9 @@ class Context:
         return self._h
 
     def close(self):
-        if self._h:
+        if self._h and self._owned:
             self._lib.ssh_destroy(self._h)
-            self._h = c_vp()
+        self._h = c_vp()
 
     def __del__(self):
         try:
@@ -280,3 +332,149 @@ class Context:
         ch, cl, sh, sl = (np.zeros(self.M) for _ in range(4))
         _check(self._lib.ssh_get_ntilde(self._h, _dp(ch), _dp(cl), _dp(sh), _dp(sl)))
         return np.stack([ch, cl], 1), np.stack([sh, sl], 1)
+
+
+def _params(params, stages=None, **kw):
+    p = params if params is not None else MinParams()
+    if stages is not None:
+        p.n_stages = len(stages)
+        for i, st in enumerate(stages):
+            p.stage_prec[i] = st
+    for k, v in kw.items():
+        if k in ("stage_floor", "stall_window"):
+            arr = getattr(p, k)
+            for i, x in enumerate(v):
+                arr[i] = x
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class Batch:
+    """Many configurations evaluated and minimised through the same launches (ssh_batch_*)."""
+
+    def __init__(self, device: int = 0):
+        self._lib = load()
+        self._h = c_vp()
+        opts = (c_int * 8)(device, 0, 0, 0, 0, 0, 0, 0)
+        _check(self._lib.ssh_batch_create(ctypes.cast(opts, c_vp), ctypes.byref(self._h)))
+        self._members = []
+
+    def close(self):
+        if self._h:
+            for m in self._members:
+                m._h = c_vp()
+            self._lib.ssh_batch_destroy(self._h)
+            self._h = c_vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add(self, d, N, L, s_hi, s_lo=None, chi=0.0, K=0.0) -> int:
+        s_hi = _rows(s_hi, N, d)
+        s_lo = _rows(s_lo, N, d)
+        slot = c_int(0)
+        _check(self._lib.ssh_batch_add(self._h, d, N, L, chi, K, _dp(s_hi), _dp(s_lo), ctypes.byref(slot)))
+        h = c_vp()
+        _check(self._lib.ssh_batch_member(self._h, slot.value, ctypes.byref(h)))
+        self._members.append(Context(0, 0, 0.0, _handle=h))
+        return slot.value
+
+    def member(self, slot: int) -> Context:
+        return self._members[slot]
+
+    def size(self):
+        n, pairs = c_int(0), c_i64(0)
+        _check(self._lib.ssh_batch_size(self._h, ctypes.byref(n), ctypes.byref(pairs)))
+        return n.value, pairs.value
+
+    def eval(self, prec: int, want_force: bool = True):
+        _check(self._lib.ssh_batch_eval(self._h, prec, 1 if want_force else 0))
+
+    def minimize(self, params: MinParams | None = None, stages=None, chunk_steps: int = 0, max_seconds: float = 0.0,
+                 **kw):
+        n = self.size()[0]
+        res = (MinResult * max(n, 1))()
+        p = _params(params, stages, **kw)
+        st = self._lib.ssh_batch_minimize(self._h, ctypes.byref(p), chunk_steps, max_seconds, res)
+        return st, [res[i].as_dict() for i in range(n)]
+
+    def begin(self, params: MinParams | None = None, stages=None, **kw):
+        p = _params(params, stages, **kw)
+        _check(self._lib.ssh_batch_begin(self._h, ctypes.byref(p)))
+
+    def steps(self, nsteps: int):
+        _check(self._lib.ssh_batch_steps(self._h, nsteps))
+
+    def prof_enable(self, on: bool = True):
+        _check(self._lib.ssh_batch_prof_enable(self._h, 1 if on else 0))
+
+    def prof_read(self):
+        ms = np.zeros(16)
+        n = np.zeros(16, dtype=np.int64)
+        _check(self._lib.ssh_batch_prof_read(self._h, 16, _dp(ms), n.ctypes.data_as(P(c_i64))))
+        return {KERNELS[i]: (float(ms[i]), int(n[i])) for i in range(len(KERNELS)) if n[i] > 0}
+
+
+class Server:
+    """Continuous-batching minimisation service (ssh_server_*): submit, poll, collect."""
+
+    def __init__(self, device: int = 0, max_slots: int = 256, hbm_budget_bytes: int = 64 << 30,
+                 chunk_steps: int = 32):
+        self._lib = load()
+        self._h = c_vp()
+        o = ServerOpts(device, max_slots, hbm_budget_bytes, chunk_steps)
+        _check(self._lib.ssh_server_create(ctypes.byref(o), ctypes.byref(self._h)))
+        self._keep = {}
+
+    def close(self):
+        if self._h:
+            self._lib.ssh_server_destroy(self._h)
+            self._h = c_vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, d, N, L, s_hi, s_lo=None, chi=0.0, K=0.0, params: MinParams | None = None,
+               want_positions: bool = False) -> int:
+        s_hi = _rows(s_hi, N, d)
+        s_lo = _rows(s_lo, N, d)
+        q = Request(d, 1 if want_positions else 0, N, L, chi, K, _dp(s_hi), _dp(s_lo),
+                    ctypes.pointer(params) if params is not None else None)
+        t = ctypes.c_uint64(0)
+        _check(self._lib.ssh_submit(self._h, ctypes.byref(q), ctypes.byref(t)))
+        self._keep[t.value] = (d, N)
+        return t.value
+
+    def poll(self, ticket: int):
+        """The result dict when finished, None while queued or running."""
+        r = Result()
+        st = self._lib.ssh_poll(self._h, ticket, ctypes.byref(r))
+        if st == 7:
+            return None
+        _check(st)
+        return r.as_dict()
+
+    def positions(self, ticket: int):
+        d, N = self._keep[ticket]
+        hi = np.zeros((N, d))
+        lo = np.zeros((N, d))
+        _check(self._lib.ssh_result_positions(self._h, ticket, _dp(hi), _dp(lo)))
+        return hi, lo
+
+    def release(self, ticket: int):
+        _check(self._lib.ssh_release(self._h, ticket))
+
+    def cancel(self, ticket: int):
+        _check(self._lib.ssh_cancel(self._h, ticket))
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(self._lib.ssh_server_get_stats(self._h, ctypes.byref(s)))
+        return {n: getattr(s, n) for n, _ in ServerStats._fields_}
