@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--no-minimize", action="store_true")
     ap.add_argument("--minimize-dd", action="store_true", help="also time FP64->dd and all-dd quenches")
     ap.add_argument("--minimize-seconds", type=float, default=150.0)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=45.0)
     return ap.parse_args()
 
 
@@ -170,6 +173,80 @@ def minimize_block(ssh, synth, w, dev, stream, with_dd=False, max_seconds=150):
                      "configs_per_hour": 3600.0 / r["wall_s"] if r["status"] == 0 else 0.0}
         c.close()
     return out
+
+
+def batched_block(ssh, synth, dev, steps=5, warmup=2, count=256):
+    """One batched FIRE step over the 256-configuration mix (d in {2, 3}, N log-uniform in [64, 8192],
+    chi in [0.10, 0.49]): every member's tiles share the same persistent launches."""
+    import torch
+    cfgs = synth.mixed_batch(4, count)
+    b = ssh.Batch(device=dev)
+    for c in cfgs:
+        b.add(c.d, c.N, c.L, synth.positions(c.seed, c.N, c.d), chi=c.chi)
+    n, pairs = b.size()
+    b.begin(stages=[ssh.FX], smax_target=1e-300)
+    b.steps(warmup)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    b.steps(steps)
+    torch.cuda.synchronize(dev)   # the batch works on its own stream: a device-wide synchronisation
+    t = (time.perf_counter() - t0) / steps
+    b.prof_enable(True)           # then one profiled step for the per-kernel split
+    b.steps(1)
+    pr = b.prof_read()
+    b.prof_enable(False)
+    b.close()
+    return {"configs": n, "pairs_per_step": pairs, "ms_per_step": t * 1e3, "pairs_per_s": pairs / t,
+            "per_kernel_ms": {k: v[0] for k, v in pr.items()},
+            "workload": "256 configurations, d in {2,3}, N log-uniform [64, 8192], chi U[0.10, 0.49], unit density, "
+                        "fixed point, one batched FIRE step (graph replay)"}
+
+
+def serving_block(ssh, synth, dev, window_s=45.0, drain_s=30.0, count=2000, mean_gap=0.020):
+    # The offered load (about 50 requests/s of up to 1.3e9 pairs per step each) exceeds one GPU by far; the
+    # server admits the smallest requests first under a cap on pairs per batched step, so the figures below
+    # describe what one B300 sustains, and still_queued / still_running show the backlog.
+    """Poisson arrivals (mean 50/s) of ensemble requests (d in {1,2,3}, N log-uniform in [64, 32768],
+    chi in [0.10, 0.49]) submitted in real time for window_s seconds; latency = submit -> converged."""
+    import threading
+    cfgs, arrivals = synth.serving_requests(5, count, mean_gap)
+    sv = ssh.Server(device=dev, max_slots=256, chunk_steps=32)
+    tickets = []
+    t0 = time.perf_counter()
+    stop = threading.Event()
+
+    def feeder():
+        for c, ta in zip(cfgs, arrivals):
+            if ta > window_s or stop.is_set():
+                break
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(sv.submit(c.d, c.N, c.L, synth.positions(c.seed, c.N, c.d), chi=c.chi))
+
+    th = threading.Thread(target=feeder)
+    th.start()
+    done = {}
+    while time.perf_counter() - t0 < window_s + drain_s:
+        for t in list(tickets):
+            if t not in done:
+                r = sv.poll(t)
+                if r is not None:
+                    done[t] = r
+        time.sleep(0.05)
+    stop.set()
+    th.join()
+    elapsed = time.perf_counter() - t0
+    st = sv.stats()
+    sv.close()
+    ok = [r for r in done.values() if r["status"] == 0]
+    lat = sorted(r["t_done"] - r["t_submit"] for r in ok)
+    pct = (lambda q: float(np.percentile(lat, q)) if lat else None)
+    return {"submitted": len(tickets), "completed": len(done), "converged": len(ok), "still_running": st["running"],
+            "still_queued": st["queued"], "p50_s": pct(50), "p99_s": pct(99),
+            "configs_per_hour": len(ok) / elapsed * 3600.0, "elapsed_s": elapsed,
+            "workload": f"Poisson arrivals mean {1 / mean_gap:.0f}/s for {window_s:.0f} s (+{drain_s:.0f} s drain), "
+                        "d in {1,2,3}, N log-uniform [64, 32768], chi U[0.10, 0.49]; latency of converged requests only"}
 
 
 def run_reference(args):
@@ -343,6 +420,12 @@ def main():
         conv = line["minimize"].get("fp64_then_fx", {})
         if conv.get("converged"):
             line["configs_per_hour"] = 3600.0 / conv["wall_s"]
+    if rank == 0 and not args.no_batched:
+        line["batched"] = batched_block(ssh, synth, dev)
+    if rank == 0 and not args.no_serve:
+        line["serving"] = serving_block(ssh, synth, dev, window_s=args.serve_seconds)
+        line["p50_s"] = line["serving"]["p50_s"]
+        line["p99_s"] = line["serving"]["p99_s"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, Ms, cores = cpu_sample(w["N"], w["d"], w["L"], w["chi"], w["seed"])
         line["cpu_baseline"] = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle",

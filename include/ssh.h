@@ -228,18 +228,25 @@ ssh_status ssh_batch_prof_read(ssh_batch* batch, int n, double* ms, int64_t* lau
 
 /*
  * Server: ensemble requests minimised with continuous batching.  A worker thread keeps a batch of running
- * configurations resident in HBM; queued requests are admitted first come first served while a slot is free
- * and the request's device footprint (plans, tables, partial sums, positions, forces, minimiser state) fits the
- * HBM budget, so requests that arrive while others run join the running batch and their steps share the same
- * launches.  Finished members are retired between chunks and their memory is released.  Thread-safe.
+ * configurations resident in HBM; queued requests are admitted (smallest M N first, or first come first served)
+ * while a slot is free, the request's device footprint (plans, tables, partial sums, positions, forces,
+ * minimiser state) fits the HBM budget and the batch's pairs per step stay under a cap, so requests that arrive
+ * while others run join the running batch and their steps share the same launches.  Every running member
+ * advances one step per batched step, so the cap bounds the step time that small requests share with large
+ * ones.  Finished members are retired between chunks and their memory is released.  Thread-safe.
  */
 typedef struct ssh_server ssh_server;
 typedef struct {
-  int device;               /* CUDA device */
-  int max_slots;            /* members running at once (default 256) */
-  int64_t hbm_budget_bytes; /* device bytes for running members (default 64 GiB) */
-  int64_t chunk_steps;      /* steps between admissions / retirements (default 32) */
-  int reserved[4];
+  int device;                  /* CUDA device */
+  int max_slots;               /* members running at once (default 256) */
+  int64_t hbm_budget_bytes;    /* device bytes for running members (default 64 GiB) */
+  int64_t chunk_steps;         /* at most this many steps between admissions / retirements (default 32); fewer
+                                  when steps are long, so that the host checks about every 0.1 s */
+  int64_t max_pairs_per_step;  /* admission stops while the running members' sum of M N would exceed it
+                                  (default 2^28, about 10 ms per step); bounds the step time that every
+                                  running request shares; a larger request runs only in an empty batch */
+  int policy;                  /* 0: smallest M N first (default), 1: first come first served */
+  int reserved[1];
 } ssh_server_opts;
 typedef struct {
   int d;

@@ -43,6 +43,7 @@ struct Member {
   ssh_min_result res;
   long long stage_step0 = 0;
   int want_positions = 0;
+  int64_t work = 0;  // M N pairs of one evaluation
 };
 
 static double now_s() {
@@ -448,6 +449,7 @@ struct Pending {
   int want_positions;
   double t_submit;
   size_t footprint;
+  int64_t work;
 };
 
 struct Done {
@@ -474,7 +476,7 @@ struct ssh_server {
   std::string worker_error;
 };
 
-static size_t estimate_footprint(int d, int64_t N, double L, double chi, double K, int sm_count) {
+static size_t estimate_footprint(int d, int64_t N, double L, double chi, double K, int sm_count, int64_t* work) {
   ssh::Ctx c;
   c.d = d;
   c.N = N;
@@ -490,6 +492,7 @@ static size_t estimate_footprint(int d, int64_t N, double L, double chi, double 
   int ks = 1;
   for (int p = 0; p < 3; p++) ks = std::max(ks, c.launch[p].f_ksplit);
   for (int p = 0; p < 3; p++) c.launch[p].f_ksplit = ks;
+  if (work) *work = c.M * c.N;
   return ssh::device_footprint(c);
 }
 
@@ -501,6 +504,7 @@ static void server_loop(ssh_server* sv) {
   r.device = sv->o.device;
   r.st = st;
   const int64_t chunk = sv->o.chunk_steps > 0 ? sv->o.chunk_steps : 32;
+  int64_t steps_now = chunk;
   for (;;) {
     std::vector<Pending> admit;
     {
@@ -508,16 +512,27 @@ static void server_loop(ssh_server* sv) {
       if (r.act.empty())
         sv->cv.wait_for(lk, std::chrono::milliseconds(20), [&] { return sv->stop || !sv->queue.empty(); });
       if (sv->stop) break;
-      // admission: first come first served while a slot is free and the footprint fits the budget
+      // admission while a slot is free, the footprint fits the HBM budget and the batch's pairs per step stay
+      // within max_pairs_per_step (a request that exceeds a limit alone is admitted into an empty batch)
+      int64_t pairs = 0;
+      for (Member& m : r.act) pairs += m.work;
       while (!sv->queue.empty() && (int)(r.act.size() + admit.size()) < sv->o.max_slots) {
-        Pending& q = sv->queue.front();
-        if (sv->state[q.ticket] == 3) { sv->queue.pop_front(); continue; }
-        if (sv->used + q.footprint > (size_t)sv->o.hbm_budget_bytes && !(r.act.empty() && admit.empty())) break;
+        size_t pick = 0;  // FIFO: the oldest; smallest-work-first: the least M N (oldest among equals)
+        if (sv->o.policy == 0)
+          for (size_t i = 1; i < sv->queue.size(); i++)
+            if (sv->queue[i].work < sv->queue[pick].work) pick = i;
+        Pending& q = sv->queue[pick];
+        if (sv->state[q.ticket] == 3) { sv->queue.erase(sv->queue.begin() + pick); continue; }
+        const bool empty = r.act.empty() && admit.empty();
+        if (!empty && (sv->used + q.footprint > (size_t)sv->o.hbm_budget_bytes ||
+                       pairs + q.work > sv->o.max_pairs_per_step))
+          break;
         sv->used += q.footprint;
+        pairs += q.work;
         sv->foot[q.ticket] = q.footprint;
         sv->state[q.ticket] = 1;
         admit.push_back(std::move(q));
-        sv->queue.pop_front();
+        sv->queue.erase(sv->queue.begin() + pick);
       }
     }
     std::vector<Member> fresh;
@@ -546,12 +561,20 @@ static void server_loop(ssh_server* sv) {
         continue;
       }
       m.want_positions = q.want_positions;
+      m.work = q.work;
       fresh.push_back(m);
     }
     cudaError_t e = cudaSuccess;
     if (!fresh.empty()) e = r.add(fresh);
     std::vector<Member> finished;
-    if (e == cudaSuccess && !r.act.empty()) e = r.chunk(chunk, finished);
+    if (e == cudaSuccess && !r.act.empty()) {
+      const double tc = ssh::now_s();
+      e = r.chunk(steps_now, finished);
+      // chunk length adapts so that admissions and retirements happen about every target_chunk seconds
+      const double per_step = (ssh::now_s() - tc) / (double)steps_now;
+      int64_t want = per_step > 0 ? (int64_t)(0.1 / per_step) : chunk;
+      steps_now = std::max<int64_t>(4, std::min<int64_t>(chunk, (want + 3) / 4 * 4));
+    }
     if (e != cudaSuccess) {
       std::lock_guard<std::mutex> lk(sv->mu);
       sv->worker_error = cudaGetErrorString(e);
@@ -612,6 +635,7 @@ ssh_status ssh_server_create(const ssh_server_opts* opts, ssh_server** out) {
   if (sv->o.max_slots <= 0) sv->o.max_slots = 256;
   if (sv->o.hbm_budget_bytes <= 0) sv->o.hbm_budget_bytes = (int64_t)64 << 30;
   if (sv->o.chunk_steps <= 0) sv->o.chunk_steps = 32;
+  if (sv->o.max_pairs_per_step <= 0) sv->o.max_pairs_per_step = (int64_t)1 << 28;
   cudaError_t e = cudaSetDevice(sv->o.device);
   if (e != cudaSuccess) { delete sv; return ssh::fail(e, "ssh_server_create"); }
   memset(&sv->stats, 0, sizeof sv->stats);
@@ -637,7 +661,8 @@ ssh_status ssh_submit(ssh_server* sv, const ssh_request* q, uint64_t* ticket) {
   if (q->d < 1 || q->d > ssh::kMaxDim || q->N < 1 || !(q->L > 0)) { set_error("ssh_submit: bad configuration"); return SSH_EINVAL; }
   int sm = 148;
   cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, sv->o.device);
-  size_t fp = estimate_footprint(q->d, q->N, q->L, q->chi, q->K, sm);
+  int64_t work = 0;
+  size_t fp = estimate_footprint(q->d, q->N, q->L, q->chi, q->K, sm, &work);
   if (fp == 0) { set_error("ssh_submit: could not build the wavevector set"); return SSH_EINVAL; }
   if ((int64_t)fp > sv->o.hbm_budget_bytes) { set_error("ssh_submit: request larger than the HBM budget"); return SSH_EINVAL; }
   Pending p;
@@ -654,6 +679,7 @@ ssh_status ssh_submit(ssh_server* sv, const ssh_request* q, uint64_t* ticket) {
   p.want_positions = q->want_positions;
   p.t_submit = ssh::now_s();
   p.footprint = fp;
+  p.work = std::max<int64_t>(1, work);
   std::lock_guard<std::mutex> lk(sv->mu);
   if (sv->stop) { set_error("ssh_submit: server stopped: " + sv->worker_error); return SSH_ECUDA; }
   p.ticket = sv->next_ticket++;

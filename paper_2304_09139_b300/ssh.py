@@ -50,7 +50,8 @@ class MinResult(ctypes.Structure):
 
 class ServerOpts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("max_slots", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_int64),
-                ("chunk_steps", ctypes.c_int64), ("reserved", ctypes.c_int * 4)]
+                ("chunk_steps", ctypes.c_int64), ("max_pairs_per_step", ctypes.c_int64), ("policy", ctypes.c_int),
+                ("reserved", ctypes.c_int * 1)]
 
 
 class Request(ctypes.Structure):
@@ -423,10 +424,10 @@ class Server:
     """Continuous-batching minimisation service (ssh_server_*): submit, poll, collect."""
 
     def __init__(self, device: int = 0, max_slots: int = 256, hbm_budget_bytes: int = 64 << 30,
-                 chunk_steps: int = 32):
+                 chunk_steps: int = 32, max_pairs_per_step: int = 0, fifo: bool = False):
         self._lib = load()
         self._h = c_vp()
-        o = ServerOpts(device, max_slots, hbm_budget_bytes, chunk_steps)
+        o = ServerOpts(device, max_slots, hbm_budget_bytes, chunk_steps, max_pairs_per_step, 1 if fifo else 0)
         _check(self._lib.ssh_server_create(ctypes.byref(o), ctypes.byref(self._h)))
         self._keep = {}
 
