@@ -285,3 +285,73 @@ __device__ __forceinline__ fxc fx_sincos_turns(const q128& t, const uint32_t (*t
   }
   return fxc_mul(fxc_mul(a, b), e);
 }
+
+// ---------------------------------------------------------------------------------------------------------------
+// First-quadrant form of a unit phasor, for the density kernel's inner loop.  z = i^q (c + i s) with c, s >= 0 as
+// unsigned Q1.127 (value = X / 2^127), and cs = c + s for the three-product complex multiply; the quadrant q
+// (0..3) lives in the two low bits of cs (an error of at most 3 * 2^-127 in cs).  Products of such values are the
+// top halves of unsigned 256-bit products, already in Q2.126: no sign correction and no shift.
+struct __align__(16) qent {
+  q128 c, s, cs;
+};
+
+__device__ __forceinline__ q128 q128_shl1(const q128& a) {
+  q128 r;
+  r.w[3] = __funnelshift_l(a.w[2], a.w[3], 1);
+  r.w[2] = __funnelshift_l(a.w[1], a.w[2], 1);
+  r.w[1] = __funnelshift_l(a.w[0], a.w[1], 1);
+  r.w[0] = a.w[0] << 1;
+  return r;
+}
+
+// signed Q2.126 phasor (|z| ~ 1) -> first-quadrant form
+__device__ __forceinline__ qent to_quadrant(const fxc& z) {
+  const bool xn = (int32_t)z.re.w[3] < 0, yn = (int32_t)z.im.w[3] < 0;
+  const uint32_t q = xn ? (yn ? 2u : 1u) : (yn ? 3u : 0u);
+  q128 c, s;
+  switch (q) {  // rotate by i^-q: both components become non-negative
+    case 0: c = z.re; s = z.im; break;
+    case 1: c = z.im; s = q128_neg(z.re); break;
+    case 2: c = q128_neg(z.re); s = q128_neg(z.im); break;
+    default: c = q128_neg(z.im); s = z.re; break;
+  }
+  qent e;
+  e.c = q128_shl1(c);
+  e.s = q128_shl1(s);
+  e.cs = q128_add(e.c, e.s);
+  e.cs.w[0] = (e.cs.w[0] & ~3u) | q;
+  return e;
+}
+
+// Top 128 bits of the unsigned 256-bit product a * b (r[1..4] of umul_top), as a q128.
+__device__ __forceinline__ q128 umulhi(const q128& a, const q128& b) {
+  uint32_t r[5];
+  umul_top(a, b, r);
+  q128 o;
+  o.w[0] = r[1];
+  o.w[1] = r[2];
+  o.w[2] = r[3];
+  o.w[3] = r[4];
+  return o;
+}
+
+// acc += (negate ? ~a : a), sign-extended to 160 bits; ~a = -a - 2^-126, the caller counts the missing units.
+__device__ __forceinline__ void q160_add_xor(q160& acc, const q128& a, uint32_t m) {
+  q128 x;
+  x.w[0] = a.w[0] ^ m;
+  x.w[1] = a.w[1] ^ m;
+  x.w[2] = a.w[2] ^ m;
+  x.w[3] = a.w[3] ^ m;
+  q160_add(acc, x);
+}
+
+// acc += k (a small non-negative count of units of 2^-126)
+__device__ __forceinline__ void q160_add_units(q160& acc, uint32_t k) {
+  asm("add.cc.u32 %0, %0, %5;\n\t"
+      "addc.cc.u32 %1, %1, 0;\n\t"
+      "addc.cc.u32 %2, %2, 0;\n\t"
+      "addc.cc.u32 %3, %3, 0;\n\t"
+      "addc.u32 %4, %4, 0;"
+      : "+r"(acc.w[0]), "+r"(acc.w[1]), "+r"(acc.w[2]), "+r"(acc.w[3]), "+r"(acc.w[4])
+      : "r"(k));
+}

@@ -258,6 +258,121 @@ __global__ void __launch_bounds__(kNtThreads) k_ntilde(const CfgDev* __restrict_
   }
 }
 
+// ---- fixed-point density kernel: first-quadrant phasors, three unsigned products per pair
+// Shared memory per particle: ng G entries (48 B each), then the 32 low-digit entries with a 16-byte skew every
+// fourth entry (entry r at 48 r + 16 (r / 4)), so the 4-strided reads of a warp fall on distinct banks; the
+// per-particle stride is 16 mod 128 bytes so that staging stores spread over the banks too.
+__host__ __device__ __forceinline__ int fx_lo_off(int r) { return 48 * r + 16 * (r >> 2); }
+__host__ __device__ __forceinline__ int fx_particle_bytes(int ng) {
+  int b = 48 * ng + 48 * kDigit + 16 * (kDigit / 4);
+  return b + (((16 - b % 128) % 128) + 128) % 128;
+}
+
+__global__ void __launch_bounds__(kNtThreads) k_ntilde_fx(const CfgDev* __restrict__ cfgs, const NtItem* __restrict__ items,
+                                                          int n_items, int* __restrict__ queue) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int s_item;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
+    __syncthreads();
+    const int ii = s_item;
+    if (ii >= n_items) return;
+    const NtItem it = items[ii];
+    const CfgDev& c = cfgs[it.cfg];
+    if (stopped(c)) continue;
+    const fxc* __restrict__ tab = reinterpret_cast<const fxc*>(c.tab);
+    const int64_t ld = c.Npad;
+    const NtBlock blk = c.blocks[it.blk];
+    const int64_t plen = c.plen[SSH_FX];
+    const int pchunk = c.pchunk[SSH_FX];
+    const int64_t j_begin = (int64_t)it.ps * plen;
+    const int64_t j_end = min(c.N, j_begin + plen);
+    const int nrow = blk.ng + kDigit;
+    const int pbytes = fx_particle_bytes(blk.ng);
+    const int lo_base_b = 48 * blk.ng;
+    const bool active = (int)threadIdx.x < blk.nslots;
+    NtSlot sl;
+    if (active) sl = c.slots[blk.slot0 + threadIdx.x];
+    else { sl.k0 = 0; sl.cnt = 0; sl.g = 0; sl.r0 = 0; }
+    q160 accC[kSlotK], accS[kSlotK];
+    uint32_t cntC[kSlotK], cntS[kSlotK];
+#pragma unroll
+    for (int i = 0; i < kSlotK; i++) {
+      accC[i] = q160_zero();
+      accS[i] = q160_zero();
+      cntC[i] = 0;
+      cntS[i] = 0;
+    }
+    for (int64_t j0 = j_begin; j0 < j_end; j0 += pchunk) {
+      const int pc = (int)min((int64_t)pchunk, j_end - j0);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < nrow * pc; idx += blockDim.x) {
+        const int row = idx / pc, jj = idx - row * pc;
+        const int64_t j = j0 + jj;
+        fxc v;
+        int off;
+        if (row < blk.ng) {
+          const int32_t* gr = c.g_rows + (int64_t)(blk.g0 + row) * kMaxDim;
+          v = PolFX::load(tab + (int64_t)gr[kMaxDim - 1] * ld + j);
+#pragma unroll
+          for (int a = 0; a < kMaxDim - 1; a++)
+            if (gr[a] >= 0) v = fxc_mul(v, PolFX::load(tab + (int64_t)gr[a] * ld + j));
+          off = 48 * row;
+        } else {
+          v = PolFX::load(tab + (int64_t)(c.lo_base + row - blk.ng) * ld + j);
+          off = lo_base_b + fx_lo_off(row - blk.ng);
+        }
+        *reinterpret_cast<qent*>(smem_raw + jj * pbytes + off) = to_quadrant(v);
+      }
+      __syncthreads();
+      if (active) {
+        for (int jj = 0; jj < pc; jj++) {
+          const unsigned char* base = smem_raw + jj * pbytes;
+          const qent G = *reinterpret_cast<const qent*>(base + 48 * sl.g);
+          const uint32_t qG = G.cs.w[0];
+#pragma unroll
+          for (int i = 0; i < kSlotK; i++) {
+            if (i < sl.cnt) {
+              const qent T = *reinterpret_cast<const qent*>(base + lo_base_b + fx_lo_off(sl.r0 + i));
+              const q128 p1 = umulhi(G.c, T.c), p2 = umulhi(G.s, T.s), p3 = umulhi(G.cs, T.cs);
+              const q128 re = q128_sub(p1, p2);
+              const q128 im = q128_sub(q128_sub(p3, p1), p2);
+              const uint32_t q = (qG + T.cs.w[0]) & 3u;
+              const bool sw = q & 1u;
+              q128 a, b;
+#pragma unroll
+              for (int w = 0; w < 4; w++) {
+                a.w[w] = sw ? im.w[w] : re.w[w];
+                b.w[w] = sw ? re.w[w] : im.w[w];
+              }
+              const uint32_t mC = 0u - (((q >> 1) ^ q) & 1u), mS = 0u - (q >> 1);
+              q160_add_xor(accC[i], a, mC);
+              q160_add_xor(accS[i], b, mS);
+              cntC[i] += mC & 1u;
+              cntS[i] += mS & 1u;
+            }
+          }
+        }
+      }
+    }
+    if (active) {
+      FxAcc* part = reinterpret_cast<FxAcc*>(c.part) + (int64_t)it.ps * c.M;
+#pragma unroll
+      for (int i = 0; i < kSlotK; i++) {
+        if (i < sl.cnt) {
+          FxAcc o;
+          o.re = accC[i];
+          o.im = accS[i];
+          q160_add_units(o.re, cntC[i]);  // the +1 units of each one's-complement negation
+          q160_add_units(o.im, cntS[i]);
+          part[sl.k0 + i] = o;
+        }
+      }
+    }
+  }
+}
+
 struct RedPart {  // per-block partials of the density reduction
   double phi_hi, phi_lo, a2max_hi, a2max_lo, cmax, pad0, pad1, pad2;
 };
@@ -464,10 +579,11 @@ void setup_launch(Ctx* c) {
     int stride = (c->nt.max_ng + kDigit) | 1;
     L.nt_stride = stride;
     size_t budget = 96 * 1024;
-    int pchunk = (int)(budget / ((size_t)stride * tab_bytes(prec)));
+    const size_t per_particle = prec == SSH_FX ? (size_t)fx_particle_bytes(c->nt.max_ng) : (size_t)stride * tab_bytes(prec);
+    int pchunk = (int)(budget / per_particle);
     pchunk = std::max(8, std::min(64, pchunk & ~7));
     L.nt_pchunk = pchunk;
-    L.nt_smem = (size_t)pchunk * stride * tab_bytes(prec);
+    L.nt_smem = (size_t)pchunk * per_particle;
     int ps = nblocks > 0 ? (target + nblocks - 1) / nblocks : 1;
     int64_t max_ps = std::max<int64_t>(1, c->N / pchunk);
     L.nt_psplit = (int)std::max<int64_t>(1, std::min<int64_t>(ps, max_ps));
@@ -490,7 +606,10 @@ static cudaError_t launch_prec(const EngineView& v, bool want_force, cudaStream_
     cudaMemsetAsync(v.counters, 0, sizeof(int), st);
     const int grid = std::min(v.nnt, 2 * v.sm_count);
     prof_begin(prof, st, kKNtilde);
-    k_ntilde<P><<<grid, kNtThreads, v.nt_smem, st>>>(v.cfgs, v.nt, v.nnt, v.counters);
+    if constexpr (P::kIdx == SSH_FX)
+      k_ntilde_fx<<<grid, kNtThreads, v.nt_smem, st>>>(v.cfgs, v.nt, v.nnt, v.counters);
+    else
+      k_ntilde<P><<<grid, kNtThreads, v.nt_smem, st>>>(v.cfgs, v.nt, v.nnt, v.counters);
     prof_end(prof, st);
   }
   const dim3 gr((unsigned)std::max(1, v.maxblk), (unsigned)v.nlist);
@@ -534,6 +653,7 @@ void kernels_set_attributes(size_t smem_max) {
   cudaFuncSetAttribute(k_ntilde<PolF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
   cudaFuncSetAttribute(k_ntilde<PolDD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
   cudaFuncSetAttribute(k_ntilde<PolFX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+  cudaFuncSetAttribute(k_ntilde_fx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
 }
 
 // ------------------------------------------------------------------------------------------------ profiler
