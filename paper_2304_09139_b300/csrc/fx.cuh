@@ -323,15 +323,40 @@ __device__ __forceinline__ qent to_quadrant(const fxc& z) {
   return e;
 }
 
-// Top 128 bits of the unsigned 256-bit product a * b (r[1..4] of umul_top), as a q128.
+// Top 128 bits (limbs 4..7) of the unsigned 256-bit product a * b from 16 multiply-adds: the high halves of the
+// limb-3 column and everything above it.  The dropped low halves of column 3 and all lower columns sum to less
+// than 7 * 2^128, so the result is low by at most 8 units of its last place (8 * 2^-126 in Q2.126).
 __device__ __forceinline__ q128 umulhi(const q128& a, const q128& b) {
-  uint32_t r[5];
-  umul_top(a, b, r);
   q128 o;
-  o.w[0] = r[1];
-  o.w[1] = r[2];
-  o.w[2] = r[3];
-  o.w[3] = r[4];
+  asm("mul.hi.u32 %0, %4, %11;\n\t"
+      "mad.hi.cc.u32 %0, %5, %10, %0;\n\t"
+      "addc.u32 %1, 0, 0;\n\t"
+      "mad.hi.cc.u32 %0, %6, %9, %0;\n\t"
+      "addc.u32 %1, %1, 0;\n\t"
+      "mad.hi.cc.u32 %0, %7, %8, %0;\n\t"
+      "addc.u32 %1, %1, 0;\n\t"
+      // column 4: a1 b3, a2 b2, a3 b1
+      "mad.lo.cc.u32 %0, %5, %11, %0;\n\t"
+      "madc.hi.cc.u32 %1, %5, %11, %1;\n\t"
+      "addc.u32 %2, 0, 0;\n\t"
+      "mad.lo.cc.u32 %0, %6, %10, %0;\n\t"
+      "madc.hi.cc.u32 %1, %6, %10, %1;\n\t"
+      "addc.u32 %2, %2, 0;\n\t"
+      "mad.lo.cc.u32 %0, %7, %9, %0;\n\t"
+      "madc.hi.cc.u32 %1, %7, %9, %1;\n\t"
+      "addc.u32 %2, %2, 0;\n\t"
+      // column 5: a2 b3, a3 b2
+      "mad.lo.cc.u32 %1, %6, %11, %1;\n\t"
+      "madc.hi.cc.u32 %2, %6, %11, %2;\n\t"
+      "addc.u32 %3, 0, 0;\n\t"
+      "mad.lo.cc.u32 %1, %7, %10, %1;\n\t"
+      "madc.hi.cc.u32 %2, %7, %10, %2;\n\t"
+      "addc.u32 %3, %3, 0;\n\t"
+      // column 6: a3 b3
+      "mad.lo.cc.u32 %2, %7, %11, %2;\n\t"
+      "madc.hi.u32 %3, %7, %11, %3;"
+      : "=&r"(o.w[0]), "=&r"(o.w[1]), "=&r"(o.w[2]), "=&r"(o.w[3])
+      : "r"(a.w[0]), "r"(a.w[1]), "r"(a.w[2]), "r"(a.w[3]), "r"(b.w[0]), "r"(b.w[1]), "r"(b.w[2]), "r"(b.w[3]));
   return o;
 }
 
@@ -354,4 +379,37 @@ __device__ __forceinline__ void q160_add_units(q160& acc, uint32_t k) {
       "addc.u32 %4, %4, 0;"
       : "+r"(acc.w[0]), "+r"(acc.w[1]), "+r"(acc.w[2]), "+r"(acc.w[3]), "+r"(acc.w[4])
       : "r"(k));
+}
+
+// z * b for first-quadrant phasors, renormalised to the first quadrant: three unsigned products give
+// re = c1 c2 - s1 s2 and im = (c1 + s1)(c2 + s2) - c1 c2 - s1 s2 >= 0; if re < 0 the result is rotated by -i
+// (c, s) = (im, -re) and the quadrant advances.  The Q2.126 results are doubled back to Q1.127.
+__device__ __forceinline__ qent qmul(const qent& z, const qent& b) {
+  const q128 p1 = umulhi(z.c, b.c), p2 = umulhi(z.s, b.s), p3 = umulhi(z.cs, b.cs);
+  const q128 re = q128_sub(p1, p2);
+  const q128 im = q128_sub(q128_sub(p3, p1), p2);
+  uint32_t q = (z.cs.w[0] + b.cs.w[0]) & 3u;
+  const bool neg = (int32_t)re.w[3] < 0;
+  const q128 nre = q128_neg(re);
+  q128 c, s;
+#pragma unroll
+  for (int w = 0; w < 4; w++) {
+    c.w[w] = neg ? im.w[w] : re.w[w];
+    s.w[w] = neg ? nre.w[w] : im.w[w];
+  }
+  q = (q + (neg ? 1u : 0u)) & 3u;
+  qent r;
+  r.c = q128_shl1(c);
+  r.s = q128_shl1(s);
+  r.cs = q128_add(r.c, r.s);
+  r.cs.w[0] = (r.cs.w[0] & ~3u) | q;
+  return r;
+}
+
+// Sign-magnitude Q1.127 of a Q2.126 value with |x| < 1/2: the magnitude doubled, the sign in bit 127.
+__device__ __forceinline__ q128 q127_signmag(const q128& x) {
+  const bool neg = (int32_t)x.w[3] < 0;
+  q128 m = q128_shl1(neg ? q128_neg(x) : x);
+  if (neg) m.w[3] |= 0x80000000u;
+  return m;
 }

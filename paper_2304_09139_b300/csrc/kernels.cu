@@ -140,10 +140,11 @@ struct PolFX {
   static __device__ __forceinline__ RAcc rmul_int(const RAcc& a, int k) { return q160_mul_int(a, k); }
   static __device__ __forceinline__ RAcc rsub(const RAcc& a, const RAcc& b) { return q160_sub160(a, b); }
   static __device__ __forceinline__ dd r_to_dd(const RAcc& a) { dd r; q160_to_dd(a, &r.hi, &r.lo); return r; }
+  // (C, S) 2^-e (|.| < 1/2) as sign-magnitude Q1.127 for the fixed-point force kernel
   static __device__ __forceinline__ Coef make_coef(dd c, dd s, int e) {
     fxc z;
-    z.re = q126_from_dd(ldexp(c.hi, -e), ldexp(c.lo, -e));
-    z.im = q126_from_dd(ldexp(s.hi, -e), ldexp(s.lo, -e));
+    z.re = q127_signmag(q126_from_dd(ldexp(c.hi, -e), ldexp(c.lo, -e)));
+    z.im = q127_signmag(q126_from_dd(ldexp(s.hi, -e), ldexp(s.lo, -e)));
     return z;
   }
   static __device__ __forceinline__ Tab phasor(int32_t m, double sh, double sl) {
@@ -548,6 +549,104 @@ __global__ void __launch_bounds__(kForceThreads) k_force(const CfgDev* __restric
   }
 }
 
+// ---- fixed-point force kernel: phase recurrence and coefficient products on first-quadrant unsigned values
+// With z = i^q (c + i s) and conj(n~) = C - i S, w = Im(conj(n~) z) is
+//   q = 0: C s - S c,   q = 1: S s + C c,   q = 2: -C s + S c,   q = 3: -S s - C c,
+// i.e. +-X s +- Y c with (X, Y) = (C, S) for even q and (S, C) for odd q: two unsigned products of the
+// sign-magnitude coefficients.  Negations are one's complements whose missing units are counted (cntA for
+// A = sum w, cntB for B = sum A) and added exactly at the end of the column.
+__global__ void __launch_bounds__(kForceThreads) k_force_fx(const CfgDev* __restrict__ cfgs, const FItem* __restrict__ items,
+                                                            int n_items, int* __restrict__ queue) {
+  __shared__ int s_item;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
+    __syncthreads();
+    const int ii = s_item;
+    if (ii >= n_items) return;
+    const FItem it = items[ii];
+    const CfgDev& c = cfgs[it.cfg];
+    if (stopped(c)) continue;
+    const fxc* __restrict__ tab = reinterpret_cast<const fxc*>(c.tab);
+    const uint4* __restrict__ coef = reinterpret_cast<const uint4*>(c.coef);
+    const int64_t ld = c.Npad, N = c.N;
+    const int d = c.d;
+    const int64_t j = (int64_t)it.pb * kForceThreads + threadIdx.x;
+    const int64_t jj = j < N ? j : N - 1;
+    const qent bq = to_quadrant(PolFX::load(tab + (int64_t)(c.lo_base + 1) * ld + jj));
+    q160 F[kMaxDim];
+#pragma unroll
+    for (int a = 0; a < kMaxDim; a++) F[a] = q160_zero();
+    const int c_end = c.fsplit[it.ks + 1];
+    for (int ci = c.fsplit[it.ks]; ci < c_end; ci++) {
+      const FCol col = c.cols[ci];
+      fxc G = PolFX::one();
+      const bool hasG = d > 1;
+#pragma unroll
+      for (int a = 0; a < kMaxDim - 1; a++) {
+        if (a + 1 < d) {
+          fxc t = PolFX::load(tab + (int64_t)col.rows[a] * ld + jj);
+          G = a > 0 ? fxc_mul(G, t) : t;
+        }
+      }
+      int q = floordiv_d(col.nlo, kDigit);
+      int r = col.nlo - q * kDigit;
+      fxc zs = PolFX::load(tab + (int64_t)(c.hi_base + q - c.qmin) * ld + jj);
+      if (hasG) zs = fxc_mul(G, zs);
+      if (r != 0) zs = fxc_mul(zs, PolFX::load(tab + (int64_t)(c.lo_base + r) * ld + jj));
+      qent z = to_quadrant(zs);
+      q160 A = q160_zero(), B = q160_zero();
+      uint32_t cntA = 0, cntB = 0;
+      for (int i = 0; i < col.len; i++) {
+        if (i > 0) {
+          if (++r == kDigit) {  // re-anchor at each digit boundary
+            r = 0;
+            q++;
+            zs = PolFX::load(tab + (int64_t)(c.hi_base + q - c.qmin) * ld + jj);
+            if (hasG) zs = fxc_mul(G, zs);
+            z = to_quadrant(zs);
+          } else {
+            z = qmul(z, bq);
+          }
+        }
+        const uint4 cr = __ldg(coef + 2 * (col.k0 + i)), sr = __ldg(coef + 2 * (col.k0 + i) + 1);
+        const uint32_t qz = z.cs.w[0] & 3u;
+        const bool odd = qz & 1u;
+        q128 X, Y;
+        X.w[0] = odd ? sr.x : cr.x;  Y.w[0] = odd ? cr.x : sr.x;
+        X.w[1] = odd ? sr.y : cr.y;  Y.w[1] = odd ? cr.y : sr.y;
+        X.w[2] = odd ? sr.z : cr.z;  Y.w[2] = odd ? cr.z : sr.z;
+        X.w[3] = odd ? sr.w : cr.w;  Y.w[3] = odd ? cr.w : sr.w;
+        const uint32_t sX = X.w[3] >> 31, sY = Y.w[3] >> 31;
+        X.w[3] &= 0x7FFFFFFFu;
+        Y.w[3] &= 0x7FFFFFFFu;
+        const uint32_t negA = (qz >> 1) ^ sX;                      // sign of the X s term
+        const uint32_t negB = (((qz ^ (qz >> 1)) & 1u) ^ 1u) ^ sY;  // sign of the Y c term
+        const q128 pa = umulhi(X, z.s), pb = umulhi(Y, z.c);
+        q160_add_xor(A, pa, 0u - negA);
+        q160_add_xor(A, pb, 0u - negB);
+        cntA += negA + negB;
+        q160_add160(B, A);
+        cntB += cntA;
+      }
+      q160_add_units(A, cntA);
+      q160_add_units(B, cntB);
+      const q160 last = q160_sub160(q160_mul_int(A, col.nlo + col.len), B);
+#pragma unroll
+      for (int a = 0; a < kMaxDim; a++) {
+        if (a + 1 < d) q160_add160(F[a], q160_mul_int(A, col.pre[a < kMaxDim - 1 ? a : 0]));
+        else if (a + 1 == d) q160_add160(F[a], last);
+      }
+    }
+    if (j < N) {
+      q160* fpart = reinterpret_cast<q160*>(c.fpart);
+#pragma unroll
+      for (int a = 0; a < kMaxDim; a++)
+        if (a < d) fpart[((int64_t)it.ks * d + a) * N + j] = F[a];
+    }
+  }
+}
+
 // grid (coordinate blocks, configurations of this precision)
 template <class P>
 __global__ void k_f_reduce(const CfgDev* __restrict__ cfgs, const int* __restrict__ list) {
@@ -628,7 +727,10 @@ static cudaError_t launch_prec(const EngineView& v, bool want_force, cudaStream_
       cudaMemsetAsync(v.counters + 1, 0, sizeof(int), st);
       const int grid = std::min(v.nfi, 5 * v.sm_count);
       prof_begin(prof, st, kKForce);
-      k_force<P><<<grid, kForceThreads, 0, st>>>(v.cfgs, v.fi, v.nfi, v.counters + 1);
+      if constexpr (P::kIdx == SSH_FX)
+        k_force_fx<<<grid, kForceThreads, 0, st>>>(v.cfgs, v.fi, v.nfi, v.counters + 1);
+      else
+        k_force<P><<<grid, kForceThreads, 0, st>>>(v.cfgs, v.fi, v.nfi, v.counters + 1);
       prof_end(prof, st);
     }
     const dim3 gf((unsigned)std::max<int64_t>(1, (v.maxND + 255) / 256), (unsigned)v.nlist);
