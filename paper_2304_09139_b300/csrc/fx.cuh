@@ -323,9 +323,9 @@ __device__ __forceinline__ qent to_quadrant(const fxc& z) {
   return e;
 }
 
-// Top 128 bits (limbs 4..7) of the unsigned 256-bit product a * b from 16 multiply-adds: the high halves of the
-// limb-3 column and everything above it.  The dropped low halves of column 3 and all lower columns sum to less
-// than 7 * 2^128, so the result is low by at most 8 units of its last place (8 * 2^-126 in Q2.126).
+// Top 128 bits (limbs 4..7) of the unsigned 256-bit product a * b from 16 multiply-adds in carry chains: the high
+// halves of the limb-3 column and everything above it.  The dropped low halves of column 3 and all lower columns
+// sum to less than 7 * 2^128, so the result is low by at most 8 units of its last place (8 * 2^-126 in Q2.126).
 __device__ __forceinline__ q128 umulhi(const q128& a, const q128& b) {
   q128 o;
   asm("mul.hi.u32 %0, %4, %11;\n\t"

@@ -686,8 +686,10 @@ void setup_launch(Ctx* c) {
     int ps = nblocks > 0 ? (target + nblocks - 1) / nblocks : 1;
     int64_t max_ps = std::max<int64_t>(1, c->N / pchunk);
     L.nt_psplit = (int)std::max<int64_t>(1, std::min<int64_t>(ps, max_ps));
+    // force items: enough (configuration, particle block, column split) tiles to keep every SM busy with several
+    // resident CTAs of the persistent kernel
     int pblocks = (int)((c->N + kForceThreads - 1) / kForceThreads);
-    int kspl = (target + pblocks - 1) / pblocks;
+    int kspl = (8 * c->sm_count + pblocks - 1) / pblocks;
     kspl = std::max(1, std::min(kspl, (int)c->fp.cols.size()));
     L.f_ksplit = kspl;
   }
