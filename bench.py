@@ -31,10 +31,10 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 # Algorithmic integer multiply-add (IMAD pipe) instructions per (k, particle) pair in the fixed-point
-# kernels: one truncated 128x128 product is 20 32-bit multiply-adds; the density kernel does one complex
-# product per pair (4 products), the force kernel one complex product (phase recurrence) plus the two
-# products of C sin - S cos.
-FX_IMAD_PER_PAIR = {"ntilde": 80, "force": 120}
+# kernels: one truncated 128x128 top half is 16 32-bit multiply-adds; a complex multiply of first-quadrant
+# phasors is three of them; the density kernel does one complex multiply per pair (48), the force kernel one
+# (the phase recurrence) plus the two products of C sin - S cos (80).
+FX_IMAD_PER_PAIR = {"ntilde": 48, "force": 80}
 # Algorithmic FP64 instructions per pair on the double-double path (dd_mul = 8, dd_add = 20 flops as
 # written in dd.cuh): density = complex dd multiply (4 mul + 2 add = 72) + complex accumulate (2 add = 40);
 # force = complex multiply (72) + w = C sin - S cos (2 mul + 1 add = 36) + A += w, B += A (40).
@@ -50,9 +50,8 @@ WORKLOAD = dict(d=2, N=10_000, L=100.0, chi=0.45, seed=2)
 
 # DRAM bytes (read + write) per launch from one ncu capture of this workload (profiles/), valid only while
 # the kernel sources hash to the value recorded with them; otherwise the traffic is reported as null.
-# (captured at source hash 4b684e8da53d; 14456463733e differs from it only in comments)
-NCU_TRAFFIC = {("fx", "force"): ("14456463733e", 35_851_520 + 2_560),
-               ("fx", "ntilde"): ("14456463733e", 36_560_896 + 2_560)}
+NCU_TRAFFIC = {("fx", "force"): ("9a8b45757c86", 35_869_184 + 5_888_000),
+               ("fx", "ntilde"): ("9a8b45757c86", 36_598_272 + 43_264_000)}
 
 
 def kernel_source_hash() -> str:
@@ -87,6 +86,26 @@ def dist_info():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def replica_seed(seed: int, rank: int) -> int:
+    """Each rank quenches its own configuration (an independent replica): same sizes, its own draw."""
+    return seed + rank
+
+
+def max_over_ranks(x: float, dist=None, device=None) -> float:
+    """The slowest rank's time: every rank holds the same per-GPU work, so the job ends with the last one."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(pairs_per_gpu: int, world: int, steps: int, tot_ms: float) -> float:
+    """Whole-job throughput: the pairs all ranks processed over the slowest rank's time."""
+    return pairs_per_gpu * world * steps / (tot_ms / 1e3)
 
 
 class Clocks:
@@ -296,7 +315,7 @@ def main():
     stream = torch.cuda.Stream(dev)          # a real (non-legacy) stream shared by torch and the library
     ctx.set_stream(stream.cuda_stream)
     torch.cuda.set_stream(stream)
-    s = synth.positions(w["seed"] + rank, w["N"], w["d"])
+    s = synth.positions(replica_seed(w["seed"], rank), w["N"], w["d"])
     ctx.set_positions_frac(s)
     pairs = ctx.M * ctx.N
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
@@ -340,11 +359,8 @@ def main():
     tot_ms = sum(step_ms)
     prof = ctx.prof_read()
     ctx.prof_enable(False)
-    if dist:
-        t = torch.tensor([tot_ms], device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = pairs * world * args.steps / (tot_ms / 1e3)
+    tot_ms = max_over_ranks(tot_ms, dist, device=f"cuda:{dev}")
+    value = job_value(pairs, world, args.steps, tot_ms)
     # every profiled id is one kernel, except "fire": its two event pairs per step cover 3 + 2 kernels
     launches = sum(n for k, n in ((k, v[1]) for k, v in prof.items()) if k != "fire") + \
         5 * prof.get("fire", (0, 0))[1] // 2
@@ -378,11 +394,13 @@ def main():
     ctx.set_positions_frac(s2)
     ctx.energy_grad(prec)
     torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
     t0 = time.perf_counter()
     for i in range(e2e_steps):
         ctx.set_positions_frac(s2 if i % 2 == 0 else s)
         ctx.energy_grad(prec)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, dist, device=f"cuda:{dev}")
     h2d = 2 * 8 * w["d"] * w["N"]
     d2h = 2 * 8 * w["d"] * w["N"] + 16 * 8
 
@@ -412,7 +430,7 @@ def main():
                        "l2": "flushed between timed steps (256 MiB write, outside the step events)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "gpu_launches": launches, "wall_s": t_wall,
-            "e2e": {"value": pairs / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "e2e": {"value": pairs * world / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": clk.summary(), "variants_pairs_per_s": variants}
     if rank == 0 and not args.no_minimize:
         line["minimize"] = minimize_block(ssh, synth, w, dev, stream, with_dd=args.minimize_dd,
