@@ -39,12 +39,27 @@ FX_IMAD_PER_PAIR = {"ntilde": 48, "force": 80}
 # written in dd.cuh): density = complex dd multiply (4 mul + 2 add = 72) + complex accumulate (2 add = 40);
 # force = complex multiply (72) + w = C sin - S cos (2 mul + 1 add = 36) + A += w, B += A (40).
 DD_FP64_PER_PAIR = {"ntilde": 112, "force": 148}
+# Tensor-core fixed point (d = 2): every real product of two 2^-104 fixed-point values is 120 bf16 digit-pair
+# products.  The density needs 2 real products per (k, particle) pair (4 real products serve k = (n1, +m) and
+# (n1, -m)), the force 4 (G and the n2-weighted G', cos and sin terms, again for both signs of m).
+TC_FLOP_PER_PAIR = {"ntilde": 2 * 2 * 120, "force": 2 * 4 * 120}
 F64_FP64_PER_PAIR = {"ntilde": 6, "force": 8}
 # Peaks derived from unit counts and the maximum SM clock (148 SMs, 2032 MHz): 64 IMAD lanes per SM per
 # clock; 2 FP64 FMA lanes per SM per clock (1.2 TFLOP/s).
 SM_COUNT, SM_MAX_MHZ = 148, 2032.0
 IMAD_PEAK = 64 * SM_COUNT * SM_MAX_MHZ * 1e6
 FP64_PEAK = 2 * SM_COUNT * SM_MAX_MHZ * 1e6
+
+
+def _measured_bf16_peak() -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]) * 1e12
+    except (OSError, KeyError, ValueError):
+        return 1.8e15   # one earlier B300 measurement, used only when the measured file is absent
+
+
+BF16_PEAK = _measured_bf16_peak()
 
 WORKLOAD = dict(d=2, N=10_000, L=100.0, chi=0.45, seed=2)
 
@@ -69,6 +84,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--prec", default="fx", choices=["fx", "dd", "fp64"])
+    ap.add_argument("--fx-impl", default="auto", choices=["auto", "integer", "tensor"],
+                    help="fixed-point implementation: integer pipes or exact-digit tensor-core GEMMs (d = 2)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
@@ -109,17 +126,50 @@ def job_value(pairs_per_gpu: int, world: int, steps: int, tot_ms: float) -> floa
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clock and throttle reasons while the timed region runs."""
+    """SM clock and clock-event (throttle) reasons sampled while the timed region runs: through NVML every
+    millisecond from a thread (the device found by its PCI bus id), else nvidia-smi -lms 200."""
 
     FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
              "clocks_event_reasons.sw_power_cap"
+    REASONS = {"hw_slowdown": 0x8, "hw_thermal_slowdown": 0x40, "sw_thermal_slowdown": 0x20, "sw_power_cap": 0x4}
 
     def __init__(self, device: int):
         self.device = device
         self.proc = None
+        self.thread = None
+        self.samples = []
+        self.max_mhz = None
+
+    def _nvml_handle(self):
+        import pynvml
+        import torch
+        pynvml.nvmlInit()
+        p = torch.cuda.get_device_properties(self.device)
+        bus = f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+        return pynvml, pynvml.nvmlDeviceGetHandleByPciBusId(bus)
+
+    def _poll(self, nv, h):
+        get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self.stop.is_set():
+            try:
+                self.samples.append((float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)), int(get_reasons(h))))
+            except Exception:
+                break
+            time.sleep(0.001)
 
     def __enter__(self):
+        import threading
+        try:
+            nv, h = self._nvml_handle()
+            self.max_mhz = float(nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM))
+            self.stop = threading.Event()
+            self.thread = threading.Thread(target=self._poll, args=(nv, h), daemon=True)
+            self.thread.start()
+            return self
+        except Exception:
+            self.thread = None
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -130,6 +180,9 @@ class Clocks:
 
     def __exit__(self, *a):
         self.lines = []
+        if self.thread:
+            self.stop.set()
+            self.thread.join(timeout=5)
         if self.proc:
             self.proc.terminate()
             try:
@@ -140,6 +193,12 @@ class Clocks:
             self.lines = [ln for ln in out.splitlines() if ln.strip()]
 
     def summary(self):
+        if self.thread is not None:
+            if not self.samples:
+                return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": [], "samples": 0, "source": "nvml"}
+            reasons = sorted(nm for nm, bit in self.REASONS.items() if any(r & bit for _, r in self.samples))
+            return {"sm_mhz": statistics.median(m for m, _ in self.samples), "sm_max_mhz": self.max_mhz,
+                    "reasons": reasons, "samples": len(self.samples), "source": "nvml, 1 ms"}
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in getattr(self, "lines", []):
@@ -155,8 +214,9 @@ class Clocks:
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0, "source": "nvidia-smi"}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm),
+                "source": "nvidia-smi, 200 ms"}
 
 
 def cpu_sample(N, d, L, chi, seed, frac_k=8, nthreads=0):
@@ -311,7 +371,8 @@ def main():
     _build.build()
     prec = {"fx": ssh.FX, "dd": ssh.DD, "fp64": ssh.FP64}[args.prec]
     w = WORKLOAD
-    ctx = ssh.Context(w["d"], w["N"], w["L"], chi=w["chi"], device=dev)
+    fx_impl = {"auto": ssh.FX_AUTO, "integer": ssh.FX_INTEGER, "tensor": ssh.FX_TENSOR}[args.fx_impl]
+    ctx = ssh.Context(w["d"], w["N"], w["L"], chi=w["chi"], device=dev, fx_impl=fx_impl)
     stream = torch.cuda.Stream(dev)          # a real (non-legacy) stream shared by torch and the library
     ctx.set_stream(stream.cuda_stream)
     torch.cuda.set_stream(stream)
@@ -369,7 +430,14 @@ def main():
     dom = max(prof.items(), key=lambda kv: kv[1][0])
     dom_name, (dom_ms, dom_n) = dom
     per_launch_s = dom_ms / 1e3 / dom_n
-    if prec == ssh.FX:
+    tensor = prec == ssh.FX and ctx.fx_impl == ssh.FX_TENSOR
+    if tensor:
+        # the dominant of the two contractions (the digit preparation is reported in per_kernel_ms)
+        dom_name = max(("ntilde", "force"), key=lambda k: prof.get(k, (0.0, 1))[0])
+        dom_ms, dom_n = prof[dom_name]
+        per_launch_s = dom_ms / 1e3 / dom_n
+        per_pair, peak, unit, bound, what = TC_FLOP_PER_PAIR, BF16_PEAK, "FLOP/s", "tensor", "bf16"
+    elif prec == ssh.FX:
         per_pair, peak, unit, bound, what = FX_IMAD_PER_PAIR, IMAD_PEAK, "IMAD/s", "alu", "IMAD"
     elif prec == ssh.DD:
         per_pair, peak, unit, bound, what = DD_FP64_PER_PAIR, FP64_PEAK, "FP64 instr/s", "fp64", "FP64"
@@ -381,10 +449,12 @@ def main():
         roof = {"bound": bound, "kernel": dom_name, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "traffic": None,
                 "traffic_unit": "bytes per launch (dram read + write, ncu)",
-                "peak_source": f"unit counts x max clock: {'64 IMAD' if what == 'IMAD' else '2 FP64 FMA'} "
-                               f"lanes/SM/clk x 148 SMs x 2032 MHz",
+                "peak_source": ("MEASURED_PEAKS.json bf16_tflops (cuBLAS bf16 GEMM, burst), of measured"
+                                if what == "bf16" else
+                                f"unit counts x max clock: {'64 IMAD' if what == 'IMAD' else '2 FP64 FMA'} "
+                                f"lanes/SM/clk x 148 SMs x 2032 MHz"),
                 "per_kernel_ms": {k: v[0] / v[1] for k, v in prof.items()}}
-        tr = NCU_TRAFFIC.get((args.prec, dom_name))
+        tr = NCU_TRAFFIC.get(("fx-tensor" if tensor else args.prec, dom_name))
         if tr and tr[0] == kernel_source_hash():
             roof["traffic"] = tr[1]
 
@@ -417,12 +487,28 @@ def main():
                 ctx.eval(p)
             ctx.sync()
             variants[name] = pairs / ((time.perf_counter() - t0) / reps)
+        if prec == ssh.FX and w["d"] == 2:
+            # the other fixed-point implementation on the same positions
+            other = ssh.FX_INTEGER if tensor else ssh.FX_TENSOR
+            with ssh.Context(w["d"], w["N"], w["L"], chi=w["chi"], device=dev, fx_impl=other) as c2:
+                c2.set_stream(stream.cuda_stream)
+                c2.set_positions_frac(s)
+                c2.eval(ssh.FX)
+                c2.sync()
+                t0 = time.perf_counter()
+                for _ in range(3):
+                    c2.eval(ssh.FX)
+                c2.sync()
+                variants["fx_integer" if tensor else "fx_tensor"] = pairs / ((time.perf_counter() - t0) / 3)
 
     line = {"metric": "dd (k,particle) pairs/s per Phi+grad", "value": value, "unit": "pairs/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fx": "q2.126 fixed point (4 x int32 limbs)", "dd": "double-double (2 x f64)",
-                      "fp64": "f64"}[args.prec],
+            "dtype": ("bf16 digit products (15 balanced 7-bit digits of 2^-104 fixed point), exact f32 "
+                      "accumulation, q34.126 sums" if tensor else
+                      {"fx": "q2.126 fixed point (4 x int32 limbs)", "dd": "double-double (2 x f64)",
+                       "fp64": "f64"}[args.prec]),
+            "fx_impl": ("tensor" if tensor else "integer") if prec == ssh.FX else None,
             "data": "synthetic",
             "config": {"workload": f"d={w['d']} N={w['N']} L={w['L']} chi={w['chi']} M={ctx.M}, uniform random "
                                    f"(SplitMix64 seed {w['seed']}+rank), one device FIRE step (Phi + force + "

@@ -52,9 +52,18 @@ typedef enum {
  */
 typedef enum { SSH_FP64 = 0, SSH_DD = 1, SSH_FX = 2 } ssh_prec;
 
+/* Implementation of SSH_FX evaluations (same arithmetic class, results agree to the 1e-28 normwise bound):
+ *   SSH_FX_AUTO    -- the library's choice: the tensor cores for d = 2, the integer pipes otherwise
+ *   SSH_FX_INTEGER -- 128-bit fixed point on the integer pipes, any d
+ *   SSH_FX_TENSOR  -- d = 2 only: both sums as exact-digit GEMMs on the tensor cores (15 balanced 7-bit digits per
+ *                     2^-104 fixed-point value in bf16, fp32 accumulation kept exact by bounded read-outs) */
+enum { SSH_FX_AUTO = 0, SSH_FX_INTEGER = 1, SSH_FX_TENSOR = 2 };
+#define SSH_FX_AUTO_TENSOR 1
+
 typedef struct {
   int device;       /* CUDA device ordinal (default 0) */
-  int reserved[7];  /* zero */
+  int fx_impl;      /* SSH_FX_AUTO (0, default), SSH_FX_INTEGER or SSH_FX_TENSOR */
+  int reserved[6];  /* zero */
 } ssh_opts;
 
 /* Library version string, e.g. "ssh 0.1 sm_103a". Never NULL. */
@@ -78,6 +87,9 @@ void ssh_destroy(ssh_ctx* ctx);
 
 /* Sizes: any pointer may be NULL. */
 ssh_status ssh_get_dims(const ssh_ctx* ctx, int* d, int64_t* N, int64_t* M, double* L);
+
+/* The implementation SSH_FX evaluations of this context use: SSH_FX_INTEGER or SSH_FX_TENSOR. */
+ssh_status ssh_get_fx_impl(const ssh_ctx* ctx, int* impl);
 
 /* The M wavevector indices n (k = 2 pi n / L) in public order: by |n|^2, then lexicographic.
  * n: caller buffer of M*d int32 (row-major), or NULL to query M only. */
@@ -246,7 +258,8 @@ typedef struct {
                                   (default 2^28, about 10 ms per step); bounds the step time that every
                                   running request shares; a larger request runs only in an empty batch */
   int policy;                  /* 0: smallest M N first (default), 1: first come first served */
-  int reserved[1];
+  int fx_impl;                 /* fixed-point implementation of the members (ssh_opts.fx_impl; SSH_FX_TENSOR
+                                  applies to the d = 2 requests, the others use the integer pipes) */
 } ssh_server_opts;
 typedef struct {
   int d;

@@ -62,6 +62,14 @@ ssh_status ssh_create(int d, int64_t N, double L, double chi, double K, const ss
   c.N = N;
   c.L = L;
   c.device = opts ? opts->device : 0;
+  const int fx_impl = opts ? opts->fx_impl : SSH_FX_AUTO;
+  if (fx_impl < SSH_FX_AUTO || fx_impl > SSH_FX_TENSOR) { delete h; set_error("ssh_create: bad fx_impl"); return SSH_EINVAL; }
+  if (fx_impl == SSH_FX_TENSOR && d != 2) {
+    delete h;
+    set_error("ssh_create: the tensor-core fixed-point path needs d = 2");
+    return SSH_EINVAL;
+  }
+  c.tc_requested = fx_impl == SSH_FX_TENSOR || (fx_impl == SSH_FX_AUTO && d == 2 && SSH_FX_AUTO_TENSOR);
   if (ssh::build_kset(d, N, L, chi, K, &c.ks) != 0) {
     delete h;
     set_error("ssh_create: could not build the wavevector set");
@@ -105,6 +113,7 @@ void ssh_destroy(ssh_ctx* h) {
     delete c.eng;
     c.eng = nullptr;
   }
+  ssh::tc_free(&c);
   for (ssh::DevBuf* b : {&c.s_hi, &c.s_lo, &c.rows, &c.slots, &c.blocks, &c.grows, &c.cols, &c.fsplit, &c.tab, &c.part,
                          &c.C_hi, &c.C_lo, &c.S_hi, &c.S_lo, &c.coef, &c.blk, &c.scal, &c.fpart, &c.F_hi, &c.F_lo})
     free_buf(*b);
@@ -121,6 +130,12 @@ ssh_status ssh_get_dims(const ssh_ctx* h, int* d, int64_t* N, int64_t* M, double
   if (N) *N = h->c.N;
   if (M) *M = h->c.M;
   if (L) *L = h->c.L;
+  return SSH_OK;
+}
+
+ssh_status ssh_get_fx_impl(const ssh_ctx* h, int* impl) {
+  if (!h || !impl) { set_error("ssh_get_fx_impl: NULL argument"); return SSH_EINVAL; }
+  *impl = h->c.tc.on ? SSH_FX_TENSOR : SSH_FX_INTEGER;
   return SSH_OK;
 }
 
@@ -256,7 +271,16 @@ ssh_status ssh_get_results(ssh_ctx* h, double phi[2], double smax[2], double* F_
     SSH_CUDA(cudaMemcpyAsync(hs, c.F_hi.p, sizeof(double) * d * N, cudaMemcpyDeviceToHost, c.stream), "download force");
     SSH_CUDA(cudaMemcpyAsync(ls, c.F_lo.p, sizeof(double) * d * N, cudaMemcpyDeviceToHost, c.stream), "download force");
   }
+  int tc_err = 0;
+  if (c.tc.on)
+    SSH_CUDA(cudaMemcpyAsync(&tc_err, c.tc.err.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "download status");
   SSH_CUDA(cudaStreamSynchronize(c.stream), "ssh_get_results");
+  if (tc_err != 0) {
+    // a bounded wait inside a tensor-core kernel gave up: the results of that evaluation are not valid
+    cudaMemsetAsync(c.tc.err.p, 0, sizeof(int), c.stream);
+    set_error("tensor-core kernel: a bounded wait gave up (status " + std::to_string(tc_err) + ")");
+    return SSH_ETIMEOUT;
+  }
   if (phi) { phi[0] = sc[ssh::kScPhiHi]; phi[1] = sc[ssh::kScPhiLo]; }
   if (smax) { smax[0] = sc[ssh::kScSmaxHi]; smax[1] = sc[ssh::kScSmaxLo]; }
   bool bad = !isfinite(sc[ssh::kScPhiHi]) || !isfinite(sc[ssh::kScSmaxHi]);

@@ -236,6 +236,7 @@ using ssh::set_error;
 
 struct ssh_batch {
   int device = 0;
+  int fx_impl = 0;  // members' ssh_opts.fx_impl (SSH_FX_TENSOR applies to d = 2 members)
   cudaStream_t stream = nullptr;
   std::vector<ssh_ctx*> members;
   std::vector<ssh_min_result> results;
@@ -250,6 +251,7 @@ ssh_status ssh_batch_create(const ssh_opts* opts, ssh_batch** out) {
   ssh_batch* b = new (std::nothrow) ssh_batch();
   if (!b) { set_error("ssh_batch_create: out of host memory"); return SSH_ENOMEM; }
   b->device = opts ? opts->device : 0;
+  b->fx_impl = opts ? opts->fx_impl : 0;
   cudaError_t e = cudaSetDevice(b->device);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) { delete b; return ssh::fail(e, "ssh_batch_create"); }
@@ -275,6 +277,7 @@ ssh_status ssh_batch_add(ssh_batch* b, int d, int64_t N, double L, double chi, d
   ssh_opts o;
   memset(&o, 0, sizeof o);
   o.device = b->device;
+  o.fx_impl = (b->fx_impl == SSH_FX_TENSOR && d != 2) ? SSH_FX_INTEGER : b->fx_impl;
   ssh_ctx* h = nullptr;
   ssh_status s = ssh_create(d, N, L, chi, K, &o, &h);
   if (s != SSH_OK) return s;
@@ -541,6 +544,7 @@ static void server_loop(ssh_server* sv) {
       ssh_opts o;
       memset(&o, 0, sizeof o);
       o.device = sv->o.device;
+      o.fx_impl = (sv->o.fx_impl == SSH_FX_TENSOR && q.d != 2) ? SSH_FX_INTEGER : sv->o.fx_impl;
       ssh_status s = ssh_create(q.d, q.N, q.L, q.chi, q.K, &o, &m.h);
       if (s == SSH_OK) s = ssh_set_stream(m.h, st);
       if (s == SSH_OK) s = ssh_set_positions_frac(m.h, q.s_hi.data(), q.s_lo.empty() ? nullptr : q.s_lo.data());

@@ -57,13 +57,15 @@ CfgDev make_cfgdev(const Ctx* c, bool fire_mode) {
   g.F_lo = (double*)c->F_lo.p;
   g.pref = c->pref;
   g.inv_L = c->inv_L;
+  tc_fill_cfgdev(c, &g);
   if (c->fire) fire_fill_cfgdev(c, &g);
   if (!fire_mode) g.run = nullptr;
   return g;
 }
 
 void engine_free(Engine* e) {
-  for (DevBuf* b : {&e->d_cfgs, &e->d_lists, &e->d_tw, &e->d_nt, &e->d_f, &e->d_counters}) {
+  for (DevBuf* b : {&e->d_cfgs, &e->d_lists, &e->d_tw, &e->d_nt, &e->d_f, &e->d_counters, &e->d_tclist, &e->d_tcprep,
+                    &e->d_tcdens, &e->d_tcforce}) {
     if (b->p) cudaFree(b->p);
     b->p = nullptr;
     b->bytes = 0;
@@ -123,6 +125,7 @@ cudaError_t engine_build(Engine* e, const std::vector<Ctx*>& members, const std:
     for (int i : lists[p]) {
       const Ctx* c = members[i];
       const CfgDev& g = e->host_cfgs[i];
+      if (p == SSH_FX && c->tc.on) continue;  // tensor-core members have their own work lists
       const int64_t total = (int64_t)g.nrows * g.Npad;
       for (int64_t s = 0; s < total; s += kTwThreads) e->h_tw.push_back({i, 0, s});
       for (int b = 0; b < (int)c->nt.blocks.size(); b++)
@@ -147,7 +150,22 @@ cudaError_t engine_build(Engine* e, const std::vector<Ctx*>& members, const std:
     nt_n[p] = (int)e->h_nt.size() - nt_off[p];
     f_n[p] = (int)e->h_f.size() - f_off[p];
   }
+  // tensor-core members (fixed point)
+  std::vector<int> tcl;
+  std::vector<TwItem> tcp;
+  std::vector<TcItem> tcd, tcf;
+  int64_t tc_grid = 0;
+  for (int i : lists[SSH_FX])
+    if (members[i]->tc.on) {
+      tcl.push_back(i);
+      tc_items(members[i], i, tcp, tcd, tcf);
+      tc_grid = std::max<int64_t>(tc_grid, (int64_t)(members[i]->tc.R1 + 1) * (members[i]->tc.R2 + 1));
+    }
   cudaError_t err;
+  if ((err = up(&e->d_tclist, tcl.data(), sizeof(int) * tcl.size(), st)) != cudaSuccess) return err;
+  if ((err = up(&e->d_tcprep, tcp.data(), sizeof(TwItem) * tcp.size(), st)) != cudaSuccess) return err;
+  if ((err = up(&e->d_tcdens, tcd.data(), sizeof(TcItem) * tcd.size(), st)) != cudaSuccess) return err;
+  if ((err = up(&e->d_tcforce, tcf.data(), sizeof(TcItem) * tcf.size(), st)) != cudaSuccess) return err;
   if ((err = up(&e->d_cfgs, e->host_cfgs.data(), sizeof(CfgDev) * n, st)) != cudaSuccess) return err;
   if ((err = up(&e->d_lists, e->h_lists.data(), sizeof(int) * e->h_lists.size(), st)) != cudaSuccess) return err;
   if ((err = up(&e->d_tw, e->h_tw.data(), sizeof(TwItem) * e->h_tw.size(), st)) != cudaSuccess) return err;
@@ -172,6 +190,17 @@ cudaError_t engine_build(Engine* e, const std::vector<Ctx*>& members, const std:
     v.nfi = f_n[p];
     v.counters = (int*)e->d_counters.p;
     v.sm_count = e->sm_count;
+    if (p == SSH_FX) {
+      v.tc_list = (const int*)e->d_tclist.p;
+      v.ntc_list = (int)tcl.size();
+      v.tc_prep = (const TwItem*)e->d_tcprep.p;
+      v.ntc_prep = (int)tcp.size();
+      v.tc_dens = (const TcItem*)e->d_tcdens.p;
+      v.ntc_dens = (int)tcd.size();
+      v.tc_force = (const TcItem*)e->d_tcforce.p;
+      v.ntc_force = (int)tcf.size();
+      v.tc_max_grid = tc_grid;
+    }
     for (int i : lists[p]) {
       const Ctx* c = members[i];
       v.nt_smem = std::max(v.nt_smem, c->launch[p].nt_smem);

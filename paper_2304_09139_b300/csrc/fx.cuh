@@ -175,6 +175,11 @@ struct fxc {
   q128 re, im;
 };
 
+// complex Q34.126 accumulator (one partial or final n~(k))
+struct FxAcc {
+  q160 re, im;
+};
+
 __device__ __forceinline__ fxc fxc_mul(const fxc& a, const fxc& b) {
   fxc z;
   z.re = q128_sub(mul126(a.re, b.re), mul126(a.im, b.im));

@@ -102,10 +102,6 @@ struct PolDD {
   }
 };
 
-struct FxAcc {
-  q160 re, im;
-};
-
 struct PolFX {
   using Tab = fxc;
   using Ph = fxc;
@@ -462,7 +458,7 @@ __global__ void __launch_bounds__(kRedThreads) k_finalize(const CfgDev* __restri
 template <class P>
 __global__ void k_coef(const CfgDev* __restrict__ cfgs, const int* __restrict__ list) {
   const CfgDev& c = cfgs[list[blockIdx.y]];
-  if (stopped(c)) return;
+  if (stopped(c) || (P::kIdx == SSH_FX && c.tc)) return;  // the tensor-core path builds its own coefficients
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= c.M) return;
   const int e = (int)c.scal[kScScaleExp];
@@ -657,7 +653,8 @@ __global__ void k_f_reduce(const CfgDev* __restrict__ cfgs, const int* __restric
   if (i >= nd) return;
   const typename P::RAcc* fpart = reinterpret_cast<const typename P::RAcc*>(c.fpart);
   typename P::RAcc s = fpart[i];
-  for (int k = 1; k < c.ksplit; k++) P::radd_r(s, fpart[(int64_t)k * nd + i]);
+  const int nsplit = (P::kIdx == SSH_FX && c.tc) ? c.tc_fsplit : c.ksplit;
+  for (int k = 1; k < nsplit; k++) P::radd_r(s, fpart[(int64_t)k * nd + i]);
   dd f = dd_mul(P::r_to_dd(s), c.pref);
   const int e = P::kIdx == SSH_FX ? (int)c.scal[kScScaleExp] : 0;
   c.F_hi[i] = ldexp(f.hi, e);
@@ -703,6 +700,10 @@ static cudaError_t launch_prec(const EngineView& v, bool want_force, cudaStream_
     k_twiddle<P><<<(unsigned)v.ntw, kTwThreads, 0, st>>>(v.cfgs, v.tw);
     prof_end(prof, st);
   }
+  if constexpr (P::kIdx == SSH_FX) {
+    cudaError_t te = tc_launch_density(v, st, prof);
+    if (te != cudaSuccess) return te;
+  }
   if (v.nnt > 0) {
     cudaMemsetAsync(v.counters, 0, sizeof(int), st);
     const int grid = std::min(v.nnt, 2 * v.sm_count);
@@ -725,6 +726,10 @@ static cudaError_t launch_prec(const EngineView& v, bool want_force, cudaStream_
     prof_begin(prof, st, kKCoef);
     k_coef<P><<<gc, 256, 0, st>>>(v.cfgs, v.list);
     prof_end(prof, st);
+    if constexpr (P::kIdx == SSH_FX) {
+      cudaError_t te = tc_launch_force(v, st, prof);
+      if (te != cudaSuccess) return te;
+    }
     if (v.nfi > 0) {
       cudaMemsetAsync(v.counters + 1, 0, sizeof(int), st);
       const int grid = std::min(v.nfi, 5 * v.sm_count);
@@ -851,7 +856,9 @@ cudaError_t plan_upload(Ctx* c) {
   c->n_red_blocks = (int)((c->M + kRedThreads - 1) / kRedThreads);
   if ((e = dev_alloc(&c->blk, (size_t)std::max(1, c->n_red_blocks) * sizeof(RedPart))) != cudaSuccess) return e;
   if ((e = dev_alloc(&c->scal, sizeof(double) * kScCount)) != cudaSuccess) return e;
-  if ((e = dev_alloc(&c->fpart, (size_t)ks * nd * kRAccBytes)) != cudaSuccess) return e;
+  if ((e = tc_setup(c)) != cudaSuccess) return e;
+  const int fslots = std::max(ks, c->tc.on ? 2 * c->tc.CTf : 1);
+  if ((e = dev_alloc(&c->fpart, (size_t)fslots * nd * kRAccBytes)) != cudaSuccess) return e;
   if ((e = dev_alloc(&c->F_hi, nd * 8)) != cudaSuccess) return e;
   if ((e = dev_alloc(&c->F_lo, nd * 8)) != cudaSuccess) return e;
   cudaMemsetAsync(c->scal.p, 0, sizeof(double) * kScCount, st);
@@ -877,6 +884,8 @@ size_t device_footprint(const Ctx& c) {
   b += nd * 8 * (4 + 6);                                       // positions, force, velocity, undo copies
   b += c.nt.slots.size() * sizeof(NtSlot) + c.nt.g_rows.size() * 4 + c.fp.cols.size() * sizeof(FCol);
   b += c.tl.rows.size() * sizeof(TabRow) + 64 * 1024;          // small buffers and allocation granularity
+  b += tc_footprint(c);                                        // tensor-core digit slices and partials
+  if (c.tc.on) b += (size_t)2 * c.tc.CTf * nd * kRAccBytes;
   return b;
 }
 

@@ -20,6 +20,14 @@ constexpr int kForceThreads = 128;
 
 struct FireBufs;  // fire.cu
 
+// work item of the tensor-core GEMM (tc.cu): one CTA
+struct TcItem {
+  int32_t cfg, kind;    // kind 0: density tile, 1: force tile
+  int32_t a, b;         // row tile (density) / particle tile (force); column tile
+  int32_t ks0, nks;     // K-step range
+  int32_t slot, pad;    // density: partial slot (tile * ksplit + split)
+};
+
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -73,6 +81,15 @@ struct CfgDev {
   void* fpart;
   double *F_hi, *F_lo;
   dd pref, inv_L;
+  // tensor-core fixed-point path (tc.cu); tc = 0 when the configuration uses the integer-pipe kernels
+  int tc, tc_R1, tc_R2, tc_RT, tc_CTd, tc_PT, tc_KSf, tc_CTf, tc_bexp, tc_ksplit, tc_fsplit, tc_gs, tc_ts;
+  int64_t tc_KS;
+  uint8_t *tc_dA, *tc_dB, *tc_fA, *tc_fB;
+  void* tc_a1;
+  long long* tc_part;
+  const int32_t* tc_kmap;
+  const int32_t* tc_tilemap;
+  int* tc_err;
   // minimiser state (null when the context has not minimised yet)
   void* fs;
   double *v_hi, *v_lo, *bs_hi, *bs_lo, *bF_hi, *bF_lo, *fdots;
@@ -108,6 +125,16 @@ struct EngineView {
   int maxblk = 0;
   int* counters = nullptr;  // two ints: density queue, force queue
   int sm_count = 148;
+  // tensor-core members (fixed point only)
+  const int* tc_list = nullptr;
+  int ntc_list = 0;
+  const TwItem* tc_prep = nullptr;
+  int ntc_prep = 0;
+  const TcItem* tc_dens = nullptr;
+  int ntc_dens = 0;
+  const TcItem* tc_force = nullptr;
+  int ntc_force = 0;
+  int64_t tc_max_grid = 0;  // largest (R1 + 1) (R2 + 1) of the members
 };
 
 struct Ctx;
@@ -139,7 +166,7 @@ struct Engine {
   std::vector<int> prec_of;  // current precision per member; -1 = listed under every precision
   bool fire_mode = false;
   std::vector<CfgDev> host_cfgs;
-  DevBuf d_cfgs, d_lists, d_all, d_tw, d_nt, d_f, d_counters;
+  DevBuf d_cfgs, d_lists, d_all, d_tw, d_nt, d_f, d_counters, d_tclist, d_tcprep, d_tcdens, d_tcforce;
   EngineView view[3];
   std::vector<int> h_lists;
   std::vector<TwItem> h_tw;
@@ -149,6 +176,22 @@ struct Engine {
   int nall = 0;
   int64_t maxND_all = 0;
   int max_nb_fire = 0;
+};
+
+// tile plan and buffers of the tensor-core path of one configuration (tc.cu)
+struct TcPlan {
+  bool on = false;
+  int R1 = 0, R2 = 0;            // n1 in [0, R1], |n2| <= R2
+  int64_t KS = 0;                // density K-steps (16 particles each)
+  int RT = 0, CTd = 0;           // density row tiles (128 rows (n1, cos/sin)), column tiles (32 columns (m, cos/sin))
+  int PT = 0, KSf = 0, CTf = 0;  // force particle tiles, K-steps, column tiles (8 values of n1 each)
+  int bexp = 0;                  // 2^bexp > R2: scale of the n2-weighted force coefficients
+  int ksplit = 1;                // K ranges per density tile
+  int gs = 0, ts = 0;            // force epilogue scales
+  std::vector<int32_t> tiles;    // density tiles in use: rt * CTd + ct
+  std::vector<int32_t> tilemap;  // [RT * CTd] -> index into tiles, or -1
+  std::vector<int32_t> kmap;     // [(R1 + 1) (2 R2 + 1)] internal index of (n1, n2), or -1
+  DevBuf dA, dB, fA, fB, a1, part, kmap_d, tilemap_d, err;
 };
 
 struct Ctx {
@@ -186,6 +229,8 @@ struct Ctx {
   dd inv_L;                       // 1 / L
   FireBufs* fire = nullptr;       // minimiser state, allocated on first ssh_minimize
   Engine* eng = nullptr;          // this context alone (plain evaluations)
+  bool tc_requested = false;      // fixed point on the tensor cores (d = 2)
+  TcPlan tc;
 };
 
 // record an event pair around a launch when profiling is on
@@ -212,6 +257,16 @@ cudaError_t fire_stage_init_engine(const Engine* e, const std::vector<int>& idx,
 
 // device scalar block written by k_finalize (doubles)
 enum { kScPhiHi = 0, kScPhiLo, kScSmaxHi, kScSmaxLo, kScCmax, kScScaleExp, kScA2MaxHi, kScA2MaxLo, kScCount = 16 };
+
+// tc.cu (tensor-core fixed-point path, d = 2)
+bool tc_eligible(const Ctx& c);
+cudaError_t tc_setup(Ctx* c);
+void tc_free(Ctx* c);
+size_t tc_footprint(const Ctx& c);
+void tc_fill_cfgdev(const Ctx* c, CfgDev* g);
+void tc_items(const Ctx* c, int i, std::vector<TwItem>& prep, std::vector<TcItem>& dens, std::vector<TcItem>& force);
+cudaError_t tc_launch_density(const EngineView& v, cudaStream_t st, Prof* prof);
+cudaError_t tc_launch_force(const EngineView& v, cudaStream_t st, Prof* prof);
 
 // kernels.cu
 cudaError_t plan_upload(Ctx* c);

@@ -1,0 +1,687 @@
+// tc.cu -- the fixed-point hot path for d = 2 on the tensor cores (Eqs. ntilde and force of arXiv:2304.09139).
+//
+// With a_j(n1) = e^{2 pi i n1 s_j1} and b_j(n2) = e^{2 pi i n2 s_j2}, the collective density factorises per
+// axis, n~(n1, n2) = sum_j a_j(n1) b_j(n2): a matrix product over the particles.  Since b_j(-m) = conj(b_j(m)),
+// the four real products P_pq(n1, m) = sum_j p_j(n1) q_j(m) (p the cos / sin of axis 1, q of axis 2, m >= 0)
+// give both n~(n1, m) = (P_cc - P_ss) + i (P_cs + P_sc) and n~(n1, -m) = (P_cc + P_ss) + i (P_sc - P_cs):
+// one real GEMM with rows (n1, p), columns (m, q) and K = particles.
+//
+// The force F_j = (4 pi / L) sum_k n [C sin th - S cos th] = (4 pi / L) Im sum_k n W_k a_j(n1) b_j(n2), with
+// W = C - i S, is grouped per n1: G_j(n1) = sum_n2 W b_j(n2) = sum_{m >= 0} [U(n1, m) cos(2 pi m s_j2) +
+// V(n1, m) sin(2 pi m s_j2)], U = W(n1, m) + W(n1, -m), V = i (W(n1, m) - W(n1, -m)) (m = 0: U = W(n1, 0),
+// V = 0), and likewise G' with the weight n2.  Rows = particles, K = (m, cos / sin), columns = (n1, Re G,
+// Im G, Re G', Im G'); the epilogue forms F_j1 = (4 pi / L) Im sum n1 a_j(n1) G_j(n1) and F_j2 = (4 pi / L)
+// Im sum a_j(n1) G'_j(n1).
+//
+// Both products use the exact digit arithmetic of tc.cuh: operands are 15 bf16 digit slices, the 120 kept
+// digit pairs accumulate into 15 TMEM level accumulators, read out exactly every 64 products.
+//
+// Kernels (one launch each per evaluation, over every tensor-core member of the engine):
+//   k_tc_prep         per particle: powers e^{2 pi i m s} of both axes (an exact-phase anchor every 16 powers,
+//                     one multiply per power in between), written as digit slices in the tile layouts of the
+//                     two GEMMs, and a_j(n1) as Q2.126 for the force epilogue
+//   k_tc_gemm         warp-specialised tcgen05 GEMM: one producer thread (bulk async copies, two stages), one
+//                     MMA thread (22 MMAs per K-step), eight epilogue warps (level read-out, exact folding)
+//   k_tc_dens_finish  fixed-order sum over K ranges, the four real products -> n~(n1, +-m) as Q34.126 partials
+//   k_tc_coef         U, V, U', V' from the exact n~ and the power-of-two scale, as digit slices of the force GEMM
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "fx.cuh"
+#include "ssh_internal.h"
+#include "tc.cuh"
+
+#define SSH_TABLE_QUAL __device__
+#include "gen/tables.h"
+
+namespace ssh {
+
+using namespace tc;
+
+namespace {
+
+constexpr int kEpiWarps = 8;
+constexpr int kGemmThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
+constexpr long long kWaitLimit = 2000000000LL;     // clock cycles (about one second) for any single wait
+constexpr size_t kGemmSmem = (size_t)kStages * kStageBytes;
+
+__device__ __forceinline__ bool stopped(const CfgDev& c) { return c.run && *c.run; }
+
+__device__ __forceinline__ __int128 q128_to_i128(const q128& a) {
+  return (__int128)(((unsigned __int128)a.w[3] << 96) | ((unsigned __int128)a.w[2] << 64) |
+                    ((unsigned __int128)a.w[1] << 32) | (unsigned __int128)a.w[0]);
+}
+
+// e^{2 pi i t} of an unsigned Q0.128 turn, Q2.126
+__device__ __forceinline__ fxc phasor_turn(const q128& t) {
+  q128 piq;
+#pragma unroll
+  for (int i = 0; i < 4; i++) piq.w[i] = SSH_FX_PI_Q3_125[i];
+  return fx_sincos_turns(t, SSH_FX_TAB_A, SSH_FX_TAB_B, piq, SSH_FX_INV_FACT);
+}
+
+// (t * m) mod 1 for an unsigned Q0.128 turn: exact
+__device__ __forceinline__ q128 turn_times(const q128& t, int m) {
+  const unsigned __int128 u = (unsigned __int128)q128_to_i128(t);
+  return q128_from_i128((__int128)(u * (unsigned __int128)(unsigned)m));
+}
+
+// 64 * (128^14 - 1) / 127: the offset that turns balanced digits d_0..d_13 into ordinary base-128 digits
+__device__ __forceinline__ __int128 digit_bias() {
+  __int128 b = 0;
+#pragma unroll
+  for (int i = 0; i < 14; i++) b |= (__int128)64 << (7 * i);
+  return b;
+}
+
+// The 15 balanced digits of X (|X| <= 2^104) as bf16, slice s holding digit 14 - s (top digit first).
+__device__ __forceinline__ void put_digits_x(uint8_t* base, uint32_t slice_stride, uint32_t off, __int128 X) {
+  const __int128 Y = X + digit_bias();
+#pragma unroll
+  for (int s = 0; s < kDigits; s++) {
+    const int i = kDigits - 1 - s;
+    const int d = i == kDigits - 1 ? (int)(Y >> 98) : (int)((Y >> (7 * i)) & 127) - 64;
+    *reinterpret_cast<uint16_t*>(base + (size_t)s * slice_stride + off) =
+        __bfloat16_as_ushort(__float2bfloat16_rn((float)d));
+  }
+}
+
+// digits of a Q2.126 value in [-1, 1]: X = round(x 2^104)
+__device__ __forceinline__ void put_digits_q126(uint8_t* base, uint32_t slice_stride, uint32_t off, const q128& w) {
+  const __int128 v = q128_to_i128(w);
+  put_digits_x(base, slice_stride, off, (v + ((__int128)1 << 21)) >> 22);
+}
+
+// 192-bit two's-complement accumulator
+struct i192 {
+  unsigned long long w[3];
+};
+__device__ __forceinline__ void i192_zero(i192& a) { a.w[0] = a.w[1] = a.w[2] = 0ull; }
+// a += v << sh (0 <= sh < 128)
+__device__ __forceinline__ void i192_add_shl(i192& a, __int128 v, int sh) {
+  const unsigned __int128 lo = (unsigned __int128)v << sh;
+  const unsigned long long top =
+      sh == 0 ? (v < 0 ? ~0ull : 0ull) : (unsigned long long)(v >> (128 - sh));  // bits 128..191 of v << sh
+  const unsigned __int128 a01 = ((unsigned __int128)a.w[1] << 64) | a.w[0];
+  const unsigned __int128 s01 = a01 + lo;
+  const unsigned long long carry = s01 < a01 ? 1ull : 0ull;
+  a.w[0] = (unsigned long long)s01;
+  a.w[1] = (unsigned long long)(s01 >> 64);
+  a.w[2] = a.w[2] + top + carry;
+}
+// the low 160 bits of a << sh (0 <= sh < 64) as a Q34.126 accumulator
+__device__ __forceinline__ q160 i192_to_q160_shl(const i192& a, int sh) {
+  unsigned long long w0 = a.w[0], w1 = a.w[1], w2 = a.w[2];
+  if (sh > 0) {
+    w2 = (w2 << sh) | (w1 >> (64 - sh));
+    w1 = (w1 << sh) | (w0 >> (64 - sh));
+    w0 <<= sh;
+  }
+  q160 r;
+  r.w[0] = (uint32_t)w0;
+  r.w[1] = (uint32_t)(w0 >> 32);
+  r.w[2] = (uint32_t)w1;
+  r.w[3] = (uint32_t)(w1 >> 32);
+  r.w[4] = (uint32_t)w2;
+  return r;
+}
+
+// round(a / 2^sh) of a Q34.126 accumulator, for results with |.| <= 2^104; sh may be negative (left shift)
+__device__ __forceinline__ __int128 q160_shr_round(const q160& a, int sh) {
+  i192 t;  // the 160-bit value sign-extended to 192 bits
+  t.w[0] = ((unsigned long long)a.w[1] << 32) | a.w[0];
+  t.w[1] = ((unsigned long long)a.w[3] << 32) | a.w[2];
+  t.w[2] = (unsigned long long)(long long)(int32_t)a.w[4];
+  if (sh <= 0) return (__int128)((((unsigned __int128)t.w[1] << 64) | t.w[0]) << (-sh));
+  i192_add_shl(t, (__int128)1, sh - 1);  // round half up
+  if (sh >= 64)  // bits sh .. sh + 127, arithmetic
+    return (__int128)(((unsigned __int128)t.w[2] << 64) | t.w[1]) >> (sh - 64);
+  const unsigned __int128 lo = ((unsigned __int128)t.w[1] << 64) | t.w[0];
+  return (__int128)((lo >> sh) | ((unsigned __int128)t.w[2] << (128 - sh)));
+}
+
+__device__ __forceinline__ q160 load_q160(const void* p) {
+  const uint32_t* u = reinterpret_cast<const uint32_t*>(p);
+  q160 r;
+#pragma unroll
+  for (int i = 0; i < 5; i++) r.w[i] = u[i];
+  return r;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------ k_tc_prep
+
+// Thread per (particle j, axis, block of 16 powers).  Items: TwItem {cfg, start} over
+// (nb1 + nb2) * N threads per configuration, 128 per item.
+__global__ void __launch_bounds__(kTwThreads) k_tc_prep(const CfgDev* __restrict__ cfgs, const TwItem* __restrict__ items) {
+  const TwItem it = items[blockIdx.x];
+  const CfgDev& c = cfgs[it.cfg];
+  if (stopped(c)) return;
+  const int64_t N = c.N;
+  const int nb1 = c.tc_R1 / 16 + 1, nb2 = c.tc_R2 / 16 + 1;
+  const int64_t idx = it.start + threadIdx.x;
+  if (idx >= (int64_t)(nb1 + nb2) * N) return;
+  const int64_t j = idx % N;
+  const int blk = (int)(idx / N);
+  const int axis = blk < nb1 ? 0 : 1;
+  const int b = axis == 0 ? blk : blk - nb1;
+  const int R = axis == 0 ? c.tc_R1 : c.tc_R2;
+  const q128 u = turns_from_dd(c.s_hi[axis * N + j], c.s_lo[axis * N + j]);
+  const fxc e1 = phasor_turn(u);
+  fxc z = phasor_turn(turn_times(u, 16 * b));
+  const int64_t ks = j >> 4;
+  const int kk = (int)(j & 15);
+  for (int i = 0; i < 16; i++) {
+    const int m = 16 * b + i;
+    if (m > R) break;
+    if (i > 0) z = fxc_mul(z, e1);
+    if (axis == 0) {
+      reinterpret_cast<fxc*>(c.tc_a1)[(int64_t)m * N + j] = z;
+#pragma unroll
+      for (int p = 0; p < 2; p++) {
+        const int r = 2 * m + p;
+        uint8_t* base = c.tc_dA + ((int64_t)(r >> 7) * c.tc_KS + ks) * kStageA;
+        put_digits_q126(base, kSliceA, slice_off(r & 127, kk), p == 0 ? z.re : z.im);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 2; q++) {
+        const int col = 2 * m + q;
+        uint8_t* bd = c.tc_dB + ((int64_t)(col >> 5) * c.tc_KS + ks) * kStageB;
+        put_digits_q126(bd, kSliceB, slice_off(col & 31, kk), q == 0 ? z.re : z.im);
+        uint8_t* bf = c.tc_fA + ((int64_t)(j >> 7) * c.tc_KSf + (col >> 4)) * kStageA;
+        put_digits_q126(bf, kSliceA, slice_off((int)(j & 127), col & 15), q == 0 ? z.re : z.im);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------ k_tc_gemm
+
+// One CTA per item.  Density items: A = density row tile it.a, B = column tile it.b, K-steps [ks0, ks0 + nks);
+// the epilogue stores the three int64 level groups of every output into tc_part slot it.slot.  Force items:
+// A = particle tile it.a, B = column tile it.b (8 values of n1), every K-step; the epilogue writes force
+// partials fpart[2 it.b + half][axis][j].
+__global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __restrict__ cfgs,
+                                                              const TcItem* __restrict__ items) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ uint64_t bar_full[kStages], bar_empty[kStages], bar_acc_full, bar_acc_empty, bar_drain;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+  const TcItem it = items[blockIdx.x];
+  const CfgDev& c = cfgs[it.cfg];
+  if (stopped(c)) return;  // uniform over the CTA, before any barrier or allocation
+  int* err = c.tc_err;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint8_t* gA;
+  const uint8_t* gB;
+  if (it.kind == 0) {
+    gA = c.tc_dA + ((int64_t)it.a * c.tc_KS + it.ks0) * kStageA;
+    gB = c.tc_dB + ((int64_t)it.b * c.tc_KS + it.ks0) * kStageB;
+  } else {
+    gA = c.tc_fA + ((int64_t)it.a * c.tc_KSf + it.ks0) * kStageA;
+    gB = c.tc_fB + ((int64_t)it.b * c.tc_KSf + it.ks0) * kStageB;
+  }
+  const int nks = it.nks;
+  const int nch = (nks + kChunkSteps - 1) / kChunkSteps;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; s++) {
+      mbar_init(&bar_full[s], 1);
+      mbar_init(&bar_empty[s], 1);
+    }
+    mbar_init(&bar_acc_full, 1);
+    mbar_init(&bar_acc_empty, kEpiWarps);
+    mbar_init(&bar_drain, 1);
+    abort_sh = 0;
+    mbar_fence_init();
+  }
+  if (warp == 1) tmem_alloc(&tmem_base_sh, kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = tmem_base_sh;
+  volatile int* abort_flag = &abort_sh;
+
+  if (warp == 0) {
+    // ---- producer: one thread streams the K-steps through the stages
+    if (lane == 0) {
+      int issued = 0;
+      for (int ks = 0; ks < nks; ks++) {
+        const int s = ks % kStages, use = ks / kStages;
+        if (use > 0 && !mbar_wait(&bar_empty[s], (use - 1) & 1, kWaitLimit, abort_flag)) {
+          *abort_flag = 1;
+          atomicOr(err, 1);
+          break;
+        }
+        uint8_t* dst = smem + (size_t)s * kStageBytes;
+        mbar_expect_tx(&bar_full[s], kStageBytes);
+        bulk_g2s(dst, gA + (size_t)ks * kStageA, kStageA, &bar_full[s]);
+        bulk_g2s(dst + kStageA, gB + (size_t)ks * kStageB, kStageB, &bar_full[s]);
+        issued = ks + 1;
+      }
+      if (*abort_flag) {
+        // let the copies in flight land before the CTA can exit
+        for (int ks = issued > kStages ? issued - kStages : 0; ks < issued; ks++)
+          mbar_wait(&bar_full[ks % kStages], (ks / kStages) & 1, kWaitLimit, nullptr);
+      }
+    }
+  } else if (warp == 1) {
+    // ---- MMA issuer: 22 MMAs per K-step; level u of the accumulator receives digit slice pairs (s, u - s)
+    if (lane == 0) {
+      for (int ks = 0; ks < nks; ks++) {
+        const int s = ks % kStages, use = ks / kStages;
+        const int ch = ks / kChunkSteps;
+        const bool first = ks % kChunkSteps == 0;
+        const bool last = ks % kChunkSteps == kChunkSteps - 1 || ks == nks - 1;
+        if (!mbar_wait(&bar_full[s], use & 1, kWaitLimit, abort_flag)) {
+          *abort_flag = 1;
+          atomicOr(err, 2);
+          break;
+        }
+        if (first && ch > 0 && !mbar_wait(&bar_acc_empty, (ch - 1) & 1, kWaitLimit, abort_flag)) {
+          *abort_flag = 1;
+          atomicOr(err, 4);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(smem + (size_t)s * kStageBytes);
+        const uint32_t b0 = a0 + kStageA;
+#pragma unroll
+        for (int sl = 0; sl < kDigits; sl++) {
+          const int ntot = (kLevels - sl) * kTileN;
+          const int n1 = ntot < 256 ? ntot : 256;
+          const uint32_t acc = (first && sl == 0) ? 0u : 1u;
+          const uint64_t ad = make_sdesc(a0 + sl * kSliceA);
+          mma_bf16(tbase + sl * kTileN, ad, make_sdesc(b0), make_idesc(kTileM, n1), acc);
+          if (ntot > 256) mma_bf16(tbase + sl * kTileN + 256, ad, make_sdesc(b0 + 256 * 32), make_idesc(kTileM, ntot - 256), acc);
+        }
+        mma_commit(&bar_empty[s]);
+        if (last) mma_commit(&bar_acc_full);
+      }
+      // every MMA issued by this thread has completed once the drain barrier flips
+      mma_commit(&bar_drain);
+      if (!mbar_wait(&bar_drain, 0, kWaitLimit, nullptr)) atomicOr(err, 8);
+    }
+  } else {
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 and accumulator columns 16 h .. 16 h + 15
+    const int q = warp & 3, h = (warp - 2) >> 2;
+    long long st[3][16];
+#pragma unroll
+    for (int g = 0; g < 3; g++)
+#pragma unroll
+      for (int i = 0; i < 16; i++) st[g][i] = 0;
+    bool ok = true;
+    for (int ch = 0; ch < nch; ch++) {
+      // the warp leaves together (tcgen05.ld is warp-collective)
+      const bool got = mbar_wait(&bar_acc_full, ch & 1, kWaitLimit, abort_flag);
+      if (!__all_sync(0xffffffffu, got)) {
+        *abort_flag = 1;
+        if (lane == 0) atomicOr(err, 16);
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t trow = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * h);
+#pragma unroll
+      for (int g = 0; g < 3; g++) {
+        long long t[16];
+#pragma unroll
+        for (int i = 0; i < 16; i++) t[i] = 0;
+#pragma unroll
+        for (int l = 0; l < 5; l++) {
+          uint32_t r[16];
+          tmem_ld16(trow + (uint32_t)((5 * g + l) * kTileN), r);
+          tmem_ld_wait();
+#pragma unroll
+          for (int i = 0; i < 16; i++) t[i] += (long long)acc_int(r[i]) * (1ll << (7 * (4 - l)));
+        }
+#pragma unroll
+        for (int i = 0; i < 16; i++) st[g][i] += t[i];
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar_acc_empty);
+    }
+    if (ok) {
+      const int row = 32 * q + lane;
+      if (it.kind == 0) {
+        // level groups of every output: R' = st0 2^70 + st1 2^35 + st2 (value = R' 2^-110)
+        long long* out = c.tc_part + (size_t)it.slot * (3 * kTileN * kTileM);
+#pragma unroll
+        for (int g = 0; g < 3; g++)
+#pragma unroll
+          for (int i = 0; i < 16; i++) out[((size_t)g * kTileN + 16 * h + i) * kTileM + row] = st[g][i];
+      } else {
+        const int64_t j = (int64_t)it.a * kTileM + row;
+        if (j < c.N) {
+          // four n1 values per half tile, columns (Re G, Im G, Re G', Im G') each.  G~ = R' 2^-110 is taken
+          // as R' 2^gs (|.| < 2^126); the top halves of a * G are value 2^(108 + gs), shifted to value 2^ts.
+          const int gs = c.tc_gs, tsh = 108 + c.tc_gs - c.tc_ts;
+          __int128 F1 = 0, F2 = 0;  // value 2^ts
+#pragma unroll
+          for (int v = 0; v < 4; v++) {
+            const int n1 = it.b * 8 + h * 4 + v;
+            if (n1 > c.tc_R1) continue;
+            q128 gcol[4];
+#pragma unroll
+            for (int g4 = 0; g4 < 4; g4++) {
+              const int i = 4 * v + g4;
+              const __int128 R = ((__int128)st[0][i] << 70) + ((__int128)st[1][i] << 35) + (__int128)st[2][i];
+              gcol[g4] = q128_from_i128(R << gs);
+            }
+            const fxc a = reinterpret_cast<const fxc*>(c.tc_a1)[(int64_t)n1 * c.N + j];
+            uint32_t p[5], r2[5];
+            // Im(a G) = Re a Im G + Im a Re G
+            smul_top(a.re, gcol[1], p);
+            smul_top(a.im, gcol[0], r2);
+            __int128 T = (q128_to_i128(q128{{p[1], p[2], p[3], p[4]}}) + q128_to_i128(q128{{r2[1], r2[2], r2[3], r2[4]}})) >> tsh;
+            F1 += T * (__int128)n1;
+            smul_top(a.re, gcol[3], p);
+            smul_top(a.im, gcol[2], r2);
+            T = (q128_to_i128(q128{{p[1], p[2], p[3], p[4]}}) + q128_to_i128(q128{{r2[1], r2[2], r2[3], r2[4]}})) >> tsh;
+            F2 += T;
+          }
+          q160* fpart = reinterpret_cast<q160*>(c.fpart);
+          const int slot = 2 * it.b + h;
+          i192 a1, a2;
+          i192_zero(a1);
+          i192_zero(a2);
+          i192_add_shl(a1, F1, 126 - c.tc_ts);                // Q34.126, in units of 2^e
+          i192_add_shl(a2, F2, 126 - c.tc_ts + c.tc_bexp);    // G' was scaled by 2^-(e + bexp)
+          fpart[((int64_t)slot * 2 + 0) * c.N + j] = i192_to_q160_shl(a1, 0);
+          fpart[((int64_t)slot * 2 + 1) * c.N + j] = i192_to_q160_shl(a2, 0);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tbase, kTmemCols);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------ finish
+
+// grid ((R1 + 1) (R2 + 1) / 128 blocks, tensor-core members): n~(n1, m), n~(n1, -m) from the four real products
+__global__ void k_tc_dens_finish(const CfgDev* __restrict__ cfgs, const int* __restrict__ list) {
+  const CfgDev& c = cfgs[list[blockIdx.y]];
+  if (stopped(c)) return;
+  const int W2 = c.tc_R2 + 1;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)(c.tc_R1 + 1) * W2) return;
+  const int n1 = (int)(idx / W2), m = (int)(idx % W2);
+  const int span = 2 * c.tc_R2 + 1;
+  const int kp = c.tc_kmap[(int64_t)n1 * span + (c.tc_R2 + m)];
+  const int km = m > 0 ? c.tc_kmap[(int64_t)n1 * span + (c.tc_R2 - m)] : -1;
+  if (kp < 0 && km < 0) return;
+  const int r = 2 * n1, col = 2 * m;
+  const int ti = c.tc_tilemap[(r >> 7) * c.tc_CTd + (col >> 5)];
+  if (ti < 0) return;
+  const int rr = r & 127, cc = col & 31;
+  // group sums of P_pq over the K ranges, fixed order
+  __int128 Pg[4][3];
+#pragma unroll
+  for (int x = 0; x < 4; x++)
+#pragma unroll
+    for (int g = 0; g < 3; g++) Pg[x][g] = 0;
+  for (int sp = 0; sp < c.tc_ksplit; sp++) {
+    const long long* src = c.tc_part + (size_t)(ti * c.tc_ksplit + sp) * (3 * kTileN * kTileM);
+#pragma unroll
+    for (int p = 0; p < 2; p++)
+#pragma unroll
+      for (int qq = 0; qq < 2; qq++)
+#pragma unroll
+        for (int g = 0; g < 3; g++) Pg[2 * p + qq][g] += src[((size_t)g * kTileN + cc + qq) * kTileM + rr + p];
+  }
+  // P index: 0 = cc, 1 = cs, 2 = sc, 3 = ss
+  FxAcc* part = reinterpret_cast<FxAcc*>(c.part);
+  // C = P_cc + ss_sign P_ss, S = cs_sign P_cs + P_sc
+  auto emit = [&](int k, int ss_sign, int cs_sign) {
+    i192 C, S;
+    i192_zero(C);
+    i192_zero(S);
+#pragma unroll
+    for (int g = 0; g < 3; g++) {
+      const int sh = 70 - 35 * g;
+      i192_add_shl(C, Pg[0][g] + (ss_sign > 0 ? Pg[3][g] : -Pg[3][g]), sh);
+      i192_add_shl(S, (cs_sign > 0 ? Pg[1][g] : -Pg[1][g]) + Pg[2][g], sh);
+    }
+    FxAcc o;
+    o.re = i192_to_q160_shl(C, 16);  // value 2^-110 -> Q34.126
+    o.im = i192_to_q160_shl(S, 16);
+    part[k] = o;
+  };
+  if (kp >= 0) emit(kp, -1, +1);  // n~(n1, m) = (P_cc - P_ss) + i (P_cs + P_sc)
+  if (km >= 0) emit(km, +1, -1);  // n~(n1, -m) = (P_cc + P_ss) + i (P_sc - P_cs)
+}
+
+// grid ((R1 + 1) (R2 + 1) / 128 blocks, tensor-core members): the force GEMM's coefficient digits
+__global__ void k_tc_coef(const CfgDev* __restrict__ cfgs, const int* __restrict__ list) {
+  const CfgDev& c = cfgs[list[blockIdx.y]];
+  if (stopped(c)) return;
+  const int W2 = c.tc_R2 + 1;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)(c.tc_R1 + 1) * W2) return;
+  const int n1 = (int)(idx / W2), m = (int)(idx % W2);
+  const int span = 2 * c.tc_R2 + 1;
+  const int kp = c.tc_kmap[(int64_t)n1 * span + (c.tc_R2 + m)];
+  const int km = m > 0 ? c.tc_kmap[(int64_t)n1 * span + (c.tc_R2 - m)] : -1;
+  const FxAcc* part = reinterpret_cast<const FxAcc*>(c.part);
+  const q160 z = q160_zero();
+  const q160 Cp = kp >= 0 ? load_q160(&part[kp].re) : z, Sp = kp >= 0 ? load_q160(&part[kp].im) : z;
+  const q160 Cm = km >= 0 ? load_q160(&part[km].re) : z, Sm = km >= 0 ? load_q160(&part[km].im) : z;
+  const int e = (int)c.scal[kScScaleExp];
+  // W = C - i S:  Re U = C+ + C-,  Im U = -(S+ + S-),  Re V = S+ - S-,  Im V = C+ - C-
+  //               Re U' = m (C+ - C-), Im U' = -m (S+ - S-), Re V' = m (S+ + S-), Im V' = m (C+ + C-)
+  q160 cpl = Cp, cmi = Cp, spl = Sp, smi = Sp;
+  q160_add160(cpl, Cm);
+  cmi = q160_sub160(Cp, Cm);
+  q160_add160(spl, Sm);
+  smi = q160_sub160(Sp, Sm);
+  const int shG = 22 + e, shW = 22 + e + c.tc_bexp;
+  __int128 X[4][2];
+  X[0][0] = q160_shr_round(cpl, shG);
+  X[0][1] = q160_shr_round(smi, shG);
+  X[1][0] = -q160_shr_round(spl, shG);
+  X[1][1] = q160_shr_round(cmi, shG);
+  X[2][0] = q160_shr_round(q160_mul_int(cmi, m), shW);
+  X[2][1] = q160_shr_round(q160_mul_int(spl, m), shW);
+  X[3][0] = -q160_shr_round(q160_mul_int(smi, m), shW);
+  X[3][1] = q160_shr_round(q160_mul_int(cpl, m), shW);
+  if (m == 0) {  // sin(0) = 0 and the weight n2 = 0
+    X[0][1] = X[1][1] = 0;
+    X[2][0] = X[2][1] = X[3][0] = X[3][1] = 0;
+  }
+#pragma unroll
+  for (int g = 0; g < 4; g++) {
+    const int col = 4 * n1 + g;
+#pragma unroll
+    for (int qq = 0; qq < 2; qq++) {
+      const int kf = 2 * m + qq;
+      uint8_t* base = c.tc_fB + ((int64_t)(col >> 5) * c.tc_KSf + (kf >> 4)) * kStageB;
+      put_digits_x(base, kSliceB, slice_off(col & 31, kf & 15), X[g][qq]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------------ host side
+
+static cudaError_t tc_dev_alloc(DevBuf* b, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) bytes = 16;
+  b->bytes = bytes;
+  cudaError_t e = cudaMalloc(&b->p, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaMemsetAsync(b->p, 0, bytes, st);  // padding rows, columns and K stay zero for good
+}
+
+bool tc_eligible(const Ctx& c) { return c.d == 2 && c.N >= 1 && c.M >= 1; }
+
+// Tile plan and device buffers of one configuration.
+cudaError_t tc_setup(Ctx* c) {
+  TcPlan& t = c->tc;
+  t = TcPlan();
+  if (!c->tc_requested || !tc_eligible(*c)) return cudaSuccess;
+  const KSet& ks = c->ks;
+  t.R1 = std::max(0, ks.nmax[0]);
+  t.R2 = std::max(std::abs(ks.nmin[1]), std::abs(ks.nmax[1]));
+  t.KS = (c->N + kStepK - 1) / kStepK;
+  t.RT = (2 * (t.R1 + 1) + kTileM - 1) / kTileM;
+  t.CTd = (2 * (t.R2 + 1) + kTileN - 1) / kTileN;
+  t.PT = (int)((c->N + kTileM - 1) / kTileM);
+  t.KSf = (2 * (t.R2 + 1) + kStepK - 1) / kStepK;
+  t.CTf = (4 * (t.R1 + 1) + kTileN - 1) / kTileN;
+  t.bexp = 0;
+  while ((1 << t.bexp) <= t.R2) t.bexp++;
+  const int span = 2 * t.R2 + 1;
+  t.kmap.assign((size_t)(t.R1 + 1) * span, -1);
+  t.tilemap.assign((size_t)t.RT * t.CTd, -1);
+  for (int64_t k = 0; k < c->M; k++) {
+    const int n1 = ks.n_int[2 * k], n2 = ks.n_int[2 * k + 1];
+    t.kmap[(size_t)n1 * span + (n2 + t.R2)] = (int32_t)k;
+    const int ti = ((2 * n1) >> 7) * t.CTd + ((2 * std::abs(n2)) >> 5);
+    t.tilemap[ti] = 1;
+  }
+  t.tiles.clear();
+  for (int i = 0; i < t.RT * t.CTd; i++)
+    if (t.tilemap[i] >= 0) {
+      t.tilemap[i] = (int32_t)t.tiles.size();
+      t.tiles.push_back(i);
+    }
+  const int nt = (int)t.tiles.size();
+  const int64_t max_split = std::max<int64_t>(1, t.KS / kChunkSteps);
+  t.ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(max_split, (c->sm_count + nt - 1) / std::max(1, nt)));
+  // each K range holds at most 4096 read-outs, so the int64 level groups (below 2^50.1 per read-out) cannot overflow
+  t.ksplit = (int)std::max<int64_t>(t.ksplit, (t.KS + 4096 * kChunkSteps - 1) / (4096 * kChunkSteps));
+  cudaStream_t st = c->stream;
+  cudaError_t e;
+  if ((e = tc_dev_alloc(&t.dA, (size_t)t.RT * t.KS * kStageA, st)) != cudaSuccess) return e;
+  if ((e = tc_dev_alloc(&t.dB, (size_t)t.CTd * t.KS * kStageB, st)) != cudaSuccess) return e;
+  if ((e = tc_dev_alloc(&t.fA, (size_t)t.PT * t.KSf * kStageA, st)) != cudaSuccess) return e;
+  if ((e = tc_dev_alloc(&t.fB, (size_t)t.CTf * t.KSf * kStageB, st)) != cudaSuccess) return e;
+  if ((e = tc_dev_alloc(&t.a1, (size_t)(t.R1 + 1) * c->N * sizeof(fxc), st)) != cudaSuccess) return e;
+  if ((e = tc_dev_alloc(&t.part, (size_t)nt * t.ksplit * 3 * kTileN * kTileM * 8, st)) != cudaSuccess) return e;
+  if ((e = tc_dev_alloc(&t.kmap_d, t.kmap.size() * 4, st)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(t.kmap_d.p, t.kmap.data(), t.kmap.size() * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return e;
+  if ((e = tc_dev_alloc(&t.tilemap_d, t.tilemap.size() * 4, st)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(t.tilemap_d.p, t.tilemap.data(), t.tilemap.size() * 4, cudaMemcpyHostToDevice, st)) !=
+      cudaSuccess)
+    return e;
+  if ((e = tc_dev_alloc(&t.err, 16, st)) != cudaSuccess) return e;
+  // force epilogue scales: G~ (|.| <= 2 (R2 + 1)) held as R' 2^gs below 2^126; partial sums of four n1 terms
+  // weighted by n1 <= R1 held at value 2^ts below 2^126
+  int lg = 0;
+  while ((1ll << lg) < 2ll * (t.R2 + 1)) lg++;
+  t.gs = 16 - lg;
+  int lf = 0;
+  while ((1ll << lf) < 4ll * std::max(1, t.R1) * 2ll * (t.R2 + 1)) lf++;
+  t.ts = 126 - lf;
+  if (t.gs < 1 || t.ts < 64) return cudaErrorInvalidValue;  // wavevector range beyond the scales used here
+  t.on = true;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
+    attr = true;
+  }
+  return cudaGetLastError();
+}
+
+void tc_free(Ctx* c) {
+  TcPlan& t = c->tc;
+  for (DevBuf* b : {&t.dA, &t.dB, &t.fA, &t.fB, &t.a1, &t.part, &t.kmap_d, &t.tilemap_d, &t.err}) {
+    if (b->p) cudaFree(b->p);
+    b->p = nullptr;
+    b->bytes = 0;
+  }
+  t.on = false;
+}
+
+size_t tc_footprint(const Ctx& c) {
+  const TcPlan& t = c.tc;
+  if (!t.on) return 0;
+  return t.dA.bytes + t.dB.bytes + t.fA.bytes + t.fB.bytes + t.a1.bytes + t.part.bytes + t.kmap_d.bytes +
+         t.tilemap_d.bytes;
+}
+
+void tc_fill_cfgdev(const Ctx* c, CfgDev* g) {
+  const TcPlan& t = c->tc;
+  g->tc = t.on ? 1 : 0;
+  if (!t.on) return;
+  g->tc_R1 = t.R1;
+  g->tc_R2 = t.R2;
+  g->tc_RT = t.RT;
+  g->tc_CTd = t.CTd;
+  g->tc_PT = t.PT;
+  g->tc_KSf = t.KSf;
+  g->tc_CTf = t.CTf;
+  g->tc_bexp = t.bexp;
+  g->tc_ksplit = t.ksplit;
+  g->tc_fsplit = 2 * t.CTf;
+  g->tc_KS = t.KS;
+  g->tc_dA = (uint8_t*)t.dA.p;
+  g->tc_dB = (uint8_t*)t.dB.p;
+  g->tc_fA = (uint8_t*)t.fA.p;
+  g->tc_fB = (uint8_t*)t.fB.p;
+  g->tc_a1 = t.a1.p;
+  g->tc_part = (long long*)t.part.p;
+  g->tc_kmap = (const int32_t*)t.kmap_d.p;
+  g->tc_tilemap = (const int32_t*)t.tilemap_d.p;
+  g->tc_err = (int*)t.err.p;
+  g->tc_gs = t.gs;
+  g->tc_ts = t.ts;
+  g->psplit[SSH_FX] = 1;
+}
+
+// work items of one member (engine member index i)
+void tc_items(const Ctx* c, int i, std::vector<TwItem>& prep, std::vector<TcItem>& dens, std::vector<TcItem>& force) {
+  const TcPlan& t = c->tc;
+  const int64_t nprep = (int64_t)(t.R1 / 16 + 1 + t.R2 / 16 + 1) * c->N;
+  for (int64_t s = 0; s < nprep; s += kTwThreads) prep.push_back({i, 0, s});
+  for (int ti = 0; ti < (int)t.tiles.size(); ti++) {
+    const int rt = t.tiles[ti] / t.CTd, ct = t.tiles[ti] % t.CTd;
+    for (int sp = 0; sp < t.ksplit; sp++) {
+      const int64_t k0 = t.KS * sp / t.ksplit, k1 = t.KS * (sp + 1) / t.ksplit;
+      dens.push_back({i, 0, rt, ct, (int32_t)k0, (int32_t)(k1 - k0), ti * t.ksplit + sp, 0});
+    }
+  }
+  for (int pt = 0; pt < t.PT; pt++)
+    for (int ct = 0; ct < t.CTf; ct++) force.push_back({i, 1, pt, ct, 0, t.KSf, ct, 0});
+}
+
+size_t tc_gemm_smem() { return kGemmSmem; }
+
+cudaError_t tc_launch_density(const EngineView& v, cudaStream_t st, Prof* prof) {
+  if (v.ntc_list == 0) return cudaSuccess;
+  prof_begin(prof, st, kKTwiddle);
+  k_tc_prep<<<(unsigned)v.ntc_prep, kTwThreads, 0, st>>>(v.cfgs, v.tc_prep);
+  prof_end(prof, st);
+  prof_begin(prof, st, kKNtilde);
+  k_tc_gemm<<<(unsigned)v.ntc_dens, kGemmThreads, kGemmSmem, st>>>(v.cfgs, v.tc_dens);
+  prof_end(prof, st);
+  prof_begin(prof, st, kKNtReduce);
+  const dim3 g((unsigned)std::max<int64_t>(1, (v.tc_max_grid + 127) / 128), (unsigned)v.ntc_list);
+  k_tc_dens_finish<<<g, 128, 0, st>>>(v.cfgs, v.tc_list);
+  prof_end(prof, st);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_launch_force(const EngineView& v, cudaStream_t st, Prof* prof) {
+  if (v.ntc_list == 0) return cudaSuccess;
+  prof_begin(prof, st, kKCoef);
+  const dim3 g((unsigned)std::max<int64_t>(1, (v.tc_max_grid + 127) / 128), (unsigned)v.ntc_list);
+  k_tc_coef<<<g, 128, 0, st>>>(v.cfgs, v.tc_list);
+  prof_end(prof, st);
+  prof_begin(prof, st, kKForce);
+  k_tc_gemm<<<(unsigned)v.ntc_force, kGemmThreads, kGemmSmem, st>>>(v.cfgs, v.tc_force);
+  prof_end(prof, st);
+  return cudaGetLastError();
+}
+
+}  // namespace ssh

@@ -1,0 +1,136 @@
+// tc.cuh -- fifth-generation tensor-core primitives (sm_100 family: tcgen05, TMEM, bulk async copies,
+// mbarriers) in inline PTX, and the exact digit arithmetic the tensor-core path is built on.
+//
+// Exact products on bf16 tensor cores.  A value x in [-1, 1] is held as the integer X = round(x 2^104) and
+// written as 15 balanced base-128 digits, X = sum_i d_i 128^i with d_i in [-64, 63] (the top digit in
+// [-64, 64]).  Every digit is an integer of at most 7 bits, so it is exact in bf16, and a product of two
+// digits (|.| <= 2^12) is exact in the fp32 accumulator.  The product of two such values keeps the digit
+// pairs (i, k) with i + k >= 14: "level" u = 28 - i - k runs over 0..14 and holds u + 1 digit pairs whose
+// weight is 128^(28-u).  A level accumulator that has summed P products of each of its pairs satisfies
+// |V_u| <= 15 P 2^12; read out every 64 products it stays below 2^22, where fp32 holds integers exactly
+// and one FADD with 1.5 * 2^23 turns it into an integer.  The dropped pairs (i + k <= 13) contribute at most
+// 2^-101 of one unit product each, far below the 1e-28 normwise tolerance.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ssh {
+namespace tc {
+
+constexpr int kDigits = 15;         // balanced base-128 digits per value
+constexpr int kLevels = 15;         // kept levels (digit pairs with i + k >= 14)
+constexpr int kFracBits = 104;      // X = round(x 2^104)
+constexpr int kTileM = 128;         // accumulator rows (TMEM lanes)
+constexpr int kTileN = 32;          // accumulator columns per level
+constexpr int kStepK = 16;          // K per MMA instruction (bf16)
+constexpr int kChunkSteps = 4;      // K-steps between exact read-outs (64 products per pair)
+constexpr int kTmemCols = 512;      // kLevels * kTileN = 480 used
+constexpr uint32_t kSliceA = kTileM * kStepK * 2;   // 4096 bytes: one digit slice of one A K-step
+constexpr uint32_t kSliceB = kTileN * kStepK * 2;   // 1024 bytes: one digit slice of one B K-step
+constexpr uint32_t kStageA = kDigits * kSliceA;      // 61440
+constexpr uint32_t kStageB = kDigits * kSliceB;      // 15360
+constexpr uint32_t kStageBytes = kStageA + kStageB;  // 76800
+constexpr int kStages = 2;
+constexpr float kMagic = 12582912.0f;                // 1.5 * 2^23
+constexpr int32_t kMagicBits = 0x4B400000;
+
+// Byte offset of element (r, k) inside one K-major rows x 16 operand slice, no swizzle: 8x16-byte core
+// matrices, K-adjacent core matrices 128 bytes apart (LBO), 8-row groups 256 bytes apart (SBO).
+__host__ __device__ __forceinline__ uint32_t slice_off(int r, int k) {
+  return (uint32_t)((r >> 3) * 256 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start, LBO, SBO (bytes), version 1, no swizzle
+__device__ __forceinline__ uint64_t make_sdesc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
+         ((uint64_t)1 << 46);
+}
+
+// instruction descriptor, kind::f16: D f32, A and B bf16, both K-major, M x N
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of the given parity to complete.  Gives up (returns false) after `limit`
+// clock cycles, or as soon as *abort (when not null) is set by another thread of the CTA.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, long long limit, volatile int* abort) {
+  if (mbar_try(b, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (mbar_try(b, parity)) return true;
+    if (abort && *abort) return false;
+    if (clock64() - t0 > limit) return false;
+  }
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+}
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16), completion on the mbarrier
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+               "r"(ncols));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// D[tmem] (+)= A[sdesc] * B[sdesc]^T, issued by one thread
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
+}
+// arrive on the mbarrier when every tcgen05 operation issued so far by this thread has completed
+__device__ __forceinline__ void mma_commit(uint64_t* b) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(b))
+               : "memory");
+}
+
+// 16 consecutive accumulator columns of this warp's 32 TMEM lanes, one lane per thread
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// exact integer value of an fp32 accumulator word holding an integer of magnitude below 2^22
+__device__ __forceinline__ int32_t acc_int(uint32_t bits) {
+  return __float_as_int(__uint_as_float(bits) + kMagic) - kMagicBits;
+}
+
+}  // namespace tc
+}  // namespace ssh

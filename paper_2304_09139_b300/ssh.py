@@ -13,6 +13,7 @@ import threading
 import numpy as np
 
 FP64, DD, FX = 0, 1, 2
+FX_AUTO, FX_INTEGER, FX_TENSOR = 0, 1, 2   # ssh_opts.fx_impl
 PREC_NAMES = {FP64: "fp64", DD: "dd", FX: "fx"}
 KERNELS = ["twiddle", "ntilde", "nt_reduce", "finalize", "coef", "force", "f_reduce", "fire"]
 
@@ -51,7 +52,7 @@ class MinResult(ctypes.Structure):
 class ServerOpts(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("max_slots", ctypes.c_int), ("hbm_budget_bytes", ctypes.c_int64),
                 ("chunk_steps", ctypes.c_int64), ("max_pairs_per_step", ctypes.c_int64), ("policy", ctypes.c_int),
-                ("reserved", ctypes.c_int * 1)]
+                ("fx_impl", ctypes.c_int)]
 
 
 class Request(ctypes.Structure):
@@ -109,6 +110,7 @@ def load():
             _sig(lib, "ssh_destroy", None, [c_vp])
             _sig(lib, "ssh_get_dims", c_int, [c_vp, P(c_int), P(c_i64), P(c_i64), P(c_d)])
             _sig(lib, "ssh_get_kset", c_int, [c_vp, P(c_i64), P(c_i32)])
+            _sig(lib, "ssh_get_fx_impl", c_int, [c_vp, P(c_int)])
             _sig(lib, "ssh_kset_build", c_int, [c_int, c_i64, c_d, c_d, c_d, c_i64, P(c_i32), P(c_i64)])
             _sig(lib, "ssh_set_stream", c_int, [c_vp, c_vp])
             _sig(lib, "ssh_sync", c_int, [c_vp])
@@ -191,13 +193,14 @@ def _rows(a, N, d):
 class Context:
     """One configuration (d, N, L, chi | K) resident on the GPU.  Wraps ssh_create / ssh_destroy."""
 
-    def __init__(self, d: int, N: int, L: float, chi: float = 0.0, K: float = 0.0, device: int = 0, _handle=None):
+    def __init__(self, d: int, N: int, L: float, chi: float = 0.0, K: float = 0.0, device: int = 0,
+                 fx_impl: int = 0, _handle=None):
         lib = load()
         self._lib = lib
         self._owned = _handle is None
         self._h = c_vp()
         if _handle is None:
-            opts = (c_int * 8)(device, 0, 0, 0, 0, 0, 0, 0)
+            opts = (c_int * 8)(device, fx_impl, 0, 0, 0, 0, 0, 0)
             _check(lib.ssh_create(d, N, L, chi, K, ctypes.cast(opts, c_vp), ctypes.byref(self._h)))
         else:
             self._h = _handle
@@ -225,6 +228,13 @@ class Context:
 
     def __exit__(self, *a):
         self.close()
+
+    @property
+    def fx_impl(self) -> int:
+        """FX_INTEGER or FX_TENSOR: the implementation of this context's fixed-point evaluations."""
+        v = ctypes.c_int()
+        _check(self._lib.ssh_get_fx_impl(self._h, ctypes.byref(v)))
+        return v.value
 
     def kset(self) -> np.ndarray:
         out = np.zeros((max(self.M, 1), self.d), dtype=np.int32)
@@ -354,10 +364,10 @@ def _params(params, stages=None, **kw):
 class Batch:
     """Many configurations evaluated and minimised through the same launches (ssh_batch_*)."""
 
-    def __init__(self, device: int = 0):
+    def __init__(self, device: int = 0, fx_impl: int = 0):
         self._lib = load()
         self._h = c_vp()
-        opts = (c_int * 8)(device, 0, 0, 0, 0, 0, 0, 0)
+        opts = (c_int * 8)(device, fx_impl, 0, 0, 0, 0, 0, 0)
         _check(self._lib.ssh_batch_create(ctypes.cast(opts, c_vp), ctypes.byref(self._h)))
         self._members = []
 
@@ -424,10 +434,11 @@ class Server:
     """Continuous-batching minimisation service (ssh_server_*): submit, poll, collect."""
 
     def __init__(self, device: int = 0, max_slots: int = 256, hbm_budget_bytes: int = 64 << 30,
-                 chunk_steps: int = 32, max_pairs_per_step: int = 0, fifo: bool = False):
+                 chunk_steps: int = 32, max_pairs_per_step: int = 0, fifo: bool = False, fx_impl: int = 0):
         self._lib = load()
         self._h = c_vp()
-        o = ServerOpts(device, max_slots, hbm_budget_bytes, chunk_steps, max_pairs_per_step, 1 if fifo else 0)
+        o = ServerOpts(device, max_slots, hbm_budget_bytes, chunk_steps, max_pairs_per_step, 1 if fifo else 0,
+                       fx_impl)
         _check(self._lib.ssh_server_create(ctypes.byref(o), ctypes.byref(self._h)))
         self._keep = {}
 

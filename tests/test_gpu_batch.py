@@ -54,6 +54,29 @@ def test_batched_evaluation_equals_single(built):
     b.close()
 
 
+def test_tensor_members_equal_single(built):
+    """A batch whose d = 2 members run on the tensor cores and whose d = 1, 3 members run on the integer pipes:
+    every member bit-identical to a lone context of the same implementation, in an evaluation and a quench."""
+    cfgs = small_mix(6, 46, dims=(1, 2, 3)) + [synth.Config(d=2, N=2000, L=2000 ** 0.5, chi=0.45, seed=11)]
+    b = ssh.Batch(fx_impl=ssh.FX_TENSOR)
+    for c in cfgs:
+        b.add(c.d, c.N, c.L, synth.positions(c.seed, c.N, c.d), chi=c.chi)
+    b.eval(ssh.FX)
+    for i, c in enumerate(cfgs):
+        assert b.member(i).fx_impl == (ssh.FX_TENSOR if c.d == 2 else ssh.FX_INTEGER)
+        rb = b.member(i).results()
+        with ssh.Context(c.d, c.N, c.L, chi=c.chi, fx_impl=ssh.FX_TENSOR if c.d == 2 else ssh.FX_INTEGER) as ctx:
+            ctx.set_positions_frac(synth.positions(c.seed, c.N, c.d))
+            ra = ctx.energy_grad(ssh.FX)
+        assert np.array_equal(ra["phi"], rb["phi"]) and np.array_equal(ra["F_hi"], rb["F_hi"]), i
+        assert np.array_equal(ra["F_lo"], rb["F_lo"]), i
+    st, res = b.minimize(max_steps=40000, chunk_steps=16)
+    assert st == 0, res
+    for i, c in enumerate(cfgs):
+        assert res[i]["status"] == 0 and res[i]["smax"][0] <= 1e-36, (i, res[i])
+    b.close()
+
+
 def test_batched_quench_equals_single_and_converges(built, oracle_mod):
     cfgs = small_mix(10, 43)
     b = ssh.Batch()

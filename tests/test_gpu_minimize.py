@@ -37,10 +37,13 @@ STAGINGS = {
 }
 
 
-@pytest.mark.parametrize("name", list(STAGINGS))
-def test_small_d2_quench_converges(built, oracle_mod, name):
+CASES = [(name, ssh.FX_INTEGER) for name in STAGINGS] + [("fp64_then_fx", ssh.FX_TENSOR), ("all_fx", ssh.FX_TENSOR)]
+
+
+@pytest.mark.parametrize("name,impl", CASES, ids=[f"{n}-{'tensor' if i == ssh.FX_TENSOR else 'int'}" for n, i in CASES])
+def test_small_d2_quench_converges(built, oracle_mod, name, impl):
     cfg = synth.SMALL_D2
-    ctx = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi)
+    ctx = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi, fx_impl=impl)
     ctx.set_positions_frac(synth.positions(cfg.seed, cfg.N, cfg.d))
     r = ctx.minimize(stages=STAGINGS[name], max_steps=20000)
     assert r["status"] == 0, r
@@ -52,10 +55,11 @@ def test_small_d2_quench_converges(built, oracle_mod, name):
     assert phi <= ctx.M * cfg.N * 1.01e-36
 
 
-def test_medium_d2_staged_quench(built, oracle_mod):
+@pytest.mark.parametrize("impl", [ssh.FX_INTEGER, ssh.FX_TENSOR], ids=["int", "tensor"])
+def test_medium_d2_staged_quench(built, oracle_mod, impl):
     """The d=2, N=10^4, chi=0.45 workload: FP64 descent, then fixed-point polish, to S_max <= 1e-36."""
     cfg = synth.MEDIUM_D2
-    ctx = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi)
+    ctx = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi, fx_impl=impl)
     ctx.set_positions_frac(synth.positions(cfg.seed, cfg.N, cfg.d))
     r = ctx.minimize(stages=[ssh.FP64, ssh.FX], max_steps=60000, max_seconds=240)
     assert r["status"] == 0, r

@@ -82,6 +82,13 @@ CASES = [
 ]
 
 
+def impls(d):
+    """(fx_impl, precisions to check) per context: d = 2 runs the fixed point through both implementations."""
+    if d == 2:
+        return [(ssh.FX_INTEGER, PRECS), (ssh.FX_TENSOR, [ssh.FX])]
+    return [(ssh.FX_AUTO, PRECS)]
+
+
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_parity_against_oracle(built, oracle_mod, case):
     label, d, N, L, chi, K, seed = case
@@ -96,26 +103,33 @@ def test_parity_against_oracle(built, oracle_mod, case):
         s = np.sqrt(s) * 0.999999937 + 1e-9 * u          # arbitrary low mantissa bits
         s[: N // 8] *= 0.01                                # many coordinates below 1/64
         s_lo = (u - 0.5) * 2.0 ** -53 * s
-    ctx = ssh.Context(d, N, L, chi=chi, K=K)
-    n = ctx.kset()
-    assert np.array_equal(n, oracle_mod.kset(d, N, L, chi=chi, K=K))
-    ref = oracle_mod.phi_grad(s, s_lo, n, L, want_cs=True, nthreads=NTHREADS)
-    ctx.set_positions_frac(s, s_lo)
-    for prec in PRECS:
-        check_parity(ctx, s, s_lo, L, prec, ref, n, label=f"{label}/{ssh.PREC_NAMES[prec]}")
-    ctx.close()
+    ref = None
+    for impl, precs in impls(d):
+        ctx = ssh.Context(d, N, L, chi=chi, K=K, fx_impl=impl)
+        n = ctx.kset()
+        if ref is None:
+            assert np.array_equal(n, oracle_mod.kset(d, N, L, chi=chi, K=K))
+            ref = oracle_mod.phi_grad(s, s_lo, n, L, want_cs=True, nthreads=NTHREADS)
+        ctx.set_positions_frac(s, s_lo)
+        for prec in precs:
+            check_parity(ctx, s, s_lo, L, prec, ref, n, label=f"{label}/{ssh.PREC_NAMES[prec]}/impl{impl}")
+        ctx.close()
 
 
 def test_parity_medium_d2_full(built, oracle_mod):
     """The d=2, N=10^4, chi=0.45 workload at full size: every output against the oracle."""
     cfg = synth.MEDIUM_D2
     s = synth.positions(cfg.seed, cfg.N, cfg.d)
-    ctx = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi)
-    n = ctx.kset()
-    ref = oracle_mod.phi_grad(s, None, n, cfg.L, want_cs=True, nthreads=NTHREADS)
-    ctx.set_positions_frac(s)
-    for prec in PRECS:
-        check_parity(ctx, s, None, cfg.L, prec, ref, n, label=f"medium/{ssh.PREC_NAMES[prec]}")
+    ref = None
+    for impl, precs in impls(cfg.d):
+        ctx = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi, fx_impl=impl)
+        n = ctx.kset()
+        if ref is None:
+            ref = oracle_mod.phi_grad(s, None, n, cfg.L, want_cs=True, nthreads=NTHREADS)
+        ctx.set_positions_frac(s)
+        for prec in precs:
+            check_parity(ctx, s, None, cfg.L, prec, ref, n, label=f"medium/{ssh.PREC_NAMES[prec]}/impl{impl}")
+        ctx.close()
 
 
 def test_lattice_closed_form_on_gpu(built):
@@ -124,16 +138,18 @@ def test_lattice_closed_form_on_gpu(built):
     q, d = 16, 2   # s = m / 16 is exact in binary
     g = np.stack(np.meshgrid(np.arange(q) / q, np.arange(q) / q, indexing="ij"), -1).reshape(-1, d)
     N = len(g)
-    ctx = ssh.Context(d, N, 1.0, K=2 * math.pi * 20.5)
-    n = ctx.kset()
-    ctx.set_positions_frac(g)
-    mult = np.all(n % q == 0, axis=1)
-    for prec in PRECS:
-        ctx.energy_grad(prec)
-        C, S = ctx.ntilde()
-        tol = TOL[prec] * N
-        assert np.all(np.abs(ddv(C[~mult])) <= tol) and np.all(np.abs(ddv(S[~mult])) <= tol)
-        assert np.all(np.abs(ddv(C[mult]) - N) <= tol) and np.all(np.abs(ddv(S[mult])) <= tol)
+    for impl, precs in impls(d):
+        ctx = ssh.Context(d, N, 1.0, K=2 * math.pi * 20.5, fx_impl=impl)
+        n = ctx.kset()
+        ctx.set_positions_frac(g)
+        mult = np.all(n % q == 0, axis=1)
+        for prec in precs:
+            ctx.energy_grad(prec)
+            C, S = ctx.ntilde()
+            tol = TOL[prec] * N
+            assert np.all(np.abs(ddv(C[~mult])) <= tol) and np.all(np.abs(ddv(S[~mult])) <= tol)
+            assert np.all(np.abs(ddv(C[mult]) - N) <= tol) and np.all(np.abs(ddv(S[mult])) <= tol)
+        ctx.close()
 
 
 def test_single_particle_on_gpu(built):
@@ -150,30 +166,48 @@ def test_repeat_is_bitwise_identical(built):
     """Fixed-order reductions: two evaluations of the same positions agree bit for bit."""
     cfg = synth.MEDIUM_D2
     s = synth.positions(cfg.seed, cfg.N, cfg.d)
-    ctx = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi)
-    ctx.set_positions_frac(s)
-    for prec in PRECS:
-        a = ctx.energy_grad(prec)
-        Ca, Sa = ctx.ntilde()
-        b = ctx.energy_grad(prec)
-        Cb, Sb = ctx.ntilde()
-        assert np.array_equal(a["phi"], b["phi"]) and np.array_equal(a["F_hi"], b["F_hi"])
-        assert np.array_equal(a["F_lo"], b["F_lo"]) and np.array_equal(Ca, Cb) and np.array_equal(Sa, Sb)
+    for impl, precs in impls(cfg.d):
+        ctx = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi, fx_impl=impl)
+        ctx.set_positions_frac(s)
+        for prec in precs:
+            a = ctx.energy_grad(prec)
+            Ca, Sa = ctx.ntilde()
+            b = ctx.energy_grad(prec)
+            Cb, Sb = ctx.ntilde()
+            assert np.array_equal(a["phi"], b["phi"]) and np.array_equal(a["F_hi"], b["F_hi"])
+            assert np.array_equal(a["F_lo"], b["F_lo"]) and np.array_equal(Ca, Cb) and np.array_equal(Sa, Sb)
+        ctx.close()
 
 
 def test_physical_positions_match_fractional(built):
     """ssh_set_positions (r in [0, L), divided by L in dd) agrees with the exact fractional entry."""
     d, N, L = 2, 500, 500 ** 0.5
     s = synth.positions(77, N, d)
-    ctx = ssh.Context(d, N, L, chi=0.3)
-    ctx.set_positions_frac(s)
-    a = ctx.energy_grad(ssh.FX)
     from fractions import Fraction
     r_hi = s * L
     r_lo = np.array([float(Fraction(x) * Fraction(L) - Fraction(y)) for x, y in zip(s.ravel(), r_hi.ravel())]).reshape(s.shape)
-    ctx.set_positions(r_hi, r_lo)
-    b = ctx.energy_grad(ssh.FX)
-    assert abs(ddiff(a["phi"], b["phi"])) <= 1e-26 * ctx.M * N
+    for impl in (ssh.FX_INTEGER, ssh.FX_TENSOR):
+        ctx = ssh.Context(d, N, L, chi=0.3, fx_impl=impl)
+        ctx.set_positions_frac(s)
+        a = ctx.energy_grad(ssh.FX)
+        ctx.set_positions(r_hi, r_lo)
+        b = ctx.energy_grad(ssh.FX)
+        assert abs(ddiff(a["phi"], b["phi"])) <= 1e-26 * ctx.M * N
+        ctx.close()
+
+
+def test_fx_impl_selection(built):
+    with ssh.Context(2, 64, 8.0, chi=0.3, fx_impl=ssh.FX_TENSOR) as c:
+        assert c.fx_impl == ssh.FX_TENSOR
+    with ssh.Context(2, 64, 8.0, chi=0.3, fx_impl=ssh.FX_INTEGER) as c:
+        assert c.fx_impl == ssh.FX_INTEGER
+    with ssh.Context(3, 64, 4.0, chi=0.3) as c:
+        assert c.fx_impl == ssh.FX_INTEGER       # the tensor-core path covers d = 2
+    with pytest.raises(ssh.SshError) as e:
+        ssh.Context(3, 64, 4.0, chi=0.3, fx_impl=ssh.FX_TENSOR)
+    assert e.value.status == 1
+    with pytest.raises(ssh.SshError):
+        ssh.Context(2, 64, 8.0, chi=0.3, fx_impl=7)
 
 
 def test_bad_inputs_raise(built):
