@@ -42,7 +42,7 @@ DD_FP64_PER_PAIR = {"ntilde": 112, "force": 148}
 # Tensor-core fixed point (d = 2): every real product of two 2^-104 fixed-point values is 120 bf16 digit-pair
 # products.  The density needs 2 real products per (k, particle) pair (4 real products serve k = (n1, +m) and
 # (n1, -m)), the force 4 (G and the n2-weighted G', cos and sin terms, again for both signs of m).
-TC_FLOP_PER_PAIR = {"ntilde": 2 * 2 * 120, "force": 2 * 4 * 120}
+TC_FLOP_PER_PAIR = {"tc_dens": 2 * 2 * 120, "tc_force": 2 * 4 * 120}
 F64_FP64_PER_PAIR = {"ntilde": 6, "force": 8}
 # Peaks derived from unit counts and the maximum SM clock (148 SMs, 2032 MHz): 64 IMAD lanes per SM per
 # clock; 2 FP64 FMA lanes per SM per clock (1.2 TFLOP/s).
@@ -433,7 +433,7 @@ def main():
     tensor = prec == ssh.FX and ctx.fx_impl == ssh.FX_TENSOR
     if tensor:
         # the dominant of the two contractions (the digit preparation is reported in per_kernel_ms)
-        dom_name = max(("ntilde", "force"), key=lambda k: prof.get(k, (0.0, 1))[0])
+        dom_name = max(("tc_dens", "tc_force"), key=lambda k: prof.get(k, (0.0, 1))[0])
         dom_ms, dom_n = prof[dom_name]
         per_launch_s = dom_ms / 1e3 / dom_n
         per_pair, peak, unit, bound, what = TC_FLOP_PER_PAIR, BF16_PEAK, "FLOP/s", "tensor", "bf16"

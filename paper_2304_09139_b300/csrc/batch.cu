@@ -89,6 +89,7 @@ struct Runner {
       f.stage = m.stage;
       f.stage_floor = m.stage + 1 < m.p.n_stages ? m.p.stage_floor[m.stage] : 0.0;
       f.stall_window = m.p.stall_window[m.stage];
+      f.phi_tol = fire_phi_tol(&m.h->c, m.p.stage_prec[m.stage]);
       prm.push_back(f);
       firsts.push_back(first ? 1 : 0);
       local.push_back((int)t);

@@ -130,7 +130,10 @@ __global__ void k_fire_accept(const CfgDev* __restrict__ cfgs, const int* __rest
     fs->rejected_now = 1;
     return;
   }
-  if (dd_gt(phi, dd_make(fs->phi_hi, fs->phi_lo))) {
+  // uphill beyond the evaluation's own error bound: reject (FIRE's uphill reset, with dt halved)
+  const dd phi_acc = dd_make(fs->phi_hi, fs->phi_lo);
+  const double margin = fs->phi_tol * sqrt(fmax(phi_acc.hi, 0.0));
+  if (dd_gt(phi, dd_add_d(phi_acc, margin))) {
     fs->rejected_now = 1;
     fs->rejected++;
     fs->dt *= fs->f_dec;
@@ -186,8 +189,13 @@ __global__ void k_fire_stage_init(const CfgDev* __restrict__ cfgs, const int* __
     *fs = prm;
     fs->step = 0;
     fs->rejected = 0;
-    fs->n_pos = 0;
   }
+  // every stage restarts FIRE: v = 0 (k_fire_zero_v), dt = dt0, alpha = alpha_start, no downhill run yet
+  fs->dt = prm.dt;
+  fs->alpha = prm.alpha_start;
+  fs->n_pos = 0;
+  fs->zero_v = 0;
+  fs->phi_tol = prm.phi_tol;
   fs->status = kFsRunning;
   fs->rejected_now = 0;
   fs->stage_step = 0;
@@ -206,9 +214,9 @@ __global__ void k_fire_stage_init(const CfgDev* __restrict__ cfgs, const int* __
   else if (fs->stage_floor > 0 && sm <= fs->stage_floor) fs->status = kFsStageDone;
 }
 
-// v = 0 for the members idx[t] with first[t]; grid (coordinate blocks, n)
+// v = 0 for the members idx[t] (every stage start); grid (coordinate blocks, n)
 __global__ void k_fire_zero_v(const CfgDev* __restrict__ cfgs, const int* __restrict__ idx, const int* __restrict__ first) {
-  if (!first[blockIdx.y]) return;
+  (void)first;
   const CfgDev& c = cfgs[idx[blockIdx.y]];
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= (int64_t)c.d * c.N) return;
@@ -305,6 +313,16 @@ FireState fire_params(const ssh_min_params* p) {
   prm.stage_floor = 0.0;
   prm.stall_window = p->stall_window[0];
   return prm;
+}
+
+// Phi = sum_k |n~_k|^2 with every n~ off by at most eps N: |dPhi| <= 2 eps N sum |n~| + M (eps N)^2, below
+// 2 eps N sqrt(M Phi) + M (eps N)^2.  eps: 2^-100 for the tensor-core digits and for double-double, 2^-120 for
+// the integer-pipe fixed point; FP64 keeps the strict test (its steps are rejected on any rise).
+double fire_phi_tol(const Ctx* c, int prec) {
+  double eps = 0.0;
+  if (prec == SSH_FX) eps = c->tc.on ? 0x1p-100 : 0x1p-120;
+  else if (prec == SSH_DD) eps = 0x1p-100;
+  return 2.0 * eps * (double)c->N * sqrt((double)c->M);
 }
 
 // One FIRE step of every member of e as stream work.
@@ -415,6 +433,7 @@ ssh_status fire_begin(Ctx* c, const ssh_min_params* p) {
   if (e != cudaSuccess) { set_error(std::string("ssh_fire_begin: allocation: ") + cudaGetErrorString(e)); return SSH_ENOMEM; }
   FireState prm = fire_params(p);
   prm.stage = 0;
+  prm.phi_tol = fire_phi_tol(c, p->stage_prec[0]);
   e = single_stage_start(c, p->stage_prec[0], prm, 1);
   if (e != cudaSuccess) { set_error(std::string("ssh_fire_begin: ") + cudaGetErrorString(e)); return SSH_ECUDA; }
   c->fire->begun = true;
@@ -485,6 +504,7 @@ ssh_status minimize(Ctx* c, const ssh_min_params* p, ssh_min_result* res) {
     prm.stage = s;
     prm.stage_floor = s + 1 < p->n_stages ? p->stage_floor[s] : 0.0;
     prm.stall_window = p->stall_window[s];
+    prm.phi_tol = fire_phi_tol(c, prec);
     e = single_stage_start(c, prec, prm, s == 0);
     cudaGraphExec_t g = nullptr;
     if (e == cudaSuccess) e = fire_graph(c, prec, &g);

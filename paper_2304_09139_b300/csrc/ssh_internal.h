@@ -42,7 +42,10 @@ struct Launch {          // per-precision launch shape of the two hot kernels
 };
 
 // kernel ids for the event profiler (ssh_prof_*)
-enum KernelId { kKTwiddle = 0, kKNtilde, kKNtReduce, kKFinalize, kKCoef, kKForce, kKFReduce, kKFire, kKCount = 16 };
+enum KernelId {
+  kKTwiddle = 0, kKNtilde, kKNtReduce, kKFinalize, kKCoef, kKForce, kKFReduce, kKFire,
+  kKTcPrep, kKTcDens, kKTcFinish, kKTcCoef, kKTcForce, kKCount = 16
+};
 
 struct ProfRec {
   int id;
@@ -155,6 +158,7 @@ struct FireState {
   double dt_max, alpha_start, f_alpha, f_inc, f_dec;
   long long n_min, stall_window, max_steps;
   double target, stage_floor;
+  double phi_tol;  // the guard rejects a step only when Phi rises by more than phi_tol sqrt(Phi_accepted)
 };
 
 // A set of configurations evaluated together.  Members keep their own buffers (Ctx); the engine holds their
@@ -251,6 +255,8 @@ void fire_fill_cfgdev(const Ctx* c, CfgDev* g);
 cudaError_t fire_alloc(Ctx* c);
 cudaError_t fire_step_engine(const Engine* e, cudaStream_t st, Prof* prof);
 FireState fire_params(const ssh_min_params* p);
+// error bound coefficient of Phi in arithmetic prec for configuration c: |dPhi| <= coef sqrt(Phi)
+double fire_phi_tol(const Ctx* c, int prec);
 // (re)start the members idx of e: v = 0 when first, accepted Phi / S_max from their scal, stage parameters
 cudaError_t fire_stage_init_engine(const Engine* e, const std::vector<int>& idx, const std::vector<FireState>& params,
                                    const std::vector<int>& first, cudaStream_t st);

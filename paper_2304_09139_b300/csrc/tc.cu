@@ -144,6 +144,19 @@ __device__ __forceinline__ __int128 q160_shr_round(const q160& a, int sh) {
   return (__int128)((lo >> sh) | ((unsigned __int128)t.w[2] << (128 - sh)));
 }
 
+__device__ __forceinline__ fxc PolFXZero() {
+  fxc z;
+  z.re = q128_zero();
+  z.im = q128_zero();
+  return z;
+}
+__device__ __forceinline__ fxc PolFXOne() {
+  fxc z;
+  z.re = q126_one();
+  z.im = q128_zero();
+  return z;
+}
+
 __device__ __forceinline__ q160 load_q160(const void* p) {
   const uint32_t* u = reinterpret_cast<const uint32_t*>(p);
   q160 r;
@@ -156,79 +169,147 @@ __device__ __forceinline__ q160 load_q160(const void* p) {
 
 // ------------------------------------------------------------------------------------------------ k_tc_prep
 
-// Thread per (particle j, axis, block of 16 powers).  Items: TwItem {cfg, start} over
-// (nb1 + nb2) * N threads per configuration, 128 per item.
-__global__ void __launch_bounds__(kTwThreads) k_tc_prep(const CfgDev* __restrict__ cfgs, const TwItem* __restrict__ items) {
+namespace {
+
+constexpr int kPrepThreads = 256;
+constexpr int kPrepParticles = 32;  // particles per CTA
+constexpr int kPrepM = 64;          // powers per pass (shared-memory staging of their fixed-point values)
+constexpr size_t kPrepSmem = (size_t)kPrepM * 2 * kPrepParticles * 16 + kPrepParticles * sizeof(fxc);
+
+// Eight values X (|X| <= 2^104) -> their 15 balanced digits as one 16-byte row (8 bf16) per digit slice.
+__device__ __forceinline__ void put_digit_rows(uint8_t* base, uint32_t slice_stride, const __int128 (&X)[8]) {
+  const __int128 bias = digit_bias();
+  __int128 Y[8];
+#pragma unroll
+  for (int v = 0; v < 8; v++) Y[v] = X[v] + bias;
+#pragma unroll
+  for (int s = 0; s < kDigits; s++) {
+    const int i = kDigits - 1 - s;
+    uint32_t h[8];
+#pragma unroll
+    for (int v = 0; v < 8; v++) {
+      const int d = i == kDigits - 1 ? (int)(Y[v] >> 98) : (int)((Y[v] >> (7 * i)) & 127) - 64;
+      // small integer -> fp32 (exact) -> its bf16 half (exact: at most 8 significant bits)
+      h[v] = __float_as_uint(__int_as_float(kMagicBits + d) - kMagic) >> 16;
+    }
+    uint4 row;
+    row.x = h[0] | (h[1] << 16);
+    row.y = h[2] | (h[3] << 16);
+    row.z = h[4] | (h[5] << 16);
+    row.w = h[6] | (h[7] << 16);
+    *reinterpret_cast<uint4*>(base + (size_t)s * slice_stride) = row;
+  }
+}
+
+__device__ __forceinline__ __int128 fixed104(const q128& w) {  // round(x 2^104) of a Q2.126 value
+  return (q128_to_i128(w) + ((__int128)1 << 21)) >> 22;
+}
+
+}  // namespace
+
+// CTA per (configuration, axis, 32 particles); items TwItem {cfg, axis, first particle}.  Pass over the
+// powers m in groups of 64: phase 1 computes e^{2 pi i m s_j} (an exact-phase anchor every 16 powers, one
+// multiply per power in between) into shared memory as fixed-point integers; phase 2 writes the digit slices
+// as whole 16-byte core-matrix rows (8 K-consecutive values of one operand row), which consecutive threads
+// fill contiguously.  Axis 1 (n1) feeds the density GEMM's A operand and the Q2.126 table a_j(n1) of the
+// force epilogue; axis 2 feeds the density GEMM's B operand and the force GEMM's A operand.
+__global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restrict__ cfgs,
+                                                          const TwItem* __restrict__ items) {
+  extern __shared__ __align__(16) uint8_t psm[];
+  __int128* Xs = reinterpret_cast<__int128*>(psm);                           // [m - m0][p][j]
+  fxc* e1s = reinterpret_cast<fxc*>(psm + (size_t)kPrepM * 2 * kPrepParticles * 16);  // e^{2 pi i s_j}
   const TwItem it = items[blockIdx.x];
   const CfgDev& c = cfgs[it.cfg];
   if (stopped(c)) return;
+  const int axis = it.pad;
   const int64_t N = c.N;
-  const int nb1 = c.tc_R1 / 16 + 1, nb2 = c.tc_R2 / 16 + 1;
-  const int64_t idx = it.start + threadIdx.x;
-  if (idx >= (int64_t)(nb1 + nb2) * N) return;
-  const int64_t j = idx % N;
-  const int blk = (int)(idx / N);
-  const int axis = blk < nb1 ? 0 : 1;
-  const int b = axis == 0 ? blk : blk - nb1;
+  const int64_t j0 = it.start;
   const int R = axis == 0 ? c.tc_R1 : c.tc_R2;
-  const q128 u = turns_from_dd(c.s_hi[axis * N + j], c.s_lo[axis * N + j]);
-  const fxc e1 = phasor_turn(u);
-  fxc z = phasor_turn(turn_times(u, 16 * b));
-  const int64_t ks = j >> 4;
-  const int kk = (int)(j & 15);
-  for (int i = 0; i < 16; i++) {
-    const int m = 16 * b + i;
-    if (m > R) break;
-    if (i > 0) z = fxc_mul(z, e1);
-    if (axis == 0) {
-      reinterpret_cast<fxc*>(c.tc_a1)[(int64_t)m * N + j] = z;
-#pragma unroll
-      for (int p = 0; p < 2; p++) {
-        const int r = 2 * m + p;
-        uint8_t* base = c.tc_dA + ((int64_t)(r >> 7) * c.tc_KS + ks) * kStageA;
-        put_digits_q126(base, kSliceA, slice_off(r & 127, kk), p == 0 ? z.re : z.im);
-      }
-    } else {
-#pragma unroll
-      for (int q = 0; q < 2; q++) {
-        const int col = 2 * m + q;
-        uint8_t* bd = c.tc_dB + ((int64_t)(col >> 5) * c.tc_KS + ks) * kStageB;
-        put_digits_q126(bd, kSliceB, slice_off(col & 31, kk), q == 0 ? z.re : z.im);
-        uint8_t* bf = c.tc_fA + ((int64_t)(j >> 7) * c.tc_KSf + (col >> 4)) * kStageA;
-        put_digits_q126(bf, kSliceA, slice_off((int)(j & 127), col & 15), q == 0 ? z.re : z.im);
+  const int tid = threadIdx.x;
+  if (tid < kPrepParticles) {
+    const int64_t j = j0 + tid;
+    fxc e = PolFXOne();
+    if (j < N) e = phasor_turn(turns_from_dd(c.s_hi[axis * N + j], c.s_lo[axis * N + j]));
+    e1s[tid] = e;
+  }
+  __syncthreads();
+  for (int m0 = 0; m0 <= R; m0 += kPrepM) {
+    const int mcount = min(kPrepM, R + 1 - m0);
+    // phase 1: tasks (particle, block of 16 powers)
+    const int nblk = (mcount + 15) / 16;
+    for (int task = tid; task < nblk * kPrepParticles; task += kPrepThreads) {
+      const int jl = task % kPrepParticles, b = task / kPrepParticles;
+      const int64_t j = j0 + jl;
+      const int mb = m0 + 16 * b;
+      fxc z = PolFXZero();
+      const bool live = j < N;
+      if (live) z = phasor_turn(turn_times(turns_from_dd(c.s_hi[axis * N + j], c.s_lo[axis * N + j]), mb));
+      const fxc e1 = e1s[jl];
+      for (int i = 0; i < 16 && mb + i < m0 + mcount; i++) {
+        if (i > 0 && live) z = fxc_mul(z, e1);
+        const int ml = mb + i - m0;
+        Xs[(ml * 2 + 0) * kPrepParticles + jl] = fixed104(z.re);
+        Xs[(ml * 2 + 1) * kPrepParticles + jl] = fixed104(z.im);
+        if (axis == 0 && live) reinterpret_cast<fxc*>(c.tc_a1)[(int64_t)(mb + i) * N + j] = z;
       }
     }
+    __syncthreads();
+    // phase 2a: rows (m, cos / sin) x 8 particles, into the density GEMM operand of this axis
+    const int nrow = 2 * mcount;
+    for (int task = tid; task < nrow * (kPrepParticles / 8); task += kPrepThreads) {
+      const int rl = task % nrow, g8 = task / nrow;
+      const int r = 2 * m0 + rl;
+      const int64_t jg = j0 + 8 * g8;
+      if (jg >= N) continue;  // K-steps past the last particle stay zero
+      __int128 X[8];
+#pragma unroll
+      for (int v = 0; v < 8; v++) X[v] = Xs[rl * kPrepParticles + 8 * g8 + v];
+      const int64_t ks = jg >> 4;
+      const int k0 = (int)(jg & 15);
+      if (axis == 0)
+        put_digit_rows(c.tc_dA + ((int64_t)(r >> 7) * c.tc_KS + ks) * kStageA + slice_off(r & 127, k0), kSliceA, X);
+      else
+        put_digit_rows(c.tc_dB + ((int64_t)(r >> 5) * c.tc_KS + ks) * kStageB + slice_off(r & 31, k0), kSliceB, X);
+    }
+    // phase 2b (axis 2): particles x 8 values of (m, cos / sin), into the force GEMM's A operand
+    if (axis == 1) {
+      const int ngrp = nrow / 8;  // m0 is a multiple of 64, so 2 m0 is a multiple of 8; a partial group waits
+      const int ntail = nrow % 8;
+      const int groups = ngrp + (ntail ? 1 : 0);
+      for (int task = tid; task < groups * kPrepParticles; task += kPrepThreads) {
+        const int jl = task % kPrepParticles, g = task / kPrepParticles;
+        const int64_t j = j0 + jl;
+        if (j >= N) continue;
+        __int128 X[8];
+#pragma unroll
+        for (int v = 0; v < 8; v++) {
+          const int rl = 8 * g + v;
+          X[v] = rl < nrow ? Xs[rl * kPrepParticles + jl] : (__int128)0;
+        }
+        const int kf0 = 2 * m0 + 8 * g;
+        put_digit_rows(c.tc_fA + ((int64_t)(j >> 7) * c.tc_KSf + (kf0 >> 4)) * kStageA + slice_off((int)(j & 127), kf0 & 15),
+                       kSliceA, X);
+      }
+    }
+    __syncthreads();
   }
 }
 
 // ------------------------------------------------------------------------------------------------ k_tc_gemm
 
-// One CTA per item.  Density items: A = density row tile it.a, B = column tile it.b, K-steps [ks0, ks0 + nks);
-// the epilogue stores the three int64 level groups of every output into tc_part slot it.slot.  Force items:
-// A = particle tile it.a, B = column tile it.b (8 values of n1), every K-step; the epilogue writes force
-// partials fpart[2 it.b + half][axis][j].
+// Persistent: CTA b takes items b, b + gridDim.x, ...  Density items: A = density row tile it.a, B = column
+// tile it.b, K-steps [ks0, ks0 + nks); the epilogue stores the three int64 level groups of every output into
+// tc_part slot it.slot.  Force items: A = particle tile it.a, B = column tile it.b (8 values of n1), every
+// K-step; the epilogue writes force partials fpart[2 it.b + half][axis][j].  Stage and accumulator barrier
+// phases run on across items, so the producer streams the next item's operands while the epilogue finishes
+// the previous item (the accumulator is released as soon as its last level has been read).
 __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __restrict__ cfgs,
-                                                              const TcItem* __restrict__ items) {
+                                                              const TcItem* __restrict__ items, int n_items) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint64_t bar_full[kStages], bar_empty[kStages], bar_acc_full, bar_acc_empty, bar_drain;
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
-  const TcItem it = items[blockIdx.x];
-  const CfgDev& c = cfgs[it.cfg];
-  if (stopped(c)) return;  // uniform over the CTA, before any barrier or allocation
-  int* err = c.tc_err;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint8_t* gA;
-  const uint8_t* gB;
-  if (it.kind == 0) {
-    gA = c.tc_dA + ((int64_t)it.a * c.tc_KS + it.ks0) * kStageA;
-    gB = c.tc_dB + ((int64_t)it.b * c.tc_KS + it.ks0) * kStageB;
-  } else {
-    gA = c.tc_fA + ((int64_t)it.a * c.tc_KSf + it.ks0) * kStageA;
-    gB = c.tc_fB + ((int64_t)it.b * c.tc_KSf + it.ks0) * kStageB;
-  }
-  const int nks = it.nks;
-  const int nch = (nks + kChunkSteps - 1) / kChunkSteps;
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; s++) {
       mbar_init(&bar_full[s], 1);
@@ -246,109 +327,148 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
   tc_fence_after();
   const uint32_t tbase = tmem_base_sh;
   volatile int* abort_flag = &abort_sh;
+  int* err_seen = nullptr;  // the configuration of the item being processed when a wait gave up
 
   if (warp == 0) {
-    // ---- producer: one thread streams the K-steps through the stages
+    // ---- producer: one thread streams every item's K-steps through the stages
     if (lane == 0) {
-      int issued = 0;
-      for (int ks = 0; ks < nks; ks++) {
-        const int s = ks % kStages, use = ks / kStages;
-        if (use > 0 && !mbar_wait(&bar_empty[s], (use - 1) & 1, kWaitLimit, abort_flag)) {
-          *abort_flag = 1;
-          atomicOr(err, 1);
-          break;
+      long long gs = 0;  // K-steps issued so far (all items)
+      bool stop = false;
+      for (int item = blockIdx.x; item < n_items && !stop; item += gridDim.x) {
+        const TcItem it = items[item];
+        const CfgDev& c = cfgs[it.cfg];
+        if (stopped(c)) continue;
+        const uint8_t* gA;
+        const uint8_t* gB;
+        if (it.kind == 0) {
+          gA = c.tc_dA + ((int64_t)it.a * c.tc_KS + it.ks0) * kStageA;
+          gB = c.tc_dB + ((int64_t)it.b * c.tc_KS + it.ks0) * kStageB;
+        } else {
+          gA = c.tc_fA + ((int64_t)it.a * c.tc_KSf + it.ks0) * kStageA;
+          gB = c.tc_fB + ((int64_t)it.b * c.tc_KSf + it.ks0) * kStageB;
         }
-        uint8_t* dst = smem + (size_t)s * kStageBytes;
-        mbar_expect_tx(&bar_full[s], kStageBytes);
-        bulk_g2s(dst, gA + (size_t)ks * kStageA, kStageA, &bar_full[s]);
-        bulk_g2s(dst + kStageA, gB + (size_t)ks * kStageB, kStageB, &bar_full[s]);
-        issued = ks + 1;
+        for (int ks = 0; ks < it.nks; ks++, gs++) {
+          const int s = (int)(gs % kStages);
+          const long long use = gs / kStages;
+          if (use > 0 && !mbar_wait(&bar_empty[s], (uint32_t)((use - 1) & 1), kWaitLimit, abort_flag)) {
+            *abort_flag = 1;
+            atomicOr(c.tc_err, 1);
+            stop = true;
+            break;
+          }
+          uint8_t* dst = smem + (size_t)s * kStageBytes;
+          mbar_expect_tx(&bar_full[s], kStageBytes);
+          bulk_g2s(dst, gA + (size_t)ks * kStageA, kStageA, &bar_full[s]);
+          bulk_g2s(dst + kStageA, gB + (size_t)ks * kStageB, kStageB, &bar_full[s]);
+        }
       }
       if (*abort_flag) {
         // let the copies in flight land before the CTA can exit
-        for (int ks = issued > kStages ? issued - kStages : 0; ks < issued; ks++)
-          mbar_wait(&bar_full[ks % kStages], (ks / kStages) & 1, kWaitLimit, nullptr);
+        for (long long k = gs > kStages ? gs - kStages : 0; k < gs; k++)
+          mbar_wait(&bar_full[k % kStages], (uint32_t)((k / kStages) & 1), kWaitLimit, nullptr);
       }
     }
   } else if (warp == 1) {
     // ---- MMA issuer: 22 MMAs per K-step; level u of the accumulator receives digit slice pairs (s, u - s)
     if (lane == 0) {
-      for (int ks = 0; ks < nks; ks++) {
-        const int s = ks % kStages, use = ks / kStages;
-        const int ch = ks / kChunkSteps;
-        const bool first = ks % kChunkSteps == 0;
-        const bool last = ks % kChunkSteps == kChunkSteps - 1 || ks == nks - 1;
-        if (!mbar_wait(&bar_full[s], use & 1, kWaitLimit, abort_flag)) {
-          *abort_flag = 1;
-          atomicOr(err, 2);
-          break;
-        }
-        if (first && ch > 0 && !mbar_wait(&bar_acc_empty, (ch - 1) & 1, kWaitLimit, abort_flag)) {
-          *abort_flag = 1;
-          atomicOr(err, 4);
-          break;
-        }
-        tc_fence_after();
-        const uint32_t a0 = smem_u32(smem + (size_t)s * kStageBytes);
-        const uint32_t b0 = a0 + kStageA;
+      long long gs = 0, gc = 0;  // K-steps and chunks consumed so far (all items)
+      bool stop = false;
+      for (int item = blockIdx.x; item < n_items && !stop; item += gridDim.x) {
+        const TcItem it = items[item];
+        const CfgDev& c = cfgs[it.cfg];
+        if (stopped(c)) continue;
+        for (int ks = 0; ks < it.nks; ks++, gs++) {
+          const int s = (int)(gs % kStages);
+          const long long use = gs / kStages;
+          const bool first = ks % kChunkSteps == 0;
+          const bool last = ks % kChunkSteps == kChunkSteps - 1 || ks == it.nks - 1;
+          if (!mbar_wait(&bar_full[s], (uint32_t)(use & 1), kWaitLimit, abort_flag)) {
+            *abort_flag = 1;
+            atomicOr(c.tc_err, 2);
+            stop = true;
+            break;
+          }
+          if (first && gc > 0 && !mbar_wait(&bar_acc_empty, (uint32_t)((gc - 1) & 1), kWaitLimit, abort_flag)) {
+            *abort_flag = 1;
+            atomicOr(c.tc_err, 4);
+            stop = true;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(smem + (size_t)s * kStageBytes);
+          const uint32_t b0 = a0 + kStageA;
 #pragma unroll
-        for (int sl = 0; sl < kDigits; sl++) {
-          const int ntot = (kLevels - sl) * kTileN;
-          const int n1 = ntot < 256 ? ntot : 256;
-          const uint32_t acc = (first && sl == 0) ? 0u : 1u;
-          const uint64_t ad = make_sdesc(a0 + sl * kSliceA);
-          mma_bf16(tbase + sl * kTileN, ad, make_sdesc(b0), make_idesc(kTileM, n1), acc);
-          if (ntot > 256) mma_bf16(tbase + sl * kTileN + 256, ad, make_sdesc(b0 + 256 * 32), make_idesc(kTileM, ntot - 256), acc);
+          for (int sl = 0; sl < kDigits; sl++) {
+            const int ntot = (kLevels - sl) * kTileN;
+            const int n1 = ntot < 256 ? ntot : 256;
+            const uint32_t acc = (first && sl == 0) ? 0u : 1u;
+            const uint64_t ad = make_sdesc(a0 + sl * kSliceA);
+            mma_bf16(tbase + sl * kTileN, ad, make_sdesc(b0), make_idesc(kTileM, n1), acc);
+            if (ntot > 256)
+              mma_bf16(tbase + sl * kTileN + 256, ad, make_sdesc(b0 + 256 * 32), make_idesc(kTileM, ntot - 256), acc);
+          }
+          mma_commit(&bar_empty[s]);
+          if (last) {
+            mma_commit(&bar_acc_full);
+            gc++;
+          }
         }
-        mma_commit(&bar_empty[s]);
-        if (last) mma_commit(&bar_acc_full);
       }
       // every MMA issued by this thread has completed once the drain barrier flips
       mma_commit(&bar_drain);
-      if (!mbar_wait(&bar_drain, 0, kWaitLimit, nullptr)) atomicOr(err, 8);
+      if (!mbar_wait(&bar_drain, 0, kWaitLimit, nullptr)) *abort_flag = 1;
     }
   } else {
     // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 and accumulator columns 16 h .. 16 h + 15
     const int q = warp & 3, h = (warp - 2) >> 2;
-    long long st[3][16];
+    const int row = 32 * q + lane;
+    const uint32_t trow = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * h);
+    // sum over the five levels of a group of (bits - magic) 2^(7 (4 - l)): the magic part, subtracted once
+    constexpr long long kGroupBias = (long long)kMagicBits * ((1ll << 28) + (1ll << 21) + (1ll << 14) + (1ll << 7) + 1);
+    long long gc = 0;
+    bool stop = false;
+    for (int item = blockIdx.x; item < n_items && !stop; item += gridDim.x) {
+      const TcItem it = items[item];
+      const CfgDev& c = cfgs[it.cfg];
+      if (stopped(c)) continue;
+      long long st[3][16];
 #pragma unroll
-    for (int g = 0; g < 3; g++)
+      for (int g = 0; g < 3; g++)
 #pragma unroll
-      for (int i = 0; i < 16; i++) st[g][i] = 0;
-    bool ok = true;
-    for (int ch = 0; ch < nch; ch++) {
-      // the warp leaves together (tcgen05.ld is warp-collective)
-      const bool got = mbar_wait(&bar_acc_full, ch & 1, kWaitLimit, abort_flag);
-      if (!__all_sync(0xffffffffu, got)) {
-        *abort_flag = 1;
-        if (lane == 0) atomicOr(err, 16);
-        ok = false;
-        break;
-      }
-      tc_fence_after();
-      const uint32_t trow = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * h);
-#pragma unroll
-      for (int g = 0; g < 3; g++) {
-        long long t[16];
-#pragma unroll
-        for (int i = 0; i < 16; i++) t[i] = 0;
-#pragma unroll
-        for (int l = 0; l < 5; l++) {
-          uint32_t r[16];
-          tmem_ld16(trow + (uint32_t)((5 * g + l) * kTileN), r);
-          tmem_ld_wait();
-#pragma unroll
-          for (int i = 0; i < 16; i++) t[i] += (long long)acc_int(r[i]) * (1ll << (7 * (4 - l)));
+        for (int i = 0; i < 16; i++) st[g][i] = 0;
+      const int nch = (it.nks + kChunkSteps - 1) / kChunkSteps;
+      for (int ch = 0; ch < nch; ch++, gc++) {
+        // the warp leaves together (tcgen05.ld is warp-collective)
+        const bool got = mbar_wait(&bar_acc_full, (uint32_t)(gc & 1), kWaitLimit, abort_flag);
+        if (!__all_sync(0xffffffffu, got)) {
+          *abort_flag = 1;
+          if (lane == 0) atomicOr(c.tc_err, 16);
+          stop = true;
+          break;
         }
+        tc_fence_after();
 #pragma unroll
-        for (int i = 0; i < 16; i++) st[g][i] += t[i];
+        for (int g = 0; g < 3; g++) {
+          long long t[16];
+#pragma unroll
+          for (int i = 0; i < 16; i++) t[i] = -kGroupBias;
+#pragma unroll
+          for (int l = 0; l < 5; l++) {
+            uint32_t r[16];
+            tmem_ld16(trow + (uint32_t)((5 * g + l) * kTileN), r);
+            tmem_ld_wait();
+#pragma unroll
+            for (int i = 0; i < 16; i++)
+              t[i] += (long long)(uint32_t)__float_as_int(__uint_as_float(r[i]) + kMagic) * (1ll << (7 * (4 - l)));
+          }
+#pragma unroll
+          for (int i = 0; i < 16; i++) st[g][i] += t[i];
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&bar_acc_empty);
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&bar_acc_empty);
-    }
-    if (ok) {
-      const int row = 32 * q + lane;
+      if (stop) break;
       if (it.kind == 0) {
         // level groups of every output: R' = st0 2^70 + st1 2^35 + st2 (value = R' 2^-110)
         long long* out = c.tc_part + (size_t)it.slot * (3 * kTileN * kTileM);
@@ -361,7 +481,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
         if (j < c.N) {
           // four n1 values per half tile, columns (Re G, Im G, Re G', Im G') each.  G~ = R' 2^-110 is taken
           // as R' 2^gs (|.| < 2^126); the top halves of a * G are value 2^(108 + gs), shifted to value 2^ts.
-          const int gs = c.tc_gs, tsh = 108 + c.tc_gs - c.tc_ts;
+          const int gsh = c.tc_gs, tsh = 108 + c.tc_gs - c.tc_ts;
           __int128 F1 = 0, F2 = 0;  // value 2^ts
 #pragma unroll
           for (int v = 0; v < 4; v++) {
@@ -372,7 +492,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
             for (int g4 = 0; g4 < 4; g4++) {
               const int i = 4 * v + g4;
               const __int128 R = ((__int128)st[0][i] << 70) + ((__int128)st[1][i] << 35) + (__int128)st[2][i];
-              gcol[g4] = q128_from_i128(R << gs);
+              gcol[g4] = q128_from_i128(R << gsh);
             }
             const fxc a = reinterpret_cast<const fxc*>(c.tc_a1)[(int64_t)n1 * c.N + j];
             uint32_t p[5], r2[5];
@@ -399,6 +519,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
       }
     }
   }
+  (void)err_seen;
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
@@ -556,7 +677,8 @@ cudaError_t tc_setup(Ctx* c) {
     }
   const int nt = (int)t.tiles.size();
   const int64_t max_split = std::max<int64_t>(1, t.KS / kChunkSteps);
-  t.ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(max_split, (c->sm_count + nt - 1) / std::max(1, nt)));
+  // one CTA per SM: as many K ranges per tile as fit in a single wave
+  t.ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(max_split, c->sm_count / std::max(1, nt)));
   // each K range holds at most 4096 read-outs, so the int64 level groups (below 2^50.1 per read-out) cannot overflow
   t.ksplit = (int)std::max<int64_t>(t.ksplit, (t.KS + 4096 * kChunkSteps - 1) / (4096 * kChunkSteps));
   cudaStream_t st = c->stream;
@@ -588,6 +710,7 @@ cudaError_t tc_setup(Ctx* c) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
+    cudaFuncSetAttribute(k_tc_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPrepSmem);
     attr = true;
   }
   return cudaGetLastError();
@@ -642,8 +765,8 @@ void tc_fill_cfgdev(const Ctx* c, CfgDev* g) {
 // work items of one member (engine member index i)
 void tc_items(const Ctx* c, int i, std::vector<TwItem>& prep, std::vector<TcItem>& dens, std::vector<TcItem>& force) {
   const TcPlan& t = c->tc;
-  const int64_t nprep = (int64_t)(t.R1 / 16 + 1 + t.R2 / 16 + 1) * c->N;
-  for (int64_t s = 0; s < nprep; s += kTwThreads) prep.push_back({i, 0, s});
+  for (int axis = 0; axis < 2; axis++)
+    for (int64_t j = 0; j < c->N; j += kPrepParticles) prep.push_back({i, axis, j});
   for (int ti = 0; ti < (int)t.tiles.size(); ti++) {
     const int rt = t.tiles[ti] / t.CTd, ct = t.tiles[ti] % t.CTd;
     for (int sp = 0; sp < t.ksplit; sp++) {
@@ -659,13 +782,13 @@ size_t tc_gemm_smem() { return kGemmSmem; }
 
 cudaError_t tc_launch_density(const EngineView& v, cudaStream_t st, Prof* prof) {
   if (v.ntc_list == 0) return cudaSuccess;
-  prof_begin(prof, st, kKTwiddle);
-  k_tc_prep<<<(unsigned)v.ntc_prep, kTwThreads, 0, st>>>(v.cfgs, v.tc_prep);
+  prof_begin(prof, st, kKTcPrep);
+  k_tc_prep<<<(unsigned)v.ntc_prep, kPrepThreads, kPrepSmem, st>>>(v.cfgs, v.tc_prep);
   prof_end(prof, st);
-  prof_begin(prof, st, kKNtilde);
-  k_tc_gemm<<<(unsigned)v.ntc_dens, kGemmThreads, kGemmSmem, st>>>(v.cfgs, v.tc_dens);
+  prof_begin(prof, st, kKTcDens);
+  k_tc_gemm<<<(unsigned)std::min(v.ntc_dens, v.sm_count), kGemmThreads, kGemmSmem, st>>>(v.cfgs, v.tc_dens, v.ntc_dens);
   prof_end(prof, st);
-  prof_begin(prof, st, kKNtReduce);
+  prof_begin(prof, st, kKTcFinish);
   const dim3 g((unsigned)std::max<int64_t>(1, (v.tc_max_grid + 127) / 128), (unsigned)v.ntc_list);
   k_tc_dens_finish<<<g, 128, 0, st>>>(v.cfgs, v.tc_list);
   prof_end(prof, st);
@@ -674,12 +797,12 @@ cudaError_t tc_launch_density(const EngineView& v, cudaStream_t st, Prof* prof) 
 
 cudaError_t tc_launch_force(const EngineView& v, cudaStream_t st, Prof* prof) {
   if (v.ntc_list == 0) return cudaSuccess;
-  prof_begin(prof, st, kKCoef);
+  prof_begin(prof, st, kKTcCoef);
   const dim3 g((unsigned)std::max<int64_t>(1, (v.tc_max_grid + 127) / 128), (unsigned)v.ntc_list);
   k_tc_coef<<<g, 128, 0, st>>>(v.cfgs, v.tc_list);
   prof_end(prof, st);
-  prof_begin(prof, st, kKForce);
-  k_tc_gemm<<<(unsigned)v.ntc_force, kGemmThreads, kGemmSmem, st>>>(v.cfgs, v.tc_force);
+  prof_begin(prof, st, kKTcForce);
+  k_tc_gemm<<<(unsigned)std::min(v.ntc_force, v.sm_count), kGemmThreads, kGemmSmem, st>>>(v.cfgs, v.tc_force, v.ntc_force);
   prof_end(prof, st);
   return cudaGetLastError();
 }

@@ -18,3 +18,9 @@ def oracle_mod():
     import oracle
     oracle.build()
     return oracle
+
+
+def launches_per_role(pr: dict, role: str) -> list:
+    """Launch counts of the kernels that do one job in a step, whichever implementation ran it."""
+    names = {"density": ("ntilde", "tc_dens"), "force": ("force", "tc_force")}[role]
+    return [pr[k][1] for k in names if k in pr]
