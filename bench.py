@@ -141,31 +141,52 @@ class Clocks:
         self.samples = []
         self.max_mhz = None
 
-    def _nvml_handle(self):
-        import pynvml
-        import torch
-        pynvml.nvmlInit()
-        p = torch.cuda.get_device_properties(self.device)
-        bus = f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
-        return pynvml, pynvml.nvmlDeviceGetHandleByPciBusId(bus)
+    class _Nvml:
+        """The driver's NVML through ctypes (reads only): SM clock, maximum SM clock, clock-event reasons."""
+        SM = 1  # NVML_CLOCK_SM
 
-    def _poll(self, nv, h):
-        get_reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
-            nv.nvmlDeviceGetCurrentClocksThrottleReasons
+        def __init__(self, device: int):
+            import ctypes
+            import torch
+            self.ct = ctypes
+            self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if self.lib.nvmlInit_v2() != 0:
+                raise OSError("nvmlInit failed")
+            p = torch.cuda.get_device_properties(device)
+            bus = f"{p.pci_domain_id:08x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0".encode()
+            self.h = ctypes.c_void_p()
+            if self.lib.nvmlDeviceGetHandleByPciBusId_v2(bus, ctypes.byref(self.h)) != 0:
+                raise OSError("no NVML device for " + bus.decode())
+            self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+
+        def clock(self, fn="nvmlDeviceGetClockInfo"):
+            v = self.ct.c_uint(0)
+            if getattr(self.lib, fn)(self.h, self.SM, self.ct.byref(v)) != 0:
+                raise OSError(fn)
+            return float(v.value)
+
+        def reasons(self):
+            v = self.ct.c_ulonglong(0)
+            if self.reasons_fn(self.h, self.ct.byref(v)) != 0:
+                raise OSError("clock event reasons")
+            return int(v.value)
+
+    def _poll(self, nv):
         while not self.stop.is_set():
             try:
-                self.samples.append((float(nv.nvmlDeviceGetClockInfo(h, nv.NVML_CLOCK_SM)), int(get_reasons(h))))
-            except Exception:
+                self.samples.append((nv.clock(), nv.reasons()))
+            except OSError:
                 break
             time.sleep(0.001)
 
     def __enter__(self):
         import threading
         try:
-            nv, h = self._nvml_handle()
-            self.max_mhz = float(nv.nvmlDeviceGetMaxClockInfo(h, nv.NVML_CLOCK_SM))
+            nv = self._Nvml(self.device)
+            self.max_mhz = nv.clock("nvmlDeviceGetMaxClockInfo")
             self.stop = threading.Event()
-            self.thread = threading.Thread(target=self._poll, args=(nv, h), daemon=True)
+            self.thread = threading.Thread(target=self._poll, args=(nv,), daemon=True)
             self.thread.start()
             return self
         except Exception:
@@ -400,7 +421,7 @@ def main():
     torch.cuda.synchronize(dev)
     if dist:
         dist.barrier()
-    ctx.prof_enable(True)
+    # timed region: the production path (each step replays the library's captured one-step graph)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with Clocks(dev) as clk:
         torch.cuda.synchronize(dev)
@@ -418,6 +439,12 @@ def main():
         t_wall = time.perf_counter() - t_wall
     step_ms = [a.elapsed_time(b) for a, b in ev]
     tot_ms = sum(step_ms)
+    # per-kernel device times: the same number of steps again with the library's event profiler (direct
+    # launches, an event pair around every kernel on the launching stream), L2 flushed between steps
+    ctx.prof_enable(True)
+    for i in range(args.steps):
+        flush.zero_()
+        step()
     prof = ctx.prof_read()
     ctx.prof_enable(False)
     tot_ms = max_over_ranks(tot_ms, dist, device=f"cuda:{dev}")

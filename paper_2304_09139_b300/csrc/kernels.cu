@@ -23,6 +23,7 @@
 #include <algorithm>
 
 #include "fx.cuh"
+#include "reduce.cuh"
 #include "ssh_internal.h"
 
 #define SSH_TABLE_QUAL __device__
@@ -370,21 +371,6 @@ __global__ void __launch_bounds__(kNtThreads) k_ntilde_fx(const CfgDev* __restri
   }
 }
 
-struct RedPart {  // per-block partials of the density reduction
-  double phi_hi, phi_lo, a2max_hi, a2max_lo, cmax, pad0, pad1, pad2;
-};
-
-__device__ __forceinline__ void red_combine(RedPart& a, const RedPart& b) {
-  dd s = dd_add(dd_make(a.phi_hi, a.phi_lo), dd_make(b.phi_hi, b.phi_lo));
-  a.phi_hi = s.hi;
-  a.phi_lo = s.lo;
-  if (dd_gt(dd_make(b.a2max_hi, b.a2max_lo), dd_make(a.a2max_hi, a.a2max_lo))) {
-    a.a2max_hi = b.a2max_hi;
-    a.a2max_lo = b.a2max_lo;
-  }
-  a.cmax = fmax(a.cmax, b.cmax);
-}
-
 constexpr int kRedThreads = 256;
 
 __device__ __forceinline__ void block_reduce(RedPart& v, RedPart* sh) {
@@ -407,6 +393,7 @@ template <class P>
 __global__ void __launch_bounds__(kRedThreads) k_nt_reduce(const CfgDev* __restrict__ cfgs, const int* __restrict__ list) {
   const CfgDev& c = cfgs[list[blockIdx.y]];
   if (stopped(c) || (int)blockIdx.x >= c.nblk) return;  // uniform per block
+  if (P::kIdx == SSH_FX && c.tc) return;                 // the tensor-core finish kernel did this
   __shared__ RedPart sh[kRedThreads];
   const int64_t k = (int64_t)blockIdx.x * kRedThreads + threadIdx.x;
   const int64_t M = c.M;
@@ -433,13 +420,15 @@ __global__ void __launch_bounds__(kRedThreads) k_nt_reduce(const CfgDev* __restr
 }
 
 // scal[kScPhiHi..] as listed in ssh_internal.h.  Scale exponent e: |C|, |S| < 2^(e-1).  Grid (1, configs).
-__global__ void __launch_bounds__(kRedThreads) k_finalize(const CfgDev* __restrict__ cfgs, const int* __restrict__ list) {
+__global__ void __launch_bounds__(kRedThreads) k_finalize(const CfgDev* __restrict__ cfgs, const int* __restrict__ list,
+                                                         int prec) {
   const CfgDev& c = cfgs[list[blockIdx.y]];
   if (stopped(c)) return;
   __shared__ RedPart sh[kRedThreads];
   const RedPart* blk = reinterpret_cast<const RedPart*>(c.blk);
   RedPart v = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int i = threadIdx.x; i < c.nblk; i += kRedThreads) red_combine(v, blk[i]);
+  const int nb = (prec == SSH_FX && c.tc) ? c.tc_nblk : c.nblk;
+  for (int i = threadIdx.x; i < nb; i += kRedThreads) red_combine(v, blk[i]);
   block_reduce(v, sh);
   if (threadIdx.x == 0) {
     double* scal = c.scal;
@@ -651,10 +640,10 @@ __global__ void k_f_reduce(const CfgDev* __restrict__ cfgs, const int* __restric
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;  // over d * N, [a][j]
   const int64_t nd = (int64_t)c.d * c.N;
   if (i >= nd) return;
+  if (P::kIdx == SSH_FX && c.tc) return;  // the tensor-core force finish kernel did this
   const typename P::RAcc* fpart = reinterpret_cast<const typename P::RAcc*>(c.fpart);
   typename P::RAcc s = fpart[i];
-  const int nsplit = (P::kIdx == SSH_FX && c.tc) ? c.tc_fsplit : c.ksplit;
-  for (int k = 1; k < nsplit; k++) P::radd_r(s, fpart[(int64_t)k * nd + i]);
+  for (int k = 1; k < c.ksplit; k++) P::radd_r(s, fpart[(int64_t)k * nd + i]);
   dd f = dd_mul(P::r_to_dd(s), c.pref);
   const int e = P::kIdx == SSH_FX ? (int)c.scal[kScScaleExp] : 0;
   c.F_hi[i] = ldexp(f.hi, e);
@@ -714,18 +703,22 @@ static cudaError_t launch_prec(const EngineView& v, bool want_force, cudaStream_
       k_ntilde<P><<<grid, kNtThreads, v.nt_smem, st>>>(v.cfgs, v.nt, v.nnt, v.counters);
     prof_end(prof, st);
   }
-  const dim3 gr((unsigned)std::max(1, v.maxblk), (unsigned)v.nlist);
-  prof_begin(prof, st, kKNtReduce);
-  k_nt_reduce<P><<<gr, kRedThreads, 0, st>>>(v.cfgs, v.list);
-  prof_end(prof, st);
+  if (v.nlist > v.ntc_list) {
+    const dim3 gr((unsigned)std::max(1, v.maxblk), (unsigned)v.nlist);
+    prof_begin(prof, st, kKNtReduce);
+    k_nt_reduce<P><<<gr, kRedThreads, 0, st>>>(v.cfgs, v.list);
+    prof_end(prof, st);
+  }
   prof_begin(prof, st, kKFinalize);
-  k_finalize<<<dim3(1, (unsigned)v.nlist), kRedThreads, 0, st>>>(v.cfgs, v.list);
+  k_finalize<<<dim3(1, (unsigned)v.nlist), kRedThreads, 0, st>>>(v.cfgs, v.list, P::kIdx);
   prof_end(prof, st);
   if (want_force) {
-    const dim3 gc((unsigned)std::max<int64_t>(1, (v.maxM + 255) / 256), (unsigned)v.nlist);
-    prof_begin(prof, st, kKCoef);
-    k_coef<P><<<gc, 256, 0, st>>>(v.cfgs, v.list);
-    prof_end(prof, st);
+    if (v.nlist > v.ntc_list) {  // members that use these coefficients (the tensor-core path builds its own)
+      const dim3 gc((unsigned)std::max<int64_t>(1, (v.maxM + 255) / 256), (unsigned)v.nlist);
+      prof_begin(prof, st, kKCoef);
+      k_coef<P><<<gc, 256, 0, st>>>(v.cfgs, v.list);
+      prof_end(prof, st);
+    }
     if constexpr (P::kIdx == SSH_FX) {
       cudaError_t te = tc_launch_force(v, st, prof);
       if (te != cudaSuccess) return te;
@@ -740,10 +733,16 @@ static cudaError_t launch_prec(const EngineView& v, bool want_force, cudaStream_
         k_force<P><<<grid, kForceThreads, 0, st>>>(v.cfgs, v.fi, v.nfi, v.counters + 1);
       prof_end(prof, st);
     }
-    const dim3 gf((unsigned)std::max<int64_t>(1, (v.maxND + 255) / 256), (unsigned)v.nlist);
-    prof_begin(prof, st, kKFReduce);
-    k_f_reduce<P><<<gf, 256, 0, st>>>(v.cfgs, v.list);
-    prof_end(prof, st);
+    if (v.nlist > v.ntc_list) {
+      const dim3 gf((unsigned)std::max<int64_t>(1, (v.maxND + 255) / 256), (unsigned)v.nlist);
+      prof_begin(prof, st, kKFReduce);
+      k_f_reduce<P><<<gf, 256, 0, st>>>(v.cfgs, v.list);
+      prof_end(prof, st);
+    }
+    if constexpr (P::kIdx == SSH_FX) {
+      cudaError_t te = tc_launch_force_finish(v, st, prof);
+      if (te != cudaSuccess) return te;
+    }
   }
   return cudaGetLastError();
 }
@@ -853,12 +852,13 @@ cudaError_t plan_upload(Ctx* c) {
   for (DevBuf* b : {&c->C_hi, &c->C_lo, &c->S_hi, &c->S_lo})
     if ((e = dev_alloc(b, (size_t)c->M * 8)) != cudaSuccess) return e;
   if ((e = dev_alloc(&c->coef, (size_t)c->M * kTabBytes)) != cudaSuccess) return e;
-  c->n_red_blocks = (int)((c->M + kRedThreads - 1) / kRedThreads);
-  if ((e = dev_alloc(&c->blk, (size_t)std::max(1, c->n_red_blocks) * sizeof(RedPart))) != cudaSuccess) return e;
-  if ((e = dev_alloc(&c->scal, sizeof(double) * kScCount)) != cudaSuccess) return e;
   if ((e = tc_setup(c)) != cudaSuccess) return e;
-  const int fslots = std::max(ks, c->tc.on ? 2 * c->tc.CTf : 1);
-  if ((e = dev_alloc(&c->fpart, (size_t)fslots * nd * kRAccBytes)) != cudaSuccess) return e;
+  c->n_red_blocks = (int)((c->M + kRedThreads - 1) / kRedThreads);
+  if ((e = dev_alloc(&c->blk, (size_t)std::max(std::max(1, c->n_red_blocks), tc_finish_blocks(*c)) * sizeof(RedPart))) !=
+      cudaSuccess)
+    return e;
+  if ((e = dev_alloc(&c->scal, sizeof(double) * kScCount)) != cudaSuccess) return e;
+  if ((e = dev_alloc(&c->fpart, (size_t)ks * nd * kRAccBytes)) != cudaSuccess) return e;
   if ((e = dev_alloc(&c->F_hi, nd * 8)) != cudaSuccess) return e;
   if ((e = dev_alloc(&c->F_lo, nd * 8)) != cudaSuccess) return e;
   cudaMemsetAsync(c->scal.p, 0, sizeof(double) * kScCount, st);
@@ -885,7 +885,6 @@ size_t device_footprint(const Ctx& c) {
   b += c.nt.slots.size() * sizeof(NtSlot) + c.nt.g_rows.size() * 4 + c.fp.cols.size() * sizeof(FCol);
   b += c.tl.rows.size() * sizeof(TabRow) + 64 * 1024;          // small buffers and allocation granularity
   b += tc_footprint(c);                                        // tensor-core digit slices and partials
-  if (c.tc.on) b += (size_t)2 * c.tc.CTf * nd * kRAccBytes;
   return b;
 }
 

@@ -85,11 +85,12 @@ struct CfgDev {
   double *F_hi, *F_lo;
   dd pref, inv_L;
   // tensor-core fixed-point path (tc.cu); tc = 0 when the configuration uses the integer-pipe kernels
-  int tc, tc_R1, tc_R2, tc_RT, tc_CTd, tc_PT, tc_KSf, tc_CTf, tc_bexp, tc_ksplit, tc_fsplit, tc_gs, tc_ts;
+  int tc, tc_R1, tc_R2, tc_RT, tc_CTd, tc_PT, tc_KSf, tc_CTf, tc_bexp, tc_ksplit, tc_nblk, tc_gs, tc_ts;
   int64_t tc_KS;
   uint8_t *tc_dA, *tc_dB, *tc_fA, *tc_fB;
   void* tc_a1;
-  long long* tc_part;
+  long long* tc_acc;   // density level groups per tile [tile][3][32][128], summed by integer atomics
+  long long* tc_facc;  // force limbs [axis][3][N], summed by integer atomics
   const int32_t* tc_kmap;
   const int32_t* tc_tilemap;
   int* tc_err;
@@ -195,7 +196,7 @@ struct TcPlan {
   std::vector<int32_t> tiles;    // density tiles in use: rt * CTd + ct
   std::vector<int32_t> tilemap;  // [RT * CTd] -> index into tiles, or -1
   std::vector<int32_t> kmap;     // [(R1 + 1) (2 R2 + 1)] internal index of (n1, n2), or -1
-  DevBuf dA, dB, fA, fB, a1, part, kmap_d, tilemap_d, err;
+  DevBuf dA, dB, fA, fB, a1, acc, facc, kmap_d, tilemap_d, err;
 };
 
 struct Ctx {
@@ -266,6 +267,7 @@ enum { kScPhiHi = 0, kScPhiLo, kScSmaxHi, kScSmaxLo, kScCmax, kScScaleExp, kScA2
 
 // tc.cu (tensor-core fixed-point path, d = 2)
 bool tc_eligible(const Ctx& c);
+int tc_finish_blocks(const Ctx& c);  // blocks of the density finish kernel (its reduction partials)
 cudaError_t tc_setup(Ctx* c);
 void tc_free(Ctx* c);
 size_t tc_footprint(const Ctx& c);
@@ -273,6 +275,7 @@ void tc_fill_cfgdev(const Ctx* c, CfgDev* g);
 void tc_items(const Ctx* c, int i, std::vector<TwItem>& prep, std::vector<TcItem>& dens, std::vector<TcItem>& force);
 cudaError_t tc_launch_density(const EngineView& v, cudaStream_t st, Prof* prof);
 cudaError_t tc_launch_force(const EngineView& v, cudaStream_t st, Prof* prof);
+cudaError_t tc_launch_force_finish(const EngineView& v, cudaStream_t st, Prof* prof);
 
 // kernels.cu
 cudaError_t plan_upload(Ctx* c);

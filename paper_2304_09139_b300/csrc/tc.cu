@@ -32,6 +32,7 @@
 #include <cmath>
 
 #include "fx.cuh"
+#include "reduce.cuh"
 #include "ssh_internal.h"
 #include "tc.cuh"
 
@@ -44,10 +45,13 @@ using namespace tc;
 
 namespace {
 
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;                      // four per TMEM lane quadrant
+constexpr int kEpiCols = kTileN / (kEpiWarps / 4);  // accumulator columns per epilogue warp (8)
 constexpr int kGemmThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
 constexpr long long kWaitLimit = 2000000000LL;     // clock cycles (about one second) for any single wait
-constexpr size_t kGemmSmem = (size_t)kStages * kStageBytes;
+constexpr size_t kRedBytes = (size_t)(kEpiWarps / 4) * kTileM * 2 * 16;  // force partials of the column blocks
+constexpr size_t kGemmSmem = (size_t)kStages * kStageBytes + kRedBytes;
+constexpr int kFinThreads = 64;
 
 __device__ __forceinline__ bool stopped(const CfgDev& c) { return c.run && *c.run; }
 
@@ -130,6 +134,21 @@ __device__ __forceinline__ q160 i192_to_q160_shl(const i192& a, int sh) {
   return r;
 }
 
+// 2^e as a double (normal range)
+__device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
+
+// X 2^-S of a 192-bit integer with |X| < 2^150, as a double-double.  X = h 2^106 + m 2^53 + l with l, m in
+// [0, 2^53) and h signed are each exact in binary64; the two-sum of the top two pieces is exact, and the last
+// piece lies below the unit of the result's low word.
+__device__ __forceinline__ dd i192_to_dd(const i192& x, int S) {
+  const unsigned long long mask = (1ull << 53) - 1;
+  const unsigned long long l = x.w[0] & mask;
+  const unsigned long long m = ((x.w[0] >> 53) | (x.w[1] << 11)) & mask;
+  const long long h = (long long)((x.w[1] >> 42) | (x.w[2] << 22));
+  const dd s = two_sum((double)h * pow2(106 - S), (double)m * pow2(53 - S));
+  return fast_two_sum(s.hi, s.lo + (double)l * pow2(-S));
+}
+
 // round(a / 2^sh) of a Q34.126 accumulator, for results with |.| <= 2^104; sh may be negative (left shift)
 __device__ __forceinline__ __int128 q160_shr_round(const q160& a, int sh) {
   i192 t;  // the 160-bit value sign-extended to 192 bits
@@ -173,7 +192,8 @@ namespace {
 
 constexpr int kPrepThreads = 256;
 constexpr int kPrepParticles = 32;  // particles per CTA
-constexpr int kPrepM = 64;          // powers per pass (shared-memory staging of their fixed-point values)
+constexpr int kPrepM = 96;          // powers per pass (shared-memory staging of their fixed-point values)
+constexpr int kPrepBlocks = kPrepThreads / kPrepParticles;  // power blocks per particle and pass: one per thread
 constexpr size_t kPrepSmem = (size_t)kPrepM * 2 * kPrepParticles * 16 + kPrepParticles * sizeof(fxc);
 
 // Eight values X (|X| <= 2^104) -> their 15 balanced digits as one 16-byte row (8 bf16) per digit slice.
@@ -235,17 +255,18 @@ __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restri
   __syncthreads();
   for (int m0 = 0; m0 <= R; m0 += kPrepM) {
     const int mcount = min(kPrepM, R + 1 - m0);
-    // phase 1: tasks (particle, block of 16 powers)
-    const int nblk = (mcount + 15) / 16;
-    for (int task = tid; task < nblk * kPrepParticles; task += kPrepThreads) {
+    // phase 1: one task per thread, (particle, block of bl powers): an exact-phase anchor, then multiplies
+    const int bl = (mcount + kPrepBlocks - 1) / kPrepBlocks;
+    {
+      const int task = tid;
       const int jl = task % kPrepParticles, b = task / kPrepParticles;
       const int64_t j = j0 + jl;
-      const int mb = m0 + 16 * b;
+      const int mb = m0 + bl * b;
       fxc z = PolFXZero();
-      const bool live = j < N;
+      const bool live = j < N && mb < m0 + mcount;
       if (live) z = phasor_turn(turn_times(turns_from_dd(c.s_hi[axis * N + j], c.s_lo[axis * N + j]), mb));
       const fxc e1 = e1s[jl];
-      for (int i = 0; i < 16 && mb + i < m0 + mcount; i++) {
+      for (int i = 0; i < bl && mb + i < m0 + mcount; i++) {
         if (i > 0 && live) z = fxc_mul(z, e1);
         const int ml = mb + i - m0;
         Xs[(ml * 2 + 0) * kPrepParticles + jl] = fixed104(z.re);
@@ -307,6 +328,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
                                                               const TcItem* __restrict__ items, int n_items) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint64_t bar_full[kStages], bar_empty[kStages], bar_acc_full, bar_acc_empty, bar_drain;
+  __shared__ uint64_t bar_red_full, bar_red_free;  // force partials of a lane quadrant: written / consumed
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -318,6 +340,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
     mbar_init(&bar_acc_full, 1);
     mbar_init(&bar_acc_empty, kEpiWarps);
     mbar_init(&bar_drain, 1);
+    mbar_init(&bar_red_full, kEpiWarps - kEpiWarps / 4);  // the warps of column blocks 1..3
+    mbar_init(&bar_red_free, kEpiWarps / 4);               // the warps of column block 0
     abort_sh = 0;
     mbar_fence_init();
   }
@@ -419,23 +443,24 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
       if (!mbar_wait(&bar_drain, 0, kWaitLimit, nullptr)) *abort_flag = 1;
     }
   } else {
-    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 and accumulator columns 16 h .. 16 h + 15
-    const int q = warp & 3, h = (warp - 2) >> 2;
+    // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 and accumulator columns 8 hq .. 8 hq + 7
+    const int q = warp & 3, hq = (warp - 2) >> 2;
     const int row = 32 * q + lane;
-    const uint32_t trow = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * h);
+    const uint32_t trow = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(kEpiCols * hq);
+    __int128* red = reinterpret_cast<__int128*>(smem + (size_t)kStages * kStageBytes);  // [hq][row][2]
     // sum over the five levels of a group of (bits - magic) 2^(7 (4 - l)): the magic part, subtracted once
     constexpr long long kGroupBias = (long long)kMagicBits * ((1ll << 28) + (1ll << 21) + (1ll << 14) + (1ll << 7) + 1);
-    long long gc = 0;
+    long long gc = 0, fc = 0;  // chunks read, force items finished (all items of this CTA)
     bool stop = false;
     for (int item = blockIdx.x; item < n_items && !stop; item += gridDim.x) {
       const TcItem it = items[item];
       const CfgDev& c = cfgs[it.cfg];
       if (stopped(c)) continue;
-      long long st[3][16];
+      long long st[3][kEpiCols];
 #pragma unroll
       for (int g = 0; g < 3; g++)
 #pragma unroll
-        for (int i = 0; i < 16; i++) st[g][i] = 0;
+        for (int i = 0; i < kEpiCols; i++) st[g][i] = 0;
       const int nch = (it.nks + kChunkSteps - 1) / kChunkSteps;
       for (int ch = 0; ch < nch; ch++, gc++) {
         // the warp leaves together (tcgen05.ld is warp-collective)
@@ -449,20 +474,20 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
         tc_fence_after();
 #pragma unroll
         for (int g = 0; g < 3; g++) {
-          long long t[16];
+          long long t[kEpiCols];
 #pragma unroll
-          for (int i = 0; i < 16; i++) t[i] = -kGroupBias;
+          for (int i = 0; i < kEpiCols; i++) t[i] = -kGroupBias;
 #pragma unroll
           for (int l = 0; l < 5; l++) {
-            uint32_t r[16];
-            tmem_ld16(trow + (uint32_t)((5 * g + l) * kTileN), r);
+            uint32_t r[kEpiCols];
+            tmem_ld8(trow + (uint32_t)((5 * g + l) * kTileN), r);
             tmem_ld_wait();
 #pragma unroll
-            for (int i = 0; i < 16; i++)
+            for (int i = 0; i < kEpiCols; i++)
               t[i] += (long long)(uint32_t)__float_as_int(__uint_as_float(r[i]) + kMagic) * (1ll << (7 * (4 - l)));
           }
 #pragma unroll
-          for (int i = 0; i < 16; i++) st[g][i] += t[i];
+          for (int i = 0; i < kEpiCols; i++) st[g][i] += t[i];
         }
         tc_fence_before();
         __syncwarp();
@@ -470,52 +495,84 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
       }
       if (stop) break;
       if (it.kind == 0) {
-        // level groups of every output: R' = st0 2^70 + st1 2^35 + st2 (value = R' 2^-110)
-        long long* out = c.tc_part + (size_t)it.slot * (3 * kTileN * kTileM);
+        // level groups of every output, R' = st0 2^70 + st1 2^35 + st2 (value = R' 2^-110), added into the
+        // tile's accumulator: integer addition, so the K ranges combine exactly in any order
+        unsigned long long* out = reinterpret_cast<unsigned long long*>(c.tc_acc) + (size_t)it.slot * (3 * kTileN * kTileM);
 #pragma unroll
         for (int g = 0; g < 3; g++)
 #pragma unroll
-          for (int i = 0; i < 16; i++) out[((size_t)g * kTileN + 16 * h + i) * kTileM + row] = st[g][i];
+          for (int i = 0; i < kEpiCols; i++)
+            atomicAdd(out + ((size_t)g * kTileN + kEpiCols * hq + i) * kTileM + row, (unsigned long long)st[g][i]);
       } else {
+        // two n1 values per warp, columns (Re G, Im G, Re G', Im G') each.  G~ = R' 2^-110 is taken as R' 2^gs
+        // (|.| < 2^126); the top halves of a * G are value 2^(108 + gs), shifted to value 2^ts.
         const int64_t j = (int64_t)it.a * kTileM + row;
-        if (j < c.N) {
-          // four n1 values per half tile, columns (Re G, Im G, Re G', Im G') each.  G~ = R' 2^-110 is taken
-          // as R' 2^gs (|.| < 2^126); the top halves of a * G are value 2^(108 + gs), shifted to value 2^ts.
-          const int gsh = c.tc_gs, tsh = 108 + c.tc_gs - c.tc_ts;
-          __int128 F1 = 0, F2 = 0;  // value 2^ts
+        const int gsh = c.tc_gs, tsh = 108 + c.tc_gs - c.tc_ts;
+        __int128 F1 = 0, F2 = 0;  // value 2^ts
 #pragma unroll
-          for (int v = 0; v < 4; v++) {
-            const int n1 = it.b * 8 + h * 4 + v;
-            if (n1 > c.tc_R1) continue;
-            q128 gcol[4];
+        for (int v = 0; v < kEpiCols / 4; v++) {
+          const int n1 = it.b * (kTileN / 4) + hq * (kEpiCols / 4) + v;
+          if (n1 > c.tc_R1 || j >= c.N) continue;
+          q128 gcol[4];
 #pragma unroll
-            for (int g4 = 0; g4 < 4; g4++) {
-              const int i = 4 * v + g4;
-              const __int128 R = ((__int128)st[0][i] << 70) + ((__int128)st[1][i] << 35) + (__int128)st[2][i];
-              gcol[g4] = q128_from_i128(R << gsh);
-            }
-            const fxc a = reinterpret_cast<const fxc*>(c.tc_a1)[(int64_t)n1 * c.N + j];
-            uint32_t p[5], r2[5];
-            // Im(a G) = Re a Im G + Im a Re G
-            smul_top(a.re, gcol[1], p);
-            smul_top(a.im, gcol[0], r2);
-            __int128 T = (q128_to_i128(q128{{p[1], p[2], p[3], p[4]}}) + q128_to_i128(q128{{r2[1], r2[2], r2[3], r2[4]}})) >> tsh;
-            F1 += T * (__int128)n1;
-            smul_top(a.re, gcol[3], p);
-            smul_top(a.im, gcol[2], r2);
-            T = (q128_to_i128(q128{{p[1], p[2], p[3], p[4]}}) + q128_to_i128(q128{{r2[1], r2[2], r2[3], r2[4]}})) >> tsh;
-            F2 += T;
+          for (int g4 = 0; g4 < 4; g4++) {
+            const int i = 4 * v + g4;
+            const __int128 R = ((__int128)st[0][i] << 70) + ((__int128)st[1][i] << 35) + (__int128)st[2][i];
+            gcol[g4] = q128_from_i128(R << gsh);
           }
-          q160* fpart = reinterpret_cast<q160*>(c.fpart);
-          const int slot = 2 * it.b + h;
-          i192 a1, a2;
-          i192_zero(a1);
-          i192_zero(a2);
-          i192_add_shl(a1, F1, 126 - c.tc_ts);                // Q34.126, in units of 2^e
-          i192_add_shl(a2, F2, 126 - c.tc_ts + c.tc_bexp);    // G' was scaled by 2^-(e + bexp)
-          fpart[((int64_t)slot * 2 + 0) * c.N + j] = i192_to_q160_shl(a1, 0);
-          fpart[((int64_t)slot * 2 + 1) * c.N + j] = i192_to_q160_shl(a2, 0);
+          const fxc a = reinterpret_cast<const fxc*>(c.tc_a1)[(int64_t)n1 * c.N + j];
+          uint32_t p[5], r2[5];
+          // Im(a G) = Re a Im G + Im a Re G
+          smul_top(a.re, gcol[1], p);
+          smul_top(a.im, gcol[0], r2);
+          __int128 T = (q128_to_i128(q128{{p[1], p[2], p[3], p[4]}}) + q128_to_i128(q128{{r2[1], r2[2], r2[3], r2[4]}})) >> tsh;
+          F1 += T * (__int128)n1;
+          smul_top(a.re, gcol[3], p);
+          smul_top(a.im, gcol[2], r2);
+          T = (q128_to_i128(q128{{p[1], p[2], p[3], p[4]}}) + q128_to_i128(q128{{r2[1], r2[2], r2[3], r2[4]}})) >> tsh;
+          F2 += T;
         }
+        // The four column blocks of one lane quadrant sum through shared memory: blocks 1..3 publish their
+        // partials (red_full), block 0 adds them, writes the force partial and hands the buffer back (red_free).
+        if (hq != 0) {
+          const bool ok = fc == 0 || mbar_wait(&bar_red_free, (uint32_t)((fc - 1) & 1), kWaitLimit, abort_flag);
+          if (!__all_sync(0xffffffffu, ok)) {
+            *abort_flag = 1;
+            if (lane == 0) atomicOr(c.tc_err, 32);
+            break;
+          }
+          red[((size_t)hq * kTileM + row) * 2 + 0] = F1;
+          red[((size_t)hq * kTileM + row) * 2 + 1] = F2;
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bar_red_full);
+        } else {
+          const bool ok = mbar_wait(&bar_red_full, (uint32_t)(fc & 1), kWaitLimit, abort_flag);
+          if (!__all_sync(0xffffffffu, ok)) {
+            *abort_flag = 1;
+            if (lane == 0) atomicOr(c.tc_err, 64);
+            break;
+          }
+#pragma unroll
+          for (int b2 = 1; b2 < kEpiWarps / 4; b2++) {
+            F1 += red[((size_t)b2 * kTileM + row) * 2 + 0];
+            F2 += red[((size_t)b2 * kTileM + row) * 2 + 1];
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&bar_red_free);
+          if (j < c.N) {
+            // F = L2 2^88 + L1 2^44 + L0 (L0, L1 in [0, 2^44)): the limbs of all column tiles add up exactly
+            unsigned long long* fa = reinterpret_cast<unsigned long long*>(c.tc_facc);
+            const unsigned long long m44 = (1ull << 44) - 1;
+#pragma unroll
+            for (int a = 0; a < 2; a++) {
+              const __int128 F = a == 0 ? F1 : F2;
+              atomicAdd(fa + ((size_t)a * 3 + 0) * c.N + j, (unsigned long long)F & m44);
+              atomicAdd(fa + ((size_t)a * 3 + 1) * c.N + j, (unsigned long long)(F >> 44) & m44);
+              atomicAdd(fa + ((size_t)a * 3 + 2) * c.N + j, (unsigned long long)(long long)(F >> 88));
+            }
+          }
+        }
+        fc++;
       }
     }
   }
@@ -530,57 +587,109 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
 
 // ------------------------------------------------------------------------------------------------ finish
 
-// grid ((R1 + 1) (R2 + 1) / 128 blocks, tensor-core members): n~(n1, m), n~(n1, -m) from the four real products
-__global__ void k_tc_dens_finish(const CfgDev* __restrict__ cfgs, const int* __restrict__ list) {
+// grid (finish blocks, tensor-core members), 64 threads: n~(n1, m), n~(n1, -m) from the four real products of
+// the tile accumulator (which it clears for the next evaluation), as exact Q34.126 values (for the force
+// coefficients) and as dd (C, S), with the block's Phi / max |n~|^2 / max |C|, |S| partials.
+__global__ void __launch_bounds__(kFinThreads) k_tc_dens_finish(const CfgDev* __restrict__ cfgs,
+                                                                const int* __restrict__ list) {
+  const CfgDev& c = cfgs[list[blockIdx.y]];
+  if (stopped(c) || (int)blockIdx.x >= c.tc_nblk) return;  // uniform per block
+  RedPart v = {0, 0, 0, 0, 0, 0, 0, 0};
+  const int W1 = c.tc_R1 + 1;
+  const int64_t idx = (int64_t)blockIdx.x * kFinThreads + threadIdx.x;
+  if (idx < (int64_t)W1 * (c.tc_R2 + 1)) {
+    const int n1 = (int)(idx % W1), m = (int)(idx / W1);  // n1 fastest: neighbours read neighbouring rows
+    const int span = 2 * c.tc_R2 + 1;
+    const int kp = c.tc_kmap[(int64_t)n1 * span + (c.tc_R2 + m)];
+    const int km = m > 0 ? c.tc_kmap[(int64_t)n1 * span + (c.tc_R2 - m)] : -1;
+    const int r = 2 * n1, col = 2 * m;
+    const int ti = (kp >= 0 || km >= 0) ? c.tc_tilemap[(r >> 7) * c.tc_CTd + (col >> 5)] : -1;
+    if (ti >= 0) {
+      const int rr = r & 127, cc = col & 31;
+      long long* acc = c.tc_acc + (size_t)ti * (3 * kTileN * kTileM);
+      long long P[4][3];  // 0 = cos cos, 1 = cos sin, 2 = sin cos, 3 = sin sin
+#pragma unroll
+      for (int p = 0; p < 2; p++)
+#pragma unroll
+        for (int qq = 0; qq < 2; qq++)
+#pragma unroll
+          for (int g = 0; g < 3; g++) {
+            long long* e = acc + ((size_t)g * kTileN + cc + qq) * kTileM + rr + p;
+            P[2 * p + qq][g] = *e;
+            *e = 0;
+          }
+      FxAcc* part = reinterpret_cast<FxAcc*>(c.part);
+      // C = P_cc + ss_sign P_ss, S = cs_sign P_cs + P_sc
+      auto emit = [&](int k, int ss_sign, int cs_sign) {
+        i192 C, S;
+        i192_zero(C);
+        i192_zero(S);
+#pragma unroll
+        for (int g = 0; g < 3; g++) {
+          const int sh = 70 - 35 * g;
+          i192_add_shl(C, (__int128)P[0][g] + (ss_sign > 0 ? (__int128)P[3][g] : -(__int128)P[3][g]), sh);
+          i192_add_shl(S, (cs_sign > 0 ? (__int128)P[1][g] : -(__int128)P[1][g]) + (__int128)P[2][g], sh);
+        }
+        FxAcc o;
+        o.re = i192_to_q160_shl(C, 16);  // value 2^-110 -> Q34.126
+        o.im = i192_to_q160_shl(S, 16);
+        part[k] = o;
+        const dd cd = i192_to_dd(C, 110), sd = i192_to_dd(S, 110);
+        c.C_hi[k] = cd.hi;
+        c.C_lo[k] = cd.lo;
+        c.S_hi[k] = sd.hi;
+        c.S_lo[k] = sd.lo;
+        RedPart t;
+        const dd a2 = dd_add(dd_sqr(cd), dd_sqr(sd));
+        t.phi_hi = a2.hi;
+        t.phi_lo = a2.lo;
+        t.a2max_hi = a2.hi;
+        t.a2max_lo = a2.lo;
+        t.cmax = fmax(fabs(cd.hi), fabs(sd.hi));
+        red_combine(v, t);
+      };
+      if (kp >= 0) emit(kp, -1, +1);  // n~(n1, m) = (P_cc - P_ss) + i (P_cs + P_sc)
+      if (km >= 0) emit(km, +1, -1);  // n~(n1, -m) = (P_cc + P_ss) + i (P_sc - P_cs)
+    }
+  }
+  red_warp(v);
+  __shared__ RedPart sh[kFinThreads / 32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    RedPart a = sh[0];
+#pragma unroll
+    for (int w = 1; w < kFinThreads / 32; w++) red_combine(a, sh[w]);
+    reinterpret_cast<RedPart*>(c.blk)[blockIdx.x] = a;
+  }
+}
+
+// grid (coordinate blocks, tensor-core members), 64 threads: F[a][j] from the force limbs (which it clears),
+// times 4 pi / L and the power-of-two scale of the coefficients
+__global__ void __launch_bounds__(kFinThreads) k_tc_force_finish(const CfgDev* __restrict__ cfgs,
+                                                                 const int* __restrict__ list) {
   const CfgDev& c = cfgs[list[blockIdx.y]];
   if (stopped(c)) return;
-  const int W2 = c.tc_R2 + 1;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)(c.tc_R1 + 1) * W2) return;
-  const int n1 = (int)(idx / W2), m = (int)(idx % W2);
-  const int span = 2 * c.tc_R2 + 1;
-  const int kp = c.tc_kmap[(int64_t)n1 * span + (c.tc_R2 + m)];
-  const int km = m > 0 ? c.tc_kmap[(int64_t)n1 * span + (c.tc_R2 - m)] : -1;
-  if (kp < 0 && km < 0) return;
-  const int r = 2 * n1, col = 2 * m;
-  const int ti = c.tc_tilemap[(r >> 7) * c.tc_CTd + (col >> 5)];
-  if (ti < 0) return;
-  const int rr = r & 127, cc = col & 31;
-  // group sums of P_pq over the K ranges, fixed order
-  __int128 Pg[4][3];
-#pragma unroll
-  for (int x = 0; x < 4; x++)
-#pragma unroll
-    for (int g = 0; g < 3; g++) Pg[x][g] = 0;
-  for (int sp = 0; sp < c.tc_ksplit; sp++) {
-    const long long* src = c.tc_part + (size_t)(ti * c.tc_ksplit + sp) * (3 * kTileN * kTileM);
-#pragma unroll
-    for (int p = 0; p < 2; p++)
-#pragma unroll
-      for (int qq = 0; qq < 2; qq++)
-#pragma unroll
-        for (int g = 0; g < 3; g++) Pg[2 * p + qq][g] += src[((size_t)g * kTileN + cc + qq) * kTileM + rr + p];
-  }
-  // P index: 0 = cc, 1 = cs, 2 = sc, 3 = ss
-  FxAcc* part = reinterpret_cast<FxAcc*>(c.part);
-  // C = P_cc + ss_sign P_ss, S = cs_sign P_cs + P_sc
-  auto emit = [&](int k, int ss_sign, int cs_sign) {
-    i192 C, S;
-    i192_zero(C);
-    i192_zero(S);
-#pragma unroll
-    for (int g = 0; g < 3; g++) {
-      const int sh = 70 - 35 * g;
-      i192_add_shl(C, Pg[0][g] + (ss_sign > 0 ? Pg[3][g] : -Pg[3][g]), sh);
-      i192_add_shl(S, (cs_sign > 0 ? Pg[1][g] : -Pg[1][g]) + Pg[2][g], sh);
-    }
-    FxAcc o;
-    o.re = i192_to_q160_shl(C, 16);  // value 2^-110 -> Q34.126
-    o.im = i192_to_q160_shl(S, 16);
-    part[k] = o;
-  };
-  if (kp >= 0) emit(kp, -1, +1);  // n~(n1, m) = (P_cc - P_ss) + i (P_cs + P_sc)
-  if (km >= 0) emit(km, +1, -1);  // n~(n1, -m) = (P_cc + P_ss) + i (P_sc - P_cs)
+  const int64_t i = (int64_t)blockIdx.x * kFinThreads + threadIdx.x;  // over [a][j]
+  if (i >= 2 * c.N) return;
+  const int a = (int)(i / c.N);
+  const int64_t j = i - (int64_t)a * c.N;
+  long long* fa = c.tc_facc + (size_t)a * 3 * c.N + j;
+  const long long L0 = fa[0], L1 = fa[c.N], L2 = fa[2 * c.N];
+  fa[0] = 0;
+  fa[c.N] = 0;
+  fa[2 * c.N] = 0;
+  i192 X;
+  i192_zero(X);
+  i192_add_shl(X, (__int128)L0, 0);
+  i192_add_shl(X, (__int128)L1, 44);
+  i192_add_shl(X, (__int128)L2, 88);
+  // value = X 2^-ts in units of 2^e (axis 2: of 2^(e + bexp))
+  const int e = (int)c.scal[kScScaleExp];
+  dd f = dd_mul(i192_to_dd(X, c.tc_ts), c.pref);
+  const double sc = pow2(e + (a == 1 ? c.tc_bexp : 0));
+  c.F_hi[i] = f.hi * sc;
+  c.F_lo[i] = f.lo * sc;
 }
 
 // grid ((R1 + 1) (R2 + 1) / 128 blocks, tensor-core members): the force GEMM's coefficient digits
@@ -644,6 +753,11 @@ static cudaError_t tc_dev_alloc(DevBuf* b, size_t bytes, cudaStream_t st) {
 
 bool tc_eligible(const Ctx& c) { return c.d == 2 && c.N >= 1 && c.M >= 1; }
 
+int tc_finish_blocks(const Ctx& c) {
+  if (!c.tc.on) return 0;
+  return (int)(((int64_t)(c.tc.R1 + 1) * (c.tc.R2 + 1) + kFinThreads - 1) / kFinThreads);
+}
+
 // Tile plan and device buffers of one configuration.
 cudaError_t tc_setup(Ctx* c) {
   TcPlan& t = c->tc;
@@ -688,7 +802,8 @@ cudaError_t tc_setup(Ctx* c) {
   if ((e = tc_dev_alloc(&t.fA, (size_t)t.PT * t.KSf * kStageA, st)) != cudaSuccess) return e;
   if ((e = tc_dev_alloc(&t.fB, (size_t)t.CTf * t.KSf * kStageB, st)) != cudaSuccess) return e;
   if ((e = tc_dev_alloc(&t.a1, (size_t)(t.R1 + 1) * c->N * sizeof(fxc), st)) != cudaSuccess) return e;
-  if ((e = tc_dev_alloc(&t.part, (size_t)nt * t.ksplit * 3 * kTileN * kTileM * 8, st)) != cudaSuccess) return e;
+  if ((e = tc_dev_alloc(&t.acc, (size_t)nt * 3 * kTileN * kTileM * 8, st)) != cudaSuccess) return e;
+  if ((e = tc_dev_alloc(&t.facc, (size_t)2 * 3 * c->N * 8, st)) != cudaSuccess) return e;
   if ((e = tc_dev_alloc(&t.kmap_d, t.kmap.size() * 4, st)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(t.kmap_d.p, t.kmap.data(), t.kmap.size() * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return e;
@@ -718,7 +833,7 @@ cudaError_t tc_setup(Ctx* c) {
 
 void tc_free(Ctx* c) {
   TcPlan& t = c->tc;
-  for (DevBuf* b : {&t.dA, &t.dB, &t.fA, &t.fB, &t.a1, &t.part, &t.kmap_d, &t.tilemap_d, &t.err}) {
+  for (DevBuf* b : {&t.dA, &t.dB, &t.fA, &t.fB, &t.a1, &t.acc, &t.facc, &t.kmap_d, &t.tilemap_d, &t.err}) {
     if (b->p) cudaFree(b->p);
     b->p = nullptr;
     b->bytes = 0;
@@ -729,7 +844,7 @@ void tc_free(Ctx* c) {
 size_t tc_footprint(const Ctx& c) {
   const TcPlan& t = c.tc;
   if (!t.on) return 0;
-  return t.dA.bytes + t.dB.bytes + t.fA.bytes + t.fB.bytes + t.a1.bytes + t.part.bytes + t.kmap_d.bytes +
+  return t.dA.bytes + t.dB.bytes + t.fA.bytes + t.fB.bytes + t.a1.bytes + t.acc.bytes + t.facc.bytes + t.kmap_d.bytes +
          t.tilemap_d.bytes;
 }
 
@@ -746,14 +861,15 @@ void tc_fill_cfgdev(const Ctx* c, CfgDev* g) {
   g->tc_CTf = t.CTf;
   g->tc_bexp = t.bexp;
   g->tc_ksplit = t.ksplit;
-  g->tc_fsplit = 2 * t.CTf;
   g->tc_KS = t.KS;
   g->tc_dA = (uint8_t*)t.dA.p;
   g->tc_dB = (uint8_t*)t.dB.p;
   g->tc_fA = (uint8_t*)t.fA.p;
   g->tc_fB = (uint8_t*)t.fB.p;
   g->tc_a1 = t.a1.p;
-  g->tc_part = (long long*)t.part.p;
+  g->tc_acc = (long long*)t.acc.p;
+  g->tc_facc = (long long*)t.facc.p;
+  g->tc_nblk = tc_finish_blocks(*c);
   g->tc_kmap = (const int32_t*)t.kmap_d.p;
   g->tc_tilemap = (const int32_t*)t.tilemap_d.p;
   g->tc_err = (int*)t.err.p;
@@ -771,7 +887,7 @@ void tc_items(const Ctx* c, int i, std::vector<TwItem>& prep, std::vector<TcItem
     const int rt = t.tiles[ti] / t.CTd, ct = t.tiles[ti] % t.CTd;
     for (int sp = 0; sp < t.ksplit; sp++) {
       const int64_t k0 = t.KS * sp / t.ksplit, k1 = t.KS * (sp + 1) / t.ksplit;
-      dens.push_back({i, 0, rt, ct, (int32_t)k0, (int32_t)(k1 - k0), ti * t.ksplit + sp, 0});
+      dens.push_back({i, 0, rt, ct, (int32_t)k0, (int32_t)(k1 - k0), ti, 0});
     }
   }
   for (int pt = 0; pt < t.PT; pt++)
@@ -779,6 +895,15 @@ void tc_items(const Ctx* c, int i, std::vector<TwItem>& prep, std::vector<TcItem
 }
 
 size_t tc_gemm_smem() { return kGemmSmem; }
+
+cudaError_t tc_launch_force_finish(const EngineView& v, cudaStream_t st, Prof* prof) {
+  if (v.ntc_list == 0) return cudaSuccess;
+  prof_begin(prof, st, kKTcFinish);
+  const dim3 g((unsigned)std::max<int64_t>(1, (v.maxND + kFinThreads - 1) / kFinThreads), (unsigned)v.ntc_list);
+  k_tc_force_finish<<<g, kFinThreads, 0, st>>>(v.cfgs, v.tc_list);
+  prof_end(prof, st);
+  return cudaGetLastError();
+}
 
 cudaError_t tc_launch_density(const EngineView& v, cudaStream_t st, Prof* prof) {
   if (v.ntc_list == 0) return cudaSuccess;
@@ -789,8 +914,8 @@ cudaError_t tc_launch_density(const EngineView& v, cudaStream_t st, Prof* prof) 
   k_tc_gemm<<<(unsigned)std::min(v.ntc_dens, v.sm_count), kGemmThreads, kGemmSmem, st>>>(v.cfgs, v.tc_dens, v.ntc_dens);
   prof_end(prof, st);
   prof_begin(prof, st, kKTcFinish);
-  const dim3 g((unsigned)std::max<int64_t>(1, (v.tc_max_grid + 127) / 128), (unsigned)v.ntc_list);
-  k_tc_dens_finish<<<g, 128, 0, st>>>(v.cfgs, v.tc_list);
+  const dim3 g((unsigned)std::max<int64_t>(1, (v.tc_max_grid + kFinThreads - 1) / kFinThreads), (unsigned)v.ntc_list);
+  k_tc_dens_finish<<<g, kFinThreads, 0, st>>>(v.cfgs, v.tc_list);
   prof_end(prof, st);
   return cudaGetLastError();
 }
