@@ -35,6 +35,7 @@ __device__ __forceinline__ FireState* fstate(const CfgDev& c) { return reinterpr
 
 // grid (blocks per member, members)
 __global__ void __launch_bounds__(kFireThreads) k_fire_dots(const CfgDev* __restrict__ cfgs, const int* __restrict__ all) {
+  grid_dep_wait();
   const CfgDev& c = cfgs[all[blockIdx.y]];
   const FireState* fs = fstate(c);
   if (fs->status || (int)blockIdx.x >= c.nb_fire) return;
@@ -60,19 +61,28 @@ __global__ void __launch_bounds__(kFireThreads) k_fire_dots(const CfgDev* __rest
     for (int q = 0; q < 3; q++) c.fdots[q * c.nb_fire + blockIdx.x] = sh[q][0];
 }
 
-// one thread per member
+// one warp per member: the block partials are summed lane-strided in a fixed order, then by a fixed shuffle tree
 __global__ void k_fire_ctrl(const CfgDev* __restrict__ cfgs, const int* __restrict__ all, int n) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  grid_dep_wait();
+  const int i = blockIdx.x;
   if (i >= n) return;
   const CfgDev& c = cfgs[all[i]];
   FireState* fs = fstate(c);
-  if (fs->status) return;
+  if (fs->status) return;  // uniform over the warp
+  const int lane = threadIdx.x;
   double P = 0, f2 = 0, v2 = 0;
-  for (int b = 0; b < c.nb_fire; b++) {  // fixed order
+  for (int b = lane; b < c.nb_fire; b += 32) {
     P += c.fdots[b];
     f2 += c.fdots[c.nb_fire + b];
     v2 += c.fdots[2 * c.nb_fire + b];
   }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    P += __shfl_down_sync(0xffffffffu, P, off);
+    f2 += __shfl_down_sync(0xffffffffu, f2, off);
+    v2 += __shfl_down_sync(0xffffffffu, v2, off);
+  }
+  if (lane != 0) return;
   if (P > 0) {
     fs->zero_v = 0;
     fs->cv = 1.0 - fs->alpha;
@@ -94,6 +104,7 @@ __global__ void k_fire_ctrl(const CfgDev* __restrict__ cfgs, const int* __restri
 
 // grid (coordinate blocks, members)
 __global__ void k_fire_move(const CfgDev* __restrict__ cfgs, const int* __restrict__ all) {
+  grid_dep_wait();
   const CfgDev& c = cfgs[all[blockIdx.y]];
   const FireState* fs = fstate(c);
   if (fs->status) return;
@@ -116,6 +127,7 @@ __global__ void k_fire_move(const CfgDev* __restrict__ cfgs, const int* __restri
 
 // one thread per member
 __global__ void k_fire_accept(const CfgDev* __restrict__ cfgs, const int* __restrict__ all, int n) {
+  grid_dep_wait();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const CfgDev& c = cfgs[all[i]];
@@ -164,6 +176,7 @@ __global__ void k_fire_accept(const CfgDev* __restrict__ cfgs, const int* __rest
 // Undo of a rejected step.  Runs whatever the status, so the state the host reads is the accepted one; a
 // repeated undo restores the same saved copy again.  Grid (coordinate blocks, members).
 __global__ void k_fire_restore(const CfgDev* __restrict__ cfgs, const int* __restrict__ all) {
+  grid_dep_wait();
   const CfgDev& c = cfgs[all[blockIdx.y]];
   if (!fstate(c)->rejected_now) return;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -329,12 +342,16 @@ double fire_phi_tol(const Ctx* c, int prec) {
 cudaError_t fire_step_engine(const Engine* e, cudaStream_t st, Prof* prof) {
   if (e->nall == 0) return cudaSuccess;
   const CfgDev* cfgs = e->view[0].cfgs;
-  const unsigned gm = (unsigned)std::max<int64_t>(1, (e->maxND_all + 255) / 256);
+  // element-wise kernels in 64-thread blocks, so that one configuration spreads over every SM (their dd
+  // arithmetic runs on the FP64 pipe, a few lanes per SM on this part)
+  const unsigned gm = (unsigned)std::max<int64_t>(1, (e->maxND_all + 63) / 64);
   const unsigned gt = (unsigned)((e->nall + 127) / 128);
   prof_begin(prof, st, kKFire);
-  k_fire_dots<<<dim3((unsigned)std::max(1, e->max_nb_fire), (unsigned)e->nall), kFireThreads, 0, st>>>(cfgs, e->all);
-  k_fire_ctrl<<<gt, 128, 0, st>>>(cfgs, e->all, e->nall);
-  k_fire_move<<<dim3(gm, (unsigned)e->nall), 256, 0, st>>>(cfgs, e->all);
+  cudaError_t le = launch_pdl(k_fire_dots, dim3((unsigned)std::max(1, e->max_nb_fire), (unsigned)e->nall), dim3(kFireThreads), 0,
+                              st, cfgs, e->all);
+  if (le == cudaSuccess) le = launch_pdl(k_fire_ctrl, dim3((unsigned)e->nall), dim3(32), 0, st, cfgs, e->all, e->nall);
+  if (le == cudaSuccess) le = launch_pdl(k_fire_move, dim3(gm, (unsigned)e->nall), dim3(64), 0, st, cfgs, e->all);
+  if (le != cudaSuccess) return le;
   prof_end(prof, st);
   for (int p = 0; p < 3; p++) {
     if (e->view[p].nlist == 0) continue;
@@ -342,8 +359,9 @@ cudaError_t fire_step_engine(const Engine* e, cudaStream_t st, Prof* prof) {
     if (err != cudaSuccess) return err;
   }
   prof_begin(prof, st, kKFire);
-  k_fire_accept<<<gt, 128, 0, st>>>(cfgs, e->all, e->nall);
-  k_fire_restore<<<dim3(gm, (unsigned)e->nall), 256, 0, st>>>(cfgs, e->all);
+  le = launch_pdl(k_fire_accept, dim3(gt), dim3(128), 0, st, cfgs, e->all, e->nall);
+  if (le == cudaSuccess) le = launch_pdl(k_fire_restore, dim3(gm, (unsigned)e->nall), dim3(64), 0, st, cfgs, e->all);
+  if (le != cudaSuccess) return le;
   prof_end(prof, st);
   return cudaGetLastError();
 }

@@ -420,17 +420,26 @@ __global__ void __launch_bounds__(kRedThreads) k_nt_reduce(const CfgDev* __restr
 }
 
 // scal[kScPhiHi..] as listed in ssh_internal.h.  Scale exponent e: |C|, |S| < 2^(e-1).  Grid (1, configs).
-__global__ void __launch_bounds__(kRedThreads) k_finalize(const CfgDev* __restrict__ cfgs, const int* __restrict__ list,
-                                                         int prec) {
+// Fixed order: thread t combines partials t, t + 256, ...; then warp shuffle trees and one pass over the warps.
+constexpr int kFinalizeThreads = 64;
+__global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const CfgDev* __restrict__ cfgs,
+                                                               const int* __restrict__ list, int prec) {
+  grid_dep_wait();
   const CfgDev& c = cfgs[list[blockIdx.y]];
   if (stopped(c)) return;
-  __shared__ RedPart sh[kRedThreads];
+  __shared__ RedPart sh[kFinalizeThreads / 32];
   const RedPart* blk = reinterpret_cast<const RedPart*>(c.blk);
   RedPart v = {0, 0, 0, 0, 0, 0, 0, 0};
   const int nb = (prec == SSH_FX && c.tc) ? c.tc_nblk : c.nblk;
-  for (int i = threadIdx.x; i < nb; i += kRedThreads) red_combine(v, blk[i]);
-  block_reduce(v, sh);
+  if ((int)threadIdx.x < nb) v = blk[threadIdx.x];
+  for (int i = threadIdx.x + kFinalizeThreads; i < nb; i += kFinalizeThreads) red_combine(v, blk[i]);
+  red_warp(v);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
   if (threadIdx.x == 0) {
+    v = sh[0];
+#pragma unroll
+    for (int w = 1; w < kFinalizeThreads / 32; w++) red_combine(v, sh[w]);
     double* scal = c.scal;
     scal[kScPhiHi] = v.phi_hi;
     scal[kScPhiLo] = v.phi_lo;
@@ -710,7 +719,8 @@ static cudaError_t launch_prec(const EngineView& v, bool want_force, cudaStream_
     prof_end(prof, st);
   }
   prof_begin(prof, st, kKFinalize);
-  k_finalize<<<dim3(1, (unsigned)v.nlist), kRedThreads, 0, st>>>(v.cfgs, v.list, P::kIdx);
+  cudaError_t le = launch_pdl(k_finalize, dim3(1, (unsigned)v.nlist), dim3(kFinalizeThreads), 0, st, v.cfgs, v.list, (int)P::kIdx);
+  if (le != cudaSuccess) return le;
   prof_end(prof, st);
   if (want_force) {
     if (v.nlist > v.ntc_list) {  // members that use these coefficients (the tensor-core path builds its own)

@@ -238,6 +238,27 @@ struct Ctx {
   TcPlan tc;
 };
 
+// Launch with programmatic dependent launch: the kernel's CTAs may be made resident while the previous kernel on
+// the stream is still finishing, and each waits (grid_dep_wait, its first statement) until that kernel has
+// completed and its memory is visible.  This hides the launch gap between the short kernels of a step.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<KArgs>(args)...);
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+#endif
+
 // record an event pair around a launch when profiling is on
 void prof_begin(Prof* p, cudaStream_t st, int id);
 void prof_end(Prof* p, cudaStream_t st);

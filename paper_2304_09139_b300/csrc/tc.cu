@@ -49,8 +49,7 @@ constexpr int kEpiWarps = 16;                      // four per TMEM lane quadran
 constexpr int kEpiCols = kTileN / (kEpiWarps / 4);  // accumulator columns per epilogue warp (8)
 constexpr int kGemmThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
 constexpr long long kWaitLimit = 2000000000LL;     // clock cycles (about one second) for any single wait
-constexpr size_t kRedBytes = (size_t)(kEpiWarps / 4) * kTileM * 2 * 16;  // force partials of the column blocks
-constexpr size_t kGemmSmem = (size_t)kStages * kStageBytes + kRedBytes;
+constexpr size_t kGemmSmem = (size_t)kStages * kStageBytes;
 constexpr int kFinThreads = 64;
 
 __device__ __forceinline__ bool stopped(const CfgDev& c) { return c.run && *c.run; }
@@ -92,12 +91,6 @@ __device__ __forceinline__ void put_digits_x(uint8_t* base, uint32_t slice_strid
     *reinterpret_cast<uint16_t*>(base + (size_t)s * slice_stride + off) =
         __bfloat16_as_ushort(__float2bfloat16_rn((float)d));
   }
-}
-
-// digits of a Q2.126 value in [-1, 1]: X = round(x 2^104)
-__device__ __forceinline__ void put_digits_q126(uint8_t* base, uint32_t slice_stride, uint32_t off, const q128& w) {
-  const __int128 v = q128_to_i128(w);
-  put_digits_x(base, slice_stride, off, (v + ((__int128)1 << 21)) >> 22);
 }
 
 // 192-bit two's-complement accumulator
@@ -235,6 +228,7 @@ __device__ __forceinline__ __int128 fixed104(const q128& w) {  // round(x 2^104)
 // force epilogue; axis 2 feeds the density GEMM's B operand and the force GEMM's A operand.
 __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restrict__ cfgs,
                                                           const TwItem* __restrict__ items) {
+  grid_dep_wait();
   extern __shared__ __align__(16) uint8_t psm[];
   __int128* Xs = reinterpret_cast<__int128*>(psm);                           // [m - m0][p][j]
   fxc* e1s = reinterpret_cast<fxc*>(psm + (size_t)kPrepM * 2 * kPrepParticles * 16);  // e^{2 pi i s_j}
@@ -326,9 +320,9 @@ __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restri
 // the previous item (the accumulator is released as soon as its last level has been read).
 __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __restrict__ cfgs,
                                                               const TcItem* __restrict__ items, int n_items) {
+  grid_dep_wait();
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ uint64_t bar_full[kStages], bar_empty[kStages], bar_acc_full, bar_acc_empty, bar_drain;
-  __shared__ uint64_t bar_red_full, bar_red_free;  // force partials of a lane quadrant: written / consumed
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -340,8 +334,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
     mbar_init(&bar_acc_full, 1);
     mbar_init(&bar_acc_empty, kEpiWarps);
     mbar_init(&bar_drain, 1);
-    mbar_init(&bar_red_full, kEpiWarps - kEpiWarps / 4);  // the warps of column blocks 1..3
-    mbar_init(&bar_red_free, kEpiWarps / 4);               // the warps of column block 0
     abort_sh = 0;
     mbar_fence_init();
   }
@@ -351,7 +343,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
   tc_fence_after();
   const uint32_t tbase = tmem_base_sh;
   volatile int* abort_flag = &abort_sh;
-  int* err_seen = nullptr;  // the configuration of the item being processed when a wait gave up
 
   if (warp == 0) {
     // ---- producer: one thread streams every item's K-steps through the stages
@@ -447,10 +438,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
     const int q = warp & 3, hq = (warp - 2) >> 2;
     const int row = 32 * q + lane;
     const uint32_t trow = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(kEpiCols * hq);
-    __int128* red = reinterpret_cast<__int128*>(smem + (size_t)kStages * kStageBytes);  // [hq][row][2]
-    // sum over the five levels of a group of (bits - magic) 2^(7 (4 - l)): the magic part, subtracted once
-    constexpr long long kGroupBias = (long long)kMagicBits * ((1ll << 28) + (1ll << 21) + (1ll << 14) + (1ll << 7) + 1);
-    long long gc = 0, fc = 0;  // chunks read, force items finished (all items of this CTA)
+    long long gc = 0;  // chunks read (all items of this CTA)
     bool stop = false;
     for (int item = blockIdx.x; item < n_items && !stop; item += gridDim.x) {
       const TcItem it = items[item];
@@ -476,16 +464,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
         for (int g = 0; g < 3; g++) {
           long long t[kEpiCols];
 #pragma unroll
-          for (int i = 0; i < kEpiCols; i++) t[i] = -kGroupBias;
+          for (int i = 0; i < kEpiCols; i++) t[i] = 0;
+          uint32_t r[5][kEpiCols];  // the group's five levels, loaded together, one wait
 #pragma unroll
-          for (int l = 0; l < 5; l++) {
-            uint32_t r[kEpiCols];
-            tmem_ld8(trow + (uint32_t)((5 * g + l) * kTileN), r);
-            tmem_ld_wait();
+          for (int l = 0; l < 5; l++) tmem_ld8(trow + (uint32_t)((5 * g + l) * kTileN), r[l]);
+          tmem_ld_wait();
+#pragma unroll
+          for (int l = 0; l < 5; l++)
 #pragma unroll
             for (int i = 0; i < kEpiCols; i++)
-              t[i] += (long long)(uint32_t)__float_as_int(__uint_as_float(r[i]) + kMagic) * (1ll << (7 * (4 - l)));
-          }
+              t[i] += (long long)acc_int(r[l][i]) * (1ll << (7 * (4 - l)));
 #pragma unroll
           for (int i = 0; i < kEpiCols; i++) st[g][i] += t[i];
         }
@@ -532,51 +520,21 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
           T = (q128_to_i128(q128{{p[1], p[2], p[3], p[4]}}) + q128_to_i128(q128{{r2[1], r2[2], r2[3], r2[4]}})) >> tsh;
           F2 += T;
         }
-        // The four column blocks of one lane quadrant sum through shared memory: blocks 1..3 publish their
-        // partials (red_full), block 0 adds them, writes the force partial and hands the buffer back (red_free).
-        if (hq != 0) {
-          const bool ok = fc == 0 || mbar_wait(&bar_red_free, (uint32_t)((fc - 1) & 1), kWaitLimit, abort_flag);
-          if (!__all_sync(0xffffffffu, ok)) {
-            *abort_flag = 1;
-            if (lane == 0) atomicOr(c.tc_err, 32);
-            break;
-          }
-          red[((size_t)hq * kTileM + row) * 2 + 0] = F1;
-          red[((size_t)hq * kTileM + row) * 2 + 1] = F2;
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&bar_red_full);
-        } else {
-          const bool ok = mbar_wait(&bar_red_full, (uint32_t)(fc & 1), kWaitLimit, abort_flag);
-          if (!__all_sync(0xffffffffu, ok)) {
-            *abort_flag = 1;
-            if (lane == 0) atomicOr(c.tc_err, 64);
-            break;
-          }
+        if (j < c.N) {
+          // F = L2 2^88 + L1 2^44 + L0 (L0, L1 in [0, 2^44)): the limbs of all column blocks add up exactly
+          unsigned long long* fa = reinterpret_cast<unsigned long long*>(c.tc_facc);
+          const unsigned long long m44 = (1ull << 44) - 1;
 #pragma unroll
-          for (int b2 = 1; b2 < kEpiWarps / 4; b2++) {
-            F1 += red[((size_t)b2 * kTileM + row) * 2 + 0];
-            F2 += red[((size_t)b2 * kTileM + row) * 2 + 1];
-          }
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&bar_red_free);
-          if (j < c.N) {
-            // F = L2 2^88 + L1 2^44 + L0 (L0, L1 in [0, 2^44)): the limbs of all column tiles add up exactly
-            unsigned long long* fa = reinterpret_cast<unsigned long long*>(c.tc_facc);
-            const unsigned long long m44 = (1ull << 44) - 1;
-#pragma unroll
-            for (int a = 0; a < 2; a++) {
-              const __int128 F = a == 0 ? F1 : F2;
-              atomicAdd(fa + ((size_t)a * 3 + 0) * c.N + j, (unsigned long long)F & m44);
-              atomicAdd(fa + ((size_t)a * 3 + 1) * c.N + j, (unsigned long long)(F >> 44) & m44);
-              atomicAdd(fa + ((size_t)a * 3 + 2) * c.N + j, (unsigned long long)(long long)(F >> 88));
-            }
+          for (int a = 0; a < 2; a++) {
+            const __int128 F = a == 0 ? F1 : F2;
+            atomicAdd(fa + ((size_t)a * 3 + 0) * c.N + j, (unsigned long long)F & m44);
+            atomicAdd(fa + ((size_t)a * 3 + 1) * c.N + j, (unsigned long long)(F >> 44) & m44);
+            atomicAdd(fa + ((size_t)a * 3 + 2) * c.N + j, (unsigned long long)(long long)(F >> 88));
           }
         }
-        fc++;
       }
     }
   }
-  (void)err_seen;
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
@@ -592,6 +550,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
 // coefficients) and as dd (C, S), with the block's Phi / max |n~|^2 / max |C|, |S| partials.
 __global__ void __launch_bounds__(kFinThreads) k_tc_dens_finish(const CfgDev* __restrict__ cfgs,
                                                                 const int* __restrict__ list) {
+  grid_dep_wait();
   const CfgDev& c = cfgs[list[blockIdx.y]];
   if (stopped(c) || (int)blockIdx.x >= c.tc_nblk) return;  // uniform per block
   RedPart v = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -668,6 +627,7 @@ __global__ void __launch_bounds__(kFinThreads) k_tc_dens_finish(const CfgDev* __
 // times 4 pi / L and the power-of-two scale of the coefficients
 __global__ void __launch_bounds__(kFinThreads) k_tc_force_finish(const CfgDev* __restrict__ cfgs,
                                                                  const int* __restrict__ list) {
+  grid_dep_wait();
   const CfgDev& c = cfgs[list[blockIdx.y]];
   if (stopped(c)) return;
   const int64_t i = (int64_t)blockIdx.x * kFinThreads + threadIdx.x;  // over [a][j]
@@ -694,6 +654,7 @@ __global__ void __launch_bounds__(kFinThreads) k_tc_force_finish(const CfgDev* _
 
 // grid ((R1 + 1) (R2 + 1) / 128 blocks, tensor-core members): the force GEMM's coefficient digits
 __global__ void k_tc_coef(const CfgDev* __restrict__ cfgs, const int* __restrict__ list) {
+  grid_dep_wait();
   const CfgDev& c = cfgs[list[blockIdx.y]];
   if (stopped(c)) return;
   const int W2 = c.tc_R2 + 1;
@@ -793,8 +754,8 @@ cudaError_t tc_setup(Ctx* c) {
   const int64_t max_split = std::max<int64_t>(1, t.KS / kChunkSteps);
   // one CTA per SM: as many K ranges per tile as fit in a single wave
   t.ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(max_split, c->sm_count / std::max(1, nt)));
-  // each K range holds at most 4096 read-outs, so the int64 level groups (below 2^50.1 per read-out) cannot overflow
-  t.ksplit = (int)std::max<int64_t>(t.ksplit, (t.KS + 4096 * kChunkSteps - 1) / (4096 * kChunkSteps));
+  // each K range holds at most 1024 read-outs, so the int64 level groups (below 2^52 per read-out) cannot overflow
+  t.ksplit = (int)std::max<int64_t>(t.ksplit, (t.KS + 1024 * kChunkSteps - 1) / (1024 * kChunkSteps));
   cudaStream_t st = c->stream;
   cudaError_t e;
   if ((e = tc_dev_alloc(&t.dA, (size_t)t.RT * t.KS * kStageA, st)) != cudaSuccess) return e;
@@ -900,7 +861,8 @@ cudaError_t tc_launch_force_finish(const EngineView& v, cudaStream_t st, Prof* p
   if (v.ntc_list == 0) return cudaSuccess;
   prof_begin(prof, st, kKTcFinish);
   const dim3 g((unsigned)std::max<int64_t>(1, (v.maxND + kFinThreads - 1) / kFinThreads), (unsigned)v.ntc_list);
-  k_tc_force_finish<<<g, kFinThreads, 0, st>>>(v.cfgs, v.tc_list);
+  cudaError_t le = launch_pdl(k_tc_force_finish, g, dim3(kFinThreads), 0, st, v.cfgs, v.tc_list);
+  if (le != cudaSuccess) return le;
   prof_end(prof, st);
   return cudaGetLastError();
 }
@@ -908,14 +870,18 @@ cudaError_t tc_launch_force_finish(const EngineView& v, cudaStream_t st, Prof* p
 cudaError_t tc_launch_density(const EngineView& v, cudaStream_t st, Prof* prof) {
   if (v.ntc_list == 0) return cudaSuccess;
   prof_begin(prof, st, kKTcPrep);
-  k_tc_prep<<<(unsigned)v.ntc_prep, kPrepThreads, kPrepSmem, st>>>(v.cfgs, v.tc_prep);
+  cudaError_t le = launch_pdl(k_tc_prep, dim3((unsigned)v.ntc_prep), dim3(kPrepThreads), kPrepSmem, st, v.cfgs, v.tc_prep);
+  if (le != cudaSuccess) return le;
   prof_end(prof, st);
   prof_begin(prof, st, kKTcDens);
-  k_tc_gemm<<<(unsigned)std::min(v.ntc_dens, v.sm_count), kGemmThreads, kGemmSmem, st>>>(v.cfgs, v.tc_dens, v.ntc_dens);
+  le = launch_pdl(k_tc_gemm, dim3((unsigned)std::min(v.ntc_dens, v.sm_count)), dim3(kGemmThreads), kGemmSmem, st, v.cfgs,
+                  v.tc_dens, v.ntc_dens);
+  if (le != cudaSuccess) return le;
   prof_end(prof, st);
   prof_begin(prof, st, kKTcFinish);
   const dim3 g((unsigned)std::max<int64_t>(1, (v.tc_max_grid + kFinThreads - 1) / kFinThreads), (unsigned)v.ntc_list);
-  k_tc_dens_finish<<<g, kFinThreads, 0, st>>>(v.cfgs, v.tc_list);
+  le = launch_pdl(k_tc_dens_finish, g, dim3(kFinThreads), 0, st, v.cfgs, v.tc_list);
+  if (le != cudaSuccess) return le;
   prof_end(prof, st);
   return cudaGetLastError();
 }
@@ -924,10 +890,13 @@ cudaError_t tc_launch_force(const EngineView& v, cudaStream_t st, Prof* prof) {
   if (v.ntc_list == 0) return cudaSuccess;
   prof_begin(prof, st, kKTcCoef);
   const dim3 g((unsigned)std::max<int64_t>(1, (v.tc_max_grid + 127) / 128), (unsigned)v.ntc_list);
-  k_tc_coef<<<g, 128, 0, st>>>(v.cfgs, v.tc_list);
+  cudaError_t le = launch_pdl(k_tc_coef, g, dim3(128), 0, st, v.cfgs, v.tc_list);
+  if (le != cudaSuccess) return le;
   prof_end(prof, st);
   prof_begin(prof, st, kKTcForce);
-  k_tc_gemm<<<(unsigned)std::min(v.ntc_force, v.sm_count), kGemmThreads, kGemmSmem, st>>>(v.cfgs, v.tc_force, v.ntc_force);
+  le = launch_pdl(k_tc_gemm, dim3((unsigned)std::min(v.ntc_force, v.sm_count)), dim3(kGemmThreads), kGemmSmem, st, v.cfgs,
+                  v.tc_force, v.ntc_force);
+  if (le != cudaSuccess) return le;
   prof_end(prof, st);
   return cudaGetLastError();
 }

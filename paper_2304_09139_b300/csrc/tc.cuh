@@ -7,9 +7,9 @@
 // digits (|.| <= 2^12) is exact in the fp32 accumulator.  The product of two such values keeps the digit
 // pairs (i, k) with i + k >= 14: "level" u = 28 - i - k runs over 0..14 and holds u + 1 digit pairs whose
 // weight is 128^(28-u).  A level accumulator that has summed P products of each of its pairs satisfies
-// |V_u| <= 15 P 2^12; read out every 64 products it stays below 2^22, where fp32 holds integers exactly
-// and one FADD with 1.5 * 2^23 turns it into an integer.  The dropped pairs (i + k <= 13) contribute at most
-// 2^-101 of one unit product each, far below the 1e-28 normwise tolerance.
+// |V_u| <= 15 P 2^12; read out every 256 products it stays below 15 2^20 < 2^24, where fp32 holds every
+// integer exactly, and a round-to-nearest conversion returns it.  The dropped pairs (i + k <= 13) contribute
+// at most 2^-101 of one unit product each, far below the 1e-28 normwise tolerance.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -23,15 +23,15 @@ constexpr int kFracBits = 104;      // X = round(x 2^104)
 constexpr int kTileM = 128;         // accumulator rows (TMEM lanes)
 constexpr int kTileN = 32;          // accumulator columns per level
 constexpr int kStepK = 16;          // K per MMA instruction (bf16)
-constexpr int kChunkSteps = 4;      // K-steps between exact read-outs (64 products per pair)
+constexpr int kChunkSteps = 16;     // K-steps between exact read-outs (256 products per pair)
 constexpr int kTmemCols = 512;      // kLevels * kTileN = 480 used
 constexpr uint32_t kSliceA = kTileM * kStepK * 2;   // 4096 bytes: one digit slice of one A K-step
 constexpr uint32_t kSliceB = kTileN * kStepK * 2;   // 1024 bytes: one digit slice of one B K-step
 constexpr uint32_t kStageA = kDigits * kSliceA;      // 61440
 constexpr uint32_t kStageB = kDigits * kSliceB;      // 15360
 constexpr uint32_t kStageBytes = kStageA + kStageB;  // 76800
-constexpr int kStages = 2;
-constexpr float kMagic = 12582912.0f;                // 1.5 * 2^23
+constexpr int kStages = 3;
+constexpr float kMagic = 12582912.0f;                // 1.5 * 2^23 (small integer -> fp32 by one FADD)
 constexpr int32_t kMagicBits = 0x4B400000;
 
 // Byte offset of element (r, k) inside one K-major rows x 16 operand slice, no swizzle: 8x16-byte core
@@ -133,10 +133,8 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// exact integer value of an fp32 accumulator word holding an integer of magnitude below 2^22
-__device__ __forceinline__ int32_t acc_int(uint32_t bits) {
-  return __float_as_int(__uint_as_float(bits) + kMagic) - kMagicBits;
-}
+// exact integer value of an fp32 accumulator word holding an integer of magnitude below 2^24
+__device__ __forceinline__ int32_t acc_int(uint32_t bits) { return __float2int_rn(__uint_as_float(bits)); }
 
 }  // namespace tc
 }  // namespace ssh
