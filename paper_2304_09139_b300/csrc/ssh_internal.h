@@ -89,6 +89,8 @@ struct CfgDev {
   int64_t tc_KS;
   uint8_t *tc_dA, *tc_dB, *tc_fA, *tc_fB;
   void* tc_a1;
+  void* tc_tab;        // per (axis, particle): first-quadrant tables e^{2 pi i k s} (k < 8), e^{2 pi i 8 b s}
+  int tc_ntab;
   long long* tc_acc;   // density level groups per tile [tile][3][32][128], summed by integer atomics
   long long* tc_facc;  // force limbs [axis][3][N], summed by integer atomics
   const int32_t* tc_kmap;
@@ -196,7 +198,8 @@ struct TcPlan {
   std::vector<int32_t> tiles;    // density tiles in use: rt * CTd + ct
   std::vector<int32_t> tilemap;  // [RT * CTd] -> index into tiles, or -1
   std::vector<int32_t> kmap;     // [(R1 + 1) (2 R2 + 1)] internal index of (n1, n2), or -1
-  DevBuf dA, dB, fA, fB, a1, acc, facc, kmap_d, tilemap_d, err;
+  int ntab = 0;                  // table entries per (axis, particle)
+  DevBuf dA, dB, fA, fB, a1, tab, acc, facc, kmap_d, tilemap_d, err;
 };
 
 struct Ctx {

@@ -156,19 +156,6 @@ __device__ __forceinline__ __int128 q160_shr_round(const q160& a, int sh) {
   return (__int128)((lo >> sh) | ((unsigned __int128)t.w[2] << (128 - sh)));
 }
 
-__device__ __forceinline__ fxc PolFXZero() {
-  fxc z;
-  z.re = q128_zero();
-  z.im = q128_zero();
-  return z;
-}
-__device__ __forceinline__ fxc PolFXOne() {
-  fxc z;
-  z.re = q126_one();
-  z.im = q128_zero();
-  return z;
-}
-
 __device__ __forceinline__ q160 load_q160(const void* p) {
   const uint32_t* u = reinterpret_cast<const uint32_t*>(p);
   q160 r;
@@ -184,54 +171,124 @@ __device__ __forceinline__ q160 load_q160(const void* p) {
 namespace {
 
 constexpr int kPrepThreads = 256;
-constexpr int kPrepParticles = 32;  // particles per CTA
-constexpr int kPrepM = 96;          // powers per pass (shared-memory staging of their fixed-point values)
-constexpr int kPrepBlocks = kPrepThreads / kPrepParticles;  // power blocks per particle and pass: one per thread
-constexpr size_t kPrepSmem = (size_t)kPrepM * 2 * kPrepParticles * 16 + kPrepParticles * sizeof(fxc);
+constexpr int kPrepParticles = 16;  // particles per CTA (one K-step of the density GEMM)
+constexpr int kPrepM = 80;          // powers per pass (shared-memory staging of their fixed-point values)
+constexpr int kPrepLow = 8;         // e^{2 pi i m s} = A[m / 8] T[m % 8]
+constexpr int kPrepAnc = kPrepM / kPrepLow;
+constexpr int kPrepPitch = 2 * kPrepM + 1;  // staging row pitch (16-byte entries): odd, so rows spread over the banks
+constexpr size_t kPrepSmemY = (size_t)kPrepPitch * kPrepParticles * 16;
+constexpr size_t kPrepSmem = kPrepSmemY;
 
-// Eight values X (|X| <= 2^104) -> their 15 balanced digits as one 16-byte row (8 bf16) per digit slice.
-__device__ __forceinline__ void put_digit_rows(uint8_t* base, uint32_t slice_stride, const __int128 (&X)[8]) {
-  const __int128 bias = digit_bias();
-  __int128 Y[8];
-#pragma unroll
-  for (int v = 0; v < 8; v++) Y[v] = X[v] + bias;
+// Eight biased values Y = X + B (X = round(x 2^104), B the balanced-digit offset) -> their 15 digits as one
+// 16-byte row (8 bf16) per digit slice, slice s holding digit 14 - s.  Digit i < 14 is bits 7i..7i+6 of Y
+// minus 64 (one funnel shift from two 32-bit words); the top digit is the signed bits 98..127.
+__device__ __forceinline__ void put_digit_rows(uint8_t* base, uint32_t slice_stride, const uint4 (&Y)[8]) {
 #pragma unroll
   for (int s = 0; s < kDigits; s++) {
     const int i = kDigits - 1 - s;
-    uint32_t h[8];
+    uint32_t f[8];
 #pragma unroll
     for (int v = 0; v < 8; v++) {
-      const int d = i == kDigits - 1 ? (int)(Y[v] >> 98) : (int)((Y[v] >> (7 * i)) & 127) - 64;
-      // small integer -> fp32 (exact) -> its bf16 half (exact: at most 8 significant bits)
-      h[v] = __float_as_uint(__int_as_float(kMagicBits + d) - kMagic) >> 16;
+      const uint32_t w[4] = {Y[v].x, Y[v].y, Y[v].z, Y[v].w};
+      int d;
+      if (i == kDigits - 1) {
+        d = (int32_t)w[3] >> 2;
+      } else {
+        const int o = 7 * i;
+        d = (int)(__funnelshift_r(w[o >> 5], w[(o >> 5) + 1 < 4 ? (o >> 5) + 1 : 3], o & 31) & 127u) - 64;
+      }
+      // small integer -> fp32 (exact) whose upper half is the bf16 of the same value
+      f[v] = __float_as_uint(__int_as_float(kMagicBits + d) - kMagic);
     }
     uint4 row;
-    row.x = h[0] | (h[1] << 16);
-    row.y = h[2] | (h[3] << 16);
-    row.z = h[4] | (h[5] << 16);
-    row.w = h[6] | (h[7] << 16);
+    row.x = __byte_perm(f[0], f[1], 0x7632);
+    row.y = __byte_perm(f[2], f[3], 0x7632);
+    row.z = __byte_perm(f[4], f[5], 0x7632);
+    row.w = __byte_perm(f[6], f[7], 0x7632);
     *reinterpret_cast<uint4*>(base + (size_t)s * slice_stride) = row;
   }
 }
 
-__device__ __forceinline__ __int128 fixed104(const q128& w) {  // round(x 2^104) of a Q2.126 value
-  return (q128_to_i128(w) + ((__int128)1 << 21)) >> 22;
+// first-quadrant phasor -> (re, im) as round(x 2^104) + balanced-digit offset, and as signed Q2.126
+__device__ __forceinline__ void qent_out(const qent& z, uint4& yre, uint4& yim, fxc* q126) {
+  // unsigned Q1.127 components (value 1 is 2^127: unsigned arithmetic until after the shift)
+  const unsigned __int128 c = (unsigned __int128)q128_to_i128(z.c), sn = (unsigned __int128)q128_to_i128(z.s);
+  const uint32_t q = z.cs.w[0] & 3u;
+  const __int128 xc = (__int128)((c + ((unsigned __int128)1 << 22)) >> 23);
+  const __int128 xs = (__int128)((sn + ((unsigned __int128)1 << 22)) >> 23);
+  __int128 re, im;
+  switch (q) {  // z = i^q (c + i s)
+    case 0: re = xc; im = xs; break;
+    case 1: re = -xs; im = xc; break;
+    case 2: re = -xc; im = -xs; break;
+    default: re = xs; im = -xc; break;
+  }
+  const __int128 b = digit_bias();
+  const unsigned __int128 ur = (unsigned __int128)(re + b), ui = (unsigned __int128)(im + b);
+  yre = make_uint4((uint32_t)ur, (uint32_t)(ur >> 32), (uint32_t)(ur >> 64), (uint32_t)(ur >> 96));
+  yim = make_uint4((uint32_t)ui, (uint32_t)(ui >> 32), (uint32_t)(ui >> 64), (uint32_t)(ui >> 96));
+  if (q126) {
+    const __int128 hc = (__int128)(c >> 1), hs = (__int128)(sn >> 1);  // Q2.126
+    __int128 r2, i2;
+    switch (q) {
+      case 0: r2 = hc; i2 = hs; break;
+      case 1: r2 = -hs; i2 = hc; break;
+      case 2: r2 = -hc; i2 = -hs; break;
+      default: r2 = hs; i2 = -hc; break;
+    }
+    fxc o;
+    o.re = q128_from_i128(r2);
+    o.im = q128_from_i128(i2);
+    *q126 = o;
+  }
 }
 
 }  // namespace
 
-// CTA per (configuration, axis, 32 particles); items TwItem {cfg, axis, first particle}.  Pass over the
-// powers m in groups of 64: phase 1 computes e^{2 pi i m s_j} (an exact-phase anchor every 16 powers, one
-// multiply per power in between) into shared memory as fixed-point integers; phase 2 writes the digit slices
-// as whole 16-byte core-matrix rows (8 K-consecutive values of one operand row), which consecutive threads
-// fill contiguously.  Axis 1 (n1) feeds the density GEMM's A operand and the Q2.126 table a_j(n1) of the
-// force epilogue; axis 2 feeds the density GEMM's B operand and the force GEMM's A operand.
+// Thread per (particle, axis): the tables T[k] = e^{2 pi i k s} (k < 8) and A[b] = e^{2 pi i 8 b s}
+// (b < ceil((R + 1) / 8)) as first-quadrant phasors, from exact-phase values of e^{2 pi i s} and e^{2 pi i 8 s}
+// and chains of multiplies (each product at most 8 units of 2^-126 low; about 17 in the longest chain).
+// Grid (particle blocks, tensor-core members); layout tc_tab[(axis N + j) tc_ntab + (k | 8 + b)].
+__global__ void __launch_bounds__(128) k_tc_tables(const CfgDev* __restrict__ cfgs, const int* __restrict__ list) {
+  grid_dep_wait();
+  const CfgDev& c = cfgs[list[blockIdx.y]];
+  if (stopped(c)) return;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 2 * c.N) return;
+  const int axis = (int)(idx / c.N);
+  const int64_t j = idx - (int64_t)axis * c.N;
+  const int R = axis == 0 ? c.tc_R1 : c.tc_R2;
+  const int nA = R / kPrepLow + 1;
+  const q128 u = turns_from_dd(c.s_hi[axis * c.N + j], c.s_lo[axis * c.N + j]);
+  qent* tab = reinterpret_cast<qent*>(c.tc_tab) + idx * c.tc_ntab;
+  const qent one = to_quadrant(phasor_turn(q128_zero()));
+  const qent e1 = to_quadrant(phasor_turn(u));
+  qent t = one;
+#pragma unroll 1
+  for (int k = 0; k < kPrepLow; k++) {
+    tab[k] = t;
+    if (k + 1 < kPrepLow) t = qmul(t, e1);
+  }
+  const qent e8 = to_quadrant(phasor_turn(turn_times(u, kPrepLow)));
+  qent a = one;
+#pragma unroll 1
+  for (int b = 0; b < nA; b++) {
+    tab[kPrepLow + b] = a;
+    if (b + 1 < nA) a = qmul(a, e8);
+  }
+}
+
+// CTA per (configuration, axis, 16 particles); items TwItem {cfg, axis, first particle}.  Per pass over at
+// most 80 powers m0.. : phase 1 forms every power as one product A[m / 8] T[m % 8] of the particle's tables
+// (all threads, independent) into shared memory; phase 2 writes the digit slices as whole 16-byte
+// core-matrix rows (8 K-consecutive values of one operand row), which consecutive threads fill contiguously.
+// Axis 1 (n1) feeds the density GEMM's A operand and the Q2.126 table a_j(n1) of the force epilogue; axis 2
+// feeds the density GEMM's B operand and the force GEMM's A operand.
 __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restrict__ cfgs,
                                                           const TwItem* __restrict__ items) {
   grid_dep_wait();
   extern __shared__ __align__(16) uint8_t psm[];
-  __int128* Xs = reinterpret_cast<__int128*>(psm);                           // [m - m0][p][j]
-  fxc* e1s = reinterpret_cast<fxc*>(psm + (size_t)kPrepM * 2 * kPrepParticles * 16);  // e^{2 pi i s_j}
+  uint4* Ys = reinterpret_cast<uint4*>(psm);  // [j][2 (m - m0) + p], pitch kPrepPitch
   const TwItem it = items[blockIdx.x];
   const CfgDev& c = cfgs[it.cfg];
   if (stopped(c)) return;
@@ -240,33 +297,26 @@ __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restri
   const int64_t j0 = it.start;
   const int R = axis == 0 ? c.tc_R1 : c.tc_R2;
   const int tid = threadIdx.x;
-  if (tid < kPrepParticles) {
-    const int64_t j = j0 + tid;
-    fxc e = PolFXOne();
-    if (j < N) e = phasor_turn(turns_from_dd(c.s_hi[axis * N + j], c.s_lo[axis * N + j]));
-    e1s[tid] = e;
-  }
-  __syncthreads();
+  const __int128 bias = digit_bias();
+  const uint4 yzero = make_uint4((uint32_t)bias, (uint32_t)(bias >> 32), (uint32_t)(bias >> 64), (uint32_t)(bias >> 96));
+  const qent* tab = reinterpret_cast<const qent*>(c.tc_tab);
   for (int m0 = 0; m0 <= R; m0 += kPrepM) {
     const int mcount = min(kPrepM, R + 1 - m0);
-    // phase 1: one task per thread, (particle, block of bl powers): an exact-phase anchor, then multiplies
-    const int bl = (mcount + kPrepBlocks - 1) / kPrepBlocks;
-    {
-      const int task = tid;
-      const int jl = task % kPrepParticles, b = task / kPrepParticles;
+    // phase 1: every (particle, power) of the pass, one product each
+    for (int task = tid; task < mcount * kPrepParticles; task += kPrepThreads) {
+      const int jl = task % kPrepParticles, ml = task / kPrepParticles;
       const int64_t j = j0 + jl;
-      const int mb = m0 + bl * b;
-      fxc z = PolFXZero();
-      const bool live = j < N && mb < m0 + mcount;
-      if (live) z = phasor_turn(turn_times(turns_from_dd(c.s_hi[axis * N + j], c.s_lo[axis * N + j]), mb));
-      const fxc e1 = e1s[jl];
-      for (int i = 0; i < bl && mb + i < m0 + mcount; i++) {
-        if (i > 0 && live) z = fxc_mul(z, e1);
-        const int ml = mb + i - m0;
-        Xs[(ml * 2 + 0) * kPrepParticles + jl] = fixed104(z.re);
-        Xs[(ml * 2 + 1) * kPrepParticles + jl] = fixed104(z.im);
-        if (axis == 0 && live) reinterpret_cast<fxc*>(c.tc_a1)[(int64_t)(mb + i) * N + j] = z;
+      const int m = m0 + ml;
+      uint4 yr = yzero, yi = yzero;
+      if (j < N) {
+        const qent* tj = tab + ((int64_t)axis * N + j) * c.tc_ntab;
+        const qent z = qmul(tj[kPrepLow + (m >> 3)], tj[m & 7]);
+        fxc zq;
+        qent_out(z, yr, yi, axis == 0 ? &zq : nullptr);
+        if (axis == 0) reinterpret_cast<fxc*>(c.tc_a1)[(int64_t)m * N + j] = zq;
       }
+      Ys[jl * kPrepPitch + ml * 2 + 0] = yr;
+      Ys[jl * kPrepPitch + ml * 2 + 1] = yi;
     }
     __syncthreads();
     // phase 2a: rows (m, cos / sin) x 8 particles, into the density GEMM operand of this axis
@@ -276,34 +326,33 @@ __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restri
       const int r = 2 * m0 + rl;
       const int64_t jg = j0 + 8 * g8;
       if (jg >= N) continue;  // K-steps past the last particle stay zero
-      __int128 X[8];
+      uint4 Y[8];
 #pragma unroll
-      for (int v = 0; v < 8; v++) X[v] = Xs[rl * kPrepParticles + 8 * g8 + v];
+      for (int v = 0; v < 8; v++) Y[v] = Ys[(8 * g8 + v) * kPrepPitch + rl];
       const int64_t ks = jg >> 4;
       const int k0 = (int)(jg & 15);
       if (axis == 0)
-        put_digit_rows(c.tc_dA + ((int64_t)(r >> 7) * c.tc_KS + ks) * kStageA + slice_off(r & 127, k0), kSliceA, X);
+        put_digit_rows(c.tc_dA + ((int64_t)(r >> 7) * c.tc_KS + ks) * kStageA + slice_off(r & 127, k0), kSliceA, Y);
       else
-        put_digit_rows(c.tc_dB + ((int64_t)(r >> 5) * c.tc_KS + ks) * kStageB + slice_off(r & 31, k0), kSliceB, X);
+        put_digit_rows(c.tc_dB + ((int64_t)(r >> 5) * c.tc_KS + ks) * kStageB + slice_off(r & 31, k0), kSliceB, Y);
     }
     // phase 2b (axis 2): particles x 8 values of (m, cos / sin), into the force GEMM's A operand
     if (axis == 1) {
-      const int ngrp = nrow / 8;  // m0 is a multiple of 64, so 2 m0 is a multiple of 8; a partial group waits
-      const int ntail = nrow % 8;
-      const int groups = ngrp + (ntail ? 1 : 0);
+      const int groups = (nrow + 7) / 8;  // 2 m0 is a multiple of 8; a partial last group is padded with zeros
+      const uint4 yz = yzero;
       for (int task = tid; task < groups * kPrepParticles; task += kPrepThreads) {
         const int jl = task % kPrepParticles, g = task / kPrepParticles;
         const int64_t j = j0 + jl;
         if (j >= N) continue;
-        __int128 X[8];
+        uint4 Y[8];
 #pragma unroll
         for (int v = 0; v < 8; v++) {
           const int rl = 8 * g + v;
-          X[v] = rl < nrow ? Xs[rl * kPrepParticles + jl] : (__int128)0;
+          Y[v] = rl < nrow ? Ys[jl * kPrepPitch + rl] : yz;
         }
         const int kf0 = 2 * m0 + 8 * g;
         put_digit_rows(c.tc_fA + ((int64_t)(j >> 7) * c.tc_KSf + (kf0 >> 4)) * kStageA + slice_off((int)(j & 127), kf0 & 15),
-                       kSliceA, X);
+                       kSliceA, Y);
       }
     }
     __syncthreads();
@@ -763,6 +812,8 @@ cudaError_t tc_setup(Ctx* c) {
   if ((e = tc_dev_alloc(&t.fA, (size_t)t.PT * t.KSf * kStageA, st)) != cudaSuccess) return e;
   if ((e = tc_dev_alloc(&t.fB, (size_t)t.CTf * t.KSf * kStageB, st)) != cudaSuccess) return e;
   if ((e = tc_dev_alloc(&t.a1, (size_t)(t.R1 + 1) * c->N * sizeof(fxc), st)) != cudaSuccess) return e;
+  t.ntab = kPrepLow + std::max(t.R1, t.R2) / kPrepLow + 1;
+  if ((e = tc_dev_alloc(&t.tab, (size_t)2 * c->N * t.ntab * sizeof(qent), st)) != cudaSuccess) return e;
   if ((e = tc_dev_alloc(&t.acc, (size_t)nt * 3 * kTileN * kTileM * 8, st)) != cudaSuccess) return e;
   if ((e = tc_dev_alloc(&t.facc, (size_t)2 * 3 * c->N * 8, st)) != cudaSuccess) return e;
   if ((e = tc_dev_alloc(&t.kmap_d, t.kmap.size() * 4, st)) != cudaSuccess) return e;
@@ -794,7 +845,7 @@ cudaError_t tc_setup(Ctx* c) {
 
 void tc_free(Ctx* c) {
   TcPlan& t = c->tc;
-  for (DevBuf* b : {&t.dA, &t.dB, &t.fA, &t.fB, &t.a1, &t.acc, &t.facc, &t.kmap_d, &t.tilemap_d, &t.err}) {
+  for (DevBuf* b : {&t.dA, &t.dB, &t.fA, &t.fB, &t.a1, &t.tab, &t.acc, &t.facc, &t.kmap_d, &t.tilemap_d, &t.err}) {
     if (b->p) cudaFree(b->p);
     b->p = nullptr;
     b->bytes = 0;
@@ -805,7 +856,7 @@ void tc_free(Ctx* c) {
 size_t tc_footprint(const Ctx& c) {
   const TcPlan& t = c.tc;
   if (!t.on) return 0;
-  return t.dA.bytes + t.dB.bytes + t.fA.bytes + t.fB.bytes + t.a1.bytes + t.acc.bytes + t.facc.bytes + t.kmap_d.bytes +
+  return t.dA.bytes + t.dB.bytes + t.fA.bytes + t.fB.bytes + t.a1.bytes + t.tab.bytes + t.acc.bytes + t.facc.bytes + t.kmap_d.bytes +
          t.tilemap_d.bytes;
 }
 
@@ -828,6 +879,8 @@ void tc_fill_cfgdev(const Ctx* c, CfgDev* g) {
   g->tc_fA = (uint8_t*)t.fA.p;
   g->tc_fB = (uint8_t*)t.fB.p;
   g->tc_a1 = t.a1.p;
+  g->tc_tab = t.tab.p;
+  g->tc_ntab = t.ntab;
   g->tc_acc = (long long*)t.acc.p;
   g->tc_facc = (long long*)t.facc.p;
   g->tc_nblk = tc_finish_blocks(*c);
@@ -843,7 +896,7 @@ void tc_fill_cfgdev(const Ctx* c, CfgDev* g) {
 void tc_items(const Ctx* c, int i, std::vector<TwItem>& prep, std::vector<TcItem>& dens, std::vector<TcItem>& force) {
   const TcPlan& t = c->tc;
   for (int axis = 0; axis < 2; axis++)
-    for (int64_t j = 0; j < c->N; j += kPrepParticles) prep.push_back({i, axis, j});
+    for (int64_t j = 0; j < c->N; j += kPrepParticles) prep.push_back({i, axis, j});  // one K-step each
   for (int ti = 0; ti < (int)t.tiles.size(); ti++) {
     const int rt = t.tiles[ti] / t.CTd, ct = t.tiles[ti] % t.CTd;
     for (int sp = 0; sp < t.ksplit; sp++) {
@@ -870,7 +923,10 @@ cudaError_t tc_launch_force_finish(const EngineView& v, cudaStream_t st, Prof* p
 cudaError_t tc_launch_density(const EngineView& v, cudaStream_t st, Prof* prof) {
   if (v.ntc_list == 0) return cudaSuccess;
   prof_begin(prof, st, kKTcPrep);
-  cudaError_t le = launch_pdl(k_tc_prep, dim3((unsigned)v.ntc_prep), dim3(kPrepThreads), kPrepSmem, st, v.cfgs, v.tc_prep);
+  cudaError_t le = launch_pdl(k_tc_tables, dim3((unsigned)std::max<int64_t>(1, (v.maxND + 127) / 128), (unsigned)v.ntc_list),
+                              dim3(128), 0, st, v.cfgs, v.tc_list);
+  if (le == cudaSuccess)
+    le = launch_pdl(k_tc_prep, dim3((unsigned)v.ntc_prep), dim3(kPrepThreads), kPrepSmem, st, v.cfgs, v.tc_prep);
   if (le != cudaSuccess) return le;
   prof_end(prof, st);
   prof_begin(prof, st, kKTcDens);
