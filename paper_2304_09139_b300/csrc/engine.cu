@@ -161,6 +161,10 @@ cudaError_t engine_build(Engine* e, const std::vector<Ctx*>& members, const std:
       tc_items(members[i], i, tcp, tcd, tcf);
       tc_grid = std::max<int64_t>(tc_grid, (int64_t)(members[i]->tc.R1 + 1) * (members[i]->tc.R2 + 1));
     }
+  // largest items first over all members: the persistent GEMM assigns them round-robin
+  auto by_size = [](const TcItem& a, const TcItem& b) { return a.nks > b.nks; };
+  std::stable_sort(tcd.begin(), tcd.end(), by_size);
+  std::stable_sort(tcf.begin(), tcf.end(), by_size);
   cudaError_t err;
   if ((err = up(&e->d_tclist, tcl.data(), sizeof(int) * tcl.size(), st)) != cudaSuccess) return err;
   if ((err = up(&e->d_tcprep, tcp.data(), sizeof(TwItem) * tcp.size(), st)) != cudaSuccess) return err;

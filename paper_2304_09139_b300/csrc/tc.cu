@@ -904,8 +904,24 @@ void tc_items(const Ctx* c, int i, std::vector<TwItem>& prep, std::vector<TcItem
       dens.push_back({i, 0, rt, ct, (int32_t)k0, (int32_t)(k1 - k0), ti, 0});
     }
   }
+  // force items: column tile ct holds n1 in [8 ct, 8 ct + 8); its K range (m, cos / sin) stops at the largest m
+  // with (n1, +-m) in the set for one of those n1 (the coefficients beyond are zero).  Largest items first, so
+  // the round-robin assignment to the persistent CTAs balances.
+  const int span = 2 * t.R2 + 1;
+  std::vector<int> ks_of(t.CTf, 0);
+  for (int ct = 0; ct < t.CTf; ct++) {
+    int mmax = -1;
+    for (int n1 = 8 * ct; n1 < std::min(8 * ct + 8, t.R1 + 1); n1++)
+      for (int m = 0; m <= t.R2; m++)
+        if (t.kmap[(size_t)n1 * span + t.R2 + m] >= 0 || t.kmap[(size_t)n1 * span + t.R2 - m] >= 0) mmax = std::max(mmax, m);
+    ks_of[ct] = mmax < 0 ? 0 : (2 * (mmax + 1) + kStepK - 1) / kStepK;
+  }
+  std::vector<TcItem> fi;
   for (int pt = 0; pt < t.PT; pt++)
-    for (int ct = 0; ct < t.CTf; ct++) force.push_back({i, 1, pt, ct, 0, t.KSf, ct, 0});
+    for (int ct = 0; ct < t.CTf; ct++)
+      if (ks_of[ct] > 0) fi.push_back({i, 1, pt, ct, 0, ks_of[ct], ct, 0});
+  std::stable_sort(fi.begin(), fi.end(), [](const TcItem& a, const TcItem& b) { return a.nks > b.nks; });
+  force.insert(force.end(), fi.begin(), fi.end());
 }
 
 size_t tc_gemm_smem() { return kGemmSmem; }
