@@ -66,13 +66,15 @@ WORKLOAD = dict(d=2, N=10_000, L=100.0, chi=0.45, seed=2)
 # DRAM bytes (read + write) per launch from one ncu capture of this workload (profiles/), valid only while
 # the kernel sources hash to the value recorded with them; otherwise the traffic is reported as null.
 NCU_TRAFFIC = {("fx", "force"): ("9a8b45757c86", 35_869_184 + 5_888_000),
-               ("fx", "ntilde"): ("9a8b45757c86", 36_598_272 + 43_264_000)}
+               ("fx", "ntilde"): ("9a8b45757c86", 36_598_272 + 43_264_000),
+               ("fx-tensor", "tc_force"): ("37f79b9f30b3", 75_052_800 + 3_156_480),
+               ("fx-tensor", "tc_dens"): ("37f79b9f30b3", 125_670_656 + 4_787_968)}
 
 
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("kernels.cu", "fx.cuh", "dd.cuh"):
+    for f in ("kernels.cu", "fx.cuh", "dd.cuh", "tc.cu", "tc.cuh", "reduce.cuh"):
         with open(os.path.join(ROOT, "paper_2304_09139_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
