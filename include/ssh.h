@@ -144,7 +144,8 @@ ssh_status ssh_get_ntilde(ssh_ctx* ctx, double* C_hi, double* C_lo, double* S_hi
  * "S_max at or below a target").  Parameters; zero fields take the defaults that ssh_min_defaults writes.
  *   dt0, dt_max            time steps in physical units (defaults dt_max = 1/sqrt(2 N max|k|^2), dt0 = dt_max/10)
  *   alpha_start, f_alpha, f_inc, f_dec, n_min   FIRE constants (defaults 0.1, 0.99, 1.1, 0.5, 5)
- *   n_stages, stage_prec   precision ladder, e.g. {SSH_FP64, SSH_DD} (default {SSH_FP64, SSH_FX}); a stage
+ *   n_stages, stage_prec   precision ladder, e.g. {SSH_FP64, SSH_DD} (default {SSH_FX} when the context's
+ *                          fixed point runs on the tensor cores, else {SSH_FP64, SSH_FX}); a stage
  *                          ends when S_max <= stage_floor[s] or S_max has not halved in stall_window[s]
  *                          steps; the last stage ends only at the target, the step cap or a stall
  *   max_steps, smax_target step cap (default 200000) and convergence target (default 1e-36)
