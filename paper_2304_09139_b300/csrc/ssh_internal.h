@@ -85,16 +85,18 @@ struct CfgDev {
   double *F_hi, *F_lo;
   dd pref, inv_L;
   // tensor-core fixed-point path (tc.cu); tc = 0 when the configuration uses the integer-pipe kernels
-  int tc, tc_R1, tc_R2, tc_RT, tc_CTd, tc_PT, tc_KSf, tc_CTf, tc_bexp, tc_ksplit, tc_nblk, tc_gs, tc_ts;
-  int64_t tc_KS;
-  uint8_t *tc_dA, *tc_dB, *tc_fA, *tc_fB;
-  void* tc_a1;
+  int tc, tc_R1, tc_nP, tc_RT, tc_CTd, tc_PT, tc_KSf, tc_CTf, tc_bexp, tc_ksplit, tc_nblk, tc_gs, tc_ts, tc_ntab;
+  int tc_Rax[3];       // per axis: powers 0..tc_Rax[a] in the tables
+  int64_t tc_KS, tc_NJ, tc_NPg;  // density K-steps; particle groups and row groups of the digit tensor
+  uint8_t *tc_wT, *tc_aB, *tc_fB;  // digit tensor of w_j(p); density B (a_j(n1)); force B (coefficients)
+  void* tc_a1;         // a_j(n1) as signed Q2.126, [n1][j]
   void* tc_tab;        // per (axis, particle): first-quadrant tables e^{2 pi i k s} (k < 8), e^{2 pi i 8 b s}
-  int tc_ntab;
   long long* tc_acc;   // density level groups per tile [tile][3][32][128], summed by integer atomics
   long long* tc_facc;  // force limbs [axis][3][N], summed by integer atomics
-  const int32_t* tc_kmap;
-  const int32_t* tc_tilemap;
+  const int32_t* tc_em;       // [p][n1][2]: internal k index of (n1, +-p), or -1
+  const int32_t* tc_pvec;     // [p]: (n2 & 0xffff) | (n3 << 16)
+  const int32_t* tc_tilemap;  // [RT][CTd] -> tile slot, or -1
+  const void* tc_tmap;        // two 128-byte tensor maps of the digit tensor: density box, force box
   int* tc_err;
   // minimiser state (null when the context has not minimised yet)
   void* fs;
@@ -140,7 +142,8 @@ struct EngineView {
   int ntc_dens = 0;
   const TcItem* tc_force = nullptr;
   int ntc_force = 0;
-  int64_t tc_max_grid = 0;  // largest (R1 + 1) (R2 + 1) of the members
+  int64_t tc_max_grid = 0;  // largest (R1 + 1) nP of the members
+  size_t tc_prep_smem = 0;  // largest preparation shared memory of the members
 };
 
 struct Ctx;
@@ -188,18 +191,26 @@ struct Engine {
 // tile plan and buffers of the tensor-core path of one configuration (tc.cu)
 struct TcPlan {
   bool on = false;
-  int R1 = 0, R2 = 0;            // n1 in [0, R1], |n2| <= R2
+  int d = 0;
+  int R1 = 0;                    // n1 in [0, R1]
+  int Rax[3] = {0, 0, 0};        // largest |n_a| per axis (powers held in the tables)
+  int nP = 0;                    // canonical sub-vectors p = (n2[, n3]) of the half set, sorted by |p|^2
   int64_t KS = 0;                // density K-steps (16 particles each)
-  int RT = 0, CTd = 0;           // density row tiles (128 rows (n1, cos/sin)), column tiles (32 columns (m, cos/sin))
-  int PT = 0, KSf = 0, CTf = 0;  // force particle tiles, K-steps, column tiles (8 values of n1 each)
-  int bexp = 0;                  // 2^bexp > R2: scale of the n2-weighted force coefficients
+  int RT = 0, CTd = 0;           // density row tiles (128 rows (p, cos/sin)), column tiles (32 columns (n1, cos/sin))
+  int PT = 0, KSf = 0, CTf = 0;  // force particle tiles, K-steps (16 rows (p, cos/sin)), column tiles (16/d n1, all axes)
+  int64_t NJ = 0, NPg = 0;       // digit tensor: particle groups and row groups of 8
+  int bexp = 0;                  // 2^bexp > |n_a| (a >= 2): scale of the weighted force coefficients
   int ksplit = 1;                // K ranges per density tile
   int gs = 0, ts = 0;            // force epilogue scales
   std::vector<int32_t> tiles;    // density tiles in use: rt * CTd + ct
   std::vector<int32_t> tilemap;  // [RT * CTd] -> index into tiles, or -1
-  std::vector<int32_t> kmap;     // [(R1 + 1) (2 R2 + 1)] internal index of (n1, n2), or -1
+  std::vector<int32_t> em;       // [nP][R1 + 1][2] internal index of (n1, p) / (n1, -p), or -1
+  std::vector<int32_t> pvec;     // [nP] packed (n2, n3)
+  std::vector<int32_t> ks_ct;    // force K-steps per column tile
   int ntab = 0;                  // table entries per (axis, particle)
-  DevBuf dA, dB, fA, fB, a1, tab, acc, facc, kmap_d, tilemap_d, err;
+  size_t prep_smem = 0;          // dynamic shared memory of the preparation kernel
+  alignas(64) unsigned char tmap_h[256];  // host copy of the two tensor maps (source of the upload)
+  DevBuf wT, aB, fB, a1, tab, acc, facc, em_d, pvec_d, tilemap_d, tmap, err;
 };
 
 struct Ctx {
@@ -237,7 +248,7 @@ struct Ctx {
   dd inv_L;                       // 1 / L
   FireBufs* fire = nullptr;       // minimiser state, allocated on first ssh_minimize
   Engine* eng = nullptr;          // this context alone (plain evaluations)
-  bool tc_requested = false;      // fixed point on the tensor cores (d = 2)
+  bool tc_requested = false;      // fixed point on the tensor cores (d = 2, 3)
   TcPlan tc;
 };
 
@@ -289,7 +300,7 @@ cudaError_t fire_stage_init_engine(const Engine* e, const std::vector<int>& idx,
 // device scalar block written by k_finalize (doubles)
 enum { kScPhiHi = 0, kScPhiLo, kScSmaxHi, kScSmaxLo, kScCmax, kScScaleExp, kScA2MaxHi, kScA2MaxLo, kScCount = 16 };
 
-// tc.cu (tensor-core fixed-point path, d = 2)
+// tc.cu (tensor-core fixed-point path, d = 2 and 3)
 bool tc_eligible(const Ctx& c);
 int tc_finish_blocks(const Ctx& c);  // blocks of the density finish kernel (its reduction partials)
 cudaError_t tc_setup(Ctx* c);

@@ -1,35 +1,49 @@
-// tc.cu -- the fixed-point hot path for d = 2 on the tensor cores (Eqs. ntilde and force of arXiv:2304.09139).
+// tc.cu -- the fixed-point hot path for d = 2 and d = 3 on the tensor cores (Eqs. ntilde and force of
+// arXiv:2304.09139).
 //
-// With a_j(n1) = e^{2 pi i n1 s_j1} and b_j(n2) = e^{2 pi i n2 s_j2}, the collective density factorises per
-// axis, n~(n1, n2) = sum_j a_j(n1) b_j(n2): a matrix product over the particles.  Since b_j(-m) = conj(b_j(m)),
-// the four real products P_pq(n1, m) = sum_j p_j(n1) q_j(m) (p the cos / sin of axis 1, q of axis 2, m >= 0)
-// give both n~(n1, m) = (P_cc - P_ss) + i (P_cs + P_sc) and n~(n1, -m) = (P_cc + P_ss) + i (P_sc - P_cs):
-// one real GEMM with rows (n1, p), columns (m, q) and K = particles.
+// Write a wavevector as n = (n1, p), p = (n2) or (n2, n3), and the phasor of particle j per factor:
+// a_j(n1) = e^{2 pi i n1 s_j1}, w_j(p) = e^{2 pi i p . (s_j2, s_j3)}.  The collective density is then a matrix
+// product over the particles, n~(n1, p) = sum_j a_j(n1) w_j(p).  The half set H (first non-zero component > 0)
+// has n1 >= 0; p runs over a half of its plane, P = {p : n3 > 0, or n3 = 0 and n2 >= 0} ("canonical" p), since
+// every k in H is (n1, p) or (n1, -p) with p in P.  As a_j(-n1) = conj(a_j(n1)), the four real products
+// P_xy(p, n1) = sum_j x_j(p) y_j(n1) (x the cos / sin of w, y of a) give
+//   n~(n1, p)  = (P_cc - P_ss) + i (P_sc + P_cs),
+//   n~(n1, -p) = conj n~(-n1, p) = (P_cc + P_ss) + i (P_cs - P_sc):
+// one real GEMM with rows (p, cos / sin), columns (n1, cos / sin) and K = particles.  For d = 3, w_j(p) is the
+// product b_j(n2) c_j(n3) of the axis-2 and axis-3 powers, formed once per particle and p.
 //
-// The force F_j = (4 pi / L) sum_k n [C sin th - S cos th] = (4 pi / L) Im sum_k n W_k a_j(n1) b_j(n2), with
-// W = C - i S, is grouped per n1: G_j(n1) = sum_n2 W b_j(n2) = sum_{m >= 0} [U(n1, m) cos(2 pi m s_j2) +
-// V(n1, m) sin(2 pi m s_j2)], U = W(n1, m) + W(n1, -m), V = i (W(n1, m) - W(n1, -m)) (m = 0: U = W(n1, 0),
-// V = 0), and likewise G' with the weight n2.  Rows = particles, K = (m, cos / sin), columns = (n1, Re G,
-// Im G, Re G', Im G'); the epilogue forms F_j1 = (4 pi / L) Im sum n1 a_j(n1) G_j(n1) and F_j2 = (4 pi / L)
-// Im sum a_j(n1) G'_j(n1).
+// The force F_j = (4 pi / L) sum_k n [C sin th - S cos th] = (4 pi / L) Im sum_k n W_k e^{i th_jk}, W = C - i S,
+// is grouped per n1: G_j(n1) = sum_{p in P} [U(n1, p) cos(2 pi p . s_j) + V(n1, p) sin(2 pi p . s_j)] with
+// U = W(n1, p) + W(n1, -p), V = i (W(n1, p) - W(n1, -p)) (W = 0 off the set; p = 0 counted once), and
+// G^a_j(n1) with the weight n_a (a >= 2): U^a = n_a (W(n1, p) - W(n1, -p)), V^a = i n_a (W(n1, p) + W(n1, -p)).
+// Rows = particles, K = (p, cos / sin), columns = (n1, axis, Re / Im); the epilogue forms
+// F_j1 = (4 pi / L) Im sum n1 a_j(n1) G_j(n1) and F_ja = (4 pi / L) Im sum a_j(n1) G^a_j(n1).
 //
 // Both products use the exact digit arithmetic of tc.cuh: operands are 15 bf16 digit slices, the 120 kept
-// digit pairs accumulate into 15 TMEM level accumulators, read out exactly every 64 products.
+// digit pairs accumulate into 15 TMEM level accumulators, read out exactly every 256 products.  The digits of
+// w are written once, as a 4-D tensor [slice][row group][particle group][8 x 8 core] (a core: 8 rows (p, cos /
+// sin) x 8 particles, particles contiguous); the density GEMM reads it through a tensor-map box as its K-major A
+// operand (rows (p, cos / sin), K = particles) and the force GEMM through a second box as its MN-major A operand
+// (rows = particles, K = (p, cos / sin)).
 //
 // Kernels (one launch each per evaluation, over every tensor-core member of the engine):
-//   k_tc_prep         per particle: powers e^{2 pi i m s} of both axes (an exact-phase anchor every 16 powers,
-//                     one multiply per power in between), written as digit slices in the tile layouts of the
-//                     two GEMMs, and a_j(n1) as Q2.126 for the force epilogue
-//   k_tc_gemm         warp-specialised tcgen05 GEMM: one producer thread (bulk async copies, two stages), one
-//                     MMA thread (22 MMAs per K-step), eight epilogue warps (level read-out, exact folding)
-//   k_tc_dens_finish  fixed-order sum over K ranges, the four real products -> n~(n1, +-m) as Q34.126 partials
-//   k_tc_coef         U, V, U', V' from the exact n~ and the power-of-two scale, as digit slices of the force GEMM
+//   k_tc_tables       per (particle, axis): e^{2 pi i k s} (k < 8) and e^{2 pi i 8 b s} as first-quadrant phasors
+//   k_tc_prep         per 16 particles: a_j(n1) as digit slices of the density B operand and as Q2.126 for the
+//                     force epilogue; w_j(p) as the digit tensor
+//   k_tc_gemm         warp-specialised persistent tcgen05 GEMM: one producer thread (tensor-map and bulk async
+//                     copies, three stages), one MMA thread (22 MMAs per K-step), sixteen epilogue warps (level
+//                     read-out, exact folding, integer atomics)
+//   k_tc_dens_finish  the four real products -> n~(k) as Q34.126 partials and dd (C, S), Phi / S_max partials
+//   k_tc_coef         U, V, U^a, V^a from the exact n~ and the power-of-two scale, as digit slices of the force GEMM
+//   k_tc_force_finish force limbs -> dd F
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "fx.cuh"
 #include "reduce.cuh"
@@ -49,7 +63,7 @@ constexpr int kEpiWarps = 16;                      // four per TMEM lane quadran
 constexpr int kEpiCols = kTileN / (kEpiWarps / 4);  // accumulator columns per epilogue warp (8)
 constexpr int kGemmThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, epilogue warps
 constexpr long long kWaitLimit = 2000000000LL;     // clock cycles (about one second) for any single wait
-constexpr size_t kGemmSmem = (size_t)kStages * kStageBytes;
+constexpr size_t kGemmSmem = (size_t)kStages * kStageBytes + 128;  // + alignment slack of the stages
 constexpr int kFinThreads = 64;
 
 __device__ __forceinline__ bool stopped(const CfgDev& c) { return c.run && *c.run; }
@@ -172,17 +186,26 @@ namespace {
 
 constexpr int kPrepThreads = 256;
 constexpr int kPrepParticles = 16;  // particles per CTA (one K-step of the density GEMM)
-constexpr int kPrepM = 80;          // powers per pass (shared-memory staging of their fixed-point values)
+constexpr int kPrepM = 80;          // complex entries per pass (shared-memory staging of their fixed-point values)
 constexpr int kPrepLow = 8;         // e^{2 pi i m s} = A[m / 8] T[m % 8]
-constexpr int kPrepAnc = kPrepM / kPrepLow;
 constexpr int kPrepPitch = 2 * kPrepM + 1;  // staging row pitch (16-byte entries): odd, so rows spread over the banks
 constexpr size_t kPrepSmemY = (size_t)kPrepPitch * kPrepParticles * 16;
-constexpr size_t kPrepSmem = kPrepSmemY;
+constexpr size_t kPrepSmemMax = 200 * 1024;
+
+// conj of a first-quadrant phasor: conj(i^q (c + i s)) = i^{-q} (c - i s) = i^{3 - q} (s + i c)
+__device__ __forceinline__ qent qconj(const qent& z) {
+  qent r;
+  r.c = z.s;
+  r.s = z.c;
+  r.cs = z.cs;
+  r.cs.w[0] = (z.cs.w[0] & ~3u) | ((3u - (z.cs.w[0] & 3u)) & 3u);
+  return r;
+}
 
 // Eight biased values Y = X + B (X = round(x 2^104), B the balanced-digit offset) -> their 15 digits as one
 // 16-byte row (8 bf16) per digit slice, slice s holding digit 14 - s.  Digit i < 14 is bits 7i..7i+6 of Y
 // minus 64 (one funnel shift from two 32-bit words); the top digit is the signed bits 98..127.
-__device__ __forceinline__ void put_digit_rows(uint8_t* base, uint32_t slice_stride, const uint4 (&Y)[8]) {
+__device__ __forceinline__ void put_digit_rows(uint8_t* base, size_t slice_stride, const uint4 (&Y)[8]) {
 #pragma unroll
   for (int s = 0; s < kDigits; s++) {
     const int i = kDigits - 1 - s;
@@ -243,22 +266,22 @@ __device__ __forceinline__ void qent_out(const qent& z, uint4& yre, uint4& yim, 
   }
 }
 
+
 }  // namespace
 
 // Thread per (particle, axis): the tables T[k] = e^{2 pi i k s} (k < 8) and A[b] = e^{2 pi i 8 b s}
-// (b < ceil((R + 1) / 8)) as first-quadrant phasors, from exact-phase values of e^{2 pi i s} and e^{2 pi i 8 s}
-// and chains of multiplies (each product at most 8 units of 2^-126 low; about 17 in the longest chain).
+// (b <= Rax / 8) as first-quadrant phasors, from exact-phase values of e^{2 pi i s} and e^{2 pi i 8 s} and
+// chains of multiplies (each product at most 8 units of 2^-126 low; about 17 in the longest chain).
 // Grid (particle blocks, tensor-core members); layout tc_tab[(axis N + j) tc_ntab + (k | 8 + b)].
 __global__ void __launch_bounds__(128) k_tc_tables(const CfgDev* __restrict__ cfgs, const int* __restrict__ list) {
   grid_dep_wait();
   const CfgDev& c = cfgs[list[blockIdx.y]];
   if (stopped(c)) return;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= 2 * c.N) return;
+  if (idx >= (int64_t)c.d * c.N) return;
   const int axis = (int)(idx / c.N);
   const int64_t j = idx - (int64_t)axis * c.N;
-  const int R = axis == 0 ? c.tc_R1 : c.tc_R2;
-  const int nA = R / kPrepLow + 1;
+  const int nA = c.tc_Rax[axis] / kPrepLow + 1;
   const q128 u = turns_from_dd(c.s_hi[axis * c.N + j], c.s_lo[axis * c.N + j]);
   qent* tab = reinterpret_cast<qent*>(c.tc_tab) + idx * c.tc_ntab;
   const qent one = to_quadrant(phasor_turn(q128_zero()));
@@ -278,82 +301,92 @@ __global__ void __launch_bounds__(128) k_tc_tables(const CfgDev* __restrict__ cf
   }
 }
 
-// CTA per (configuration, axis, 16 particles); items TwItem {cfg, axis, first particle}.  Per pass over at
-// most 80 powers m0.. : phase 1 forms every power as one product A[m / 8] T[m % 8] of the particle's tables
-// (all threads, independent) into shared memory; phase 2 writes the digit slices as whole 16-byte
-// core-matrix rows (8 K-consecutive values of one operand row), which consecutive threads fill contiguously.
-// Axis 1 (n1) feeds the density GEMM's A operand and the Q2.126 table a_j(n1) of the force epilogue; axis 2
-// feeds the density GEMM's B operand and the force GEMM's A operand.
+// CTA per (configuration, kind, 16 particles); items TwItem {cfg, kind, first particle}.
+// Kind 0: a_j(n1), n1 in [0, R1] -> density B digit slices (rows (n1, cos / sin) of K-major 32 x 16 tiles) and
+// the Q2.126 table of the force epilogue.  Kind 1: w_j(p) for the nP canonical p -> the digit tensor.  Per pass
+// over at most 80 entries: phase 1 forms every entry as one product (all threads, independent) into shared
+// memory; phase 2 writes the digit slices as whole 16-byte core-matrix rows (one row (entry, cos / sin), eight
+// particles), which consecutive threads fill contiguously.  For d = 3 the CTA's axis-2 and axis-3 powers b_j(n2),
+// c_j(n3) (n2, n3 >= 0) are staged in shared memory first (phase 0); b_j(-n2) = conj b_j(n2).
 __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restrict__ cfgs,
                                                           const TwItem* __restrict__ items) {
   grid_dep_wait();
   extern __shared__ __align__(16) uint8_t psm[];
-  uint4* Ys = reinterpret_cast<uint4*>(psm);  // [j][2 (m - m0) + p], pitch kPrepPitch
+  uint4* Ys = reinterpret_cast<uint4*>(psm);  // [j][2 (entry - m0) + p], pitch kPrepPitch
+  qent* Pw = reinterpret_cast<qent*>(psm + kPrepSmemY);
   const TwItem it = items[blockIdx.x];
   const CfgDev& c = cfgs[it.cfg];
   if (stopped(c)) return;
-  const int axis = it.pad;
+  const int kind = it.pad;
   const int64_t N = c.N;
   const int64_t j0 = it.start;
-  const int R = axis == 0 ? c.tc_R1 : c.tc_R2;
   const int tid = threadIdx.x;
   const __int128 bias = digit_bias();
   const uint4 yzero = make_uint4((uint32_t)bias, (uint32_t)(bias >> 32), (uint32_t)(bias >> 64), (uint32_t)(bias >> 96));
   const qent* tab = reinterpret_cast<const qent*>(c.tc_tab);
-  for (int m0 = 0; m0 <= R; m0 += kPrepM) {
-    const int mcount = min(kPrepM, R + 1 - m0);
-    // phase 1: every (particle, power) of the pass, one product each
+  const bool three = c.d == 3;
+  const int W2 = c.tc_Rax[1] + 1, W23 = W2 + (three ? c.tc_Rax[2] + 1 : 0);
+  if (kind == 1 && three) {
+    for (int task = tid; task < kPrepParticles * W23; task += kPrepThreads) {
+      const int jl = task % kPrepParticles, e = task / kPrepParticles;
+      const int64_t j = min(j0 + jl, N - 1);  // rows of particles past N are never read
+      const int axis = e < W2 ? 1 : 2;
+      const int m = e < W2 ? e : e - W2;
+      const qent* tj = tab + ((int64_t)axis * N + j) * c.tc_ntab;
+      Pw[jl * W23 + e] = qmul(tj[kPrepLow + (m >> 3)], tj[m & 7]);
+    }
+    __syncthreads();
+  }
+  const int count = kind == 0 ? c.tc_R1 + 1 : c.tc_nP;
+  const size_t wstride = (size_t)c.tc_NPg * (size_t)c.tc_NJ * 128;  // bytes between digit slices of the tensor
+  for (int m0 = 0; m0 < count; m0 += kPrepM) {
+    const int mcount = min(kPrepM, count - m0);
+    // phase 1: every (particle, entry) of the pass, one product each
     for (int task = tid; task < mcount * kPrepParticles; task += kPrepThreads) {
       const int jl = task % kPrepParticles, ml = task / kPrepParticles;
       const int64_t j = j0 + jl;
-      const int m = m0 + ml;
+      const int e = m0 + ml;
       uint4 yr = yzero, yi = yzero;
       if (j < N) {
-        const qent* tj = tab + ((int64_t)axis * N + j) * c.tc_ntab;
-        const qent z = qmul(tj[kPrepLow + (m >> 3)], tj[m & 7]);
-        fxc zq;
-        qent_out(z, yr, yi, axis == 0 ? &zq : nullptr);
-        if (axis == 0) reinterpret_cast<fxc*>(c.tc_a1)[(int64_t)m * N + j] = zq;
+        if (kind == 0) {
+          const qent* tj = tab + j * c.tc_ntab;
+          const qent z = qmul(tj[kPrepLow + (e >> 3)], tj[e & 7]);
+          fxc zq;
+          qent_out(z, yr, yi, &zq);
+          reinterpret_cast<fxc*>(c.tc_a1)[(int64_t)e * N + j] = zq;
+        } else {
+          const int32_t pv = c.tc_pvec[e];
+          const int n2 = (int)(int16_t)(pv & 0xffff), n3 = pv >> 16;
+          qent z;
+          if (three) {
+            const qent b = Pw[jl * W23 + (n2 < 0 ? -n2 : n2)];
+            z = qmul(n2 < 0 ? qconj(b) : b, Pw[jl * W23 + W2 + n3]);
+          } else {
+            const qent* tj = tab + (N + j) * c.tc_ntab;  // n2 >= 0 in d = 2
+            z = qmul(tj[kPrepLow + (n2 >> 3)], tj[n2 & 7]);
+          }
+          qent_out(z, yr, yi, nullptr);
+        }
       }
       Ys[jl * kPrepPitch + ml * 2 + 0] = yr;
       Ys[jl * kPrepPitch + ml * 2 + 1] = yi;
     }
     __syncthreads();
-    // phase 2a: rows (m, cos / sin) x 8 particles, into the density GEMM operand of this axis
+    // phase 2: rows (entry, cos / sin) x 8 particles
     const int nrow = 2 * mcount;
     for (int task = tid; task < nrow * (kPrepParticles / 8); task += kPrepThreads) {
       const int rl = task % nrow, g8 = task / nrow;
       const int r = 2 * m0 + rl;
       const int64_t jg = j0 + 8 * g8;
-      if (jg >= N) continue;  // K-steps past the last particle stay zero
+      if (jg >= N) continue;  // particle groups past the last particle stay zero
       uint4 Y[8];
 #pragma unroll
       for (int v = 0; v < 8; v++) Y[v] = Ys[(8 * g8 + v) * kPrepPitch + rl];
-      const int64_t ks = jg >> 4;
-      const int k0 = (int)(jg & 15);
-      if (axis == 0)
-        put_digit_rows(c.tc_dA + ((int64_t)(r >> 7) * c.tc_KS + ks) * kStageA + slice_off(r & 127, k0), kSliceA, Y);
+      if (kind == 0)
+        put_digit_rows(c.tc_aB + ((int64_t)(r >> 5) * c.tc_KS + (jg >> 4)) * kStageB + slice_off(r & 31, (int)(jg & 15)),
+                       kSliceB, Y);
       else
-        put_digit_rows(c.tc_dB + ((int64_t)(r >> 5) * c.tc_KS + ks) * kStageB + slice_off(r & 31, k0), kSliceB, Y);
-    }
-    // phase 2b (axis 2): particles x 8 values of (m, cos / sin), into the force GEMM's A operand
-    if (axis == 1) {
-      const int groups = (nrow + 7) / 8;  // 2 m0 is a multiple of 8; a partial last group is padded with zeros
-      const uint4 yz = yzero;
-      for (int task = tid; task < groups * kPrepParticles; task += kPrepThreads) {
-        const int jl = task % kPrepParticles, g = task / kPrepParticles;
-        const int64_t j = j0 + jl;
-        if (j >= N) continue;
-        uint4 Y[8];
-#pragma unroll
-        for (int v = 0; v < 8; v++) {
-          const int rl = 8 * g + v;
-          Y[v] = rl < nrow ? Ys[jl * kPrepPitch + rl] : yz;
-        }
-        const int kf0 = 2 * m0 + 8 * g;
-        put_digit_rows(c.tc_fA + ((int64_t)(j >> 7) * c.tc_KSf + (kf0 >> 4)) * kStageA + slice_off((int)(j & 127), kf0 & 15),
-                       kSliceA, Y);
-      }
+        put_digit_rows(c.tc_wT + ((size_t)(r >> 3) * (size_t)c.tc_NJ + (size_t)(jg >> 3)) * 128 + (r & 7) * 16, wstride, Y);
     }
     __syncthreads();
   }
@@ -361,16 +394,20 @@ __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restri
 
 // ------------------------------------------------------------------------------------------------ k_tc_gemm
 
-// Persistent: CTA b takes items b, b + gridDim.x, ...  Density items: A = density row tile it.a, B = column
-// tile it.b, K-steps [ks0, ks0 + nks); the epilogue stores the three int64 level groups of every output into
-// tc_part slot it.slot.  Force items: A = particle tile it.a, B = column tile it.b (8 values of n1), every
-// K-step; the epilogue writes force partials fpart[2 it.b + half][axis][j].  Stage and accumulator barrier
-// phases run on across items, so the producer streams the next item's operands while the epilogue finishes
-// the previous item (the accumulator is released as soon as its last level has been read).
+// Persistent: CTA b takes items b, b + gridDim.x, ...  Density items: A = rows (p, cos / sin) of row tile it.a
+// (tensor-map box, K-major), B = column tile it.b of the a_j(n1) slices, K-steps [ks0, ks0 + nks) of 16
+// particles; the epilogue adds the three int64 level groups of every output into tile accumulator it.slot.
+// Force items: A = particle tile it.a (tensor-map box, MN-major), B = column tile it.b (16 / d values of n1, all
+// axes) of the coefficient slices, K-steps of 16 rows (p, cos / sin); the epilogue adds the tile's force limbs.
+// Stage and accumulator barrier phases run on across items, so the producer streams the next item's operands
+// while the epilogue finishes the previous item (the accumulator is released as soon as its last level has
+// been read).
 __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __restrict__ cfgs,
                                                               const TcItem* __restrict__ items, int n_items) {
   grid_dep_wait();
-  extern __shared__ __align__(128) uint8_t smem[];
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  // tensor-map destinations must be 128-byte aligned
+  uint8_t* smem = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
   __shared__ uint64_t bar_full[kStages], bar_empty[kStages], bar_acc_full, bar_acc_empty, bar_drain;
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
@@ -402,15 +439,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
         const TcItem it = items[item];
         const CfgDev& c = cfgs[it.cfg];
         if (stopped(c)) continue;
-        const uint8_t* gA;
-        const uint8_t* gB;
-        if (it.kind == 0) {
-          gA = c.tc_dA + ((int64_t)it.a * c.tc_KS + it.ks0) * kStageA;
-          gB = c.tc_dB + ((int64_t)it.b * c.tc_KS + it.ks0) * kStageB;
-        } else {
-          gA = c.tc_fA + ((int64_t)it.a * c.tc_KSf + it.ks0) * kStageA;
-          gB = c.tc_fB + ((int64_t)it.b * c.tc_KSf + it.ks0) * kStageB;
-        }
+        const void* tmap = reinterpret_cast<const uint8_t*>(c.tc_tmap) + (it.kind == 0 ? 0 : 128);
+        tmap_acquire(tmap);
+        const uint8_t* gB = it.kind == 0 ? c.tc_aB + ((int64_t)it.b * c.tc_KS + it.ks0) * kStageB
+                                         : c.tc_fB + ((int64_t)it.b * c.tc_KSf + it.ks0) * kStageB;
         for (int ks = 0; ks < it.nks; ks++, gs++) {
           const int s = (int)(gs % kStages);
           const long long use = gs / kStages;
@@ -421,8 +453,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
             break;
           }
           uint8_t* dst = smem + (size_t)s * kStageBytes;
+          const int kg = it.ks0 + ks;
           mbar_expect_tx(&bar_full[s], kStageBytes);
-          bulk_g2s(dst, gA + (size_t)ks * kStageA, kStageA, &bar_full[s]);
+          if (it.kind == 0)
+            tma_load_4d(dst, tmap, 0, 2 * kg, 16 * it.a, 0, &bar_full[s]);  // particle groups 2 kg, +1; row groups 16 a..
+          else
+            tma_load_4d(dst, tmap, 0, 16 * it.a, 2 * kg, 0, &bar_full[s]);  // particle groups 16 a..; row groups 2 kg, +1
           bulk_g2s(dst + kStageA, gB + (size_t)ks * kStageB, kStageB, &bar_full[s]);
         }
       }
@@ -441,6 +477,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
         const TcItem it = items[item];
         const CfgDev& c = cfgs[it.cfg];
         if (stopped(c)) continue;
+        // density A: K-major, core matrices 128 bytes apart along K and 256 along M; force A: MN-major, 128
+        // bytes apart along M (particles) and 2048 along K
+        const int mn = it.kind == 0 ? 0 : 1;
+        const uint32_t lbo = mn ? 2048u : 128u, sbo = mn ? 128u : 256u;
         for (int ks = 0; ks < it.nks; ks++, gs++) {
           const int s = (int)(gs % kStages);
           const long long use = gs / kStages;
@@ -466,10 +506,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
             const int ntot = (kLevels - sl) * kTileN;
             const int n1 = ntot < 256 ? ntot : 256;
             const uint32_t acc = (first && sl == 0) ? 0u : 1u;
-            const uint64_t ad = make_sdesc(a0 + sl * kSliceA);
-            mma_bf16(tbase + sl * kTileN, ad, make_sdesc(b0), make_idesc(kTileM, n1), acc);
+            const uint64_t ad = make_sdesc(a0 + sl * kSliceA, lbo, sbo);
+            mma_bf16(tbase + sl * kTileN, ad, make_sdesc(b0), make_idesc(kTileM, n1, mn), acc);
             if (ntot > 256)
-              mma_bf16(tbase + sl * kTileN + 256, ad, make_sdesc(b0 + 256 * 32), make_idesc(kTileM, ntot - 256), acc);
+              mma_bf16(tbase + sl * kTileN + 256, ad, make_sdesc(b0 + 256 * 32), make_idesc(kTileM, ntot - 256, mn), acc);
           }
           mma_commit(&bar_empty[s]);
           if (last) {
@@ -541,44 +581,46 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
           for (int i = 0; i < kEpiCols; i++)
             atomicAdd(out + ((size_t)g * kTileN + kEpiCols * hq + i) * kTileM + row, (unsigned long long)st[g][i]);
       } else {
-        // two n1 values per warp, columns (Re G, Im G, Re G', Im G') each.  G~ = R' 2^-110 is taken as R' 2^gs
-        // (|.| < 2^126); the top halves of a * G are value 2^(108 + gs), shifted to value 2^ts.
+        // column tile ct: the 16 / d values n1 = (16 / d) ct + i / d, every axis t = i % d of each, as column
+        // pairs (Re G, Im G) i = 0, 1, ...; this warp holds pairs 4 hq .. 4 hq + 3.  G~ = R' 2^-110 is taken as
+        // R' 2^gs (|.| < 2^126); the top halves of a * G are value 2^(108 + gs), shifted to value 2^ts.
         const int64_t j = (int64_t)it.a * kTileM + row;
+        const int d = c.d, npt = 16 / d;
         const int gsh = c.tc_gs, tsh = 108 + c.tc_gs - c.tc_ts;
-        __int128 F1 = 0, F2 = 0;  // value 2^ts
+        __int128 F0 = 0, F1 = 0, F2 = 0;  // per axis, value 2^ts (at most four terms each)
 #pragma unroll
-        for (int v = 0; v < kEpiCols / 4; v++) {
-          const int n1 = it.b * (kTileN / 4) + hq * (kEpiCols / 4) + v;
-          if (n1 > c.tc_R1 || j >= c.N) continue;
-          q128 gcol[4];
-#pragma unroll
-          for (int g4 = 0; g4 < 4; g4++) {
-            const int i = 4 * v + g4;
-            const __int128 R = ((__int128)st[0][i] << 70) + ((__int128)st[1][i] << 35) + (__int128)st[2][i];
-            gcol[g4] = q128_from_i128(R << gsh);
+        for (int v = 0; v < kEpiCols / 2; v++) {
+          const int i = (kEpiCols / 2) * hq + v;
+          const int n1 = npt * it.b + i / d, t = i - (i / d) * d;
+          if (i >= npt * d || n1 > c.tc_R1 || j >= c.N) continue;
+          q128 gre, gim;
+          {
+            const __int128 Rr = ((__int128)st[0][2 * v] << 70) + ((__int128)st[1][2 * v] << 35) + (__int128)st[2][2 * v];
+            const __int128 Ri =
+                ((__int128)st[0][2 * v + 1] << 70) + ((__int128)st[1][2 * v + 1] << 35) + (__int128)st[2][2 * v + 1];
+            gre = q128_from_i128(Rr << gsh);
+            gim = q128_from_i128(Ri << gsh);
           }
           const fxc a = reinterpret_cast<const fxc*>(c.tc_a1)[(int64_t)n1 * c.N + j];
           uint32_t p[5], r2[5];
           // Im(a G) = Re a Im G + Im a Re G
-          smul_top(a.re, gcol[1], p);
-          smul_top(a.im, gcol[0], r2);
-          __int128 T = (q128_to_i128(q128{{p[1], p[2], p[3], p[4]}}) + q128_to_i128(q128{{r2[1], r2[2], r2[3], r2[4]}})) >> tsh;
-          F1 += T * (__int128)n1;
-          smul_top(a.re, gcol[3], p);
-          smul_top(a.im, gcol[2], r2);
-          T = (q128_to_i128(q128{{p[1], p[2], p[3], p[4]}}) + q128_to_i128(q128{{r2[1], r2[2], r2[3], r2[4]}})) >> tsh;
-          F2 += T;
+          smul_top(a.re, gim, p);
+          smul_top(a.im, gre, r2);
+          const __int128 T =
+              (q128_to_i128(q128{{p[1], p[2], p[3], p[4]}}) + q128_to_i128(q128{{r2[1], r2[2], r2[3], r2[4]}})) >> tsh;
+          if (t == 0) F0 += T * (__int128)n1;
+          else if (t == 1) F1 += T;
+          else F2 += T;
         }
         if (j < c.N) {
-          // F = L2 2^88 + L1 2^44 + L0 (L0, L1 in [0, 2^44)): the limbs of all column blocks add up exactly
-          unsigned long long* fa = reinterpret_cast<unsigned long long*>(c.tc_facc);
+          // F = L2 2^88 + L1 2^44 + L0 (L0, L1 in [0, 2^44)): the limbs of all column tiles add up exactly
           const unsigned long long m44 = (1ull << 44) - 1;
-#pragma unroll
-          for (int a = 0; a < 2; a++) {
-            const __int128 F = a == 0 ? F1 : F2;
-            atomicAdd(fa + ((size_t)a * 3 + 0) * c.N + j, (unsigned long long)F & m44);
-            atomicAdd(fa + ((size_t)a * 3 + 1) * c.N + j, (unsigned long long)(F >> 44) & m44);
-            atomicAdd(fa + ((size_t)a * 3 + 2) * c.N + j, (unsigned long long)(long long)(F >> 88));
+          for (int t = 0; t < d; t++) {
+            const __int128 F = t == 0 ? F0 : (t == 1 ? F1 : F2);
+            unsigned long long* fa = reinterpret_cast<unsigned long long*>(c.tc_facc) + (size_t)t * 3 * c.N + j;
+            atomicAdd(fa, (unsigned long long)F & m44);
+            atomicAdd(fa + c.N, (unsigned long long)(F >> 44) & m44);
+            atomicAdd(fa + 2 * c.N, (unsigned long long)(long long)(F >> 88));
           }
         }
       }
@@ -594,9 +636,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
 
 // ------------------------------------------------------------------------------------------------ finish
 
-// grid (finish blocks, tensor-core members), 64 threads: n~(n1, m), n~(n1, -m) from the four real products of
-// the tile accumulator (which it clears for the next evaluation), as exact Q34.126 values (for the force
-// coefficients) and as dd (C, S), with the block's Phi / max |n~|^2 / max |C|, |S| partials.
+// grid (finish blocks, tensor-core members), 64 threads, thread per (n1, p), n1 fastest: n~(n1, p) and
+// n~(n1, -p) from the four real products of the tile accumulator (which it clears for the next evaluation), as
+// exact Q34.126 values (for the force coefficients) and as dd (C, S), with the block's Phi / max |n~|^2 /
+// max |C|, |S| partials.
 __global__ void __launch_bounds__(kFinThreads) k_tc_dens_finish(const CfgDev* __restrict__ cfgs,
                                                                 const int* __restrict__ list) {
   grid_dep_wait();
@@ -605,38 +648,37 @@ __global__ void __launch_bounds__(kFinThreads) k_tc_dens_finish(const CfgDev* __
   RedPart v = {0, 0, 0, 0, 0, 0, 0, 0};
   const int W1 = c.tc_R1 + 1;
   const int64_t idx = (int64_t)blockIdx.x * kFinThreads + threadIdx.x;
-  if (idx < (int64_t)W1 * (c.tc_R2 + 1)) {
-    const int n1 = (int)(idx % W1), m = (int)(idx / W1);  // n1 fastest: neighbours read neighbouring rows
-    const int span = 2 * c.tc_R2 + 1;
-    const int kp = c.tc_kmap[(int64_t)n1 * span + (c.tc_R2 + m)];
-    const int km = m > 0 ? c.tc_kmap[(int64_t)n1 * span + (c.tc_R2 - m)] : -1;
-    const int r = 2 * n1, col = 2 * m;
+  if (idx < (int64_t)W1 * c.tc_nP) {
+    const int n1 = (int)(idx % W1), p = (int)(idx / W1);
+    const int kp = c.tc_em[idx * 2 + 0], km = c.tc_em[idx * 2 + 1];  // em is [p][n1][2]
+    const int r = 2 * p, col = 2 * n1;
     const int ti = (kp >= 0 || km >= 0) ? c.tc_tilemap[(r >> 7) * c.tc_CTd + (col >> 5)] : -1;
     if (ti >= 0) {
       const int rr = r & 127, cc = col & 31;
       long long* acc = c.tc_acc + (size_t)ti * (3 * kTileN * kTileM);
-      long long P[4][3];  // 0 = cos cos, 1 = cos sin, 2 = sin cos, 3 = sin sin
+      long long P[4][3];  // [2 x + y]: x the cos / sin of w (row), y of a (column)
 #pragma unroll
-      for (int p = 0; p < 2; p++)
+      for (int x = 0; x < 2; x++)
 #pragma unroll
-        for (int qq = 0; qq < 2; qq++)
+        for (int y = 0; y < 2; y++)
 #pragma unroll
           for (int g = 0; g < 3; g++) {
-            long long* e = acc + ((size_t)g * kTileN + cc + qq) * kTileM + rr + p;
-            P[2 * p + qq][g] = *e;
+            long long* e = acc + ((size_t)g * kTileN + cc + y) * kTileM + rr + x;
+            P[2 * x + y][g] = *e;
             *e = 0;
           }
       FxAcc* part = reinterpret_cast<FxAcc*>(c.part);
-      // C = P_cc + ss_sign P_ss, S = cs_sign P_cs + P_sc
-      auto emit = [&](int k, int ss_sign, int cs_sign) {
+      // C = P_cc + ss P_ss, S = s1 P_cs + s2 P_sc
+      auto emit = [&](int k, int ss, int s1, int s2) {
         i192 C, S;
         i192_zero(C);
         i192_zero(S);
 #pragma unroll
         for (int g = 0; g < 3; g++) {
           const int sh = 70 - 35 * g;
-          i192_add_shl(C, (__int128)P[0][g] + (ss_sign > 0 ? (__int128)P[3][g] : -(__int128)P[3][g]), sh);
-          i192_add_shl(S, (cs_sign > 0 ? (__int128)P[1][g] : -(__int128)P[1][g]) + (__int128)P[2][g], sh);
+          i192_add_shl(C, (__int128)P[0][g] + (ss > 0 ? (__int128)P[3][g] : -(__int128)P[3][g]), sh);
+          i192_add_shl(S, (s1 > 0 ? (__int128)P[1][g] : -(__int128)P[1][g]) + (s2 > 0 ? (__int128)P[2][g] : -(__int128)P[2][g]),
+                       sh);
         }
         FxAcc o;
         o.re = i192_to_q160_shl(C, 16);  // value 2^-110 -> Q34.126
@@ -656,8 +698,8 @@ __global__ void __launch_bounds__(kFinThreads) k_tc_dens_finish(const CfgDev* __
         t.cmax = fmax(fabs(cd.hi), fabs(sd.hi));
         red_combine(v, t);
       };
-      if (kp >= 0) emit(kp, -1, +1);  // n~(n1, m) = (P_cc - P_ss) + i (P_cs + P_sc)
-      if (km >= 0) emit(km, +1, -1);  // n~(n1, -m) = (P_cc + P_ss) + i (P_sc - P_cs)
+      if (kp >= 0) emit(kp, -1, +1, +1);  // n~(n1, p)  = (P_cc - P_ss) + i (P_cs + P_sc)
+      if (km >= 0) emit(km, +1, +1, -1);  // n~(n1, -p) = (P_cc + P_ss) + i (P_cs - P_sc)
     }
   }
   red_warp(v);
@@ -680,7 +722,7 @@ __global__ void __launch_bounds__(kFinThreads) k_tc_force_finish(const CfgDev* _
   const CfgDev& c = cfgs[list[blockIdx.y]];
   if (stopped(c)) return;
   const int64_t i = (int64_t)blockIdx.x * kFinThreads + threadIdx.x;  // over [a][j]
-  if (i >= 2 * c.N) return;
+  if (i >= (int64_t)c.d * c.N) return;
   const int a = (int)(i / c.N);
   const int64_t j = i - (int64_t)a * c.N;
   long long* fa = c.tc_facc + (size_t)a * 3 * c.N + j;
@@ -693,60 +735,69 @@ __global__ void __launch_bounds__(kFinThreads) k_tc_force_finish(const CfgDev* _
   i192_add_shl(X, (__int128)L0, 0);
   i192_add_shl(X, (__int128)L1, 44);
   i192_add_shl(X, (__int128)L2, 88);
-  // value = X 2^-ts in units of 2^e (axis 2: of 2^(e + bexp))
+  // value = X 2^-ts in units of 2^e (axes 2, 3: of 2^(e + bexp))
   const int e = (int)c.scal[kScScaleExp];
   dd f = dd_mul(i192_to_dd(X, c.tc_ts), c.pref);
-  const double sc = pow2(e + (a == 1 ? c.tc_bexp : 0));
+  const double sc = pow2(e + (a > 0 ? c.tc_bexp : 0));
   c.F_hi[i] = f.hi * sc;
   c.F_lo[i] = f.lo * sc;
 }
 
-// grid ((R1 + 1) (R2 + 1) / 128 blocks, tensor-core members): the force GEMM's coefficient digits
+// grid ((R1 + 1) nP / 128 blocks, tensor-core members), thread per (n1, p), p fastest: the force GEMM's
+// coefficient digits of every axis
 __global__ void k_tc_coef(const CfgDev* __restrict__ cfgs, const int* __restrict__ list) {
   grid_dep_wait();
   const CfgDev& c = cfgs[list[blockIdx.y]];
   if (stopped(c)) return;
-  const int W2 = c.tc_R2 + 1;
+  const int W1 = c.tc_R1 + 1;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)(c.tc_R1 + 1) * W2) return;
-  const int n1 = (int)(idx / W2), m = (int)(idx % W2);
-  const int span = 2 * c.tc_R2 + 1;
-  const int kp = c.tc_kmap[(int64_t)n1 * span + (c.tc_R2 + m)];
-  const int km = m > 0 ? c.tc_kmap[(int64_t)n1 * span + (c.tc_R2 - m)] : -1;
+  if (idx >= (int64_t)W1 * c.tc_nP) return;
+  const int n1 = (int)(idx / c.tc_nP), p = (int)(idx % c.tc_nP);
+  const int32_t* em = c.tc_em + ((int64_t)p * W1 + n1) * 2;
+  const int kp = em[0], km = em[1];
   const FxAcc* part = reinterpret_cast<const FxAcc*>(c.part);
   const q160 z = q160_zero();
   const q160 Cp = kp >= 0 ? load_q160(&part[kp].re) : z, Sp = kp >= 0 ? load_q160(&part[kp].im) : z;
   const q160 Cm = km >= 0 ? load_q160(&part[km].re) : z, Sm = km >= 0 ? load_q160(&part[km].im) : z;
   const int e = (int)c.scal[kScScaleExp];
+  const int32_t pv = c.tc_pvec[p];
+  const int nw[3] = {1, (int)(int16_t)(pv & 0xffff), pv >> 16};
+  const bool p0 = pv == 0;
   // W = C - i S:  Re U = C+ + C-,  Im U = -(S+ + S-),  Re V = S+ - S-,  Im V = C+ - C-
-  //               Re U' = m (C+ - C-), Im U' = -m (S+ - S-), Re V' = m (S+ + S-), Im V' = m (C+ + C-)
-  q160 cpl = Cp, cmi = Cp, spl = Sp, smi = Sp;
+  //               Re U^a = n_a (C+ - C-), Im U^a = -n_a (S+ - S-), Re V^a = n_a (S+ + S-), Im V^a = n_a (C+ + C-)
+  q160 cpl = Cp, spl = Sp;
   q160_add160(cpl, Cm);
-  cmi = q160_sub160(Cp, Cm);
+  const q160 cmi = q160_sub160(Cp, Cm);
   q160_add160(spl, Sm);
-  smi = q160_sub160(Sp, Sm);
+  const q160 smi = q160_sub160(Sp, Sm);
   const int shG = 22 + e, shW = 22 + e + c.tc_bexp;
-  __int128 X[4][2];
-  X[0][0] = q160_shr_round(cpl, shG);
-  X[0][1] = q160_shr_round(smi, shG);
-  X[1][0] = -q160_shr_round(spl, shG);
-  X[1][1] = q160_shr_round(cmi, shG);
-  X[2][0] = q160_shr_round(q160_mul_int(cmi, m), shW);
-  X[2][1] = q160_shr_round(q160_mul_int(spl, m), shW);
-  X[3][0] = -q160_shr_round(q160_mul_int(smi, m), shW);
-  X[3][1] = q160_shr_round(q160_mul_int(cpl, m), shW);
-  if (m == 0) {  // sin(0) = 0 and the weight n2 = 0
-    X[0][1] = X[1][1] = 0;
-    X[2][0] = X[2][1] = X[3][0] = X[3][1] = 0;
-  }
+  const int kf = 2 * p;
+  for (int t = 0; t < c.d; t++) {
+    __int128 X[2][2];  // [Re / Im column][cos / sin row]
+    if (t == 0) {
+      X[0][0] = q160_shr_round(cpl, shG);
+      X[0][1] = q160_shr_round(smi, shG);
+      X[1][0] = -q160_shr_round(spl, shG);
+      X[1][1] = q160_shr_round(cmi, shG);
+    } else {
+      const int n = nw[t];
+      X[0][0] = q160_shr_round(q160_mul_int(cmi, n), shW);
+      X[0][1] = q160_shr_round(q160_mul_int(spl, n), shW);
+      X[1][0] = -q160_shr_round(q160_mul_int(smi, n), shW);
+      X[1][1] = q160_shr_round(q160_mul_int(cpl, n), shW);
+    }
+    if (p0) X[0][1] = X[1][1] = 0;  // sin(0) = 0 (and every weight n_a is 0)
+    const int npt = 16 / c.d;         // n1 values per column tile, all axes of each
+    const int ct = n1 / npt;
 #pragma unroll
-  for (int g = 0; g < 4; g++) {
-    const int col = 4 * n1 + g;
+    for (int ri = 0; ri < 2; ri++) {
+      const int col = 2 * (c.d * (n1 - ct * npt) + t) + ri;
 #pragma unroll
-    for (int qq = 0; qq < 2; qq++) {
-      const int kf = 2 * m + qq;
-      uint8_t* base = c.tc_fB + ((int64_t)(col >> 5) * c.tc_KSf + (kf >> 4)) * kStageB;
-      put_digits_x(base, kSliceB, slice_off(col & 31, kf & 15), X[g][qq]);
+      for (int qq = 0; qq < 2; qq++) {
+        const int kk = kf + qq;
+        uint8_t* base = c.tc_fB + ((int64_t)ct * c.tc_KSf + (kk >> 4)) * kStageB;
+        put_digits_x(base, kSliceB, slice_off(col, kk & 15), X[ri][qq]);
+      }
     }
   }
 }
@@ -761,83 +812,198 @@ static cudaError_t tc_dev_alloc(DevBuf* b, size_t bytes, cudaStream_t st) {
   return cudaMemsetAsync(b->p, 0, bytes, st);  // padding rows, columns and K stay zero for good
 }
 
-bool tc_eligible(const Ctx& c) { return c.d == 2 && c.N >= 1 && c.M >= 1; }
+bool tc_eligible(const Ctx& c) { return (c.d == 2 || c.d == 3) && c.N >= 1 && c.M >= 1; }
 
 int tc_finish_blocks(const Ctx& c) {
   if (!c.tc.on) return 0;
-  return (int)(((int64_t)(c.tc.R1 + 1) * (c.tc.R2 + 1) + kFinThreads - 1) / kFinThreads);
+  return (int)(((int64_t)(c.tc.R1 + 1) * c.tc.nP + kFinThreads - 1) / kFinThreads);
 }
 
-// Tile plan and device buffers of one configuration.
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// sub-vector p = (n2, n3) of axes 2..d of internal wavevector k (n3 = 0 for d = 2)
+inline void sub_vec(const Ctx& c, int64_t k, int& n1, int& n2, int& n3) {
+  const int32_t* n = &c.ks.n_int[(size_t)k * c.d];
+  n1 = n[0];
+  n2 = n[1];
+  n3 = c.d == 3 ? n[2] : 0;
+}
+inline bool canonical(int n2, int n3) { return n3 > 0 || (n3 == 0 && n2 >= 0); }
+
+}  // namespace
+
+// Tile plan and device buffers of one configuration.  Returns success with t.on = false when the configuration
+// does not fit the path's limits (the integer-pipe kernels serve it then).
 cudaError_t tc_setup(Ctx* c) {
   TcPlan& t = c->tc;
-  t = TcPlan();
-  if (!c->tc_requested || !tc_eligible(*c)) return cudaSuccess;
-  const KSet& ks = c->ks;
-  t.R1 = std::max(0, ks.nmax[0]);
-  t.R2 = std::max(std::abs(ks.nmin[1]), std::abs(ks.nmax[1]));
-  t.KS = (c->N + kStepK - 1) / kStepK;
-  t.RT = (2 * (t.R1 + 1) + kTileM - 1) / kTileM;
-  t.CTd = (2 * (t.R2 + 1) + kTileN - 1) / kTileN;
-  t.PT = (int)((c->N + kTileM - 1) / kTileM);
-  t.KSf = (2 * (t.R2 + 1) + kStepK - 1) / kStepK;
-  t.CTf = (4 * (t.R1 + 1) + kTileN - 1) / kTileN;
-  t.bexp = 0;
-  while ((1 << t.bexp) <= t.R2) t.bexp++;
-  const int span = 2 * t.R2 + 1;
-  t.kmap.assign((size_t)(t.R1 + 1) * span, -1);
-  t.tilemap.assign((size_t)t.RT * t.CTd, -1);
-  for (int64_t k = 0; k < c->M; k++) {
-    const int n1 = ks.n_int[2 * k], n2 = ks.n_int[2 * k + 1];
-    t.kmap[(size_t)n1 * span + (n2 + t.R2)] = (int32_t)k;
-    const int ti = ((2 * n1) >> 7) * t.CTd + ((2 * std::abs(n2)) >> 5);
-    t.tilemap[ti] = 1;
-  }
+  t.on = false;
+  t.d = 0;
   t.tiles.clear();
+  t.tilemap.clear();
+  t.em.clear();
+  t.pvec.clear();
+  t.ks_ct.clear();
+  if (!c->tc_requested || !tc_eligible(*c)) return cudaSuccess;
+  const int d = c->d;
+  const int64_t M = c->M;
+  // canonical sub-vectors present in the set, sorted by |p|^2 (then n3, n2): a prefix of the list is a disk
+  int R1 = 0, Rp = 0;
+  for (int64_t k = 0; k < M; k++) {
+    int n1, n2, n3;
+    sub_vec(*c, k, n1, n2, n3);
+    R1 = std::max(R1, n1);
+    Rp = std::max(Rp, std::max(std::abs(n2), std::abs(n3)));
+  }
+  const int span = 2 * Rp + 1;
+  std::vector<int32_t> pid((size_t)span * span, -1);
+  std::vector<std::pair<int, int>> plist;
+  for (int64_t k = 0; k < M; k++) {
+    int n1, n2, n3;
+    sub_vec(*c, k, n1, n2, n3);
+    if (!canonical(n2, n3)) {
+      n2 = -n2;
+      n3 = -n3;
+    }
+    int32_t& slot = pid[(size_t)(n3 + Rp) * span + (n2 + Rp)];
+    if (slot < 0) {
+      slot = 0;
+      plist.push_back({n2, n3});
+    }
+  }
+  std::sort(plist.begin(), plist.end(), [](const std::pair<int, int>& a, const std::pair<int, int>& b) {
+    const int ra = a.first * a.first + a.second * a.second, rb = b.first * b.first + b.second * b.second;
+    if (ra != rb) return ra < rb;
+    if (a.second != b.second) return a.second < b.second;
+    return a.first < b.first;
+  });
+  const int nP = (int)plist.size();
+  int R2 = 0, R3 = 0;
+  for (int i = 0; i < nP; i++) {
+    pid[(size_t)(plist[i].second + Rp) * span + (plist[i].first + Rp)] = i;
+    R2 = std::max(R2, std::abs(plist[i].first));
+    R3 = std::max(R3, plist[i].second);
+  }
+  // limits: the prep kernel's shared memory, the force epilogue scales
+  const size_t prep_smem = kPrepSmemY + (d == 3 ? (size_t)kPrepParticles * (R2 + 1 + R3 + 1) * sizeof(qent) : 0);
+  int lg = 0;
+  while ((1ll << lg) < 2ll * nP) lg++;
+  int lf = 0;
+  while ((1ll << lf) < 4ll * std::max(1, R1) * 2ll * nP) lf++;
+  if (prep_smem > kPrepSmemMax || 16 - lg < 1 || 126 - lf < 64 || encode_tiled() == nullptr) return cudaSuccess;
+  t.d = d;
+  t.R1 = R1;
+  t.Rax[0] = R1;
+  t.Rax[1] = R2;
+  t.Rax[2] = d == 3 ? R3 : 0;
+  t.nP = nP;
+  t.gs = 16 - lg;  // G~ (|.| <= 2 nP) held as R' 2^gs below 2^126
+  t.ts = 126 - lf;  // partial sums of four n1 terms weighted by n1 <= R1, value 2^ts, below 2^126
+  t.prep_smem = prep_smem;
+  t.pvec.resize(nP);
+  for (int i = 0; i < nP; i++) t.pvec[i] = (int32_t)((uint32_t)(plist[i].first & 0xffff) | ((uint32_t)plist[i].second << 16));
+  const int W1 = R1 + 1;
+  t.KS = (c->N + kStepK - 1) / kStepK;
+  t.PT = (int)((c->N + kTileM - 1) / kTileM);
+  t.RT = (2 * nP + kTileM - 1) / kTileM;
+  t.CTd = (2 * W1 + kTileN - 1) / kTileN;
+  t.KSf = (2 * nP + kStepK - 1) / kStepK;
+  const int npt = 16 / d;  // force column tile: n1 in [npt ct, npt ct + npt), every axis of each (2 d columns per n1)
+  t.CTf = (W1 + npt - 1) / npt;
+  t.NJ = (int64_t)t.PT * (kTileM / 8);
+  t.NPg = (int64_t)t.RT * (kTileM / 8);
+  t.bexp = 0;
+  while ((1 << t.bexp) <= std::max(R2, R3)) t.bexp++;
+  // emit map: k = (n1, p) -> [p][n1][0], k = (n1, -p) -> [p][n1][1]
+  t.em.assign((size_t)nP * W1 * 2, -1);
+  t.tilemap.assign((size_t)t.RT * t.CTd, -1);
+  std::vector<int> pmax_ct(t.CTf, -1);
+  for (int64_t k = 0; k < M; k++) {
+    int n1, n2, n3;
+    sub_vec(*c, k, n1, n2, n3);
+    const bool can = canonical(n2, n3);
+    const int p = pid[(size_t)((can ? n3 : -n3) + Rp) * span + ((can ? n2 : -n2) + Rp)];
+    t.em[((size_t)p * W1 + n1) * 2 + (can ? 0 : 1)] = (int32_t)k;
+    t.tilemap[(size_t)((2 * p) >> 7) * t.CTd + ((2 * n1) >> 5)] = 1;
+    pmax_ct[n1 / npt] = std::max(pmax_ct[n1 / npt], p);
+  }
   for (int i = 0; i < t.RT * t.CTd; i++)
     if (t.tilemap[i] >= 0) {
       t.tilemap[i] = (int32_t)t.tiles.size();
       t.tiles.push_back(i);
     }
+  // force K range of each column tile: the rows (p, cos / sin) up to the last p with a set member at one of its n1
+  // (p is sorted by |p|: the range of a tile of large n1 is a small disk)
+  t.ks_ct.resize(t.CTf);
+  for (int ct = 0; ct < t.CTf; ct++) t.ks_ct[ct] = pmax_ct[ct] < 0 ? 0 : (2 * (pmax_ct[ct] + 1) + kStepK - 1) / kStepK;
   const int nt = (int)t.tiles.size();
   const int64_t max_split = std::max<int64_t>(1, t.KS / kChunkSteps);
   // one CTA per SM: as many K ranges per tile as fit in a single wave
   t.ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(max_split, c->sm_count / std::max(1, nt)));
   // each K range holds at most 1024 read-outs, so the int64 level groups (below 2^52 per read-out) cannot overflow
   t.ksplit = (int)std::max<int64_t>(t.ksplit, (t.KS + 1024 * kChunkSteps - 1) / (1024 * kChunkSteps));
+  t.ntab = kPrepLow + std::max(R1, std::max(R2, R3)) / kPrepLow + 1;
   cudaStream_t st = c->stream;
   cudaError_t e;
-  if ((e = tc_dev_alloc(&t.dA, (size_t)t.RT * t.KS * kStageA, st)) != cudaSuccess) return e;
-  if ((e = tc_dev_alloc(&t.dB, (size_t)t.CTd * t.KS * kStageB, st)) != cudaSuccess) return e;
-  if ((e = tc_dev_alloc(&t.fA, (size_t)t.PT * t.KSf * kStageA, st)) != cudaSuccess) return e;
+  if ((e = tc_dev_alloc(&t.wT, (size_t)kDigits * t.NPg * t.NJ * 128, st)) != cudaSuccess) return e;
+  if ((e = tc_dev_alloc(&t.aB, (size_t)t.CTd * t.KS * kStageB, st)) != cudaSuccess) return e;
   if ((e = tc_dev_alloc(&t.fB, (size_t)t.CTf * t.KSf * kStageB, st)) != cudaSuccess) return e;
-  if ((e = tc_dev_alloc(&t.a1, (size_t)(t.R1 + 1) * c->N * sizeof(fxc), st)) != cudaSuccess) return e;
-  t.ntab = kPrepLow + std::max(t.R1, t.R2) / kPrepLow + 1;
-  if ((e = tc_dev_alloc(&t.tab, (size_t)2 * c->N * t.ntab * sizeof(qent), st)) != cudaSuccess) return e;
+  if ((e = tc_dev_alloc(&t.a1, (size_t)W1 * c->N * sizeof(fxc), st)) != cudaSuccess) return e;
+  if ((e = tc_dev_alloc(&t.tab, (size_t)d * c->N * t.ntab * sizeof(qent), st)) != cudaSuccess) return e;
   if ((e = tc_dev_alloc(&t.acc, (size_t)nt * 3 * kTileN * kTileM * 8, st)) != cudaSuccess) return e;
-  if ((e = tc_dev_alloc(&t.facc, (size_t)2 * 3 * c->N * 8, st)) != cudaSuccess) return e;
-  if ((e = tc_dev_alloc(&t.kmap_d, t.kmap.size() * 4, st)) != cudaSuccess) return e;
-  if ((e = cudaMemcpyAsync(t.kmap_d.p, t.kmap.data(), t.kmap.size() * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+  if ((e = tc_dev_alloc(&t.facc, (size_t)d * 3 * c->N * 8, st)) != cudaSuccess) return e;
+  if ((e = tc_dev_alloc(&t.em_d, t.em.size() * 4, st)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(t.em_d.p, t.em.data(), t.em.size() * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+  if ((e = tc_dev_alloc(&t.pvec_d, t.pvec.size() * 4, st)) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(t.pvec_d.p, t.pvec.data(), t.pvec.size() * 4, cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return e;
   if ((e = tc_dev_alloc(&t.tilemap_d, t.tilemap.size() * 4, st)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(t.tilemap_d.p, t.tilemap.data(), t.tilemap.size() * 4, cudaMemcpyHostToDevice, st)) !=
       cudaSuccess)
     return e;
   if ((e = tc_dev_alloc(&t.err, 16, st)) != cudaSuccess) return e;
-  // force epilogue scales: G~ (|.| <= 2 (R2 + 1)) held as R' 2^gs below 2^126; partial sums of four n1 terms
-  // weighted by n1 <= R1 held at value 2^ts below 2^126
-  int lg = 0;
-  while ((1ll << lg) < 2ll * (t.R2 + 1)) lg++;
-  t.gs = 16 - lg;
-  int lf = 0;
-  while ((1ll << lf) < 4ll * std::max(1, t.R1) * 2ll * (t.R2 + 1)) lf++;
-  t.ts = 126 - lf;
-  if (t.gs < 1 || t.ts < 64) return cudaErrorInvalidValue;  // wavevector range beyond the scales used here
+  // tensor maps of the digit tensor [slice][row group][particle group][64 bf16]: the density box (two particle
+  // groups x sixteen row groups) and the force box (sixteen particle groups x two row groups), all 15 slices
+  {
+    const cuuint64_t gdim[4] = {64, (cuuint64_t)t.NJ, (cuuint64_t)t.NPg, (cuuint64_t)kDigits};
+    const cuuint64_t gstr[3] = {128, (cuuint64_t)t.NJ * 128, (cuuint64_t)t.NJ * (cuuint64_t)t.NPg * 128};
+    const cuuint32_t box_d[4] = {64, 2, 16, (cuuint32_t)kDigits}, box_f[4] = {64, 16, 2, (cuuint32_t)kDigits};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    CUtensorMap* maps = reinterpret_cast<CUtensorMap*>(t.tmap_h);
+    for (int m = 0; m < 2; m++) {
+      const CUresult r = encode_tiled()(&maps[m], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, t.wT.p, gdim, gstr,
+                                        m == 0 ? box_d : box_f, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    }
+    if ((e = tc_dev_alloc(&t.tmap, 2 * sizeof(CUtensorMap), st)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(t.tmap.p, t.tmap_h, 2 * sizeof(CUtensorMap), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      return e;
+    // the host copy must outlive the asynchronous upload
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  }
   t.on = true;
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
-    cudaFuncSetAttribute(k_tc_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPrepSmem);
+    cudaFuncSetAttribute(k_tc_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPrepSmemMax);
     attr = true;
   }
   return cudaGetLastError();
@@ -845,7 +1011,7 @@ cudaError_t tc_setup(Ctx* c) {
 
 void tc_free(Ctx* c) {
   TcPlan& t = c->tc;
-  for (DevBuf* b : {&t.dA, &t.dB, &t.fA, &t.fB, &t.a1, &t.tab, &t.acc, &t.facc, &t.kmap_d, &t.tilemap_d, &t.err}) {
+  for (DevBuf* b : {&t.wT, &t.aB, &t.fB, &t.a1, &t.tab, &t.acc, &t.facc, &t.em_d, &t.pvec_d, &t.tilemap_d, &t.tmap, &t.err}) {
     if (b->p) cudaFree(b->p);
     b->p = nullptr;
     b->bytes = 0;
@@ -856,8 +1022,10 @@ void tc_free(Ctx* c) {
 size_t tc_footprint(const Ctx& c) {
   const TcPlan& t = c.tc;
   if (!t.on) return 0;
-  return t.dA.bytes + t.dB.bytes + t.fA.bytes + t.fB.bytes + t.a1.bytes + t.tab.bytes + t.acc.bytes + t.facc.bytes + t.kmap_d.bytes +
-         t.tilemap_d.bytes;
+  size_t b = 0;
+  for (const DevBuf* x : {&t.wT, &t.aB, &t.fB, &t.a1, &t.tab, &t.acc, &t.facc, &t.em_d, &t.pvec_d, &t.tilemap_d, &t.tmap})
+    b += x->bytes;
+  return b;
 }
 
 void tc_fill_cfgdev(const Ctx* c, CfgDev* g) {
@@ -865,7 +1033,8 @@ void tc_fill_cfgdev(const Ctx* c, CfgDev* g) {
   g->tc = t.on ? 1 : 0;
   if (!t.on) return;
   g->tc_R1 = t.R1;
-  g->tc_R2 = t.R2;
+  g->tc_nP = t.nP;
+  for (int a = 0; a < 3; a++) g->tc_Rax[a] = t.Rax[a];
   g->tc_RT = t.RT;
   g->tc_CTd = t.CTd;
   g->tc_PT = t.PT;
@@ -874,9 +1043,10 @@ void tc_fill_cfgdev(const Ctx* c, CfgDev* g) {
   g->tc_bexp = t.bexp;
   g->tc_ksplit = t.ksplit;
   g->tc_KS = t.KS;
-  g->tc_dA = (uint8_t*)t.dA.p;
-  g->tc_dB = (uint8_t*)t.dB.p;
-  g->tc_fA = (uint8_t*)t.fA.p;
+  g->tc_NJ = t.NJ;
+  g->tc_NPg = t.NPg;
+  g->tc_wT = (uint8_t*)t.wT.p;
+  g->tc_aB = (uint8_t*)t.aB.p;
   g->tc_fB = (uint8_t*)t.fB.p;
   g->tc_a1 = t.a1.p;
   g->tc_tab = t.tab.p;
@@ -884,8 +1054,10 @@ void tc_fill_cfgdev(const Ctx* c, CfgDev* g) {
   g->tc_acc = (long long*)t.acc.p;
   g->tc_facc = (long long*)t.facc.p;
   g->tc_nblk = tc_finish_blocks(*c);
-  g->tc_kmap = (const int32_t*)t.kmap_d.p;
+  g->tc_em = (const int32_t*)t.em_d.p;
+  g->tc_pvec = (const int32_t*)t.pvec_d.p;
   g->tc_tilemap = (const int32_t*)t.tilemap_d.p;
+  g->tc_tmap = t.tmap.p;
   g->tc_err = (int*)t.err.p;
   g->tc_gs = t.gs;
   g->tc_ts = t.ts;
@@ -895,8 +1067,8 @@ void tc_fill_cfgdev(const Ctx* c, CfgDev* g) {
 // work items of one member (engine member index i)
 void tc_items(const Ctx* c, int i, std::vector<TwItem>& prep, std::vector<TcItem>& dens, std::vector<TcItem>& force) {
   const TcPlan& t = c->tc;
-  for (int axis = 0; axis < 2; axis++)
-    for (int64_t j = 0; j < c->N; j += kPrepParticles) prep.push_back({i, axis, j});  // one K-step each
+  for (int kind = 1; kind >= 0; kind--)  // the heavier w items first
+    for (int64_t j = 0; j < c->N; j += kPrepParticles) prep.push_back({i, kind, j});
   for (int ti = 0; ti < (int)t.tiles.size(); ti++) {
     const int rt = t.tiles[ti] / t.CTd, ct = t.tiles[ti] % t.CTd;
     for (int sp = 0; sp < t.ksplit; sp++) {
@@ -904,22 +1076,12 @@ void tc_items(const Ctx* c, int i, std::vector<TwItem>& prep, std::vector<TcItem
       dens.push_back({i, 0, rt, ct, (int32_t)k0, (int32_t)(k1 - k0), ti, 0});
     }
   }
-  // force items: column tile ct holds n1 in [8 ct, 8 ct + 8); its K range (m, cos / sin) stops at the largest m
-  // with (n1, +-m) in the set for one of those n1 (the coefficients beyond are zero).  Largest items first, so
-  // the round-robin assignment to the persistent CTAs balances.
-  const int span = 2 * t.R2 + 1;
-  std::vector<int> ks_of(t.CTf, 0);
-  for (int ct = 0; ct < t.CTf; ct++) {
-    int mmax = -1;
-    for (int n1 = 8 * ct; n1 < std::min(8 * ct + 8, t.R1 + 1); n1++)
-      for (int m = 0; m <= t.R2; m++)
-        if (t.kmap[(size_t)n1 * span + t.R2 + m] >= 0 || t.kmap[(size_t)n1 * span + t.R2 - m] >= 0) mmax = std::max(mmax, m);
-    ks_of[ct] = mmax < 0 ? 0 : (2 * (mmax + 1) + kStepK - 1) / kStepK;
-  }
+  // force items: particle tile x column tile, with the K range of the column tile (the coefficients beyond are
+  // zero).  Largest items first, so the round-robin assignment to the persistent CTAs balances.
   std::vector<TcItem> fi;
   for (int pt = 0; pt < t.PT; pt++)
     for (int ct = 0; ct < t.CTf; ct++)
-      if (ks_of[ct] > 0) fi.push_back({i, 1, pt, ct, 0, ks_of[ct], ct, 0});
+      if (t.ks_ct[ct] > 0) fi.push_back({i, 1, pt, ct, 0, t.ks_ct[ct], ct, 0});
   std::stable_sort(fi.begin(), fi.end(), [](const TcItem& a, const TcItem& b) { return a.nks > b.nks; });
   force.insert(force.end(), fi.begin(), fi.end());
 }
@@ -942,7 +1104,7 @@ cudaError_t tc_launch_density(const EngineView& v, cudaStream_t st, Prof* prof) 
   cudaError_t le = launch_pdl(k_tc_tables, dim3((unsigned)std::max<int64_t>(1, (v.maxND + 127) / 128), (unsigned)v.ntc_list),
                               dim3(128), 0, st, v.cfgs, v.tc_list);
   if (le == cudaSuccess)
-    le = launch_pdl(k_tc_prep, dim3((unsigned)v.ntc_prep), dim3(kPrepThreads), kPrepSmem, st, v.cfgs, v.tc_prep);
+    le = launch_pdl(k_tc_prep, dim3((unsigned)v.ntc_prep), dim3(kPrepThreads), v.tc_prep_smem, st, v.cfgs, v.tc_prep);
   if (le != cudaSuccess) return le;
   prof_end(prof, st);
   prof_begin(prof, st, kKTcDens);

@@ -42,15 +42,18 @@ __host__ __device__ __forceinline__ uint32_t slice_off(int r, int k) {
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// shared-memory matrix descriptor: start, LBO, SBO (bytes), version 1, no swizzle
-__device__ __forceinline__ uint64_t make_sdesc(uint32_t saddr) {
-  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
+// Shared-memory matrix descriptor, no swizzle, version 1.  lbo: byte distance of core matrices adjacent along K;
+// sbo: along M (or N).  A core matrix is eight 16-byte rows: for a K-major operand each row holds 8 K-consecutive
+// elements of one M row, for an MN-major operand 8 M-consecutive elements of one K row.
+__device__ __forceinline__ uint64_t make_sdesc(uint32_t saddr, uint32_t lbo = 128, uint32_t sbo = 256) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
          ((uint64_t)1 << 46);
 }
 
-// instruction descriptor, kind::f16: D f32, A and B bf16, both K-major, M x N
-__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// instruction descriptor, kind::f16: D f32, A and B bf16, B K-major, A K-major (a_mn = 0) or MN-major (1), M x N
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N, int a_mn = 0) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t* b, int count) {
@@ -90,6 +93,19 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                    smem_u32(dst)),
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
+}
+
+// make a tensor map that the host wrote into global memory visible to the tensor-map proxy of this thread
+__device__ __forceinline__ void tmap_acquire(const void* tmap) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(tmap) : "memory");
+}
+// 4-D tiled tensor copy global -> shared (coordinates in elements, innermost first), completion on the mbarrier
+__device__ __forceinline__ void tma_load_4d(void* dst, const void* tmap, int c0, int c1, int c2, int c3, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(smem_u32(dst)),
+      "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
 }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {

@@ -56,7 +56,7 @@ def test_batched_evaluation_equals_single(built):
 
 
 def test_tensor_members_equal_single(built):
-    """A batch whose d = 2 members run on the tensor cores and whose d = 1, 3 members run on the integer pipes:
+    """A batch whose d = 2, 3 members run on the tensor cores and whose d = 1 members run on the integer pipes:
     every member bit-identical to a lone context of the same implementation, in an evaluation and a quench."""
     cfgs = small_mix(6, 46, dims=(1, 2, 3)) + [synth.Config(d=2, N=2000, L=2000 ** 0.5, chi=0.45, seed=11)]
     b = ssh.Batch(fx_impl=ssh.FX_TENSOR)
@@ -64,9 +64,10 @@ def test_tensor_members_equal_single(built):
         b.add(c.d, c.N, c.L, synth.positions(c.seed, c.N, c.d), chi=c.chi)
     b.eval(ssh.FX)
     for i, c in enumerate(cfgs):
-        assert b.member(i).fx_impl == (ssh.FX_TENSOR if c.d == 2 else ssh.FX_INTEGER)
+        impl = ssh.FX_TENSOR if c.d in (2, 3) else ssh.FX_INTEGER
+        assert b.member(i).fx_impl == impl
         rb = b.member(i).results()
-        with ssh.Context(c.d, c.N, c.L, chi=c.chi, fx_impl=ssh.FX_TENSOR if c.d == 2 else ssh.FX_INTEGER) as ctx:
+        with ssh.Context(c.d, c.N, c.L, chi=c.chi, fx_impl=impl) as ctx:
             ctx.set_positions_frac(synth.positions(c.seed, c.N, c.d))
             ra = ctx.energy_grad(ssh.FX)
         assert np.array_equal(ra["phi"], rb["phi"]) and np.array_equal(ra["F_hi"], rb["F_hi"]), i

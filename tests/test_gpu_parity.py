@@ -79,12 +79,15 @@ CASES = [
     # draws are multiples of 2^-53, which makes every phase reduction exact and hides rounding in it
     ("fullbits_d2", 2, 700, 700 ** 0.5, 0.45, 0.0, -13),
     ("fullbits_d3", 3, 400, 400 ** (1 / 3), 0.40, 0.0, -14),
+    # |n| <= 17.5: n1 in [0, 17] (two column tiles of the tensor-core density), about 480 canonical (n2, n3)
+    # (eight row tiles), 1500 particles (a ragged last particle tile)
+    ("d3_wide_kmode", 3, 1500, 1500 ** (1 / 3), 0.0, 2 * math.pi * 17.5 / 1500 ** (1 / 3), 15),
 ]
 
 
 def impls(d):
-    """(fx_impl, precisions to check) per context: d = 2 runs the fixed point through both implementations."""
-    if d == 2:
+    """(fx_impl, precisions to check) per context: d = 2, 3 run the fixed point through both implementations."""
+    if d in (2, 3):
         return [(ssh.FX_INTEGER, PRECS), (ssh.FX_TENSOR, [ssh.FX])]
     return [(ssh.FX_AUTO, PRECS)]
 
@@ -130,6 +133,43 @@ def test_parity_medium_d2_full(built, oracle_mod):
         for prec in precs:
             check_parity(ctx, s, None, cfg.L, prec, ref, n, label=f"medium/{ssh.PREC_NAMES[prec]}/impl{impl}")
         ctx.close()
+
+
+def test_parity_large_d3_sampled(built, oracle_mod):
+    """The d=3, N=32768, chi=0.40 workload (M = 39320) at full size, in the launch configuration of a plain
+    evaluation: n~ on 256 sampled wavevectors against the oracle (each one a full sum over the particles);
+    F of the tensor-core path against the integer-pipe path (each checked against the oracle on the smaller
+    cases) within the normwise bound, and sum_j F_j = 0."""
+    cfg = synth.LARGE_D3
+    s = synth.positions(cfg.seed, cfg.N, cfg.d)
+    res = {}
+    for impl in (ssh.FX_TENSOR, ssh.FX_INTEGER):
+        ctx = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi, fx_impl=impl)
+        assert ctx.fx_impl == impl
+        n = ctx.kset()
+        ctx.set_positions_frac(s)
+        r = ctx.energy_grad(ssh.FX)
+        C, S = ctx.ntilde()
+        res[impl] = (r, C, S)
+        ctx.close()
+    rng = np.random.default_rng(20240)
+    pick = np.sort(rng.choice(len(n), 256, replace=False))
+    ref = oracle_mod.phi_grad(s, None, n[pick], cfg.L, want_force=False, want_cs=True, nthreads=NTHREADS)
+    tol, N = 1e-28, cfg.N
+    for impl, (r, C, S) in res.items():
+        assert np.all(np.abs(ddiff(C[pick], ref["C"])) <= tol * N), (impl, np.abs(ddiff(C[pick], ref["C"])).max())
+        assert np.all(np.abs(ddiff(S[pick], ref["S"])) <= tol * N), (impl, np.abs(ddiff(S[pick], ref["S"])).max())
+    (rt, Ct, St), (ri, Ci, Si) = res[ssh.FX_TENSOR], res[ssh.FX_INTEGER]
+    assert np.all(np.abs(ddiff(Ct, Ci)) <= 2 * tol * N) and np.all(np.abs(ddiff(St, Si)) <= 2 * tol * N)
+    Cabs = np.abs(ddv(Ci)) + np.abs(ddv(Si)) + math.sqrt(N)
+    scale = tol * 4 * math.pi / cfg.L * (np.abs(n).astype(np.float64) * Cabs[:, None]).sum(0)
+    Ft = np.stack([rt["F_hi"], rt["F_lo"]], -1)
+    Fi = np.stack([ri["F_hi"], ri["F_lo"]], -1)
+    assert np.all(np.abs(ddiff(Ft, Fi)) <= 2 * scale[None, :]), (np.abs(ddiff(Ft, Fi)) / scale[None, :]).max()
+    # sum_j F_j = 0 (Newton's third law of the pair form): N terms of the bound each
+    for F in (Ft, Fi):
+        tot = np.array([math.fsum(np.concatenate([F[:, a, 0], F[:, a, 1]])) for a in range(cfg.d)])  # exact sums
+        assert np.all(np.abs(tot) <= N * scale * 4), (tot, scale)
 
 
 def test_lattice_closed_form_on_gpu(built):
@@ -202,9 +242,11 @@ def test_fx_impl_selection(built):
     with ssh.Context(2, 64, 8.0, chi=0.3, fx_impl=ssh.FX_INTEGER) as c:
         assert c.fx_impl == ssh.FX_INTEGER
     with ssh.Context(3, 64, 4.0, chi=0.3) as c:
-        assert c.fx_impl == ssh.FX_INTEGER       # the tensor-core path covers d = 2
+        assert c.fx_impl == ssh.FX_TENSOR        # the tensor-core path covers d = 2 and 3
+    with ssh.Context(1, 64, 64.0, chi=0.3) as c:
+        assert c.fx_impl == ssh.FX_INTEGER
     with pytest.raises(ssh.SshError) as e:
-        ssh.Context(3, 64, 4.0, chi=0.3, fx_impl=ssh.FX_TENSOR)
+        ssh.Context(4, 64, 64 ** 0.25, chi=0.3, fx_impl=ssh.FX_TENSOR)
     assert e.value.status == 1
     with pytest.raises(ssh.SshError):
         ssh.Context(2, 64, 8.0, chi=0.3, fx_impl=7)
