@@ -39,10 +39,16 @@ FX_IMAD_PER_PAIR = {"ntilde": 48, "force": 80}
 # written in dd.cuh): density = complex dd multiply (4 mul + 2 add = 72) + complex accumulate (2 add = 40);
 # force = complex multiply (72) + w = C sin - S cos (2 mul + 1 add = 36) + A += w, B += A (40).
 DD_FP64_PER_PAIR = {"ntilde": 112, "force": 148}
-# Tensor-core fixed point (d = 2): every real product of two 2^-104 fixed-point values is 120 bf16 digit-pair
-# products.  The density needs 2 real products per (k, particle) pair (4 real products serve k = (n1, +m) and
-# (n1, -m)), the force 4 (G and the n2-weighted G', cos and sin terms, again for both signs of m).
-TC_FLOP_PER_PAIR = {"tc_dens": 2 * 2 * 120, "tc_force": 2 * 4 * 120}
+# Tensor-core fixed point: every real product of two 2^-104 fixed-point values is 120 bf16 digit-pair products
+# (2 FLOP each).  The density needs 2 real products per (k, particle) pair (4 real products serve k = (n1, p)
+# and (n1, -p)), the force 2 d (G and the d - 1 weighted G^a, Re and Im, cos and sin terms, again for both
+# signs of p).
+
+
+def tc_flop_per_pair(d: int) -> dict:
+    return {"tc_dens": 2 * 2 * 120, "tc_force": 2 * 2 * d * 120}
+
+
 F64_FP64_PER_PAIR = {"ntilde": 6, "force": 8}
 # Peaks derived from unit counts and the maximum SM clock (148 SMs, 2032 MHz): 64 IMAD lanes per SM per
 # clock; 2 FP64 FMA lanes per SM per clock (1.2 TFLOP/s).
@@ -87,7 +93,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--prec", default="fx", choices=["fx", "dd", "fp64"])
     ap.add_argument("--fx-impl", default="auto", choices=["auto", "integer", "tensor"],
-                    help="fixed-point implementation: integer pipes or exact-digit tensor-core GEMMs (d = 2)")
+                    help="fixed-point implementation: integer pipes or exact-digit tensor-core GEMMs (d = 2, 3)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
@@ -95,6 +101,8 @@ def parse():
     ap.add_argument("--minimize-dd", action="store_true", help="also time FP64->dd and all-dd quenches")
     ap.add_argument("--minimize-seconds", type=float, default=150.0)
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the d=3, N=32768 block")
+    ap.add_argument("--no-large-staged", action="store_true", help="skip its staged FP64 -> fixed point quench")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=45.0)
     return ap.parse_args()
@@ -380,6 +388,95 @@ def run_reference(args):
     return 0
 
 
+def large_d3_block(ssh, synth, dev, stream, flush, steps=5, warmup=3, max_seconds=150.0, staged=True):
+    """The d=3, N=32768, chi=0.40 workload (M = 39320): one device FIRE step in the library's default fixed
+    point (per-kernel split and tensor roofline), one evaluation in every arithmetic, and full quenches to
+    S_max <= 1e-36 with the default ladder and with the paper's staged FP64 -> fixed point ladder.  An all-dd
+    quench (several hundred dd evaluations of about a second each) is not run; its projection is the measured
+    dd evaluation time times the step count of the default quench, and is labelled as such."""
+    import torch
+    cfg = synth.LARGE_D3
+    ctx = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi, device=dev)
+    ctx.set_stream(stream.cuda_stream)
+    s = synth.positions(cfg.seed, cfg.N, cfg.d)
+    ctx.set_positions_frac(s)
+    pairs = ctx.M * ctx.N
+    out = {"workload": f"d=3 N={cfg.N} L={cfg.L} chi={cfg.chi} M={ctx.M}, uniform random (SplitMix64 seed "
+                       f"{cfg.seed}); L2 flushed between timed steps",
+           "fx_impl": "tensor" if ctx.fx_impl == ssh.FX_TENSOR else "integer"}
+    fp = ctx.min_defaults()
+    fp.n_stages = 1
+    fp.stage_prec[0] = ssh.FX
+    fp.smax_target = 1e-300
+    fp.max_steps = 1 << 40
+    fp.stall_window[0] = 1 << 40
+    ctx.fire_begin(fp)
+    for _ in range(warmup):
+        ctx.fire_steps(ssh.FX, 1)
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        ctx.fire_steps(ssh.FX, 1)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize(dev)
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    ctx.prof_enable(True)
+    for _ in range(steps):
+        flush.zero_()
+        ctx.fire_steps(ssh.FX, 1)
+    prof = ctx.prof_read()
+    ctx.prof_enable(False)
+    out["step"] = {"ms": ms, "pairs_per_s": pairs / (ms * 1e-3),
+                   "per_kernel_ms": {k: v[0] / v[1] for k, v in prof.items()}}
+    if ctx.fx_impl == ssh.FX_TENSOR:
+        fl = tc_flop_per_pair(cfg.d)
+        out["step"]["tensor_frac_of_measured_bf16_peak"] = {
+            k: fl[k] * pairs / (prof[k][0] / prof[k][1] * 1e-3) / BF16_PEAK for k in fl if k in prof}
+    # one evaluation (Phi, S_max, F) in every arithmetic
+    evals = {}
+    for name, prec, reps in (("fx", ssh.FX, 3), ("fp64", ssh.FP64, 3), ("dd", ssh.DD, 1)):
+        ctx.eval(prec)
+        ctx.sync()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            ctx.eval(prec)
+        ctx.sync()
+        evals[name] = (time.perf_counter() - t0) / reps
+    with ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi, device=dev, fx_impl=ssh.FX_INTEGER) as c2:
+        c2.set_stream(stream.cuda_stream)
+        c2.set_positions_frac(s)
+        c2.eval(ssh.FX)
+        c2.sync()
+        t0 = time.perf_counter()
+        for _ in range(2):
+            c2.eval(ssh.FX)
+        c2.sync()
+        evals["fx_integer"] = (time.perf_counter() - t0) / 2
+    out["eval_ms"] = {k: v * 1e3 for k, v in evals.items()}
+    out["eval_pairs_per_s"] = {k: pairs / v for k, v in evals.items()}
+    ctx.close()
+    runs = [("default", None)] + ([("fp64_then_fx", [ssh.FP64, ssh.FX])] if staged else [])
+    q = {}
+    for name, stages in runs:
+        c = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi, device=dev)
+        c.set_stream(stream.cuda_stream)
+        c.set_positions_frac(s)
+        r = c.minimize(stages=stages, max_steps=100000, max_seconds=max_seconds)
+        ns = r["stages_used"]
+        q[name] = {"converged": r["status"] == 0, "status": r["status"], "wall_s": r["wall_s"], "steps": r["steps"],
+                   "stage_steps": r["stage_steps"][:ns], "stage_wall_s": r["stage_wall_s"][:ns], "smax": r["smax"][0],
+                   "configs_per_hour": 3600.0 / r["wall_s"] if r["status"] == 0 else 0.0}
+        c.close()
+    if q["default"]["converged"]:
+        q["all_dd_projected"] = {"wall_s": evals["dd"] * q["default"]["steps"],
+                                 "basis": "projection, not a run: measured dd evaluation time x step count of "
+                                          "the default quench"}
+    out["minimize"] = q
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -469,7 +566,7 @@ def main():
         dom_name = max(("tc_dens", "tc_force"), key=lambda k: prof.get(k, (0.0, 1))[0])
         dom_ms, dom_n = prof[dom_name]
         per_launch_s = dom_ms / 1e3 / dom_n
-        per_pair, peak, unit, bound, what = TC_FLOP_PER_PAIR, BF16_PEAK, "FLOP/s", "tensor", "bf16"
+        per_pair, peak, unit, bound, what = tc_flop_per_pair(w["d"]), BF16_PEAK, "FLOP/s", "tensor", "bf16"
     elif prec == ssh.FX:
         per_pair, peak, unit, bound, what = FX_IMAD_PER_PAIR, IMAD_PEAK, "IMAD/s", "alu", "IMAD"
     elif prec == ssh.DD:
@@ -520,7 +617,7 @@ def main():
                 ctx.eval(p)
             ctx.sync()
             variants[name] = pairs / ((time.perf_counter() - t0) / reps)
-        if prec == ssh.FX and w["d"] == 2:
+        if prec == ssh.FX and w["d"] in (2, 3):
             # the other fixed-point implementation on the same positions
             other = ssh.FX_INTEGER if tensor else ssh.FX_TENSOR
             with ssh.Context(w["d"], w["N"], w["L"], chi=w["chi"], device=dev, fx_impl=other) as c2:
@@ -551,15 +648,19 @@ def main():
             "roofline": roof, "gpu_launches": launches, "wall_s": t_wall,
             "e2e": {"value": pairs * world / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": clk.summary(), "variants_pairs_per_s": variants}
-    if rank == 0 and not args.no_minimize:
+    # the further blocks run at N = 1 only (a multi-GPU run holds every GPU while rank 0 works)
+    if rank == 0 and world == 1 and not args.no_minimize:
         line["minimize"] = minimize_block(ssh, synth, w, dev, stream, with_dd=args.minimize_dd,
                                           max_seconds=args.minimize_seconds)
         conv = line["minimize"].get("default", {})
         if conv.get("converged"):
             line["configs_per_hour"] = 3600.0 / conv["wall_s"]
-    if rank == 0 and not args.no_batched:
+    if rank == 0 and world == 1 and not args.no_batched:
         line["batched"] = batched_block(ssh, synth, dev)
-    if rank == 0 and not args.no_serve:
+    if rank == 0 and world == 1 and not args.no_large:
+        line["large_d3"] = large_d3_block(ssh, synth, dev, stream, flush, max_seconds=args.minimize_seconds,
+                                          staged=not args.no_large_staged)
+    if rank == 0 and world == 1 and not args.no_serve:
         line["serving"] = serving_block(ssh, synth, dev, window_s=args.serve_seconds)
         line["p50_s"] = line["serving"]["p50_s"]
         line["p99_s"] = line["serving"]["p99_s"]

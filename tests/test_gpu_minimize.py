@@ -135,3 +135,37 @@ def test_stepper_counts_steps_and_stops_at_convergence(built):
     n_conv = st["steps"]
     ctx.fire_steps(ssh.FX, 16)
     assert ctx.fire_state()["steps"] == n_conv
+
+
+def test_large_d3_staged_error_per_stage(built, oracle_mod):
+    """The d=3, N=32768, chi=0.40 workload and the paper's staged quench: an FP64 descent to S_max <= 1e-24,
+    then the fixed-point polish to 1e-36, run as two single-stage minimisations (FIRE restarts at every stage,
+    so this is the two-stage ladder).  At the end of each stage that stage's arithmetic is compared with the
+    oracle on 128 sampled wavevectors (each a full sum over the particles): within the normwise bound of its
+    arithmetic, and the sampled S(k) of the final state at or below the target."""
+    cfg = synth.LARGE_D3
+    ctx = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi)
+    n = ctx.kset()
+    ctx.set_positions_frac(synth.positions(cfg.seed, cfg.N, cfg.d))
+    pick = np.sort(np.random.default_rng(5).choice(len(n), 128, replace=False))
+
+    def stage_error(prec):
+        ctx.energy_grad(prec)
+        C, S = ctx.ntilde()
+        hi, lo = ctx.positions_frac()
+        ref = oracle_mod.phi_grad(hi, lo, n[pick], cfg.L, want_force=False, want_cs=True, nthreads=NTHREADS)
+        dC = np.abs((C[pick, 0] - ref["C"][:, 0]) + (C[pick, 1] - ref["C"][:, 1]))
+        dS = np.abs((S[pick, 0] - ref["S"][:, 0]) + (S[pick, 1] - ref["S"][:, 1]))
+        sk = ((ref["C"][:, 0] + ref["C"][:, 1]) ** 2 + (ref["S"][:, 0] + ref["S"][:, 1]) ** 2) / cfg.N
+        return max(dC.max(), dS.max()) / cfg.N, sk.max()
+
+    r1 = ctx.minimize(stages=[ssh.FP64], smax_target=1e-24, max_steps=20000, max_seconds=300)
+    assert r1["status"] in (0, 5), r1          # at the stage floor, or stalled near it
+    e1, _ = stage_error(ssh.FP64)
+    assert e1 <= 1e-13, e1
+    r2 = ctx.minimize(stages=[ssh.FX], max_steps=40000, max_seconds=300)
+    assert r2["status"] == 0, r2
+    e2, sk2 = stage_error(ssh.FX)
+    assert e2 <= 1e-28, e2
+    assert sk2 <= 1.01e-36, sk2
+    ctx.close()
