@@ -28,7 +28,7 @@
 //
 // Kernels (one launch each per evaluation, over every tensor-core member of the engine):
 //   k_tc_tables       per (particle, axis): e^{2 pi i k s} (k < 8) and e^{2 pi i 8 b s} as first-quadrant phasors
-//   k_tc_prep         per 16 particles: a_j(n1) as digit slices of the density B operand and as Q2.126 for the
+//   k_tc_prep         per particle block: a_j(n1) as digit slices of the density B operand and as Q2.126 for the
 //                     force epilogue; w_j(p) as the digit tensor
 //   k_tc_gemm         warp-specialised persistent tcgen05 GEMM: one producer thread (tensor-map and bulk async
 //                     copies, three stages), one MMA thread (22 MMAs per K-step), sixteen epilogue warps (level
@@ -185,11 +185,9 @@ __device__ __forceinline__ q160 load_q160(const void* p) {
 namespace {
 
 constexpr int kPrepThreads = 256;
-constexpr int kPrepParticles = 16;  // particles per CTA (one K-step of the density GEMM)
-constexpr int kPrepM = 80;          // complex entries per pass (shared-memory staging of their fixed-point values)
+constexpr int kPrepStaged = 16;     // particles per d = 3 w item (their powers b(n2), c(n3) staged in shared memory)
+constexpr int kPrepTable = 128;     // particles per table item (a(n1); w of d = 2): products of two table entries
 constexpr int kPrepLow = 8;         // e^{2 pi i m s} = A[m / 8] T[m % 8]
-constexpr int kPrepPitch = 2 * kPrepM + 1;  // staging row pitch (16-byte entries): odd, so rows spread over the banks
-constexpr size_t kPrepSmemY = (size_t)kPrepPitch * kPrepParticles * 16;
 constexpr size_t kPrepSmemMax = 200 * 1024;
 
 // conj of a first-quadrant phasor: conj(i^q (c + i s)) = i^{-q} (c - i s) = i^{3 - q} (s + i c)
@@ -203,23 +201,16 @@ __device__ __forceinline__ qent qconj(const qent& z) {
 }
 
 // Eight biased values Y = X + B (X = round(x 2^104), B the balanced-digit offset) -> their 15 digits as one
-// 16-byte row (8 bf16) per digit slice, slice s holding digit 14 - s.  Digit i < 14 is bits 7i..7i+6 of Y
-// minus 64 (one funnel shift from two 32-bit words); the top digit is the signed bits 98..127.
+// 16-byte row (8 bf16) per digit slice, slice s holding digit 14 - s.  Digit i < 14 is d = u - 64 with u the
+// bits 7i..7i+6 of Y; the bf16 of 192 + d = 128 + u is 0x4300 | u (exponent 2^7, mantissa u), so one packed
+// bf16 subtraction of 192 gives two digits exactly.  The top digit, the signed bits 98..127 (it may be 64), is
+// converted through fp32.
 __device__ __forceinline__ void put_digit_rows(uint8_t* base, size_t slice_stride, const uint4 (&Y)[8]) {
-#pragma unroll
-  for (int s = 0; s < kDigits; s++) {
-    const int i = kDigits - 1 - s;
+  {
     uint32_t f[8];
 #pragma unroll
     for (int v = 0; v < 8; v++) {
-      const uint32_t w[4] = {Y[v].x, Y[v].y, Y[v].z, Y[v].w};
-      int d;
-      if (i == kDigits - 1) {
-        d = (int32_t)w[3] >> 2;
-      } else {
-        const int o = 7 * i;
-        d = (int)(__funnelshift_r(w[o >> 5], w[(o >> 5) + 1 < 4 ? (o >> 5) + 1 : 3], o & 31) & 127u) - 64;
-      }
+      const int d = (int32_t)Y[v].w >> 2;
       // small integer -> fp32 (exact) whose upper half is the bf16 of the same value
       f[v] = __float_as_uint(__int_as_float(kMagicBits + d) - kMagic);
     }
@@ -228,7 +219,25 @@ __device__ __forceinline__ void put_digit_rows(uint8_t* base, size_t slice_strid
     row.y = __byte_perm(f[2], f[3], 0x7632);
     row.z = __byte_perm(f[4], f[5], 0x7632);
     row.w = __byte_perm(f[6], f[7], 0x7632);
-    *reinterpret_cast<uint4*>(base + (size_t)s * slice_stride) = row;
+    *reinterpret_cast<uint4*>(base) = row;
+  }
+  const __nv_bfloat162 b192 = __halves2bfloat162(__ushort_as_bfloat16((unsigned short)0x4340),
+                                                 __ushort_as_bfloat16((unsigned short)0x4340));
+#pragma unroll
+  for (int s = 1; s < kDigits; s++) {
+    const int o = 7 * (kDigits - 1 - s);
+    const int lo = o >> 5, hi = lo + 1 < 4 ? lo + 1 : 3;
+    uint32_t wv[4];
+#pragma unroll
+    for (int pr = 0; pr < 4; pr++) {
+      const uint32_t a0[4] = {Y[2 * pr].x, Y[2 * pr].y, Y[2 * pr].z, Y[2 * pr].w};
+      const uint32_t a1[4] = {Y[2 * pr + 1].x, Y[2 * pr + 1].y, Y[2 * pr + 1].z, Y[2 * pr + 1].w};
+      const uint32_t u0 = __funnelshift_r(a0[lo], a0[hi], o & 31), u1 = __funnelshift_r(a1[lo], a1[hi], o & 31);
+      const uint32_t t = (__byte_perm(u0, u1, 0x5410) & 0x007F007Fu) | 0x43004300u;
+      const __nv_bfloat162 r = __hsub2(*reinterpret_cast<const __nv_bfloat162*>(&t), b192);
+      wv[pr] = *reinterpret_cast<const uint32_t*>(&r);
+    }
+    *reinterpret_cast<uint4*>(base + (size_t)s * slice_stride) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
   }
 }
 
@@ -301,94 +310,111 @@ __global__ void __launch_bounds__(128) k_tc_tables(const CfgDev* __restrict__ cf
   }
 }
 
-// CTA per (configuration, kind, 16 particles); items TwItem {cfg, kind, first particle}.
-// Kind 0: a_j(n1), n1 in [0, R1] -> density B digit slices (rows (n1, cos / sin) of K-major 32 x 16 tiles) and
-// the Q2.126 table of the force epilogue.  Kind 1: w_j(p) for the nP canonical p -> the digit tensor.  Per pass
-// over at most 80 entries: phase 1 forms every entry as one product (all threads, independent) into shared
-// memory; phase 2 writes the digit slices as whole 16-byte core-matrix rows (one row (entry, cos / sin), eight
-// particles), which consecutive threads fill contiguously.  For d = 3 the CTA's axis-2 and axis-3 powers b_j(n2),
-// c_j(n3) (n2, n3 >= 0) are staged in shared memory first (phase 0); b_j(-n2) = conj b_j(n2).
+// CTA per (configuration, kind, particle block); items TwItem {cfg, kind | groups << 8, first particle}, a block
+// of 8 * groups particles.  Kind 0: a_j(n1), n1 in [0, R1] -> density B digit slices (rows (n1, cos / sin) of
+// K-major 32 x 16 tiles) and the Q2.126 table of the force epilogue.  Kind 1: w_j(p) for the nP canonical p ->
+// the digit tensor.  A lane pair takes one entry and eight consecutive particles: each lane forms four of the
+// products, the pair swaps halves, and lane 0 writes the entry's cos row, lane 1 its sin row, as 16-byte
+// core-matrix rows, so that a warp's store covers whole 128-byte core matrices.  Table items (kind 0, and kind
+// 1 for d = 2) multiply two entries of each particle's tables; d = 3 w items cover 16 particles whose axis-2
+// and axis-3 powers b_j(n2), c_j(n3) (n2, n3 >= 0) are formed first into shared memory, and
+// w = b_j(|n2|) (conjugated for n2 < 0) c_j(n3).
 __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restrict__ cfgs,
                                                           const TwItem* __restrict__ items) {
   grid_dep_wait();
   extern __shared__ __align__(16) uint8_t psm[];
-  uint4* Ys = reinterpret_cast<uint4*>(psm);  // [j][2 (entry - m0) + p], pitch kPrepPitch
-  qent* Pw = reinterpret_cast<qent*>(psm + kPrepSmemY);
   const TwItem it = items[blockIdx.x];
   const CfgDev& c = cfgs[it.cfg];
   if (stopped(c)) return;
-  const int kind = it.pad;
+  const int kind = it.pad & 0xff, ng = it.pad >> 8;  // particle groups of 8
+  const bool staged = kind == 1 && c.d == 3;
   const int64_t N = c.N;
   const int64_t j0 = it.start;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, h = lane & 1;
   const __int128 bias = digit_bias();
   const uint4 yzero = make_uint4((uint32_t)bias, (uint32_t)(bias >> 32), (uint32_t)(bias >> 64), (uint32_t)(bias >> 96));
   const qent* tab = reinterpret_cast<const qent*>(c.tc_tab);
-  const bool three = c.d == 3;
-  const int W2 = c.tc_Rax[1] + 1, W23 = W2 + (three ? c.tc_Rax[2] + 1 : 0);
-  if (kind == 1 && three) {
-    for (int task = tid; task < kPrepParticles * W23; task += kPrepThreads) {
-      const int jl = task % kPrepParticles, e = task / kPrepParticles;
-      const int64_t j = min(j0 + jl, N - 1);  // rows of particles past N are never read
-      const int axis = e < W2 ? 1 : 2;
-      const int m = e < W2 ? e : e - W2;
-      const qent* tj = tab + ((int64_t)axis * N + j) * c.tc_ntab;
-      Pw[jl * W23 + e] = qmul(tj[kPrepLow + (m >> 3)], tj[m & 7]);
+  const int W2 = c.tc_Rax[1] + 1, W23 = W2 + (c.d == 3 ? c.tc_Rax[2] + 1 : 0);
+  const int count = kind == 0 ? c.tc_R1 + 1 : c.tc_nP;
+  int32_t* pvs = reinterpret_cast<int32_t*>(psm);  // kind 1: the packed (n2, n3) of every entry
+  qent* Pw = reinterpret_cast<qent*>(psm + (((size_t)c.tc_nP * 4 + 15) & ~(size_t)15));  // [particle][n2, then n3]
+  if (kind == 1) {
+    for (int e = tid; e < count; e += kPrepThreads) pvs[e] = c.tc_pvec[e];
+    if (staged) {
+      for (int task = tid; task < kPrepStaged * W23; task += kPrepThreads) {
+        const int jl = task % kPrepStaged, e = task / kPrepStaged;
+        const int64_t j = min(j0 + jl, N - 1);  // entries of particles past N are never read
+        const int axis = e < W2 ? 1 : 2;
+        const int m = e < W2 ? e : e - W2;
+        const qent* tj = tab + ((int64_t)axis * N + j) * c.tc_ntab;
+        Pw[jl * W23 + e] = qmul(tj[kPrepLow + (m >> 3)], tj[m & 7]);
+      }
     }
     __syncthreads();
   }
-  const int count = kind == 0 ? c.tc_R1 + 1 : c.tc_nP;
+  const int axis = kind == 0 ? 0 : 1;
   const size_t wstride = (size_t)c.tc_NPg * (size_t)c.tc_NJ * 128;  // bytes between digit slices of the tensor
-  for (int m0 = 0; m0 < count; m0 += kPrepM) {
-    const int mcount = min(kPrepM, count - m0);
-    // phase 1: every (particle, entry) of the pass, one product each
-    for (int task = tid; task < mcount * kPrepParticles; task += kPrepThreads) {
-      const int jl = task % kPrepParticles, ml = task / kPrepParticles;
-      const int64_t j = j0 + jl;
-      const int e = m0 + ml;
-      uint4 yr = yzero, yi = yzero;
-      if (j < N) {
+  const int total = count * ng;                                     // (entry, group) pairs of lanes
+  for (int q0 = (tid >> 5) * 16; q0 < total; q0 += kPrepThreads / 2) {  // warp-uniform: 16 pairs per warp
+    const int q = q0 + (lane >> 1);
+    const bool valid = q < total;
+    const int e = valid ? q % count : 0, g = valid ? q / count : 0;
+    const int64_t jg = j0 + 8 * g;
+    const bool live = valid && jg < N;  // particle groups past the last particle stay zero
+    int m = e, n2 = 0, n3 = 0;
+    if (kind == 1) {
+      const int32_t pv = pvs[e];
+      n2 = (int)(int16_t)(pv & 0xffff);
+      n3 = pv >> 16;
+      m = n2;  // d = 2: n2 = m >= 0
+    }
+    uint4 Yr[4], Yi[4];
+#pragma unroll
+    for (int v = 0; v < 4; v++) {
+      const int jl = 8 * g + 4 * h + v;
+      const int64_t j = jg + 4 * h + v;
+      Yr[v] = yzero;
+      Yi[v] = yzero;
+      if (live && j < N) {
+        qent z;
+        if (staged) {
+          const qent* pj = Pw + jl * W23;
+          const qent b = pj[n2 < 0 ? -n2 : n2];
+          z = qmul(n2 < 0 ? qconj(b) : b, pj[W2 + n3]);
+        } else {
+          const qent* tj = tab + ((int64_t)axis * N + j) * c.tc_ntab;
+          z = qmul(tj[kPrepLow + (m >> 3)], tj[m & 7]);
+        }
         if (kind == 0) {
-          const qent* tj = tab + j * c.tc_ntab;
-          const qent z = qmul(tj[kPrepLow + (e >> 3)], tj[e & 7]);
           fxc zq;
-          qent_out(z, yr, yi, &zq);
+          qent_out(z, Yr[v], Yi[v], &zq);
           reinterpret_cast<fxc*>(c.tc_a1)[(int64_t)e * N + j] = zq;
         } else {
-          const int32_t pv = c.tc_pvec[e];
-          const int n2 = (int)(int16_t)(pv & 0xffff), n3 = pv >> 16;
-          qent z;
-          if (three) {
-            const qent b = Pw[jl * W23 + (n2 < 0 ? -n2 : n2)];
-            z = qmul(n2 < 0 ? qconj(b) : b, Pw[jl * W23 + W2 + n3]);
-          } else {
-            const qent* tj = tab + (N + j) * c.tc_ntab;  // n2 >= 0 in d = 2
-            z = qmul(tj[kPrepLow + (n2 >> 3)], tj[n2 & 7]);
-          }
-          qent_out(z, yr, yi, nullptr);
+          qent_out(z, Yr[v], Yi[v], nullptr);
         }
       }
-      Ys[jl * kPrepPitch + ml * 2 + 0] = yr;
-      Ys[jl * kPrepPitch + ml * 2 + 1] = yi;
     }
-    __syncthreads();
-    // phase 2: rows (entry, cos / sin) x 8 particles
-    const int nrow = 2 * mcount;
-    for (int task = tid; task < nrow * (kPrepParticles / 8); task += kPrepThreads) {
-      const int rl = task % nrow, g8 = task / nrow;
-      const int r = 2 * m0 + rl;
-      const int64_t jg = j0 + 8 * g8;
-      if (jg >= N) continue;  // particle groups past the last particle stay zero
-      uint4 Y[8];
+    // lane 0 of the pair keeps the cos values and receives those of particles 4..7; lane 1 the sin values of
+    // particles 0..3
+    uint4 Y[8];
 #pragma unroll
-      for (int v = 0; v < 8; v++) Y[v] = Ys[(8 * g8 + v) * kPrepPitch + rl];
-      if (kind == 0)
-        put_digit_rows(c.tc_aB + ((int64_t)(r >> 5) * c.tc_KS + (jg >> 4)) * kStageB + slice_off(r & 31, (int)(jg & 15)),
-                       kSliceB, Y);
-      else
-        put_digit_rows(c.tc_wT + ((size_t)(r >> 3) * (size_t)c.tc_NJ + (size_t)(jg >> 3)) * 128 + (r & 7) * 16, wstride, Y);
+    for (int v = 0; v < 4; v++) {
+      const uint4 send = h == 0 ? Yi[v] : Yr[v];
+      uint4 got;
+      got.x = __shfl_xor_sync(0xffffffffu, send.x, 1);
+      got.y = __shfl_xor_sync(0xffffffffu, send.y, 1);
+      got.z = __shfl_xor_sync(0xffffffffu, send.z, 1);
+      got.w = __shfl_xor_sync(0xffffffffu, send.w, 1);
+      Y[v] = h == 0 ? Yr[v] : got;
+      Y[4 + v] = h == 0 ? got : Yi[v];
     }
-    __syncthreads();
+    if (live) {
+      const int r = 2 * e + h;  // row (entry, cos / sin)
+      uint8_t* base = kind == 0
+          ? c.tc_aB + ((int64_t)(r >> 5) * c.tc_KS + (jg >> 4)) * kStageB + slice_off(r & 31, (int)(jg & 15))
+          : c.tc_wT + ((size_t)(r >> 3) * (size_t)c.tc_NJ + (size_t)(jg >> 3)) * 128 + (r & 7) * 16;
+      put_digit_rows(base, kind == 0 ? (size_t)kSliceB : wstride, Y);
+    }
   }
 }
 
@@ -902,7 +928,8 @@ cudaError_t tc_setup(Ctx* c) {
     R3 = std::max(R3, plist[i].second);
   }
   // limits: the prep kernel's shared memory, the force epilogue scales
-  const size_t prep_smem = kPrepSmemY + (d == 3 ? (size_t)kPrepParticles * (R2 + 1 + R3 + 1) * sizeof(qent) : 0);
+  const size_t prep_smem =
+      (((size_t)nP * 4 + 15) & ~(size_t)15) + (d == 3 ? (size_t)kPrepStaged * (R2 + 1 + R3 + 1) * sizeof(qent) : 0);
   int lg = 0;
   while ((1ll << lg) < 2ll * nP) lg++;
   int lf = 0;
@@ -1067,8 +1094,16 @@ void tc_fill_cfgdev(const Ctx* c, CfgDev* g) {
 // work items of one member (engine member index i)
 void tc_items(const Ctx* c, int i, std::vector<TwItem>& prep, std::vector<TcItem>& dens, std::vector<TcItem>& force) {
   const TcPlan& t = c->tc;
-  for (int kind = 1; kind >= 0; kind--)  // the heavier w items first
-    for (int64_t j = 0; j < c->N; j += kPrepParticles) prep.push_back({i, kind, j});
+  // the heavier w items first.  d = 3 w items cover 16 particles (their powers fill shared memory); a table
+  // item covers enough groups of 8 particles for 128 (entry, group) lane pairs, at most 128 particles
+  for (int kind = 1; kind >= 0; kind--) {
+    const int count = kind == 0 ? t.R1 + 1 : t.nP;
+    int ng = 1;
+    if (kind == 1 && t.d == 3) ng = kPrepStaged / 8;
+    else
+      while (ng < kPrepTable / 8 && ng * count < kPrepThreads / 2) ng *= 2;
+    for (int64_t j = 0; j < c->N; j += 8 * ng) prep.push_back({i, kind | (ng << 8), j});
+  }
   for (int ti = 0; ti < (int)t.tiles.size(); ti++) {
     const int rt = t.tiles[ti] / t.CTd, ct = t.tiles[ti] % t.CTd;
     for (int sp = 0; sp < t.ksplit; sp++) {
