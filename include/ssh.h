@@ -53,13 +53,14 @@ typedef enum {
 typedef enum { SSH_FP64 = 0, SSH_DD = 1, SSH_FX = 2 } ssh_prec;
 
 /* Implementation of SSH_FX evaluations (same arithmetic class, results agree to the 1e-28 normwise bound):
- *   SSH_FX_AUTO    -- the library's choice: the tensor cores for d = 2 and 3, the integer pipes otherwise
+ *   SSH_FX_AUTO    -- the library's choice: the tensor cores for d <= 3, the integer pipes otherwise
  *   SSH_FX_INTEGER -- 128-bit fixed point on the integer pipes, any d
- *   SSH_FX_TENSOR  -- d = 2 or 3 (else SSH_EINVAL): both sums as exact-digit GEMMs on the tensor cores (15
+ *   SSH_FX_TENSOR  -- d <= 3 (else SSH_EINVAL): both sums as exact-digit GEMMs on the tensor cores (15
  *                     balanced 7-bit digits per 2^-104 fixed-point value in bf16, fp32 accumulation kept exact by
- *                     bounded read-outs).  A wavevector set beyond the path's limits (d = 3 with max |n_2| +
- *                     max |n_3| above 211, or more than 16384 distinct (n_2, n_3)) runs on the integer pipes;
- *                     ssh_get_fx_impl reports which implementation a context uses. */
+ *                     bounded read-outs; d = 1 runs on two lifted axes, n = 2^b n_1 + n_2).  A wavevector set
+ *                     beyond the path's limits (d = 3 with max |n_2| + max |n_3| above 211, or more than 16384
+ *                     distinct (n_2, n_3)) runs on the integer pipes; ssh_get_fx_impl reports which
+ *                     implementation a context uses. */
 enum { SSH_FX_AUTO = 0, SSH_FX_INTEGER = 1, SSH_FX_TENSOR = 2 };
 #define SSH_FX_AUTO_TENSOR 1
 
@@ -263,7 +264,7 @@ typedef struct {
                                   running request shares; a larger request runs only in an empty batch */
   int policy;                  /* 0: smallest M N first (default), 1: first come first served */
   int fx_impl;                 /* fixed-point implementation of the members (ssh_opts.fx_impl; SSH_FX_TENSOR
-                                  applies to the d = 2, 3 requests, the others use the integer pipes) */
+                                  applies to the d <= 3 requests, the others use the integer pipes) */
 } ssh_server_opts;
 typedef struct {
   int d;

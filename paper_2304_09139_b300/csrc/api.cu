@@ -64,12 +64,12 @@ ssh_status ssh_create(int d, int64_t N, double L, double chi, double K, const ss
   c.device = opts ? opts->device : 0;
   const int fx_impl = opts ? opts->fx_impl : SSH_FX_AUTO;
   if (fx_impl < SSH_FX_AUTO || fx_impl > SSH_FX_TENSOR) { delete h; set_error("ssh_create: bad fx_impl"); return SSH_EINVAL; }
-  if (fx_impl == SSH_FX_TENSOR && d != 2 && d != 3) {
+  if (fx_impl == SSH_FX_TENSOR && d > 3) {
     delete h;
-    set_error("ssh_create: the tensor-core fixed-point path needs d = 2 or 3");
+    set_error("ssh_create: the tensor-core fixed-point path needs d <= 3");
     return SSH_EINVAL;
   }
-  c.tc_requested = fx_impl == SSH_FX_TENSOR || (fx_impl == SSH_FX_AUTO && (d == 2 || d == 3) && SSH_FX_AUTO_TENSOR);
+  c.tc_requested = fx_impl == SSH_FX_TENSOR || (fx_impl == SSH_FX_AUTO && d <= 3 && SSH_FX_AUTO_TENSOR);
   if (ssh::build_kset(d, N, L, chi, K, &c.ks) != 0) {
     delete h;
     set_error("ssh_create: could not build the wavevector set");

@@ -156,12 +156,14 @@ cudaError_t engine_build(Engine* e, const std::vector<Ctx*>& members, const std:
   std::vector<TcItem> tcd, tcf;
   int64_t tc_grid = 0;
   size_t tc_smem = 0;
+  int64_t tc_nd = 0;
   for (int i : lists[SSH_FX])
     if (members[i]->tc.on) {
       tcl.push_back(i);
       tc_items(members[i], i, tcp, tcd, tcf);
       tc_grid = std::max<int64_t>(tc_grid, (int64_t)(members[i]->tc.R1 + 1) * members[i]->tc.nP);
       tc_smem = std::max(tc_smem, members[i]->tc.prep_smem);
+      tc_nd = std::max<int64_t>(tc_nd, (int64_t)members[i]->tc.d * members[i]->N);
     }
   // largest items first over all members: the persistent GEMM assigns them round-robin
   auto by_size = [](const TcItem& a, const TcItem& b) { return a.nks > b.nks; };
@@ -207,6 +209,7 @@ cudaError_t engine_build(Engine* e, const std::vector<Ctx*>& members, const std:
       v.ntc_force = (int)tcf.size();
       v.tc_max_grid = tc_grid;
       v.tc_prep_smem = tc_smem;
+      v.tc_maxND = tc_nd;
     }
     for (int i : lists[p]) {
       const Ctx* c = members[i];

@@ -86,6 +86,7 @@ struct CfgDev {
   dd pref, inv_L;
   // tensor-core fixed-point path (tc.cu); tc = 0 when the configuration uses the integer-pipe kernels
   int tc, tc_R1, tc_nP, tc_RT, tc_CTd, tc_PT, tc_KSf, tc_CTf, tc_bexp, tc_ksplit, tc_nblk, tc_gs, tc_ts, tc_ntab;
+  int tc_d, tc_lift;   // the path's number of axes (2 or 3); d = 1 on two lifted axes: n = 2^tc_lift n1 + n2
   int tc_Rax[3];       // per axis: powers 0..tc_Rax[a] in the tables
   int64_t tc_KS, tc_NJ, tc_NPg;  // density K-steps; particle groups and row groups of the digit tensor
   uint8_t *tc_wT, *tc_aB, *tc_fB;  // digit tensor of w_j(p); density B (a_j(n1)); force B (coefficients)
@@ -144,6 +145,7 @@ struct EngineView {
   int ntc_force = 0;
   int64_t tc_max_grid = 0;  // largest (R1 + 1) nP of the members
   size_t tc_prep_smem = 0;  // largest preparation shared memory of the members
+  int64_t tc_maxND = 0;     // largest (the path's axes) x N of the members (d = 1 runs on two lifted axes)
 };
 
 struct Ctx;
@@ -191,7 +193,8 @@ struct Engine {
 // tile plan and buffers of the tensor-core path of one configuration (tc.cu)
 struct TcPlan {
   bool on = false;
-  int d = 0;
+  int d = 0;                     // the path's number of axes: 2 or 3 (d = 1 runs on two lifted axes)
+  int lift = 0;                  // d = 1: n = 2^lift n1 + n2, n2 in [-2^(lift - 1), 2^(lift - 1))
   int R1 = 0;                    // n1 in [0, R1]
   int Rax[3] = {0, 0, 0};        // largest |n_a| per axis (powers held in the tables)
   int nP = 0;                    // canonical sub-vectors p = (n2[, n3]) of the half set, sorted by |p|^2
@@ -248,7 +251,7 @@ struct Ctx {
   dd inv_L;                       // 1 / L
   FireBufs* fire = nullptr;       // minimiser state, allocated on first ssh_minimize
   Engine* eng = nullptr;          // this context alone (plain evaluations)
-  bool tc_requested = false;      // fixed point on the tensor cores (d = 2, 3)
+  bool tc_requested = false;      // fixed point on the tensor cores (d = 1, 2, 3)
   TcPlan tc;
 };
 
@@ -300,7 +303,7 @@ cudaError_t fire_stage_init_engine(const Engine* e, const std::vector<int>& idx,
 // device scalar block written by k_finalize (doubles)
 enum { kScPhiHi = 0, kScPhiLo, kScSmaxHi, kScSmaxLo, kScCmax, kScScaleExp, kScA2MaxHi, kScA2MaxLo, kScCount = 16 };
 
-// tc.cu (tensor-core fixed-point path, d = 2 and 3)
+// tc.cu (tensor-core fixed-point path, d = 1, 2, 3)
 bool tc_eligible(const Ctx& c);
 int tc_finish_blocks(const Ctx& c);  // blocks of the density finish kernel (its reduction partials)
 cudaError_t tc_setup(Ctx* c);

@@ -124,6 +124,24 @@ __device__ __forceinline__ void i192_add_shl(i192& a, __int128 v, int sh) {
   a.w[1] = (unsigned long long)(s01 >> 64);
   a.w[2] = a.w[2] + top + carry;
 }
+// a << sh (0 <= sh < 64), two's complement
+__device__ __forceinline__ i192 i192_shl(const i192& a, int sh) {
+  if (sh == 0) return a;
+  i192 r;
+  r.w[2] = (a.w[2] << sh) | (a.w[1] >> (64 - sh));
+  r.w[1] = (a.w[1] << sh) | (a.w[0] >> (64 - sh));
+  r.w[0] = a.w[0] << sh;
+  return r;
+}
+__device__ __forceinline__ i192 i192_add(const i192& a, const i192& b) {
+  const unsigned __int128 a01 = ((unsigned __int128)a.w[1] << 64) | a.w[0];
+  const unsigned __int128 s01 = a01 + (((unsigned __int128)b.w[1] << 64) | b.w[0]);
+  i192 r;
+  r.w[0] = (unsigned long long)s01;
+  r.w[1] = (unsigned long long)(s01 >> 64);
+  r.w[2] = a.w[2] + b.w[2] + (s01 < a01 ? 1ull : 0ull);
+  return r;
+}
 // the low 160 bits of a << sh (0 <= sh < 64) as a Q34.126 accumulator
 __device__ __forceinline__ q160 i192_to_q160_shl(const i192& a, int sh) {
   unsigned long long w0 = a.w[0], w1 = a.w[1], w2 = a.w[2];
@@ -287,11 +305,14 @@ __global__ void __launch_bounds__(128) k_tc_tables(const CfgDev* __restrict__ cf
   const CfgDev& c = cfgs[list[blockIdx.y]];
   if (stopped(c)) return;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)c.d * c.N) return;
+  if (idx >= (int64_t)c.tc_d * c.N) return;
   const int axis = (int)(idx / c.N);
   const int64_t j = idx - (int64_t)axis * c.N;
   const int nA = c.tc_Rax[axis] / kPrepLow + 1;
-  const q128 u = turns_from_dd(c.s_hi[axis * c.N + j], c.s_lo[axis * c.N + j]);
+  // d = 1 lifted to two axes: axis 0 holds the phase 2^lift s (mod 1, exact), axis 1 the phase s
+  const int src = c.tc_lift ? 0 : axis;
+  q128 u = turns_from_dd(c.s_hi[src * c.N + j], c.s_lo[src * c.N + j]);
+  if (c.tc_lift && axis == 0) u = turn_times(u, 1 << c.tc_lift);
   qent* tab = reinterpret_cast<qent*>(c.tc_tab) + idx * c.tc_ntab;
   const qent one = to_quadrant(phasor_turn(q128_zero()));
   const qent e1 = to_quadrant(phasor_turn(u));
@@ -327,14 +348,14 @@ __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restri
   const CfgDev& c = cfgs[it.cfg];
   if (stopped(c)) return;
   const int kind = it.pad & 0xff, ng = it.pad >> 8;  // particle groups of 8
-  const bool staged = kind == 1 && c.d == 3;
+  const bool staged = kind == 1 && c.tc_d == 3;
   const int64_t N = c.N;
   const int64_t j0 = it.start;
   const int tid = threadIdx.x, lane = tid & 31, h = lane & 1;
   const __int128 bias = digit_bias();
   const uint4 yzero = make_uint4((uint32_t)bias, (uint32_t)(bias >> 32), (uint32_t)(bias >> 64), (uint32_t)(bias >> 96));
   const qent* tab = reinterpret_cast<const qent*>(c.tc_tab);
-  const int W2 = c.tc_Rax[1] + 1, W23 = W2 + (c.d == 3 ? c.tc_Rax[2] + 1 : 0);
+  const int W2 = c.tc_Rax[1] + 1, W23 = W2 + (c.tc_d == 3 ? c.tc_Rax[2] + 1 : 0);
   const int count = kind == 0 ? c.tc_R1 + 1 : c.tc_nP;
   int32_t* pvs = reinterpret_cast<int32_t*>(psm);  // kind 1: the packed (n2, n3) of every entry
   qent* Pw = reinterpret_cast<qent*>(psm + (((size_t)c.tc_nP * 4 + 15) & ~(size_t)15));  // [particle][n2, then n3]
@@ -611,7 +632,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
         // pairs (Re G, Im G) i = 0, 1, ...; this warp holds pairs 4 hq .. 4 hq + 3.  G~ = R' 2^-110 is taken as
         // R' 2^gs (|.| < 2^126); the top halves of a * G are value 2^(108 + gs), shifted to value 2^ts.
         const int64_t j = (int64_t)it.a * kTileM + row;
-        const int d = c.d, npt = 16 / d;
+        const int d = c.tc_d, npt = 16 / d;
         const int gsh = c.tc_gs, tsh = 108 + c.tc_gs - c.tc_ts;
         __int128 F0 = 0, F1 = 0, F2 = 0;  // per axis, value 2^ts (at most four terms each)
 #pragma unroll
@@ -751,20 +772,33 @@ __global__ void __launch_bounds__(kFinThreads) k_tc_force_finish(const CfgDev* _
   if (i >= (int64_t)c.d * c.N) return;
   const int a = (int)(i / c.N);
   const int64_t j = i - (int64_t)a * c.N;
-  long long* fa = c.tc_facc + (size_t)a * 3 * c.N + j;
-  const long long L0 = fa[0], L1 = fa[c.N], L2 = fa[2 * c.N];
-  fa[0] = 0;
-  fa[c.N] = 0;
-  fa[2 * c.N] = 0;
-  i192 X;
-  i192_zero(X);
-  i192_add_shl(X, (__int128)L0, 0);
-  i192_add_shl(X, (__int128)L1, 44);
-  i192_add_shl(X, (__int128)L2, 88);
-  // value = X 2^-ts in units of 2^e (axes 2, 3: of 2^(e + bexp))
+  // sum of the limbs of one axis of the GEMM's force, value X 2^-ts in units of 2^e (axes 2, 3: of 2^(e + bexp))
+  auto limbs = [&](int ax) {
+    long long* fa = c.tc_facc + (size_t)ax * 3 * c.N + j;
+    const long long L0 = fa[0], L1 = fa[c.N], L2 = fa[2 * c.N];
+    fa[0] = 0;
+    fa[c.N] = 0;
+    fa[2 * c.N] = 0;
+    i192 X;
+    i192_zero(X);
+    i192_add_shl(X, (__int128)L0, 0);
+    i192_add_shl(X, (__int128)L1, 44);
+    i192_add_shl(X, (__int128)L2, 88);
+    return X;
+  };
   const int e = (int)c.scal[kScScaleExp];
+  i192 X = limbs(a);
+  int se = e + (a > 0 ? c.tc_bexp : 0);
+  if (c.tc_lift) {
+    // d = 1 on two lifted axes, n = 2^lift n1 + n2: F = 2^lift F_1 + F_2 = 2^(e + bexp - ts) (X_1 2^(lift - bexp)
+    // + X_2), added exactly as integers.  X_1 is non-zero only when some n >= 2^(lift - 1), and then |n2| reaches
+    // 2^(lift - 1) - 1, so lift - bexp <= 1 and the sum stays far below 2^150.
+    X = i192_shl(X, c.tc_lift - c.tc_bexp);
+    X = i192_add(X, limbs(1));
+    se = e + c.tc_bexp;
+  }
   dd f = dd_mul(i192_to_dd(X, c.tc_ts), c.pref);
-  const double sc = pow2(e + (a > 0 ? c.tc_bexp : 0));
+  const double sc = pow2(se);
   c.F_hi[i] = f.hi * sc;
   c.F_lo[i] = f.lo * sc;
 }
@@ -798,7 +832,7 @@ __global__ void k_tc_coef(const CfgDev* __restrict__ cfgs, const int* __restrict
   const q160 smi = q160_sub160(Sp, Sm);
   const int shG = 22 + e, shW = 22 + e + c.tc_bexp;
   const int kf = 2 * p;
-  for (int t = 0; t < c.d; t++) {
+  for (int t = 0; t < c.tc_d; t++) {
     __int128 X[2][2];  // [Re / Im column][cos / sin row]
     if (t == 0) {
       X[0][0] = q160_shr_round(cpl, shG);
@@ -813,11 +847,11 @@ __global__ void k_tc_coef(const CfgDev* __restrict__ cfgs, const int* __restrict
       X[1][1] = q160_shr_round(q160_mul_int(cpl, n), shW);
     }
     if (p0) X[0][1] = X[1][1] = 0;  // sin(0) = 0 (and every weight n_a is 0)
-    const int npt = 16 / c.d;         // n1 values per column tile, all axes of each
+    const int npt = 16 / c.tc_d;      // n1 values per column tile, all axes of each
     const int ct = n1 / npt;
 #pragma unroll
     for (int ri = 0; ri < 2; ri++) {
-      const int col = 2 * (c.d * (n1 - ct * npt) + t) + ri;
+      const int col = 2 * (c.tc_d * (n1 - ct * npt) + t) + ri;
 #pragma unroll
       for (int qq = 0; qq < 2; qq++) {
         const int kk = kf + qq;
@@ -838,7 +872,7 @@ static cudaError_t tc_dev_alloc(DevBuf* b, size_t bytes, cudaStream_t st) {
   return cudaMemsetAsync(b->p, 0, bytes, st);  // padding rows, columns and K stay zero for good
 }
 
-bool tc_eligible(const Ctx& c) { return (c.d == 2 || c.d == 3) && c.N >= 1 && c.M >= 1; }
+bool tc_eligible(const Ctx& c) { return c.d >= 1 && c.d <= 3 && c.N >= 1 && c.M >= 1; }
 
 int tc_finish_blocks(const Ctx& c) {
   if (!c.tc.on) return 0;
@@ -865,12 +899,54 @@ EncodeTiledFn encode_tiled() {
   return fn;
 }
 
-// sub-vector p = (n2, n3) of axes 2..d of internal wavevector k (n3 = 0 for d = 2)
-inline void sub_vec(const Ctx& c, int64_t k, int& n1, int& n2, int& n3) {
+// (n1, p) of internal wavevector k: p = (n2, n3) of axes 2..d (n3 = 0 for d = 2).  For d = 1 the single index
+// n > 0 is split as n = 2^lift n1 + n2 with n2 in [-2^(lift - 1), 2^(lift - 1)): the phase n s is n1 (2^lift s)
+// + n2 s, a wavevector of two lifted axes, and n > 0 exactly when (n1, n2) lies in the two-axis half set.
+inline void sub_vec(const Ctx& c, int lift, int64_t k, int& n1, int& n2, int& n3) {
   const int32_t* n = &c.ks.n_int[(size_t)k * c.d];
+  n3 = 0;
+  if (c.d == 1) {
+    const int64_t B = (int64_t)1 << lift;
+    n1 = (int)((n[0] + B / 2) >> lift);
+    n2 = (int)(n[0] - B * n1);
+    return;
+  }
   n1 = n[0];
   n2 = n[1];
   n3 = c.d == 3 ? n[2] : 0;
+}
+
+// d = 1: the split 2^lift minimising the padded work of both GEMMs (rows (n2, cos / sin) in tiles of 128 and
+// columns (n1, cos / sin) in tiles of 32 for the density; 8 values of n1 per 32 columns and K in steps of 16
+// rows for the force)
+int choose_lift(const Ctx& c) {
+  int64_t nmax = 1;
+  for (int64_t k = 0; k < c.M; k++) nmax = std::max<int64_t>(nmax, c.ks.n_int[k]);
+  int best = 4;
+  double best_cost = 0;
+  for (int lift = 4; lift <= 15; lift++) {  // |n2| <= 2^14 fits the 16-bit field of the packed p
+    const int64_t B = (int64_t)1 << lift;
+    std::vector<char> seen(B / 2 + 1, 0);
+    int64_t nP = 0, R1 = 0;
+    for (int64_t k = 0; k < c.M; k++) {
+      int n1, n2, n3;
+      sub_vec(c, lift, k, n1, n2, n3);
+      R1 = std::max<int64_t>(R1, n1);
+      const int a = std::abs(n2);
+      if (!seen[a]) {
+        seen[a] = 1;
+        nP++;
+      }
+    }
+    auto pad = [](int64_t x, int64_t m) { return (x + m - 1) / m * m; };
+    const double cost = (double)pad(2 * nP, 128) * pad(2 * (R1 + 1), 32) + (double)pad(R1 + 1, 8) * 4 * pad(2 * nP, 16);
+    if (lift == 4 || cost < best_cost) {
+      best = lift;
+      best_cost = cost;
+    }
+    if (B / 2 > nmax) break;  // every larger split puts the whole set in n1 = 0
+  }
+  return best;
 }
 inline bool canonical(int n2, int n3) { return n3 > 0 || (n3 == 0 && n2 >= 0); }
 
@@ -888,13 +964,14 @@ cudaError_t tc_setup(Ctx* c) {
   t.pvec.clear();
   t.ks_ct.clear();
   if (!c->tc_requested || !tc_eligible(*c)) return cudaSuccess;
-  const int d = c->d;
+  const int d = c->d == 1 ? 2 : c->d;  // the path's number of axes (d = 1 runs on two lifted axes)
+  const int lift = c->d == 1 ? choose_lift(*c) : 0;
   const int64_t M = c->M;
   // canonical sub-vectors present in the set, sorted by |p|^2 (then n3, n2): a prefix of the list is a disk
   int R1 = 0, Rp = 0;
   for (int64_t k = 0; k < M; k++) {
     int n1, n2, n3;
-    sub_vec(*c, k, n1, n2, n3);
+    sub_vec(*c, lift, k, n1, n2, n3);
     R1 = std::max(R1, n1);
     Rp = std::max(Rp, std::max(std::abs(n2), std::abs(n3)));
   }
@@ -903,7 +980,7 @@ cudaError_t tc_setup(Ctx* c) {
   std::vector<std::pair<int, int>> plist;
   for (int64_t k = 0; k < M; k++) {
     int n1, n2, n3;
-    sub_vec(*c, k, n1, n2, n3);
+    sub_vec(*c, lift, k, n1, n2, n3);
     if (!canonical(n2, n3)) {
       n2 = -n2;
       n3 = -n3;
@@ -936,6 +1013,7 @@ cudaError_t tc_setup(Ctx* c) {
   while ((1ll << lf) < 4ll * std::max(1, R1) * 2ll * nP) lf++;
   if (prep_smem > kPrepSmemMax || 16 - lg < 1 || 126 - lf < 64 || encode_tiled() == nullptr) return cudaSuccess;
   t.d = d;
+  t.lift = lift;
   t.R1 = R1;
   t.Rax[0] = R1;
   t.Rax[1] = R2;
@@ -964,7 +1042,7 @@ cudaError_t tc_setup(Ctx* c) {
   std::vector<int> pmax_ct(t.CTf, -1);
   for (int64_t k = 0; k < M; k++) {
     int n1, n2, n3;
-    sub_vec(*c, k, n1, n2, n3);
+    sub_vec(*c, lift, k, n1, n2, n3);
     const bool can = canonical(n2, n3);
     const int p = pid[(size_t)((can ? n3 : -n3) + Rp) * span + ((can ? n2 : -n2) + Rp)];
     t.em[((size_t)p * W1 + n1) * 2 + (can ? 0 : 1)] = (int32_t)k;
@@ -1059,6 +1137,8 @@ void tc_fill_cfgdev(const Ctx* c, CfgDev* g) {
   const TcPlan& t = c->tc;
   g->tc = t.on ? 1 : 0;
   if (!t.on) return;
+  g->tc_d = t.d;
+  g->tc_lift = t.lift;
   g->tc_R1 = t.R1;
   g->tc_nP = t.nP;
   for (int a = 0; a < 3; a++) g->tc_Rax[a] = t.Rax[a];
@@ -1136,7 +1216,7 @@ cudaError_t tc_launch_force_finish(const EngineView& v, cudaStream_t st, Prof* p
 cudaError_t tc_launch_density(const EngineView& v, cudaStream_t st, Prof* prof) {
   if (v.ntc_list == 0) return cudaSuccess;
   prof_begin(prof, st, kKTcPrep);
-  cudaError_t le = launch_pdl(k_tc_tables, dim3((unsigned)std::max<int64_t>(1, (v.maxND + 127) / 128), (unsigned)v.ntc_list),
+  cudaError_t le = launch_pdl(k_tc_tables, dim3((unsigned)std::max<int64_t>(1, (v.tc_maxND + 127) / 128), (unsigned)v.ntc_list),
                               dim3(128), 0, st, v.cfgs, v.tc_list);
   if (le == cudaSuccess)
     le = launch_pdl(k_tc_prep, dim3((unsigned)v.ntc_prep), dim3(kPrepThreads), v.tc_prep_smem, st, v.cfgs, v.tc_prep);

@@ -32,10 +32,11 @@ def small_mix(count, seed, n_lo=64, n_hi=400, dims=(2, 3)):
     return synth.mixed_batch(seed, count, n_lo=n_lo, n_hi=n_hi, dims=dims)
 
 
-def test_batched_evaluation_equals_single(built):
+@pytest.mark.parametrize("impl", [ssh.FX_AUTO, ssh.FX_INTEGER], ids=["auto", "int"])
+def test_batched_evaluation_equals_single(built, impl):
     cfgs = small_mix(7, 41) + [synth.Config(d=1, N=300, L=300.0, chi=0.3, seed=9),
                               synth.Config(d=2, N=2000, L=2000 ** 0.5, chi=0.45, seed=10)]
-    b = ssh.Batch()
+    b = ssh.Batch(fx_impl=impl)
     for c in cfgs:
         b.add(c.d, c.N, c.L, synth.positions(c.seed, c.N, c.d), chi=c.chi)
     n, pairs = b.size()
@@ -45,7 +46,7 @@ def test_batched_evaluation_equals_single(built):
         for i, c in enumerate(cfgs):
             rb = b.member(i).results()
             Cb, Sb = b.member(i).ntilde()
-            with ssh.Context(c.d, c.N, c.L, chi=c.chi) as ctx:
+            with ssh.Context(c.d, c.N, c.L, chi=c.chi, fx_impl=impl) as ctx:
                 ctx.set_positions_frac(synth.positions(c.seed, c.N, c.d))
                 ra = ctx.energy_grad(prec)
                 Ca, Sa = ctx.ntilde()
@@ -56,15 +57,16 @@ def test_batched_evaluation_equals_single(built):
 
 
 def test_tensor_members_equal_single(built):
-    """A batch whose d = 2, 3 members run on the tensor cores and whose d = 1 members run on the integer pipes:
+    """A batch whose d = 1, 2, 3 members run on the tensor cores and whose d = 4 member runs on the integer pipes:
     every member bit-identical to a lone context of the same implementation, in an evaluation and a quench."""
-    cfgs = small_mix(6, 46, dims=(1, 2, 3)) + [synth.Config(d=2, N=2000, L=2000 ** 0.5, chi=0.45, seed=11)]
+    cfgs = small_mix(6, 46, dims=(1, 2, 3)) + [synth.Config(d=2, N=2000, L=2000 ** 0.5, chi=0.45, seed=11),
+                                              synth.Config(d=4, N=120, L=120 ** 0.25, chi=0.3, seed=12)]
     b = ssh.Batch(fx_impl=ssh.FX_TENSOR)
     for c in cfgs:
         b.add(c.d, c.N, c.L, synth.positions(c.seed, c.N, c.d), chi=c.chi)
     b.eval(ssh.FX)
     for i, c in enumerate(cfgs):
-        impl = ssh.FX_TENSOR if c.d in (2, 3) else ssh.FX_INTEGER
+        impl = ssh.FX_TENSOR if c.d <= 3 else ssh.FX_INTEGER
         assert b.member(i).fx_impl == impl
         rb = b.member(i).results()
         with ssh.Context(c.d, c.N, c.L, chi=c.chi, fx_impl=impl) as ctx:

@@ -71,6 +71,8 @@ CASES = [
     ("small_d2", 2, 100, 1.0, 0.30, 0.0, 1),
     ("ragged_d2", 2, 333, 333 ** 0.5, 0.45, 0.0, 7),
     ("d1", 1, 257, 257.0, 0.45, 0.0, 8),
+    # d = 1 on the tensor cores splits n = 2^b n1 + n2: M = 1800 spans several row and column tiles
+    ("d1_wide", 1, 4000, 4000.0, 0.45, 0.0, 16),
     ("d3", 3, 300, 300 ** (1 / 3), 0.40, 0.0, 9),
     ("d3_kmode", 3, 150, 4.0, 0.0, 2 * math.pi * 3.3 / 4.0, 10),
     ("d4", 4, 120, 120 ** 0.25, 0.3, 0.0, 11),
@@ -86,8 +88,8 @@ CASES = [
 
 
 def impls(d):
-    """(fx_impl, precisions to check) per context: d = 2, 3 run the fixed point through both implementations."""
-    if d in (2, 3):
+    """(fx_impl, precisions to check) per context: d <= 3 runs the fixed point through both implementations."""
+    if d <= 3:
         return [(ssh.FX_INTEGER, PRECS), (ssh.FX_TENSOR, [ssh.FX])]
     return [(ssh.FX_AUTO, PRECS)]
 
@@ -242,8 +244,10 @@ def test_fx_impl_selection(built):
     with ssh.Context(2, 64, 8.0, chi=0.3, fx_impl=ssh.FX_INTEGER) as c:
         assert c.fx_impl == ssh.FX_INTEGER
     with ssh.Context(3, 64, 4.0, chi=0.3) as c:
-        assert c.fx_impl == ssh.FX_TENSOR        # the tensor-core path covers d = 2 and 3
+        assert c.fx_impl == ssh.FX_TENSOR        # the tensor-core path covers d = 1, 2 and 3
     with ssh.Context(1, 64, 64.0, chi=0.3) as c:
+        assert c.fx_impl == ssh.FX_TENSOR        # d = 1 on two lifted axes
+    with ssh.Context(4, 64, 64 ** 0.25, chi=0.3) as c:
         assert c.fx_impl == ssh.FX_INTEGER
     with pytest.raises(ssh.SshError) as e:
         ssh.Context(4, 64, 64 ** 0.25, chi=0.3, fx_impl=ssh.FX_TENSOR)
