@@ -151,7 +151,8 @@ ssh_status ssh_get_ntilde(ssh_ctx* ctx, double* C_hi, double* C_lo, double* S_hi
  *   n_stages, stage_prec   precision ladder, e.g. {SSH_FP64, SSH_DD} (default {SSH_FX} when the context's
  *                          fixed point runs on the tensor cores, else {SSH_FP64, SSH_FX}); a stage
  *                          ends when S_max <= stage_floor[s] or S_max has not halved in stall_window[s]
- *                          steps; the last stage ends only at the target, the step cap or a stall
+ *                          steps (0, the default: 200 for an FP64 stage, 5000 for dd or fixed point); the
+ *                          last stage ends only at the target, the step cap or a stall
  *   max_steps, smax_target step cap (default 200000) and convergence target (default 1e-36)
  *   chunk                  steps between host checks of the device status word (default 64)
  *   max_seconds            wall-time limit, 0 = none

@@ -343,9 +343,10 @@ ssh_status ssh_min_defaults(const ssh_ctx* h, ssh_min_params* p) {
   p->stage_prec[1] = SSH_FX;
   p->stage_prec[2] = SSH_FX;
   p->stage_floor[0] = 1e-24;
-  p->stall_window[0] = 200;
-  p->stall_window[1] = 5000;
-  p->stall_window[2] = 5000;
+  // stall windows 0: by the stage's precision (complete_params), whatever ladder the caller sets
+  p->stall_window[0] = 0;
+  p->stall_window[1] = 0;
+  p->stall_window[2] = 0;
   p->max_steps = 200000;
   p->smax_target = 1e-36;
   p->chunk = 64;
@@ -371,8 +372,10 @@ ssh_status ssh::complete_params(const ssh_ctx* h, const ssh_min_params* pin, ssh
     p.n_stages = d.n_stages;
     for (int i = 0; i < 3; i++) { p.stage_prec[i] = d.stage_prec[i]; p.stage_floor[i] = d.stage_floor[i]; }
   }
+  // an FP64 stage reaches its rounding floor quickly and hands over after 200 steps without halving; a dd or
+  // fixed-point stage is the last word on the quench and keeps going for 5000 (slow d = 1 quenches need it)
   for (int i = 0; i < 3; i++)
-    if (p.stall_window[i] <= 0) p.stall_window[i] = d.stall_window[i];
+    if (p.stall_window[i] <= 0) p.stall_window[i] = p.stage_prec[i] == SSH_FP64 ? 200 : 5000;
   if (p.max_steps <= 0) p.max_steps = d.max_steps;
   if (p.smax_target <= 0) p.smax_target = d.smax_target;
   if (p.chunk <= 0) p.chunk = d.chunk;
