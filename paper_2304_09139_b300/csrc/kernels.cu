@@ -426,31 +426,10 @@ __global__ void __launch_bounds__(kFinalizeThreads) k_finalize(const CfgDev* __r
                                                                const int* __restrict__ list, int prec) {
   grid_dep_wait();
   const CfgDev& c = cfgs[list[blockIdx.y]];
-  if (stopped(c)) return;
+  // tensor-core members finalise fixed-point evaluations in the last block of their density finish
+  if (stopped(c) || (prec == SSH_FX && c.tc)) return;
   __shared__ RedPart sh[kFinalizeThreads / 32];
-  const RedPart* blk = reinterpret_cast<const RedPart*>(c.blk);
-  RedPart v = {0, 0, 0, 0, 0, 0, 0, 0};
-  const int nb = (prec == SSH_FX && c.tc) ? c.tc_nblk : c.nblk;
-  if ((int)threadIdx.x < nb) v = blk[threadIdx.x];
-  for (int i = threadIdx.x + kFinalizeThreads; i < nb; i += kFinalizeThreads) red_combine(v, blk[i]);
-  red_warp(v);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    v = sh[0];
-#pragma unroll
-    for (int w = 1; w < kFinalizeThreads / 32; w++) red_combine(v, sh[w]);
-    double* scal = c.scal;
-    scal[kScPhiHi] = v.phi_hi;
-    scal[kScPhiLo] = v.phi_lo;
-    dd sm = c.N > 0 ? dd_div(dd_make(v.a2max_hi, v.a2max_lo), dd_make((double)c.N)) : dd_make(0.0);
-    scal[kScSmaxHi] = sm.hi;
-    scal[kScSmaxLo] = sm.lo;
-    scal[kScCmax] = v.cmax;
-    scal[kScScaleExp] = v.cmax > 0 ? (double)(ilogb(v.cmax) + 2) : 0.0;
-    scal[kScA2MaxHi] = v.a2max_hi;
-    scal[kScA2MaxLo] = v.a2max_lo;
-  }
+  finalize_block<kFinalizeThreads>(reinterpret_cast<const RedPart*>(c.blk), c.nblk, c.N, c.scal, sh);
 }
 
 template <class P>
@@ -718,10 +697,13 @@ static cudaError_t launch_prec(const EngineView& v, bool want_force, cudaStream_
     k_nt_reduce<P><<<gr, kRedThreads, 0, st>>>(v.cfgs, v.list);
     prof_end(prof, st);
   }
-  prof_begin(prof, st, kKFinalize);
-  cudaError_t le = launch_pdl(k_finalize, dim3(1, (unsigned)v.nlist), dim3(kFinalizeThreads), 0, st, v.cfgs, v.list, (int)P::kIdx);
-  if (le != cudaSuccess) return le;
-  prof_end(prof, st);
+  if (P::kIdx != SSH_FX || v.nlist > v.ntc_list) {
+    prof_begin(prof, st, kKFinalize);
+    cudaError_t le =
+        launch_pdl(k_finalize, dim3(1, (unsigned)v.nlist), dim3(kFinalizeThreads), 0, st, v.cfgs, v.list, (int)P::kIdx);
+    if (le != cudaSuccess) return le;
+    prof_end(prof, st);
+  }
   if (want_force) {
     if (v.nlist > v.ntc_list) {  // members that use these coefficients (the tensor-core path builds its own)
       const dim3 gc((unsigned)std::max<int64_t>(1, (v.maxM + 255) / 256), (unsigned)v.nlist);
