@@ -204,7 +204,7 @@ namespace {
 
 constexpr int kPrepThreads = 256;
 constexpr int kPrepStaged = 16;     // particles per d = 3 w item (their powers b(n2), c(n3) staged in shared memory)
-constexpr int kPrepItemPairs = 256; // (entry, 8 particles) pairs per table item (a(n1); w of d = 1, 2)
+constexpr int kPrepTable = 128;     // at most this many particles per table item (a(n1); w of d = 1, 2)
 constexpr int kPrepLow = 8;         // e^{2 pi i m s} = A[m / 8] T[m % 8]
 constexpr size_t kPrepSmemMax = 200 * 1024;
 
@@ -304,10 +304,8 @@ __global__ void __launch_bounds__(128) k_tc_tables(const CfgDev* __restrict__ cf
   grid_dep_wait();
   const CfgDev& c = cfgs[list[blockIdx.y]];
   if (stopped(c)) return;
-  const int64_t idx2 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx2 >= 2 * (int64_t)c.tc_d * c.N) return;
-  const int part = (int)(idx2 & 1);  // adjacent threads: the T chain and the A chain of one (axis, particle)
-  const int64_t idx = idx2 >> 1;
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)c.tc_d * c.N) return;
   const int axis = (int)(idx / c.N);
   const int64_t j = idx - (int64_t)axis * c.N;
   const int nA = c.tc_Rax[axis] / kPrepLow + 1;
@@ -316,29 +314,30 @@ __global__ void __launch_bounds__(128) k_tc_tables(const CfgDev* __restrict__ cf
   q128 u = turns_from_dd(c.s_hi[src * c.N + j], c.s_lo[src * c.N + j]);
   if (c.tc_lift && axis == 0) u = turn_times(u, 1 << c.tc_lift);
   qent* tab = reinterpret_cast<qent*>(c.tc_tab) + idx * c.tc_ntab;
-  const qent one = to_quadrant(phasor_turn(q128_zero()));
-  if (part == 0) {
-    const qent e1 = to_quadrant(phasor_turn(u));
-    qent t = one;
+  // e^0 = 1 exactly (the exact-phase evaluation returns (2^126, 0) at t = 0): c = 1 in Q1.127, s = 0, quadrant 0
+  qent one;
+  one.c = q128_zero();
+  one.c.w[3] = 0x80000000u;
+  one.s = q128_zero();
+  one.cs = one.c;
+  const qent e1 = to_quadrant(phasor_turn(u));
+  qent t = one;
 #pragma unroll 1
-    for (int k = 0; k < kPrepLow; k++) {
-      tab[k] = t;
-      if (k + 1 < kPrepLow) t = qmul(t, e1);
-    }
-  } else {
-    const qent e8 = to_quadrant(phasor_turn(turn_times(u, kPrepLow)));
-    qent a = one;
+  for (int k = 0; k < kPrepLow; k++) {
+    tab[k] = t;
+    if (k + 1 < kPrepLow) t = qmul(t, e1);
+  }
+  const qent e8 = to_quadrant(phasor_turn(turn_times(u, kPrepLow)));
+  qent a = one;
 #pragma unroll 1
-    for (int b = 0; b < nA; b++) {
-      tab[kPrepLow + b] = a;
-      if (b + 1 < nA) a = qmul(a, e8);
-    }
+  for (int b = 0; b < nA; b++) {
+    tab[kPrepLow + b] = a;
+    if (b + 1 < nA) a = qmul(a, e8);
   }
 }
 
-// CTA per item.  Items TwItem {cfg, kind | staged << 8, start}: a staged item (d = 3, kind 1) covers the 16
-// particles from start; a table item covers kPrepItemPairs (entry, particle group of 8) pairs of the whole
-// configuration from pair start (pair q: entry q % count, group q / count).  Kind 0: a_j(n1), n1 in [0, R1] -> density B digit slices (rows (n1, cos / sin) of
+// CTA per item.  Items TwItem {cfg, kind | staged << 8 | groups << 9, first particle}: 8 x groups particles (16
+// for a staged d = 3 w item; a table item enough for 128 (entry, group) lane pairs, at most 128).  Kind 0: a_j(n1), n1 in [0, R1] -> density B digit slices (rows (n1, cos / sin) of
 // K-major 32 x 16 tiles) and the Q2.126 table of the force epilogue.  Kind 1: w_j(p) for the nP canonical p ->
 // the digit tensor.  A lane pair takes one entry and eight consecutive particles: each lane forms four of the
 // products, the pair swaps halves, and lane 0 writes the entry's cos row, lane 1 its sin row, as 16-byte
@@ -353,10 +352,10 @@ __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restri
   const TwItem it = items[blockIdx.x];
   const CfgDev& c = cfgs[it.cfg];
   if (stopped(c)) return;
-  const int kind = it.pad & 0xff;
+  const int kind = it.pad & 0xff, ng = it.pad >> 9;  // particle groups of 8
   const bool staged = (it.pad >> 8) & 1;
   const int64_t N = c.N;
-  const int64_t j0 = staged ? it.start : 0;
+  const int64_t j0 = it.start;
   const int tid = threadIdx.x, lane = tid & 31, h = lane & 1;
   const __int128 bias = digit_bias();
   const uint4 yzero = make_uint4((uint32_t)bias, (uint32_t)(bias >> 32), (uint32_t)(bias >> 64), (uint32_t)(bias >> 96));
@@ -381,16 +380,12 @@ __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restri
   }
   const int axis = kind == 0 ? 0 : 1;
   const size_t wstride = (size_t)c.tc_NPg * (size_t)c.tc_NJ * 128;  // bytes between digit slices of the tensor
-  // (entry, group) pairs of lanes: [qbeg, qend)
-  const int64_t qbeg = staged ? 0 : it.start;
-  const int64_t qall = (int64_t)count * ((N + 7) / 8);
-  const int64_t qend = staged ? 2 * (int64_t)count : (it.start + kPrepItemPairs < qall ? it.start + kPrepItemPairs : qall);
-  for (int64_t q0 = qbeg + (tid >> 5) * 16; q0 < qend; q0 += kPrepThreads / 2) {  // warp-uniform, 16 pairs a warp
-    const int64_t q = q0 + (lane >> 1);
-    const bool valid = q < qend;
-    const int e = valid ? (int)(q % count) : 0;
-    const int g = valid ? (int)(q / count) : 0;
-    const int64_t jg = j0 + 8 * (int64_t)g;
+  const int total = count * ng;  // (entry, group) pairs of lanes
+  for (int q0 = (tid >> 5) * 16; q0 < total; q0 += kPrepThreads / 2) {  // warp-uniform: 16 pairs per warp
+    const int q = q0 + (lane >> 1);
+    const bool valid = q < total;
+    const int e = valid ? q % count : 0, g = valid ? q / count : 0;
+    const int64_t jg = j0 + 8 * g;
     const bool live = valid && jg < N;  // particle groups past the last particle stay zero
     int m = e, n2 = 0, n3 = 0;
     if (kind == 1) {
@@ -1195,15 +1190,14 @@ void tc_fill_cfgdev(const Ctx* c, CfgDev* g) {
 void tc_items(const Ctx* c, int i, std::vector<TwItem>& prep, std::vector<TcItem>& dens, std::vector<TcItem>& force) {
   const TcPlan& t = c->tc;
   // the heavier w items first.  d = 3 w items cover 16 particles (their powers fill shared memory); a table
-  // item covers kPrepItemPairs (entry, particle group) pairs, so every CTA has full lanes whatever the count
+  // item covers enough groups of 8 particles for 128 (entry, group) lane pairs, at most 128 particles
   for (int kind = 1; kind >= 0; kind--) {
-    const int64_t count = kind == 0 ? t.R1 + 1 : t.nP;
-    if (kind == 1 && t.d == 3) {
-      for (int64_t j = 0; j < c->N; j += kPrepStaged) prep.push_back({i, 1 | (1 << 8), j});
-    } else {
-      const int64_t total = count * ((c->N + 7) / 8);
-      for (int64_t q = 0; q < total; q += kPrepItemPairs) prep.push_back({i, kind, q});
-    }
+    const int count = kind == 0 ? t.R1 + 1 : t.nP;
+    const bool staged = kind == 1 && t.d == 3;
+    int ng = staged ? kPrepStaged / 8 : 1;
+    if (!staged)
+      while (ng < kPrepTable / 8 && ng * count < kPrepThreads / 2) ng *= 2;
+    for (int64_t j = 0; j < c->N; j += 8 * ng) prep.push_back({i, kind | (staged ? 1 << 8 : 0) | (ng << 9), j});
   }
   for (int ti = 0; ti < (int)t.tiles.size(); ti++) {
     const int rt = t.tiles[ti] / t.CTd, ct = t.tiles[ti] % t.CTd;
@@ -1237,7 +1231,7 @@ cudaError_t tc_launch_force_finish(const EngineView& v, cudaStream_t st, Prof* p
 cudaError_t tc_launch_density(const EngineView& v, cudaStream_t st, Prof* prof) {
   if (v.ntc_list == 0) return cudaSuccess;
   prof_begin(prof, st, kKTcPrep);
-  cudaError_t le = launch_pdl(k_tc_tables, dim3((unsigned)std::max<int64_t>(1, (2 * v.tc_maxND + 127) / 128), (unsigned)v.ntc_list),
+  cudaError_t le = launch_pdl(k_tc_tables, dim3((unsigned)std::max<int64_t>(1, (v.tc_maxND + 127) / 128), (unsigned)v.ntc_list),
                               dim3(128), 0, st, v.cfgs, v.tc_list);
   if (le == cudaSuccess)
     le = launch_pdl(k_tc_prep, dim3((unsigned)v.ntc_prep), dim3(kPrepThreads), v.tc_prep_smem, st, v.cfgs, v.tc_prep);
