@@ -65,7 +65,7 @@ CfgDev make_cfgdev(const Ctx* c, bool fire_mode) {
 
 void engine_free(Engine* e) {
   for (DevBuf* b : {&e->d_cfgs, &e->d_lists, &e->d_tw, &e->d_nt, &e->d_f, &e->d_counters, &e->d_tclist, &e->d_tcprep,
-                    &e->d_tcdens, &e->d_tcforce}) {
+                    &e->d_tcdens, &e->d_tcforce, &e->d_bm}) {
     if (b->p) cudaFree(b->p);
     b->p = nullptr;
     b->bytes = 0;
@@ -174,6 +174,36 @@ cudaError_t engine_build(Engine* e, const std::vector<Ctx*>& members, const std:
   if ((err = up(&e->d_tcprep, tcp.data(), sizeof(TwItem) * tcp.size(), st)) != cudaSuccess) return err;
   if ((err = up(&e->d_tcdens, tcd.data(), sizeof(TcItem) * tcd.size(), st)) != cudaSuccess) return err;
   if ((err = up(&e->d_tcforce, tcf.data(), sizeof(TcItem) * tcf.size(), st)) != cudaSuccess) return err;
+  // block maps: only the blocks each member needs
+  std::vector<BlockMap> bm;
+  auto add_blocks = [&](int cfg, int64_t nb) {
+    for (int64_t b = 0; b < nb; b++) bm.push_back({cfg, (int32_t)b});
+  };
+  size_t bm_off[6], bm_n[6];
+  bm_off[0] = bm.size();
+  for (int i = 0; i < n; i++) add_blocks(i, e->host_cfgs[i].nb_fire);
+  bm_n[0] = bm.size() - bm_off[0];
+  bm_off[1] = bm.size();
+  for (int i = 0; i < n; i++) add_blocks(i, ((int64_t)members[i]->d * members[i]->N + 63) / 64);
+  bm_n[1] = bm.size() - bm_off[1];
+  bm_off[2] = bm.size();
+  for (int i : tcl) add_blocks(i, ((int64_t)members[i]->tc.d * members[i]->N + 127) / 128);
+  bm_n[2] = bm.size() - bm_off[2];
+  bm_off[3] = bm.size();
+  for (int i : tcl) add_blocks(i, tc_finish_blocks(*members[i]));
+  bm_n[3] = bm.size() - bm_off[3];
+  bm_off[4] = bm.size();
+  for (int i : tcl) add_blocks(i, tc_coef_blocks(*members[i]));
+  bm_n[4] = bm.size() - bm_off[4];
+  bm_off[5] = bm.size();
+  for (int i : tcl) add_blocks(i, ((int64_t)members[i]->d * members[i]->N + 63) / 64);
+  bm_n[5] = bm.size() - bm_off[5];
+  if ((err = up(&e->d_bm, bm.data(), sizeof(BlockMap) * bm.size(), st)) != cudaSuccess) return err;
+  const BlockMap* dbm = (const BlockMap*)e->d_bm.p;
+  e->bm_dots = dbm + bm_off[0];
+  e->nbm_dots = (int)bm_n[0];
+  e->bm_nd = dbm + bm_off[1];
+  e->nbm_nd = (int)bm_n[1];
   if ((err = up(&e->d_cfgs, e->host_cfgs.data(), sizeof(CfgDev) * n, st)) != cudaSuccess) return err;
   if ((err = up(&e->d_lists, e->h_lists.data(), sizeof(int) * e->h_lists.size(), st)) != cudaSuccess) return err;
   if ((err = up(&e->d_tw, e->h_tw.data(), sizeof(TwItem) * e->h_tw.size(), st)) != cudaSuccess) return err;
@@ -210,6 +240,14 @@ cudaError_t engine_build(Engine* e, const std::vector<Ctx*>& members, const std:
       v.tc_max_grid = tc_grid;
       v.tc_prep_smem = tc_smem;
       v.tc_maxND = tc_nd;
+      v.tc_bm_tab = dbm + bm_off[2];
+      v.ntc_bm_tab = (int)bm_n[2];
+      v.tc_bm_fin = dbm + bm_off[3];
+      v.ntc_bm_fin = (int)bm_n[3];
+      v.tc_bm_coef = dbm + bm_off[4];
+      v.ntc_bm_coef = (int)bm_n[4];
+      v.tc_bm_ff = dbm + bm_off[5];
+      v.ntc_bm_ff = (int)bm_n[5];
     }
     for (int i : lists[p]) {
       const Ctx* c = members[i];

@@ -33,16 +33,18 @@ constexpr int kFireGraphSteps = 8;
 
 __device__ __forceinline__ FireState* fstate(const CfgDev& c) { return reinterpret_cast<FireState*>(c.fs); }
 
-// grid (blocks per member, members)
-__global__ void __launch_bounds__(kFireThreads) k_fire_dots(const CfgDev* __restrict__ cfgs, const int* __restrict__ all) {
+// block map: nb_fire blocks per member
+__global__ void __launch_bounds__(kFireThreads) k_fire_dots(const CfgDev* __restrict__ cfgs,
+                                                            const BlockMap* __restrict__ bm) {
   grid_dep_wait();
-  const CfgDev& c = cfgs[all[blockIdx.y]];
+  const BlockMap m = bm[blockIdx.x];
+  const CfgDev& c = cfgs[m.cfg];
   const FireState* fs = fstate(c);
-  if (fs->status || (int)blockIdx.x >= c.nb_fire) return;
+  if (fs->status) return;
   __shared__ double sh[3][kFireThreads];
   const int64_t nd = (int64_t)c.d * c.N;
   double p = 0, f2 = 0, v2 = 0;
-  for (int64_t i = (int64_t)blockIdx.x * kFireThreads + threadIdx.x; i < nd; i += (int64_t)c.nb_fire * kFireThreads) {
+  for (int64_t i = (int64_t)m.blk * kFireThreads + threadIdx.x; i < nd; i += (int64_t)c.nb_fire * kFireThreads) {
     double f = c.F_hi[i], w = c.v_hi[i];
     p = fma(f, w, p);
     f2 = fma(f, f, f2);
@@ -58,7 +60,7 @@ __global__ void __launch_bounds__(kFireThreads) k_fire_dots(const CfgDev* __rest
     __syncthreads();
   }
   if (threadIdx.x == 0)
-    for (int q = 0; q < 3; q++) c.fdots[q * c.nb_fire + blockIdx.x] = sh[q][0];
+    for (int q = 0; q < 3; q++) c.fdots[q * c.nb_fire + m.blk] = sh[q][0];
 }
 
 // one warp per member: the block partials are summed lane-strided in a fixed order, then by a fixed shuffle tree
@@ -102,13 +104,14 @@ __global__ void k_fire_ctrl(const CfgDev* __restrict__ cfgs, const int* __restri
   }
 }
 
-// grid (coordinate blocks, members)
-__global__ void k_fire_move(const CfgDev* __restrict__ cfgs, const int* __restrict__ all) {
+// block map: d N / 64 blocks per member
+__global__ void k_fire_move(const CfgDev* __restrict__ cfgs, const BlockMap* __restrict__ bm) {
   grid_dep_wait();
-  const CfgDev& c = cfgs[all[blockIdx.y]];
+  const BlockMap m = bm[blockIdx.x];
+  const CfgDev& c = cfgs[m.cfg];
   const FireState* fs = fstate(c);
   if (fs->status) return;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = (int64_t)m.blk * blockDim.x + threadIdx.x;
   if (i >= (int64_t)c.d * c.N) return;
   dd F = dd_make(c.F_hi[i], c.F_lo[i]);
   dd v = fs->zero_v ? dd_make(0.0) : dd_add(dd_mul_d(dd_make(c.v_hi[i], c.v_lo[i]), fs->cv), dd_mul_d(F, fs->cf));
@@ -174,12 +177,13 @@ __global__ void k_fire_accept(const CfgDev* __restrict__ cfgs, const int* __rest
 }
 
 // Undo of a rejected step.  Runs whatever the status, so the state the host reads is the accepted one; a
-// repeated undo restores the same saved copy again.  Grid (coordinate blocks, members).
-__global__ void k_fire_restore(const CfgDev* __restrict__ cfgs, const int* __restrict__ all) {
+// repeated undo restores the same saved copy again.  Block map: d N / 64 blocks per member.
+__global__ void k_fire_restore(const CfgDev* __restrict__ cfgs, const BlockMap* __restrict__ bm) {
   grid_dep_wait();
-  const CfgDev& c = cfgs[all[blockIdx.y]];
+  const BlockMap m = bm[blockIdx.x];
+  const CfgDev& c = cfgs[m.cfg];
   if (!fstate(c)->rejected_now) return;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t i = (int64_t)m.blk * blockDim.x + threadIdx.x;
   if (i >= (int64_t)c.d * c.N) return;
   c.s_hi[i] = c.bs_hi[i];
   c.s_lo[i] = c.bs_lo[i];
@@ -344,13 +348,12 @@ cudaError_t fire_step_engine(const Engine* e, cudaStream_t st, Prof* prof) {
   const CfgDev* cfgs = e->view[0].cfgs;
   // element-wise kernels in 64-thread blocks, so that one configuration spreads over every SM (their dd
   // arithmetic runs on the FP64 pipe, a few lanes per SM on this part)
-  const unsigned gm = (unsigned)std::max<int64_t>(1, (e->maxND_all + 63) / 64);
   const unsigned gt = (unsigned)((e->nall + 127) / 128);
   prof_begin(prof, st, kKFire);
-  cudaError_t le = launch_pdl(k_fire_dots, dim3((unsigned)std::max(1, e->max_nb_fire), (unsigned)e->nall), dim3(kFireThreads), 0,
-                              st, cfgs, e->all);
+  if (e->nbm_dots == 0 || e->nbm_nd == 0) return cudaErrorInvalidValue;  // members without minimiser buffers
+  cudaError_t le = launch_pdl(k_fire_dots, dim3((unsigned)e->nbm_dots), dim3(kFireThreads), 0, st, cfgs, e->bm_dots);
   if (le == cudaSuccess) le = launch_pdl(k_fire_ctrl, dim3((unsigned)e->nall), dim3(32), 0, st, cfgs, e->all, e->nall);
-  if (le == cudaSuccess) le = launch_pdl(k_fire_move, dim3(gm, (unsigned)e->nall), dim3(64), 0, st, cfgs, e->all);
+  if (le == cudaSuccess) le = launch_pdl(k_fire_move, dim3((unsigned)e->nbm_nd), dim3(64), 0, st, cfgs, e->bm_nd);
   if (le != cudaSuccess) return le;
   prof_end(prof, st);
   for (int p = 0; p < 3; p++) {
@@ -360,7 +363,7 @@ cudaError_t fire_step_engine(const Engine* e, cudaStream_t st, Prof* prof) {
   }
   prof_begin(prof, st, kKFire);
   le = launch_pdl(k_fire_accept, dim3(gt), dim3(128), 0, st, cfgs, e->all, e->nall);
-  if (le == cudaSuccess) le = launch_pdl(k_fire_restore, dim3(gm, (unsigned)e->nall), dim3(64), 0, st, cfgs, e->all);
+  if (le == cudaSuccess) le = launch_pdl(k_fire_restore, dim3((unsigned)e->nbm_nd), dim3(64), 0, st, cfgs, e->bm_nd);
   if (le != cudaSuccess) return le;
   prof_end(prof, st);
   return cudaGetLastError();

@@ -105,6 +105,12 @@ struct CfgDev {
   const int* run;  // status word that turns this configuration's kernels into no-ops when non-zero, or null
 };
 
+// compact launch grid over several configurations: block b of a launch works on block blk of configuration cfg
+// (only the blocks each configuration needs are launched)
+struct BlockMap {
+  int32_t cfg, blk;
+};
+
 // work items of the persistent kernels and of the twiddle kernel
 struct TwItem {
   int32_t cfg, pad;
@@ -146,6 +152,10 @@ struct EngineView {
   int64_t tc_max_grid = 0;  // largest (R1 + 1) nP of the members
   size_t tc_prep_smem = 0;  // largest preparation shared memory of the members
   int64_t tc_maxND = 0;     // largest (the path's axes) x N of the members (d = 1 runs on two lifted axes)
+  // block maps of the tensor-core members' light kernels: tables (128 threads over the path's axes x N),
+  // density finish (64 threads), coefficients (128 threads over (R1 + 1) nP), force finish (64 threads over d N)
+  const BlockMap *tc_bm_tab = nullptr, *tc_bm_fin = nullptr, *tc_bm_coef = nullptr, *tc_bm_ff = nullptr;
+  int ntc_bm_tab = 0, ntc_bm_fin = 0, ntc_bm_coef = 0, ntc_bm_ff = 0;
 };
 
 struct Ctx;
@@ -178,7 +188,7 @@ struct Engine {
   std::vector<int> prec_of;  // current precision per member; -1 = listed under every precision
   bool fire_mode = false;
   std::vector<CfgDev> host_cfgs;
-  DevBuf d_cfgs, d_lists, d_all, d_tw, d_nt, d_f, d_counters, d_tclist, d_tcprep, d_tcdens, d_tcforce;
+  DevBuf d_cfgs, d_lists, d_all, d_tw, d_nt, d_f, d_counters, d_tclist, d_tcprep, d_tcdens, d_tcforce, d_bm;
   EngineView view[3];
   std::vector<int> h_lists;
   std::vector<TwItem> h_tw;
@@ -188,6 +198,10 @@ struct Engine {
   int nall = 0;
   int64_t maxND_all = 0;
   int max_nb_fire = 0;
+  // block maps of the minimiser's kernels: dot products (nb_fire blocks of 256 per member), element-wise
+  // updates (64 threads over d N)
+  const BlockMap *bm_dots = nullptr, *bm_nd = nullptr;
+  int nbm_dots = 0, nbm_nd = 0;
 };
 
 // tile plan and buffers of the tensor-core path of one configuration (tc.cu)
@@ -304,6 +318,7 @@ cudaError_t fire_stage_init_engine(const Engine* e, const std::vector<int>& idx,
 enum { kScPhiHi = 0, kScPhiLo, kScSmaxHi, kScSmaxLo, kScCmax, kScScaleExp, kScA2MaxHi, kScA2MaxLo, kScCount = 16 };
 
 // tc.cu (tensor-core fixed-point path, d = 1, 2, 3)
+int64_t tc_coef_blocks(const Ctx& c);  // blocks (128 threads) of the coefficient kernel
 bool tc_eligible(const Ctx& c);
 int tc_finish_blocks(const Ctx& c);  // blocks of the density finish kernel (its reduction partials)
 cudaError_t tc_setup(Ctx* c);

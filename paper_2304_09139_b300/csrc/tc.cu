@@ -299,12 +299,13 @@ __device__ __forceinline__ void qent_out(const qent& z, uint4& yre, uint4& yim, 
 // Thread per (particle, axis): the tables T[k] = e^{2 pi i k s} (k < 8) and A[b] = e^{2 pi i 8 b s}
 // (b <= Rax / 8) as first-quadrant phasors, from exact-phase values of e^{2 pi i s} and e^{2 pi i 8 s} and
 // chains of multiplies (each product at most 8 units of 2^-126 low; about 17 in the longest chain).
-// Grid (particle blocks, tensor-core members); layout tc_tab[(axis N + j) tc_ntab + (k | 8 + b)].
-__global__ void __launch_bounds__(128) k_tc_tables(const CfgDev* __restrict__ cfgs, const int* __restrict__ list) {
+// Block map over the tensor-core members; layout tc_tab[(axis N + j) tc_ntab + (k | 8 + b)].
+__global__ void __launch_bounds__(128) k_tc_tables(const CfgDev* __restrict__ cfgs, const BlockMap* __restrict__ bm) {
   grid_dep_wait();
-  const CfgDev& c = cfgs[list[blockIdx.y]];
+  const BlockMap m = bm[blockIdx.x];
+  const CfgDev& c = cfgs[m.cfg];
   if (stopped(c)) return;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t idx = (int64_t)m.blk * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)c.tc_d * c.N) return;
   const int axis = (int)(idx / c.N);
   const int64_t j = idx - (int64_t)axis * c.N;
@@ -688,18 +689,19 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
 
 // ------------------------------------------------------------------------------------------------ finish
 
-// grid (finish blocks, tensor-core members), 64 threads, thread per (n1, p), n1 fastest: n~(n1, p) and
+// block map over the tensor-core members (tc_nblk blocks each), 64 threads, thread per (n1, p), n1 fastest: n~(n1, p) and
 // n~(n1, -p) from the four real products of the tile accumulator (which it clears for the next evaluation), as
 // exact Q34.126 values (for the force coefficients) and as dd (C, S), with the block's Phi / max |n~|^2 /
 // max |C|, |S| partials; the last block to finish reduces the partials to Phi, S_max and the scale.
 __global__ void __launch_bounds__(kFinThreads) k_tc_dens_finish(const CfgDev* __restrict__ cfgs,
-                                                                const int* __restrict__ list) {
+                                                                const BlockMap* __restrict__ bm) {
   grid_dep_wait();
-  const CfgDev& c = cfgs[list[blockIdx.y]];
-  if (stopped(c) || (int)blockIdx.x >= c.tc_nblk) return;  // uniform per block
+  const BlockMap m = bm[blockIdx.x];
+  const CfgDev& c = cfgs[m.cfg];
+  if (stopped(c)) return;  // uniform per block
   RedPart v = {0, 0, 0, 0, 0, 0, 0, 0};
   const int W1 = c.tc_R1 + 1;
-  const int64_t idx = (int64_t)blockIdx.x * kFinThreads + threadIdx.x;
+  const int64_t idx = (int64_t)m.blk * kFinThreads + threadIdx.x;
   if (idx < (int64_t)W1 * c.tc_nP) {
     const int n1 = (int)(idx % W1), p = (int)(idx / W1);
     const int kp = c.tc_em[idx * 2 + 0], km = c.tc_em[idx * 2 + 1];  // em is [p][n1][2]
@@ -763,7 +765,7 @@ __global__ void __launch_bounds__(kFinThreads) k_tc_dens_finish(const CfgDev* __
     RedPart a = sh[0];
 #pragma unroll
     for (int w = 1; w < kFinThreads / 32; w++) red_combine(a, sh[w]);
-    reinterpret_cast<RedPart*>(c.blk)[blockIdx.x] = a;
+    reinterpret_cast<RedPart*>(c.blk)[m.blk] = a;
     // the block that finishes last reduces every block's partial (tc_err[1] counts finished blocks)
     __threadfence();
     last = atomicAdd(c.tc_err + 1, 1) == c.tc_nblk - 1;
@@ -776,14 +778,15 @@ __global__ void __launch_bounds__(kFinThreads) k_tc_dens_finish(const CfgDev* __
   }
 }
 
-// grid (coordinate blocks, tensor-core members), 64 threads: F[a][j] from the force limbs (which it clears),
+// block map over the tensor-core members (d N / 64 blocks each), 64 threads: F[a][j] from the force limbs (which it clears),
 // times 4 pi / L and the power-of-two scale of the coefficients
 __global__ void __launch_bounds__(kFinThreads) k_tc_force_finish(const CfgDev* __restrict__ cfgs,
-                                                                 const int* __restrict__ list) {
+                                                                 const BlockMap* __restrict__ bm) {
   grid_dep_wait();
-  const CfgDev& c = cfgs[list[blockIdx.y]];
+  const BlockMap m = bm[blockIdx.x];
+  const CfgDev& c = cfgs[m.cfg];
   if (stopped(c)) return;
-  const int64_t i = (int64_t)blockIdx.x * kFinThreads + threadIdx.x;  // over [a][j]
+  const int64_t i = (int64_t)m.blk * kFinThreads + threadIdx.x;  // over [a][j]
   if (i >= (int64_t)c.d * c.N) return;
   const int a = (int)(i / c.N);
   const int64_t j = i - (int64_t)a * c.N;
@@ -818,14 +821,15 @@ __global__ void __launch_bounds__(kFinThreads) k_tc_force_finish(const CfgDev* _
   c.F_lo[i] = f.lo * sc;
 }
 
-// grid ((R1 + 1) nP / 128 blocks, tensor-core members), thread per (n1, p), p fastest: the force GEMM's
+// block map over the tensor-core members ((R1 + 1) nP / 128 blocks each), thread per (n1, p), p fastest: the force GEMM's
 // coefficient digits of every axis
-__global__ void k_tc_coef(const CfgDev* __restrict__ cfgs, const int* __restrict__ list) {
+__global__ void k_tc_coef(const CfgDev* __restrict__ cfgs, const BlockMap* __restrict__ bm) {
   grid_dep_wait();
-  const CfgDev& c = cfgs[list[blockIdx.y]];
+  const BlockMap m = bm[blockIdx.x];
+  const CfgDev& c = cfgs[m.cfg];
   if (stopped(c)) return;
   const int W1 = c.tc_R1 + 1;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t idx = (int64_t)m.blk * blockDim.x + threadIdx.x;
   if (idx >= (int64_t)W1 * c.tc_nP) return;
   const int n1 = (int)(idx / c.tc_nP), p = (int)(idx % c.tc_nP);
   const int32_t* em = c.tc_em + ((int64_t)p * W1 + n1) * 2;
@@ -888,6 +892,11 @@ static cudaError_t tc_dev_alloc(DevBuf* b, size_t bytes, cudaStream_t st) {
 }
 
 bool tc_eligible(const Ctx& c) { return c.d >= 1 && c.d <= 3 && c.N >= 1 && c.M >= 1; }
+
+int64_t tc_coef_blocks(const Ctx& c) {
+  if (!c.tc.on) return 0;
+  return ((int64_t)(c.tc.R1 + 1) * c.tc.nP + 127) / 128;
+}
 
 int tc_finish_blocks(const Ctx& c) {
   if (!c.tc.on) return 0;
@@ -1221,8 +1230,7 @@ size_t tc_gemm_smem() { return kGemmSmem; }
 cudaError_t tc_launch_force_finish(const EngineView& v, cudaStream_t st, Prof* prof) {
   if (v.ntc_list == 0) return cudaSuccess;
   prof_begin(prof, st, kKTcFinish);
-  const dim3 g((unsigned)std::max<int64_t>(1, (v.maxND + kFinThreads - 1) / kFinThreads), (unsigned)v.ntc_list);
-  cudaError_t le = launch_pdl(k_tc_force_finish, g, dim3(kFinThreads), 0, st, v.cfgs, v.tc_list);
+  cudaError_t le = launch_pdl(k_tc_force_finish, dim3((unsigned)v.ntc_bm_ff), dim3(kFinThreads), 0, st, v.cfgs, v.tc_bm_ff);
   if (le != cudaSuccess) return le;
   prof_end(prof, st);
   return cudaGetLastError();
@@ -1231,8 +1239,7 @@ cudaError_t tc_launch_force_finish(const EngineView& v, cudaStream_t st, Prof* p
 cudaError_t tc_launch_density(const EngineView& v, cudaStream_t st, Prof* prof) {
   if (v.ntc_list == 0) return cudaSuccess;
   prof_begin(prof, st, kKTcPrep);
-  cudaError_t le = launch_pdl(k_tc_tables, dim3((unsigned)std::max<int64_t>(1, (v.tc_maxND + 127) / 128), (unsigned)v.ntc_list),
-                              dim3(128), 0, st, v.cfgs, v.tc_list);
+  cudaError_t le = launch_pdl(k_tc_tables, dim3((unsigned)v.ntc_bm_tab), dim3(128), 0, st, v.cfgs, v.tc_bm_tab);
   if (le == cudaSuccess)
     le = launch_pdl(k_tc_prep, dim3((unsigned)v.ntc_prep), dim3(kPrepThreads), v.tc_prep_smem, st, v.cfgs, v.tc_prep);
   if (le != cudaSuccess) return le;
@@ -1243,8 +1250,7 @@ cudaError_t tc_launch_density(const EngineView& v, cudaStream_t st, Prof* prof) 
   if (le != cudaSuccess) return le;
   prof_end(prof, st);
   prof_begin(prof, st, kKTcFinish);
-  const dim3 g((unsigned)std::max<int64_t>(1, (v.tc_max_grid + kFinThreads - 1) / kFinThreads), (unsigned)v.ntc_list);
-  le = launch_pdl(k_tc_dens_finish, g, dim3(kFinThreads), 0, st, v.cfgs, v.tc_list);
+  le = launch_pdl(k_tc_dens_finish, dim3((unsigned)v.ntc_bm_fin), dim3(kFinThreads), 0, st, v.cfgs, v.tc_bm_fin);
   if (le != cudaSuccess) return le;
   prof_end(prof, st);
   return cudaGetLastError();
@@ -1253,8 +1259,7 @@ cudaError_t tc_launch_density(const EngineView& v, cudaStream_t st, Prof* prof) 
 cudaError_t tc_launch_force(const EngineView& v, cudaStream_t st, Prof* prof) {
   if (v.ntc_list == 0) return cudaSuccess;
   prof_begin(prof, st, kKTcCoef);
-  const dim3 g((unsigned)std::max<int64_t>(1, (v.tc_max_grid + 127) / 128), (unsigned)v.ntc_list);
-  cudaError_t le = launch_pdl(k_tc_coef, g, dim3(128), 0, st, v.cfgs, v.tc_list);
+  cudaError_t le = launch_pdl(k_tc_coef, dim3((unsigned)v.ntc_bm_coef), dim3(128), 0, st, v.cfgs, v.tc_bm_coef);
   if (le != cudaSuccess) return le;
   prof_end(prof, st);
   prof_begin(prof, st, kKTcForce);
