@@ -311,7 +311,8 @@ ssh_status ssh_server_get_stats(ssh_server* server, ssh_server_stats* out);
  * Kernel ids: 0 twiddle tables, 1 collective density n~, 2 density reduction, 3 Phi/S_max finalise,
  * 4 force coefficients, 5 force, 6 force reduction, 7 minimiser kernels of a FIRE step (two event pairs
  * per step: update, acceptance); tensor-core fixed point (SSH_FX_TENSOR): 8 digit preparation, 9 density
- * GEMM, 10 density finish, 11 force coefficient digits, 12 force GEMM.  n entries are written (at most 16).
+ * GEMM, 10 density and force finish, 11 force coefficient digits, 12 force GEMM, 13 per-particle power
+ * tables.  n entries are written (at most 16).
  */
 ssh_status ssh_prof_enable(ssh_ctx* ctx, int on);
 ssh_status ssh_prof_read(ssh_ctx* ctx, int n, double* ms, int64_t* launches);

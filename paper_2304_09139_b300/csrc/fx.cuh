@@ -387,12 +387,15 @@ __device__ __forceinline__ void q160_add_units(q160& acc, uint32_t k) {
 }
 
 // z * b for first-quadrant phasors, renormalised to the first quadrant: three unsigned products give
-// re = c1 c2 - s1 s2 and im = (c1 + s1)(c2 + s2) - c1 c2 - s1 s2 >= 0; if re < 0 the result is rotated by -i
+// re = c1 c2 - s1 s2 and im = (c1 + s1)(c2 + s2) - c1 c2 - s1 s2 >= 0 (clamped at 0); if re < 0 the result is rotated by -i
 // (c, s) = (im, -re) and the quadrant advances.  The Q2.126 results are doubled back to Q1.127.
 __device__ __forceinline__ qent qmul(const qent& z, const qent& b) {
   const q128 p1 = umulhi(z.c, b.c), p2 = umulhi(z.s, b.s), p3 = umulhi(z.cs, b.cs);
   const q128 re = q128_sub(p1, p2);
-  const q128 im = q128_sub(q128_sub(p3, p1), p2);
+  q128 im = q128_sub(q128_sub(p3, p1), p2);
+  // im = c1 s2 + s1 c2 >= 0 exactly; each truncated top half is up to 8 units low, so on the real axis (both
+  // factors inexact) the computed value can fall a few units below 0 and would wrap: it is 0 within its error
+  if ((int32_t)im.w[3] < 0) im = q128_zero();
   uint32_t q = (z.cs.w[0] + b.cs.w[0]) & 3u;
   const bool neg = (int32_t)re.w[3] < 0;
   const q128 nre = q128_neg(re);

@@ -44,7 +44,7 @@ struct Launch {          // per-precision launch shape of the two hot kernels
 // kernel ids for the event profiler (ssh_prof_*)
 enum KernelId {
   kKTwiddle = 0, kKNtilde, kKNtReduce, kKFinalize, kKCoef, kKForce, kKFReduce, kKFire,
-  kKTcPrep, kKTcDens, kKTcFinish, kKTcCoef, kKTcForce, kKCount = 16
+  kKTcPrep, kKTcDens, kKTcFinish, kKTcCoef, kKTcForce, kKTcTables, kKCount = 16
 };
 
 struct ProfRec {

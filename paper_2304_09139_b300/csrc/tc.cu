@@ -297,8 +297,9 @@ __device__ __forceinline__ void qent_out(const qent& z, uint4& yre, uint4& yim, 
 }  // namespace
 
 // Thread per (particle, axis): the tables T[k] = e^{2 pi i k s} (k < 8) and A[b] = e^{2 pi i 8 b s}
-// (b <= Rax / 8) as first-quadrant phasors, from exact-phase values of e^{2 pi i s} and e^{2 pi i 8 s} and
-// chains of multiplies (each product at most 8 units of 2^-126 low; about 17 in the longest chain).
+// (b <= Rax / 8) as first-quadrant phasors, from the exact-phase value of e^{2 pi i s} and chains of multiplies
+// (e^{2 pi i 8 s} = T[4]^2; each product at most 8 units of 2^-126 low, the error of a power grows linearly in
+// its exponent: far below the 2^-104 digits).
 // Block map over the tensor-core members; layout tc_tab[(axis N + j) tc_ntab + (k | 8 + b)].
 __global__ void __launch_bounds__(128) k_tc_tables(const CfgDev* __restrict__ cfgs, const BlockMap* __restrict__ bm) {
   grid_dep_wait();
@@ -322,13 +323,14 @@ __global__ void __launch_bounds__(128) k_tc_tables(const CfgDev* __restrict__ cf
   one.s = q128_zero();
   one.cs = one.c;
   const qent e1 = to_quadrant(phasor_turn(u));
-  qent t = one;
+  qent t = one, e4 = one;
 #pragma unroll 1
   for (int k = 0; k < kPrepLow; k++) {
     tab[k] = t;
+    if (k == kPrepLow / 2) e4 = t;
     if (k + 1 < kPrepLow) t = qmul(t, e1);
   }
-  const qent e8 = to_quadrant(phasor_turn(turn_times(u, kPrepLow)));
+  const qent e8 = qmul(e4, e4);  // e^{2 pi i 8 s} = T[4]^2: one product instead of a second exact-phase evaluation
   qent a = one;
 #pragma unroll 1
   for (int b = 0; b < nA; b++) {
@@ -1238,10 +1240,12 @@ cudaError_t tc_launch_force_finish(const EngineView& v, cudaStream_t st, Prof* p
 
 cudaError_t tc_launch_density(const EngineView& v, cudaStream_t st, Prof* prof) {
   if (v.ntc_list == 0) return cudaSuccess;
-  prof_begin(prof, st, kKTcPrep);
+  prof_begin(prof, st, kKTcTables);
   cudaError_t le = launch_pdl(k_tc_tables, dim3((unsigned)v.ntc_bm_tab), dim3(128), 0, st, v.cfgs, v.tc_bm_tab);
-  if (le == cudaSuccess)
-    le = launch_pdl(k_tc_prep, dim3((unsigned)v.ntc_prep), dim3(kPrepThreads), v.tc_prep_smem, st, v.cfgs, v.tc_prep);
+  if (le != cudaSuccess) return le;
+  prof_end(prof, st);
+  prof_begin(prof, st, kKTcPrep);
+  le = launch_pdl(k_tc_prep, dim3((unsigned)v.ntc_prep), dim3(kPrepThreads), v.tc_prep_smem, st, v.cfgs, v.tc_prep);
   if (le != cudaSuccess) return le;
   prof_end(prof, st);
   prof_begin(prof, st, kKTcDens);

@@ -16,7 +16,7 @@ FP64, DD, FX = 0, 1, 2
 FX_AUTO, FX_INTEGER, FX_TENSOR = 0, 1, 2   # ssh_opts.fx_impl
 PREC_NAMES = {FP64: "fp64", DD: "dd", FX: "fx"}
 KERNELS = ["twiddle", "ntilde", "nt_reduce", "finalize", "coef", "force", "f_reduce", "fire",
-           "tc_prep", "tc_dens", "tc_finish", "tc_coef", "tc_force"]
+           "tc_prep", "tc_dens", "tc_finish", "tc_coef", "tc_force", "tc_tables"]
 
 _STATUS = {0: "SSH_OK", 1: "SSH_EINVAL", 2: "SSH_ENOMEM", 3: "SSH_ECUDA", 4: "SSH_ENAN", 5: "SSH_ENOTCONV",
            6: "SSH_ETIMEOUT", 7: "SSH_EBUSY", 8: "SSH_ENOTFOUND"}

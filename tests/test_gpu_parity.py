@@ -174,14 +174,14 @@ def test_parity_large_d3_sampled(built, oracle_mod):
         assert np.all(np.abs(tot) <= N * scale * 4), (tot, scale)
 
 
-def test_lattice_closed_form_on_gpu(built):
-    """N = q^d lattice points: n~(k) = 0 unless every n_a = 0 (mod q), where it is N (geometric sums)."""
-    from fractions import Fraction
-    q, d = 16, 2   # s = m / 16 is exact in binary
-    g = np.stack(np.meshgrid(np.arange(q) / q, np.arange(q) / q, indexing="ij"), -1).reshape(-1, d)
+@pytest.mark.parametrize("d,q,R", [(1, 64, 200.5), (2, 16, 20.5), (3, 8, 10.5)])
+def test_lattice_closed_form_on_gpu(built, d, q, R):
+    """N = q^d lattice points: n~(k) = 0 unless every n_a = 0 (mod q), where it is N (geometric sums).  Lattice
+    phases sit on the axes, where products of rounded phasors are most delicate."""
+    g = np.stack(np.meshgrid(*([np.arange(q) / q] * d), indexing="ij"), -1).reshape(-1, d)  # m / q: exact in binary
     N = len(g)
     for impl, precs in impls(d):
-        ctx = ssh.Context(d, N, 1.0, K=2 * math.pi * 20.5, fx_impl=impl)
+        ctx = ssh.Context(d, N, 1.0, K=2 * math.pi * R, fx_impl=impl)
         n = ctx.kset()
         ctx.set_positions_frac(g)
         mult = np.all(n % q == 0, axis=1)
