@@ -4,6 +4,7 @@ Metric: (k, particle) pairs per second per Phi+grad, pairs = M * N (one of the t
 Eqs. ntilde / force; the paper counts the work of one step as two such sums of M N terms).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fx|dd|fp64] [--impl ours|reference]
+                  [--workload d2-n10000|d3-n32768]
 
 Default workload: d = 2, N = 10^4 uniform random points (SplitMix64 seed 2) in a periodic square at unit
 density (L = 100), chi = 0.45, so M = 8999.  Inputs are resident in HBM when the timed region starts;
@@ -67,14 +68,17 @@ def _measured_bf16_peak() -> float:
 
 BF16_PEAK = _measured_bf16_peak()
 
-WORKLOAD = dict(d=2, N=10_000, L=100.0, chi=0.45, seed=2)
+# The headline workload (the default) and the d = 3 one, selectable with --workload.
+WORKLOADS = {"d2-n10000": dict(d=2, N=10_000, L=100.0, chi=0.45, seed=2),
+             "d3-n32768": dict(d=3, N=32_768, L=32.0, chi=0.40, seed=3)}
+WORKLOAD = WORKLOADS["d2-n10000"]
 
 # DRAM bytes (read + write) per launch from one ncu capture of this workload (profiles/), valid only while
 # the kernel sources hash to the value recorded with them; otherwise the traffic is reported as null.
-NCU_TRAFFIC = {("fx", "force"): ("9a8b45757c86", 35_869_184 + 5_888_000),
-               ("fx", "ntilde"): ("9a8b45757c86", 36_598_272 + 43_264_000),
-               ("fx-tensor", "tc_force"): ("37f79b9f30b3", 75_052_800 + 3_156_480),
-               ("fx-tensor", "tc_dens"): ("37f79b9f30b3", 125_670_656 + 4_787_968)}
+NCU_TRAFFIC = {("d2-n10000", "fx", "force"): ("9a8b45757c86", 35_869_184 + 5_888_000),
+               ("d2-n10000", "fx", "ntilde"): ("9a8b45757c86", 36_598_272 + 43_264_000),
+               ("d2-n10000", "fx-tensor", "tc_force"): ("23287a2950f7", 78_166_272 + 2_166_272),
+               ("d2-n10000", "fx-tensor", "tc_dens"): ("23287a2950f7", 125_670_400 + 4_452_096)}
 
 
 def kernel_source_hash() -> str:
@@ -92,8 +96,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--prec", default="fx", choices=["fx", "dd", "fp64"])
+    ap.add_argument("--workload", default="d2-n10000", choices=sorted(WORKLOADS),
+                    help="the timed configuration: d=2 N=10^4 chi=0.45 (default) or d=3 N=32768 chi=0.40")
     ap.add_argument("--fx-impl", default="auto", choices=["auto", "integer", "tensor"],
-                    help="fixed-point implementation: integer pipes or exact-digit tensor-core GEMMs (d = 2, 3)")
+                    help="fixed-point implementation: integer pipes or exact-digit tensor-core GEMMs (d <= 3)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
@@ -367,7 +373,7 @@ def run_reference(args):
     rank, world, local = dist_info()
     if rank != 0:
         return 0
-    w = WORKLOAD
+    w = WORKLOADS[args.workload]
     times, pairs = [], None
     for i in range(args.warmup + args.steps):
         rate, Ms, cores = cpu_sample(w["N"], w["d"], w["L"], w["chi"], w["seed"])
@@ -494,7 +500,7 @@ def main():
     torch.cuda.set_device(dev)
     _build.build()
     prec = {"fx": ssh.FX, "dd": ssh.DD, "fp64": ssh.FP64}[args.prec]
-    w = WORKLOAD
+    w = WORKLOADS[args.workload]
     fx_impl = {"auto": ssh.FX_AUTO, "integer": ssh.FX_INTEGER, "tensor": ssh.FX_TENSOR}[args.fx_impl]
     ctx = ssh.Context(w["d"], w["N"], w["L"], chi=w["chi"], device=dev, fx_impl=fx_impl)
     stream = torch.cuda.Stream(dev)          # a real (non-legacy) stream shared by torch and the library
@@ -584,7 +590,7 @@ def main():
                                 f"unit counts x max clock: {'64 IMAD' if what == 'IMAD' else '2 FP64 FMA'} "
                                 f"lanes/SM/clk x 148 SMs x 2032 MHz"),
                 "per_kernel_ms": {k: v[0] / v[1] for k, v in prof.items()}}
-        tr = NCU_TRAFFIC.get(("fx-tensor" if tensor else args.prec, dom_name))
+        tr = NCU_TRAFFIC.get((args.workload, "fx-tensor" if tensor else args.prec, dom_name))
         if tr and tr[0] == kernel_source_hash():
             roof["traffic"] = tr[1]
 
