@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
 #include <numeric>
 
 #include "ssh_internal.h"
@@ -157,18 +158,30 @@ cudaError_t engine_build(Engine* e, const std::vector<Ctx*>& members, const std:
   int64_t tc_grid = 0;
   size_t tc_smem = 0;
   int64_t tc_nd = 0;
+  int64_t tc_steps = 0;  // density K-steps of every tensor-core member: each gets its share of the SMs
+  for (int i : lists[SSH_FX])
+    if (members[i]->tc.on) tc_steps += tc_density_steps(members[i]);
   for (int i : lists[SSH_FX])
     if (members[i]->tc.on) {
       tcl.push_back(i);
-      tc_items(members[i], i, tcp, tcd, tcf);
+      const int64_t share = (int64_t)((double)e->sm_count * (double)tc_density_steps(members[i]) / (double)std::max<int64_t>(1, tc_steps));
+      tc_items(members[i], i, share, tcp, tcd, tcf);
       tc_grid = std::max<int64_t>(tc_grid, (int64_t)(members[i]->tc.R1 + 1) * members[i]->tc.nP);
       tc_smem = std::max(tc_smem, members[i]->tc.prep_smem);
       tc_nd = std::max<int64_t>(tc_nd, (int64_t)members[i]->tc.d * members[i]->N);
     }
-  // largest items first over all members: the persistent GEMM assigns them round-robin
+  // largest first over all members (the persistent GEMM takes items from a queue in list order): density items
+  // one by one; force items by bundle (the column tiles of one particle tile, kept together so that they share
+  // its digits in L2), bundles by their total K-steps (a stable sort keeps each bundle contiguous and in order)
   auto by_size = [](const TcItem& a, const TcItem& b) { return a.nks > b.nks; };
   std::stable_sort(tcd.begin(), tcd.end(), by_size);
-  std::stable_sort(tcf.begin(), tcf.end(), by_size);
+  {
+    std::map<std::pair<int, int>, int64_t> bundle;
+    for (const TcItem& it : tcf) bundle[{it.cfg, it.a}] += it.nks;
+    std::stable_sort(tcf.begin(), tcf.end(), [&](const TcItem& a, const TcItem& b) {
+      return bundle[{a.cfg, a.a}] > bundle[{b.cfg, b.a}];
+    });
+  }
   cudaError_t err;
   if ((err = up(&e->d_tclist, tcl.data(), sizeof(int) * tcl.size(), st)) != cudaSuccess) return err;
   if ((err = up(&e->d_tcprep, tcp.data(), sizeof(TwItem) * tcp.size(), st)) != cudaSuccess) return err;
@@ -210,7 +223,11 @@ cudaError_t engine_build(Engine* e, const std::vector<Ctx*>& members, const std:
   if ((err = up(&e->d_nt, e->h_nt.data(), sizeof(NtItem) * e->h_nt.size(), st)) != cudaSuccess) return err;
   if ((err = up(&e->d_f, e->h_f.data(), sizeof(FItem) * e->h_f.size(), st)) != cudaSuccess) return err;
   if (!e->d_counters.p) {
-    if ((err = up(&e->d_counters, nullptr, 0, st)) != cudaSuccess) return err;
+    // [0], [1] integer-pipe density and force queues; [2], [3] and [4], [5] tensor-core density and force
+    // queues with their finished-CTA counts (reset by the kernels themselves)
+    e->d_counters.bytes = 64;
+    if ((err = cudaMalloc(&e->d_counters.p, 64)) != cudaSuccess) return err;
+    if ((err = cudaMemsetAsync(e->d_counters.p, 0, 64, st)) != cudaSuccess) return err;
   }
   const CfgDev* dc = (const CfgDev*)e->d_cfgs.p;
   const int* dl = (const int*)e->d_lists.p;

@@ -85,7 +85,7 @@ struct CfgDev {
   double *F_hi, *F_lo;
   dd pref, inv_L;
   // tensor-core fixed-point path (tc.cu); tc = 0 when the configuration uses the integer-pipe kernels
-  int tc, tc_R1, tc_nP, tc_RT, tc_CTd, tc_PT, tc_KSf, tc_CTf, tc_bexp, tc_ksplit, tc_nblk, tc_gs, tc_ts, tc_ntab;
+  int tc, tc_R1, tc_nP, tc_RT, tc_CTd, tc_PT, tc_KSf, tc_CTf, tc_bexp, tc_nblk, tc_gs, tc_ts, tc_ntab;
   int tc_d, tc_lift;   // the path's number of axes (2 or 3); d = 1 on two lifted axes: n = 2^tc_lift n1 + n2
   int tc_Rax[3];       // per axis: powers 0..tc_Rax[a] in the tables
   int64_t tc_KS, tc_NJ, tc_NPg;  // density K-steps; particle groups and row groups of the digit tensor
@@ -217,7 +217,6 @@ struct TcPlan {
   int PT = 0, KSf = 0, CTf = 0;  // force particle tiles, K-steps (16 rows (p, cos/sin)), column tiles (16/d n1, all axes)
   int64_t NJ = 0, NPg = 0;       // digit tensor: particle groups and row groups of 8
   int bexp = 0;                  // 2^bexp > |n_a| (a >= 2): scale of the weighted force coefficients
-  int ksplit = 1;                // K ranges per density tile
   int gs = 0, ts = 0;            // force epilogue scales
   std::vector<int32_t> tiles;    // density tiles in use: rt * CTd + ct
   std::vector<int32_t> tilemap;  // [RT * CTd] -> index into tiles, or -1
@@ -325,7 +324,9 @@ cudaError_t tc_setup(Ctx* c);
 void tc_free(Ctx* c);
 size_t tc_footprint(const Ctx& c);
 void tc_fill_cfgdev(const Ctx* c, CfgDev* g);
-void tc_items(const Ctx* c, int i, std::vector<TwItem>& prep, std::vector<TcItem>& dens, std::vector<TcItem>& force);
+int64_t tc_density_steps(const Ctx* c);  // tiles x K-steps of the density GEMM
+void tc_items(const Ctx* c, int i, int64_t pieces, std::vector<TwItem>& prep, std::vector<TcItem>& dens,
+              std::vector<TcItem>& force);
 cudaError_t tc_launch_density(const EngineView& v, cudaStream_t st, Prof* prof);
 cudaError_t tc_launch_force(const EngineView& v, cudaStream_t st, Prof* prof);
 cudaError_t tc_launch_force_finish(const EngineView& v, cudaStream_t st, Prof* prof);

@@ -65,6 +65,7 @@ constexpr int kGemmThreads = 64 + 32 * kEpiWarps;  // producer warp, MMA warp, e
 constexpr long long kWaitLimit = 2000000000LL;     // clock cycles (about one second) for any single wait
 constexpr size_t kGemmSmem = (size_t)kStages * kStageBytes + 128;  // + alignment slack of the stages
 constexpr int kFinThreads = 64;
+constexpr int kRing = 8;                           // item indices in flight between the producer and consumers
 
 __device__ __forceinline__ bool stopped(const CfgDev& c) { return c.run && *c.run; }
 
@@ -449,7 +450,10 @@ __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restri
 
 // ------------------------------------------------------------------------------------------------ k_tc_gemm
 
-// Persistent: CTA b takes items b, b + gridDim.x, ...  Density items: A = rows (p, cos / sin) of row tile it.a
+// Persistent, with a dynamic queue: the producer thread claims items in list order (queue[0], an atomic
+// counter) and passes each index to the MMA thread and the epilogue warps through a ring in shared memory, so a
+// CTA that finishes early takes the next item (queue[1] counts finished CTAs; the last one resets both).
+// Density items: A = rows (p, cos / sin) of row tile it.a
 // (tensor-map box, K-major), B = column tile it.b of the a_j(n1) slices, K-steps [ks0, ks0 + nks) of 16
 // particles; the epilogue adds the three int64 level groups of every output into tile accumulator it.slot.
 // Force items: A = particle tile it.a (tensor-map box, MN-major), B = column tile it.b (16 / d values of n1, all
@@ -458,12 +462,15 @@ __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restri
 // while the epilogue finishes the previous item (the accumulator is released as soon as its last level has
 // been read).
 __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __restrict__ cfgs,
-                                                              const TcItem* __restrict__ items, int n_items) {
+                                                              const TcItem* __restrict__ items, int n_items,
+                                                              int* __restrict__ queue) {
   grid_dep_wait();
   extern __shared__ __align__(128) uint8_t smem_raw[];
   // tensor-map destinations must be 128-byte aligned
   uint8_t* smem = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
   __shared__ uint64_t bar_full[kStages], bar_empty[kStages], bar_acc_full, bar_acc_empty, bar_drain;
+  __shared__ uint64_t bar_item_full[kRing], bar_item_empty[kRing];
+  __shared__ int item_ring[kRing];
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -471,6 +478,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
     for (int s = 0; s < kStages; s++) {
       mbar_init(&bar_full[s], 1);
       mbar_init(&bar_empty[s], 1);
+    }
+    for (int r = 0; r < kRing; r++) {
+      mbar_init(&bar_item_full[r], 1);
+      mbar_init(&bar_item_empty[r], 1 + kEpiWarps);  // the MMA thread and every epilogue warp have read it
     }
     mbar_init(&bar_acc_full, 1);
     mbar_init(&bar_acc_empty, kEpiWarps);
@@ -490,7 +501,20 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
     if (lane == 0) {
       long long gs = 0;  // K-steps issued so far (all items)
       bool stop = false;
-      for (int item = blockIdx.x; item < n_items && !stop; item += gridDim.x) {
+      int pre = -1;      // the next claim, made while the previous item's last K-step is copied (-1: none yet)
+      for (long long n = 0; !stop; n++) {
+        // claim the next item and publish it to the MMA thread and the epilogue warps
+        const int r = (int)(n % kRing);
+        const long long use = n / kRing;
+        if (use > 0 && !mbar_wait(&bar_item_empty[r], (uint32_t)((use - 1) & 1), kWaitLimit, abort_flag)) {
+          *abort_flag = 1;
+          break;
+        }
+        const int item = pre >= 0 ? pre : atomicAdd(queue, 1);
+        pre = -1;
+        item_ring[r] = item < n_items ? item : -1;
+        mbar_arrive(&bar_item_full[r]);
+        if (item >= n_items) break;
         const TcItem it = items[item];
         const CfgDev& c = cfgs[it.cfg];
         if (stopped(c)) continue;
@@ -507,6 +531,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
             stop = true;
             break;
           }
+          if (ks == it.nks - 1) pre = atomicAdd(queue, 1);  // its latency overlaps the last copies and MMAs
           uint8_t* dst = smem + (size_t)s * kStageBytes;
           const int kg = it.ks0 + ks;
           mbar_expect_tx(&bar_full[s], kStageBytes);
@@ -528,7 +553,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
     if (lane == 0) {
       long long gs = 0, gc = 0;  // K-steps and chunks consumed so far (all items)
       bool stop = false;
-      for (int item = blockIdx.x; item < n_items && !stop; item += gridDim.x) {
+      for (long long n = 0; !stop; n++) {
+        const int r = (int)(n % kRing);
+        if (!mbar_wait(&bar_item_full[r], (uint32_t)((n / kRing) & 1), kWaitLimit, abort_flag)) {
+          *abort_flag = 1;
+          break;
+        }
+        const int item = item_ring[r];
+        mbar_arrive(&bar_item_empty[r]);
+        if (item < 0) break;
         const TcItem it = items[item];
         const CfgDev& c = cfgs[it.cfg];
         if (stopped(c)) continue;
@@ -584,7 +617,17 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
     const uint32_t trow = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(kEpiCols * hq);
     long long gc = 0;  // chunks read (all items of this CTA)
     bool stop = false;
-    for (int item = blockIdx.x; item < n_items && !stop; item += gridDim.x) {
+    for (long long n = 0; !stop; n++) {
+      const int r = (int)(n % kRing);
+      const bool have = mbar_wait(&bar_item_full[r], (uint32_t)((n / kRing) & 1), kWaitLimit, abort_flag);
+      if (!__all_sync(0xffffffffu, have)) {
+        *abort_flag = 1;
+        break;
+      }
+      const int item = item_ring[r];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar_item_empty[r]);
+      if (item < 0) break;
       const TcItem it = items[item];
       const CfgDev& c = cfgs[it.cfg];
       if (stopped(c)) continue;
@@ -686,6 +729,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tbase, kTmemCols);
+  }
+  // the last CTA out resets the queue for the next launch (every CTA's producer has made its last claim)
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(queue + 1, 1) == (int)gridDim.x - 1) {
+      queue[0] = 0;
+      queue[1] = 0;
+      __threadfence();
+    }
   }
 }
 
@@ -1085,11 +1137,7 @@ cudaError_t tc_setup(Ctx* c) {
   t.ks_ct.resize(t.CTf);
   for (int ct = 0; ct < t.CTf; ct++) t.ks_ct[ct] = pmax_ct[ct] < 0 ? 0 : (2 * (pmax_ct[ct] + 1) + kStepK - 1) / kStepK;
   const int nt = (int)t.tiles.size();
-  const int64_t max_split = std::max<int64_t>(1, t.KS / kChunkSteps);
-  // one CTA per SM: as many K ranges per tile as fit in a single wave
-  t.ksplit = (int)std::max<int64_t>(1, std::min<int64_t>(max_split, c->sm_count / std::max(1, nt)));
-  // each K range holds at most 1024 read-outs, so the int64 level groups (below 2^52 per read-out) cannot overflow
-  t.ksplit = (int)std::max<int64_t>(t.ksplit, (t.KS + 1024 * kChunkSteps - 1) / (1024 * kChunkSteps));
+
   t.ntab = kPrepLow + std::max(R1, std::max(R2, R3)) / kPrepLow + 1;
   cudaStream_t st = c->stream;
   cudaError_t e;
@@ -1174,7 +1222,6 @@ void tc_fill_cfgdev(const Ctx* c, CfgDev* g) {
   g->tc_KSf = t.KSf;
   g->tc_CTf = t.CTf;
   g->tc_bexp = t.bexp;
-  g->tc_ksplit = t.ksplit;
   g->tc_KS = t.KS;
   g->tc_NJ = t.NJ;
   g->tc_NPg = t.NPg;
@@ -1198,7 +1245,12 @@ void tc_fill_cfgdev(const Ctx* c, CfgDev* g) {
 }
 
 // work items of one member (engine member index i)
-void tc_items(const Ctx* c, int i, std::vector<TwItem>& prep, std::vector<TcItem>& dens, std::vector<TcItem>& force) {
+int64_t tc_density_steps(const Ctx* c) { return c->tc.on ? (int64_t)c->tc.tiles.size() * c->tc.KS : 0; }
+
+// work items of one member (engine member index i); pieces: the density pieces this member should be cut into
+// (about its share of the SMs)
+void tc_items(const Ctx* c, int i, int64_t pieces, std::vector<TwItem>& prep, std::vector<TcItem>& dens,
+              std::vector<TcItem>& force) {
   const TcPlan& t = c->tc;
   // the heavier w items first.  d = 3 w items cover 16 particles (their powers fill shared memory); a table
   // item covers enough groups of 8 particles for 128 (entry, group) lane pairs, at most 128 particles
@@ -1210,21 +1262,41 @@ void tc_items(const Ctx* c, int i, std::vector<TwItem>& prep, std::vector<TcItem
       while (ng < kPrepTable / 8 && ng * count < kPrepThreads / 2) ng *= 2;
     for (int64_t j = 0; j < c->N; j += 8 * ng) prep.push_back({i, kind | (staged ? 1 << 8 : 0) | (ng << 9), j});
   }
+  // density pieces.  Each tile splits uniformly into `split` K ranges (at most one per read-out chunk); when
+  // the tiles do not divide the pieces and the pieces are long (128 K-steps and more), the K-steps of all tiles
+  // are laid end to end and cut every `len` steps instead, so that every SM gets the same work (a piece also
+  // stops at its tile's end).  A piece holds at most 1024 read-outs, so the int64 level groups (below 2^52 per
+  // read-out) cannot overflow.
+  const int64_t nt = (int64_t)t.tiles.size();
+  const int64_t total = nt * t.KS;
+  const int64_t want = std::max<int64_t>(1, pieces);
+  const int64_t len = std::min<int64_t>(1024 * kChunkSteps, std::max<int64_t>(1, (total + want - 1) / want));
+  const bool cross = want > nt && want % nt != 0 && len >= 8 * kChunkSteps;
+  int64_t split = std::max<int64_t>(1, std::min<int64_t>((t.KS + kChunkSteps - 1) / kChunkSteps, want / nt));
+  split = std::max<int64_t>(split, (t.KS + 1024 * kChunkSteps - 1) / (1024 * kChunkSteps));
   for (int ti = 0; ti < (int)t.tiles.size(); ti++) {
     const int rt = t.tiles[ti] / t.CTd, ct = t.tiles[ti] % t.CTd;
-    for (int sp = 0; sp < t.ksplit; sp++) {
-      const int64_t k0 = t.KS * sp / t.ksplit, k1 = t.KS * (sp + 1) / t.ksplit;
-      dens.push_back({i, 0, rt, ct, (int32_t)k0, (int32_t)(k1 - k0), ti, 0});
+    if (cross) {
+      int64_t k0 = 0;
+      while (k0 < t.KS) {  // cut where the global K-step (ti KS + k) reaches a multiple of len
+        const int64_t g = (int64_t)ti * t.KS + k0;
+        const int64_t k1 = std::min<int64_t>(t.KS, k0 + (len - g % len));
+        dens.push_back({i, 0, rt, ct, (int32_t)k0, (int32_t)(k1 - k0), ti, 0});
+        k0 = k1;
+      }
+    } else {
+      for (int64_t sp = 0; sp < split; sp++) {
+        const int64_t k0 = t.KS * sp / split, k1 = t.KS * (sp + 1) / split;
+        if (k1 > k0) dens.push_back({i, 0, rt, ct, (int32_t)k0, (int32_t)(k1 - k0), ti, 0});
+      }
     }
   }
   // force items: particle tile x column tile, with the K range of the column tile (the coefficients beyond are
-  // zero).  Largest items first, so the round-robin assignment to the persistent CTAs balances.
-  std::vector<TcItem> fi;
+  // zero), particle-tile-major: the column tiles of one particle tile are claimed together from the queue and
+  // read the particle tile's digits from L2 once they are in
   for (int pt = 0; pt < t.PT; pt++)
     for (int ct = 0; ct < t.CTf; ct++)
-      if (t.ks_ct[ct] > 0) fi.push_back({i, 1, pt, ct, 0, t.ks_ct[ct], ct, 0});
-  std::stable_sort(fi.begin(), fi.end(), [](const TcItem& a, const TcItem& b) { return a.nks > b.nks; });
-  force.insert(force.end(), fi.begin(), fi.end());
+      if (t.ks_ct[ct] > 0) force.push_back({i, 1, pt, ct, 0, t.ks_ct[ct], ct, 0});
 }
 
 size_t tc_gemm_smem() { return kGemmSmem; }
@@ -1250,7 +1322,7 @@ cudaError_t tc_launch_density(const EngineView& v, cudaStream_t st, Prof* prof) 
   prof_end(prof, st);
   prof_begin(prof, st, kKTcDens);
   le = launch_pdl(k_tc_gemm, dim3((unsigned)std::min(v.ntc_dens, v.sm_count)), dim3(kGemmThreads), kGemmSmem, st, v.cfgs,
-                  v.tc_dens, v.ntc_dens);
+                  v.tc_dens, v.ntc_dens, v.counters + 2);
   if (le != cudaSuccess) return le;
   prof_end(prof, st);
   prof_begin(prof, st, kKTcFinish);
@@ -1268,7 +1340,7 @@ cudaError_t tc_launch_force(const EngineView& v, cudaStream_t st, Prof* prof) {
   prof_end(prof, st);
   prof_begin(prof, st, kKTcForce);
   le = launch_pdl(k_tc_gemm, dim3((unsigned)std::min(v.ntc_force, v.sm_count)), dim3(kGemmThreads), kGemmSmem, st, v.cfgs,
-                  v.tc_force, v.ntc_force);
+                  v.tc_force, v.ntc_force, v.counters + 4);
   if (le != cudaSuccess) return le;
   prof_end(prof, st);
   return cudaGetLastError();
