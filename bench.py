@@ -272,11 +272,12 @@ def cpu_sample(N, d, L, chi, seed, frac_k=8, nthreads=0):
 
 def minimize_block(ssh, synth, w, dev, stream, with_dd=False, max_seconds=150):
     """Time full quenches of the workload from its random start to S_max <= 1e-36 (configs per hour): the
-    library's default ladder (all fixed point on a tensor-core context), staged FP64 -> fixed point (the
-    paper's cheap first stage), and all fixed point on the integer pipes; with --minimize-dd also FP64 -> dd
+    library's default ladder (all fixed point on a tensor-core context) with FIRE (the paper's minimiser) and
+    with L-BFGS, staged FP64 -> fixed point (the paper's cheap first stage), and all fixed point on the integer
+    pipes; with --minimize-dd also FP64 -> dd
     and all-dd, the paper's arithmetic (about a minute and several minutes)."""
     out = {}
-    runs = [("default", None), ("fp64_then_fx", [ssh.FP64, ssh.FX]), ("all_fx", [ssh.FX]),
+    runs = [("default", None), ("lbfgs", None), ("fp64_then_fx", [ssh.FP64, ssh.FX]), ("all_fx", [ssh.FX]),
             ("all_fx_integer", [ssh.FX])]
     if with_dd:
         runs += [("fp64_then_dd", [ssh.FP64, ssh.DD]), ("all_dd", [ssh.DD])]
@@ -285,7 +286,8 @@ def minimize_block(ssh, synth, w, dev, stream, with_dd=False, max_seconds=150):
         c = ssh.Context(w["d"], w["N"], w["L"], chi=w["chi"], device=dev, fx_impl=impl)
         c.set_stream(stream.cuda_stream)
         c.set_positions_frac(synth.positions(w["seed"], w["N"], w["d"]))
-        r = c.minimize(stages=stages, max_steps=100000, max_seconds=max_seconds)
+        r = c.minimize(stages=stages, max_steps=100000, max_seconds=max_seconds,
+                       method=ssh.MIN_LBFGS if name == "lbfgs" else ssh.MIN_FIRE)
         ns = r["stages_used"]
         out[name] = {"converged": r["status"] == 0, "status": r["status"], "wall_s": r["wall_s"],
                      "steps": r["steps"], "stage_steps": r["stage_steps"][:ns],
@@ -463,13 +465,14 @@ def large_d3_block(ssh, synth, dev, stream, flush, steps=5, warmup=3, max_second
     out["eval_ms"] = {k: v * 1e3 for k, v in evals.items()}
     out["eval_pairs_per_s"] = {k: pairs / v for k, v in evals.items()}
     ctx.close()
-    runs = [("default", None)] + ([("fp64_then_fx", [ssh.FP64, ssh.FX])] if staged else [])
+    runs = [("default", None), ("lbfgs", None)] + ([("fp64_then_fx", [ssh.FP64, ssh.FX])] if staged else [])
     q = {}
     for name, stages in runs:
         c = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi, device=dev)
         c.set_stream(stream.cuda_stream)
         c.set_positions_frac(s)
-        r = c.minimize(stages=stages, max_steps=100000, max_seconds=max_seconds)
+        r = c.minimize(stages=stages, max_steps=100000, max_seconds=max_seconds,
+                       method=ssh.MIN_LBFGS if name == "lbfgs" else ssh.MIN_FIRE)
         ns = r["stages_used"]
         q[name] = {"converged": r["status"] == 0, "status": r["status"], "wall_s": r["wall_s"], "steps": r["steps"],
                    "stage_steps": r["stage_steps"][:ns], "stage_wall_s": r["stage_wall_s"][:ns], "smax": r["smax"][0],
@@ -661,6 +664,9 @@ def main():
         conv = line["minimize"].get("default", {})
         if conv.get("converged"):
             line["configs_per_hour"] = 3600.0 / conv["wall_s"]
+        conv = line["minimize"].get("lbfgs", {})
+        if conv.get("converged"):
+            line["configs_per_hour_lbfgs"] = 3600.0 / conv["wall_s"]
     if rank == 0 and world == 1 and not args.no_batched:
         line["batched"] = batched_block(ssh, synth, dev)
     if rank == 0 and world == 1 and not args.no_large:

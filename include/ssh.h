@@ -156,13 +156,18 @@ ssh_status ssh_get_ntilde(ssh_ctx* ctx, double* C_hi, double* C_lo, double* S_hi
  *   max_steps, smax_target step cap (default 200000) and convergence target (default 1e-36)
  *   chunk                  steps between host checks of the device status word (default 64)
  *   max_seconds            wall-time limit, 0 = none
+ *   method                 SSH_MIN_FIRE (the paper's minimiser) or SSH_MIN_LBFGS: limited-memory BFGS (8 pairs,
+ *                          compact representation of Byrd, Nocedal and Schnabel 1994) with a backtracking Armijo
+ *                          line search on the same energy and force, the same stop rules and precision ladder;
+ *                          no particle moves more than a tenth of the mean spacing in one step
  */
+enum { SSH_MIN_FIRE = 0, SSH_MIN_LBFGS = 1 };
 typedef struct {
   double dt0, dt_max, alpha_start, f_alpha, f_inc, f_dec;
   int n_min;
   int n_stages;
   int stage_prec[3];
-  int pad0;
+  int method;                /* SSH_MIN_FIRE (0, default) or SSH_MIN_LBFGS */
   double stage_floor[3];
   int64_t stall_window[3];
   int64_t max_steps;

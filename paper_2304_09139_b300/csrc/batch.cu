@@ -128,6 +128,9 @@ struct Runner {
       precs.push_back(m.p.stage_prec[m.stage]);
     }
     cudaError_t e = engine_build(&eng, ms, precs, true, st);
+    eng.methods = 0;
+    for (Member& m : act) eng.methods |= 1 << (m.p.method == SSH_MIN_LBFGS ? kMethodLbfgs : kMethodFire);
+    if (act.empty()) eng.methods = 1 << kMethodFire;
     if (graph) {
       cudaGraphExecDestroy(graph);
       graph = nullptr;

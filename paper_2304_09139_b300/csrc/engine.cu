@@ -58,6 +58,7 @@ CfgDev make_cfgdev(const Ctx* c, bool fire_mode) {
   g.F_lo = (double*)c->F_lo.p;
   g.pref = c->pref;
   g.inv_L = c->inv_L;
+  g.L = c->L;
   tc_fill_cfgdev(c, &g);
   if (c->fire) fire_fill_cfgdev(c, &g);
   if (!fire_mode) g.run = nullptr;

@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kFireThreads) k_fire_dots(const CfgDev* __rest
   const BlockMap m = bm[blockIdx.x];
   const CfgDev& c = cfgs[m.cfg];
   const FireState* fs = fstate(c);
-  if (fs->status) return;
+  if (fs->status || fs->method != kMethodFire) return;
   __shared__ double sh[3][kFireThreads];
   const int64_t nd = (int64_t)c.d * c.N;
   double p = 0, f2 = 0, v2 = 0;
@@ -70,7 +70,7 @@ __global__ void k_fire_ctrl(const CfgDev* __restrict__ cfgs, const int* __restri
   if (i >= n) return;
   const CfgDev& c = cfgs[all[i]];
   FireState* fs = fstate(c);
-  if (fs->status) return;  // uniform over the warp
+  if (fs->status || fs->method != kMethodFire) return;  // uniform over the warp
   const int lane = threadIdx.x;
   double P = 0, f2 = 0, v2 = 0;
   for (int b = lane; b < c.nb_fire; b += 32) {
@@ -110,7 +110,7 @@ __global__ void k_fire_move(const CfgDev* __restrict__ cfgs, const BlockMap* __r
   const BlockMap m = bm[blockIdx.x];
   const CfgDev& c = cfgs[m.cfg];
   const FireState* fs = fstate(c);
-  if (fs->status) return;
+  if (fs->status || fs->method != kMethodFire) return;
   const int64_t i = (int64_t)m.blk * blockDim.x + threadIdx.x;
   if (i >= (int64_t)c.d * c.N) return;
   dd F = dd_make(c.F_hi[i], c.F_lo[i]);
@@ -135,7 +135,7 @@ __global__ void k_fire_accept(const CfgDev* __restrict__ cfgs, const int* __rest
   if (i >= n) return;
   const CfgDev& c = cfgs[all[i]];
   FireState* fs = fstate(c);
-  if (fs->status) return;
+  if (fs->status || fs->method != kMethodFire) return;
   dd phi = dd_make(c.scal[kScPhiHi], c.scal[kScPhiLo]);
   dd smx = dd_make(c.scal[kScSmaxHi], c.scal[kScSmaxLo]);
   fs->step++;
@@ -225,6 +225,19 @@ __global__ void k_fire_stage_init(const CfgDev* __restrict__ cfgs, const int* __
   fs->best_step = 0;
   fs->stage_floor = prm.stage_floor;
   fs->stall_window = prm.stall_window;
+  // L-BFGS restarts every stage too: no history, steepest descent first; no particle moves more than a tenth of
+  // the mean spacing in one step
+  fs->method = prm.method;
+  fs->lb_count = 0;
+  fs->lb_head = kLbMaxPairs - 1;
+  fs->lb_need_dir = 1;
+  fs->lb_accepted = 0;
+  fs->lb_sd = 1;
+  fs->lb_backtracks = 0;
+  fs->lb_alpha = 0.0;
+  fs->lb_gp = 0.0;
+  fs->lb_gamma = 1.0;
+  fs->lb_dmax = 0.1 / pow((double)c.N, 1.0 / c.d);
   double sm = fs->best_smax;
   if (!isfinite(sm) || !isfinite(fs->phi_hi)) fs->status = kFsNan;
   else if (sm <= fs->target) fs->status = kFsConverged;
@@ -245,6 +258,8 @@ __global__ void k_fire_zero_v(const CfgDev* __restrict__ cfgs, const int* __rest
 
 struct FireBufs {
   DevBuf v_hi, v_lo, bs_hi, bs_lo, bF_hi, bF_lo, part, fs;
+  DevBuf lb_S, lb_Y, lb_G, lb_P, lb_part, lb_mat;  // L-BFGS history, gradient, direction, partials, matrices
+  int method = kMethodFire;                         // minimiser the cached step graphs were captured for
   DevBuf init_idx, init_prm, init_first;  // arguments of k_fire_stage_init (single context)
   FireState* h_fs = nullptr;               // pinned
   Engine* eng[3] = {nullptr, nullptr, nullptr};             // this context alone, minimising in precision p
@@ -267,6 +282,14 @@ cudaError_t fire_alloc(Ctx* c) {
   f->nb = (int)std::max<int64_t>(1, std::min<int64_t>(256, ((int64_t)nd + kFireThreads - 1) / kFireThreads));
   f->part.bytes = sizeof(double) * 3 * f->nb;
   if (e == cudaSuccess) e = cudaMalloc(&f->part.p, f->part.bytes);
+  f->lb_S.bytes = f->lb_Y.bytes = std::max<size_t>((size_t)kLbMaxPairs * nd * 8, 16);
+  f->lb_G.bytes = f->lb_P.bytes = std::max<size_t>(nd * 8, 16);
+  f->lb_part.bytes = sizeof(double) * kLbPartStride * f->nb;
+  f->lb_mat.bytes = sizeof(LbMat);
+  for (DevBuf* b : {&f->lb_S, &f->lb_Y, &f->lb_G, &f->lb_P, &f->lb_part, &f->lb_mat}) {
+    if (e == cudaSuccess) e = cudaMalloc(&b->p, b->bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->p, 0, b->bytes, c->stream);
+  }
   f->fs.bytes = sizeof(FireState);
   if (e == cudaSuccess) e = cudaMalloc(&f->fs.p, f->fs.bytes);
   if (e == cudaSuccess) e = cudaMemsetAsync(f->fs.p, 0, f->fs.bytes, c->stream);
@@ -292,6 +315,12 @@ void fire_fill_cfgdev(const Ctx* c, CfgDev* g) {
   g->bF_lo = (double*)f->bF_lo.p;
   g->fdots = (double*)f->part.p;
   g->nb_fire = f->nb;
+  g->lb_S = (double*)f->lb_S.p;
+  g->lb_Y = (double*)f->lb_Y.p;
+  g->lb_G = (double*)f->lb_G.p;
+  g->lb_P = (double*)f->lb_P.p;
+  g->lb_part = (double*)f->lb_part.p;
+  g->lb_mat = f->lb_mat.p;
   g->run = &reinterpret_cast<FireState*>(f->fs.p)->status;
 }
 
@@ -299,7 +328,7 @@ void fire_free(Ctx* c) {
   FireBufs* f = c->fire;
   if (!f) return;
   for (DevBuf* b : {&f->v_hi, &f->v_lo, &f->bs_hi, &f->bs_lo, &f->bF_hi, &f->bF_lo, &f->part, &f->fs, &f->init_idx,
-                    &f->init_prm, &f->init_first})
+                    &f->init_prm, &f->init_first, &f->lb_S, &f->lb_Y, &f->lb_G, &f->lb_P, &f->lb_part, &f->lb_mat})
     if (b->p) cudaFree(b->p);
   if (f->h_fs) cudaFreeHost(f->h_fs);
   for (int p = 0; p < 3; p++) {
@@ -329,6 +358,7 @@ FireState fire_params(const ssh_min_params* p) {
   prm.target = p->smax_target;
   prm.stage_floor = 0.0;
   prm.stall_window = p->stall_window[0];
+  prm.method = p->method == SSH_MIN_LBFGS ? kMethodLbfgs : kMethodFire;
   return prm;
 }
 
@@ -351,9 +381,14 @@ cudaError_t fire_step_engine(const Engine* e, cudaStream_t st, Prof* prof) {
   const unsigned gt = (unsigned)((e->nall + 127) / 128);
   prof_begin(prof, st, kKFire);
   if (e->nbm_dots == 0 || e->nbm_nd == 0) return cudaErrorInvalidValue;  // members without minimiser buffers
-  cudaError_t le = launch_pdl(k_fire_dots, dim3((unsigned)e->nbm_dots), dim3(kFireThreads), 0, st, cfgs, e->bm_dots);
-  if (le == cudaSuccess) le = launch_pdl(k_fire_ctrl, dim3((unsigned)e->nall), dim3(32), 0, st, cfgs, e->all, e->nall);
-  if (le == cudaSuccess) le = launch_pdl(k_fire_move, dim3((unsigned)e->nbm_nd), dim3(64), 0, st, cfgs, e->bm_nd);
+  const bool fire = e->methods & (1 << kMethodFire), lbfgs = e->methods & (1 << kMethodLbfgs);
+  cudaError_t le = cudaSuccess;
+  if (fire) {
+    le = launch_pdl(k_fire_dots, dim3((unsigned)e->nbm_dots), dim3(kFireThreads), 0, st, cfgs, e->bm_dots);
+    if (le == cudaSuccess) le = launch_pdl(k_fire_ctrl, dim3((unsigned)e->nall), dim3(32), 0, st, cfgs, e->all, e->nall);
+    if (le == cudaSuccess) le = launch_pdl(k_fire_move, dim3((unsigned)e->nbm_nd), dim3(64), 0, st, cfgs, e->bm_nd);
+  }
+  if (lbfgs && le == cudaSuccess) le = lbfgs_pre(e, st);
   if (le != cudaSuccess) return le;
   prof_end(prof, st);
   for (int p = 0; p < 3; p++) {
@@ -362,8 +397,10 @@ cudaError_t fire_step_engine(const Engine* e, cudaStream_t st, Prof* prof) {
     if (err != cudaSuccess) return err;
   }
   prof_begin(prof, st, kKFire);
-  le = launch_pdl(k_fire_accept, dim3(gt), dim3(128), 0, st, cfgs, e->all, e->nall);
+  if (fire) le = launch_pdl(k_fire_accept, dim3(gt), dim3(128), 0, st, cfgs, e->all, e->nall);
+  if (lbfgs && le == cudaSuccess) le = lbfgs_post_accept(e, st);
   if (le == cudaSuccess) le = launch_pdl(k_fire_restore, dim3((unsigned)e->nbm_nd), dim3(64), 0, st, cfgs, e->bm_nd);
+  if (lbfgs && le == cudaSuccess) le = lbfgs_post_pairs(e, st);
   if (le != cudaSuccess) return le;
   prof_end(prof, st);
   return cudaGetLastError();
@@ -375,7 +412,9 @@ static cudaError_t stage_init_launch(const CfgDev* cfgs, int64_t maxND, const in
   k_fire_zero_v<<<dim3((unsigned)std::max<int64_t>(1, (maxND + 255) / 256), (unsigned)n), 256, 0, st>>>(cfgs, d_idx,
                                                                                                        d_first);
   k_fire_stage_init<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(cfgs, d_idx, n, d_prm, d_first);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = lbfgs_stage_g(cfgs, maxND, d_idx, n, st);  // L-BFGS members: G at the start
+  return e;
 }
 
 cudaError_t fire_stage_init_engine(const Engine* e, const std::vector<int>& idx, const std::vector<FireState>& params,
@@ -408,8 +447,21 @@ static cudaError_t fire_engine(Ctx* c, int prec, Engine** out) {
     cudaError_t e = engine_build(f->eng[prec], {c}, {prec}, true, c->stream);
     if (e != cudaSuccess) return e;
   }
+  f->eng[prec]->methods = 1 << f->method;
   *out = f->eng[prec];
   return cudaSuccess;
+}
+
+// the minimiser of the next run; the step graphs captured for the other one are dropped
+static void fire_set_method(Ctx* c, int method) {
+  FireBufs* f = c->fire;
+  if (f->method == method) return;
+  for (int p = 0; p < 3; p++) {
+    if (f->graph[p]) cudaGraphExecDestroy(f->graph[p]);
+    if (f->graph1[p]) cudaGraphExecDestroy(f->graph1[p]);
+    f->graph[p] = f->graph1[p] = nullptr;
+  }
+  f->method = method;
 }
 
 static cudaError_t fire_graph(Ctx* c, int prec, cudaGraphExec_t* out, int steps = kFireGraphSteps) {
@@ -453,6 +505,7 @@ ssh_status fire_begin(Ctx* c, const ssh_min_params* p) {
   cudaError_t e = fire_alloc(c);
   if (e != cudaSuccess) { set_error(std::string("ssh_fire_begin: allocation: ") + cudaGetErrorString(e)); return SSH_ENOMEM; }
   FireState prm = fire_params(p);
+  fire_set_method(c, prm.method);
   prm.stage = 0;
   prm.phi_tol = fire_phi_tol(c, p->stage_prec[0]);
   e = single_stage_start(c, p->stage_prec[0], prm, 1);
@@ -512,6 +565,7 @@ ssh_status minimize(Ctx* c, const ssh_min_params* p, ssh_min_result* res) {
   FireBufs* f = c->fire;
   cudaStream_t st = c->stream;
   FireState prm = fire_params(p);
+  fire_set_method(c, prm.method);
   ssh_min_result r;
   memset(&r, 0, sizeof r);
   r.status = SSH_ENOTCONV;

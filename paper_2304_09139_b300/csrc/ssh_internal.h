@@ -100,6 +100,9 @@ struct CfgDev {
   const void* tc_tmap;        // two 128-byte tensor maps of the digit tensor: density box, force box
   int* tc_err;
   // minimiser state (null when the context has not minimised yet)
+  double L;  // box length
+  double *lb_S, *lb_Y, *lb_G, *lb_P, *lb_part;  // L-BFGS: history [pair][d N], gradient, direction, partials
+  void* lb_mat;
   void* fs;
   double *v_hi, *v_lo, *bs_hi, *bs_lo, *bF_hi, *bF_lo, *fdots;
   const int* run;  // status word that turns this configuration's kernels into no-ops when non-zero, or null
@@ -177,6 +180,20 @@ struct FireState {
   long long n_min, stall_window, max_steps;
   double target, stage_floor;
   double phi_tol;  // the guard rejects a step only when Phi rises by more than phi_tol sqrt(Phi_accepted)
+  // minimiser: kMethodFire or kMethodLbfgs (lbfgs.cu), and the L-BFGS state
+  int method;
+  int lb_count, lb_head;      // history pairs kept; ring slot of the newest
+  int lb_need_dir, lb_accepted, lb_sd, lb_backtracks;
+  double lb_alpha, lb_gp, lb_gamma, lb_dmax;  // step length, G.p, scale of H0, largest fractional move
+};
+enum { kMethodFire = 0, kMethodLbfgs = 1 };
+constexpr int kLbMaxPairs = 8;
+constexpr int kLbPartStride = 48;  // doubles per block partial of the L-BFGS passes (>= 5 kLbMaxPairs + 1)
+struct LbMat {                     // per member: S^T Y and Y^T Y by ring slot, the direction's coefficients
+  double StY[kLbMaxPairs][kLbMaxPairs], YtY[kLbMaxPairs][kLbMaxPairs];
+  double t[kLbMaxPairs], w1[kLbMaxPairs];
+  int ticket_dir, ticket_pairs;    // last-block counters of the two passes
+  int pad[2];
 };
 
 // A set of configurations evaluated together.  Members keep their own buffers (Ctx); the engine holds their
@@ -202,6 +219,7 @@ struct Engine {
   // updates (64 threads over d N)
   const BlockMap *bm_dots = nullptr, *bm_nd = nullptr;
   int nbm_dots = 0, nbm_nd = 0;
+  int methods = 1;  // minimisers present among the members: bit kMethodFire, bit kMethodLbfgs (set by the caller)
 };
 
 // tile plan and buffers of the tensor-core path of one configuration (tc.cu)
@@ -315,6 +333,12 @@ cudaError_t fire_stage_init_engine(const Engine* e, const std::vector<int>& idx,
 
 // device scalar block written by k_finalize (doubles)
 enum { kScPhiHi = 0, kScPhiLo, kScSmaxHi, kScSmaxLo, kScCmax, kScScaleExp, kScA2MaxHi, kScA2MaxLo, kScCount = 16 };
+
+// lbfgs.cu (the L-BFGS minimiser's step kernels)
+cudaError_t lbfgs_pre(const Engine* e, cudaStream_t st);
+cudaError_t lbfgs_post_accept(const Engine* e, cudaStream_t st);
+cudaError_t lbfgs_post_pairs(const Engine* e, cudaStream_t st);
+cudaError_t lbfgs_stage_g(const CfgDev* cfgs, int64_t maxND, const int* d_idx, int n, cudaStream_t st);
 
 // tc.cu (tensor-core fixed-point path, d = 1, 2, 3)
 int64_t tc_coef_blocks(const Ctx& c);  // blocks (128 threads) of the coefficient kernel

@@ -14,6 +14,7 @@ import numpy as np
 
 FP64, DD, FX = 0, 1, 2
 FX_AUTO, FX_INTEGER, FX_TENSOR = 0, 1, 2   # ssh_opts.fx_impl
+MIN_FIRE, MIN_LBFGS = 0, 1                 # ssh_min_params.method
 PREC_NAMES = {FP64: "fp64", DD: "dd", FX: "fx"}
 KERNELS = ["twiddle", "ntilde", "nt_reduce", "finalize", "coef", "force", "f_reduce", "fire",
            "tc_prep", "tc_dens", "tc_finish", "tc_coef", "tc_force", "tc_tables"]
@@ -32,7 +33,7 @@ class MinParams(ctypes.Structure):
     _fields_ = [("dt0", ctypes.c_double), ("dt_max", ctypes.c_double), ("alpha_start", ctypes.c_double),
                 ("f_alpha", ctypes.c_double), ("f_inc", ctypes.c_double), ("f_dec", ctypes.c_double),
                 ("n_min", ctypes.c_int), ("n_stages", ctypes.c_int), ("stage_prec", ctypes.c_int * 3),
-                ("pad0", ctypes.c_int), ("stage_floor", ctypes.c_double * 3), ("stall_window", ctypes.c_int64 * 3),
+                ("method", ctypes.c_int), ("stage_floor", ctypes.c_double * 3), ("stall_window", ctypes.c_int64 * 3),
                 ("max_steps", ctypes.c_int64), ("smax_target", ctypes.c_double), ("chunk", ctypes.c_int64),
                 ("max_seconds", ctypes.c_double)]
 

@@ -193,3 +193,24 @@ def test_server_admission_by_memory_budget_and_cancel(built):
         big = synth.Config(d=2, N=20000, L=20000 ** 0.5, chi=0.45, seed=4)
         sv.submit(big.d, big.N, big.L, synth.positions(4, big.N, 2), chi=big.chi)
     sv.close()
+
+
+def test_batched_lbfgs_equals_single(built):
+    """A batch quenched with L-BFGS: each member's quench is bit-identical to a lone run (fixed-order reductions
+    everywhere, so a member's arithmetic does not depend on the batch)."""
+    cfgs = small_mix(6, 47, dims=(1, 2, 3))
+    b = ssh.Batch()
+    for c in cfgs:
+        b.add(c.d, c.N, c.L, synth.positions(c.seed, c.N, c.d), chi=c.chi)
+    st, res = b.minimize(max_steps=40000, chunk_steps=16, method=ssh.MIN_LBFGS)
+    assert st == 0, res
+    for i, c in enumerate(cfgs):
+        assert res[i]["status"] == 0 and res[i]["smax"][0] <= 1e-36, (i, res[i])
+        hb, lb = b.member(i).positions_frac()
+        with ssh.Context(c.d, c.N, c.L, chi=c.chi) as ctx:
+            ctx.set_positions_frac(synth.positions(c.seed, c.N, c.d))
+            ra = ctx.minimize(method=ssh.MIN_LBFGS, max_steps=40000)
+            ha, la = ctx.positions_frac()
+        assert ra["steps"] == res[i]["steps"] and ra["smax"] == res[i]["smax"], (i, ra, res[i])
+        assert np.array_equal(ha, hb) and np.array_equal(la, lb), i
+    b.close()

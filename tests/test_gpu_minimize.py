@@ -172,3 +172,33 @@ def test_large_d3_staged_error_per_stage(built, oracle_mod):
     assert e2 <= 1e-28, e2
     assert sk2 <= 1.01e-36, sk2
     ctx.close()
+
+
+LBFGS_CASES = [(2, 100, 1.0, 0.30, 1), (3, 200, 200 ** (1 / 3), 0.40, 31), (1, 150, 150.0, 0.30, 32)]
+
+
+@pytest.mark.parametrize("d,N,L,chi,seed", LBFGS_CASES, ids=[f"d{c[0]}" for c in LBFGS_CASES])
+def test_lbfgs_quench_converges(built, oracle_mod, d, N, L, chi, seed):
+    """The L-BFGS minimiser (compact representation, backtracking Armijo line search) reaches S_max <= 1e-36
+    from a random start, confirmed by the binary128 oracle at the returned positions."""
+    ctx = ssh.Context(d, N, L, chi=chi)
+    ctx.set_positions_frac(synth.positions(seed, N, d))
+    r = ctx.minimize(method=ssh.MIN_LBFGS, max_steps=40000)
+    assert r["status"] == 0, r
+    hi, lo = ctx.positions_frac()
+    sm, phi = oracle_smax(oracle_mod, ctx, hi, lo)
+    assert sm <= 1.01e-36, (sm, r)
+    ctx.close()
+
+
+def test_medium_d2_lbfgs(built, oracle_mod):
+    """The d=2, N=10^4, chi=0.45 workload quenched with L-BFGS in fixed point, confirmed by the oracle."""
+    cfg = synth.MEDIUM_D2
+    ctx = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi)
+    ctx.set_positions_frac(synth.positions(cfg.seed, cfg.N, cfg.d))
+    r = ctx.minimize(method=ssh.MIN_LBFGS, max_steps=60000, max_seconds=240)
+    assert r["status"] == 0, r
+    hi, lo = ctx.positions_frac()
+    sm, _ = oracle_smax(oracle_mod, ctx, hi, lo)
+    assert sm <= 1.01e-36, (sm, r)
+    ctx.close()
