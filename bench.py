@@ -111,6 +111,8 @@ def parse():
     ap.add_argument("--no-large-staged", action="store_true", help="skip its staged FP64 -> fixed point quench")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=45.0)
+    ap.add_argument("--serve-method", default="lbfgs", choices=["lbfgs", "fire"],
+                    help="minimiser of the serving requests")
     return ap.parse_args()
 
 
@@ -324,7 +326,7 @@ def batched_block(ssh, synth, dev, steps=5, warmup=2, count=256):
                         "fixed point, one batched FIRE step (graph replay)"}
 
 
-def serving_block(ssh, synth, dev, window_s=45.0, drain_s=30.0, count=2000, mean_gap=0.020):
+def serving_block(ssh, synth, dev, window_s=45.0, drain_s=30.0, count=2000, mean_gap=0.020, method="lbfgs"):
     # The offered load (about 50 requests/s of up to 1.3e9 pairs per step each) exceeds one GPU by far; the
     # server admits the smallest requests first under a cap on pairs per batched step, so the figures below
     # describe what one B300 sustains, and still_queued / still_running show the backlog.
@@ -333,6 +335,8 @@ def serving_block(ssh, synth, dev, window_s=45.0, drain_s=30.0, count=2000, mean
     import threading
     cfgs, arrivals = synth.serving_requests(5, count, mean_gap)
     sv = ssh.Server(device=dev, max_slots=256, chunk_steps=32)
+    params = ssh.MinParams()  # zero fields: the library's defaults
+    params.method = ssh.MIN_LBFGS if method == "lbfgs" else ssh.MIN_FIRE
     tickets = []
     t0 = time.perf_counter()
     stop = threading.Event()
@@ -344,7 +348,7 @@ def serving_block(ssh, synth, dev, window_s=45.0, drain_s=30.0, count=2000, mean
             dt = ta - (time.perf_counter() - t0)
             if dt > 0:
                 time.sleep(dt)
-            tickets.append(sv.submit(c.d, c.N, c.L, synth.positions(c.seed, c.N, c.d), chi=c.chi))
+            tickets.append(sv.submit(c.d, c.N, c.L, synth.positions(c.seed, c.N, c.d), chi=c.chi, params=params))
 
     th = threading.Thread(target=feeder)
     th.start()
@@ -367,6 +371,7 @@ def serving_block(ssh, synth, dev, window_s=45.0, drain_s=30.0, count=2000, mean
     return {"submitted": len(tickets), "completed": len(done), "converged": len(ok), "still_running": st["running"],
             "still_queued": st["queued"], "p50_s": pct(50), "p99_s": pct(99),
             "configs_per_hour": len(ok) / elapsed * 3600.0, "elapsed_s": elapsed,
+            "minimiser": method,
             "workload": f"Poisson arrivals mean {1 / mean_gap:.0f}/s for {window_s:.0f} s (+{drain_s:.0f} s drain), "
                         "d in {1,2,3}, N log-uniform [64, 32768], chi U[0.10, 0.49]; latency of converged requests only"}
 
@@ -673,7 +678,7 @@ def main():
         line["large_d3"] = large_d3_block(ssh, synth, dev, stream, flush, max_seconds=args.minimize_seconds,
                                           staged=not args.no_large_staged)
     if rank == 0 and world == 1 and not args.no_serve:
-        line["serving"] = serving_block(ssh, synth, dev, window_s=args.serve_seconds)
+        line["serving"] = serving_block(ssh, synth, dev, window_s=args.serve_seconds, method=args.serve_method)
         line["p50_s"] = line["serving"]["p50_s"]
         line["p99_s"] = line["serving"]["p99_s"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
