@@ -77,8 +77,10 @@ WORKLOAD = WORKLOADS["d2-n10000"]
 # the kernel sources hash to the value recorded with them; otherwise the traffic is reported as null.
 NCU_TRAFFIC = {("d2-n10000", "fx", "force"): ("9a8b45757c86", 35_869_184 + 5_888_000),
                ("d2-n10000", "fx", "ntilde"): ("9a8b45757c86", 36_598_272 + 43_264_000),
-               ("d2-n10000", "fx-tensor", "tc_force"): ("23287a2950f7", 78_166_272 + 2_166_272),
-               ("d2-n10000", "fx-tensor", "tc_dens"): ("23287a2950f7", 125_670_400 + 4_452_096)}
+               ("d2-n10000", "fx-tensor", "tc_force"): ("520cf6512eec", 74_686_464 + 2_572_288),
+               ("d2-n10000", "fx-tensor", "tc_dens"): ("520cf6512eec", 125_957_376 + 3_907_072),
+               ("d3-n32768", "fx-tensor", "tc_force"): ("520cf6512eec", 2_292_000_000 + 15_411_000),
+               ("d3-n32768", "fx-tensor", "tc_dens"): ("520cf6512eec", 4_390_640_000 + 7_504_000)}
 
 
 def kernel_source_hash() -> str:
