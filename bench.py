@@ -568,9 +568,9 @@ def main():
     ctx.prof_enable(False)
     tot_ms = max_over_ranks(tot_ms, dist, device=f"cuda:{dev}")
     value = job_value(pairs, world, args.steps, tot_ms)
-    # every profiled id is one kernel, except "fire": its two event pairs per step cover 3 + 2 kernels
+    # every profiled id is one kernel, except "fire": its two event pairs per step cover 2 + 2 kernels
     launches = sum(n for k, n in ((k, v[1]) for k, v in prof.items()) if k != "fire") + \
-        5 * prof.get("fire", (0, 0))[1] // 2
+        4 * prof.get("fire", (0, 0))[1] // 2
 
     # roofline of the dominant kernel (largest share of device time in the timed region)
     dom = max(prof.items(), key=lambda kv: kv[1][0])

@@ -201,7 +201,7 @@ cudaError_t engine_build(Engine* e, const std::vector<Ctx*>& members, const std:
   for (int i = 0; i < n; i++) add_blocks(i, ((int64_t)members[i]->d * members[i]->N + 63) / 64);
   bm_n[1] = bm.size() - bm_off[1];
   bm_off[2] = bm.size();
-  for (int i : tcl) add_blocks(i, ((int64_t)members[i]->tc.d * members[i]->N + 127) / 128);
+  for (int i : tcl) add_blocks(i, (2 * (int64_t)members[i]->tc.d * members[i]->N + 127) / 128);  // two chains each
   bm_n[2] = bm.size() - bm_off[2];
   bm_off[3] = bm.size();
   for (int i : tcl) add_blocks(i, tc_finish_blocks(*members[i]));

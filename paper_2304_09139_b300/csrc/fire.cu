@@ -2,8 +2,8 @@
 // configuration or for every member of a batch at once.
 //
 // One step, for the force F and energy Phi at the accepted positions and the velocity v of the last step:
-//   k_fire_dots     P = F.v, |F|^2, |v|^2 (per-block partials, fixed order)
-//   k_fire_ctrl     FIRE rules: P > 0 -> v <- (1-a) v + a |v| F/|F|; after more than n_min such steps
+//   k_fire_dots     P = F.v, |F|^2, |v|^2 (per-block partials, fixed order); the last block of a member applies
+//                   the FIRE rules: P > 0 -> v <- (1-a) v + a |v| F/|F|; after more than n_min such steps
 //                   dt <- min(dt f_inc, dt_max), a <- a f_alpha;  P <= 0 -> v <- 0, dt <- dt f_dec, a <- a_start
 //   k_fire_move     semi-implicit Euler with unit mass: v <- v + dt F, r <- r + dt v (dd, wrapped into the box);
 //                   the accepted positions and force are kept for a possible undo
@@ -33,15 +33,18 @@ constexpr int kFireGraphSteps = 8;
 
 __device__ __forceinline__ FireState* fstate(const CfgDev& c) { return reinterpret_cast<FireState*>(c.fs); }
 
-// block map: nb_fire blocks per member
+// block map: nb_fire blocks per member, grid-strided over the coordinates: the block partials of F.v, F.F and v.v;
+// the last block of a member to finish sums them (lane-strided in a fixed order, then a fixed shuffle tree) and
+// sets the FIRE controls of the step: mixing, velocity reset, dt and alpha
 __global__ void __launch_bounds__(kFireThreads) k_fire_dots(const CfgDev* __restrict__ cfgs,
                                                             const BlockMap* __restrict__ bm) {
   grid_dep_wait();
   const BlockMap m = bm[blockIdx.x];
   const CfgDev& c = cfgs[m.cfg];
-  const FireState* fs = fstate(c);
-  if (fs->status || fs->method != kMethodFire) return;
+  FireState* fs = fstate(c);
+  if (fs->status || fs->method != kMethodFire) return;  // uniform over the member's blocks
   __shared__ double sh[3][kFireThreads];
+  __shared__ int last;
   const int64_t nd = (int64_t)c.d * c.N;
   double p = 0, f2 = 0, v2 = 0;
   for (int64_t i = (int64_t)m.blk * kFireThreads + threadIdx.x; i < nd; i += (int64_t)c.nb_fire * kFireThreads) {
@@ -59,20 +62,18 @@ __global__ void __launch_bounds__(kFireThreads) k_fire_dots(const CfgDev* __rest
       for (int q = 0; q < 3; q++) sh[q][threadIdx.x] += sh[q][threadIdx.x + s];
     __syncthreads();
   }
-  if (threadIdx.x == 0)
+  if (threadIdx.x == 0) {
     for (int q = 0; q < 3; q++) c.fdots[q * c.nb_fire + m.blk] = sh[q][0];
-}
-
-// one warp per member: the block partials are summed lane-strided in a fixed order, then by a fixed shuffle tree
-__global__ void k_fire_ctrl(const CfgDev* __restrict__ cfgs, const int* __restrict__ all, int n) {
-  grid_dep_wait();
-  const int i = blockIdx.x;
-  if (i >= n) return;
-  const CfgDev& c = cfgs[all[i]];
-  FireState* fs = fstate(c);
-  if (fs->status || fs->method != kMethodFire) return;  // uniform over the warp
+    __threadfence();
+    last = atomicAdd(&fs->dots_ticket, 1) == c.nb_fire - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x >= 32) return;
+  __threadfence();
   const int lane = threadIdx.x;
-  double P = 0, f2 = 0, v2 = 0;
+  double P = 0;
+  f2 = 0;
+  v2 = 0;
   for (int b = lane; b < c.nb_fire; b += 32) {
     P += c.fdots[b];
     f2 += c.fdots[c.nb_fire + b];
@@ -85,6 +86,7 @@ __global__ void k_fire_ctrl(const CfgDev* __restrict__ cfgs, const int* __restri
     v2 += __shfl_down_sync(0xffffffffu, v2, off);
   }
   if (lane != 0) return;
+  fs->dots_ticket = 0;  // for the next step
   if (P > 0) {
     fs->zero_v = 0;
     fs->cv = 1.0 - fs->alpha;
@@ -225,6 +227,7 @@ __global__ void k_fire_stage_init(const CfgDev* __restrict__ cfgs, const int* __
   fs->best_step = 0;
   fs->stage_floor = prm.stage_floor;
   fs->stall_window = prm.stall_window;
+  fs->dots_ticket = 0;
   // L-BFGS restarts every stage too: no history, steepest descent first; no particle moves more than a tenth of
   // the mean spacing in one step
   fs->method = prm.method;
@@ -385,7 +388,6 @@ cudaError_t fire_step_engine(const Engine* e, cudaStream_t st, Prof* prof) {
   cudaError_t le = cudaSuccess;
   if (fire) {
     le = launch_pdl(k_fire_dots, dim3((unsigned)e->nbm_dots), dim3(kFireThreads), 0, st, cfgs, e->bm_dots);
-    if (le == cudaSuccess) le = launch_pdl(k_fire_ctrl, dim3((unsigned)e->nall), dim3(32), 0, st, cfgs, e->all, e->nall);
     if (le == cudaSuccess) le = launch_pdl(k_fire_move, dim3((unsigned)e->nbm_nd), dim3(64), 0, st, cfgs, e->bm_nd);
   }
   if (lbfgs && le == cudaSuccess) le = lbfgs_pre(e, st);

@@ -185,6 +185,7 @@ struct FireState {
   int lb_count, lb_head;      // history pairs kept; ring slot of the newest
   int lb_need_dir, lb_accepted, lb_sd, lb_backtracks;
   double lb_alpha, lb_gp, lb_gamma, lb_dmax;  // step length, G.p, scale of H0, largest fractional move
+  int dots_ticket, pad_ticket;                 // last-block counter of the FIRE dot products
 };
 enum { kMethodFire = 0, kMethodLbfgs = 1 };
 constexpr int kLbMaxPairs = 8;

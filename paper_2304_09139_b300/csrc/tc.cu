@@ -96,15 +96,27 @@ __device__ __forceinline__ __int128 digit_bias() {
   return b;
 }
 
-// The 15 balanced digits of X (|X| <= 2^104) as bf16, slice s holding digit 14 - s (top digit first).
-__device__ __forceinline__ void put_digits_x(uint8_t* base, uint32_t slice_stride, uint32_t off, __int128 X) {
-  const __int128 Y = X + digit_bias();
+// The 15 balanced digits of two values X0, X1 (|X| <= 2^104) as bf16 pairs, one 32-bit word per slice (X0 in the
+// low half), slice s holding digit 14 - s (top digit first).  Digit i < 14 is d = u - 64 with u the bits 7i..7i+6
+// of X + B (B the balanced-digit offset); the bf16 of 192 + d is 0x4300 | u, so one packed bf16 subtraction of
+// 192 gives both digits exactly.  The top digit, the signed bits 98..127 (it may be 64), goes through fp32.
+__device__ __forceinline__ void put_digit_pair(uint8_t* base, uint32_t slice_stride, uint32_t off, __int128 X0,
+                                               __int128 X1) {
+  const unsigned __int128 Y0 = (unsigned __int128)(X0 + digit_bias()), Y1 = (unsigned __int128)(X1 + digit_bias());
+  {
+    const uint32_t f0 = __float_as_uint(__int_as_float(kMagicBits + (int)((__int128)Y0 >> 98)) - kMagic);
+    const uint32_t f1 = __float_as_uint(__int_as_float(kMagicBits + (int)((__int128)Y1 >> 98)) - kMagic);
+    *reinterpret_cast<uint32_t*>(base + off) = __byte_perm(f0, f1, 0x7632);
+  }
+  const __nv_bfloat162 b192 = __halves2bfloat162(__ushort_as_bfloat16((unsigned short)0x4340),
+                                                 __ushort_as_bfloat16((unsigned short)0x4340));
 #pragma unroll
-  for (int s = 0; s < kDigits; s++) {
+  for (int s = 1; s < kDigits; s++) {
     const int i = kDigits - 1 - s;
-    const int d = i == kDigits - 1 ? (int)(Y >> 98) : (int)((Y >> (7 * i)) & 127) - 64;
-    *reinterpret_cast<uint16_t*>(base + (size_t)s * slice_stride + off) =
-        __bfloat16_as_ushort(__float2bfloat16_rn((float)d));
+    const uint32_t u0 = (uint32_t)(Y0 >> (7 * i)) & 127u, u1 = (uint32_t)(Y1 >> (7 * i)) & 127u;
+    const uint32_t t = u0 | (u1 << 16) | 0x43004300u;
+    const __nv_bfloat162 r = __hsub2(*reinterpret_cast<const __nv_bfloat162*>(&t), b192);
+    *reinterpret_cast<uint32_t*>(base + (size_t)s * slice_stride + off) = *reinterpret_cast<const uint32_t*>(&r);
   }
 }
 
@@ -297,46 +309,41 @@ __device__ __forceinline__ void qent_out(const qent& z, uint4& yre, uint4& yim, 
 
 }  // namespace
 
-// Thread per (particle, axis): the tables T[k] = e^{2 pi i k s} (k < 8) and A[b] = e^{2 pi i 8 b s}
-// (b <= Rax / 8) as first-quadrant phasors, from the exact-phase value of e^{2 pi i s} and chains of multiplies
-// (e^{2 pi i 8 s} = T[4]^2; each product at most 8 units of 2^-126 low, the error of a power grows linearly in
-// its exponent: far below the 2^-104 digits).
+// Two threads per (particle, axis), in two halves of the grid so that every warp runs one of the two chains:
+// half 0 the tables T[k] = e^{2 pi i k s} (k < 8), half 1 the tables A[b] = e^{2 pi i 8 b s} (b <= Rax / 8), as
+// first-quadrant phasors.  Each chain starts from an exact-phase evaluation (e^{2 pi i s}, e^{2 pi i 8 s}) and
+// multiplies on (each product at most 8 units of 2^-126 low, so the error of a power grows linearly in its
+// exponent: far below the 2^-104 digits).
 // Block map over the tensor-core members; layout tc_tab[(axis N + j) tc_ntab + (k | 8 + b)].
 __global__ void __launch_bounds__(128) k_tc_tables(const CfgDev* __restrict__ cfgs, const BlockMap* __restrict__ bm) {
   grid_dep_wait();
   const BlockMap m = bm[blockIdx.x];
   const CfgDev& c = cfgs[m.cfg];
   if (stopped(c)) return;
+  const int64_t nd = (int64_t)c.tc_d * c.N;
   const int64_t idx = (int64_t)m.blk * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)c.tc_d * c.N) return;
-  const int axis = (int)(idx / c.N);
-  const int64_t j = idx - (int64_t)axis * c.N;
-  const int nA = c.tc_Rax[axis] / kPrepLow + 1;
+  if (idx >= 2 * nd) return;
+  const int h = idx >= nd ? 1 : 0;
+  const int64_t r = idx - h * nd;
+  const int axis = (int)(r / c.N);
+  const int64_t j = r - (int64_t)axis * c.N;
+  const int cnt = h == 0 ? kPrepLow : c.tc_Rax[axis] / kPrepLow + 1;
   // d = 1 lifted to two axes: axis 0 holds the phase 2^lift s (mod 1, exact), axis 1 the phase s
   const int src = c.tc_lift ? 0 : axis;
   q128 u = turns_from_dd(c.s_hi[src * c.N + j], c.s_lo[src * c.N + j]);
   if (c.tc_lift && axis == 0) u = turn_times(u, 1 << c.tc_lift);
-  qent* tab = reinterpret_cast<qent*>(c.tc_tab) + idx * c.tc_ntab;
+  qent* tab = reinterpret_cast<qent*>(c.tc_tab) + r * c.tc_ntab + (h == 0 ? 0 : kPrepLow);
   // e^0 = 1 exactly (the exact-phase evaluation returns (2^126, 0) at t = 0): c = 1 in Q1.127, s = 0, quadrant 0
-  qent one;
-  one.c = q128_zero();
-  one.c.w[3] = 0x80000000u;
-  one.s = q128_zero();
-  one.cs = one.c;
-  const qent e1 = to_quadrant(phasor_turn(u));
-  qent t = one, e4 = one;
+  qent x;
+  x.c = q128_zero();
+  x.c.w[3] = 0x80000000u;
+  x.s = q128_zero();
+  x.cs = x.c;
+  const qent e = to_quadrant(phasor_turn(h == 0 ? u : turn_times(u, kPrepLow)));
 #pragma unroll 1
-  for (int k = 0; k < kPrepLow; k++) {
-    tab[k] = t;
-    if (k == kPrepLow / 2) e4 = t;
-    if (k + 1 < kPrepLow) t = qmul(t, e1);
-  }
-  const qent e8 = qmul(e4, e4);  // e^{2 pi i 8 s} = T[4]^2: one product instead of a second exact-phase evaluation
-  qent a = one;
-#pragma unroll 1
-  for (int b = 0; b < nA; b++) {
-    tab[kPrepLow + b] = a;
-    if (b + 1 < nA) a = qmul(a, e8);
+  for (int k = 0; k < cnt; k++) {
+    tab[k] = x;
+    if (k + 1 < cnt) x = qmul(x, e);
   }
 }
 
@@ -589,15 +596,23 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
           tc_fence_after();
           const uint32_t a0 = smem_u32(smem + (size_t)s * kStageBytes);
           const uint32_t b0 = a0 + kStageA;
+          // slice 0 starts every level: levels 0..6 (kHeldLevels) at the first K-step of every second chunk of
+          // the item, levels 7..14 at the first K-step of every chunk
+          {
+            const bool even = ((ks / kChunkSteps) & 1) == 0;
+            const uint64_t ad = make_sdesc(a0, lbo, sbo);
+            mma_bf16(tbase, ad, make_sdesc(b0), make_idesc(kTileM, kHeldLevels * kTileN, mn), (first && even) ? 0u : 1u);
+            mma_bf16(tbase + kHeldLevels * kTileN, ad, make_sdesc(b0 + kHeldLevels * kSliceB),
+                     make_idesc(kTileM, (kLevels - kHeldLevels) * kTileN, mn), first ? 0u : 1u);
+          }
 #pragma unroll
-          for (int sl = 0; sl < kDigits; sl++) {
+          for (int sl = 1; sl < kDigits; sl++) {
             const int ntot = (kLevels - sl) * kTileN;
             const int n1 = ntot < 256 ? ntot : 256;
-            const uint32_t acc = (first && sl == 0) ? 0u : 1u;
             const uint64_t ad = make_sdesc(a0 + sl * kSliceA, lbo, sbo);
-            mma_bf16(tbase + sl * kTileN, ad, make_sdesc(b0), make_idesc(kTileM, n1, mn), acc);
+            mma_bf16(tbase + sl * kTileN, ad, make_sdesc(b0), make_idesc(kTileM, n1, mn), 1u);
             if (ntot > 256)
-              mma_bf16(tbase + sl * kTileN + 256, ad, make_sdesc(b0 + 256 * 32), make_idesc(kTileM, ntot - 256, mn), acc);
+              mma_bf16(tbase + sl * kTileN + 256, ad, make_sdesc(b0 + 256 * 32), make_idesc(kTileM, ntot - 256, mn), 1u);
           }
           mma_commit(&bar_empty[s]);
           if (last) {
@@ -647,26 +662,48 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
           break;
         }
         tc_fence_after();
+        // levels 0..6 run on over two chunks (their sums stay below 2^24), so they are read after every second
+        // chunk and after the item's last; levels 7..14 after every chunk.  The accumulator is released as soon as
+        // the last group is in registers, before its conversion.
+        const bool full = (ch & 1) || ch == nch - 1;
 #pragma unroll
         for (int g = 0; g < 3; g++) {
-          long long t[kEpiCols];
+          if (g == 0 && !full) continue;  // uniform over the CTA
+          const int l0 = (g == 1 && !full) ? 2 : 0;
+          uint32_t r[5][kEpiCols];  // the group's levels, loaded together, one wait
 #pragma unroll
-          for (int i = 0; i < kEpiCols; i++) t[i] = 0;
-          uint32_t r[5][kEpiCols];  // the group's five levels, loaded together, one wait
+          for (int l = 0; l < 5; l++) {
+            if (l < l0) {
 #pragma unroll
-          for (int l = 0; l < 5; l++) tmem_ld8(trow + (uint32_t)((5 * g + l) * kTileN), r[l]);
+              for (int i = 0; i < kEpiCols; i++) r[l][i] = 0;  // +0.0f
+            } else {
+              tmem_ld8(trow + (uint32_t)((5 * g + l) * kTileN), r[l]);
+            }
+          }
           tmem_ld_wait();
+          if (g == 2) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&bar_acc_empty);
+          }
+          // |x| of level u is at most (u + 1) 2^20 per chunk (u + 1 digit pairs, 256 products of at most 64^2
+          // each), twice that for u <= 6: level 0 takes one add; of the others, levels 2, 4, 8, 11, 13 convert on
+          // the fp32 pipe and the rest on the conversion unit, which balances the two
 #pragma unroll
-          for (int l = 0; l < 5; l++)
+          for (int i = 0; i < kEpiCols; i++) {
+            int32_t v[5];
 #pragma unroll
-            for (int i = 0; i < kEpiCols; i++)
-              t[i] += (long long)acc_int(r[l][i]) * (1ll << (7 * (4 - l)));
-#pragma unroll
-          for (int i = 0; i < kEpiCols; i++) st[g][i] += t[i];
+            for (int l = 0; l < 5; l++) {
+              const int u = 5 * g + l;
+              v[l] = u == 0 ? acc_int_small(r[l][i])
+                            : (u == 2 || u == 4 || u == 8 || u == 11 || u == 13) ? acc_int_fma(r[l][i])
+                                                                                  : acc_int(r[l][i]);
+            }
+            // x0 2^28 + x1 2^21 + x2 2^14 + x3 2^7 + x4, with x0 128 + x1 and x2 128 + x3 below 2^31 in magnitude
+            const int32_t a = v[0] * 128 + v[1], b = v[2] * 128 + v[3];
+            st[g][i] += (long long)a * (1ll << 21) + (long long)b * 128 + v[4];
+          }
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&bar_acc_empty);
       }
       if (stop) break;
       if (it.kind == 0) {
@@ -743,10 +780,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
 
 // ------------------------------------------------------------------------------------------------ finish
 
-// block map over the tensor-core members (tc_nblk blocks each), 64 threads, thread per (n1, p), n1 fastest: n~(n1, p) and
-// n~(n1, -p) from the four real products of the tile accumulator (which it clears for the next evaluation), as
-// exact Q34.126 values (for the force coefficients) and as dd (C, S), with the block's Phi / max |n~|^2 /
-// max |C|, |S| partials; the last block to finish reduces the partials to Phi, S_max and the scale.
+// block map over the tensor-core members (tc_nblk blocks each), 64 threads, a lane pair per (n1, p), n1 fastest:
+// the even lane n~(n1, p), the odd lane n~(n1, -p), from the four real products of the tile accumulator (which the
+// even lane clears for the next evaluation once both have read it), as exact Q34.126 values (for the force
+// coefficients) and as dd (C, S), with the block's Phi / max |n~|^2 / max |C|, |S| partials; the last block to
+// finish reduces the partials to Phi, S_max and the scale.
 __global__ void __launch_bounds__(kFinThreads) k_tc_dens_finish(const CfgDev* __restrict__ cfgs,
                                                                 const BlockMap* __restrict__ bm) {
   grid_dep_wait();
@@ -755,60 +793,65 @@ __global__ void __launch_bounds__(kFinThreads) k_tc_dens_finish(const CfgDev* __
   if (stopped(c)) return;  // uniform per block
   RedPart v = {0, 0, 0, 0, 0, 0, 0, 0};
   const int W1 = c.tc_R1 + 1;
-  const int64_t idx = (int64_t)m.blk * kFinThreads + threadIdx.x;
+  const int64_t idx = ((int64_t)m.blk * kFinThreads + threadIdx.x) >> 1;
+  const int neg = threadIdx.x & 1;
+  int k = -1, ti = -1, rr = 0, cc = 0;
+  long long P[4][3];  // [2 x + y]: x the cos / sin of w (row), y of a (column)
+  long long* acc = nullptr;
   if (idx < (int64_t)W1 * c.tc_nP) {
     const int n1 = (int)(idx % W1), p = (int)(idx / W1);
     const int kp = c.tc_em[idx * 2 + 0], km = c.tc_em[idx * 2 + 1];  // em is [p][n1][2]
+    k = neg ? km : kp;
     const int r = 2 * p, col = 2 * n1;
-    const int ti = (kp >= 0 || km >= 0) ? c.tc_tilemap[(r >> 7) * c.tc_CTd + (col >> 5)] : -1;
+    ti = (kp >= 0 || km >= 0) ? c.tc_tilemap[(r >> 7) * c.tc_CTd + (col >> 5)] : -1;
     if (ti >= 0) {
-      const int rr = r & 127, cc = col & 31;
-      long long* acc = c.tc_acc + (size_t)ti * (3 * kTileN * kTileM);
-      long long P[4][3];  // [2 x + y]: x the cos / sin of w (row), y of a (column)
+      rr = r & 127;
+      cc = col & 31;
+      acc = c.tc_acc + (size_t)ti * (3 * kTileN * kTileM);
 #pragma unroll
       for (int x = 0; x < 2; x++)
 #pragma unroll
         for (int y = 0; y < 2; y++)
 #pragma unroll
-          for (int g = 0; g < 3; g++) {
-            long long* e = acc + ((size_t)g * kTileN + cc + y) * kTileM + rr + x;
-            P[2 * x + y][g] = *e;
-            *e = 0;
-          }
-      FxAcc* part = reinterpret_cast<FxAcc*>(c.part);
-      // C = P_cc + ss P_ss, S = s1 P_cs + s2 P_sc
-      auto emit = [&](int k, int ss, int s1, int s2) {
-        i192 C, S;
-        i192_zero(C);
-        i192_zero(S);
-#pragma unroll
-        for (int g = 0; g < 3; g++) {
-          const int sh = 70 - 35 * g;
-          i192_add_shl(C, (__int128)P[0][g] + (ss > 0 ? (__int128)P[3][g] : -(__int128)P[3][g]), sh);
-          i192_add_shl(S, (s1 > 0 ? (__int128)P[1][g] : -(__int128)P[1][g]) + (s2 > 0 ? (__int128)P[2][g] : -(__int128)P[2][g]),
-                       sh);
-        }
-        FxAcc o;
-        o.re = i192_to_q160_shl(C, 16);  // value 2^-110 -> Q34.126
-        o.im = i192_to_q160_shl(S, 16);
-        part[k] = o;
-        const dd cd = i192_to_dd(C, 110), sd = i192_to_dd(S, 110);
-        c.C_hi[k] = cd.hi;
-        c.C_lo[k] = cd.lo;
-        c.S_hi[k] = sd.hi;
-        c.S_lo[k] = sd.lo;
-        RedPart t;
-        const dd a2 = dd_add(dd_sqr(cd), dd_sqr(sd));
-        t.phi_hi = a2.hi;
-        t.phi_lo = a2.lo;
-        t.a2max_hi = a2.hi;
-        t.a2max_lo = a2.lo;
-        t.cmax = fmax(fabs(cd.hi), fabs(sd.hi));
-        red_combine(v, t);
-      };
-      if (kp >= 0) emit(kp, -1, +1, +1);  // n~(n1, p)  = (P_cc - P_ss) + i (P_cs + P_sc)
-      if (km >= 0) emit(km, +1, +1, -1);  // n~(n1, -p) = (P_cc + P_ss) + i (P_cs - P_sc)
+          for (int g = 0; g < 3; g++) P[2 * x + y][g] = acc[((size_t)g * kTileN + cc + y) * kTileM + rr + x];
     }
+  }
+  __syncwarp();
+  if (ti >= 0 && !neg) {
+#pragma unroll
+    for (int x = 0; x < 2; x++)
+#pragma unroll
+      for (int y = 0; y < 2; y++)
+#pragma unroll
+        for (int g = 0; g < 3; g++) acc[((size_t)g * kTileN + cc + y) * kTileM + rr + x] = 0;
+  }
+  if (ti >= 0 && k >= 0) {
+    // n~(n1, p)  = (P_cc - P_ss) + i (P_cs + P_sc);  n~(n1, -p) = (P_cc + P_ss) + i (P_cs - P_sc)
+    FxAcc* part = reinterpret_cast<FxAcc*>(c.part);
+    i192 C, S;
+    i192_zero(C);
+    i192_zero(S);
+#pragma unroll
+    for (int g = 0; g < 3; g++) {
+      const int sh = 70 - 35 * g;
+      i192_add_shl(C, (__int128)P[0][g] + (neg ? (__int128)P[3][g] : -(__int128)P[3][g]), sh);
+      i192_add_shl(S, (__int128)P[1][g] + (neg ? -(__int128)P[2][g] : (__int128)P[2][g]), sh);
+    }
+    FxAcc o;
+    o.re = i192_to_q160_shl(C, 16);  // value 2^-110 -> Q34.126
+    o.im = i192_to_q160_shl(S, 16);
+    part[k] = o;
+    const dd cd = i192_to_dd(C, 110), sd = i192_to_dd(S, 110);
+    c.C_hi[k] = cd.hi;
+    c.C_lo[k] = cd.lo;
+    c.S_hi[k] = sd.hi;
+    c.S_lo[k] = sd.lo;
+    const dd a2 = dd_add(dd_sqr(cd), dd_sqr(sd));
+    v.phi_hi = a2.hi;
+    v.phi_lo = a2.lo;
+    v.a2max_hi = a2.hi;
+    v.a2max_lo = a2.lo;
+    v.cmax = fmax(fabs(cd.hi), fabs(sd.hi));
   }
   red_warp(v);
   __shared__ RedPart sh[kFinThreads / 32];
@@ -875,17 +918,21 @@ __global__ void __launch_bounds__(kFinThreads) k_tc_force_finish(const CfgDev* _
   c.F_lo[i] = f.lo * sc;
 }
 
-// block map over the tensor-core members ((R1 + 1) nP / 128 blocks each), thread per (n1, p), p fastest: the force GEMM's
-// coefficient digits of every axis
-__global__ void k_tc_coef(const CfgDev* __restrict__ cfgs, const BlockMap* __restrict__ bm) {
+// block map over the tensor-core members (2 d (R1 + 1) nP / 128 blocks each), thread per (column, n1, p), p fastest:
+// the force GEMM's coefficient digits of one column (n1, axis t, Re / Im) in both rows (p, cos / sin)
+__global__ void __launch_bounds__(128) k_tc_coef(const CfgDev* __restrict__ cfgs, const BlockMap* __restrict__ bm) {
   grid_dep_wait();
   const BlockMap m = bm[blockIdx.x];
   const CfgDev& c = cfgs[m.cfg];
   if (stopped(c)) return;
   const int W1 = c.tc_R1 + 1;
+  const int64_t np = (int64_t)W1 * c.tc_nP;
   const int64_t idx = (int64_t)m.blk * blockDim.x + threadIdx.x;
-  if (idx >= (int64_t)W1 * c.tc_nP) return;
-  const int n1 = (int)(idx / c.tc_nP), p = (int)(idx % c.tc_nP);
+  if (idx >= 2 * c.tc_d * np) return;
+  const int qc = (int)(idx / np);  // 2 t + ri: axis t, Re (0) / Im (1) column
+  const int t = qc >> 1, ri = qc & 1;
+  const int64_t rem = idx - (int64_t)qc * np;
+  const int n1 = (int)(rem / c.tc_nP), p = (int)(rem % c.tc_nP);
   const int32_t* em = c.tc_em + ((int64_t)p * W1 + n1) * 2;
   const int kp = em[0], km = em[1];
   const FxAcc* part = reinterpret_cast<const FxAcc*>(c.part);
@@ -894,45 +941,45 @@ __global__ void k_tc_coef(const CfgDev* __restrict__ cfgs, const BlockMap* __res
   const q160 Cm = km >= 0 ? load_q160(&part[km].re) : z, Sm = km >= 0 ? load_q160(&part[km].im) : z;
   const int e = (int)c.scal[kScScaleExp];
   const int32_t pv = c.tc_pvec[p];
-  const int nw[3] = {1, (int)(int16_t)(pv & 0xffff), pv >> 16};
-  const bool p0 = pv == 0;
   // W = C - i S:  Re U = C+ + C-,  Im U = -(S+ + S-),  Re V = S+ - S-,  Im V = C+ - C-
   //               Re U^a = n_a (C+ - C-), Im U^a = -n_a (S+ - S-), Re V^a = n_a (S+ + S-), Im V^a = n_a (C+ + C-)
-  q160 cpl = Cp, spl = Sp;
-  q160_add160(cpl, Cm);
-  const q160 cmi = q160_sub160(Cp, Cm);
-  q160_add160(spl, Sm);
-  const q160 smi = q160_sub160(Sp, Sm);
-  const int shG = 22 + e, shW = 22 + e + c.tc_bexp;
-  const int kf = 2 * p;
-  for (int t = 0; t < c.tc_d; t++) {
-    __int128 X[2][2];  // [Re / Im column][cos / sin row]
-    if (t == 0) {
-      X[0][0] = q160_shr_round(cpl, shG);
-      X[0][1] = q160_shr_round(smi, shG);
-      X[1][0] = -q160_shr_round(spl, shG);
-      X[1][1] = q160_shr_round(cmi, shG);
+  // column Re holds (Re U, Re V) in rows (cos, sin), column Im holds (Im U, Im V); likewise U^a, V^a
+  __int128 X0, X1;
+  if (t == 0) {
+    const int sh = 22 + e;
+    if (ri == 0) {
+      q160 a = Cp;
+      q160_add160(a, Cm);
+      X0 = q160_shr_round(a, sh);
+      X1 = q160_shr_round(q160_sub160(Sp, Sm), sh);
     } else {
-      const int n = nw[t];
-      X[0][0] = q160_shr_round(q160_mul_int(cmi, n), shW);
-      X[0][1] = q160_shr_round(q160_mul_int(spl, n), shW);
-      X[1][0] = -q160_shr_round(q160_mul_int(smi, n), shW);
-      X[1][1] = q160_shr_round(q160_mul_int(cpl, n), shW);
+      q160 a = Sp;
+      q160_add160(a, Sm);
+      X0 = -q160_shr_round(a, sh);
+      X1 = q160_shr_round(q160_sub160(Cp, Cm), sh);
     }
-    if (p0) X[0][1] = X[1][1] = 0;  // sin(0) = 0 (and every weight n_a is 0)
-    const int npt = 16 / c.tc_d;      // n1 values per column tile, all axes of each
-    const int ct = n1 / npt;
-#pragma unroll
-    for (int ri = 0; ri < 2; ri++) {
-      const int col = 2 * (c.tc_d * (n1 - ct * npt) + t) + ri;
-#pragma unroll
-      for (int qq = 0; qq < 2; qq++) {
-        const int kk = kf + qq;
-        uint8_t* base = c.tc_fB + ((int64_t)ct * c.tc_KSf + (kk >> 4)) * kStageB;
-        put_digits_x(base, kSliceB, slice_off(col, kk & 15), X[ri][qq]);
-      }
+  } else {
+    const int n = t == 1 ? (int)(int16_t)(pv & 0xffff) : pv >> 16;
+    const int sh = 22 + e + c.tc_bexp;
+    if (ri == 0) {
+      q160 a = Sp;
+      q160_add160(a, Sm);
+      X0 = q160_shr_round(q160_mul_int(q160_sub160(Cp, Cm), n), sh);
+      X1 = q160_shr_round(q160_mul_int(a, n), sh);
+    } else {
+      q160 a = Cp;
+      q160_add160(a, Cm);
+      X0 = -q160_shr_round(q160_mul_int(q160_sub160(Sp, Sm), n), sh);
+      X1 = q160_shr_round(q160_mul_int(a, n), sh);
     }
   }
+  if (pv == 0) X1 = 0;  // sin(0) = 0 (and every weight n_a is 0)
+  const int npt = 16 / c.tc_d;  // n1 values per column tile, all axes of each
+  const int ct = n1 / npt;
+  const int col = 2 * (c.tc_d * (n1 - ct * npt) + t) + ri;
+  const int kk = 2 * p;  // rows (p, cos), (p, sin): adjacent K positions of one core row
+  uint8_t* base = c.tc_fB + ((int64_t)ct * c.tc_KSf + (kk >> 4)) * kStageB;
+  put_digit_pair(base, kSliceB, slice_off(col, kk & 15), X0, X1);
 }
 
 // ------------------------------------------------------------------------------------------------ host side
@@ -949,12 +996,12 @@ bool tc_eligible(const Ctx& c) { return c.d >= 1 && c.d <= 3 && c.N >= 1 && c.M 
 
 int64_t tc_coef_blocks(const Ctx& c) {
   if (!c.tc.on) return 0;
-  return ((int64_t)(c.tc.R1 + 1) * c.tc.nP + 127) / 128;
+  return (2 * (int64_t)c.tc.d * (c.tc.R1 + 1) * c.tc.nP + 127) / 128;  // a thread per (column, n1, p)
 }
 
 int tc_finish_blocks(const Ctx& c) {
   if (!c.tc.on) return 0;
-  return (int)(((int64_t)(c.tc.R1 + 1) * c.tc.nP + kFinThreads - 1) / kFinThreads);
+  return (int)((2 * (int64_t)(c.tc.R1 + 1) * c.tc.nP + kFinThreads - 1) / kFinThreads);  // a lane pair per (n1, p)
 }
 
 namespace {
@@ -1262,11 +1309,13 @@ void tc_items(const Ctx* c, int i, int64_t pieces, std::vector<TwItem>& prep, st
       while (ng < kPrepTable / 8 && ng * count < kPrepThreads / 2) ng *= 2;
     for (int64_t j = 0; j < c->N; j += 8 * ng) prep.push_back({i, kind | (staged ? 1 << 8 : 0) | (ng << 9), j});
   }
-  // density pieces.  Each tile splits uniformly into `split` K ranges (at most one per read-out chunk); when
-  // the tiles do not divide the pieces and the pieces are long (128 K-steps and more), the K-steps of all tiles
-  // are laid end to end and cut every `len` steps instead, so that every SM gets the same work (a piece also
-  // stops at its tile's end).  A piece holds at most 1024 read-outs, so the int64 level groups (below 2^52 per
-  // read-out) cannot overflow.
+  // density pieces.  The column tiles of a row tile read the same rows of w, so their pieces share K ranges and
+  // sit next to each other in the list: CTAs claim them together and the second read of each w stage hits L2.
+  // Each row tile splits uniformly into `split` K ranges (at most one per read-out chunk); when the tiles do not
+  // divide the pieces and the pieces are long (128 K-steps and more), the K-steps of the row tiles are laid end to
+  // end and cut every `len` steps instead, so that every SM gets about the same work (a cut also falls at each row
+  // tile's end).  A piece holds at most 1024 read-outs, so the int64 level groups (below 2^52 per read-out)
+  // cannot overflow.
   const int64_t nt = (int64_t)t.tiles.size();
   const int64_t total = nt * t.KS;
   const int64_t want = std::max<int64_t>(1, pieces);
@@ -1274,22 +1323,28 @@ void tc_items(const Ctx* c, int i, int64_t pieces, std::vector<TwItem>& prep, st
   const bool cross = want > nt && want % nt != 0 && len >= 8 * kChunkSteps;
   int64_t split = std::max<int64_t>(1, std::min<int64_t>((t.KS + kChunkSteps - 1) / kChunkSteps, want / nt));
   split = std::max<int64_t>(split, (t.KS + 1024 * kChunkSteps - 1) / (1024 * kChunkSteps));
-  for (int ti = 0; ti < (int)t.tiles.size(); ti++) {
-    const int rt = t.tiles[ti] / t.CTd, ct = t.tiles[ti] % t.CTd;
+  auto emit = [&](int ti0, int ti1, int64_t k0, int64_t k1) {  // one piece per column tile of the row tile
+    for (int ti = ti0; ti < ti1; ti++)
+      dens.push_back({i, 0, t.tiles[ti] / t.CTd, t.tiles[ti] % t.CTd, (int32_t)k0, (int32_t)(k1 - k0), ti, 0});
+  };
+  int64_t g0 = 0;  // K-steps of the row tiles before this one (cut grid)
+  for (int ti0 = 0; ti0 < (int)nt;) {
+    int ti1 = ti0;  // tiles are listed row tile by row tile
+    while (ti1 < (int)nt && t.tiles[ti1] / t.CTd == t.tiles[ti0] / t.CTd) ti1++;
     if (cross) {
-      int64_t k0 = 0;
-      while (k0 < t.KS) {  // cut where the global K-step (ti KS + k) reaches a multiple of len
-        const int64_t g = (int64_t)ti * t.KS + k0;
-        const int64_t k1 = std::min<int64_t>(t.KS, k0 + (len - g % len));
-        dens.push_back({i, 0, rt, ct, (int32_t)k0, (int32_t)(k1 - k0), ti, 0});
+      for (int64_t k0 = 0; k0 < t.KS;) {  // cut where the global K-step g0 + k reaches a multiple of len
+        const int64_t k1 = std::min<int64_t>(t.KS, k0 + (len - (g0 + k0) % len));
+        emit(ti0, ti1, k0, k1);
         k0 = k1;
       }
+      g0 += t.KS;
     } else {
       for (int64_t sp = 0; sp < split; sp++) {
         const int64_t k0 = t.KS * sp / split, k1 = t.KS * (sp + 1) / split;
-        if (k1 > k0) dens.push_back({i, 0, rt, ct, (int32_t)k0, (int32_t)(k1 - k0), ti, 0});
+        if (k1 > k0) emit(ti0, ti1, k0, k1);
       }
     }
+    ti0 = ti1;
   }
   // force items: particle tile x column tile, with the K range of the column tile (the coefficients beyond are
   // zero), particle-tile-major: the column tiles of one particle tile are claimed together from the queue and

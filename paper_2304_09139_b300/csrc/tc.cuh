@@ -24,6 +24,7 @@ constexpr int kTileM = 128;         // accumulator rows (TMEM lanes)
 constexpr int kTileN = 32;          // accumulator columns per level
 constexpr int kStepK = 16;          // K per MMA instruction (bf16)
 constexpr int kChunkSteps = 16;     // K-steps between exact read-outs (256 products per pair)
+constexpr int kHeldLevels = 7;      // levels 0..6 (at most 7 pairs) are read out after every second chunk
 constexpr int kTmemCols = 512;      // kLevels * kTileN = 480 used
 constexpr uint32_t kSliceA = kTileM * kStepK * 2;   // 4096 bytes: one digit slice of one A K-step
 constexpr uint32_t kSliceB = kTileN * kStepK * 2;   // 1024 bytes: one digit slice of one B K-step
@@ -149,8 +150,25 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// exact integer value of an fp32 accumulator word holding an integer of magnitude below 2^24
+// Exact integer value of an fp32 accumulator word holding an integer x of magnitude below 2^24.  Three forms,
+// so that a read-out can spread its conversions over two pipes (the fp32-to-int unit runs at 16 per clock per SM,
+// an eighth of the fp32 rate):
+//   acc_int       the conversion instruction;
+//   acc_int_fma   on the fp32 pipe: q = rint(x / 4096) from the bits of x 2^-12 + 1.5 2^23 (one rounding, to an
+//                 integer in [2^23, 2^24), where the spacing is 1), r = x - 4096 q exactly (|r| <= 2048), and r from
+//                 the bits of r + 1.5 2^23; x = 4096 q + r, computed modulo 2^32 from the two bit patterns;
+//   acc_int_small for |x| < 2^22 only: the bits of x + 1.5 2^23.
 __device__ __forceinline__ int32_t acc_int(uint32_t bits) { return __float2int_rn(__uint_as_float(bits)); }
+__device__ __forceinline__ int32_t acc_int_fma(uint32_t bits) {
+  const float x = __uint_as_float(bits);
+  const float h = __fmaf_rn(x, 0x1p-12f, kMagic);
+  const float r = __fmaf_rn(__fsub_rn(h, kMagic), -4096.0f, x);
+  const float l = __fadd_rn(r, kMagic);
+  return (int32_t)(__float_as_uint(h) * 4096u + __float_as_uint(l) - (uint32_t)kMagicBits * 4097u);
+}
+__device__ __forceinline__ int32_t acc_int_small(uint32_t bits) {
+  return (int32_t)(__float_as_uint(__fadd_rn(__uint_as_float(bits), kMagic)) - (uint32_t)kMagicBits);
+}
 
 }  // namespace tc
 }  // namespace ssh
