@@ -112,6 +112,8 @@ def parse():
     ap.add_argument("--no-large", action="store_true", help="skip the d=3, N=32768 block")
     ap.add_argument("--no-large-staged", action="store_true", help="skip its staged FP64 -> fixed point quench")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-paper-scale", action="store_true",
+                    help="skip the d=2 N=2x10^6 chi=0.10 step (the context holds about 170 GB)")
     ap.add_argument("--serve-seconds", type=float, default=45.0)
     ap.add_argument("--serve-method", default="lbfgs", choices=["lbfgs", "fire"],
                     help="minimiser of the serving requests")
@@ -403,6 +405,61 @@ def run_reference(args):
     return 0
 
 
+def paper_scale_block(ssh, synth, dev, stream, flush, steps=2, warmup=1):
+    """The paper's system size, d=2, N=2x10^6 at unit density, chi=0.10 (M = 400000, 8x10^11 pairs per sum):
+    one device FIRE step in the default fixed point on the tensor cores, with its per-kernel split and the
+    GEMMs' fractions of the bf16 peak, and the device memory the context holds.  Inputs are far larger than
+    L2; L2 is flushed between steps all the same."""
+    import torch
+    cfg = synth.PAPER_D2
+    torch.cuda.synchronize(dev)
+    free0 = torch.cuda.mem_get_info(dev)[0]
+    ctx = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi, device=dev)
+    try:
+        ctx.set_stream(stream.cuda_stream)
+        ctx.set_positions_frac(synth.positions(cfg.seed, cfg.N, cfg.d))
+        torch.cuda.synchronize(dev)
+        held = free0 - torch.cuda.mem_get_info(dev)[0]
+        pairs = ctx.M * ctx.N
+        fp = ctx.min_defaults()
+        fp.n_stages = 1
+        fp.stage_prec[0] = ssh.FX
+        fp.smax_target = 1e-300
+        fp.max_steps = 1 << 40
+        fp.stall_window[0] = 1 << 40
+        ctx.fire_begin(fp)
+        for _ in range(warmup):
+            ctx.fire_steps(ssh.FX, 1)
+        torch.cuda.synchronize(dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            ctx.fire_steps(ssh.FX, 1)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize(dev)
+        ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+        ctx.prof_enable(True)
+        for _ in range(steps):
+            flush.zero_()
+            ctx.fire_steps(ssh.FX, 1)
+        prof = ctx.prof_read()
+        ctx.prof_enable(False)
+        out = {"workload": f"d=2 N={cfg.N} L={cfg.L:.4f} chi={cfg.chi} M={ctx.M}, uniform random (SplitMix64 seed "
+                           f"{cfg.seed}); one FIRE step in fixed point, L2 flushed between timed steps",
+               "fx_impl": "tensor" if ctx.fx_impl == ssh.FX_TENSOR else "integer",
+               "device_bytes_held": int(held),
+               "step": {"ms": ms, "pairs_per_s": pairs / (ms * 1e-3),
+                        "per_kernel_ms": {k: v[0] / v[1] for k, v in prof.items()}}}
+        if ctx.fx_impl == ssh.FX_TENSOR:
+            fl = tc_flop_per_pair(cfg.d)
+            out["step"]["tensor_frac_of_measured_bf16_peak"] = {
+                k: fl[k] * pairs / (prof[k][0] / prof[k][1] * 1e-3) / BF16_PEAK for k in fl if k in prof}
+        return out
+    finally:
+        ctx.close()
+
+
 def large_d3_block(ssh, synth, dev, stream, flush, steps=5, warmup=3, max_seconds=150.0, staged=True):
     """The d=3, N=32768, chi=0.40 workload (M = 39320): one device FIRE step in the library's default fixed
     point (per-kernel split and tensor roofline), one evaluation in every arithmetic, and full quenches to
@@ -679,6 +736,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_large:
         line["large_d3"] = large_d3_block(ssh, synth, dev, stream, flush, max_seconds=args.minimize_seconds,
                                           staged=not args.no_large_staged)
+    if rank == 0 and world == 1 and not args.no_paper_scale:
+        line["paper_scale"] = paper_scale_block(ssh, synth, dev, stream, flush)
     if rank == 0 and world == 1 and not args.no_serve:
         line["serving"] = serving_block(ssh, synth, dev, window_s=args.serve_seconds, method=args.serve_method)
         line["p50_s"] = line["serving"]["p50_s"]

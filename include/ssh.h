@@ -59,8 +59,8 @@ typedef enum { SSH_FP64 = 0, SSH_DD = 1, SSH_FX = 2 } ssh_prec;
  *                     balanced 7-bit digits per 2^-104 fixed-point value in bf16, fp32 accumulation kept exact by
  *                     bounded read-outs; d = 1 runs on two lifted axes, n = 2^b n_1 + n_2).  A wavevector set
  *                     beyond the path's limits (d = 3 with max |n_2| + max |n_3| above 211, or more than 16384
- *                     distinct (n_2, n_3)) runs on the integer pipes; ssh_get_fx_impl reports which
- *                     implementation a context uses. */
+ *                     distinct (n_2, n_3)), or N above 2^22, runs on the integer pipes; ssh_get_fx_impl reports
+ *                     which implementation a context uses. */
 enum { SSH_FX_AUTO = 0, SSH_FX_INTEGER = 1, SSH_FX_TENSOR = 2 };
 #define SSH_FX_AUTO_TENSOR 1
 

@@ -707,9 +707,20 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
       }
       if (stop) break;
       if (it.kind == 0) {
-        // level groups of every output, R' = st0 2^70 + st1 2^35 + st2 (value = R' 2^-110), added into the
-        // tile's accumulator: integer addition, so the K ranges combine exactly in any order
+        // level groups of every output, R' = st0 2^70 + st1 2^35 + st2 (value = R' 2^-110), normalised so that
+        // st1, st2 lie in [0, 2^35), and added into the tile's accumulator: integer addition, so the K ranges
+        // combine exactly in any order.  The tile's lower groups then stay below (pieces) 2^35 and its top group
+        // near R' 2^-70 <= N 2^40, whatever the digit sums of the pieces were.
         unsigned long long* out = reinterpret_cast<unsigned long long*>(c.tc_acc) + (size_t)it.slot * (3 * kTileN * kTileM);
+#pragma unroll
+        for (int i = 0; i < kEpiCols; i++) {
+          const long long c2 = st[2][i] >> 35;
+          st[2][i] -= c2 * (1ll << 35);
+          st[1][i] += c2;
+          const long long c1 = st[1][i] >> 35;
+          st[1][i] -= c1 * (1ll << 35);
+          st[0][i] += c1;
+        }
 #pragma unroll
         for (int g = 0; g < 3; g++)
 #pragma unroll
@@ -992,7 +1003,8 @@ static cudaError_t tc_dev_alloc(DevBuf* b, size_t bytes, cudaStream_t st) {
   return cudaMemsetAsync(b->p, 0, bytes, st);  // padding rows, columns and K stay zero for good
 }
 
-bool tc_eligible(const Ctx& c) { return c.d >= 1 && c.d <= 3 && c.N >= 1 && c.M >= 1; }
+// N <= 2^22: the top level group of a density tile accumulates about N 2^40 (int64), and n~ stays inside Q34.126
+bool tc_eligible(const Ctx& c) { return c.d >= 1 && c.d <= 3 && c.N >= 1 && c.N <= (1 << 22) && c.M >= 1; }
 
 int64_t tc_coef_blocks(const Ctx& c) {
   if (!c.tc.on) return 0;
