@@ -113,7 +113,7 @@ def parse():
     ap.add_argument("--no-large-staged", action="store_true", help="skip its staged FP64 -> fixed point quench")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-paper-scale", action="store_true",
-                    help="skip the d=2 N=2x10^6 chi=0.10 step (the context holds about 170 GB)")
+                    help="skip the d=2 N=2x10^6 steps at chi=0.10 and 0.40 (each context holds about 200 GB)")
     ap.add_argument("--serve-seconds", type=float, default=45.0)
     ap.add_argument("--serve-method", default="lbfgs", choices=["lbfgs", "fire"],
                     help="minimiser of the serving requests")
@@ -406,12 +406,17 @@ def run_reference(args):
 
 
 def paper_scale_block(ssh, synth, dev, stream, flush, steps=2, warmup=1):
-    """The paper's system size, d=2, N=2x10^6 at unit density, chi=0.10 (M = 400000, 8x10^11 pairs per sum):
-    one device FIRE step in the default fixed point on the tensor cores, with its per-kernel split and the
-    GEMMs' fractions of the bf16 peak, and the device memory the context holds.  Inputs are far larger than
-    L2; L2 is flushed between steps all the same."""
+    """The paper's system size, d=2, N=2x10^6 at unit density, at chi=0.10 (M = 400000, 8x10^11 pairs per sum) and
+    chi=0.40 (M = 1.6x10^6, 3.2x10^12 pairs): one device FIRE step each in the default fixed point on the tensor
+    cores, with the per-kernel split, the GEMMs' fractions of the bf16 peak, the particle chunks the context
+    chose and the device memory it holds.  Inputs are far larger than L2; L2 is flushed between steps all the
+    same."""
+    return {f"chi={cfg.chi:.2f}": paper_scale_step(ssh, synth, cfg, dev, stream, flush, steps, warmup)
+            for cfg in (synth.PAPER_D2, synth.PAPER_D2_CHI40)}
+
+
+def paper_scale_step(ssh, synth, cfg, dev, stream, flush, steps, warmup):
     import torch
-    cfg = synth.PAPER_D2
     torch.cuda.synchronize(dev)
     free0 = torch.cuda.mem_get_info(dev)[0]
     ctx = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi, device=dev)
@@ -445,16 +450,19 @@ def paper_scale_block(ssh, synth, dev, stream, flush, steps=2, warmup=1):
             ctx.fire_steps(ssh.FX, 1)
         prof = ctx.prof_read()
         ctx.prof_enable(False)
+        # per step: a chunked context launches the preparation and both GEMMs once per chunk
+        per_step = {k: v[0] / steps for k, v in prof.items()}
         out = {"workload": f"d=2 N={cfg.N} L={cfg.L:.4f} chi={cfg.chi} M={ctx.M}, uniform random (SplitMix64 seed "
                            f"{cfg.seed}); one FIRE step in fixed point, L2 flushed between timed steps",
                "fx_impl": "tensor" if ctx.fx_impl == ssh.FX_TENSOR else "integer",
+               "particle_chunks": list(ctx.tc_chunks),
                "device_bytes_held": int(held),
-               "step": {"ms": ms, "pairs_per_s": pairs / (ms * 1e-3),
-                        "per_kernel_ms": {k: v[0] / v[1] for k, v in prof.items()}}}
+               "step": {"ms": ms, "pairs_per_s": pairs / (ms * 1e-3), "per_kernel_ms_per_step": per_step,
+                        "launches_per_step": {k: v[1] // steps for k, v in prof.items()}}}
         if ctx.fx_impl == ssh.FX_TENSOR:
             fl = tc_flop_per_pair(cfg.d)
             out["step"]["tensor_frac_of_measured_bf16_peak"] = {
-                k: fl[k] * pairs / (prof[k][0] / prof[k][1] * 1e-3) / BF16_PEAK for k in fl if k in prof}
+                k: fl[k] * pairs / (per_step[k] * 1e-3) / BF16_PEAK for k in fl if k in per_step}
         return out
     finally:
         ctx.close()

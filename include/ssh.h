@@ -67,7 +67,12 @@ enum { SSH_FX_AUTO = 0, SSH_FX_INTEGER = 1, SSH_FX_TENSOR = 2 };
 typedef struct {
   int device;       /* CUDA device ordinal (default 0) */
   int fx_impl;      /* SSH_FX_AUTO (0, default), SSH_FX_INTEGER or SSH_FX_TENSOR */
-  int reserved[6];  /* zero */
+  int tc_chunk;     /* tensor-core path: particles per chunk (0, default: every particle at once when the chunk
+                     * buffers fit in about 70% of the free device memory, else as many equal chunks as needed).
+                     * Chunks run one after another through the same buffers; results do not depend on the
+                     * chunking (the sums are exact integers).  Rounded up to a multiple of 128 and to at most
+                     * 64 chunks. */
+  int reserved[5];  /* zero */
 } ssh_opts;
 
 /* Library version string, e.g. "ssh 0.1 sm_103a". Never NULL. */
@@ -94,6 +99,10 @@ ssh_status ssh_get_dims(const ssh_ctx* ctx, int* d, int64_t* N, int64_t* M, doub
 
 /* The implementation SSH_FX evaluations of this context use: SSH_FX_INTEGER or SSH_FX_TENSOR. */
 ssh_status ssh_get_fx_impl(const ssh_ctx* ctx, int* impl);
+
+/* Particle chunks of the tensor-core path (ssh_opts.tc_chunk): their number and the particles per chunk; both 0
+ * when the context uses the integer pipes.  Either pointer may be NULL. */
+ssh_status ssh_get_tc_chunks(const ssh_ctx* ctx, int* nchunk, int64_t* chunk);
 
 /* The M wavevector indices n (k = 2 pi n / L) in public order: by |n|^2, then lexicographic.
  * n: caller buffer of M*d int32 (row-major), or NULL to query M only. */

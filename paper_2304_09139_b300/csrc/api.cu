@@ -70,6 +70,8 @@ ssh_status ssh_create(int d, int64_t N, double L, double chi, double K, const ss
     return SSH_EINVAL;
   }
   c.tc_requested = fx_impl == SSH_FX_TENSOR || (fx_impl == SSH_FX_AUTO && d <= 3 && SSH_FX_AUTO_TENSOR);
+  c.tc_chunk_req = opts ? opts->tc_chunk : 0;
+  if (c.tc_chunk_req < 0) { delete h; set_error("ssh_create: tc_chunk must be >= 0"); return SSH_EINVAL; }
   if (ssh::build_kset(d, N, L, chi, K, &c.ks) != 0) {
     delete h;
     set_error("ssh_create: could not build the wavevector set");
@@ -136,6 +138,13 @@ ssh_status ssh_get_dims(const ssh_ctx* h, int* d, int64_t* N, int64_t* M, double
 ssh_status ssh_get_fx_impl(const ssh_ctx* h, int* impl) {
   if (!h || !impl) { set_error("ssh_get_fx_impl: NULL argument"); return SSH_EINVAL; }
   *impl = h->c.tc.on ? SSH_FX_TENSOR : SSH_FX_INTEGER;
+  return SSH_OK;
+}
+
+ssh_status ssh_get_tc_chunks(const ssh_ctx* h, int* nchunk, int64_t* chunk) {
+  if (!h) { set_error("ssh_get_tc_chunks: null context"); return SSH_EINVAL; }
+  if (nchunk) *nchunk = h->c.tc.on ? h->c.tc.nchunk : 0;
+  if (chunk) *chunk = h->c.tc.on ? h->c.tc.Nc : 0;
   return SSH_OK;
 }
 

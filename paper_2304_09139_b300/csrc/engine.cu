@@ -152,36 +152,76 @@ cudaError_t engine_build(Engine* e, const std::vector<Ctx*>& members, const std:
     nt_n[p] = (int)e->h_nt.size() - nt_off[p];
     f_n[p] = (int)e->h_f.size() - f_off[p];
   }
-  // tensor-core members (fixed point)
+  // tensor-core members (fixed point), in particle-chunk phases: phase ph holds chunk ph of every member that has
+  // one; chunks after the first get descriptors of their own, after the members'
   std::vector<int> tcl;
   std::vector<TwItem> tcp;
   std::vector<TcItem> tcd, tcf;
   int64_t tc_grid = 0;
   size_t tc_smem = 0;
   int64_t tc_nd = 0;
-  int64_t tc_steps = 0;  // density K-steps of every tensor-core member: each gets its share of the SMs
-  for (int i : lists[SSH_FX])
-    if (members[i]->tc.on) tc_steps += tc_density_steps(members[i]);
+  int nph = 0;
   for (int i : lists[SSH_FX])
     if (members[i]->tc.on) {
       tcl.push_back(i);
-      const int64_t share = (int64_t)((double)e->sm_count * (double)tc_density_steps(members[i]) / (double)std::max<int64_t>(1, tc_steps));
-      tc_items(members[i], i, share, tcp, tcd, tcf);
+      nph = std::max(nph, tc_chunks(members[i]));
       tc_grid = std::max<int64_t>(tc_grid, (int64_t)(members[i]->tc.R1 + 1) * members[i]->tc.nP);
       tc_smem = std::max(tc_smem, members[i]->tc.prep_smem);
       tc_nd = std::max<int64_t>(tc_nd, (int64_t)members[i]->tc.d * members[i]->N);
     }
-  // largest first over all members (the persistent GEMM takes items from a queue in list order): density items
-  // one by one; force items by bundle (the column tiles of one particle tile, kept together so that they share
-  // its digits in L2), bundles by their total K-steps (a stable sort keeps each bundle contiguous and in order)
+  if (nph > kMaxTcPhases) return cudaErrorInvalidValue;
+  std::vector<std::vector<int>> ccfg(n);  // [member][chunk] -> descriptor index
+  for (int i : tcl) {
+    ccfg[i].assign(tc_chunks(members[i]), i);
+    for (int ch = 1; ch < (int)ccfg[i].size(); ch++) {
+      CfgDev g = e->host_cfgs[i];
+      tc_chunk_cfgdev(members[i], ch, &g);
+      ccfg[i][ch] = (int)e->host_cfgs.size();
+      e->host_cfgs.push_back(g);
+    }
+  }
+  TcPhase phs[kMaxTcPhases];
+  std::vector<std::vector<BlockMap>> tab_bm(nph), rtab_bm(nph);
+  // largest first over all members of a phase (the persistent GEMM takes items from a queue in list order):
+  // density items one by one; force items by bundle (the column tiles of one particle tile, kept together so that
+  // they share its digits in L2), bundles by their total K-steps (a stable sort keeps each bundle contiguous and
+  // in order)
   auto by_size = [](const TcItem& a, const TcItem& b) { return a.nks > b.nks; };
-  std::stable_sort(tcd.begin(), tcd.end(), by_size);
-  {
+  for (int ph = 0; ph < nph; ph++) {
+    TcPhase& P = phs[ph];
+    int64_t steps = 0;  // density K-steps of the phase: each member gets its share of the SMs
+    for (int i : tcl)
+      if (tc_chunks(members[i]) > ph) steps += tc_density_steps(members[i], ph);
+    P.prep_off = (int)tcp.size();
+    P.dens_off = (int)tcd.size();
+    P.force_off = (int)tcf.size();
+    for (int i : tcl) {
+      if (tc_chunks(members[i]) <= ph) continue;
+      const int cfg = ccfg[i][ph];
+      for (int64_t b = 0; b < tc_table_blocks(members[i], ph); b++) tab_bm[ph].push_back({cfg, (int32_t)b});
+      tc_prep_items(members[i], cfg, ph, tcp);
+      const int64_t share = (int64_t)((double)e->sm_count * (double)tc_density_steps(members[i], ph) /
+                                      (double)std::max<int64_t>(1, steps));
+      tc_gemm_items(members[i], cfg, ph, share, tcd, tcf);
+    }
+    P.prep_n = (int)tcp.size() - P.prep_off;
+    P.dens_n = (int)tcd.size() - P.dens_off;
+    P.force_n = (int)tcf.size() - P.force_off;
+    std::stable_sort(tcd.begin() + P.dens_off, tcd.end(), by_size);
     std::map<std::pair<int, int>, int64_t> bundle;
-    for (const TcItem& it : tcf) bundle[{it.cfg, it.a}] += it.nks;
-    std::stable_sort(tcf.begin(), tcf.end(), [&](const TcItem& a, const TcItem& b) {
+    for (size_t k = P.force_off; k < tcf.size(); k++) bundle[{tcf[k].cfg, tcf[k].a}] += tcf[k].nks;
+    std::stable_sort(tcf.begin() + P.force_off, tcf.end(), [&](const TcItem& a, const TcItem& b) {
       return bundle[{a.cfg, a.a}] > bundle[{b.cfg, b.a}];
     });
+    // before the force items of this chunk: the preparation again for members whose buffers hold a later chunk
+    P.rprep_off = (int)tcp.size();
+    for (int i : tcl) {
+      if (tc_chunks(members[i]) - 1 <= ph) continue;
+      const int cfg = ccfg[i][ph];
+      for (int64_t b = 0; b < tc_table_blocks(members[i], ph); b++) rtab_bm[ph].push_back({cfg, (int32_t)b});
+      tc_prep_items(members[i], cfg, ph, tcp);
+    }
+    P.rprep_n = (int)tcp.size() - P.rprep_off;
   }
   cudaError_t err;
   if ((err = up(&e->d_tclist, tcl.data(), sizeof(int) * tcl.size(), st)) != cudaSuccess) return err;
@@ -200,8 +240,15 @@ cudaError_t engine_build(Engine* e, const std::vector<Ctx*>& members, const std:
   bm_off[1] = bm.size();
   for (int i = 0; i < n; i++) add_blocks(i, ((int64_t)members[i]->d * members[i]->N + 63) / 64);
   bm_n[1] = bm.size() - bm_off[1];
-  bm_off[2] = bm.size();
-  for (int i : tcl) add_blocks(i, (2 * (int64_t)members[i]->tc.d * members[i]->N + 127) / 128);  // two chains each
+  bm_off[2] = bm.size();  // tables, phase by phase
+  for (int ph = 0; ph < nph; ph++) {
+    phs[ph].tab_off = (int)(bm.size() - bm_off[2]);
+    bm.insert(bm.end(), tab_bm[ph].begin(), tab_bm[ph].end());
+    phs[ph].tab_n = (int)tab_bm[ph].size();
+    phs[ph].rtab_off = (int)(bm.size() - bm_off[2]);
+    bm.insert(bm.end(), rtab_bm[ph].begin(), rtab_bm[ph].end());
+    phs[ph].rtab_n = (int)rtab_bm[ph].size();
+  }
   bm_n[2] = bm.size() - bm_off[2];
   bm_off[3] = bm.size();
   for (int i : tcl) add_blocks(i, tc_finish_blocks(*members[i]));
@@ -218,7 +265,7 @@ cudaError_t engine_build(Engine* e, const std::vector<Ctx*>& members, const std:
   e->nbm_dots = (int)bm_n[0];
   e->bm_nd = dbm + bm_off[1];
   e->nbm_nd = (int)bm_n[1];
-  if ((err = up(&e->d_cfgs, e->host_cfgs.data(), sizeof(CfgDev) * n, st)) != cudaSuccess) return err;
+  if ((err = up(&e->d_cfgs, e->host_cfgs.data(), sizeof(CfgDev) * e->host_cfgs.size(), st)) != cudaSuccess) return err;
   if ((err = up(&e->d_lists, e->h_lists.data(), sizeof(int) * e->h_lists.size(), st)) != cudaSuccess) return err;
   if ((err = up(&e->d_tw, e->h_tw.data(), sizeof(TwItem) * e->h_tw.size(), st)) != cudaSuccess) return err;
   if ((err = up(&e->d_nt, e->h_nt.data(), sizeof(NtItem) * e->h_nt.size(), st)) != cudaSuccess) return err;
@@ -260,6 +307,8 @@ cudaError_t engine_build(Engine* e, const std::vector<Ctx*>& members, const std:
       v.tc_maxND = tc_nd;
       v.tc_bm_tab = dbm + bm_off[2];
       v.ntc_bm_tab = (int)bm_n[2];
+      v.ntc_phase = nph;
+      for (int ph = 0; ph < nph; ph++) v.tc_ph[ph] = phs[ph];
       v.tc_bm_fin = dbm + bm_off[3];
       v.ntc_bm_fin = (int)bm_n[3];
       v.tc_bm_coef = dbm + bm_off[4];

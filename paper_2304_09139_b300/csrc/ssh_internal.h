@@ -88,7 +88,8 @@ struct CfgDev {
   int tc, tc_R1, tc_nP, tc_RT, tc_CTd, tc_PT, tc_KSf, tc_CTf, tc_bexp, tc_nblk, tc_gs, tc_ts, tc_ntab;
   int tc_d, tc_lift;   // the path's number of axes (2 or 3); d = 1 on two lifted axes: n = 2^tc_lift n1 + n2
   int tc_Rax[3];       // per axis: powers 0..tc_Rax[a] in the tables
-  int64_t tc_KS, tc_NJ, tc_NPg;  // density K-steps; particle groups and row groups of the digit tensor
+  int64_t tc_KS, tc_NJ, tc_NPg;  // density K-steps; particle groups and row groups of the digit tensor (a chunk)
+  int64_t tc_j0, tc_n, tc_nbuf;  // this chunk: first particle, particles, particle stride of the chunk buffers
   uint8_t *tc_wT, *tc_aB, *tc_fB;  // digit tensor of w_j(p); density B (a_j(n1)); force B (coefficients)
   void* tc_a1;         // a_j(n1) as signed Q2.126, [n1][j]
   void* tc_tab;        // per (axis, particle): first-quadrant tables e^{2 pi i k s} (k < 8), e^{2 pi i 8 b s}
@@ -128,6 +129,12 @@ struct FItem {
 constexpr int kTwThreads = 128;
 
 // launch view of an engine (device pointers, counts, grid extents) for one precision
+constexpr int kMaxTcPhases = 64;  // particle chunks of a tensor-core member, at most
+struct TcPhase {
+  int tab_off = 0, tab_n = 0, prep_off = 0, prep_n = 0, dens_off = 0, dens_n = 0, force_off = 0, force_n = 0;
+  int rtab_off = 0, rtab_n = 0, rprep_off = 0, rprep_n = 0;  // the preparation again, before the force items
+};
+
 struct EngineView {
   const CfgDev* cfgs = nullptr;
   const int* list = nullptr;  // configurations evaluated in this precision
@@ -152,6 +159,11 @@ struct EngineView {
   int ntc_dens = 0;
   const TcItem* tc_force = nullptr;
   int ntc_force = 0;
+  // particle chunks: phase c runs chunk c of every member that has one (its tables, preparation and density
+  // items), and, in reverse order, its force items, preceded by the preparation again where the member's
+  // buffers no longer hold that chunk.  Offsets index the arrays above (items) and the block maps (tables).
+  int ntc_phase = 0;
+  TcPhase tc_ph[kMaxTcPhases];
   int64_t tc_max_grid = 0;  // largest (R1 + 1) nP of the members
   size_t tc_prep_smem = 0;  // largest preparation shared memory of the members
   int64_t tc_maxND = 0;     // largest (the path's axes) x N of the members (d = 1 runs on two lifted axes)
@@ -231,10 +243,12 @@ struct TcPlan {
   int R1 = 0;                    // n1 in [0, R1]
   int Rax[3] = {0, 0, 0};        // largest |n_a| per axis (powers held in the tables)
   int nP = 0;                    // canonical sub-vectors p = (n2[, n3]) of the half set, sorted by |p|^2
-  int64_t KS = 0;                // density K-steps (16 particles each)
+  int64_t Nc = 0;                // particles per chunk (the buffers below hold one chunk), a multiple of 128
+  int nchunk = 1;                // chunks of N, evaluated one after another
+  int64_t KS = 0;                // density K-steps (16 particles each) of a full chunk
   int RT = 0, CTd = 0;           // density row tiles (128 rows (p, cos/sin)), column tiles (32 columns (n1, cos/sin))
-  int PT = 0, KSf = 0, CTf = 0;  // force particle tiles, K-steps (16 rows (p, cos/sin)), column tiles (16/d n1, all axes)
-  int64_t NJ = 0, NPg = 0;       // digit tensor: particle groups and row groups of 8
+  int PT = 0, KSf = 0, CTf = 0;  // force particle tiles (of a chunk), K-steps (16 rows (p, cos/sin)), column tiles (16/d n1, all axes)
+  int64_t NJ = 0, NPg = 0;       // digit tensor: particle groups (of a chunk) and row groups of 8
   int bexp = 0;                  // 2^bexp > |n_a| (a >= 2): scale of the weighted force coefficients
   int gs = 0, ts = 0;            // force epilogue scales
   std::vector<int32_t> tiles;    // density tiles in use: rt * CTd + ct
@@ -284,6 +298,7 @@ struct Ctx {
   FireBufs* fire = nullptr;       // minimiser state, allocated on first ssh_minimize
   Engine* eng = nullptr;          // this context alone (plain evaluations)
   bool tc_requested = false;      // fixed point on the tensor cores (d = 1, 2, 3)
+  int64_t tc_chunk_req = 0;        // particles per chunk on that path (0: as device memory allows)
   TcPlan tc;
 };
 
@@ -349,9 +364,14 @@ cudaError_t tc_setup(Ctx* c);
 void tc_free(Ctx* c);
 size_t tc_footprint(const Ctx& c);
 void tc_fill_cfgdev(const Ctx* c, CfgDev* g);
-int64_t tc_density_steps(const Ctx* c);  // tiles x K-steps of the density GEMM
-void tc_items(const Ctx* c, int i, int64_t pieces, std::vector<TwItem>& prep, std::vector<TcItem>& dens,
-              std::vector<TcItem>& force);
+// particle chunks of a tensor-core member: their number, the descriptor of chunk ch (from the member's), and the
+// work of one chunk: density K-steps (tiles x K-steps), tables blocks, preparation items, GEMM items
+int tc_chunks(const Ctx* c);
+void tc_chunk_cfgdev(const Ctx* c, int ch, CfgDev* g);
+int64_t tc_density_steps(const Ctx* c, int ch);
+int64_t tc_table_blocks(const Ctx* c, int ch);
+void tc_prep_items(const Ctx* c, int cfg, int ch, std::vector<TwItem>& prep);
+void tc_gemm_items(const Ctx* c, int cfg, int ch, int64_t pieces, std::vector<TcItem>& dens, std::vector<TcItem>& force);
 cudaError_t tc_launch_density(const EngineView& v, cudaStream_t st, Prof* prof);
 cudaError_t tc_launch_force(const EngineView& v, cudaStream_t st, Prof* prof);
 cudaError_t tc_launch_force_finish(const EngineView& v, cudaStream_t st, Prof* prof);

@@ -314,25 +314,26 @@ __device__ __forceinline__ void qent_out(const qent& z, uint4& yre, uint4& yim, 
 // first-quadrant phasors.  Each chain starts from an exact-phase evaluation (e^{2 pi i s}, e^{2 pi i 8 s}) and
 // multiplies on (each product at most 8 units of 2^-126 low, so the error of a power grows linearly in its
 // exponent: far below the 2^-104 digits).
-// Block map over the tensor-core members; layout tc_tab[(axis N + j) tc_ntab + (k | 8 + b)].
+// Block map over the tensor-core members' chunks; layout tc_tab[(axis nbuf + j) tc_ntab + (k | 8 + b)], j within
+// the chunk.
 __global__ void __launch_bounds__(128) k_tc_tables(const CfgDev* __restrict__ cfgs, const BlockMap* __restrict__ bm) {
   grid_dep_wait();
   const BlockMap m = bm[blockIdx.x];
   const CfgDev& c = cfgs[m.cfg];
   if (stopped(c)) return;
-  const int64_t nd = (int64_t)c.tc_d * c.N;
+  const int64_t nd = (int64_t)c.tc_d * c.tc_n;  // this chunk's particles
   const int64_t idx = (int64_t)m.blk * blockDim.x + threadIdx.x;
   if (idx >= 2 * nd) return;
   const int h = idx >= nd ? 1 : 0;
   const int64_t r = idx - h * nd;
-  const int axis = (int)(r / c.N);
-  const int64_t j = r - (int64_t)axis * c.N;
+  const int axis = (int)(r / c.tc_n);
+  const int64_t j = r - (int64_t)axis * c.tc_n;  // within the chunk; particle tc_j0 + j
   const int cnt = h == 0 ? kPrepLow : c.tc_Rax[axis] / kPrepLow + 1;
   // d = 1 lifted to two axes: axis 0 holds the phase 2^lift s (mod 1, exact), axis 1 the phase s
   const int src = c.tc_lift ? 0 : axis;
-  q128 u = turns_from_dd(c.s_hi[src * c.N + j], c.s_lo[src * c.N + j]);
+  q128 u = turns_from_dd(c.s_hi[src * c.N + c.tc_j0 + j], c.s_lo[src * c.N + c.tc_j0 + j]);
   if (c.tc_lift && axis == 0) u = turn_times(u, 1 << c.tc_lift);
-  qent* tab = reinterpret_cast<qent*>(c.tc_tab) + r * c.tc_ntab + (h == 0 ? 0 : kPrepLow);
+  qent* tab = reinterpret_cast<qent*>(c.tc_tab) + ((int64_t)axis * c.tc_nbuf + j) * c.tc_ntab + (h == 0 ? 0 : kPrepLow);
   // e^0 = 1 exactly (the exact-phase evaluation returns (2^126, 0) at t = 0): c = 1 in Q1.127, s = 0, quadrant 0
   qent x;
   x.c = q128_zero();
@@ -365,7 +366,8 @@ __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restri
   if (stopped(c)) return;
   const int kind = it.pad & 0xff, ng = it.pad >> 9;  // particle groups of 8
   const bool staged = (it.pad >> 8) & 1;
-  const int64_t N = c.N;
+  const int64_t N = c.tc_n;                 // this chunk's particles (indices within the chunk)
+  const int64_t Npad = (N + 15) & ~(int64_t)15;  // groups up to the K-step boundary are written (zeros past N)
   const int64_t j0 = it.start;
   const int tid = threadIdx.x, lane = tid & 31, h = lane & 1;
   const __int128 bias = digit_bias();
@@ -383,7 +385,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restri
         const int64_t j = min(j0 + jl, N - 1);  // entries of particles past N are never read
         const int axis = e < W2 ? 1 : 2;
         const int m = e < W2 ? e : e - W2;
-        const qent* tj = tab + ((int64_t)axis * N + j) * c.tc_ntab;
+        const qent* tj = tab + ((int64_t)axis * c.tc_nbuf + j) * c.tc_ntab;
         Pw[jl * W23 + e] = qmul(tj[kPrepLow + (m >> 3)], tj[m & 7]);
       }
     }
@@ -397,7 +399,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restri
     const bool valid = q < total;
     const int e = valid ? q % count : 0, g = valid ? q / count : 0;
     const int64_t jg = j0 + 8 * g;
-    const bool live = valid && jg < N;  // particle groups past the last particle stay zero
+    const bool live = valid && jg < Npad;  // digits of particles past the last one are written as zeros
     int m = e, n2 = 0, n3 = 0;
     if (kind == 1) {
       const int32_t pv = pvs[e];
@@ -419,13 +421,13 @@ __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restri
           const qent b = pj[n2 < 0 ? -n2 : n2];
           z = qmul(n2 < 0 ? qconj(b) : b, pj[W2 + n3]);
         } else {
-          const qent* tj = tab + ((int64_t)axis * N + j) * c.tc_ntab;
+          const qent* tj = tab + ((int64_t)axis * c.tc_nbuf + j) * c.tc_ntab;
           z = qmul(tj[kPrepLow + (m >> 3)], tj[m & 7]);
         }
         if (kind == 0) {
           fxc zq;
           qent_out(z, Yr[v], Yi[v], &zq);
-          reinterpret_cast<fxc*>(c.tc_a1)[(int64_t)e * N + j] = zq;
+          reinterpret_cast<fxc*>(c.tc_a1)[(int64_t)e * c.tc_nbuf + j] = zq;
         } else {
           qent_out(z, Yr[v], Yi[v], nullptr);
         }
@@ -738,7 +740,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
         for (int v = 0; v < kEpiCols / 2; v++) {
           const int i = (kEpiCols / 2) * hq + v;
           const int n1 = npt * it.b + i / d, t = i - (i / d) * d;
-          if (i >= npt * d || n1 > c.tc_R1 || j >= c.N) continue;
+          if (i >= npt * d || n1 > c.tc_R1 || j >= c.tc_n) continue;
           q128 gre, gim;
           {
             const __int128 Rr = ((__int128)st[0][2 * v] << 70) + ((__int128)st[1][2 * v] << 35) + (__int128)st[2][2 * v];
@@ -747,7 +749,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
             gre = q128_from_i128(Rr << gsh);
             gim = q128_from_i128(Ri << gsh);
           }
-          const fxc a = reinterpret_cast<const fxc*>(c.tc_a1)[(int64_t)n1 * c.N + j];
+          const fxc a = reinterpret_cast<const fxc*>(c.tc_a1)[(int64_t)n1 * c.tc_nbuf + j];
           uint32_t p[5], r2[5];
           // Im(a G) = Re a Im G + Im a Re G
           smul_top(a.re, gim, p);
@@ -758,12 +760,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
           else if (t == 1) F1 += T;
           else F2 += T;
         }
-        if (j < c.N) {
+        if (j < c.tc_n) {
           // F = L2 2^88 + L1 2^44 + L0 (L0, L1 in [0, 2^44)): the limbs of all column tiles add up exactly
           const unsigned long long m44 = (1ull << 44) - 1;
           for (int t = 0; t < d; t++) {
             const __int128 F = t == 0 ? F0 : (t == 1 ? F1 : F2);
-            unsigned long long* fa = reinterpret_cast<unsigned long long*>(c.tc_facc) + (size_t)t * 3 * c.N + j;
+            unsigned long long* fa = reinterpret_cast<unsigned long long*>(c.tc_facc) + (size_t)t * 3 * c.N + c.tc_j0 + j;
             atomicAdd(fa, (unsigned long long)F & m44);
             atomicAdd(fa + c.N, (unsigned long long)(F >> 44) & m44);
             atomicAdd(fa + 2 * c.N, (unsigned long long)(long long)(F >> 88));
@@ -1162,14 +1164,11 @@ cudaError_t tc_setup(Ctx* c) {
   t.pvec.resize(nP);
   for (int i = 0; i < nP; i++) t.pvec[i] = (int32_t)((uint32_t)(plist[i].first & 0xffff) | ((uint32_t)plist[i].second << 16));
   const int W1 = R1 + 1;
-  t.KS = (c->N + kStepK - 1) / kStepK;
-  t.PT = (int)((c->N + kTileM - 1) / kTileM);
   t.RT = (2 * nP + kTileM - 1) / kTileM;
   t.CTd = (2 * W1 + kTileN - 1) / kTileN;
   t.KSf = (2 * nP + kStepK - 1) / kStepK;
   const int npt = 16 / d;  // force column tile: n1 in [npt ct, npt ct + npt), every axis of each (2 d columns per n1)
   t.CTf = (W1 + npt - 1) / npt;
-  t.NJ = (int64_t)t.PT * (kTileM / 8);
   t.NPg = (int64_t)t.RT * (kTileM / 8);
   t.bexp = 0;
   while ((1 << t.bexp) <= std::max(R2, R3)) t.bexp++;
@@ -1198,13 +1197,40 @@ cudaError_t tc_setup(Ctx* c) {
   const int nt = (int)t.tiles.size();
 
   t.ntab = kPrepLow + std::max(R1, std::max(R2, R3)) / kPrepLow + 1;
+  // particles per chunk.  The digit tensor, the density B digits, the Q2.126 a_j(n1) and the tables hold one
+  // chunk; the density sums run over the chunks into the same exact accumulators and the force rows of a chunk
+  // are its own particles, so the results do not depend on the chunking.  By default every particle is one
+  // chunk when these buffers fit in 70% of the free device memory.
+  {
+    const double bpp = (double)kDigits * t.NPg * 16 + (double)t.CTd * kStageB / kStepK + (double)W1 * sizeof(fxc) +
+                       (double)d * t.ntab * sizeof(qent);  // bytes per particle of the chunk buffers
+    const int64_t Nr = (c->N + kTileM - 1) / kTileM * kTileM;
+    int64_t Nc = Nr;
+    if (c->tc_chunk_req > 0) {
+      Nc = c->tc_chunk_req;
+    } else {
+      size_t fr = 0, tot = 0;
+      if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && bpp * (double)Nr > 0.7 * (double)fr) {
+        const int64_t nch = (int64_t)std::ceil(bpp * (double)Nr / (0.7 * (double)fr));
+        Nc = (c->N + nch - 1) / nch;
+      }
+    }
+    const int64_t Nmin = (c->N + kMaxTcPhases - 1) / kMaxTcPhases;  // at most kMaxTcPhases chunks
+    Nc = std::max(Nc, Nmin);
+    Nc = std::min((Nc + kTileM - 1) / kTileM * kTileM, Nr);
+    t.Nc = Nc;
+    t.nchunk = (int)((c->N + Nc - 1) / Nc);
+  }
+  t.KS = t.Nc / kStepK;
+  t.PT = (int)(t.Nc / kTileM);
+  t.NJ = (int64_t)t.PT * (kTileM / 8);
   cudaStream_t st = c->stream;
   cudaError_t e;
   if ((e = tc_dev_alloc(&t.wT, (size_t)kDigits * t.NPg * t.NJ * 128, st)) != cudaSuccess) return e;
   if ((e = tc_dev_alloc(&t.aB, (size_t)t.CTd * t.KS * kStageB, st)) != cudaSuccess) return e;
   if ((e = tc_dev_alloc(&t.fB, (size_t)t.CTf * t.KSf * kStageB, st)) != cudaSuccess) return e;
-  if ((e = tc_dev_alloc(&t.a1, (size_t)W1 * c->N * sizeof(fxc), st)) != cudaSuccess) return e;
-  if ((e = tc_dev_alloc(&t.tab, (size_t)d * c->N * t.ntab * sizeof(qent), st)) != cudaSuccess) return e;
+  if ((e = tc_dev_alloc(&t.a1, (size_t)W1 * t.Nc * sizeof(fxc), st)) != cudaSuccess) return e;
+  if ((e = tc_dev_alloc(&t.tab, (size_t)d * t.Nc * t.ntab * sizeof(qent), st)) != cudaSuccess) return e;
   if ((e = tc_dev_alloc(&t.acc, (size_t)nt * 3 * kTileN * kTileM * 8, st)) != cudaSuccess) return e;
   if ((e = tc_dev_alloc(&t.facc, (size_t)d * 3 * c->N * 8, st)) != cudaSuccess) return e;
   if ((e = tc_dev_alloc(&t.em_d, t.em.size() * 4, st)) != cudaSuccess) return e;
@@ -1284,6 +1310,9 @@ void tc_fill_cfgdev(const Ctx* c, CfgDev* g) {
   g->tc_KS = t.KS;
   g->tc_NJ = t.NJ;
   g->tc_NPg = t.NPg;
+  g->tc_j0 = 0;  // chunk 0 (tc_chunk_cfgdev for the others)
+  g->tc_n = std::min<int64_t>(c->N, t.Nc);
+  g->tc_nbuf = t.Nc;
   g->tc_wT = (uint8_t*)t.wT.p;
   g->tc_aB = (uint8_t*)t.aB.p;
   g->tc_fB = (uint8_t*)t.fB.p;
@@ -1303,24 +1332,45 @@ void tc_fill_cfgdev(const Ctx* c, CfgDev* g) {
   g->psplit[SSH_FX] = 1;
 }
 
-// work items of one member (engine member index i)
-int64_t tc_density_steps(const Ctx* c) { return c->tc.on ? (int64_t)c->tc.tiles.size() * c->tc.KS : 0; }
+int tc_chunks(const Ctx* c) { return c->tc.on ? c->tc.nchunk : 0; }
 
-// work items of one member (engine member index i); pieces: the density pieces this member should be cut into
-// (about its share of the SMs)
-void tc_items(const Ctx* c, int i, int64_t pieces, std::vector<TwItem>& prep, std::vector<TcItem>& dens,
-              std::vector<TcItem>& force) {
+static int64_t chunk_len(const Ctx* c, int ch) { return std::min<int64_t>(c->tc.Nc, c->N - (int64_t)ch * c->tc.Nc); }
+
+void tc_chunk_cfgdev(const Ctx* c, int ch, CfgDev* g) {
+  g->tc_j0 = (int64_t)ch * c->tc.Nc;
+  g->tc_n = chunk_len(c, ch);
+}
+
+// density K-steps (tiles x K-steps) of one chunk
+int64_t tc_density_steps(const Ctx* c, int ch) {
+  return c->tc.on ? (int64_t)c->tc.tiles.size() * ((chunk_len(c, ch) + kStepK - 1) / kStepK) : 0;
+}
+
+// blocks (128 threads) of the tables kernel for one chunk: two threads per (axis, particle)
+int64_t tc_table_blocks(const Ctx* c, int ch) { return (2 * (int64_t)c->tc.d * chunk_len(c, ch) + 127) / 128; }
+
+// preparation items of one chunk (cfg: its descriptor in the engine), the heavier w items first.  d = 3 w items
+// cover 16 particles (their powers fill shared memory); a table item covers enough groups of 8 particles for 128
+// (entry, group) lane pairs, at most 128 particles.  They reach the chunk's last K-step boundary, so that stale
+// digits of an earlier, longer chunk never enter the density sums.
+void tc_prep_items(const Ctx* c, int cfg, int ch, std::vector<TwItem>& prep) {
   const TcPlan& t = c->tc;
-  // the heavier w items first.  d = 3 w items cover 16 particles (their powers fill shared memory); a table
-  // item covers enough groups of 8 particles for 128 (entry, group) lane pairs, at most 128 particles
+  const int64_t npad = (chunk_len(c, ch) + kStepK - 1) / kStepK * kStepK;
   for (int kind = 1; kind >= 0; kind--) {
     const int count = kind == 0 ? t.R1 + 1 : t.nP;
     const bool staged = kind == 1 && t.d == 3;
     int ng = staged ? kPrepStaged / 8 : 1;
     if (!staged)
       while (ng < kPrepTable / 8 && ng * count < kPrepThreads / 2) ng *= 2;
-    for (int64_t j = 0; j < c->N; j += 8 * ng) prep.push_back({i, kind | (staged ? 1 << 8 : 0) | (ng << 9), j});
+    for (int64_t j = 0; j < npad; j += 8 * ng) prep.push_back({cfg, kind | (staged ? 1 << 8 : 0) | (ng << 9), j});
   }
+}
+
+// GEMM items of one chunk; pieces: the density pieces this chunk should be cut into (about its share of the SMs)
+void tc_gemm_items(const Ctx* c, int cfg, int ch, int64_t pieces, std::vector<TcItem>& dens, std::vector<TcItem>& force) {
+  const TcPlan& t = c->tc;
+  const int64_t n = chunk_len(c, ch);
+  const int64_t KS = (n + kStepK - 1) / kStepK;
   // density pieces.  The column tiles of a row tile read the same rows of w, so their pieces share K ranges and
   // sit next to each other in the list: CTAs claim them together and the second read of each w stage hits L2.
   // Each row tile splits uniformly into `split` K ranges (at most one per read-out chunk); when the tiles do not
@@ -1329,30 +1379,30 @@ void tc_items(const Ctx* c, int i, int64_t pieces, std::vector<TwItem>& prep, st
   // tile's end).  A piece holds at most 1024 read-outs, so the int64 level groups (below 2^52 per read-out)
   // cannot overflow.
   const int64_t nt = (int64_t)t.tiles.size();
-  const int64_t total = nt * t.KS;
+  const int64_t total = nt * KS;
   const int64_t want = std::max<int64_t>(1, pieces);
   const int64_t len = std::min<int64_t>(1024 * kChunkSteps, std::max<int64_t>(1, (total + want - 1) / want));
   const bool cross = want > nt && want % nt != 0 && len >= 8 * kChunkSteps;
-  int64_t split = std::max<int64_t>(1, std::min<int64_t>((t.KS + kChunkSteps - 1) / kChunkSteps, want / nt));
-  split = std::max<int64_t>(split, (t.KS + 1024 * kChunkSteps - 1) / (1024 * kChunkSteps));
+  int64_t split = std::max<int64_t>(1, std::min<int64_t>((KS + kChunkSteps - 1) / kChunkSteps, want / nt));
+  split = std::max<int64_t>(split, (KS + 1024 * kChunkSteps - 1) / (1024 * kChunkSteps));
   auto emit = [&](int ti0, int ti1, int64_t k0, int64_t k1) {  // one piece per column tile of the row tile
     for (int ti = ti0; ti < ti1; ti++)
-      dens.push_back({i, 0, t.tiles[ti] / t.CTd, t.tiles[ti] % t.CTd, (int32_t)k0, (int32_t)(k1 - k0), ti, 0});
+      dens.push_back({cfg, 0, t.tiles[ti] / t.CTd, t.tiles[ti] % t.CTd, (int32_t)k0, (int32_t)(k1 - k0), ti, 0});
   };
   int64_t g0 = 0;  // K-steps of the row tiles before this one (cut grid)
   for (int ti0 = 0; ti0 < (int)nt;) {
     int ti1 = ti0;  // tiles are listed row tile by row tile
     while (ti1 < (int)nt && t.tiles[ti1] / t.CTd == t.tiles[ti0] / t.CTd) ti1++;
     if (cross) {
-      for (int64_t k0 = 0; k0 < t.KS;) {  // cut where the global K-step g0 + k reaches a multiple of len
-        const int64_t k1 = std::min<int64_t>(t.KS, k0 + (len - (g0 + k0) % len));
+      for (int64_t k0 = 0; k0 < KS;) {  // cut where the global K-step g0 + k reaches a multiple of len
+        const int64_t k1 = std::min<int64_t>(KS, k0 + (len - (g0 + k0) % len));
         emit(ti0, ti1, k0, k1);
         k0 = k1;
       }
-      g0 += t.KS;
+      g0 += KS;
     } else {
       for (int64_t sp = 0; sp < split; sp++) {
-        const int64_t k0 = t.KS * sp / split, k1 = t.KS * (sp + 1) / split;
+        const int64_t k0 = KS * sp / split, k1 = KS * (sp + 1) / split;
         if (k1 > k0) emit(ti0, ti1, k0, k1);
       }
     }
@@ -1361,9 +1411,10 @@ void tc_items(const Ctx* c, int i, int64_t pieces, std::vector<TwItem>& prep, st
   // force items: particle tile x column tile, with the K range of the column tile (the coefficients beyond are
   // zero), particle-tile-major: the column tiles of one particle tile are claimed together from the queue and
   // read the particle tile's digits from L2 once they are in
-  for (int pt = 0; pt < t.PT; pt++)
+  const int PT = (int)((n + kTileM - 1) / kTileM);
+  for (int pt = 0; pt < PT; pt++)
     for (int ct = 0; ct < t.CTf; ct++)
-      if (t.ks_ct[ct] > 0) force.push_back({i, 1, pt, ct, 0, t.ks_ct[ct], ct, 0});
+      if (t.ks_ct[ct] > 0) force.push_back({cfg, 1, pt, ct, 0, t.ks_ct[ct], ct, 0});
 }
 
 size_t tc_gemm_smem() { return kGemmSmem; }
@@ -1377,39 +1428,68 @@ cudaError_t tc_launch_force_finish(const EngineView& v, cudaStream_t st, Prof* p
   return cudaGetLastError();
 }
 
+static cudaError_t launch_tables_prep(const EngineView& v, int tab_off, int tab_n, int prep_off, int prep_n,
+                                      cudaStream_t st, Prof* prof) {
+  if (tab_n > 0) {
+    prof_begin(prof, st, kKTcTables);
+    const cudaError_t le =
+        launch_pdl(k_tc_tables, dim3((unsigned)tab_n), dim3(128), 0, st, v.cfgs, v.tc_bm_tab + tab_off);
+    if (le != cudaSuccess) return le;
+    prof_end(prof, st);
+  }
+  if (prep_n > 0) {
+    prof_begin(prof, st, kKTcPrep);
+    const cudaError_t le =
+        launch_pdl(k_tc_prep, dim3((unsigned)prep_n), dim3(kPrepThreads), v.tc_prep_smem, st, v.cfgs, v.tc_prep + prep_off);
+    if (le != cudaSuccess) return le;
+    prof_end(prof, st);
+  }
+  return cudaSuccess;
+}
+
+// chunk by chunk: tables, preparation, density GEMM (into the exact tile accumulators); then the finish
 cudaError_t tc_launch_density(const EngineView& v, cudaStream_t st, Prof* prof) {
   if (v.ntc_list == 0) return cudaSuccess;
-  prof_begin(prof, st, kKTcTables);
-  cudaError_t le = launch_pdl(k_tc_tables, dim3((unsigned)v.ntc_bm_tab), dim3(128), 0, st, v.cfgs, v.tc_bm_tab);
-  if (le != cudaSuccess) return le;
-  prof_end(prof, st);
-  prof_begin(prof, st, kKTcPrep);
-  le = launch_pdl(k_tc_prep, dim3((unsigned)v.ntc_prep), dim3(kPrepThreads), v.tc_prep_smem, st, v.cfgs, v.tc_prep);
-  if (le != cudaSuccess) return le;
-  prof_end(prof, st);
-  prof_begin(prof, st, kKTcDens);
-  le = launch_pdl(k_tc_gemm, dim3((unsigned)std::min(v.ntc_dens, v.sm_count)), dim3(kGemmThreads), kGemmSmem, st, v.cfgs,
-                  v.tc_dens, v.ntc_dens, v.counters + 2);
-  if (le != cudaSuccess) return le;
-  prof_end(prof, st);
+  for (int ph = 0; ph < v.ntc_phase; ph++) {
+    const TcPhase& P = v.tc_ph[ph];
+    cudaError_t le = launch_tables_prep(v, P.tab_off, P.tab_n, P.prep_off, P.prep_n, st, prof);
+    if (le != cudaSuccess) return le;
+    if (P.dens_n > 0) {
+      prof_begin(prof, st, kKTcDens);
+      le = launch_pdl(k_tc_gemm, dim3((unsigned)std::min(P.dens_n, v.sm_count)), dim3(kGemmThreads), kGemmSmem, st,
+                      v.cfgs, v.tc_dens + P.dens_off, P.dens_n, v.counters + 2);
+      if (le != cudaSuccess) return le;
+      prof_end(prof, st);
+    }
+  }
   prof_begin(prof, st, kKTcFinish);
-  le = launch_pdl(k_tc_dens_finish, dim3((unsigned)v.ntc_bm_fin), dim3(kFinThreads), 0, st, v.cfgs, v.tc_bm_fin);
+  const cudaError_t le =
+      launch_pdl(k_tc_dens_finish, dim3((unsigned)v.ntc_bm_fin), dim3(kFinThreads), 0, st, v.cfgs, v.tc_bm_fin);
   if (le != cudaSuccess) return le;
   prof_end(prof, st);
   return cudaGetLastError();
 }
 
+// the coefficients, then chunk by chunk in reverse order (the last chunk's digits are still in the buffers): the
+// preparation again where needed, and the force GEMM
 cudaError_t tc_launch_force(const EngineView& v, cudaStream_t st, Prof* prof) {
   if (v.ntc_list == 0) return cudaSuccess;
   prof_begin(prof, st, kKTcCoef);
   cudaError_t le = launch_pdl(k_tc_coef, dim3((unsigned)v.ntc_bm_coef), dim3(128), 0, st, v.cfgs, v.tc_bm_coef);
   if (le != cudaSuccess) return le;
   prof_end(prof, st);
-  prof_begin(prof, st, kKTcForce);
-  le = launch_pdl(k_tc_gemm, dim3((unsigned)std::min(v.ntc_force, v.sm_count)), dim3(kGemmThreads), kGemmSmem, st, v.cfgs,
-                  v.tc_force, v.ntc_force, v.counters + 4);
-  if (le != cudaSuccess) return le;
-  prof_end(prof, st);
+  for (int ph = v.ntc_phase - 1; ph >= 0; ph--) {
+    const TcPhase& P = v.tc_ph[ph];
+    le = launch_tables_prep(v, P.rtab_off, P.rtab_n, P.rprep_off, P.rprep_n, st, prof);
+    if (le != cudaSuccess) return le;
+    if (P.force_n > 0) {
+      prof_begin(prof, st, kKTcForce);
+      le = launch_pdl(k_tc_gemm, dim3((unsigned)std::min(P.force_n, v.sm_count)), dim3(kGemmThreads), kGemmSmem, st,
+                      v.cfgs, v.tc_force + P.force_off, P.force_n, v.counters + 4);
+      if (le != cudaSuccess) return le;
+      prof_end(prof, st);
+    }
+  }
   return cudaGetLastError();
 }
 

@@ -113,6 +113,7 @@ def load():
             _sig(lib, "ssh_get_dims", c_int, [c_vp, P(c_int), P(c_i64), P(c_i64), P(c_d)])
             _sig(lib, "ssh_get_kset", c_int, [c_vp, P(c_i64), P(c_i32)])
             _sig(lib, "ssh_get_fx_impl", c_int, [c_vp, P(c_int)])
+            _sig(lib, "ssh_get_tc_chunks", c_int, [c_vp, P(c_int), P(c_i64)])
             _sig(lib, "ssh_kset_build", c_int, [c_int, c_i64, c_d, c_d, c_d, c_i64, P(c_i32), P(c_i64)])
             _sig(lib, "ssh_set_stream", c_int, [c_vp, c_vp])
             _sig(lib, "ssh_sync", c_int, [c_vp])
@@ -196,13 +197,13 @@ class Context:
     """One configuration (d, N, L, chi | K) resident on the GPU.  Wraps ssh_create / ssh_destroy."""
 
     def __init__(self, d: int, N: int, L: float, chi: float = 0.0, K: float = 0.0, device: int = 0,
-                 fx_impl: int = 0, _handle=None):
+                 fx_impl: int = 0, tc_chunk: int = 0, _handle=None):
         lib = load()
         self._lib = lib
         self._owned = _handle is None
         self._h = c_vp()
         if _handle is None:
-            opts = (c_int * 8)(device, fx_impl, 0, 0, 0, 0, 0, 0)
+            opts = (c_int * 8)(device, fx_impl, tc_chunk, 0, 0, 0, 0, 0)  # ssh_opts
             _check(lib.ssh_create(d, N, L, chi, K, ctypes.cast(opts, c_vp), ctypes.byref(self._h)))
         else:
             self._h = _handle
@@ -237,6 +238,13 @@ class Context:
         v = ctypes.c_int()
         _check(self._lib.ssh_get_fx_impl(self._h, ctypes.byref(v)))
         return v.value
+
+    @property
+    def tc_chunks(self) -> tuple[int, int]:
+        """(number of particle chunks, particles per chunk) of the tensor-core path; (0, 0) on the integer pipes."""
+        n, c = c_int(), c_i64()
+        _check(self._lib.ssh_get_tc_chunks(self._h, ctypes.byref(n), ctypes.byref(c)))
+        return n.value, c.value
 
     def kset(self) -> np.ndarray:
         out = np.zeros((max(self.M, 1), self.d), dtype=np.int32)

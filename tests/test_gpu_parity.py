@@ -267,3 +267,37 @@ def test_bad_inputs_raise(built):
     assert e.value.status == 4
     with pytest.raises(ssh.SshError):
         ctx.eval(7)
+
+
+@pytest.mark.parametrize("d,N,L,chi,chunk", [(2, 10_000, 100.0, 0.45, 2048), (3, 3000, 3000 ** (1 / 3), 0.30, 1024),
+                                              (1, 5000, 5000.0, 0.30, 1280)])
+def test_chunked_equals_unchunked(built, d, N, L, chi, chunk):
+    """Particle chunks on the tensor-core path (ssh_opts.tc_chunk; the last chunk ragged, not a whole number of
+    K-steps): the sums are exact integers, so n~, Phi, S_max and F are bit-identical to one chunk, and so is a
+    FIRE segment."""
+    s = synth.positions(77 + d, N, d)
+    out = {}
+    for ch in (0, chunk):
+        ctx = ssh.Context(d, N, L, chi=chi, fx_impl=ssh.FX_TENSOR, tc_chunk=ch)
+        nc, size = ctx.tc_chunks
+        if ch:
+            assert size == chunk and nc == -(-N // chunk) and nc > 1
+        else:
+            assert nc == 1
+        ctx.set_positions_frac(s)
+        r = ctx.energy_grad(ssh.FX)
+        C, S = ctx.ntilde()
+        fp = ctx.min_defaults()
+        fp.n_stages = 1
+        fp.stage_prec[0] = ssh.FX
+        fp.smax_target = 1e-300
+        fp.max_steps = 1 << 40
+        ctx.fire_begin(fp)
+        ctx.fire_steps(ssh.FX, 20)
+        out[ch] = (r, C, S, ctx.positions_frac())
+        ctx.close()
+    (ra, Ca, Sa, pa), (rb, Cb, Sb, pb) = out[0], out[chunk]
+    for k in ("phi", "smax", "F_hi", "F_lo"):
+        assert np.array_equal(ra[k], rb[k]), k
+    assert np.array_equal(Ca, Cb) and np.array_equal(Sa, Sb)
+    assert all(np.array_equal(x, y) for x, y in zip(pa, pb))
