@@ -100,6 +100,14 @@ ssh_status ssh_get_dims(const ssh_ctx* ctx, int* d, int64_t* N, int64_t* M, doub
 /* The implementation SSH_FX evaluations of this context use: SSH_FX_INTEGER or SSH_FX_TENSOR. */
 ssh_status ssh_get_fx_impl(const ssh_ctx* ctx, int* impl);
 
+/* Weights v~(k) of the wavevectors (the paper's general positive v~(k), which funnel the minimiser to chosen
+ * ground states): Phi = sum_k v~(k) |n~(k)|^2 and F = -grad Phi; S(k) and S_max do not change.  w holds M values
+ * in the order of ssh_get_kset, each finite and in [0, 1024]; NULL restores 1 for every wavevector (the
+ * default).  Weight 1 keeps the exact integer force coefficients of the fixed-point paths; other weights enter
+ * them through a double-double product (relative error 2^-105).  Stream-ordered; takes effect at the next
+ * evaluation.  Errors: SSH_EINVAL. */
+ssh_status ssh_set_weights(ssh_ctx* ctx, const double* w);
+
 /* Particle chunks of the tensor-core path (ssh_opts.tc_chunk): their number and the particles per chunk; both 0
  * when the context uses the integer pipes.  Either pointer may be NULL. */
 ssh_status ssh_get_tc_chunks(const ssh_ctx* ctx, int* nchunk, int64_t* chunk);

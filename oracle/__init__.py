@@ -61,6 +61,9 @@ def _load():
             lib.oracle_phi_grad.restype = ctypes.c_int
             lib.oracle_phi_grad.argtypes = [ctypes.c_int, i64, d, P(d), P(d), i64, P(i32), P(d), P(d), P(d),
                                             P(d), P(d), ctypes.c_int]
+            lib.oracle_phi_grad_w.restype = ctypes.c_int
+            lib.oracle_phi_grad_w.argtypes = [ctypes.c_int, i64, d, P(d), P(d), i64, P(i32), P(d), P(d), P(d), P(d),
+                                              P(d), P(d), ctypes.c_int]
             lib.oracle_fire.restype = ctypes.c_int
             lib.oracle_fire.argtypes = [ctypes.c_int, i64, d, P(d), P(d), i64, P(i32), P(FireParams), P(i64),
                                         P(d), P(d), ctypes.c_int]
@@ -120,8 +123,10 @@ def ntilde(s_hi, s_lo, n, nthreads: int = 0):
     return C[:M], S[:M]
 
 
-def phi_grad(s_hi, s_lo, n, L: float, want_force: bool = True, want_cs: bool = False, nthreads: int = 0):
-    """Phi (Eq. energy, constant dropped), S_max (Eq. smax) and F (Eq. force) in binary128.
+def phi_grad(s_hi, s_lo, n, L: float, want_force: bool = True, want_cs: bool = False, nthreads: int = 0,
+             weights=None):
+    """Phi (Eq. energy, constant dropped), S_max (Eq. smax) and F (Eq. force) in binary128, optionally with a
+    weight v~(k) >= 0 per wavevector (Phi = sum v~ |n~|^2, F = -grad Phi, S unweighted).
 
     Returns a dict with 'phi' and 'smax' as (hi, lo) pairs, 'F' as an [N, d, 2] array (or None), and
     'C', 'S' as [M, 2] arrays when want_cs.
@@ -135,8 +140,9 @@ def phi_grad(s_hi, s_lo, n, L: float, want_force: bool = True, want_cs: bool = F
     F = np.zeros((max(N, 1), d, 2)) if want_force else None
     C = np.zeros((max(M, 1), 2)) if want_cs else None
     S = np.zeros((max(M, 1), 2)) if want_cs else None
-    rc = _load().oracle_phi_grad(d, N, L, _dp(s_hi), _dp(s_lo), M, _ip(n), _dp(phi), _dp(smax), _dp(F), _dp(C),
-                                 _dp(S), nthreads)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64).reshape(M)
+    rc = _load().oracle_phi_grad_w(d, N, L, _dp(s_hi), _dp(s_lo), M, _ip(n), _dp(w), _dp(phi), _dp(smax), _dp(F),
+                                   _dp(C), _dp(S), nthreads)
     if rc != 0:
         raise RuntimeError(f"oracle_phi_grad rc={rc}")
     out = {"phi": phi, "smax": smax, "F": None if F is None else F[:N]}

@@ -14,6 +14,8 @@
  *   Phi, S(k), S_max -- Phi = sum over the half-space of |n~(k)|^2 (constant term dropped, eps0 = 1),
  *                       S(k) = |n~(k)|^2 / N, S_max = max S(k)              (Eqs. energy, structurefactor, smax)
  *   F_j              -- F_j = -grad_j Phi                                   (Eq. force)
+ *   weights          -- a general non-negative v~(k) per wavevector (the paper's v~(k) > 0 that selects
+ *                       ground states): Phi = sum v~ |n~|^2, F = -grad Phi; S(k) is unweighted (Eqs. energy, force)
  *   FIRE             -- Bitzek et al. 2006 structural relaxation, the minimiser the paper uses (Simulations)
  *
  * Conventions (readings of the paper, restated here so the file stands alone):
@@ -208,9 +210,10 @@ int oracle_ntilde(int d, int64_t N, const double *s_hi, const double *s_lo, int6
 
 /* Phi, S_max and F.  Any output pointer may be NULL.  F_out is [N][d][2] (hi, lo).
  * Sum orders: Phi over k ascending; F_j over k ascending; each C_k over j ascending. */
-int oracle_phi_grad(int d, int64_t N, double L, const double *s_hi, const double *s_lo, int64_t M,
-                    const int32_t *n, double *phi, double *smax, double *F_out, double *C_out, double *S_out,
-                    int nthreads) {
+/* Phi, S_max, F with per-wavevector weights w (NULL: every weight 1) */
+int oracle_phi_grad_w(int d, int64_t N, double L, const double *s_hi, const double *s_lo, int64_t M,
+                      const int32_t *n, const double *w, double *phi, double *smax, double *F_out, double *C_out,
+                      double *S_out, int nthreads) {
   if (d < 1 || d > 4 || N < 0 || M < 0 || !(L > 0)) return -1;
   set_threads(nthreads);
   q_t *C = (q_t *)malloc(sizeof(q_t) * (size_t)(M > 0 ? M : 1));
@@ -219,7 +222,7 @@ int oracle_phi_grad(int d, int64_t N, double L, const double *s_hi, const double
   q_t P = 0, smx = 0;
   for (int64_t k = 0; k < M; k++) {
     q_t a2 = C[k] * C[k] + S[k] * S[k];
-    P += a2;
+    P += (w ? (q_t)w[k] : (q_t)1) * a2;
     q_t sk = N > 0 ? a2 / (q_t)N : 0;
     if (sk > smx) smx = sk;
   }
@@ -238,8 +241,8 @@ int oracle_phi_grad(int d, int64_t N, double L, const double *s_hi, const double
         q_t c, s;
         q_t t = phase_turns(d, n + k * d, s_hi + j * d, s_lo ? s_lo + j * d : NULL);
         cos_sin_turns(t, &c, &s);
-        q_t w = C[k] * s - S[k] * c;
-        for (int a = 0; a < d; a++) f[a] += (q_t)n[k * d + a] * w;
+        q_t t2 = (w ? (q_t)w[k] : (q_t)1) * (C[k] * s - S[k] * c);
+        for (int a = 0; a < d; a++) f[a] += (q_t)n[k * d + a] * t2;
       }
       for (int a = 0; a < d; a++) q_to_dd(pref * f[a], &F_out[(j * d + a) * 2], &F_out[(j * d + a) * 2 + 1]);
     }
@@ -247,6 +250,12 @@ int oracle_phi_grad(int d, int64_t N, double L, const double *s_hi, const double
   free(C);
   free(S);
   return 0;
+}
+
+int oracle_phi_grad(int d, int64_t N, double L, const double *s_hi, const double *s_lo, int64_t M,
+                    const int32_t *n, double *phi, double *smax, double *F_out, double *C_out, double *S_out,
+                    int nthreads) {
+  return oracle_phi_grad_w(d, N, L, s_hi, s_lo, M, n, NULL, phi, smax, F_out, C_out, S_out, nthreads);
 }
 
 /* ---------------------------------------------------------------- FIRE (Bitzek et al. 2006) */

@@ -117,7 +117,7 @@ void ssh_destroy(ssh_ctx* h) {
   }
   ssh::tc_free(&c);
   for (ssh::DevBuf* b : {&c.s_hi, &c.s_lo, &c.rows, &c.slots, &c.blocks, &c.grows, &c.cols, &c.fsplit, &c.tab, &c.part,
-                         &c.C_hi, &c.C_lo, &c.S_hi, &c.S_lo, &c.coef, &c.blk, &c.scal, &c.fpart, &c.F_hi, &c.F_lo})
+                         &c.C_hi, &c.C_lo, &c.S_hi, &c.S_lo, &c.wk, &c.coef, &c.blk, &c.scal, &c.fpart, &c.F_hi, &c.F_lo})
     free_buf(*b);
   if (h->h_stage) cudaFreeHost(h->h_stage);
   for (ssh::ProfRec& r : c.prof.pending) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
@@ -138,6 +138,30 @@ ssh_status ssh_get_dims(const ssh_ctx* h, int* d, int64_t* N, int64_t* M, double
 ssh_status ssh_get_fx_impl(const ssh_ctx* h, int* impl) {
   if (!h || !impl) { set_error("ssh_get_fx_impl: NULL argument"); return SSH_EINVAL; }
   *impl = h->c.tc.on ? SSH_FX_TENSOR : SSH_FX_INTEGER;
+  return SSH_OK;
+}
+
+ssh_status ssh_set_weights(ssh_ctx* h, const double* w) {
+  if (!h) { set_error("ssh_set_weights: NULL context"); return SSH_EINVAL; }
+  ssh::Ctx& c = h->c;
+  const int64_t M = c.M;
+  if (M == 0) return SSH_OK;
+  std::vector<double> wi((size_t)M, 1.0);  // internal order
+  double wmax = 1.0;
+  if (w) {
+    wmax = 0.0;
+    for (int64_t k = 0; k < M; k++) {
+      const double x = w[c.ks.int2pub[k]];
+      if (!(x >= 0.0 && x <= 1024.0)) { set_error("ssh_set_weights: weights must be finite, in [0, 1024]"); return SSH_EINVAL; }
+      wi[k] = x;
+      wmax = std::max(wmax, x);
+    }
+  }
+  cudaSetDevice(c.device);
+  SSH_CUDA(cudaMemcpyAsync(c.wk.p, wi.data(), sizeof(double) * M, cudaMemcpyHostToDevice, c.stream), "ssh_set_weights");
+  SSH_CUDA(cudaStreamSynchronize(c.stream), "ssh_set_weights");  // the host vector goes out of scope
+  c.wmax = wmax;
+  c.have_result = false;
   return SSH_OK;
 }
 

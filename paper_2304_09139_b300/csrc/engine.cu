@@ -42,6 +42,7 @@ CfgDev make_cfgdev(const Ctx* c, bool fire_mode) {
   g.slots = (const NtSlot*)c->slots.p;
   g.blocks = (const NtBlock*)c->blocks.p;
   g.g_rows = (const int32_t*)c->grows.p;
+  g.wk = (const double*)c->wk.p;
   g.cols = (const FCol*)c->cols.p;
   g.fsplit = (const int32_t*)c->fsplit.p;
   g.tab = c->tab.p;

@@ -366,13 +366,13 @@ FireState fire_params(const ssh_min_params* p) {
 }
 
 // Phi = sum_k |n~_k|^2 with every n~ off by at most eps N: |dPhi| <= 2 eps N sum |n~| + M (eps N)^2, below
-// 2 eps N sqrt(M Phi) + M (eps N)^2.  eps: 2^-100 for the tensor-core digits and for double-double, 2^-120 for
+// 2 eps N sqrt(M Phi) + M (eps N)^2; with weights v~(k), sum_k v~ |n~|^2, it is below 2 eps N sqrt(M max v~ Phi).  eps: 2^-100 for the tensor-core digits and for double-double, 2^-120 for
 // the integer-pipe fixed point; FP64 keeps the strict test (its steps are rejected on any rise).
 double fire_phi_tol(const Ctx* c, int prec) {
   double eps = 0.0;
   if (prec == SSH_FX) eps = c->tc.on ? 0x1p-100 : 0x1p-120;
   else if (prec == SSH_DD) eps = 0x1p-100;
-  return 2.0 * eps * (double)c->N * sqrt((double)c->M);
+  return 2.0 * eps * (double)c->N * sqrt((double)c->M * c->wmax);
 }
 
 // One FIRE step of every member of e as stream work.

@@ -409,11 +409,13 @@ __global__ void __launch_bounds__(kRedThreads) k_nt_reduce(const CfgDev* __restr
     c.S_hi[k] = ss.hi;
     c.S_lo[k] = ss.lo;
     dd a2 = dd_add(dd_sqr(cc), dd_sqr(ss));
-    v.phi_hi = a2.hi;
-    v.phi_lo = a2.lo;
+    const double w = c.wk[k];  // Phi and the force coefficients carry the weight; S_max does not
+    const dd wa2 = w == 1.0 ? a2 : dd_mul_d(a2, w);
+    v.phi_hi = wa2.hi;
+    v.phi_lo = wa2.lo;
     v.a2max_hi = a2.hi;
     v.a2max_lo = a2.lo;
-    v.cmax = fmax(fabs(cc.hi), fabs(ss.hi));
+    v.cmax = w * fmax(fabs(cc.hi), fabs(ss.hi));
   }
   block_reduce(v, sh);
   if (threadIdx.x == 0) reinterpret_cast<RedPart*>(c.blk)[blockIdx.x] = v;
@@ -439,8 +441,13 @@ __global__ void k_coef(const CfgDev* __restrict__ cfgs, const int* __restrict__ 
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= c.M) return;
   const int e = (int)c.scal[kScScaleExp];
-  reinterpret_cast<typename P::Coef*>(c.coef)[k] =
-      P::make_coef(dd_make(c.C_hi[k], c.C_lo[k]), dd_make(c.S_hi[k], c.S_lo[k]), e);
+  const double w = c.wk[k];
+  dd C = dd_make(c.C_hi[k], c.C_lo[k]), S = dd_make(c.S_hi[k], c.S_lo[k]);
+  if (w != 1.0) {
+    C = dd_mul_d(C, w);
+    S = dd_mul_d(S, w);
+  }
+  reinterpret_cast<typename P::Coef*>(c.coef)[k] = P::make_coef(C, S, e);
 }
 
 __device__ __forceinline__ int floordiv_d(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
@@ -843,6 +850,13 @@ cudaError_t plan_upload(Ctx* c) {
   if ((e = dev_alloc(&c->part, (size_t)max_ps * c->M * kAccBytes)) != cudaSuccess) return e;
   for (DevBuf* b : {&c->C_hi, &c->C_lo, &c->S_hi, &c->S_lo})
     if ((e = dev_alloc(b, (size_t)c->M * 8)) != cudaSuccess) return e;
+  {
+    const std::vector<double> ones((size_t)std::max<int64_t>(c->M, 1), 1.0);
+    if ((e = dev_alloc(&c->wk, ones.size() * 8)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(c->wk.p, ones.data(), ones.size() * 8, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;  // the host vector goes out of scope
+    c->wmax = 1.0;
+  }
   if ((e = dev_alloc(&c->coef, (size_t)c->M * kTabBytes)) != cudaSuccess) return e;
   if ((e = tc_setup(c)) != cudaSuccess) return e;
   c->n_red_blocks = (int)((c->M + kRedThreads - 1) / kRedThreads);

@@ -78,6 +78,7 @@ struct CfgDev {
   void* tab;
   void* part;
   double *C_hi, *C_lo, *S_hi, *S_lo;
+  const double* wk;  // [M] internal order: the weight v~(k) of each wavevector in Phi and F (1 by default)
   void* coef;
   void* blk;
   double* scal;
@@ -282,6 +283,8 @@ struct Ctx {
   DevBuf tab;                  // [nrows][Npad] table entries
   DevBuf part;                 // [psplit][M] partial sums
   DevBuf C_hi, C_lo, S_hi, S_lo;  // [M] internal order
+  DevBuf wk;                   // [M] internal order: weights v~(k) (ssh_set_weights), 1 by default
+  double wmax = 1.0;           // the largest weight (the energy guard's error bound scales with it)
   DevBuf coef;                 // [M]
   DevBuf blk;                  // per reduce block partials
   DevBuf scal;                 // scalars (see k_finalize)

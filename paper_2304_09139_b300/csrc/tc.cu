@@ -172,6 +172,20 @@ __device__ __forceinline__ q160 i192_to_q160_shl(const i192& a, int sh) {
   return r;
 }
 
+// a += round(x 2^126) for a double with |x| < 2^33 (round half up; terms below 2^-190 are dropped)
+__device__ __forceinline__ void i192_add_double_126(i192& a, double x) {
+  if (x == 0.0) return;
+  int ex;
+  const double fr = frexp(x, &ex);                 // x = fr 2^ex, 1/2 <= |fr| < 1
+  const long long m = (long long)ldexp(fr, 53);     // exact: x = m 2^(ex - 53)
+  const int sh = ex - 53 + 126;
+  if (sh >= 0) {
+    i192_add_shl(a, (__int128)m, sh);
+  } else if (sh > -62) {
+    i192_add_shl(a, (__int128)((m + (1ll << (-sh - 1))) >> (-sh)), 0);
+  }
+}
+
 // 2^e as a double (normal range)
 __device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
 
@@ -850,21 +864,38 @@ __global__ void __launch_bounds__(kFinThreads) k_tc_dens_finish(const CfgDev* __
       i192_add_shl(C, (__int128)P[0][g] + (neg ? (__int128)P[3][g] : -(__int128)P[3][g]), sh);
       i192_add_shl(S, (__int128)P[1][g] + (neg ? -(__int128)P[2][g] : (__int128)P[2][g]), sh);
     }
-    FxAcc o;
-    o.re = i192_to_q160_shl(C, 16);  // value 2^-110 -> Q34.126
-    o.im = i192_to_q160_shl(S, 16);
-    part[k] = o;
     const dd cd = i192_to_dd(C, 110), sd = i192_to_dd(S, 110);
     c.C_hi[k] = cd.hi;
     c.C_lo[k] = cd.lo;
     c.S_hi[k] = sd.hi;
     c.S_lo[k] = sd.lo;
+    // the force coefficients take the weighted value v~(k) n~(k): exact for weight 1, else v~ n~ in dd (relative
+    // error 2^-105) rounded to Q34.126
+    const double w = c.wk[k];
+    FxAcc o;
+    if (w == 1.0) {
+      o.re = i192_to_q160_shl(C, 16);  // value 2^-110 -> Q34.126
+      o.im = i192_to_q160_shl(S, 16);
+    } else {
+      const dd wc = dd_mul_d(cd, w), ws = dd_mul_d(sd, w);
+      i192 X, Y;
+      i192_zero(X);
+      i192_zero(Y);
+      i192_add_double_126(X, wc.hi);
+      i192_add_double_126(X, wc.lo);
+      i192_add_double_126(Y, ws.hi);
+      i192_add_double_126(Y, ws.lo);
+      o.re = i192_to_q160_shl(X, 0);
+      o.im = i192_to_q160_shl(Y, 0);
+    }
+    part[k] = o;
     const dd a2 = dd_add(dd_sqr(cd), dd_sqr(sd));
-    v.phi_hi = a2.hi;
-    v.phi_lo = a2.lo;
+    const dd wa2 = w == 1.0 ? a2 : dd_mul_d(a2, w);
+    v.phi_hi = wa2.hi;
+    v.phi_lo = wa2.lo;
     v.a2max_hi = a2.hi;
     v.a2max_lo = a2.lo;
-    v.cmax = fmax(fabs(cd.hi), fabs(sd.hi));
+    v.cmax = w * fmax(fabs(cd.hi), fabs(sd.hi));
   }
   red_warp(v);
   __shared__ RedPart sh[kFinThreads / 32];

@@ -114,6 +114,7 @@ def load():
             _sig(lib, "ssh_get_kset", c_int, [c_vp, P(c_i64), P(c_i32)])
             _sig(lib, "ssh_get_fx_impl", c_int, [c_vp, P(c_int)])
             _sig(lib, "ssh_get_tc_chunks", c_int, [c_vp, P(c_int), P(c_i64)])
+            _sig(lib, "ssh_set_weights", c_int, [c_vp, P(c_d)])
             _sig(lib, "ssh_kset_build", c_int, [c_int, c_i64, c_d, c_d, c_d, c_i64, P(c_i32), P(c_i64)])
             _sig(lib, "ssh_set_stream", c_int, [c_vp, c_vp])
             _sig(lib, "ssh_sync", c_int, [c_vp])
@@ -238,6 +239,16 @@ class Context:
         v = ctypes.c_int()
         _check(self._lib.ssh_get_fx_impl(self._h, ctypes.byref(v)))
         return v.value
+
+    def set_weights(self, w=None):
+        """Weights v~(k) in the order of kset() (None: all 1): Phi = sum v~ |n~|^2 and F = -grad Phi."""
+        if w is None:
+            _check(self._lib.ssh_set_weights(self._h, None))
+        else:
+            w = np.ascontiguousarray(w, dtype=np.float64)
+            if w.shape != (self.M,):
+                raise ValueError(f"need {self.M} weights")
+            _check(self._lib.ssh_set_weights(self._h, _dp(w)))
 
     @property
     def tc_chunks(self) -> tuple[int, int]:

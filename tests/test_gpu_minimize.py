@@ -202,3 +202,19 @@ def test_medium_d2_lbfgs(built, oracle_mod):
     sm, _ = oracle_smax(oracle_mod, ctx, hi, lo)
     assert sm <= 1.01e-36, (sm, r)
     ctx.close()
+
+
+@pytest.mark.parametrize("method", [ssh.MIN_FIRE, ssh.MIN_LBFGS])
+def test_weighted_quench_converges(built, oracle_mod, method):
+    """With weights v~(k) in [0.25, 4] the weighted energy still has its minima at n~ = 0 on the set: both
+    minimisers reach S_max <= 1e-36, confirmed by the binary128 oracle."""
+    cfg = synth.SMALL_D2
+    ctx = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi)
+    ctx.set_positions_frac(synth.positions(cfg.seed, cfg.N, cfg.d))
+    ctx.set_weights(0.25 + 3.75 * synth.uniform01(55, ctx.M))
+    r = ctx.minimize(method=method, max_steps=40000)
+    assert r["status"] == 0, r
+    hi, lo = ctx.positions_frac()
+    sm, _ = oracle_smax(oracle_mod, ctx, hi, lo)
+    assert sm <= 1.01e-36, (sm, r)
+    ctx.close()

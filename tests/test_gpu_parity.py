@@ -301,3 +301,52 @@ def test_chunked_equals_unchunked(built, d, N, L, chi, chunk):
         assert np.array_equal(ra[k], rb[k]), k
     assert np.array_equal(Ca, Cb) and np.array_equal(Sa, Sb)
     assert all(np.array_equal(x, y) for x, y in zip(pa, pb))
+
+
+@pytest.mark.parametrize("d,N,L,chi", [(1, 300, 300.0, 0.45), (2, 500, 500 ** 0.5, 0.45), (3, 400, 400 ** (1 / 3), 0.40),
+                                       (4, 120, 120 ** 0.25, 0.30)])
+def test_weighted_parity(built, oracle_mod, d, N, L, chi):
+    """Weights v~(k) in [0.25, 4] (every seventh exactly 1, which keeps the exact coefficient path): Phi = sum
+    v~ |n~|^2 and F against the oracle in every arithmetic and both fixed-point implementations; n~ and S_max
+    carry no weight.  The force bound weights each wavevector's term by its v~."""
+    s = synth.positions(90 + d, N, d)
+    ref = None
+    for impl, precs in impls(d):
+        ctx = ssh.Context(d, N, L, chi=chi, fx_impl=impl)
+        n = ctx.kset()
+        w = 0.25 + 3.75 * synth.uniform01(40 + d, len(n))
+        w[::7] = 1.0
+        if ref is None:
+            ref = oracle_mod.phi_grad(s, None, n, L, want_cs=True, weights=w, nthreads=NTHREADS)
+        ctx.set_positions_frac(s)
+        ctx.set_weights(w)
+        M = len(n)
+        for prec in precs:
+            tol = TOL[prec]
+            r = ctx.energy_grad(prec)
+            C, S = ctx.ntilde()
+            assert np.all(np.abs(ddiff(C, ref["C"])) <= tol * N) and np.all(np.abs(ddiff(S, ref["S"])) <= tol * N)
+            assert abs(ddiff(r["phi"], ref["phi"])) <= tol * 4 * w.max() * max(ddv(ref["phi"]), M * N), (prec, impl)
+            sm = ddv(ref["smax"])
+            assert abs(ddiff(r["smax"], ref["smax"])) <= tol * 4 * (2 * math.sqrt(N * sm) + 1)
+            Cabs = np.abs(ddv(ref["C"])) + np.abs(ddv(ref["S"])) + math.sqrt(N)
+            scale = tol * 4 * math.pi / L * (np.abs(n).astype(np.float64) * (w * Cabs)[:, None]).sum(0)
+            F = np.stack([r["F_hi"], r["F_lo"]], -1)
+            err = np.abs(ddiff(F, ref["F"]))
+            assert np.all(err <= scale[None, :]), (prec, impl, (err / scale[None, :]).max())
+        # back to unit weights: the unweighted results again
+        ctx.set_weights(None)
+        r1 = ctx.energy_grad(ssh.FX)
+        ref1 = oracle_mod.phi_grad(s, None, n, L, want_force=False, nthreads=NTHREADS)
+        assert abs(ddiff(r1["phi"], ref1["phi"])) <= 1e-28 * 4 * max(ddv(ref1["phi"]), M * N)
+        ctx.close()
+
+
+def test_weights_rejected_when_out_of_range(built):
+    ctx = ssh.Context(2, 100, 1.0, chi=0.3)
+    for bad in (-1.0, float("nan"), 2000.0):
+        w = np.ones(ctx.M)
+        w[3] = bad
+        with pytest.raises(ssh.SshError):
+            ctx.set_weights(w)
+    ctx.close()

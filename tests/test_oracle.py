@@ -280,3 +280,45 @@ def test_fire_quench_reaches_stealthy_ground_state(oracle_mod):
     r = oracle_mod.phi_grad(sh, sl, n, cfg.L, want_force=False)
     assert dd(r["smax"]) <= 1e-36
     assert dd(r["phi"]) <= len(n) * cfg.N * 1e-36   # Phi = N sum_k S(k) <= N M S_max
+
+
+# ------------------------------------------------------------------ weights v~(k) (Eqs. energy and force)
+
+def test_weights_indicator_equals_smaller_set(oracle_mod):
+    """Weight 1 on the first m wavevectors of the ordered set and 0 on the rest gives exactly the energy and force
+    of the first m alone (a zero weight adds exact zeros), and weight 1 everywhere gives the unweighted values."""
+    cfg = synth.SMALL_D2
+    s = synth.positions(cfg.seed, cfg.N, cfg.d)
+    n = oracle_mod.kset(cfg.d, cfg.N, cfg.L, chi=cfg.chi)
+    m = 23
+    w = np.zeros(len(n))
+    w[:m] = 1.0
+    a = oracle_mod.phi_grad(s, None, n, cfg.L, weights=w)
+    b = oracle_mod.phi_grad(s, None, n[:m], cfg.L)
+    assert np.array_equal(a["phi"], b["phi"]) and np.array_equal(a["F"], b["F"])
+    full = oracle_mod.phi_grad(s, None, n, cfg.L)
+    ones = oracle_mod.phi_grad(s, None, n, cfg.L, weights=np.ones(len(n)))
+    assert np.array_equal(full["phi"], ones["phi"]) and np.array_equal(full["F"], ones["F"])
+    assert np.array_equal(full["smax"], a["smax"])  # S(k) carries no weight
+
+
+def test_weighted_finite_differences(oracle_mod):
+    """With weights in [0.5, 2], F = -grad of the weighted Phi: central differences converge at second order."""
+    cfg = synth.SMALL_D2
+    s = synth.positions(cfg.seed, cfg.N, cfg.d)
+    n = oracle_mod.kset(cfg.d, cfg.N, cfg.L, chi=cfg.chi)
+    w = 0.5 + 1.5 * synth.uniform01(31, len(n))
+    F = dd(oracle_mod.phi_grad(s, None, n, cfg.L, weights=w)["F"])
+    for j, a in [(3, 0), (50, 1)]:
+        errs = []
+        for h in (1e-5, 5e-6):
+            lo_p = np.zeros_like(s)
+            lo_m = np.zeros_like(s)
+            lo_p[j, a] = h
+            lo_m[j, a] = -h
+            pp = oracle_mod.phi_grad(s, lo_p, n, cfg.L, want_force=False, weights=w)["phi"]
+            pm = oracle_mod.phi_grad(s, lo_m, n, cfg.L, want_force=False, weights=w)["phi"]
+            diff = (mp_dd(pp) - mp_dd(pm)) / (2 * h)
+            errs.append(float(abs(diff + cfg.L * F[j, a])))
+        assert errs[0] < 1e-6 * abs(cfg.L * F[j, a]) + 1e-3
+        assert 3.0 < errs[0] / errs[1] < 5.0, errs
