@@ -112,9 +112,25 @@ ssh_status ssh_set_weights(ssh_ctx* ctx, const double* w);
  * when the context uses the integer pipes.  Either pointer may be NULL. */
 ssh_status ssh_get_tc_chunks(const ssh_ctx* ctx, int* nchunk, int64_t* chunk);
 
-/* The M wavevector indices n (k = 2 pi n / L) in public order: by |n|^2, then lexicographic.
- * n: caller buffer of M*d int32 (row-major), or NULL to query M only. */
+/* The M wavevector indices n (k = 2 pi n / L) in public order: by |n|^2, then lexicographic (a context of
+ * ssh_create_kset: the order of its list).  n: caller buffer of M*d int32 (row-major), or NULL to query M only. */
 ssh_status ssh_get_kset(const ssh_ctx* ctx, int64_t* M, int32_t* n);
+
+/* A context over a given wavevector set instead of the ball (the paper's other exclusion regions, e.g. the
+ * anisotropic ones of ssh_kset_build_region): M distinct vectors n (row-major [M][d] int32), each in the half
+ * space (first non-zero component positive) with |n_a| <= 32767.  Public order is the list's.  Otherwise as
+ * ssh_create (d, N, L, opts).  Errors: SSH_EINVAL (a vector out of the half space, repeated or out of range),
+ * SSH_ECUDA, SSH_ENOMEM. */
+ssh_status ssh_create_kset(int d, int64_t N, double L, int64_t M, const int32_t* n, const ssh_opts* opts,
+                           ssh_ctx** out);
+
+/* Host only: the wavevectors of an anisotropic exclusion region sum_a w_a n_a^2 <= R^2 (w: d integers in
+ * [1, 2^20]; NULL: the ball, as ssh_kset_build).  K mode: every half-space n with that norm at most
+ * (K L / 2 pi)^2 (1 + 1e-12); chi mode: the first M = round-half-even(chi d (N - 1)) in the order (norm, then
+ * lexicographic on the signed components), which is also the list's order.  n: cap rows of d int32 or NULL
+ * to query M.  Errors: SSH_EINVAL (bad arguments, cap < M with M still written). */
+ssh_status ssh_kset_build_region(int d, int64_t N, double L, double chi, double K, const int32_t* w, int64_t cap,
+                                 int32_t* n, int64_t* M);
 
 /* Host only (no GPU needed): the wavevector set that ssh_create would build for these arguments, in public
  * order.  n: caller buffer of cap rows of d int32, or NULL to query M.  Errors: SSH_EINVAL for bad

@@ -16,6 +16,7 @@ minimised states are judged by S_max only.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -101,6 +102,42 @@ def kset(d: int, N: int, L: float, chi: float = 0.0, K: float = 0.0) -> np.ndarr
     if rc != 0:
         raise RuntimeError(f"oracle_kset failed rc={rc}")
     return out[:M.value].copy()
+
+
+def kset_region(d: int, N: int, L: float, axis_weights, chi: float = 0.0, K: float = 0.0) -> np.ndarray:
+    """An anisotropic exclusion region by brute force (Definitions, with the ball |n|^2 <= R^2 replaced by
+    sum_a w_a n_a^2 <= R^2): the half-space vectors (first non-zero component positive) of the region, ordered by
+    that norm, then lexicographically; K mode keeps every one with norm <= (K L / 2 pi)^2 (1 + 1e-12), chi mode
+    the first round-half-even(chi d (N - 1))."""
+    import itertools
+    import mpmath
+    w = np.asarray(axis_weights, dtype=np.int64).reshape(d)
+
+    def region(r2):
+        R = [int(math.isqrt(r2 // int(w[a]))) + 1 for a in range(d)]
+        pts = np.array(list(itertools.product(*[range(-R[a], R[a] + 1) for a in range(d)])), dtype=np.int64)
+        q = (pts ** 2 * w[None, :]).sum(1)
+        nz = pts != 0
+        first = pts[np.arange(len(pts)), np.argmax(nz, axis=1)]
+        keep = (q <= r2) & nz.any(1) & (first > 0)
+        pts, q = pts[keep], q[keep]
+        order = np.lexsort(tuple(pts[:, a] for a in range(d - 1, -1, -1)) + (q,))
+        return pts[order]
+
+    if K > 0:
+        with mpmath.workdps(40):
+            r2 = int(mpmath.floor((mpmath.mpf(K) * L / (2 * mpmath.pi)) ** 2 * (1 + mpmath.mpf("1e-12"))))
+        out = region(r2)
+    else:
+        M = chi_to_m(d, N, chi)
+        r2 = 1
+        while True:
+            out = region(r2)
+            if len(out) >= M:
+                break
+            r2 *= 2
+        out = out[:M]
+    return out.astype(np.int32)
 
 
 def _pos(s_hi, s_lo, d):

@@ -44,17 +44,8 @@ const char* ssh_version(void) { return "ssh 0.1 sm_103a"; }
 
 const char* ssh_last_error(void) { return ssh::g_err.c_str(); }
 
-ssh_status ssh_create(int d, int64_t N, double L, double chi, double K, const ssh_opts* opts, ssh_ctx** out) {
-  if (!out) { set_error("ssh_create: out is NULL"); return SSH_EINVAL; }
-  *out = nullptr;
-  if (d < 1 || d > ssh::kMaxDim) { set_error("ssh_create: d must be 1..4"); return SSH_EINVAL; }
-  if (N < 1 || N > (int64_t)1 << 31) { set_error("ssh_create: N must be in [1, 2^31]"); return SSH_EINVAL; }
-  if (!(L > 0) || !isfinite(L)) { set_error("ssh_create: L must be positive and finite"); return SSH_EINVAL; }
-  if (!isfinite(chi) || !isfinite(K) || chi < 0 || K < 0 || (chi > 0) == (K > 0)) {
-    set_error("ssh_create: give exactly one of chi > 0 or K > 0");
-    return SSH_EINVAL;
-  }
-  if (chi >= 1.0) { set_error("ssh_create: chi must be < 1"); return SSH_EINVAL; }
+// The context of a built wavevector set (ks moves in); argument checks of d, N, L and the set done by the caller.
+static ssh_status create_from(int d, int64_t N, double L, ssh::KSet&& ks, const ssh_opts* opts, ssh_ctx** out) {
   ssh_ctx* h = new (std::nothrow) ssh_ctx();
   if (!h) { set_error("ssh_create: out of host memory"); return SSH_ENOMEM; }
   ssh::Ctx& c = h->c;
@@ -72,11 +63,7 @@ ssh_status ssh_create(int d, int64_t N, double L, double chi, double K, const ss
   c.tc_requested = fx_impl == SSH_FX_TENSOR || (fx_impl == SSH_FX_AUTO && d <= 3 && SSH_FX_AUTO_TENSOR);
   c.tc_chunk_req = opts ? opts->tc_chunk : 0;
   if (c.tc_chunk_req < 0) { delete h; set_error("ssh_create: tc_chunk must be >= 0"); return SSH_EINVAL; }
-  if (ssh::build_kset(d, N, L, chi, K, &c.ks) != 0) {
-    delete h;
-    set_error("ssh_create: could not build the wavevector set");
-    return SSH_EINVAL;
-  }
+  c.ks = std::move(ks);
   c.M = c.ks.M;
   if (c.M > (int64_t)1 << 30) { delete h; set_error("ssh_create: M too large"); return SSH_EINVAL; }
   c.tl = ssh::build_table_layout(c.ks);
@@ -101,6 +88,65 @@ ssh_status ssh_create(int d, int64_t N, double L, double chi, double K, const ss
                                           : cuda_fail(e, "ssh_create: set-up");
   }
   *out = h;
+  return SSH_OK;
+}
+
+static bool check_dnl(const char* fn, int d, int64_t N, double L) {
+  if (d < 1 || d > ssh::kMaxDim) { set_error(std::string(fn) + ": d must be 1..4"); return false; }
+  if (N < 1 || N > (int64_t)1 << 31) { set_error(std::string(fn) + ": N must be in [1, 2^31]"); return false; }
+  if (!(L > 0) || !isfinite(L)) { set_error(std::string(fn) + ": L must be positive and finite"); return false; }
+  return true;
+}
+
+static bool check_mode(const char* fn, double chi, double K) {
+  if (!isfinite(chi) || !isfinite(K) || chi < 0 || K < 0 || (chi > 0) == (K > 0)) {
+    set_error(std::string(fn) + ": give exactly one of chi > 0 or K > 0");
+    return false;
+  }
+  if (chi >= 1.0) { set_error(std::string(fn) + ": chi must be < 1"); return false; }
+  return true;
+}
+
+ssh_status ssh_create(int d, int64_t N, double L, double chi, double K, const ssh_opts* opts, ssh_ctx** out) {
+  if (!out) { set_error("ssh_create: out is NULL"); return SSH_EINVAL; }
+  *out = nullptr;
+  if (!check_dnl("ssh_create", d, N, L) || !check_mode("ssh_create", chi, K)) return SSH_EINVAL;
+  ssh::KSet ks;
+  if (ssh::build_kset(d, N, L, chi, K, &ks) != 0) {
+    set_error("ssh_create: could not build the wavevector set");
+    return SSH_EINVAL;
+  }
+  return create_from(d, N, L, std::move(ks), opts, out);
+}
+
+ssh_status ssh_create_kset(int d, int64_t N, double L, int64_t M, const int32_t* n, const ssh_opts* opts, ssh_ctx** out) {
+  if (!out) { set_error("ssh_create_kset: out is NULL"); return SSH_EINVAL; }
+  *out = nullptr;
+  if (!check_dnl("ssh_create_kset", d, N, L)) return SSH_EINVAL;
+  if (M < 1 || M > (int64_t)1 << 30 || !n) { set_error("ssh_create_kset: need 1 <= M <= 2^30 vectors"); return SSH_EINVAL; }
+  ssh::KSet ks;
+  if (ssh::build_kset_list(d, M, n, L, &ks) != 0) {
+    set_error("ssh_create_kset: the vectors must be distinct, in the half space (first non-zero component > 0), "
+              "with |n_a| <= 32767");
+    return SSH_EINVAL;
+  }
+  return create_from(d, N, L, std::move(ks), opts, out);
+}
+
+ssh_status ssh_kset_build_region(int d, int64_t N, double L, double chi, double K, const int32_t* w, int64_t cap,
+                                 int32_t* n, int64_t* M) {
+  if (!check_dnl("ssh_kset_build_region", d, N, L) || !check_mode("ssh_kset_build_region", chi, K)) return SSH_EINVAL;
+  std::vector<int32_t> v;
+  if (ssh::kset_region(d, N, L, chi, K, w, &v) != 0) {
+    set_error("ssh_kset_build_region: bad arguments (axis weights must be integers in [1, 2^20])");
+    return SSH_EINVAL;
+  }
+  const int64_t m = (int64_t)v.size() / d;
+  if (M) *M = m;
+  if (n) {
+    if (cap < m) { set_error("ssh_kset_build_region: buffer too small"); return SSH_EINVAL; }
+    if (m > 0) memcpy(n, v.data(), sizeof(int32_t) * v.size());
+  }
   return SSH_OK;
 }
 

@@ -16,7 +16,7 @@ int64_t chi_to_m(int d, int64_t N, double chi) {
 namespace {
 
 struct Vec {
-  int64_t n2;
+  int64_t n2;  // the norm that orders the set: |n|^2, or sum_a c_a n_a^2 for an anisotropic region
   int32_t c[kMaxDim];
 };
 
@@ -27,17 +27,22 @@ bool half_space(const int32_t* c, int d) {
   return false;
 }
 
-// All n in H with |n|^2 <= r2, visited axis by axis (odometer over the box [-R, R]^d).
-void collect(int d, int64_t r2, std::vector<Vec>* out) {
-  int64_t R = (int64_t)std::floor(std::sqrt((double)r2));
-  while ((R + 1) * (R + 1) <= r2) R++;
-  while (R * R > r2) R--;
+// All n in H with sum_a w_a n_a^2 <= r2 (w_a >= 1 integers; all 1: the ball |n|^2 <= r2), visited axis by axis
+// (odometer over the box |n_a| <= R_a, R_a = floor(sqrt(r2 / w_a))).
+void collect(int d, const int64_t* w, int64_t r2, std::vector<Vec>* out) {
+  int64_t R[kMaxDim] = {0, 0, 0, 0};
+  for (int a = 0; a < d; a++) {
+    int64_t r = (int64_t)std::floor(std::sqrt((double)r2 / (double)w[a]));
+    while (w[a] * (r + 1) * (r + 1) <= r2) r++;
+    while (r > 0 && w[a] * r * r > r2) r--;
+    R[a] = r;
+  }
   int32_t c[kMaxDim] = {0, 0, 0, 0};
-  for (int a = 0; a < d; a++) c[a] = (int32_t)-R;
+  for (int a = 0; a < d; a++) c[a] = (int32_t)-R[a];
   out->clear();
   for (;;) {
     int64_t s = 0;
-    for (int a = 0; a < d; a++) s += (int64_t)c[a] * c[a];
+    for (int a = 0; a < d; a++) s += w[a] * (int64_t)c[a] * c[a];
     if (s <= r2 && half_space(c, d)) {
       Vec v;
       v.n2 = s;
@@ -45,7 +50,7 @@ void collect(int d, int64_t r2, std::vector<Vec>* out) {
       out->push_back(v);
     }
     int a = d - 1;
-    while (a >= 0 && c[a] == R) { c[a] = (int32_t)-R; a--; }
+    while (a >= 0 && c[a] == R[a]) { c[a] = (int32_t)-R[a]; a--; }
     if (a < 0) break;
     c[a]++;
   }
@@ -60,30 +65,9 @@ bool pub_less(const Vec& x, const Vec& y, int d) {
 
 }  // namespace
 
-int build_kset(int d, int64_t N, double L, double chi, double K, KSet* out) {
-  if (d < 1 || d > kMaxDim || N < 1 || !(L > 0) || !std::isfinite(L)) return -1;
-  if ((chi > 0) == (K > 0)) return -1;
-  std::vector<Vec> v;
-  int64_t M;
-  if (K > 0) {
-    long double rr = (long double)K * (long double)L / (2.0L * 3.14159265358979323846264338327950288L);
-    int64_t r2 = (int64_t)std::floor(rr * rr * (1.0L + 1e-12L));
-    collect(d, r2, &v);
-    M = (int64_t)v.size();
-  } else {
-    M = chi_to_m(d, N, chi);
-    if (M < 0) return -1;
-    // smallest ball holding M half-space vectors: its volume V_d R^d / 2 ~ M, then grow until enough
-    double est = std::pow(2.0 * (double)M + 1.0, 2.0 / d);
-    int64_t r2 = std::max<int64_t>(1, (int64_t)est);
-    for (;;) {
-      collect(d, r2, &v);
-      if ((int64_t)v.size() >= M) break;
-      r2 = r2 + r2 / 4 + 1;
-    }
-  }
-  std::sort(v.begin(), v.end(), [d](const Vec& x, const Vec& y) { return pub_less(x, y, d); });
-  v.resize((size_t)M);
+// The set's public order is v's; internal order: prefix lexicographic, then last component.
+static void fill_kset(int d, double L, const std::vector<Vec>& v, KSet* out) {
+  const int64_t M = (int64_t)v.size();
   KSet& ks = *out;
   ks = KSet();
   ks.d = d;
@@ -91,11 +75,14 @@ int build_kset(int d, int64_t N, double L, double chi, double K, KSet* out) {
   ks.n_pub.resize((size_t)M * d);
   int64_t n2max = 0;
   for (int64_t i = 0; i < M; i++) {
-    for (int a = 0; a < d; a++) ks.n_pub[i * d + a] = v[i].c[a];
-    n2max = std::max(n2max, v[i].n2);
+    int64_t n2 = 0;
+    for (int a = 0; a < d; a++) {
+      ks.n_pub[i * d + a] = v[i].c[a];
+      n2 += (int64_t)v[i].c[a] * v[i].c[a];
+    }
+    n2max = std::max(n2max, n2);
   }
   ks.k2max = (2.0 * M_PI / L) * (2.0 * M_PI / L) * (double)n2max;
-  // internal order: prefix lexicographic, then last component
   std::vector<int64_t> idx((size_t)M);
   for (int64_t i = 0; i < M; i++) idx[i] = i;
   std::sort(idx.begin(), idx.end(), [&](int64_t x, int64_t y) {
@@ -114,6 +101,78 @@ int build_kset(int d, int64_t N, double L, double chi, double K, KSet* out) {
       if (i == 0 || c > ks.nmax[a]) ks.nmax[a] = c;
     }
   }
+}
+
+// The set of an exclusion region sum_a w_a n_a^2 <= R^2 (w = NULL: the ball), in the order (that norm, then
+// lexicographic on the signed components).  K mode: every n in H with the norm <= (K L / 2 pi)^2 (1 + 1e-12);
+// chi mode: the first M = round-half-even(chi d (N - 1)).
+static int region_vectors(int d, int64_t N, double L, double chi, double K, const int32_t* wts, std::vector<Vec>* out) {
+  if (d < 1 || d > kMaxDim || N < 1 || !(L > 0) || !std::isfinite(L)) return -1;
+  if ((chi > 0) == (K > 0)) return -1;
+  int64_t w[kMaxDim] = {1, 1, 1, 1};
+  if (wts)
+    for (int a = 0; a < d; a++) {
+      if (wts[a] < 1 || wts[a] > 1 << 20) return -1;
+      w[a] = wts[a];
+    }
+  std::vector<Vec>& v = *out;
+  int64_t M;
+  if (K > 0) {
+    long double rr = (long double)K * (long double)L / (2.0L * 3.14159265358979323846264338327950288L);
+    int64_t r2 = (int64_t)std::floor(rr * rr * (1.0L + 1e-12L));
+    collect(d, w, r2, &v);
+    M = (int64_t)v.size();
+  } else {
+    M = chi_to_m(d, N, chi);
+    if (M < 0) return -1;
+    // smallest region holding M half-space vectors: its volume V_d R^d / (2 sqrt(prod w)) ~ M, then grow
+    double wprod = 1.0;
+    for (int a = 0; a < d; a++) wprod *= (double)w[a];
+    double est = std::pow(2.0 * (double)M + 1.0, 2.0 / d) * std::pow(wprod, 1.0 / d);
+    int64_t r2 = std::max<int64_t>(1, (int64_t)est);
+    for (;;) {
+      collect(d, w, r2, &v);
+      if ((int64_t)v.size() >= M) break;
+      r2 = r2 + r2 / 4 + 1;
+    }
+  }
+  std::sort(v.begin(), v.end(), [d](const Vec& x, const Vec& y) { return pub_less(x, y, d); });
+  v.resize((size_t)M);
+  return 0;
+}
+
+int build_kset(int d, int64_t N, double L, double chi, double K, KSet* out) {
+  std::vector<Vec> v;
+  if (region_vectors(d, N, L, chi, K, nullptr, &v) != 0) return -1;
+  fill_kset(d, L, v, out);
+  return 0;
+}
+
+int kset_region(int d, int64_t N, double L, double chi, double K, const int32_t* w, std::vector<int32_t>* n) {
+  std::vector<Vec> v;
+  if (region_vectors(d, N, L, chi, K, w, &v) != 0) return -1;
+  n->resize(v.size() * d);
+  for (size_t i = 0; i < v.size(); i++)
+    for (int a = 0; a < d; a++) (*n)[i * d + a] = v[i].c[a];
+  return 0;
+}
+
+int build_kset_list(int d, int64_t M, const int32_t* n, double L, KSet* out) {
+  if (d < 1 || d > kMaxDim || M < 1 || !n || !(L > 0) || !std::isfinite(L)) return -1;
+  std::vector<Vec> v((size_t)M);
+  for (int64_t i = 0; i < M; i++) {
+    Vec& x = v[i];
+    x.n2 = 0;
+    for (int a = 0; a < kMaxDim; a++) x.c[a] = a < d ? n[i * d + a] : 0;
+    for (int a = 0; a < d; a++)
+      if (x.c[a] < -32767 || x.c[a] > 32767) return -1;
+    if (!half_space(x.c, d)) return -1;
+  }
+  std::vector<Vec> s = v;  // every vector once
+  std::sort(s.begin(), s.end(), [d](const Vec& x, const Vec& y) { return pub_less(x, y, d); });
+  for (size_t i = 1; i < s.size(); i++)
+    if (!pub_less(s[i - 1], s[i], d)) return -1;
+  fill_kset(d, L, v, out);
   return 0;
 }
 

@@ -30,6 +30,11 @@ struct KSet {
 
 // Returns 0 on success, -1 on bad arguments.
 int build_kset(int d, int64_t N, double L, double chi, double K, KSet* out);
+// An anisotropic exclusion region sum_a w_a n_a^2 <= R^2 (integer w_a >= 1), in either mode, as a list in the
+// order (that norm, lexicographic): the vectors only.
+int kset_region(int d, int64_t N, double L, double chi, double K, const int32_t* w, std::vector<int32_t>* n);
+// A given list of distinct half-space vectors (|n_a| <= 32767); the public order is the list's.
+int build_kset_list(int d, int64_t M, const int32_t* n, double L, KSet* out);
 int64_t chi_to_m(int d, int64_t N, double chi);
 
 // ---- per-particle power tables: row r holds e^{2 pi i m s_{j,axis}} for every particle j

@@ -115,6 +115,8 @@ def load():
             _sig(lib, "ssh_get_fx_impl", c_int, [c_vp, P(c_int)])
             _sig(lib, "ssh_get_tc_chunks", c_int, [c_vp, P(c_int), P(c_i64)])
             _sig(lib, "ssh_set_weights", c_int, [c_vp, P(c_d)])
+            _sig(lib, "ssh_create_kset", c_int, [c_int, c_i64, c_d, c_i64, P(c_i32), c_vp, P(c_vp)])
+            _sig(lib, "ssh_kset_build_region", c_int, [c_int, c_i64, c_d, c_d, c_d, P(c_i32), c_i64, P(c_i32), P(c_i64)])
             _sig(lib, "ssh_kset_build", c_int, [c_int, c_i64, c_d, c_d, c_d, c_i64, P(c_i32), P(c_i64)])
             _sig(lib, "ssh_set_stream", c_int, [c_vp, c_vp])
             _sig(lib, "ssh_sync", c_int, [c_vp])
@@ -180,6 +182,19 @@ def kset_build(d: int, N: int, L: float, chi: float = 0.0, K: float = 0.0) -> np
     return out[:M.value].copy()
 
 
+def kset_region(d: int, N: int, L: float, axis_weights, chi: float = 0.0, K: float = 0.0) -> np.ndarray:
+    """Host-only wavevectors of the anisotropic exclusion region sum_a w_a n_a^2 <= R^2 (integer w_a >= 1), in the
+    order (that norm, lexicographic); pass the result to Context(..., kset=...)."""
+    lib = load()
+    w = np.ascontiguousarray(axis_weights, dtype=np.int32).reshape(d)
+    wp = w.ctypes.data_as(P(c_i32))
+    M = c_i64(0)
+    _check(lib.ssh_kset_build_region(d, N, L, chi, K, wp, 0, None, ctypes.byref(M)))
+    out = np.zeros((max(M.value, 1), d), dtype=np.int32)
+    _check(lib.ssh_kset_build_region(d, N, L, chi, K, wp, M.value, out.ctypes.data_as(P(c_i32)), ctypes.byref(M)))
+    return out[:M.value].copy()
+
+
 def ntilde_noalloc(d: int, N: int, M: int, s_hi_ptr: int, s_lo_ptr: int | None, n_ptr: int, C_hi_ptr: int,
                    C_lo_ptr: int, S_hi_ptr: int, S_lo_ptr: int, stream_ptr: int | None = None):
     """ssh_ntilde_noalloc with raw device pointers (allocation-free n~(k); enqueued, not synchronised)."""
@@ -198,14 +213,20 @@ class Context:
     """One configuration (d, N, L, chi | K) resident on the GPU.  Wraps ssh_create / ssh_destroy."""
 
     def __init__(self, d: int, N: int, L: float, chi: float = 0.0, K: float = 0.0, device: int = 0,
-                 fx_impl: int = 0, tc_chunk: int = 0, _handle=None):
+                 fx_impl: int = 0, tc_chunk: int = 0, kset=None, _handle=None):
+        """kset: an explicit [M, d] wavevector list (ssh_create_kset) in place of chi / K."""
         lib = load()
         self._lib = lib
         self._owned = _handle is None
         self._h = c_vp()
         if _handle is None:
             opts = (c_int * 8)(device, fx_impl, tc_chunk, 0, 0, 0, 0, 0)  # ssh_opts
-            _check(lib.ssh_create(d, N, L, chi, K, ctypes.cast(opts, c_vp), ctypes.byref(self._h)))
+            if kset is not None:
+                n = np.ascontiguousarray(kset, dtype=np.int32).reshape(-1, d)
+                _check(lib.ssh_create_kset(d, N, L, n.shape[0], n.ctypes.data_as(P(c_i32)), ctypes.cast(opts, c_vp),
+                                           ctypes.byref(self._h)))
+            else:
+                _check(lib.ssh_create(d, N, L, chi, K, ctypes.cast(opts, c_vp), ctypes.byref(self._h)))
         else:
             self._h = _handle
         dd_, NN, MM, LL = c_int(), c_i64(), c_i64(), c_d()

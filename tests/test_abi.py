@@ -71,3 +71,32 @@ def test_kset_buffer_too_small_reports_m(lib):
     buf = (ctypes.c_int32 * 4)()
     st = lib.ssh_kset_build(2, 100, 1.0, 0.3, 0.0, 2, buf, ctypes.byref(M))
     assert st == 1 and M.value == 59
+
+
+@pytest.mark.parametrize("d,N,L,w,chi,K", [
+    (2, 500, 500 ** 0.5, (1, 3), 0.3, 0.0), (2, 2000, 2000 ** 0.5, (4, 1), 0.45, 0.0),
+    (3, 400, 400 ** (1 / 3), (1, 2, 5), 0.3, 0.0), (1, 300, 300.0, (3,), 0.4, 0.0),
+    (4, 200, 200 ** 0.25, (1, 1, 2, 3), 0.2, 0.0), (2, 10, 1.0, (1, 1), 0.0, 2 * math.pi * math.sqrt(30.5)),
+    (3, 10, 2.0, (2, 1, 3), 0.0, 2 * math.pi * math.sqrt(40.5) / 2.0)])
+def test_region_bit_exact_against_bruteforce(lib, oracle_mod, d, N, L, w, chi, K):
+    """Anisotropic exclusion regions sum_a w_a n_a^2 <= R^2 (the paper's other region shapes): the library's set
+    equals the oracle's brute-force enumeration, order included; all weights 1 gives the ball's set."""
+    a = ssh.kset_region(d, N, L, w, chi=chi, K=K)
+    b = oracle_mod.kset_region(d, N, L, w, chi=chi, K=K)
+    assert a.shape == b.shape and np.array_equal(a, b)
+    if chi > 0:
+        assert np.array_equal(ssh.kset_region(d, N, L, (1,) * d, chi=chi), oracle_mod.kset(d, N, L, chi=chi))
+
+
+def test_create_kset_rejects_bad_lists(lib):
+    good = np.array([[1, 0], [0, 1], [1, 1]], dtype=np.int32)
+    for bad in (np.array([[1, 0], [-1, 0]]), np.array([[1, 0], [1, 0]]), np.array([[0, 0]]),
+                np.array([[0, -2]]), np.array([[40000, 1]])):
+        n = np.ascontiguousarray(bad, dtype=np.int32)
+        h = ctypes.c_void_p()
+        st = lib.ssh_create_kset(2, 10, 1.0, n.shape[0], n.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), None,
+                                 ctypes.byref(h))
+        assert st == 1 and not h.value, bad
+    assert good.shape == (3, 2)
+    with pytest.raises(ssh.SshError):
+        ssh.kset_region(2, 10, 1.0, (0, 1), chi=0.3)

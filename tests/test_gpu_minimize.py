@@ -218,3 +218,19 @@ def test_weighted_quench_converges(built, oracle_mod, method):
     sm, _ = oracle_smax(oracle_mod, ctx, hi, lo)
     assert sm <= 1.01e-36, (sm, r)
     ctx.close()
+
+
+def test_anisotropic_region_quench_converges(built, oracle_mod):
+    """A stealthy state for an anisotropic exclusion region (sum w_a n_a^2 <= R^2, w = (1, 3)): FIRE in the
+    default fixed point reaches S_max <= 1e-36 over that set, confirmed by the binary128 oracle."""
+    d, N = 2, 200
+    L = N ** 0.5
+    n = ssh.kset_region(d, N, L, (1, 3), chi=0.25)
+    ctx = ssh.Context(d, N, L, kset=n)
+    ctx.set_positions_frac(synth.positions(71, N, d))
+    r = ctx.minimize(max_steps=40000)
+    assert r["status"] == 0, r
+    hi, lo = ctx.positions_frac()
+    sm, _ = oracle_smax(oracle_mod, ctx, hi, lo)
+    assert sm <= 1.01e-36, (sm, r)
+    ctx.close()

@@ -350,3 +350,36 @@ def test_weights_rejected_when_out_of_range(built):
         with pytest.raises(ssh.SshError):
             ctx.set_weights(w)
     ctx.close()
+
+
+REGION_CASES = [
+    # (label, d, N, axis weights or None, chi): anisotropic regions, and sets with gaps (every third vector of
+    # the ball dropped), which leave holes in the columns of both fixed-point implementations
+    ("aniso_d2", 2, 500, (1, 3), 0.30),
+    ("aniso_d3", 3, 400, (1, 2, 5), 0.30),
+    ("gaps_d2", 2, 700, None, 0.40),
+    ("gaps_d1", 1, 400, None, 0.40),
+    ("gaps_d3", 3, 300, None, 0.40),
+]
+
+
+@pytest.mark.parametrize("case", REGION_CASES, ids=[c[0] for c in REGION_CASES])
+def test_region_parity(built, oracle_mod, case):
+    """Contexts over a given wavevector set (ssh_create_kset): every output against the oracle on the same list,
+    in every arithmetic and both fixed-point implementations."""
+    label, d, N, w, chi = case
+    L = N ** (1 / d)
+    if w is not None:
+        n = ssh.kset_region(d, N, L, w, chi=chi)
+    else:
+        ball = ssh.kset_build(d, N, L, chi=chi)
+        n = ball[np.arange(len(ball)) % 3 != 1]
+    s = synth.positions(60 + d, N, d)
+    ref = oracle_mod.phi_grad(s, None, n, L, want_cs=True, nthreads=NTHREADS)
+    for impl, precs in impls(d):
+        ctx = ssh.Context(d, N, L, kset=n, fx_impl=impl)
+        assert ctx.fx_impl == impl and np.array_equal(ctx.kset(), n)
+        ctx.set_positions_frac(s)
+        for prec in precs:
+            check_parity(ctx, s, None, L, prec, ref, n, label=f"{label}/{ssh.PREC_NAMES[prec]}/impl{impl}")
+        ctx.close()
