@@ -112,6 +112,7 @@ def parse():
     ap.add_argument("--no-large", action="store_true", help="skip the d=3, N=32768 block")
     ap.add_argument("--no-large-staged", action="store_true", help="skip its staged FP64 -> fixed point quench")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-post", action="store_true", help="skip the pair-histogram (g_2) timing")
     ap.add_argument("--no-paper-scale", action="store_true",
                     help="skip the d=2 N=2x10^6 steps at chi=0.10 and 0.40 (each context holds about 200 GB)")
     ap.add_argument("--serve-seconds", type=float, default=45.0)
@@ -403,6 +404,24 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def post_block(ssh, synth, dev):
+    """Post-processing on the GPU: the pair histogram behind g_2(r) (exact integer distances) for the d=2, N=10^4
+    workload, every particle a reference, r_max = 0.49 L, 512 bins: ordered pairs per second (host round trip
+    included: the call is synchronous)."""
+    cfg = synth.MEDIUM_D2
+    with ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi, device=dev) as ctx:
+        ctx.set_positions_frac(synth.positions(cfg.seed, cfg.N, cfg.d))
+        ctx.pair_histogram(cfg.N, 0.49 * cfg.L, 512)
+        reps = 5
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            ctx.pair_histogram(cfg.N, 0.49 * cfg.L, 512)
+        t = (time.perf_counter() - t0) / reps
+    pairs = cfg.N * (cfg.N - 1)
+    return {"workload": "pair histogram, d=2 N=10^4, n_ref=N, r_max=0.49 L, 512 bins", "ms": t * 1e3,
+            "pairs_per_s": pairs / t}
 
 
 def paper_scale_block(ssh, synth, dev, stream, flush, steps=2, warmup=1):
@@ -744,6 +763,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_large:
         line["large_d3"] = large_d3_block(ssh, synth, dev, stream, flush, max_seconds=args.minimize_seconds,
                                           staged=not args.no_large_staged)
+    if rank == 0 and world == 1 and not args.no_post:
+        line["post"] = post_block(ssh, synth, dev)
     if rank == 0 and world == 1 and not args.no_paper_scale:
         line["paper_scale"] = paper_scale_block(ssh, synth, dev, stream, flush)
     if rank == 0 and world == 1 and not args.no_serve:

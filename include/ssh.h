@@ -108,6 +108,14 @@ ssh_status ssh_get_fx_impl(const ssh_ctx* ctx, int* impl);
  * evaluation.  Errors: SSH_EINVAL. */
 ssh_status ssh_set_weights(ssh_ctx* ctx, const double* w);
 
+/* Post-processing (the supplement's Fig. S1b, g_2(r) of a state): counts of ordered particle pairs (i, j), i < n_ref,
+ * j != i, by minimum-image distance, nbins bins of width r_max / nbins on [0, r_max), 0 < r_max < L / 2.  Decided
+ * in exact integers: coordinates floor(s 2^32) of the high words of the current positions, squared distances in
+ * units (L 2^-32)^2, bin edges ceil(b^2 q^2 / nbins^2) with q = floor(r_max / L 2^32) (bins exact to one unit).
+ * g_2 of bin b is counts[b] / (n_ref (N - 1) / L^d) / (volume of the shell b).  1 <= n_ref <= N, 1 <= nbins <= 4096;
+ * counts: nbins host uint64.  Synchronous.  Errors: SSH_EINVAL, SSH_ECUDA. */
+ssh_status ssh_pair_histogram(ssh_ctx* ctx, int64_t n_ref, double r_max, int nbins, uint64_t* counts);
+
 /* Particle chunks of the tensor-core path (ssh_opts.tc_chunk): their number and the particles per chunk; both 0
  * when the context uses the integer pipes.  Either pointer may be NULL. */
 ssh_status ssh_get_tc_chunks(const ssh_ctx* ctx, int* nchunk, int64_t* chunk);

@@ -140,6 +140,29 @@ def kset_region(d: int, N: int, L: float, axis_weights, chi: float = 0.0, K: flo
     return out.astype(np.int32)
 
 
+def pair_histogram(s_hi, L: float, n_ref: int, r_max: float, nbins: int) -> np.ndarray:
+    """Ordered pairs (i < n_ref, j != i) by minimum-image distance (the pair correlation function's histogram, the
+    supplement's Fig. S1b), decided in exact integers: coordinates floor(s 2^32), differences wrapped to the
+    nearest image, squared distances summed exactly, bin b for E_b <= r2 < E_(b+1), E_b = ceil(b^2 q^2 / nbins^2),
+    q = floor(r_max / L 2^32)."""
+    s = np.asarray(s_hi, dtype=np.float64)
+    s = s.reshape(s.shape[0], -1)
+    u = np.floor(s * 2.0 ** 32).astype(np.int64)
+    q = int(math.floor(r_max / L * 2.0 ** 32))
+    E = np.array([-(-(b * b * q * q) // (nbins * nbins)) for b in range(nbins + 1)], dtype=object)
+    Eu = np.array([int(x) for x in E], dtype=np.uint64)
+    counts = np.zeros(nbins, dtype=np.int64)
+    for i in range(n_ref):
+        dx = (u[i][None, :] - u + 2 ** 31) % 2 ** 32 - 2 ** 31
+        dx = np.delete(dx, i, axis=0)
+        ok = np.all(np.abs(dx) < q, axis=1)
+        r2 = (dx[ok].astype(np.uint64) ** 2).sum(1, dtype=np.uint64)
+        r2 = r2[r2 < Eu[nbins]]
+        b = np.searchsorted(Eu, r2, side="right") - 1
+        counts += np.bincount(b, minlength=nbins)[:nbins]
+    return counts.astype(np.uint64)
+
+
 def _pos(s_hi, s_lo, d):
     s_hi = np.ascontiguousarray(s_hi, dtype=np.float64).reshape(-1, d)
     s_lo = np.zeros_like(s_hi) if s_lo is None else np.ascontiguousarray(s_lo, dtype=np.float64).reshape(-1, d)

@@ -7,6 +7,7 @@ fallback: if the library is missing or cannot be loaded, every call raises.  Bui
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import threading
 
@@ -115,6 +116,7 @@ def load():
             _sig(lib, "ssh_get_fx_impl", c_int, [c_vp, P(c_int)])
             _sig(lib, "ssh_get_tc_chunks", c_int, [c_vp, P(c_int), P(c_i64)])
             _sig(lib, "ssh_set_weights", c_int, [c_vp, P(c_d)])
+            _sig(lib, "ssh_pair_histogram", c_int, [c_vp, c_i64, c_d, c_int, P(ctypes.c_uint64)])
             _sig(lib, "ssh_create_kset", c_int, [c_int, c_i64, c_d, c_i64, P(c_i32), c_vp, P(c_vp)])
             _sig(lib, "ssh_kset_build_region", c_int, [c_int, c_i64, c_d, c_d, c_d, P(c_i32), c_i64, P(c_i32), P(c_i64)])
             _sig(lib, "ssh_kset_build", c_int, [c_int, c_i64, c_d, c_d, c_d, c_i64, P(c_i32), P(c_i64)])
@@ -195,6 +197,46 @@ def kset_region(d: int, N: int, L: float, axis_weights, chi: float = 0.0, K: flo
     return out[:M.value].copy()
 
 
+def g2(counts, d: int, N: int, L: float, n_ref: int, r_max: float):
+    """g_2(r) from pair_histogram counts: (bin centres, g_2), each bin's count over the count an ideal gas of the
+    same density would give in that shell, n_ref (N - 1) / L^d x shell volume."""
+    nb = len(counts)
+    edges = np.arange(nb + 1) * (r_max / nb)
+    vd = math.pi ** (d / 2) / math.gamma(d / 2 + 1)
+    shell = vd * (edges[1:] ** d - edges[:-1] ** d)
+    return 0.5 * (edges[1:] + edges[:-1]), np.asarray(counts, dtype=np.float64) / (n_ref * (N - 1) / L ** d * shell)
+
+
+def structure_factor_radial(n, C, S, L: float, N: int, nbins: int, k_max: float | None = None):
+    """S(k) = |n~(k)|^2 / N (Eq. structurefactor) averaged over shells of |k| = 2 pi |n| / L: (bin centres, mean
+    S, vectors per bin).  n, C, S as from Context.kset() / ntilde() (C, S as (hi, lo) pairs); a context built in
+    K mode with a cutoff beyond the exclusion region gives S(k) beyond it."""
+    kk = 2 * math.pi / L * np.sqrt((np.asarray(n, dtype=np.float64) ** 2).sum(1))
+    Cv, Sv = np.asarray(C)[..., 0] + np.asarray(C)[..., 1], np.asarray(S)[..., 0] + np.asarray(S)[..., 1]
+    sk = (Cv ** 2 + Sv ** 2) / N
+    top = kk.max() if k_max is None else k_max
+    b = np.minimum((kk / top * nbins).astype(np.int64), nbins - 1)
+    keep = kk <= top
+    cnt = np.bincount(b[keep], minlength=nbins)
+    tot = np.bincount(b[keep], weights=sk[keep], minlength=nbins)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        mean = tot / cnt
+    return (np.arange(nbins) + 0.5) * top / nbins, mean, cnt
+
+
+def tau_estimate(n, C, S, L: float, N: int, K: float) -> float:
+    """The order metric of Eq. tau from one configuration, truncated to the context's wavevectors:
+    (1 / ((2 pi D)^d rho^2)) sum over k of [S(k) - 1]^2 (2 pi / L)^d, over both k and -k, with D = 1 / K and
+    rho = N / L^d.  The paper's tau is an ensemble, thermodynamic-limit integral; this finite lattice sum is
+    for qualitative comparison only."""
+    n = np.asarray(n)
+    d = n.shape[1]
+    Cv, Sv = np.asarray(C)[..., 0] + np.asarray(C)[..., 1], np.asarray(S)[..., 0] + np.asarray(S)[..., 1]
+    sk = (Cv ** 2 + Sv ** 2) / N
+    rho = N / L ** d
+    return float(2 * ((sk - 1.0) ** 2).sum() * (2 * math.pi / L) ** d / ((2 * math.pi / K) ** d * rho ** 2))
+
+
 def ntilde_noalloc(d: int, N: int, M: int, s_hi_ptr: int, s_lo_ptr: int | None, n_ptr: int, C_hi_ptr: int,
                    C_lo_ptr: int, S_hi_ptr: int, S_lo_ptr: int, stream_ptr: int | None = None):
     """ssh_ntilde_noalloc with raw device pointers (allocation-free n~(k); enqueued, not synchronised)."""
@@ -270,6 +312,13 @@ class Context:
             if w.shape != (self.M,):
                 raise ValueError(f"need {self.M} weights")
             _check(self._lib.ssh_set_weights(self._h, _dp(w)))
+
+    def pair_histogram(self, n_ref: int, r_max: float, nbins: int) -> np.ndarray:
+        """Counts of ordered pairs (i < n_ref, j != i) by minimum-image distance in nbins bins on [0, r_max)
+        (ssh_pair_histogram; exact integer decisions); g2() turns them into g_2(r)."""
+        out = np.zeros(nbins, dtype=np.uint64)
+        _check(self._lib.ssh_pair_histogram(self._h, n_ref, r_max, nbins, out.ctypes.data_as(P(ctypes.c_uint64))))
+        return out
 
     @property
     def tc_chunks(self) -> tuple[int, int]:

@@ -322,3 +322,31 @@ def test_weighted_finite_differences(oracle_mod):
             errs.append(float(abs(diff + cfg.L * F[j, a])))
         assert errs[0] < 1e-6 * abs(cfg.L * F[j, a]) + 1e-3
         assert 3.0 < errs[0] / errs[1] < 5.0, errs
+
+
+# ------------------------------------------------------------------ pair histogram (g_2(r), supplement Fig. S1b)
+
+def test_pair_histogram_square_lattice_closed_form(oracle_mod):
+    """On a 16 x 16 square lattice of spacing 1 every particle has r_2(m) neighbours at squared distance m (Jacobi's
+    two-square count) within half the box, so with bins of width 1/4 the counts are 256 sum r_2(m) over the m with
+    floor(4 sqrt m) = b."""
+    g = np.arange(16) / 16.0
+    s = np.stack(np.meshgrid(g, g, indexing="ij"), -1).reshape(-1, 2) + 0.25 / 16
+    counts = oracle_mod.pair_histogram(s, 16.0, 256, 7.5, 30)
+    want = np.zeros(30, dtype=np.int64)
+    for m in range(1, 57):
+        want[math.isqrt(16 * m)] += 256 * jacobi_r2(m)
+    assert np.array_equal(counts.astype(np.int64), want)
+
+
+def test_pair_histogram_chain_and_symmetry(oracle_mod):
+    """A periodic chain of 32 points, spacing 1: two neighbours at each distance 1..15, in bins of width 1/2 at
+    b = 2 m; and for random points the counts with n_ref = N are even (each unordered pair twice)."""
+    s = (np.arange(32) + 0.5) / 32.0
+    counts = oracle_mod.pair_histogram(s[:, None], 32.0, 32, 15.5, 31)
+    want = np.zeros(31, dtype=np.int64)
+    want[2:31:2] = 64
+    assert np.array_equal(counts.astype(np.int64), want)
+    r = synth.positions(5, 300, 2)
+    c = oracle_mod.pair_histogram(r, 300 ** 0.5, 300, 0.45 * 300 ** 0.5, 50).astype(np.int64)
+    assert np.all(c % 2 == 0) and c.sum() > 0
