@@ -77,10 +77,10 @@ WORKLOAD = WORKLOADS["d2-n10000"]
 # the kernel sources hash to the value recorded with them; otherwise the traffic is reported as null.
 NCU_TRAFFIC = {("d2-n10000", "fx", "force"): ("9a8b45757c86", 35_869_184 + 5_888_000),
                ("d2-n10000", "fx", "ntilde"): ("9a8b45757c86", 36_598_272 + 43_264_000),
-               ("d2-n10000", "fx-tensor", "tc_force"): ("8cf9354e7506", 74_689_280 + 2_308_352),
-               ("d2-n10000", "fx-tensor", "tc_dens"): ("8cf9354e7506", 126_251_776 + 5_060_864),
-               ("d3-n32768", "fx-tensor", "tc_force"): ("8cf9354e7506", 2_302_616_000 + 20_895_000),
-               ("d3-n32768", "fx-tensor", "tc_dens"): ("8cf9354e7506", 3_009_255_000 + 8_040_000)}
+               ("d2-n10000", "fx-tensor", "tc_force"): ("8664f06be3ec", 74_689_792 + 2_762_240),
+               ("d2-n10000", "fx-tensor", "tc_dens"): ("8664f06be3ec", 126_253_312 + 5_029_632),
+               ("d3-n32768", "fx-tensor", "tc_force"): ("8664f06be3ec", 2_293_464_000 + 20_805_000),
+               ("d3-n32768", "fx-tensor", "tc_dens"): ("8664f06be3ec", 3_008_868_000 + 8_570_000)}
 
 
 def kernel_source_hash() -> str:
