@@ -275,6 +275,23 @@ ssh_status ssh_batch_size(const ssh_batch* batch, int* n, int64_t* pairs);
 /* The context of member `slot` (owned by the batch; valid until ssh_batch_destroy), for ssh_get_results,
  * ssh_get_ntilde, ssh_get_positions_frac. */
 ssh_status ssh_batch_member(ssh_batch* batch, int slot, ssh_ctx** ctx);
+/* The batch autotuner (the work decomposition of the tensor-core GEMMs for this mix of members): each candidate is
+ * timed over reps evaluations of prec, with one untimed evaluation first.  The candidates are density K-range pieces
+ * per member at 50, 100, 200 or 400% of its share of the SMs, and force items in particle-tile bundles or one by
+ * one.  The fastest becomes the batch's decomposition for ssh_batch_eval and its steps.  It is remembered for the
+ * process per set of member shapes (d, N, M, chunks) and precision; a repeated call times only the default and the
+ * remembered choice (candidates = 0).  Results do not change: only the order of exact integer sums does.
+ * Synchronous.  Errors: SSH_EINVAL (bad arguments, empty batch, a member without positions), SSH_ECUDA. */
+typedef struct {
+  int dens_pieces_pct; /* chosen density pieces, % of each member's SM share (default 100) */
+  int force_bundles;   /* chosen force order: 1 bundles (default), 0 one by one */
+  double ms_default;   /* mean evaluation time with the defaults */
+  double ms_tuned;     /* with the chosen decomposition */
+  int candidates;      /* decompositions timed (0: the process's remembered choice) */
+  int reserved[3];
+} ssh_tune;
+ssh_status ssh_batch_autotune(ssh_batch* b, int prec, int reps, ssh_tune* out);
+
 /* Phi, S_max and F (want_force) of every member in one batched evaluation; synchronises. */
 ssh_status ssh_batch_eval(ssh_batch* batch, int prec, int want_force);
 /* Minimise every member to completion (p as for ssh_minimize; zero fields take each member's defaults).  Steps

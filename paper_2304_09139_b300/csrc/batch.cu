@@ -21,6 +21,7 @@
 #include <thread>
 #include <vector>
 
+#include <cstring>
 #include "ssh_internal.h"
 
 namespace ssh {
@@ -57,6 +58,7 @@ static ssh_status fail(cudaError_t e, const char* what) {
 
 struct Runner {
   int device = 0;
+  EngineTune tune;  // the batch's work decomposition (ssh_batch_autotune)
   cudaStream_t st = nullptr;
   std::vector<Member> act;
   Engine eng;
@@ -96,6 +98,7 @@ struct Runner {
       m.stage_t0 = now_s();
     }
     Engine tmp;
+    tmp.tune = tune;
     cudaError_t e = engine_build(&tmp, ms, precs, false, st);
     for (int p = 0; p < 3 && e == cudaSuccess; p++)
       if (tmp.view[p].nlist) e = engine_eval(&tmp, p, true, st, prof);
@@ -127,6 +130,7 @@ struct Runner {
       ms.push_back(&m.h->c);
       precs.push_back(m.p.stage_prec[m.stage]);
     }
+    eng.tune = tune;
     cudaError_t e = engine_build(&eng, ms, precs, true, st);
     eng.methods = 0;
     for (Member& m : act) eng.methods |= 1 << (m.p.method == SSH_MIN_LBFGS ? kMethodLbfgs : kMethodFire);
@@ -246,6 +250,7 @@ struct ssh_batch {
   std::vector<ssh_min_result> results;
   ssh::Prof prof;
   Runner* stepper = nullptr;  // ssh_batch_begin / ssh_batch_steps
+  ssh::EngineTune tune;       // ssh_batch_autotune's choice (defaults until then)
 };
 
 extern "C" {
@@ -324,6 +329,7 @@ ssh_status ssh_batch_eval(ssh_batch* b, int prec, int want_force) {
     precs.push_back(prec);
   }
   ssh::Engine e;
+  e.tune = b->tune;
   cudaError_t err = ssh::engine_build(&e, ms, precs, false, b->stream);
   if (err == cudaSuccess) err = ssh::engine_eval(&e, prec, want_force != 0, b->stream, &b->prof);
   if (err == cudaSuccess) err = cudaStreamSynchronize(b->stream);
@@ -337,6 +343,108 @@ ssh_status ssh_batch_eval(ssh_batch* b, int prec, int want_force) {
   return SSH_OK;
 }
 
+// The batch autotuner: times the evaluation of every member together under each candidate work decomposition of
+// the tensor-core GEMMs (density pieces at 50, 100, 200, 400% of each member's SM share; force items in bundles or
+// one by one), keeps the fastest, and remembers it per member shape set for the rest of the process.  The
+// decomposition changes only the order of exact integer sums, so results are the same bit for bit.
+namespace {
+std::mutex g_tune_mu;
+std::map<std::string, ssh::EngineTune> g_tune_cache;
+}  // namespace
+
+ssh_status ssh_batch_autotune(ssh_batch* b, int prec, int reps, ssh_tune* out) {
+  if (!b || prec < SSH_FP64 || prec > SSH_FX || reps < 1 || reps > 1000) {
+    set_error("ssh_batch_autotune: bad arguments");
+    return SSH_EINVAL;
+  }
+  cudaSetDevice(b->device);
+  std::vector<ssh::Ctx*> ms;
+  std::vector<int> precs;
+  std::vector<std::string> shapes;
+  for (ssh_ctx* h : b->members) {
+    if (!h->c.have_positions) { set_error("ssh_batch_autotune: a member has no positions"); return SSH_EINVAL; }
+    ms.push_back(&h->c);
+    precs.push_back(prec);
+    shapes.push_back(std::to_string(h->c.d) + "/" + std::to_string(h->c.N) + "/" + std::to_string(h->c.M) + "/" +
+                     std::to_string(h->c.tc.on ? h->c.tc.nchunk : 0));
+  }
+  if (ms.empty()) { set_error("ssh_batch_autotune: empty batch"); return SSH_EINVAL; }
+  std::sort(shapes.begin(), shapes.end());
+  std::string key = std::to_string(prec);
+  for (const std::string& x : shapes) key += ";" + x;
+  ssh_tune rep;
+  memset(&rep, 0, sizeof rep);
+  // mean time of one evaluation (Phi, S_max, F) under a decomposition: one untimed, then reps timed
+  auto time_it = [&](const ssh::EngineTune& t, double* ms_out) -> cudaError_t {
+    ssh::Engine e;
+    e.tune = t;
+    cudaError_t err = ssh::engine_build(&e, ms, precs, false, b->stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (err == cudaSuccess) err = cudaEventCreate(&e0);
+    if (err == cudaSuccess) err = cudaEventCreate(&e1);
+    if (err == cudaSuccess) err = ssh::engine_eval(&e, prec, true, b->stream, nullptr);
+    if (err == cudaSuccess) err = cudaEventRecord(e0, b->stream);
+    for (int r = 0; r < reps && err == cudaSuccess; r++) err = ssh::engine_eval(&e, prec, true, b->stream, nullptr);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, b->stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float msf = 0.0f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&msf, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    ssh::engine_free(&e);
+    *ms_out = (double)msf / reps;
+    return err;
+  };
+  ssh::EngineTune best;
+  bool cached = false;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      best = it->second;
+      cached = true;
+    }
+  }
+  cudaError_t err = cudaSuccess;
+  if (cached) {
+    err = time_it(ssh::EngineTune(), &rep.ms_default);
+    if (err == cudaSuccess) err = time_it(best, &rep.ms_tuned);
+  } else {
+    static const int kPct[4] = {50, 100, 200, 400};
+    double best_ms = 0.0;
+    for (int fb = 1; fb >= 0 && err == cudaSuccess; fb--)
+      for (int pi = 0; pi < 4 && err == cudaSuccess; pi++) {
+        ssh::EngineTune t;
+        t.dens_pct = kPct[pi];
+        t.force_bundle = fb;
+        double msv = 0.0;
+        err = time_it(t, &msv);
+        rep.candidates++;
+        if (err != cudaSuccess) break;
+        if (t.dens_pct == 100 && t.force_bundle == 1) rep.ms_default = msv;
+        if (rep.candidates == 1 || msv < best_ms) {
+          best_ms = msv;
+          best = t;
+        }
+      }
+    rep.ms_tuned = best_ms;
+    if (err == cudaSuccess) {
+      std::lock_guard<std::mutex> lk(g_tune_mu);
+      g_tune_cache[key] = best;
+    }
+  }
+  if (err != cudaSuccess) return ssh::fail(err, "ssh_batch_autotune");
+  b->tune = best;
+  if (b->stepper) {
+    b->stepper->tune = best;
+    b->stepper->dirty = true;  // the next chunk of steps rebuilds its engine and graph with it
+  }
+  rep.dens_pieces_pct = best.dens_pct;
+  rep.force_bundles = best.force_bundle;
+  if (out) *out = rep;
+  return SSH_OK;
+}
+
 // Minimise every member to completion through batched steps (the same FIRE step, stages and stopping rules as
 // ssh_minimize, per member).
 ssh_status ssh_batch_minimize(ssh_batch* b, const ssh_min_params* pin, int64_t chunk_steps, double max_seconds,
@@ -344,6 +452,7 @@ ssh_status ssh_batch_minimize(ssh_batch* b, const ssh_min_params* pin, int64_t c
   if (!b) { set_error("ssh_batch_minimize: NULL batch"); return SSH_EINVAL; }
   cudaSetDevice(b->device);
   Runner r;
+  r.tune = b->tune;
   r.device = b->device;
   r.st = b->stream;
   r.prof = b->prof.on ? &b->prof : nullptr;
@@ -391,6 +500,7 @@ ssh_status ssh_batch_begin(ssh_batch* b, const ssh_min_params* pin) {
   cudaSetDevice(b->device);
   delete b->stepper;
   b->stepper = new Runner();
+  b->stepper->tune = b->tune;
   b->stepper->device = b->device;
   b->stepper->st = b->stream;
   std::vector<Member> fresh;

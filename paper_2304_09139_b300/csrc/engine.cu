@@ -202,18 +202,22 @@ cudaError_t engine_build(Engine* e, const std::vector<Ctx*>& members, const std:
       for (int64_t b = 0; b < tc_table_blocks(members[i], ph); b++) tab_bm[ph].push_back({cfg, (int32_t)b});
       tc_prep_items(members[i], cfg, ph, tcp);
       const int64_t share = (int64_t)((double)e->sm_count * (double)tc_density_steps(members[i], ph) /
-                                      (double)std::max<int64_t>(1, steps));
+                                      (double)std::max<int64_t>(1, steps) * (double)e->tune.dens_pct / 100.0);
       tc_gemm_items(members[i], cfg, ph, share, tcd, tcf);
     }
     P.prep_n = (int)tcp.size() - P.prep_off;
     P.dens_n = (int)tcd.size() - P.dens_off;
     P.force_n = (int)tcf.size() - P.force_off;
     std::stable_sort(tcd.begin() + P.dens_off, tcd.end(), by_size);
-    std::map<std::pair<int, int>, int64_t> bundle;
-    for (size_t k = P.force_off; k < tcf.size(); k++) bundle[{tcf[k].cfg, tcf[k].a}] += tcf[k].nks;
-    std::stable_sort(tcf.begin() + P.force_off, tcf.end(), [&](const TcItem& a, const TcItem& b) {
-      return bundle[{a.cfg, a.a}] > bundle[{b.cfg, b.a}];
-    });
+    if (e->tune.force_bundle) {
+      std::map<std::pair<int, int>, int64_t> bundle;
+      for (size_t k = P.force_off; k < tcf.size(); k++) bundle[{tcf[k].cfg, tcf[k].a}] += tcf[k].nks;
+      std::stable_sort(tcf.begin() + P.force_off, tcf.end(), [&](const TcItem& a, const TcItem& b) {
+        return bundle[{a.cfg, a.a}] > bundle[{b.cfg, b.a}];
+      });
+    } else {
+      std::stable_sort(tcf.begin() + P.force_off, tcf.end(), by_size);
+    }
     // before the force items of this chunk: the preparation again for members whose buffers hold a later chunk
     P.rprep_off = (int)tcp.size();
     for (int i : tcl) {

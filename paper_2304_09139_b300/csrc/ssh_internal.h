@@ -212,8 +212,17 @@ struct LbMat {                     // per member: S^T Y and Y^T Y by ring slot, 
 
 // A set of configurations evaluated together.  Members keep their own buffers (Ctx); the engine holds their
 // descriptors, the per-precision member lists and the work lists, all in device memory.
+// Work decomposition of the tensor-core GEMMs, chosen by the batch autotuner (ssh_batch_autotune): density
+// K-range pieces per member as a percentage of its share of the SMs, and whether force items run in
+// particle-tile bundles (largest bundle first) or one by one (largest first).
+struct EngineTune {
+  int dens_pct = 100;
+  int force_bundle = 1;
+};
+
 struct Engine {
   int device = 0;
+  EngineTune tune;  // set by the caller before engine_build
   int sm_count = 148;
   std::vector<Ctx*> members;
   std::vector<int> prec_of;  // current precision per member; -1 = listed under every precision

@@ -144,6 +144,7 @@ def load():
             _sig(lib, "ssh_batch_size", c_int, [c_vp, P(c_int), P(c_i64)])
             _sig(lib, "ssh_batch_member", c_int, [c_vp, c_int, P(c_vp)])
             _sig(lib, "ssh_batch_eval", c_int, [c_vp, c_int, c_int])
+            _sig(lib, "ssh_batch_autotune", c_int, [c_vp, c_int, c_int, P(TuneReport)])
             _sig(lib, "ssh_batch_minimize", c_int, [c_vp, P(MinParams), c_i64, c_d, P(MinResult)])
             _sig(lib, "ssh_batch_begin", c_int, [c_vp, P(MinParams)])
             _sig(lib, "ssh_batch_steps", c_int, [c_vp, c_i64])
@@ -452,6 +453,11 @@ def _params(params, stages=None, **kw):
     return p
 
 
+class TuneReport(ctypes.Structure):
+    _fields_ = [("dens_pieces_pct", ctypes.c_int), ("force_bundles", ctypes.c_int), ("ms_default", ctypes.c_double),
+                ("ms_tuned", ctypes.c_double), ("candidates", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+
+
 class Batch:
     """Many configurations evaluated and minimised through the same launches (ssh_batch_*)."""
 
@@ -484,6 +490,14 @@ class Batch:
         _check(self._lib.ssh_batch_member(self._h, slot.value, ctypes.byref(h)))
         self._members.append(Context(0, 0, 0.0, _handle=h))
         return slot.value
+
+    def autotune(self, prec: int = 2, reps: int = 5) -> dict:
+        """ssh_batch_autotune: time the candidate work decompositions of the tensor-core GEMMs for this mix and keep
+        the fastest (results are unchanged bit for bit)."""
+        r = TuneReport()
+        _check(self._lib.ssh_batch_autotune(self._h, prec, reps, ctypes.byref(r)))
+        return {"dens_pieces_pct": r.dens_pieces_pct, "force_bundles": r.force_bundles, "ms_default": r.ms_default,
+                "ms_tuned": r.ms_tuned, "candidates": r.candidates}
 
     def member(self, slot: int) -> Context:
         return self._members[slot]

@@ -214,3 +214,32 @@ def test_batched_lbfgs_equals_single(built):
         assert ra["steps"] == res[i]["steps"] and ra["smax"] == res[i]["smax"], (i, ra, res[i])
         assert np.array_equal(ha, hb) and np.array_equal(la, lb), i
     b.close()
+
+
+def test_autotune_keeps_results_and_remembers(built):
+    """The batch autotuner times every candidate decomposition of the tensor-core GEMMs, keeps one, and the
+    batch's evaluations stay bit-identical (only the order of exact integer sums changes); a second call on the
+    same member shapes reuses the remembered choice."""
+    cfgs = small_mix(12, 47, dims=(1, 2, 3)) + [synth.Config(d=2, N=3000, L=3000 ** 0.5, chi=0.45, seed=13)]
+    b = ssh.Batch()
+    for c in cfgs:
+        b.add(c.d, c.N, c.L, synth.positions(c.seed, c.N, c.d), chi=c.chi)
+    b.eval(ssh.FX)
+    before = [(b.member(i).results(), b.member(i).ntilde()) for i in range(len(cfgs))]
+    t = b.autotune(ssh.FX, reps=3)
+    assert t["candidates"] == 8 and t["dens_pieces_pct"] in (50, 100, 200, 400) and t["force_bundles"] in (0, 1)
+    assert 0 < t["ms_tuned"] <= t["ms_default"]
+    b.eval(ssh.FX)
+    for i in range(len(cfgs)):
+        ra, (Ca, Sa) = before[i]
+        rb = b.member(i).results()
+        Cb, Sb = b.member(i).ntilde()
+        for k in ("phi", "smax", "F_hi", "F_lo"):
+            assert np.array_equal(ra[k], rb[k]), (i, k)
+        assert np.array_equal(Ca, Cb) and np.array_equal(Sa, Sb), i
+    t2 = b.autotune(ssh.FX, reps=2)
+    assert t2["candidates"] == 0 and (t2["dens_pieces_pct"], t2["force_bundles"]) == (t["dens_pieces_pct"], t["force_bundles"])
+    # batched steps run with the tuned decomposition and still converge
+    st, r = b.minimize(stages=[ssh.FX], max_seconds=120)
+    assert all(x["status"] == 0 for x in r), r
+    b.close()
