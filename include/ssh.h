@@ -162,6 +162,10 @@ ssh_status ssh_set_positions_frac(ssh_ctx* ctx, const double* s_hi, const double
 /* Current fractional positions s in [0, 1) as dd (N*d row-major); either pointer may be NULL. */
 ssh_status ssh_get_positions_frac(ssh_ctx* ctx, double* s_hi, double* s_lo);
 
+/* Current positions in physical units, r = L s in [0, L) as dd (N*d row-major; the dd product of the stored s
+ * with L); either pointer may be NULL.  Errors: SSH_EINVAL (no positions), SSH_ECUDA. */
+ssh_status ssh_get_positions(ssh_ctx* ctx, double* r_hi, double* r_lo);
+
 /*
  * One evaluation of Phi, S_max and F at the current positions in arithmetic `prec` (Eqs. energy, smax,
  * force), results copied to the caller: phi[2] and smax[2] as dd (either may be NULL), F_hi / F_lo the

@@ -320,6 +320,21 @@ ssh_status ssh_get_positions_frac(ssh_ctx* h, double* s_hi, double* s_lo) {
   return SSH_OK;
 }
 
+ssh_status ssh_get_positions(ssh_ctx* h, double* r_hi, double* r_lo) {
+  if (!h) { set_error("ssh_get_positions: NULL context"); return SSH_EINVAL; }
+  ssh::Ctx& c = h->c;
+  const int64_t nd = (int64_t)c.d * c.N;
+  std::vector<double> hi((size_t)nd), lo((size_t)nd);
+  const ssh_status st = ssh_get_positions_frac(h, hi.data(), lo.data());
+  if (st != SSH_OK) return st;
+  for (int64_t i = 0; i < nd; i++) {
+    const dd r = dd_mul_d(dd_make(hi[i], lo[i]), c.L);
+    if (r_hi) r_hi[i] = r.hi;
+    if (r_lo) r_lo[i] = r.lo;
+  }
+  return SSH_OK;
+}
+
 ssh_status ssh_eval(ssh_ctx* h, int prec, int want_force) {
   if (!h) { set_error("ssh_eval: NULL context"); return SSH_EINVAL; }
   ssh::Ctx& c = h->c;

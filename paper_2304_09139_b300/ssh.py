@@ -116,6 +116,7 @@ def load():
             _sig(lib, "ssh_get_fx_impl", c_int, [c_vp, P(c_int)])
             _sig(lib, "ssh_get_tc_chunks", c_int, [c_vp, P(c_int), P(c_i64)])
             _sig(lib, "ssh_set_weights", c_int, [c_vp, P(c_d)])
+            _sig(lib, "ssh_get_positions", c_int, [c_vp, P(c_d), P(c_d)])
             _sig(lib, "ssh_pair_histogram", c_int, [c_vp, c_i64, c_d, c_int, P(ctypes.c_uint64)])
             _sig(lib, "ssh_create_kset", c_int, [c_int, c_i64, c_d, c_i64, P(c_i32), c_vp, P(c_vp)])
             _sig(lib, "ssh_kset_build_region", c_int, [c_int, c_i64, c_d, c_d, c_d, P(c_i32), c_i64, P(c_i32), P(c_i64)])
@@ -349,6 +350,13 @@ class Context:
         r_hi = _rows(r_hi, self.N, self.d)
         r_lo = _rows(r_lo, self.N, self.d)
         _check(self._lib.ssh_set_positions(self._h, _dp(r_hi), _dp(r_lo)))
+
+    def positions(self):
+        """Current positions in physical units, r = L s, as (hi, lo) [N, d] arrays (ssh_get_positions)."""
+        hi = np.zeros((self.N, self.d))
+        lo = np.zeros((self.N, self.d))
+        _check(self._lib.ssh_get_positions(self._h, _dp(hi), _dp(lo)))
+        return hi, lo
 
     def positions_frac(self):
         hi = np.zeros((self.N, self.d))

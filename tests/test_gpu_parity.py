@@ -235,6 +235,10 @@ def test_physical_positions_match_fractional(built):
         ctx.set_positions(r_hi, r_lo)
         b = ctx.energy_grad(ssh.FX)
         assert abs(ddiff(a["phi"], b["phi"])) <= 1e-26 * ctx.M * N
+        # ssh_get_positions returns r = L s (dd): the given r to dd rounding
+        ph, pl = ctx.positions()
+        err = np.abs((ph - r_hi) + (pl - r_lo))
+        assert err.max() <= 1e-29 * L, err.max()
         ctx.close()
 
 
