@@ -75,8 +75,8 @@ WORKLOAD = WORKLOADS["d2-n10000"]
 
 # DRAM bytes (read + write) per launch from one ncu capture of this workload (profiles/), valid only while
 # the kernel sources hash to the value recorded with them; otherwise the traffic is reported as null.
-NCU_TRAFFIC = {("d2-n10000", "fx", "force"): ("9a8b45757c86", 35_869_184 + 5_888_000),
-               ("d2-n10000", "fx", "ntilde"): ("9a8b45757c86", 36_598_272 + 43_264_000),
+NCU_TRAFFIC = {("d2-n10000", "fx", "force"): ("8664f06be3ec", 35_869_696 + 1_536),
+               ("d2-n10000", "fx", "ntilde"): ("8664f06be3ec", 36_569_600 + 13_568),
                ("d2-n10000", "fx-tensor", "tc_force"): ("8664f06be3ec", 74_689_792 + 2_762_240),
                ("d2-n10000", "fx-tensor", "tc_dens"): ("8664f06be3ec", 126_253_312 + 5_029_632),
                ("d3-n32768", "fx-tensor", "tc_force"): ("8664f06be3ec", 2_293_464_000 + 20_805_000),
