@@ -100,8 +100,8 @@ ssh_status ssh_get_dims(const ssh_ctx* ctx, int* d, int64_t* N, int64_t* M, doub
 /* The implementation SSH_FX evaluations of this context use: SSH_FX_INTEGER or SSH_FX_TENSOR. */
 ssh_status ssh_get_fx_impl(const ssh_ctx* ctx, int* impl);
 
-/* Weights v~(k) of the wavevectors (the paper's general positive v~(k), which funnel the minimiser to chosen
- * ground states): Phi = sum_k v~(k) |n~(k)|^2 and F = -grad Phi; S(k) and S_max do not change.  w holds M values
+/* Weights v~(k) of the wavevectors (Eq. energy's v~(k); the paper notes that a general positive v~(k) funnels the
+ * minimiser to chosen ground states): Phi = sum_k v~(k) |n~(k)|^2 and F = -grad Phi; S(k) and S_max do not change.  w holds M values
  * in the order of ssh_get_kset, each finite and in [0, 1024]; NULL restores 1 for every wavevector (the
  * default).  Weight 1 keeps the exact integer force coefficients of the fixed-point paths; other weights enter
  * them through a double-double product (relative error 2^-105).  Stream-ordered; takes effect at the next
@@ -279,7 +279,8 @@ ssh_status ssh_batch_size(const ssh_batch* batch, int* n, int64_t* pairs);
 /* The context of member `slot` (owned by the batch; valid until ssh_batch_destroy), for ssh_get_results,
  * ssh_get_ntilde, ssh_get_positions_frac. */
 ssh_status ssh_batch_member(ssh_batch* batch, int slot, ssh_ctx** ctx);
-/* The batch autotuner (the work decomposition of the tensor-core GEMMs for this mix of members): each candidate is
+/* The batch autotuner (no counterpart in the paper; it tunes this library's work decomposition of the tensor-core
+ * GEMMs for this mix of members): each candidate is
  * timed over reps evaluations of prec, with one untimed evaluation first.  The candidates are density K-range pieces
  * per member at 50, 100, 200 or 400% of its share of the SMs, and force items in particle-tile bundles or one by
  * one.  The fastest becomes the batch's decomposition for ssh_batch_eval and its steps.  It is remembered for the
