@@ -38,6 +38,44 @@ static void free_buf(ssh::DevBuf& b) {
   b.bytes = 0;
 }
 
+namespace ssh {
+
+void eval_graphs_reset(Ctx* c) {
+  for (auto& row : c->eval_graph)
+    for (cudaGraphExec_t& g : row) {
+      if (g) cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+}  // namespace ssh
+
+// One evaluation: replays a CUDA graph of the context engine's launches (captured at the first call for this
+// precision), which removes the host launch gaps; with the profiler on, or when the stream is itself being captured
+// by the caller, the kernels are launched directly.
+static cudaError_t eval_replayed(ssh::Ctx& c, int prec, bool want_force) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(c.stream, &cs);
+  if (e != cudaSuccess) return e;
+  if (c.prof.on || cs != cudaStreamCaptureStatusNone) return ssh::eval_phi_grad(&c, prec, want_force);
+  cudaGraphExec_t& g = c.eval_graph[prec][want_force ? 1 : 0];
+  if (!g) {
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(c.stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    e = ssh::eval_phi_grad(&c, prec, want_force);
+    const cudaError_t e2 = cudaStreamEndCapture(c.stream, &graph);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      g = nullptr;
+      return e;
+    }
+  }
+  return cudaGraphLaunch(g, c.stream);
+}
+
 extern "C" {
 
 const char* ssh_version(void) { return "ssh 0.1 sm_103a"; }
@@ -156,6 +194,7 @@ void ssh_destroy(ssh_ctx* h) {
   cudaSetDevice(c.device);
   if (c.stream) cudaStreamSynchronize(c.stream);
   ssh::fire_free(&c);
+  ssh::eval_graphs_reset(&c);
   if (c.eng) {
     ssh::engine_free(c.eng);
     delete c.eng;
@@ -341,7 +380,7 @@ ssh_status ssh_eval(ssh_ctx* h, int prec, int want_force) {
   if (prec < SSH_FP64 || prec > SSH_FX) { set_error("ssh_eval: unknown precision"); return SSH_EINVAL; }
   if (!c.have_positions) { set_error("ssh_eval: no positions set"); return SSH_EINVAL; }
   cudaSetDevice(c.device);
-  cudaError_t e = ssh::eval_phi_grad(&c, prec, want_force != 0);
+  cudaError_t e = eval_replayed(c, prec, want_force != 0);
   if (e != cudaSuccess) return cuda_fail(e, "ssh_eval: launch");
   c.have_result = true;
   c.last_prec = prec;

@@ -303,6 +303,7 @@ cudaError_t fire_alloc(Ctx* c) {
   if (e == cudaSuccess) e = cudaMallocHost(&f->h_fs, sizeof(FireState));
   c->fire = f;
   // the context's own engine now carries the minimiser pointers too (still without a status word)
+  eval_graphs_reset(c);
   if (e == cudaSuccess) e = engine_build(c->eng, {c}, {-1}, false, c->stream);
   return e;
 }

@@ -309,6 +309,7 @@ struct Ctx {
   dd inv_L;                       // 1 / L
   FireBufs* fire = nullptr;       // minimiser state, allocated on first ssh_minimize
   Engine* eng = nullptr;          // this context alone (plain evaluations)
+  cudaGraphExec_t eval_graph[3][2] = {};  // one evaluation per (precision, with force), replayed; reset with eng
   bool tc_requested = false;      // fixed point on the tensor cores (d = 1, 2, 3)
   int64_t tc_chunk_req = 0;        // particles per chunk on that path (0: as device memory allows)
   TcPlan tc;
@@ -390,6 +391,7 @@ cudaError_t tc_launch_force_finish(const EngineView& v, cudaStream_t st, Prof* p
 
 // kernels.cu
 cudaError_t plan_upload(Ctx* c);
+void eval_graphs_reset(Ctx* c);  // drop the cached evaluation graphs (the engine changed)
 cudaError_t eval_phi_grad(Ctx* c, int prec, bool want_force);
 void setup_launch(Ctx* c);
 

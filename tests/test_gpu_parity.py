@@ -205,7 +205,8 @@ def test_single_particle_on_gpu(built):
 
 
 def test_repeat_is_bitwise_identical(built):
-    """Fixed-order reductions: two evaluations of the same positions agree bit for bit."""
+    """Fixed-order reductions: two evaluations of the same positions agree bit for bit, and so do the replayed
+    evaluation graph and direct launches."""
     cfg = synth.MEDIUM_D2
     s = synth.positions(cfg.seed, cfg.N, cfg.d)
     for impl, precs in impls(cfg.d):
@@ -218,6 +219,12 @@ def test_repeat_is_bitwise_identical(built):
             Cb, Sb = ctx.ntilde()
             assert np.array_equal(a["phi"], b["phi"]) and np.array_equal(a["F_hi"], b["F_hi"])
             assert np.array_equal(a["F_lo"], b["F_lo"]) and np.array_equal(Ca, Cb) and np.array_equal(Sa, Sb)
+            # evaluations replay a captured graph; with the profiler on the same kernels launch directly
+            ctx.prof_enable(True)
+            c = ctx.energy_grad(prec)
+            ctx.prof_enable(False)
+            assert np.array_equal(a["phi"], c["phi"]) and np.array_equal(a["F_hi"], c["F_hi"])
+            assert np.array_equal(a["F_lo"], c["F_lo"])
         ctx.close()
 
 
