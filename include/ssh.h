@@ -284,7 +284,7 @@ ssh_status ssh_batch_member(ssh_batch* batch, int slot, ssh_ctx** ctx);
  * timed over reps evaluations of prec, with one untimed evaluation first.  The candidates are density K-range pieces
  * per member at 50, 100, 200 or 400% of its share of the SMs, and force items in particle-tile bundles or one by
  * one.  The fastest becomes the batch's decomposition for ssh_batch_eval and its steps.  It is remembered for the
- * process per set of member shapes (d, N, M, chunks) and precision; a repeated call times only the default and the
+ * process per device, set of member shapes (d, N, M, chunks) and precision; a repeated call times only the default and the
  * remembered choice (candidates = 0).  Results do not change: only the order of exact integer sums does.
  * Synchronous.  Errors: SSH_EINVAL (bad arguments, empty batch, a member without positions), SSH_ECUDA. */
 typedef struct {

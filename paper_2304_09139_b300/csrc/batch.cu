@@ -370,7 +370,7 @@ ssh_status ssh_batch_autotune(ssh_batch* b, int prec, int reps, ssh_tune* out) {
   }
   if (ms.empty()) { set_error("ssh_batch_autotune: empty batch"); return SSH_EINVAL; }
   std::sort(shapes.begin(), shapes.end());
-  std::string key = std::to_string(prec);
+  std::string key = std::to_string(b->device) + "/" + std::to_string(prec);
   for (const std::string& x : shapes) key += ";" + x;
   ssh_tune rep;
   memset(&rep, 0, sizeof rep);
