@@ -74,19 +74,25 @@ WORKLOADS = {"d2-n10000": dict(d=2, N=10_000, L=100.0, chi=0.45, seed=2),
 WORKLOAD = WORKLOADS["d2-n10000"]
 
 # DRAM bytes (read + write) per launch from one ncu capture of this workload (profiles/), valid only while
-# the kernel sources hash to the value recorded with them; otherwise the traffic is reported as null.
-NCU_TRAFFIC = {("d2-n10000", "fx", "force"): ("8664f06be3ec", 35_869_696 + 1_536),
-               ("d2-n10000", "fx", "ntilde"): ("8664f06be3ec", 36_569_600 + 13_568),
-               ("d2-n10000", "fx-tensor", "tc_force"): ("8664f06be3ec", 74_689_792 + 2_762_240),
-               ("d2-n10000", "fx-tensor", "tc_dens"): ("8664f06be3ec", 126_253_312 + 5_029_632),
-               ("d3-n32768", "fx-tensor", "tc_force"): ("8664f06be3ec", 2_293_464_000 + 20_805_000),
-               ("d3-n32768", "fx-tensor", "tc_dens"): ("8664f06be3ec", 3_008_868_000 + 8_570_000)}
+# the kernel's family of sources hashes to the value recorded with them; otherwise the traffic is reported as null.
+NCU_TRAFFIC = {("d2-n10000", "fx", "force"): ("2d22c6704b91", 35_869_696 + 1_536),
+               ("d2-n10000", "fx", "ntilde"): ("2d22c6704b91", 36_569_600 + 13_568),
+               ("d2-n10000", "fx-tensor", "tc_force"): ("d7bda9a5ac2c", 74_688_512 + 2_547_712),
+               ("d2-n10000", "fx-tensor", "tc_dens"): ("d7bda9a5ac2c", 126_249_216 + 4_840_960),
+               ("d3-n32768", "fx-tensor", "tc_force"): ("d7bda9a5ac2c", 2_292_177_000 + 20_520_000),
+               ("d3-n32768", "fx-tensor", "tc_dens"): ("d7bda9a5ac2c", 3_008_816_000 + 8_002_000)}
 
 
-def kernel_source_hash() -> str:
+# The sources each family of kernels is built from: the integer fixed-point and dd kernels, and the tensor-core
+# path.  A profile records the hash of its own family's sources.
+KERNEL_SOURCES = {"fx": ("kernels.cu", "fx.cuh", "dd.cuh", "reduce.cuh"),
+                  "tc": ("tc.cu", "tc.cuh", "fx.cuh", "dd.cuh", "reduce.cuh")}
+
+
+def kernel_source_hash(family: str) -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("kernels.cu", "fx.cuh", "dd.cuh", "tc.cu", "tc.cuh", "reduce.cuh"):
+    for f in KERNEL_SOURCES[family]:
         with open(os.path.join(ROOT, "paper_2304_09139_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -694,7 +700,7 @@ def main():
                                 f"lanes/SM/clk x 148 SMs x 2032 MHz"),
                 "per_kernel_ms": {k: v[0] / v[1] for k, v in prof.items()}}
         tr = NCU_TRAFFIC.get((args.workload, "fx-tensor" if tensor else args.prec, dom_name))
-        if tr and tr[0] == kernel_source_hash():
+        if tr and tr[0] == kernel_source_hash("tc" if tensor else "fx"):
             roof["traffic"] = tr[1]
 
     # end to end through the public API with host buffers (positions in, Phi / S_max / F out)

@@ -286,40 +286,39 @@ __device__ __forceinline__ void put_digit_rows(uint8_t* base, size_t slice_strid
   }
 }
 
-// first-quadrant phasor -> (re, im) as round(x 2^104) + balanced-digit offset, and as signed Q2.126
-__device__ __forceinline__ void qent_out(const qent& z, uint4& yre, uint4& yim, fxc* q126) {
-  // unsigned Q1.127 components (value 1 is 2^127: unsigned arithmetic until after the shift)
-  const unsigned __int128 c = (unsigned __int128)q128_to_i128(z.c), sn = (unsigned __int128)q128_to_i128(z.s);
-  const uint32_t q = z.cs.w[0] & 3u;
-  const __int128 xc = (__int128)((c + ((unsigned __int128)1 << 22)) >> 23);
-  const __int128 xs = (__int128)((sn + ((unsigned __int128)1 << 22)) >> 23);
-  __int128 re, im;
-  switch (q) {  // z = i^q (c + i s)
-    case 0: re = xc; im = xs; break;
-    case 1: re = -xs; im = xc; break;
-    case 2: re = -xc; im = -xs; break;
-    default: re = xs; im = -xc; break;
+// The product z b of two first-quadrant phasors -> (re, im) as round(x 2^104) + balanced-digit offset, and as
+// signed Q2.126.  The three products of qmul give (re, im), im >= 0 (clamped at 0 as there); the product is
+// i^(q1 + q2) (re + i im), turned without renormalising to the first quadrant, and each component is rounded to
+// 2^-104 on its magnitude with the sign applied after: the same bits as rounding the renormalised non-negative
+// pair (qmul) and then turning it.
+__device__ __forceinline__ void qmul_out(const qent& z, const qent& b, uint4& yre, uint4& yim, fxc* q126) {
+  const q128 p1 = umulhi(z.c, b.c), p2 = umulhi(z.s, b.s), p3 = umulhi(z.cs, b.cs);
+  const q128 re = q128_sub(p1, p2);
+  q128 im = q128_sub(q128_sub(p3, p1), p2);
+  if ((int32_t)im.w[3] < 0) im = q128_zero();
+  const uint32_t q = (z.cs.w[0] + b.cs.w[0]) & 3u;
+  const __int128 R = q128_to_i128(re), I = q128_to_i128(im);
+  __int128 xr, xi;
+  switch (q) {  // i^q (R + i I)
+    case 0: xr = R; xi = I; break;
+    case 1: xr = -I; xi = R; break;
+    case 2: xr = -R; xi = -I; break;
+    default: xr = I; xi = -R; break;
   }
-  const __int128 b = digit_bias();
-  const unsigned __int128 ur = (unsigned __int128)(re + b), ui = (unsigned __int128)(im + b);
+  const auto rnd = [](__int128 x) -> __int128 {
+    const unsigned __int128 m = (unsigned __int128)(x < 0 ? -x : x);
+    const __int128 r = (__int128)((m + ((unsigned __int128)1 << 21)) >> 22);
+    return x < 0 ? -r : r;
+  };
+  const __int128 bias = digit_bias();
+  const unsigned __int128 ur = (unsigned __int128)(rnd(xr) + bias), ui = (unsigned __int128)(rnd(xi) + bias);
   yre = make_uint4((uint32_t)ur, (uint32_t)(ur >> 32), (uint32_t)(ur >> 64), (uint32_t)(ur >> 96));
   yim = make_uint4((uint32_t)ui, (uint32_t)(ui >> 32), (uint32_t)(ui >> 64), (uint32_t)(ui >> 96));
   if (q126) {
-    const __int128 hc = (__int128)(c >> 1), hs = (__int128)(sn >> 1);  // Q2.126
-    __int128 r2, i2;
-    switch (q) {
-      case 0: r2 = hc; i2 = hs; break;
-      case 1: r2 = -hs; i2 = hc; break;
-      case 2: r2 = -hc; i2 = -hs; break;
-      default: r2 = hs; i2 = -hc; break;
-    }
-    fxc o;
-    o.re = q128_from_i128(r2);
-    o.im = q128_from_i128(i2);
-    *q126 = o;
+    q126->re = q128_from_i128(xr);
+    q126->im = q128_from_i128(xi);
   }
 }
-
 
 }  // namespace
 
@@ -429,21 +428,23 @@ __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restri
       Yr[v] = yzero;
       Yi[v] = yzero;
       if (live && j < N) {
-        qent z;
+        qent za, zb;
         if (staged) {
           const qent* pj = Pw + jl * W23;
           const qent b = pj[n2 < 0 ? -n2 : n2];
-          z = qmul(n2 < 0 ? qconj(b) : b, pj[W2 + n3]);
+          za = n2 < 0 ? qconj(b) : b;
+          zb = pj[W2 + n3];
         } else {
           const qent* tj = tab + ((int64_t)axis * c.tc_nbuf + j) * c.tc_ntab;
-          z = qmul(tj[kPrepLow + (m >> 3)], tj[m & 7]);
+          za = tj[kPrepLow + (m >> 3)];
+          zb = tj[m & 7];
         }
         if (kind == 0) {
           fxc zq;
-          qent_out(z, Yr[v], Yi[v], &zq);
+          qmul_out(za, zb, Yr[v], Yi[v], &zq);
           reinterpret_cast<fxc*>(c.tc_a1)[(int64_t)e * c.tc_nbuf + j] = zq;
         } else {
-          qent_out(z, Yr[v], Yi[v], nullptr);
+          qmul_out(za, zb, Yr[v], Yi[v], nullptr);
         }
       }
     }
