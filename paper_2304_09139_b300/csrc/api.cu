@@ -308,6 +308,12 @@ static ssh_status stage_and_upload(ssh_ctx* h, const double* s_hi, const double*
   for (int64_t j = 0; j < N; j++) {
     for (int a = 0; a < d; a++) {
       double hi = s_hi[j * d + a], lo = s_lo ? s_lo[j * d + a] : 0.0;
+      if (!physical && hi >= 0.0 && hi < 1.0 && lo == 0.0) {
+        // already in [0, 1) with a zero low word: its own fraction (+ 0.0 turns -0 into +0, as the full path does)
+        hs[a * N + j] = hi + 0.0;
+        ls[a * N + j] = 0.0;
+        continue;
+      }
       if (!isfinite(hi) || !isfinite(lo)) {
         set_error("positions contain a non-finite value");
         return SSH_ENAN;
@@ -418,13 +424,17 @@ ssh_status ssh_get_results(ssh_ctx* h, double phi[2], double smax[2], double* F_
   if (smax) { smax[0] = sc[ssh::kScSmaxHi]; smax[1] = sc[ssh::kScSmaxLo]; }
   bool bad = !isfinite(sc[ssh::kScPhiHi]) || !isfinite(sc[ssh::kScSmaxHi]);
   if (F_hi || F_lo) {
+    uint64_t nonfinite = 0;  // branch-free: an all-ones exponent is an infinity or a NaN
     for (int64_t j = 0; j < N; j++)
       for (int a = 0; a < d; a++) {
-        double fh = hs[a * N + j], fl = ls[a * N + j];
-        bad = bad || !isfinite(fh);
+        const double fh = hs[a * N + j];
+        uint64_t u;
+        memcpy(&u, &fh, sizeof u);
+        nonfinite |= (uint64_t)(((u >> 52) & 0x7ff) == 0x7ff);
         if (F_hi) F_hi[j * d + a] = fh;
-        if (F_lo) F_lo[j * d + a] = fl;
+        if (F_lo) F_lo[j * d + a] = ls[a * N + j];
       }
+    bad = bad || nonfinite != 0;
   }
   if (bad) { set_error("non-finite energy, S_max or force"); return SSH_ENAN; }
   return SSH_OK;

@@ -280,6 +280,34 @@ def test_bad_inputs_raise(built):
         ctx.eval(7)
 
 
+def test_positions_wrap_exact(built):
+    """Fractional positions are reduced into [0, 1) exactly as dd pairs: values already in [0, 1) with a zero
+    low word pass unchanged (-0 becomes +0), and every other value is wrapped by its exact fraction."""
+    from fractions import Fraction
+    N, d = 16, 2
+    hi = np.full((N, d), 0.375)
+    lo = np.zeros((N, d))
+    cases = [(-0.0, 0.0), (1.0, 0.0), (-3.25, 0.0), (0.5, 1e-20), (0.25, -1e-20), (0.0, -1e-30),
+             (0.9999999999999999, 1e-17), (7.125, 2.0 ** -60), (-1e-300, 0.0), (0.0, -0.0), (0.7, 0.0),
+             (2.0 ** -1074, 0.0)]
+    for i, (h, l) in enumerate(cases):
+        hi[i // d, i % d] = h
+        lo[i // d, i % d] = l
+    with ssh.Context(d, N, 1.0, chi=0.3) as ctx:
+        ctx.set_positions_frac(hi, lo)
+        gh, gl = ctx.positions_frac()
+    for j in range(N):
+        for a in range(d):
+            x = Fraction(hi[j, a]) + Fraction(lo[j, a])
+            f = x - (x.numerator // x.denominator)
+            got = Fraction(gh[j, a]) + Fraction(gl[j, a])
+            assert got == f, (hi[j, a], lo[j, a], gh[j, a], gl[j, a])
+            assert 0 <= got < 1
+            if lo[j, a] == 0.0 and 0.0 <= hi[j, a] < 1.0:   # unchanged, with +0 for -0
+                assert gh[j, a] == hi[j, a] and gl[j, a] == 0.0
+                assert math.copysign(1.0, gh[j, a]) == 1.0 and math.copysign(1.0, gl[j, a]) == 1.0
+
+
 @pytest.mark.parametrize("d,N,L,chi,chunk", [(2, 10_000, 100.0, 0.45, 2048), (3, 3000, 3000 ** (1 / 3), 0.30, 1024),
                                               (1, 5000, 5000.0, 0.30, 1280)])
 def test_chunked_equals_unchunked(built, d, N, L, chi, chunk):
