@@ -119,6 +119,7 @@ static ssh_status create_from(int d, int64_t N, double L, ssh::KSet&& ks, const 
   cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, c.device);
   e = ssh::plan_upload(&c);
   if (e == cudaSuccess) e = cudaMallocHost(&h->h_stage, sizeof(double) * 2 * (size_t)d * N);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->stage_done, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
   if (e != cudaSuccess) {
     ssh_destroy(h);
@@ -205,6 +206,7 @@ void ssh_destroy(ssh_ctx* h) {
                          &c.C_hi, &c.C_lo, &c.S_hi, &c.S_lo, &c.wk, &c.coef, &c.blk, &c.scal, &c.fpart, &c.F_hi, &c.F_lo})
     free_buf(*b);
   if (h->h_stage) cudaFreeHost(h->h_stage);
+  if (h->stage_done) cudaEventDestroy(h->stage_done);
   for (ssh::ProfRec& r : c.prof.pending) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
   for (cudaEvent_t ev : c.prof.pool) cudaEventDestroy(ev);
   if (c.own_stream && c.stream) cudaStreamDestroy(c.stream);
@@ -304,6 +306,9 @@ static ssh_status stage_and_upload(ssh_ctx* h, const double* s_hi, const double*
   const int d = c.d;
   double* hs = h->h_stage;
   double* ls = h->h_stage + (size_t)d * N;
+  cudaSetDevice(c.device);
+  // the previous upload from the staging buffer must have landed before it is rewritten
+  SSH_CUDA(cudaEventSynchronize(h->stage_done), "upload positions");
   dd Ld = dd_make(c.L);
   for (int64_t j = 0; j < N; j++) {
     for (int a = 0; a < d; a++) {
@@ -325,11 +330,11 @@ static ssh_status stage_and_upload(ssh_ctx* h, const double* s_hi, const double*
       ls[a * N + j] = v.lo;
     }
   }
-  cudaSetDevice(c.device);
   SSH_CUDA(cudaMemcpyAsync(c.s_hi.p, hs, sizeof(double) * d * N, cudaMemcpyHostToDevice, c.stream), "upload positions");
   SSH_CUDA(cudaMemcpyAsync(c.s_lo.p, ls, sizeof(double) * d * N, cudaMemcpyHostToDevice, c.stream), "upload positions");
-  // the staging buffer is reused by the next call: wait for the copies before returning
-  SSH_CUDA(cudaStreamSynchronize(c.stream), "upload positions");
+  // no wait here: downloads into the staging buffer are ordered after these copies on the stream, and the next
+  // upload waits for this event before it rewrites the buffer
+  SSH_CUDA(cudaEventRecord(h->stage_done, c.stream), "upload positions");
   c.have_positions = true;
   c.have_result = false;
   return SSH_OK;

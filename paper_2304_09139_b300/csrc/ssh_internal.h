@@ -416,4 +416,5 @@ size_t device_footprint(const Ctx& c);
 struct ssh_ctx {
   ssh::Ctx c;
   double* h_stage = nullptr;  // pinned staging for positions and forces: 2 * d * N doubles
+  cudaEvent_t stage_done = nullptr;  // recorded after the last upload from h_stage
 };

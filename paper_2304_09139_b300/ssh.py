@@ -370,8 +370,8 @@ class Context:
     def results(self, want_force: bool = True):
         phi = np.zeros(2)
         smax = np.zeros(2)
-        Fh = np.zeros((self.N, self.d)) if want_force else None
-        Fl = np.zeros((self.N, self.d)) if want_force else None
+        Fh = np.empty((self.N, self.d)) if want_force else None   # every entry is written (or the call raises)
+        Fl = np.empty((self.N, self.d)) if want_force else None
         _check(self._lib.ssh_get_results(self._h, _dp(phi), _dp(smax), _dp(Fh), _dp(Fl)))
         return {"phi": phi, "smax": smax, "F_hi": Fh, "F_lo": Fl}
 
@@ -379,8 +379,8 @@ class Context:
         """Phi, S_max (dd pairs) and F (physical units, hi and lo [N, d]) through ssh_energy_grad."""
         phi = np.zeros(2)
         smax = np.zeros(2)
-        Fh = np.zeros((self.N, self.d)) if want_force else None
-        Fl = np.zeros((self.N, self.d)) if want_force else None
+        Fh = np.empty((self.N, self.d)) if want_force else None   # every entry is written (or the call raises)
+        Fl = np.empty((self.N, self.d)) if want_force else None
         _check(self._lib.ssh_energy_grad(self._h, prec, _dp(phi), _dp(smax), _dp(Fh), _dp(Fl)))
         return {"phi": phi, "smax": smax, "F_hi": Fh, "F_lo": Fl}
 
