@@ -153,10 +153,14 @@ ssh_status ssh_set_stream(ssh_ctx* ctx, void* cuda_stream);
 ssh_status ssh_sync(ssh_ctx* ctx);
 
 /* Positions in physical units r (N*d row-major, dd as hi + lo; lo may be NULL for zero).  Values are
- * wrapped into [0, L) (periodic box).  Errors: SSH_ENAN for a non-finite coordinate. */
+ * wrapped into [0, L) (periodic box).  The caller's arrays are read before the call returns, so they may be
+ * reused at once; the upload itself is queued on the context's stream, ahead of any later work there.
+ * Errors: SSH_ENAN for a non-finite coordinate (the previous positions are kept). */
 ssh_status ssh_set_positions(ssh_ctx* ctx, const double* r_hi, const double* r_lo);
 
-/* Positions as fractional coordinates s = r / L (N*d row-major, dd, lo may be NULL); exact, no division. */
+/* Positions as fractional coordinates s = r / L (N*d row-major, dd, lo may be NULL); exact, no division.
+ * Each value is reduced into [0, 1) by its exact fraction; one already in [0, 1) with a zero low word is kept
+ * as it is (-0 becomes +0).  Same ownership, ordering and errors as ssh_set_positions. */
 ssh_status ssh_set_positions_frac(ssh_ctx* ctx, const double* s_hi, const double* s_lo);
 
 /* Current fractional positions s in [0, 1) as dd (N*d row-major); either pointer may be NULL. */
