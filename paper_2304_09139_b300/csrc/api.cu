@@ -300,6 +300,24 @@ ssh_status ssh_sync(ssh_ctx* h) {
 }
 
 // s (fractional, any real) -> [0, 1) as dd, SoA staging [a][j].
+// True when every s_hi is in [+0, 1) (sign bit clear, exponent below that of 1.0; NaN, infinities and -0 fail)
+// and every s_lo is a zero of either sign: such values are their own fractions.  Branch-free bit tests.
+static bool frac_all_plain(const double* s_hi, const double* s_lo, int64_t n) {
+  uint64_t bad = 0;
+  for (int64_t i = 0; i < n; i++) {
+    uint64_t u;
+    memcpy(&u, s_hi + i, sizeof u);
+    bad |= (uint64_t)((u >> 52) >= 0x3ff);
+  }
+  if (s_lo)
+    for (int64_t i = 0; i < n; i++) {
+      uint64_t u;
+      memcpy(&u, s_lo + i, sizeof u);
+      bad |= u << 1;
+    }
+  return bad == 0;
+}
+
 static ssh_status stage_and_upload(ssh_ctx* h, const double* s_hi, const double* s_lo, bool physical) {
   ssh::Ctx& c = h->c;
   const int64_t N = c.N;
@@ -309,25 +327,32 @@ static ssh_status stage_and_upload(ssh_ctx* h, const double* s_hi, const double*
   cudaSetDevice(c.device);
   // the previous upload from the staging buffer must have landed before it is rewritten
   SSH_CUDA(cudaEventSynchronize(h->stage_done), "upload positions");
-  dd Ld = dd_make(c.L);
-  for (int64_t j = 0; j < N; j++) {
-    for (int a = 0; a < d; a++) {
-      double hi = s_hi[j * d + a], lo = s_lo ? s_lo[j * d + a] : 0.0;
-      if (!physical && hi >= 0.0 && hi < 1.0 && lo == 0.0) {
-        // already in [0, 1) with a zero low word: its own fraction (+ 0.0 turns -0 into +0, as the full path does)
-        hs[a * N + j] = hi + 0.0;
-        ls[a * N + j] = 0.0;
-        continue;
+  if (!physical && frac_all_plain(s_hi, s_lo, (int64_t)d * N)) {
+    // every value is its own fraction: the staging is a transposed copy with zero low words
+    for (int64_t j = 0; j < N; j++)
+      for (int a = 0; a < d; a++) hs[a * N + j] = s_hi[j * d + a];
+    memset(ls, 0, sizeof(double) * d * N);
+  } else {
+    dd Ld = dd_make(c.L);
+    for (int64_t j = 0; j < N; j++) {
+      for (int a = 0; a < d; a++) {
+        double hi = s_hi[j * d + a], lo = s_lo ? s_lo[j * d + a] : 0.0;
+        if (!physical && hi >= 0.0 && hi < 1.0 && lo == 0.0) {
+          // already in [0, 1) with a zero low word: its own fraction (+ 0.0 turns -0 into +0, as the full path does)
+          hs[a * N + j] = hi + 0.0;
+          ls[a * N + j] = 0.0;
+          continue;
+        }
+        if (!isfinite(hi) || !isfinite(lo)) {
+          set_error("positions contain a non-finite value");
+          return SSH_ENAN;
+        }
+        dd v = two_sum(hi, lo);
+        if (physical) v = dd_div(v, Ld);
+        v = dd_frac(v);
+        hs[a * N + j] = v.hi;
+        ls[a * N + j] = v.lo;
       }
-      if (!isfinite(hi) || !isfinite(lo)) {
-        set_error("positions contain a non-finite value");
-        return SSH_ENAN;
-      }
-      dd v = two_sum(hi, lo);
-      if (physical) v = dd_div(v, Ld);
-      v = dd_frac(v);
-      hs[a * N + j] = v.hi;
-      ls[a * N + j] = v.lo;
     }
   }
   SSH_CUDA(cudaMemcpyAsync(c.s_hi.p, hs, sizeof(double) * d * N, cudaMemcpyHostToDevice, c.stream), "upload positions");
