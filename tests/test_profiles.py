@@ -1,0 +1,47 @@
+"""The committed ncu summaries and bench.py's traffic table agree (host only).
+
+Every summary names the kernel family and the source hash it was captured at; every DRAM traffic figure that
+bench.py reports is keyed to a hash that one of those summaries records; every ncu command leaves the clocks
+alone."""
+import glob
+import os
+import re
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PROFILES = sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md")))
+HASH_LINE = re.compile(r'kernel_source_hash\("(fx|tc)"\)\): ([0-9a-f]{12})')
+
+
+def _recorded():
+    out = {}
+    for p in PROFILES:
+        with open(p) as fh:
+            m = HASH_LINE.search(fh.read())
+        assert m, f"{os.path.basename(p)} does not name its kernel family and source hash"
+        out[os.path.basename(p)] = (m.group(1), m.group(2))
+    return out
+
+
+def test_profiles_exist_and_name_their_hash():
+    assert PROFILES
+    rec = _recorded()
+    assert {fam for fam, _ in rec.values()} == {"fx", "tc"}
+
+
+def test_traffic_table_keyed_to_recorded_hashes():
+    recorded = {(fam, h) for fam, h in _recorded().values()}
+    for (workload, impl, kernel), (h, nbytes) in bench.NCU_TRAFFIC.items():
+        fam = "tc" if impl == "fx-tensor" else "fx"
+        assert (fam, h) in recorded, (workload, impl, kernel, h)
+        assert nbytes > 0
+
+
+def test_ncu_commands_keep_clocks():
+    for p in PROFILES:
+        with open(p) as fh:
+            text = fh.read()
+        for line in text.splitlines():
+            if re.match(r"\s*ncu\s", line):
+                assert "--clock-control none" in line, (os.path.basename(p), line)
