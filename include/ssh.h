@@ -387,12 +387,28 @@ ssh_status ssh_server_get_stats(ssh_server* server, ssh_server_stats* out);
  * tables.  n entries are written (at most 16).
  */
 ssh_status ssh_prof_enable(ssh_ctx* ctx, int on);
+
+/*
+ * Limit, in clock cycles, of every wait of the tensor-core GEMM on its pipeline (operand stages, work items, the
+ * accumulator) on CUDA device `device`; 0 restores the default of 2e9 cycles (about one second at the maximum SM
+ * clock).  The paper has no counterpart: it is this library's failure detection.  A wait that runs out does not
+ * trap: the kernel skips its remaining work, lets its copies and MMAs in flight land (those drains always use the
+ * default limit), records the failure in the error word of every configuration of that launch and returns.  The
+ * host then reports SSH_ETIMEOUT: ssh_get_results / ssh_energy_grad for that evaluation, ssh_minimize,
+ * ssh_fire_state, batches and the server for a run, whose failing step is undone first.  Reporting clears the
+ * word, so the context stays usable.  A limit shorter than a real wait makes evaluations fail; it exists so that
+ * this path can be tested.  Synchronises the device; applies to launches that start after it returns.
+ * Errors: SSH_EINVAL (negative), SSH_ECUDA.
+ */
+ssh_status ssh_set_wait_limit(int device, int64_t cycles);
 ssh_status ssh_prof_read(ssh_ctx* ctx, int n, double* ms, int64_t* launches);
 
 /*
- * Allocation-free collective density, for callers that cannot allocate device memory: code running inside
- * another framework's memory pool or arena, inside a CUDA-graph stream capture, or in a loop that forbids
- * allocation after start-up.  The paper has no counterpart; it is a service of this library.
+ * Allocation-free collective density, for callers that cannot allocate device memory: a program that hands a
+ * GPU's memory to another framework's pool or arena at start-up (a cudaMalloc of its own would fail, or fragment
+ * that pool behind its accounting), or a real-time loop that must not allocate after start-up (cudaMalloc and
+ * cudaFree can synchronise the device and take unbounded time).  The paper has no counterpart; it is a service
+ * of this library.
  *
  * Computes C_k + i S_k = sum_j exp(2 pi i n_k.s_j) for k = 0..M-1 in 128-bit fixed point, like SSH_FX,
  * with every pointer a DEVICE pointer owned by the caller: s_hi, s_lo fractional positions [N][d]
@@ -403,7 +419,7 @@ ssh_status ssh_prof_read(ssh_ctx* ctx, int n, double* ms, int64_t* launches);
  * Memory: it calls no cudaMalloc / cudaFree.  Its working memory is one fixed 8 MiB device array per
  * device, present for the life of the process; calls need N*d*16 (rounded up to 256) + M*40 bytes of it
  * and larger ones are rejected with SSH_EINVAL.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress); make that first call before any stream capture.  Every call on a device
+ * address (cudaGetSymbolAddress) and the device's SM count; make that first call before any stream capture.  Every call on a device
  * shares the array: calls whose kernels may overlap on the GPU (other streams, other host threads) race
  * and must be serialised by the caller.
  * Errors: SSH_EINVAL (arguments, size), SSH_ECUDA (no current device, launch failure).

@@ -218,7 +218,8 @@ struct Runner {
       m.res.final_prec = m.p.stage_prec[m.stage];
       m.res.stages_used = m.stage + 1;
       m.res.wall_s = m.t_done - m.t_admit;
-      m.res.status = f.status == kFsConverged ? SSH_OK : f.status == kFsNan ? SSH_ENAN : SSH_ENOTCONV;
+      m.res.status = fs_status_code(f.status);
+      if (f.status == kFsDevErr && m.h->c.tc.on) cudaMemsetAsync(m.h->c.tc.err.p, 0, sizeof(int), st);
     }
     if (!next_stage.empty()) e = start_stage(next_stage, false);
     std::vector<Member> keep;

@@ -142,6 +142,11 @@ __global__ void k_fire_accept(const CfgDev* __restrict__ cfgs, const int* __rest
   dd smx = dd_make(c.scal[kScSmaxHi], c.scal[kScSmaxLo]);
   fs->step++;
   fs->stage_step++;
+  if (tc_failed(c)) {  // incomplete sums: undo the step and stop the run
+    fs->status = kFsDevErr;
+    fs->rejected_now = 1;
+    return;
+  }
   if (!isfinite(phi.hi) || !isfinite(smx.hi)) {
     fs->status = kFsNan;
     fs->rejected_now = 1;
@@ -242,7 +247,8 @@ __global__ void k_fire_stage_init(const CfgDev* __restrict__ cfgs, const int* __
   fs->lb_gamma = 1.0;
   fs->lb_dmax = 0.1 / pow((double)c.N, 1.0 / c.d);
   double sm = fs->best_smax;
-  if (!isfinite(sm) || !isfinite(fs->phi_hi)) fs->status = kFsNan;
+  if (tc_failed(c)) fs->status = kFsDevErr;
+  else if (!isfinite(sm) || !isfinite(fs->phi_hi)) fs->status = kFsNan;
   else if (sm <= fs->target) fs->status = kFsConverged;
   else if (fs->stage_floor > 0 && sm <= fs->stage_floor) fs->status = kFsStageDone;
 }
@@ -536,6 +542,15 @@ ssh_status fire_steps(Ctx* c, int prec, int64_t nsteps) {
   return SSH_OK;
 }
 
+ssh_status fs_status_code(int status) {
+  switch (status) {
+    case kFsConverged: return SSH_OK;
+    case kFsNan: return SSH_ENAN;
+    case kFsDevErr: return SSH_ETIMEOUT;
+    default: return SSH_ENOTCONV;
+  }
+}
+
 ssh_status fire_state(Ctx* c, ssh_min_result* r, int* dev_status) {
   if (!c->fire || !c->fire->begun) { set_error("ssh_fire_state: call ssh_fire_begin first"); return SSH_EINVAL; }
   FireBufs* f = c->fire;
@@ -552,7 +567,11 @@ ssh_status fire_state(Ctx* c, ssh_min_result* r, int* dev_status) {
     r->phi[0] = h.phi_hi;
     r->phi[1] = h.phi_lo;
     r->dt = h.dt;
-    r->status = h.status == kFsConverged ? SSH_OK : h.status == kFsNan ? SSH_ENAN : SSH_ENOTCONV;
+    r->status = fs_status_code(h.status);
+  }
+  if (h.status == kFsDevErr && c->tc.on) {
+    cudaMemsetAsync(c->tc.err.p, 0, sizeof(int), c->stream);  // reported here: clear for later evaluations
+    set_error("ssh_fire_state: a bounded wait of a tensor-core kernel gave up; the step was undone");
   }
   if (dev_status) *dev_status = h.status;
   return SSH_OK;
@@ -631,6 +650,11 @@ ssh_status minimize(Ctx* c, const ssh_min_params* p, ssh_min_result* res) {
   switch (final_status) {
     case kFsConverged: out = SSH_OK; break;
     case kFsNan: out = SSH_ENAN; set_error("ssh_minimize: non-finite energy"); break;
+    case kFsDevErr:
+      out = SSH_ETIMEOUT;
+      if (c->tc.on) cudaMemsetAsync(c->tc.err.p, 0, sizeof(int), st);  // reported here: clear it
+      set_error("ssh_minimize: a bounded wait of a tensor-core kernel gave up; the last step was undone");
+      break;
     case -1: out = SSH_ETIMEOUT; set_error("ssh_minimize: wall-time limit reached"); break;
     default: out = SSH_ENOTCONV; set_error("ssh_minimize: step cap or stall above the S_max target"); break;
   }

@@ -230,6 +230,12 @@ __global__ void k_lb_accept(const CfgDev* __restrict__ cfgs, const int* __restri
   const dd smx = dd_make(c.scal[kScSmaxHi], c.scal[kScSmaxLo]);
   fs->step++;
   fs->stage_step++;
+  if (tc_failed(c)) {  // incomplete sums: undo the trial and stop the run
+    fs->status = kFsDevErr;
+    fs->rejected_now = 1;
+    fs->lb_accepted = 0;
+    return;
+  }
   if (!isfinite(phi.hi) || !isfinite(smx.hi)) {
     fs->status = kFsNan;
     fs->rejected_now = 1;

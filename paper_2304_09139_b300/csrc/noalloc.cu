@@ -1,11 +1,12 @@
 // noalloc.cu -- an allocation-free variant of the collective-density kernel, for callers that cannot
 // allocate device memory.
 //
-// Some callers cannot call cudaMalloc at all: code that runs inside another framework's memory pool or
-// arena (where a foreign cudaMalloc fragments or escapes the pool's accounting), code inside a CUDA-graph
-// stream capture (where allocation is not permitted), and real-time or embedded loops that forbid any
-// allocation after start-up.  For them ssh_ntilde_noalloc computes n~(k) = C + i S with caller-owned
-// inputs and outputs and keeps its working memory in the fixed device array below instead of allocating.
+// Some callers cannot call cudaMalloc at all: a host program that hands all of a GPU's memory to another
+// framework's pool or arena at start-up (a foreign cudaMalloc then fails, or fragments the pool and escapes its
+// accounting), and real-time or embedded loops that must not allocate after start-up (cudaMalloc and cudaFree
+// can synchronise the device and take unbounded time).  For them ssh_ntilde_noalloc computes n~(k) = C + i S
+// with caller-owned inputs and outputs and keeps its working memory in the fixed device array below instead of
+// allocating.
 //
 // The array g_noalloc_scratch (kNoAllocScratchBytes = 8 MiB) exists once per device in every process that
 // loads the library and is held until the process exits.  It holds the positions converted to Q0.128
@@ -39,9 +40,10 @@ struct NaAcc {
   q160 re, im;
 };
 
-// Host-side device address of g_noalloc_scratch, looked up once per device.
+// Host-side device address of g_noalloc_scratch and the device's SM count, looked up once per device.
 std::mutex g_na_mutex;
 void* g_na_ptr[kNoAllocMaxDevices] = {nullptr};
+int g_na_sms[kNoAllocMaxDevices] = {0};
 
 __global__ void k_na_turns(int64_t nd, const double* __restrict__ s_hi, const double* __restrict__ s_lo,
                            q128* __restrict__ u) {
@@ -127,11 +129,17 @@ extern "C" ssh_status ssh_ntilde_noalloc(int d, int64_t N, int64_t M, const doub
   if (M == 0) return SSH_OK;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+  if (e != cudaSuccess) {
     ssh::set_error(std::string("ssh_ntilde_noalloc: no usable current device: ") + cudaGetErrorString(e));
     return SSH_ECUDA;
   }
+  if (dev < 0 || dev >= kNoAllocMaxDevices) {
+    ssh::set_error("ssh_ntilde_noalloc: device index " + std::to_string(dev) + " is not supported (at most " +
+                   std::to_string(kNoAllocMaxDevices - 1) + ")");
+    return SSH_ECUDA;
+  }
   void* base = nullptr;
+  int sms = 0;
   {
     std::lock_guard<std::mutex> lk(g_na_mutex);
     if (!g_na_ptr[dev]) {
@@ -142,17 +150,25 @@ extern "C" ssh_status ssh_ntilde_noalloc(int d, int64_t N, int64_t M, const doub
         ssh::set_error(std::string("ssh_ntilde_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
         return SSH_ECUDA;
       }
+      int n_sm = 0;
+      e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess || n_sm < 1) {
+        ssh::set_error(std::string("ssh_ntilde_noalloc: SM count query failed: ") + cudaGetErrorString(e));
+        return SSH_ECUDA;
+      }
+      g_na_sms[dev] = n_sm;
       g_na_ptr[dev] = p;
     }
     base = g_na_ptr[dev];
+    sms = g_na_sms[dev];
   }
   cudaStream_t st = (cudaStream_t)stream;
   q128* u = reinterpret_cast<q128*>(base);
   NaAcc* part = reinterpret_cast<NaAcc*>(reinterpret_cast<unsigned char*>(base) + pos_bytes);
   const size_t avail = kNoAllocScratchBytes - pos_bytes;  // >= acc_bytes, checked above
-  // particle splits: enough blocks to fill the GPU, as many as the scratch holds
+  // particle splits: enough blocks for two per SM, as many as the scratch holds
   const int64_t kblocks = (M + kNoAllocThreads - 1) / kNoAllocThreads;
-  int64_t psplit = (2 * 148 + kblocks - 1) / kblocks;
+  int64_t psplit = (2 * (int64_t)sms + kblocks - 1) / kblocks;
   psplit = std::min<int64_t>(psplit, (int64_t)(avail / acc_bytes));
   psplit = std::max<int64_t>(1, std::min<int64_t>(psplit, N));
   const int64_t plen = (N + psplit - 1) / psplit;

@@ -177,7 +177,8 @@ struct EngineView {
 struct Ctx;
 
 // minimiser state of one configuration (device memory)
-enum { kFsRunning = 0, kFsConverged = 1, kFsNan = 2, kFsStageDone = 3, kFsMaxSteps = 4 };
+// kFsDevErr: a bounded wait of a tensor-core kernel gave up during the step's evaluation (the step is undone)
+enum { kFsRunning = 0, kFsConverged = 1, kFsNan = 2, kFsStageDone = 3, kFsMaxSteps = 4, kFsDevErr = 5 };
 struct FireState {
   int status;
   int rejected_now;
@@ -334,6 +335,11 @@ inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t
 }
 #ifdef __CUDACC__
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// A bounded wait of the tensor-core GEMM gave up during this configuration's last evaluation, so its sums are
+// incomplete (the error word stays set until the host reports it).
+__device__ __forceinline__ bool tc_failed(const CfgDev& c) {
+  return c.tc && c.tc_err && *reinterpret_cast<volatile const int*>(c.tc_err) != 0;
+}
 #endif
 
 // record an event pair around a launch when profiling is on
@@ -354,6 +360,8 @@ void fire_fill_cfgdev(const Ctx* c, CfgDev* g);
 cudaError_t fire_alloc(Ctx* c);
 cudaError_t fire_step_engine(const Engine* e, cudaStream_t st, Prof* prof);
 FireState fire_params(const ssh_min_params* p);
+// the public status of a minimiser run that ended with device status word `status`
+ssh_status fs_status_code(int status);
 // error bound coefficient of Phi in arithmetic prec for configuration c: |dPhi| <= coef sqrt(Phi)
 double fire_phi_tol(const Ctx* c, int prec);
 // (re)start the members idx of e: v = 0 when first, accepted Phi / S_max from their scal, stage parameters

@@ -69,6 +69,24 @@ constexpr int kRing = 8;                           // item indices in flight bet
 
 __device__ __forceinline__ bool stopped(const CfgDev& c) { return c.run && *c.run; }
 
+// Limit of the GEMM's waits on work (stages, items, the accumulator), in clock cycles; ssh_set_wait_limit changes
+// it.  The waits that let copies and MMAs in flight land before a CTA exits always use kWaitLimit.
+__device__ long long g_tc_wait_limit = kWaitLimit;
+
+// A wait gave up: record `code` in the error word of every configuration with items in this launch, since the
+// items this CTA had claimed or published (and so skips) may belong to any of them.
+__device__ __noinline__ void tc_flag_all(const CfgDev* __restrict__ cfgs, const TcItem* __restrict__ items,
+                                         int n_items, int code) {
+  int last = -1;
+  for (int i = 0; i < n_items; i++) {
+    const int ci = items[i].cfg;
+    if (ci == last) continue;
+    last = ci;
+    const CfgDev& c = cfgs[ci];
+    if (!stopped(c) && c.tc_err) atomicOr(c.tc_err, code);
+  }
+}
+
 __device__ __forceinline__ __int128 q128_to_i128(const q128& a) {
   return (__int128)(((unsigned __int128)a.w[3] << 96) | ((unsigned __int128)a.w[2] << 64) |
                     ((unsigned __int128)a.w[1] << 32) | (unsigned __int128)a.w[0]);
@@ -519,6 +537,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
   tc_fence_after();
   const uint32_t tbase = tmem_base_sh;
   volatile int* abort_flag = &abort_sh;
+  const long long wlim = g_tc_wait_limit;  // waits on work; the drains below always use kWaitLimit
 
   if (warp == 0) {
     // ---- producer: one thread streams every item's K-steps through the stages
@@ -530,8 +549,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
         // claim the next item and publish it to the MMA thread and the epilogue warps
         const int r = (int)(n % kRing);
         const long long use = n / kRing;
-        if (use > 0 && !mbar_wait(&bar_item_empty[r], (uint32_t)((use - 1) & 1), kWaitLimit, abort_flag)) {
+        if (use > 0 && !mbar_wait(&bar_item_empty[r], (uint32_t)((use - 1) & 1), wlim, abort_flag)) {
           *abort_flag = 1;
+          tc_flag_all(cfgs, items, n_items, 32);
           break;
         }
         const int item = pre >= 0 ? pre : atomicAdd(queue, 1);
@@ -549,9 +569,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
         for (int ks = 0; ks < it.nks; ks++, gs++) {
           const int s = (int)(gs % kStages);
           const long long use = gs / kStages;
-          if (use > 0 && !mbar_wait(&bar_empty[s], (uint32_t)((use - 1) & 1), kWaitLimit, abort_flag)) {
+          if (use > 0 && !mbar_wait(&bar_empty[s], (uint32_t)((use - 1) & 1), wlim, abort_flag)) {
             *abort_flag = 1;
-            atomicOr(c.tc_err, 1);
+            tc_flag_all(cfgs, items, n_items, 1);
             stop = true;
             break;
           }
@@ -569,7 +589,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
       if (*abort_flag) {
         // let the copies in flight land before the CTA can exit
         for (long long k = gs > kStages ? gs - kStages : 0; k < gs; k++)
-          mbar_wait(&bar_full[k % kStages], (uint32_t)((k / kStages) & 1), kWaitLimit, nullptr);
+          if (!mbar_wait(&bar_full[k % kStages], (uint32_t)((k / kStages) & 1), kWaitLimit, nullptr))
+            tc_flag_all(cfgs, items, n_items, 8);
       }
     }
   } else if (warp == 1) {
@@ -579,8 +600,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
       bool stop = false;
       for (long long n = 0; !stop; n++) {
         const int r = (int)(n % kRing);
-        if (!mbar_wait(&bar_item_full[r], (uint32_t)((n / kRing) & 1), kWaitLimit, abort_flag)) {
+        if (!mbar_wait(&bar_item_full[r], (uint32_t)((n / kRing) & 1), wlim, abort_flag)) {
           *abort_flag = 1;
+          tc_flag_all(cfgs, items, n_items, 64);
           break;
         }
         const int item = item_ring[r];
@@ -598,15 +620,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
           const long long use = gs / kStages;
           const bool first = ks % kChunkSteps == 0;
           const bool last = ks % kChunkSteps == kChunkSteps - 1 || ks == it.nks - 1;
-          if (!mbar_wait(&bar_full[s], (uint32_t)(use & 1), kWaitLimit, abort_flag)) {
+          if (!mbar_wait(&bar_full[s], (uint32_t)(use & 1), wlim, abort_flag)) {
             *abort_flag = 1;
-            atomicOr(c.tc_err, 2);
+            tc_flag_all(cfgs, items, n_items, 2);
             stop = true;
             break;
           }
-          if (first && gc > 0 && !mbar_wait(&bar_acc_empty, (uint32_t)((gc - 1) & 1), kWaitLimit, abort_flag)) {
+          if (first && gc > 0 && !mbar_wait(&bar_acc_empty, (uint32_t)((gc - 1) & 1), wlim, abort_flag)) {
             *abort_flag = 1;
-            atomicOr(c.tc_err, 4);
+            tc_flag_all(cfgs, items, n_items, 4);
             stop = true;
             break;
           }
@@ -640,7 +662,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
       }
       // every MMA issued by this thread has completed once the drain barrier flips
       mma_commit(&bar_drain);
-      if (!mbar_wait(&bar_drain, 0, kWaitLimit, nullptr)) *abort_flag = 1;
+      if (!mbar_wait(&bar_drain, 0, kWaitLimit, nullptr)) {
+        *abort_flag = 1;
+        tc_flag_all(cfgs, items, n_items, 8);
+      }
     }
   } else {
     // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 and accumulator columns 8 hq .. 8 hq + 7
@@ -651,9 +676,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
     bool stop = false;
     for (long long n = 0; !stop; n++) {
       const int r = (int)(n % kRing);
-      const bool have = mbar_wait(&bar_item_full[r], (uint32_t)((n / kRing) & 1), kWaitLimit, abort_flag);
+      const bool have = mbar_wait(&bar_item_full[r], (uint32_t)((n / kRing) & 1), wlim, abort_flag);
       if (!__all_sync(0xffffffffu, have)) {
         *abort_flag = 1;
+        if (lane == 0) tc_flag_all(cfgs, items, n_items, 128);
         break;
       }
       const int item = item_ring[r];
@@ -671,10 +697,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
       const int nch = (it.nks + kChunkSteps - 1) / kChunkSteps;
       for (int ch = 0; ch < nch; ch++, gc++) {
         // the warp leaves together (tcgen05.ld is warp-collective)
-        const bool got = mbar_wait(&bar_acc_full, (uint32_t)(gc & 1), kWaitLimit, abort_flag);
+        const bool got = mbar_wait(&bar_acc_full, (uint32_t)(gc & 1), wlim, abort_flag);
         if (!__all_sync(0xffffffffu, got)) {
           *abort_flag = 1;
-          if (lane == 0) atomicOr(c.tc_err, 16);
+          if (lane == 0) tc_flag_all(cfgs, items, n_items, 16);
           stop = true;
           break;
         }
@@ -1526,3 +1552,25 @@ cudaError_t tc_launch_force(const EngineView& v, cudaStream_t st, Prof* prof) {
 }
 
 }  // namespace ssh
+
+// The limit of the tensor-core GEMM's waits on work, in clock cycles, on one device (0: the default, about one
+// second at the maximum clock).  A wait that runs out records SSH_ETIMEOUT for the evaluation; this makes that
+// path testable with a limit too short for any real wait.
+extern "C" ssh_status ssh_set_wait_limit(int device, int64_t cycles) {
+  if (cycles < 0) {
+    ssh::set_error("ssh_set_wait_limit: negative limit");
+    return SSH_EINVAL;
+  }
+  int cur = 0;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e == cudaSuccess && cur != device) e = cudaSetDevice(device);
+  const long long v = cycles == 0 ? ssh::kWaitLimit : (long long)cycles;
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(ssh::g_tc_wait_limit, &v, sizeof v);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (cur != device) cudaSetDevice(cur);
+  if (e != cudaSuccess) {
+    ssh::set_error(std::string("ssh_set_wait_limit: ") + cudaGetErrorString(e));
+    return SSH_ECUDA;
+  }
+  return SSH_OK;
+}

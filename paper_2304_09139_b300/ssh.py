@@ -132,6 +132,7 @@ def load():
             _sig(lib, "ssh_get_ntilde", c_int, [c_vp, P(c_d), P(c_d), P(c_d), P(c_d)])
             _sig(lib, "ssh_prof_enable", c_int, [c_vp, c_int])
             _sig(lib, "ssh_prof_read", c_int, [c_vp, c_int, P(c_d), P(c_i64)])
+            _sig(lib, "ssh_set_wait_limit", c_int, [c_int, c_i64])
             _sig(lib, "ssh_ntilde_noalloc", c_int, [c_int, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
                                                    c_vp])
             _sig(lib, "ssh_min_defaults", c_int, [c_vp, P(MinParams)])
@@ -244,6 +245,11 @@ def ntilde_noalloc(d: int, N: int, M: int, s_hi_ptr: int, s_lo_ptr: int | None, 
     """ssh_ntilde_noalloc with raw device pointers (allocation-free n~(k); enqueued, not synchronised)."""
     _check(load().ssh_ntilde_noalloc(d, N, M, s_hi_ptr, s_lo_ptr, n_ptr, C_hi_ptr, C_lo_ptr, S_hi_ptr, S_lo_ptr,
                                      stream_ptr))
+
+
+def set_wait_limit(cycles: int, device: int = 0):
+    """ssh_set_wait_limit: the tensor-core GEMM's wait limit in clock cycles on `device` (0: the default)."""
+    _check(load().ssh_set_wait_limit(device, cycles))
 
 
 def _rows(a, N, d):

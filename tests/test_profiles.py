@@ -7,6 +7,8 @@ import glob
 import os
 import re
 
+import pytest
+
 import bench
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -45,3 +47,14 @@ def test_ncu_commands_keep_clocks():
         for line in text.splitlines():
             if re.match(r"\s*ncu\s", line):
                 assert "--clock-control none" in line, (os.path.basename(p), line)
+
+
+def test_profiles_match_current_sources():
+    """A summary captured at other kernel sources is stale: report it (xfail) instead of passing silently."""
+    stale = []
+    for name, (fam, h) in _recorded().items():
+        now = bench.kernel_source_hash(fam)
+        if h != now:
+            stale.append(f"{name}: captured at {fam} {h}, sources now {now}")
+    if stale:
+        pytest.xfail("ncu summaries need recapturing at the current sources: " + "; ".join(stale))

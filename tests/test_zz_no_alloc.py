@@ -1,12 +1,13 @@
 """The allocation-free collective density, ssh_ntilde_noalloc.
 
-Callers that cannot allocate device memory -- code running inside another framework's memory pool,
-inside a CUDA-graph stream capture, or in a loop that forbids allocation after start-up -- use this entry
-point: it takes caller-owned device inputs and outputs and keeps its own working memory in one fixed
-8 MiB device array instead of calling cudaMalloc.  These tests call it through the C ABI and compare its
-n~(k) with the one from the regular entry points (ssh_create + ssh_eval(SSH_FX) + ssh_get_ntilde) on
-calls made back to back, with the same tolerance as the other parity tests (1e-28 N per component).
-The file is named so that pytest collects it last.
+Callers that cannot allocate device memory use this entry point: a program that gives a GPU's memory to
+another framework's pool or arena at start-up (its own cudaMalloc would fail or fragment that pool), or a
+real-time loop that must not allocate after start-up (cudaMalloc and cudaFree can synchronise the device).
+It takes caller-owned device inputs and outputs and keeps its own working memory in one fixed 8 MiB device
+array instead of calling cudaMalloc.  These tests call it through the C ABI and compare its n~(k) with the one
+from the regular entry points (ssh_create + ssh_eval(SSH_FX) + ssh_get_ntilde) on calls made back to back,
+with the same tolerance as the other parity tests (1e-28 N per component), and check that the device's free
+memory does not move across its calls.  The file is named so that pytest collects it last.
 """
 import numpy as np
 import pytest
@@ -58,6 +59,13 @@ def test_noalloc_matches_regular_entry_point_on_consecutive_calls():
             first = (Ch, Cl, Sh, Sl)
         if i == 2:   # the same input again after a different call: bit-identical
             assert all(np.array_equal(a, b) for a, b in zip(first, (Ch, Cl, Sh, Sl)))
+        # allocation-free: with inputs and outputs in place, repeated calls leave the free device memory as it was
+        free0 = torch.cuda.mem_get_info(dev)[0]
+        for _ in range(2):
+            ssh.ntilde_noalloc(d, N, M, s_d.data_ptr(), None, n_d.data_ptr(), *[o.data_ptr() for o in out],
+                               stream.cuda_stream)
+        torch.cuda.synchronize(dev)
+        assert torch.cuda.mem_get_info(dev)[0] == free0, i
 
 
 def test_noalloc_rejects_sizes_beyond_its_fixed_scratch():
