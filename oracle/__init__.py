@@ -65,6 +65,9 @@ def _load():
             lib.oracle_phi_grad_w.restype = ctypes.c_int
             lib.oracle_phi_grad_w.argtypes = [ctypes.c_int, i64, d, P(d), P(d), i64, P(i32), P(d), P(d), P(d), P(d),
                                               P(d), P(d), ctypes.c_int]
+            lib.oracle_force_at.restype = ctypes.c_int
+            lib.oracle_force_at.argtypes = [ctypes.c_int, i64, d, P(d), P(d), i64, P(i32), P(d), P(d), P(d), P(d),
+                                            ctypes.c_int]
             lib.oracle_fire.restype = ctypes.c_int
             lib.oracle_fire.argtypes = [ctypes.c_int, i64, d, P(d), P(d), i64, P(i32), P(FireParams), P(i64),
                                         P(d), P(d), ctypes.c_int]
@@ -209,6 +212,24 @@ def phi_grad(s_hi, s_lo, n, L: float, want_force: bool = True, want_cs: bool = F
     if want_cs:
         out["C"], out["S"] = C[:M], S[:M]
     return out
+
+
+def force_at(s_hi, s_lo, n, L: float, C, S, weights=None, nthreads: int = 0):
+    """F (Eq. force, physical units) at the given particles, from given collective densities (C, S) as [M, 2]
+    (hi, lo) arrays instead of the particles' own: the force on those particles inside a configuration whose
+    n~(k) is C + iS.  Returns an [P, d, 2] array."""
+    n = np.ascontiguousarray(n, dtype=np.int32)
+    d = n.shape[1]
+    s_hi, s_lo = _pos(s_hi, s_lo, d)
+    P_, M = s_hi.shape[0], n.shape[0]
+    C = np.ascontiguousarray(C, dtype=np.float64).reshape(M, 2)
+    S = np.ascontiguousarray(S, dtype=np.float64).reshape(M, 2)
+    w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float64).reshape(M)
+    F = np.zeros((max(P_, 1), d, 2))
+    rc = _load().oracle_force_at(d, P_, L, _dp(s_hi), _dp(s_lo), M, _ip(n), _dp(C), _dp(S), _dp(w), _dp(F), nthreads)
+    if rc != 0:
+        raise RuntimeError(f"oracle_force_at rc={rc}")
+    return F[:P_]
 
 
 def fire(s_hi, s_lo, n, L: float, *, dt0: float, dt_max: float, alpha_start: float = 0.1, f_alpha: float = 0.99,

@@ -13,7 +13,8 @@
  *   n~(k)            -- collective density, sum_j exp(i k.r_j)             (Eq. ntilde)
  *   Phi, S(k), S_max -- Phi = sum over the half-space of |n~(k)|^2 (constant term dropped, eps0 = 1),
  *                       S(k) = |n~(k)|^2 / N, S_max = max S(k)              (Eqs. energy, structurefactor, smax)
- *   F_j              -- F_j = -grad_j Phi                                   (Eq. force)
+ *   F_j              -- F_j = -grad_j Phi                                   (Eq. force); also at chosen
+ *                       particles from given (C, S), for checks of large systems
  *   weights          -- a general non-negative v~(k) per wavevector (the paper's v~(k) > 0 that selects
  *                       ground states): Phi = sum v~ |n~|^2, F = -grad Phi; S(k) is unweighted (Eqs. energy, force)
  *   FIRE             -- Bitzek et al. 2006 structural relaxation, the minimiser the paper uses (Simulations)
@@ -249,6 +250,32 @@ int oracle_phi_grad_w(int d, int64_t N, double L, const double *s_hi, const doub
   }
   free(C);
   free(S);
+  return 0;
+}
+
+/* F_{j,a} = (4 pi / L) sum_k v~_k n_a [C_k sin(th_jk) - S_k cos(th_jk)] (Eq. force) at P given particles, from given
+ * collective densities C_k + i S_k (dd pairs, lifted exactly to binary128) instead of the particles' own: the
+ * force on those particles inside a configuration whose n~(k) is (C, S).  The per-pair sum is the one of
+ * oracle_phi_grad_w, k ascending.  w may be NULL (every weight 1).  F_out is [P][d][2] (hi, lo). */
+int oracle_force_at(int d, int64_t P, double L, const double *s_hi, const double *s_lo, int64_t M, const int32_t *n,
+                    const double *C_in, const double *S_in, const double *w, double *F_out, int nthreads) {
+  if (d < 1 || d > 4 || P < 0 || M < 0 || !(L > 0)) return -1;
+  set_threads(nthreads);
+  const q_t pref = 2 * Q_2PI / (q_t)L; /* 4 pi / L */
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t j = 0; j < P; j++) {
+    q_t f[4] = {0, 0, 0, 0};
+    for (int64_t k = 0; k < M; k++) {
+      q_t c, s;
+      q_t t = phase_turns(d, n + k * d, s_hi + j * d, s_lo ? s_lo + j * d : NULL);
+      cos_sin_turns(t, &c, &s);
+      const q_t Ck = (q_t)C_in[2 * k] + (q_t)C_in[2 * k + 1];
+      const q_t Sk = (q_t)S_in[2 * k] + (q_t)S_in[2 * k + 1];
+      q_t t2 = (w ? (q_t)w[k] : (q_t)1) * (Ck * s - Sk * c);
+      for (int a = 0; a < d; a++) f[a] += (q_t)n[k * d + a] * t2;
+    }
+    for (int a = 0; a < d; a++) q_to_dd(pref * f[a], &F_out[(j * d + a) * 2], &F_out[(j * d + a) * 2 + 1]);
+  }
   return 0;
 }
 

@@ -350,3 +350,72 @@ def test_pair_histogram_chain_and_symmetry(oracle_mod):
     r = synth.positions(5, 300, 2)
     c = oracle_mod.pair_histogram(r, 300 ** 0.5, 300, 0.45 * 300 ** 0.5, 50).astype(np.int64)
     assert np.all(c % 2 == 0) and c.sum() > 0
+
+
+# ------------------------------------------------------------------ anisotropic exclusion regions (Conclusions)
+
+def _k_for_r2(r2: float, L: float) -> float:
+    """A cutoff K whose squared index radius (K L / 2 pi)^2 is r2 (chosen half-way between integers)."""
+    return 2 * math.pi * math.sqrt(r2) / L
+
+
+@pytest.mark.parametrize("d,w,axis,q", [(2, (1, 4), 1, 2), (2, (4, 1), 0, 2), (3, (1, 1, 9), 2, 3),
+                                         (3, (9, 1, 1), 0, 3), (3, (1, 4, 1), 1, 2)])
+def test_region_square_weight_is_the_ball_rescaled(oracle_mod, d, w, axis, q):
+    """With weight q^2 on one axis and 1 on the others, sum_a w_a n_a^2 <= R^2 is the image of the ball's vectors
+    whose component on that axis is a multiple of q, divided there by q: the norm is unchanged, division by q keeps
+    the signs (so the half space) and the lexicographic order.  The ball comes from oracle.kset, pinned by Jacobi's
+    counts and brute force.  A weight applied to the wrong axis, or divided instead of multiplied, fails."""
+    L = 10.0
+    K = _k_for_r2(300.5 if d == 2 else 60.5, L)
+    ball = oracle_mod.kset(d, 100, L, K=K)
+    keep = ball[:, axis] % q == 0
+    want = ball[keep].copy()
+    want[:, axis] //= q
+    got = oracle_mod.kset_region(d, 100, L, w, K=K)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("w3,r2", [(3, 200), (5, 333), (7, 1000)])
+def test_region_counts_by_columns(oracle_mod, w3, r2):
+    """The points of n1^2 + w n2^2 <= r2 counted column by column, sum over n2 of 2 floor(sqrt(r2 - w n2^2)) + 1,
+    give the full region; the half space holds (count - 1) / 2 of them, and the chi mode takes the first M of the
+    K-mode list."""
+    total = sum(2 * math.isqrt(r2 - w3 * b * b) + 1 for b in range(-math.isqrt(r2 // w3), math.isqrt(r2 // w3) + 1))
+    L = 10.0
+    got = oracle_mod.kset_region(2, 100, L, (1, w3), K=_k_for_r2(r2 + 0.5, L))
+    assert len(got) == (total - 1) // 2
+    q = (got.astype(np.int64) ** 2 * np.array([1, w3])).sum(1)
+    assert np.all(np.diff(q) >= 0) and q.max() <= r2
+    N = 200
+    M = oracle_mod.chi_to_m(2, N, 0.2)
+    chi_set = oracle_mod.kset_region(2, N, L, (1, w3), chi=0.2)
+    assert len(chi_set) == M and np.array_equal(chi_set, got[:M])
+
+
+# ------------------------------------------------------------------ force at chosen particles (Eq. force)
+
+@pytest.mark.parametrize("d,weighted", [(2, False), (3, False), (2, True)])
+def test_force_at_equals_the_full_force(oracle_mod, d, weighted):
+    """force_at over every particle with the configuration's own (C, S) is the full force of phi_grad (pinned above by
+    finite differences and the pair form), to the rounding of (C, S) to double-double."""
+    N = 60
+    L = N ** (1 / d)
+    s = synth.positions(77 + d, N, d)
+    n = oracle_mod.kset(d, N, L, chi=0.3)
+    w = 0.5 + synth.uniform01(5, len(n)) if weighted else None
+    r = oracle_mod.phi_grad(s, None, n, L, want_cs=True, weights=w)
+    sel = np.array([0, 7, 31, N - 1])
+    F = oracle_mod.force_at(s[sel], None, n, L, r["C"], r["S"], weights=w)
+    scale = 4 * math.pi / L * (np.abs(n) * (np.abs(dd(r["C"])) + np.abs(dd(r["S"])) + math.sqrt(N))[:, None]).sum(0)
+    assert np.all(np.abs(dd(F) - dd(r["F"][sel])) <= 1e-30 * scale[None, :])
+
+
+def test_force_at_single_particle_is_zero(oracle_mod):
+    """A lone particle feels no force from its own density: with (C, S) = (cos, sin) of its own phases,
+    C sin - S cos = 0 term by term."""
+    s = synth.positions(9, 1, 2)
+    n = oracle_mod.kset(2, 50, 7.0, chi=0.4)
+    C, S = oracle_mod.ntilde(s, None, n)
+    F = oracle_mod.force_at(s, None, n, 7.0, C, S)
+    assert np.all(np.abs(dd(F)) <= 1e-30 * len(n) * 4)
