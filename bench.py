@@ -51,11 +51,36 @@ def tc_flop_per_pair(d: int) -> dict:
 
 
 F64_FP64_PER_PAIR = {"ntilde": 6, "force": 8}
-# Peaks derived from unit counts and the maximum SM clock (148 SMs, 2032 MHz): 64 IMAD lanes per SM per
-# clock; 2 FP64 FMA lanes per SM per clock (1.2 TFLOP/s).
-SM_COUNT, SM_MAX_MHZ = 148, 2032.0
-IMAD_PEAK = 64 * SM_COUNT * SM_MAX_MHZ * 1e6
-FP64_PEAK = 2 * SM_COUNT * SM_MAX_MHZ * 1e6
+
+
+def pipe_rates_block(ssh, dev) -> dict:
+    """Measured operation rates of the pipes the non-tensor arithmetics run on (ssh_pipe_rate: every SM busy with
+    independent chains of one operation for about 100 ms, CUDA events, best of three), with the SM count read from
+    the device and the SM clock sampled while they run.  The FP64 FMA and IMAD rates are the roofline denominators
+    of the dd and integer fixed-point kernels; the nominal figures (unit counts x the maximum clock) are context."""
+    import torch
+    props = torch.cuda.get_device_properties(dev)
+    out = {"sm_count": props.multi_processor_count}
+    with Clocks(dev) as clk:
+        for kind in ("fp64_fma", "fp32_fma", "imad", "imad_hi", "dd_cmac", "fx_cmul"):
+            r, ms = ssh.pipe_rate(kind, dev)
+            out[kind] = {"ops_per_s": r, "ms": ms}
+    out["clocks"] = clk.summary()
+    sm, mhz = props.multi_processor_count, MEASURED.get("sm_max_mhz", 2032.0)
+    out["nominal"] = {"fp64_fma": 2 * sm * mhz * 1e6, "imad": 64 * sm * mhz * 1e6,
+                      "note": "unit counts x maximum SM clock: 2 FP64 FMA and 64 IMAD lanes per SM per clock"}
+    return out
+
+
+def _measured() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+MEASURED = _measured()
 
 
 def _measured_bf16_peak() -> float:
@@ -112,11 +137,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-minimize", action="store_true")
-    ap.add_argument("--minimize-dd", action="store_true", help="also time FP64->dd and all-dd quenches")
+    ap.add_argument("--no-dd-ladder", action="store_true",
+                    help="skip the FP64 -> dd and all-dd quenches of the d=2 N=100 and N=10^4 workloads (about 4 min)")
+    ap.add_argument("--dd-seconds", type=float, default=300.0, help="wall limit of each dd-ladder quench")
     ap.add_argument("--minimize-seconds", type=float, default=150.0)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the d=3, N=32768 block")
-    ap.add_argument("--no-large-staged", action="store_true", help="skip its staged FP64 -> fixed point quench")
+    ap.add_argument("--large-staged", action="store_true", help="also its staged FP64 -> fixed point quench (about 1 min)")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-post", action="store_true", help="skip the pair-histogram (g_2) timing")
     ap.add_argument("--no-paper-scale", action="store_true",
@@ -269,8 +296,9 @@ class Clocks:
                 "source": "nvidia-smi, 200 ms"}
 
 
-def cpu_sample(N, d, L, chi, seed, frac_k=8, nthreads=0):
-    """One bounded oracle Phi+grad sample: the first M/frac_k wavevectors, all particles, both sums."""
+def cpu_sample(N, d, L, chi, seed, frac_k=8, nthreads=0, want_cs=False):
+    """One bounded oracle Phi+grad sample: the first M/frac_k wavevectors, all particles, both sums.  With
+    want_cs also the oracle's (C, S) of those wavevectors ([Ms, 2] dd pairs each)."""
     import oracle
     from paper_2304_09139_b300 import synth
     oracle.build()
@@ -278,17 +306,17 @@ def cpu_sample(N, d, L, chi, seed, frac_k=8, nthreads=0):
     Ms = max(1, len(n) // frac_k)
     s = synth.positions(seed, N, d)
     t = time.perf_counter()
-    oracle.phi_grad(s, None, n[:Ms], L, nthreads=nthreads)
+    r = oracle.phi_grad(s, None, n[:Ms], L, nthreads=nthreads, want_cs=want_cs)
     dt = time.perf_counter() - t
-    return Ms * N / dt, Ms, oracle.num_threads() if nthreads == 0 else nthreads
+    out = (Ms * N / dt, Ms, oracle.num_threads() if nthreads == 0 else nthreads)
+    return out + ((r["C"], r["S"]),) if want_cs else out
 
 
 def minimize_block(ssh, synth, w, dev, stream, with_dd=False, max_seconds=150):
     """Time full quenches of the workload from its random start to S_max <= 1e-36 (configs per hour): the
     library's default ladder (all fixed point on a tensor-core context) with FIRE (the paper's minimiser) and
     with L-BFGS, staged FP64 -> fixed point (the paper's cheap first stage), and all fixed point on the integer
-    pipes; with --minimize-dd also FP64 -> dd
-    and all-dd, the paper's arithmetic (about a minute and several minutes)."""
+    pipes; with_dd also FP64 -> dd and all-dd, the paper's own arithmetic (see dd_ladder_block)."""
     out = {}
     runs = [("default", None), ("lbfgs", None), ("fp64_then_fx", [ssh.FP64, ssh.FX]), ("all_fx", [ssh.FX]),
             ("all_fx_integer", [ssh.FX])]
@@ -307,6 +335,66 @@ def minimize_block(ssh, synth, w, dev, stream, with_dd=False, max_seconds=150):
                      "stage_wall_s": r["stage_wall_s"][:ns], "smax": r["smax"][0],
                      "configs_per_hour": 3600.0 / r["wall_s"] if r["status"] == 0 else 0.0}
         c.close()
+    return out
+
+
+def dd_ladder_block(ssh, synth, dev, stream, max_seconds=300.0):
+    """The paper's precision ladder in its own arithmetic: FP64 descent to the FP64 floor, then the double-double
+    polish, against double-double from the start, both with FIRE (the paper's minimiser) to S_max <= 1e-36 from
+    the same random start, on the d=2 N=100 (chi=0.30) and N=10^4 (chi=0.45) workloads.  Each final state is
+    confirmed by the binary128 oracle's S_max over every wavevector (one evaluation), and configs per hour is
+    3600 / wall time of the quench."""
+    import oracle
+    oracle.build()
+    out = {}
+    for cfg, tag in ((synth.SMALL_D2, "d2_N100"), (synth.MEDIUM_D2, "d2_N10000")):
+        blk = {"workload": f"d=2 N={cfg.N} L={cfg.L} chi={cfg.chi}, uniform random (SplitMix64 seed {cfg.seed}), FIRE"}
+        for name, stages in (("fp64_then_dd", [ssh.FP64, ssh.DD]), ("all_dd", [ssh.DD])):
+            c = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi, device=dev)
+            c.set_stream(stream.cuda_stream)
+            c.set_positions_frac(synth.positions(cfg.seed, cfg.N, cfg.d))
+            r = c.minimize(stages=stages, max_steps=200000, max_seconds=max_seconds)
+            hi, lo = c.positions_frac()
+            n = c.kset()
+            c.close()
+            ref = oracle.phi_grad(hi, lo, n, cfg.L, want_force=False)
+            ns = r["stages_used"]
+            blk[name] = {"converged": r["status"] == 0, "status": r["status"], "wall_s": r["wall_s"],
+                         "steps": r["steps"], "stage_steps": r["stage_steps"][:ns],
+                         "stage_wall_s": r["stage_wall_s"][:ns], "smax": r["smax"][0],
+                         "oracle_smax": float(ref["smax"][0] + ref["smax"][1]),
+                         "configs_per_hour": 3600.0 / r["wall_s"] if r["status"] == 0 else 0.0}
+        a, b = blk["fp64_then_dd"], blk["all_dd"]
+        blk["staged_over_all_dd_configs_per_hour"] = (a["configs_per_hour"] / b["configs_per_hour"]
+                                                      if b["configs_per_hour"] > 0 else None)
+        out[tag] = blk
+    return out
+
+
+def dd_roofline_block(ssh, ctx, pairs, fp64_rate, cmac_rate):
+    """The double-double kernels against the measured FP64 FMA rate: algorithmic FP64 instructions per pair
+    (DD_FP64_PER_PAIR, counted from dd.cuh) x pairs / the kernel's mean event time (the library's profiler, on the
+    launching stream), over three evaluations; the density kernel's pair rate also against the measured rate of its
+    own inner operation (one complex dd multiply and add)."""
+    ctx.eval(ssh.DD)
+    ctx.sync()
+    ctx.prof_enable(True)
+    for _ in range(3):
+        ctx.eval(ssh.DD)
+    pr = ctx.prof_read()
+    ctx.prof_enable(False)
+    out = {"bound": "fp64", "unit": "FP64 instr/s", "peak": fp64_rate,
+           "peak_source": "ssh_pipe_rate fp64_fma, measured in this run", "kernels": {}}
+    for k in ("ntilde", "force"):
+        if k not in pr:
+            continue
+        ms = pr[k][0] / pr[k][1]
+        ach = DD_FP64_PER_PAIR[k] * pairs / (ms * 1e-3)
+        out["kernels"][k] = {"ms": ms, "achieved": ach, "frac": ach / fp64_rate,
+                             "fp64_per_pair": DD_FP64_PER_PAIR[k]}
+    if "ntilde" in out["kernels"]:
+        out["kernels"]["ntilde"]["frac_of_measured_cmac_rate"] = pairs / (out["kernels"]["ntilde"]["ms"] * 1e-3) / cmac_rate
+    out["per_kernel_ms"] = {k: v[0] / v[1] for k, v in pr.items()}
     return out
 
 
@@ -357,7 +445,7 @@ def serving_block(ssh, synth, dev, window_s=45.0, drain_s=30.0, count=2000, mean
     sv = ssh.Server(device=dev, max_slots=256, chunk_steps=32)
     params = ssh.MinParams()  # zero fields: the library's defaults
     params.method = ssh.MIN_LBFGS if method == "lbfgs" else ssh.MIN_FIRE
-    tickets = []
+    tickets, sub_t, sub_work = [], {}, []
     t0 = time.perf_counter()
     stop = threading.Event()
 
@@ -368,7 +456,10 @@ def serving_block(ssh, synth, dev, window_s=45.0, drain_s=30.0, count=2000, mean
             dt = ta - (time.perf_counter() - t0)
             if dt > 0:
                 time.sleep(dt)
-            tickets.append(sv.submit(c.d, c.N, c.L, synth.positions(c.seed, c.N, c.d), chi=c.chi, params=params))
+            t = sv.submit(c.d, c.N, c.L, synth.positions(c.seed, c.N, c.d), chi=c.chi, params=params)
+            sub_t[t] = time.perf_counter() - t0
+            sub_work.append(c.N * round(c.chi * c.d * (c.N - 1)))   # M N (M = round-half-even(chi d (N - 1)))
+            tickets.append(t)
 
     th = threading.Thread(target=feeder)
     th.start()
@@ -387,13 +478,28 @@ def serving_block(ssh, synth, dev, window_s=45.0, drain_s=30.0, count=2000, mean
     sv.close()
     ok = [r for r in done.values() if r["status"] == 0]
     lat = sorted(r["t_done"] - r["t_submit"] for r in ok)
-    pct = (lambda q: float(np.percentile(lat, q)) if lat else None)
-    return {"submitted": len(tickets), "completed": len(done), "converged": len(ok), "still_running": st["running"],
-            "still_queued": st["queued"], "p50_s": pct(50), "p99_s": pct(99),
+    pct = (lambda v, q: float(np.percentile(v, q)) if len(v) else None)
+    # every submitted request, the unfinished ones censored at the end of the run (a lower bound on their latency)
+    cens = sorted([r["t_done"] - r["t_submit"] for r in done.values()] +
+                  [elapsed - sub_t[t] for t in tickets if t not in done])
+    n_sub = len(tickets)
+    work = {t: w for t, w in zip(tickets, sub_work)}
+    offered = sum(sub_work) / window_s
+    sustained = sum(work[t] * r["steps"] for t, r in done.items()) / elapsed
+    return {"submitted": n_sub, "completed": len(done), "converged": len(ok), "still_running": st["running"],
+            "still_queued": st["queued"], "completion_fraction": len(done) / n_sub if n_sub else None,
+            "p50_s": pct(cens, 50), "p99_s": pct(cens, 99), "latency": "every submitted request, unfinished ones "
+            "censored at the end of the run (a lower bound)",
+            "p50_completed_s": pct(lat, 50), "p99_completed_s": pct(lat, 99),
             "configs_per_hour": len(ok) / elapsed * 3600.0, "elapsed_s": elapsed,
+            "offered_requests_per_s": n_sub / window_s, "sustained_requests_per_s": len(done) / elapsed,
+            "offered_pairs_per_s": offered, "offered_pairs": "sum of M N over the submitted requests per second of "
+            "arrivals (one evaluation of each)",
+            "sustained_pairs_per_s": sustained, "sustained_pairs": "sum of M N x steps of the finished requests per "
+            "second of the run",
             "minimiser": method,
             "workload": f"Poisson arrivals mean {1 / mean_gap:.0f}/s for {window_s:.0f} s (+{drain_s:.0f} s drain), "
-                        "d in {1,2,3}, N log-uniform [64, 32768], chi U[0.10, 0.49]; latency of converged requests only"}
+                        "d in {1,2,3}, N log-uniform [64, 32768], chi U[0.10, 0.49]"}
 
 
 def run_reference(args):
@@ -619,6 +725,7 @@ def main():
     ctx.set_positions_frac(s)
     pairs = ctx.M * ctx.N
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    pipes = pipe_rates_block(ssh, dev)   # roofline denominators of the non-tensor arithmetics, measured here
 
     # A step is one device FIRE step: twiddle tables, n~, reductions, Phi / S_max, force, the FIRE update,
     # the energy-guard acceptance and the convergence test.  The target is set out of reach so that no
@@ -683,11 +790,11 @@ def main():
         per_launch_s = dom_ms / 1e3 / dom_n
         per_pair, peak, unit, bound, what = tc_flop_per_pair(w["d"]), BF16_PEAK, "FLOP/s", "tensor", "bf16"
     elif prec == ssh.FX:
-        per_pair, peak, unit, bound, what = FX_IMAD_PER_PAIR, IMAD_PEAK, "IMAD/s", "alu", "IMAD"
+        per_pair, peak, unit, bound, what = FX_IMAD_PER_PAIR, pipes["imad"]["ops_per_s"], "IMAD/s", "alu", "IMAD"
     elif prec == ssh.DD:
-        per_pair, peak, unit, bound, what = DD_FP64_PER_PAIR, FP64_PEAK, "FP64 instr/s", "fp64", "FP64"
+        per_pair, peak, unit, bound, what = DD_FP64_PER_PAIR, pipes["fp64_fma"]["ops_per_s"], "FP64 instr/s", "fp64", "FP64"
     else:
-        per_pair, peak, unit, bound, what = F64_FP64_PER_PAIR, FP64_PEAK, "FP64 instr/s", "fp64", "FP64"
+        per_pair, peak, unit, bound, what = F64_FP64_PER_PAIR, pipes["fp64_fma"]["ops_per_s"], "FP64 instr/s", "fp64", "FP64"
     roof = None
     if dom_name in per_pair:
         achieved = per_pair[dom_name] * pairs / per_launch_s
@@ -696,8 +803,8 @@ def main():
                 "traffic_unit": "bytes per launch (dram read + write, ncu)",
                 "peak_source": ("MEASURED_PEAKS.json bf16_tflops (cuBLAS bf16 GEMM, burst), of measured"
                                 if what == "bf16" else
-                                f"unit counts x max clock: {'64 IMAD' if what == 'IMAD' else '2 FP64 FMA'} "
-                                f"lanes/SM/clk x 148 SMs x 2032 MHz"),
+                                f"ssh_pipe_rate {'imad' if what == 'IMAD' else 'fp64_fma'} measured in this run, "
+                                f"of measured"),
                 "per_kernel_ms": {k: v[0] / v[1] for k, v in prof.items()}}
         tr = NCU_TRAFFIC.get((args.workload, "fx-tensor" if tensor else args.prec, dom_name))
         if tr and tr[0] == kernel_source_hash("tc" if tensor else "fx"):
@@ -762,11 +869,17 @@ def main():
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "gpu_launches": launches, "wall_s": t_wall,
             "e2e": {"value": pairs * world / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "clocks": clk.summary(), "variants_pairs_per_s": variants}
+            "clocks": clk.summary(), "variants_pairs_per_s": variants, "pipe_rates": pipes}
+    if tensor:
+        line["arithmetic_class"] = ("dd-class: every value a 2^-104 fixed-point number held as 15 exact bf16 digits, "
+                                    "exact sums; the paper's literal double-double path is variants_pairs_per_s.dd, "
+                                    "its roofline roofline_dd")
+    if rank == 0 and not args.no_variants:
+        line["roofline_dd"] = dd_roofline_block(ssh, ctx, pairs, pipes["fp64_fma"]["ops_per_s"],
+                                                pipes["dd_cmac"]["ops_per_s"])
     # the further blocks run at N = 1 only (a multi-GPU run holds every GPU while rank 0 works)
     if rank == 0 and world == 1 and not args.no_minimize:
-        line["minimize"] = minimize_block(ssh, synth, w, dev, stream, with_dd=args.minimize_dd,
-                                          max_seconds=args.minimize_seconds)
+        line["minimize"] = minimize_block(ssh, synth, w, dev, stream, max_seconds=args.minimize_seconds)
         conv = line["minimize"].get("default", {})
         if conv.get("converged"):
             line["configs_per_hour"] = 3600.0 / conv["wall_s"]
@@ -777,7 +890,7 @@ def main():
         line["batched"] = batched_block(ssh, synth, dev)
     if rank == 0 and world == 1 and not args.no_large:
         line["large_d3"] = large_d3_block(ssh, synth, dev, stream, flush, max_seconds=args.minimize_seconds,
-                                          staged=not args.no_large_staged)
+                                          staged=args.large_staged)
     if rank == 0 and world == 1 and not args.no_post:
         line["post"] = post_block(ssh, synth, dev)
     if rank == 0 and world == 1 and not args.no_paper_scale:
@@ -786,11 +899,22 @@ def main():
         line["serving"] = serving_block(ssh, synth, dev, window_s=args.serve_seconds, method=args.serve_method)
         line["p50_s"] = line["serving"]["p50_s"]
         line["p99_s"] = line["serving"]["p99_s"]
+    if rank == 0 and world == 1 and not args.no_dd_ladder:
+        line["dd_ladder"] = dd_ladder_block(ssh, synth, dev, stream, max_seconds=args.dd_seconds)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, Ms, cores = cpu_sample(w["N"], w["d"], w["L"], w["chi"], w["seed"])
+        rate, Ms, cores, (Cr, Sr) = cpu_sample(w["N"], w["d"], w["L"], w["chi"], w["seed"], want_cs=True)
         line["cpu_baseline"] = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle",
                                 "sample": f"one oracle Phi+grad over the first {Ms} of {ctx.M} wavevectors x all "
                                           f"{w['N']} particles (binary128, OpenMP)"}
+        # accuracy of the timed arithmetic in this run: n~ of the same sample against the oracle's
+        ctx.set_positions_frac(s)
+        ctx.energy_grad(prec)
+        C, S = ctx.ntilde()
+        err = max(np.abs((C[:Ms, 0] - Cr[:, 0]) + (C[:Ms, 1] - Cr[:, 1])).max(),
+                  np.abs((S[:Ms, 0] - Sr[:, 0]) + (S[:Ms, 1] - Sr[:, 1])).max()) / w["N"]
+        line["accuracy"] = {"max_abs_dntilde_over_N": float(err), "bound": 1e-28 if prec != ssh.FP64 else 1e-13,
+                            "against": f"the binary128 oracle on the cpu_baseline sample ({Ms} wavevectors x "
+                                       f"{w['N']} particles), at the workload's seeded positions"}
     ctx.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

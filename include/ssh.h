@@ -389,6 +389,25 @@ ssh_status ssh_server_get_stats(ssh_server* server, ssh_server_stats* out);
 ssh_status ssh_prof_enable(ssh_ctx* ctx, int on);
 
 /*
+ * Measured operation rate of one pipe of the current part, for roofline denominators (the paper has no
+ * counterpart: it names no GPU and reports no timing).  A kernel keeps every SM busy (8 CTAs of 256 threads per
+ * SM) with independent chains of one operation for about 100 ms, timed with CUDA events, best of three:
+ *   SSH_PIPE_FP64_FMA  fma.rn.f64 (the pipe of the SSH_DD and SSH_FP64 kernels), per instruction
+ *   SSH_PIPE_FP32_FMA  fma.rn.f32, per instruction
+ *   SSH_PIPE_IMAD      mad.lo.u32 (the pipe of the integer SSH_FX kernels), per instruction
+ *   SSH_PIPE_IMAD_HI   mad.hi.u32, per instruction
+ *   SSH_PIPE_DD_CMAC   one complex double-double multiply plus one complex double-double add (the dd density
+ *                      kernel's work per pair), per pair of operations
+ *   SSH_PIPE_FX_CMUL   one product of first-quadrant 128-bit fixed-point phasors (three truncated 128 x 128-bit
+ *                      products), per product
+ * *ops_per_s receives the rate; *ms (may be NULL) the duration of the timed launch.  Synchronous; runs on
+ * device `device` and restores the current device.  Errors: SSH_EINVAL, SSH_ECUDA.
+ */
+enum { SSH_PIPE_FP64_FMA = 0, SSH_PIPE_FP32_FMA = 1, SSH_PIPE_IMAD = 2, SSH_PIPE_IMAD_HI = 3, SSH_PIPE_DD_CMAC = 4,
+       SSH_PIPE_FX_CMUL = 5 };
+ssh_status ssh_pipe_rate(int device, int kind, double* ops_per_s, double* ms);
+
+/*
  * Limit, in clock cycles, of every wait of the tensor-core GEMM on its pipeline (operand stages, work items, the
  * accumulator) on CUDA device `device`; 0 restores the default of 2e9 cycles (about one second at the maximum SM
  * clock).  The paper has no counterpart: it is this library's failure detection.  A wait that runs out does not

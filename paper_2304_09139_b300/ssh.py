@@ -133,6 +133,7 @@ def load():
             _sig(lib, "ssh_prof_enable", c_int, [c_vp, c_int])
             _sig(lib, "ssh_prof_read", c_int, [c_vp, c_int, P(c_d), P(c_i64)])
             _sig(lib, "ssh_set_wait_limit", c_int, [c_int, c_i64])
+            _sig(lib, "ssh_pipe_rate", c_int, [c_int, c_int, P(c_d), P(c_d)])
             _sig(lib, "ssh_ntilde_noalloc", c_int, [c_int, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
                                                    c_vp])
             _sig(lib, "ssh_min_defaults", c_int, [c_vp, P(MinParams)])
@@ -245,6 +246,16 @@ def ntilde_noalloc(d: int, N: int, M: int, s_hi_ptr: int, s_lo_ptr: int | None, 
     """ssh_ntilde_noalloc with raw device pointers (allocation-free n~(k); enqueued, not synchronised)."""
     _check(load().ssh_ntilde_noalloc(d, N, M, s_hi_ptr, s_lo_ptr, n_ptr, C_hi_ptr, C_lo_ptr, S_hi_ptr, S_lo_ptr,
                                      stream_ptr))
+
+
+PIPES = {"fp64_fma": 0, "fp32_fma": 1, "imad": 2, "imad_hi": 3, "dd_cmac": 4, "fx_cmul": 5}
+
+
+def pipe_rate(kind: str, device: int = 0) -> tuple[float, float]:
+    """ssh_pipe_rate: (operations per second, ms of the timed launch) of one pipe (a key of PIPES)."""
+    r, ms = c_d(), c_d()
+    _check(load().ssh_pipe_rate(device, PIPES[kind], ctypes.byref(r), ctypes.byref(ms)))
+    return r.value, ms.value
 
 
 def set_wait_limit(cycles: int, device: int = 0):
