@@ -72,7 +72,10 @@ typedef struct {
                      * Chunks run one after another through the same buffers; results do not depend on the
                      * chunking (the sums are exact integers).  Rounded up to a multiple of 128 and to at most
                      * 64 chunks. */
-  int reserved[5];  /* zero */
+  int shard_first;  /* particle shard (ssh_shard_*): the context's evaluations sum and force only the particles */
+  int shard_count;  /* [shard_first, shard_first + shard_count) of the N; both 0 (default): every particle.  Needs the
+                     * tensor-core path; shard_first a multiple of 2048, shard_count too unless the shard ends at N */
+  int reserved[3];  /* zero */
 } ssh_opts;
 
 /* Library version string, e.g. "ssh 0.1 sm_103a". Never NULL. */
@@ -421,6 +424,44 @@ ssh_status ssh_pipe_rate(int device, int kind, double* ops_per_s, double* ms);
  */
 ssh_status ssh_set_wait_limit(int device, int64_t cycles);
 ssh_status ssh_prof_read(ssh_ctx* ctx, int n, double* ms, int64_t* launches);
+
+/*
+ * Particle shards of one configuration (Simulations: both sums of a step are independent reductions over the
+ * particles, so the particles can be split across GPUs with one exchange per sum).  A shard context is created
+ * with ssh_opts.shard_first / shard_count over the whole configuration (N, the wavevector set and every
+ * normalisation are the whole configuration's); it holds all N positions but its evaluations sum n~ over, and
+ * compute F and FIRE moves for, its own particles only.  The caller owns the exchange: two device buffers that it
+ * sums element-wise over every shard (an all-reduce; integer addition for the density, which is exact in any
+ * order, and binary64 addition for the dot products, where each element is non-zero on one shard at most), on
+ * the context's stream or after ssh_sync.  Every shard then holds the whole configuration's Phi, S_max and n~,
+ * bit for bit the values of one unsharded context, and the same force and FIRE trajectory for its particles.
+ * Only FIRE (the paper's minimiser) in fixed point runs sharded.  The positions of other shards' particles in a
+ * shard context are never moved: read each shard's own range.  ssh_eval, ssh_energy_grad, ssh_minimize,
+ * ssh_fire_begin and ssh_fire_steps return SSH_EINVAL on a shard context.
+ *
+ *   ssh_shard_words       int64 words of the density exchange, binary64 words of the dot-product exchange
+ *   ssh_shard_density     enqueue this shard's part of the density sum (Eq. ntilde) into dens_out, a device buffer
+ *                         of dens_words int64: exact level groups of the tensor-core GEMM's tiles, to be summed
+ *   ssh_shard_finish      from dens_total (the sum over every shard): Phi, S_max, n~ and, with want_force, F of this
+ *                         shard's particles (Eqs. energy, smax, force); read with ssh_get_results / ssh_get_ntilde
+ *   ssh_shard_fire_begin  a FIRE run from the results of the last ssh_shard_finish (with force): p as for
+ *                         ssh_fire_begin (method FIRE, one fixed-point stage)
+ *   ssh_shard_step_dots   one FIRE step, first part: the dot products F.v, F.F, v.v of this shard's particles as
+ *                         partial sums per chunk of 2048 particles into dots_out (dots_words binary64)
+ *   ssh_shard_step_move   second part, from dots_total (the sum over every shard): the FIRE controls, the move of
+ *                         this shard's particles and their density sum into dens_out
+ *   ssh_shard_step_finish third part, from dens_total: Phi, S_max, F, the energy guard's acceptance or undo, the
+ *                         stop rules; ssh_fire_state then reports the step (the same on every shard)
+ * All enqueue work on the context's stream and return without synchronising.  Errors: SSH_EINVAL (not a shard
+ * context, no positions, no FIRE run begun, a NULL buffer), SSH_ECUDA.
+ */
+ssh_status ssh_shard_words(const ssh_ctx* ctx, int64_t* dens_words, int64_t* dots_words);
+ssh_status ssh_shard_density(ssh_ctx* ctx, int64_t* dens_out);
+ssh_status ssh_shard_finish(ssh_ctx* ctx, const int64_t* dens_total, int want_force);
+ssh_status ssh_shard_fire_begin(ssh_ctx* ctx, const ssh_min_params* p);
+ssh_status ssh_shard_step_dots(ssh_ctx* ctx, double* dots_out);
+ssh_status ssh_shard_step_move(ssh_ctx* ctx, const double* dots_total, int64_t* dens_out);
+ssh_status ssh_shard_step_finish(ssh_ctx* ctx, const int64_t* dens_total);
 
 /*
  * Allocation-free collective density, for callers that cannot allocate device memory: a program that hands a

@@ -101,6 +101,19 @@ static ssh_status create_from(int d, int64_t N, double L, ssh::KSet&& ks, const 
   c.tc_requested = fx_impl == SSH_FX_TENSOR || (fx_impl == SSH_FX_AUTO && d <= 3 && SSH_FX_AUTO_TENSOR);
   c.tc_chunk_req = opts ? opts->tc_chunk : 0;
   if (c.tc_chunk_req < 0) { delete h; set_error("ssh_create: tc_chunk must be >= 0"); return SSH_EINVAL; }
+  const int64_t sp0 = opts ? opts->shard_first : 0, spn = opts ? opts->shard_count : 0;
+  if (sp0 != 0 || spn != 0) {
+    // a particle shard: aligned to the dot-product chunks, so that every chunk's partial sums belong to one shard
+    if (sp0 < 0 || spn < 1 || sp0 + spn > N || sp0 % ssh::kDotChunk != 0 ||
+        (sp0 + spn < N && spn % ssh::kDotChunk != 0)) {
+      delete h;
+      set_error("ssh_create: a shard [shard_first, shard_first + shard_count) must lie in [0, N), start on a multiple "
+                "of 2048 and hold a multiple of 2048 particles unless it ends at N");
+      return SSH_EINVAL;
+    }
+    c.shard_p0 = sp0;
+    c.shard_n = spn;
+  }
   c.ks = std::move(ks);
   c.M = c.ks.M;
   if (c.M > (int64_t)1 << 30) { delete h; set_error("ssh_create: M too large"); return SSH_EINVAL; }
@@ -126,8 +139,20 @@ static ssh_status create_from(int d, int64_t N, double L, ssh::KSet&& ks, const 
     return e == cudaErrorMemoryAllocation ? (set_error("ssh_create: out of device memory"), SSH_ENOMEM)
                                           : cuda_fail(e, "ssh_create: set-up");
   }
+  if (c.shard_n > 0 && !c.tc.on) {
+    ssh_destroy(h);
+    set_error("ssh_create: a particle shard needs the tensor-core fixed-point path (d <= 3, a set within its limits)");
+    return SSH_EINVAL;
+  }
   *out = h;
   return SSH_OK;
+}
+
+// A shard context's evaluations need the other shards' densities: they run through ssh_shard_* only.
+static bool whole(const ssh::Ctx& c, const char* fn) {
+  if (c.shard_n == 0) return true;
+  set_error(std::string(fn) + ": a particle-shard context evaluates and minimises through ssh_shard_*");
+  return false;
 }
 
 static bool check_dnl(const char* fn, int d, int64_t N, double L) {
@@ -415,6 +440,7 @@ ssh_status ssh_eval(ssh_ctx* h, int prec, int want_force) {
   ssh::Ctx& c = h->c;
   if (prec < SSH_FP64 || prec > SSH_FX) { set_error("ssh_eval: unknown precision"); return SSH_EINVAL; }
   if (!c.have_positions) { set_error("ssh_eval: no positions set"); return SSH_EINVAL; }
+  if (!whole(c, "ssh_eval")) return SSH_EINVAL;
   cudaSetDevice(c.device);
   cudaError_t e = eval_replayed(c, prec, want_force != 0);
   if (e != cudaSuccess) return cuda_fail(e, "ssh_eval: launch");
@@ -572,6 +598,7 @@ ssh_status ssh_minimize(ssh_ctx* h, const ssh_min_params* pin, ssh_min_result* r
   if (!h) { set_error("ssh_minimize: NULL context"); return SSH_EINVAL; }
   ssh::Ctx& c = h->c;
   if (!c.have_positions) { set_error("ssh_minimize: no positions set"); return SSH_EINVAL; }
+  if (!whole(c, "ssh_minimize")) return SSH_EINVAL;
   ssh_min_params p;
   ssh_status st = ssh::complete_params(h, pin, &p);
   if (st != SSH_OK) return st;
@@ -583,6 +610,7 @@ ssh_status ssh_fire_begin(ssh_ctx* h, const ssh_min_params* pin) {
   if (!h) { set_error("ssh_fire_begin: NULL context"); return SSH_EINVAL; }
   ssh::Ctx& c = h->c;
   if (!c.have_positions) { set_error("ssh_fire_begin: no positions set"); return SSH_EINVAL; }
+  if (!whole(c, "ssh_fire_begin")) return SSH_EINVAL;
   ssh_min_params p;
   ssh_status st = ssh::complete_params(h, pin, &p);
   if (st != SSH_OK) return st;
@@ -592,6 +620,7 @@ ssh_status ssh_fire_begin(ssh_ctx* h, const ssh_min_params* pin) {
 
 ssh_status ssh_fire_steps(ssh_ctx* h, int prec, int64_t nsteps) {
   if (!h || prec < SSH_FP64 || prec > SSH_FX || nsteps < 0) { set_error("ssh_fire_steps: bad arguments"); return SSH_EINVAL; }
+  if (!whole(h->c, "ssh_fire_steps")) return SSH_EINVAL;
   cudaSetDevice(h->c.device);
   return ssh::fire_steps(&h->c, prec, nsteps);
 }

@@ -258,6 +258,10 @@ extern "C" {
 
 ssh_status ssh_batch_create(const ssh_opts* opts, ssh_batch** out) {
   if (!out) { set_error("ssh_batch_create: out is NULL"); return SSH_EINVAL; }
+  if (opts && (opts->shard_first != 0 || opts->shard_count != 0)) {
+    set_error("ssh_batch_create: batch members hold every particle (no shard fields)");
+    return SSH_EINVAL;
+  }
   ssh_batch* b = new (std::nothrow) ssh_batch();
   if (!b) { set_error("ssh_batch_create: out of host memory"); return SSH_ENOMEM; }
   b->device = opts ? opts->device : 0;

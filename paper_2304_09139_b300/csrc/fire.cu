@@ -2,7 +2,9 @@
 // configuration or for every member of a batch at once.
 //
 // One step, for the force F and energy Phi at the accepted positions and the velocity v of the last step:
-//   k_fire_dots     P = F.v, |F|^2, |v|^2 (per-block partials, fixed order); the last block of a member applies
+//   k_fire_dots     P = F.v, |F|^2, |v|^2 (partials per chunk of 2048 particles of an axis, fixed order; a shard
+//                   computes its chunks' partials and the caller sums them, k_fire_dots_part / k_fire_control);
+//                   the last block of a member applies
 //                   the FIRE rules: P > 0 -> v <- (1-a) v + a |v| F/|F|; after more than n_min such steps
 //                   dt <- min(dt f_inc, dt_max), a <- a f_alpha;  P <= 0 -> v <- 0, dt <- dt f_dec, a <- a_start
 //   k_fire_move     semi-implicit Euler with unit mass: v <- v + dt F, r <- r + dt v (dd, wrapped into the box);
@@ -33,22 +35,18 @@ constexpr int kFireGraphSteps = 8;
 
 __device__ __forceinline__ FireState* fstate(const CfgDev& c) { return reinterpret_cast<FireState*>(c.fs); }
 
-// block map: nb_fire blocks per member, grid-strided over the coordinates: the block partials of F.v, F.F and v.v;
-// the last block of a member to finish sums them (lane-strided in a fixed order, then a fixed shuffle tree) and
-// sets the FIRE controls of the step: mixing, velocity reset, dt and alpha
-__global__ void __launch_bounds__(kFireThreads) k_fire_dots(const CfgDev* __restrict__ cfgs,
-                                                            const BlockMap* __restrict__ bm) {
-  grid_dep_wait();
-  const BlockMap m = bm[blockIdx.x];
-  const CfgDev& c = cfgs[m.cfg];
-  FireState* fs = fstate(c);
-  if (fs->status || fs->method != kMethodFire) return;  // uniform over the member's blocks
-  __shared__ double sh[3][kFireThreads];
-  __shared__ int last;
-  const int64_t nd = (int64_t)c.d * c.N;
+// Partial sums P = F.v, |F|^2, |v|^2 (high words) of dot chunk q of member c: axis a = q / nq1, particles
+// [jb kDotChunk, (jb + 1) kDotChunk) (q = a nq1 + jb), each thread over a fixed stride, then a fixed tree.  The
+// chunking depends on N alone, so a chunk's partial is the same whichever launch or shard computes it.  Every
+// thread of the block calls it; thread 0 returns the three sums.
+__device__ void dots_chunk(const CfgDev& c, int64_t q, double (*sh)[kFireThreads], double out[3]) {
+  const int64_t nq1 = (c.N + kDotChunk - 1) / kDotChunk;
+  const int a = (int)(q / nq1);
+  const int64_t j0 = (q - (int64_t)a * nq1) * kDotChunk, j1 = min(c.N, j0 + kDotChunk);
   double p = 0, f2 = 0, v2 = 0;
-  for (int64_t i = (int64_t)m.blk * kFireThreads + threadIdx.x; i < nd; i += (int64_t)c.nb_fire * kFireThreads) {
-    double f = c.F_hi[i], w = c.v_hi[i];
+  for (int64_t j = j0 + threadIdx.x; j < j1; j += kFireThreads) {
+    const int64_t i = (int64_t)a * c.N + j;
+    const double f = c.F_hi[i], w = c.v_hi[i];
     p = fma(f, w, p);
     f2 = fma(f, f, f2);
     v2 = fma(w, w, v2);
@@ -57,27 +55,24 @@ __global__ void __launch_bounds__(kFireThreads) k_fire_dots(const CfgDev* __rest
   sh[1][threadIdx.x] = f2;
   sh[2][threadIdx.x] = v2;
   __syncthreads();
-  for (int s = kFireThreads / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s)
-      for (int q = 0; q < 3; q++) sh[q][threadIdx.x] += sh[q][threadIdx.x + s];
+  for (int st = kFireThreads / 2; st > 0; st >>= 1) {
+    if ((int)threadIdx.x < st)
+      for (int r = 0; r < 3; r++) sh[r][threadIdx.x] += sh[r][threadIdx.x + st];
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < 3; q++) c.fdots[q * c.nb_fire + m.blk] = sh[q][0];
-    __threadfence();
-    last = atomicAdd(&fs->dots_ticket, 1) == c.nb_fire - 1;
-  }
+  if (threadIdx.x == 0)
+    for (int r = 0; r < 3; r++) out[r] = sh[r][0];
   __syncthreads();
-  if (!last || threadIdx.x >= 32) return;
-  __threadfence();
-  const int lane = threadIdx.x;
-  double P = 0;
-  f2 = 0;
-  v2 = 0;
-  for (int b = lane; b < c.nb_fire; b += 32) {
-    P += c.fdots[b];
-    f2 += c.fdots[c.nb_fire + b];
-    v2 += c.fdots[2 * c.nb_fire + b];
+}
+
+// The FIRE controls of a step from the chunk partials part[3][nq], summed by one warp (lane-strided in chunk order,
+// then a fixed shuffle tree): mixing, velocity reset, dt and alpha (Bitzek et al. 2006).
+__device__ void dots_control(FireState* fs, const double* part, int64_t nq, int lane) {
+  double P = 0, f2 = 0, v2 = 0;
+  for (int64_t b = lane; b < nq; b += 32) {
+    P += part[b];
+    f2 += part[nq + b];
+    v2 += part[2 * nq + b];
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
@@ -104,6 +99,60 @@ __global__ void __launch_bounds__(kFireThreads) k_fire_dots(const CfgDev* __rest
     fs->alpha = fs->alpha_start;
     fs->n_pos = 0;
   }
+}
+
+// block map: nb_fire blocks per member, each over the dot chunks q = blk, blk + nb_fire, ...; the last block of a
+// member to finish applies the FIRE controls from every chunk's partials
+__global__ void __launch_bounds__(kFireThreads) k_fire_dots(const CfgDev* __restrict__ cfgs,
+                                                            const BlockMap* __restrict__ bm) {
+  grid_dep_wait();
+  const BlockMap m = bm[blockIdx.x];
+  const CfgDev& c = cfgs[m.cfg];
+  FireState* fs = fstate(c);
+  if (fs->status || fs->method != kMethodFire) return;  // uniform over the member's blocks
+  __shared__ double sh[3][kFireThreads];
+  __shared__ int last;
+  for (int64_t q = m.blk; q < c.n_dchunk; q += c.nb_fire) {
+    double r[3];
+    dots_chunk(c, q, sh, r);
+    if (threadIdx.x == 0)
+      for (int k = 0; k < 3; k++) c.fdots[k * c.n_dchunk + q] = r[k];
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&fs->dots_ticket, 1) == c.nb_fire - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x >= 32) return;
+  __threadfence();
+  dots_control(fs, c.fdots, c.n_dchunk, threadIdx.x);
+}
+
+// A shard's half of k_fire_dots: every chunk's partials into out[3][n_dchunk] (exactly 0 for chunks of particles
+// outside the shard, whose force and velocity stay 0), for the caller to sum over the shards.  One member.
+__global__ void __launch_bounds__(kFireThreads) k_fire_dots_part(const CfgDev* __restrict__ cfgs,
+                                                                 const BlockMap* __restrict__ bm, double* out) {
+  grid_dep_wait();
+  const BlockMap m = bm[blockIdx.x];
+  const CfgDev& c = cfgs[m.cfg];
+  const FireState* fs = fstate(c);
+  if (fs->status || fs->method != kMethodFire) return;
+  __shared__ double sh[3][kFireThreads];
+  for (int64_t q = m.blk; q < c.n_dchunk; q += c.nb_fire) {
+    double r[3];
+    dots_chunk(c, q, sh, r);
+    if (threadIdx.x == 0)
+      for (int k = 0; k < 3; k++) out[k * c.n_dchunk + q] = r[k];
+  }
+}
+
+// The other half: the FIRE controls from the partials summed over every shard (one warp, one member)
+__global__ void k_fire_control(const CfgDev* __restrict__ cfgs, const double* __restrict__ tot) {
+  grid_dep_wait();
+  const CfgDev& c = cfgs[0];
+  FireState* fs = fstate(c);
+  if (fs->status || fs->method != kMethodFire) return;
+  dots_control(fs, tot, c.n_dchunk, threadIdx.x);
 }
 
 // block map: d N / 64 blocks per member
@@ -289,7 +338,7 @@ cudaError_t fire_alloc(Ctx* c) {
     if (e == cudaSuccess) e = cudaMemsetAsync(b->p, 0, b->bytes, c->stream);
   }
   f->nb = (int)std::max<int64_t>(1, std::min<int64_t>(256, ((int64_t)nd + kFireThreads - 1) / kFireThreads));
-  f->part.bytes = sizeof(double) * 3 * f->nb;
+  f->part.bytes = sizeof(double) * 3 * dot_chunks(c->d, c->N);
   if (e == cudaSuccess) e = cudaMalloc(&f->part.p, f->part.bytes);
   f->lb_S.bytes = f->lb_Y.bytes = std::max<size_t>((size_t)kLbMaxPairs * nd * 8, 16);
   f->lb_G.bytes = f->lb_P.bytes = std::max<size_t>(nd * 8, 16);
@@ -324,6 +373,7 @@ void fire_fill_cfgdev(const Ctx* c, CfgDev* g) {
   g->bF_hi = (double*)f->bF_hi.p;
   g->bF_lo = (double*)f->bF_lo.p;
   g->fdots = (double*)f->part.p;
+  g->n_dchunk = (int)dot_chunks(c->d, c->N);
   g->nb_fire = f->nb;
   g->lb_S = (double*)f->lb_S.p;
   g->lb_Y = (double*)f->lb_Y.p;
@@ -508,6 +558,58 @@ static cudaError_t single_stage_start(Ctx* c, int prec, const FireState& prm, in
                           (const int*)f->init_first.p, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host arguments above live on this stack frame
   return e;
+}
+
+cudaError_t fire_engine_for(Ctx* c, int prec, Engine** out) { return fire_engine(c, prec, out); }
+
+bool fire_begun(const Ctx* c) { return c->fire && c->fire->begun; }
+
+cudaError_t fire_dots_partials(const Engine* e, double* out, cudaStream_t st) {
+  if (e->nall != 1 || e->nbm_dots == 0) return cudaErrorInvalidValue;
+  return launch_pdl(k_fire_dots_part, dim3((unsigned)e->nbm_dots), dim3(kFireThreads), 0, st, e->view[0].cfgs, e->bm_dots,
+                    out);
+}
+
+cudaError_t fire_control_move(const Engine* e, const double* tot, cudaStream_t st) {
+  if (e->nall != 1 || e->nbm_nd == 0) return cudaErrorInvalidValue;
+  const CfgDev* cfgs = e->view[0].cfgs;
+  cudaError_t le = launch_pdl(k_fire_control, dim3(1), dim3(32), 0, st, cfgs, tot);
+  if (le == cudaSuccess) le = launch_pdl(k_fire_move, dim3((unsigned)e->nbm_nd), dim3(64), 0, st, cfgs, e->bm_nd);
+  return le;
+}
+
+cudaError_t fire_accept_restore(const Engine* e, cudaStream_t st) {
+  const CfgDev* cfgs = e->view[0].cfgs;
+  const unsigned gt = (unsigned)((e->nall + 127) / 128);
+  cudaError_t le = launch_pdl(k_fire_accept, dim3(gt), dim3(128), 0, st, cfgs, e->all, e->nall);
+  if (le == cudaSuccess) le = launch_pdl(k_fire_restore, dim3((unsigned)e->nbm_nd), dim3(64), 0, st, cfgs, e->bm_nd);
+  return le;
+}
+
+// A FIRE run from the Phi, S_max and F already in the context (a shard's exchanged evaluation): the stage start of
+// fire_begin without its evaluation.  One fixed-point stage, FIRE only.
+ssh_status fire_begin_from_results(Ctx* c, const ssh_min_params* p) {
+  cudaError_t e = fire_alloc(c);
+  if (e != cudaSuccess) { set_error(std::string("shard FIRE begin: allocation: ") + cudaGetErrorString(e)); return SSH_ENOMEM; }
+  FireState prm = fire_params(p);
+  fire_set_method(c, prm.method);
+  prm.stage = 0;
+  prm.phi_tol = fire_phi_tol(c, SSH_FX);
+  FireBufs* f = c->fire;
+  cudaStream_t st = c->stream;
+  Engine* E = nullptr;
+  e = fire_engine(c, SSH_FX, &E);
+  int idx = 0, first = 1;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f->init_idx.p, &idx, sizeof(int), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f->init_prm.p, &prm, sizeof(FireState), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(f->init_first.p, &first, sizeof(int), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = stage_init_launch(E->view[0].cfgs, E->maxND_all, (const int*)f->init_idx.p, 1, (const FireState*)f->init_prm.p,
+                          (const int*)f->init_first.p, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host arguments above live on this stack frame
+  if (e != cudaSuccess) { set_error(std::string("shard FIRE begin: ") + cudaGetErrorString(e)); return SSH_ECUDA; }
+  f->begun = true;
+  return SSH_OK;
 }
 
 ssh_status fire_begin(Ctx* c, const ssh_min_params* p) {

@@ -173,15 +173,17 @@ struct PipeOp<SSH_PIPE_FX_CMUL> {
 };
 
 template <int KIND>
-__global__ void __launch_bounds__(kPipeThreads) k_pipe(long long iters, double b, double c, double* sink) {
+__global__ void __launch_bounds__(kPipeThreads) k_pipe(long long iters, double b, double c, long long key, double* sink) {
   PipeOp<KIND> op;
   op.init(blockIdx.x * kPipeThreads + threadIdx.x);
   for (long long it = 0; it < iters; it++) {
 #pragma unroll
     for (int u = 0; u < PipeOp<KIND>::kUnroll; u++) op.step(b, c);
   }
+  // a store under a condition the compiler cannot decide (key is a run-time value that no result matches in
+  // practice) keeps every chain live; a constant there would let it prove the store dead and drop the work
   const double r = op.result();
-  if (r == 12345.678) sink[0] = r;  // practically never taken; keeps every chain live
+  if (__double_as_longlong(r) == key) sink[0] = r;
 }
 
 template <int KIND>
@@ -192,7 +194,7 @@ cudaError_t time_pipe(int sms, long long iters, double* sink, float* ms) {
   e = cudaEventCreate(&e1);
   if (e == cudaSuccess) e = cudaEventRecord(e0, 0);
   if (e == cudaSuccess) {
-    k_pipe<KIND><<<sms * kPipeCtasPerSm, kPipeThreads>>>(iters, 0.9999999, 1e-7, sink);
+    k_pipe<KIND><<<sms * kPipeCtasPerSm, kPipeThreads>>>(iters, 0.9999999, 1e-7, 0x7ff4dead5eed1234ll, sink);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaEventRecord(e1, 0);
@@ -210,12 +212,13 @@ cudaError_t pipe_rate(int sms, double* sink, double* per_s, double* ms_out) {
   float ms = 0;
   long long iters = 64;
   cudaError_t e = time_pipe<KIND>(sms, iters, sink, &ms);
-  for (int g = 0; e == cudaSuccess && ms < 10.0f && g < 20; g++) {
+  for (int g = 0; e == cudaSuccess && ms < 10.0f && g < 10; g++) {
     iters *= 4;
     e = time_pipe<KIND>(sms, iters, sink, &ms);
   }
   if (e != cudaSuccess) return e;
-  iters = (long long)((double)iters * 100.0 / (double)(ms > 0 ? ms : 1.0f)) + 1;
+  if (ms < 10.0f) return cudaErrorUnknown;  // the work did not scale with the iterations: no rate to report
+  iters = (long long)((double)iters * 100.0 / (double)ms) + 1;
   float best = 0;
   for (int r = 0; r < 3 && e == cudaSuccess; r++) {
     e = time_pipe<KIND>(sms, iters, sink, &ms);

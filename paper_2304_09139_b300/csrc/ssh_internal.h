@@ -106,7 +106,8 @@ struct CfgDev {
   double *lb_S, *lb_Y, *lb_G, *lb_P, *lb_part;  // L-BFGS: history [pair][d N], gradient, direction, partials
   void* lb_mat;
   void* fs;
-  double *v_hi, *v_lo, *bs_hi, *bs_lo, *bF_hi, *bF_lo, *fdots;
+  double *v_hi, *v_lo, *bs_hi, *bs_lo, *bF_hi, *bF_lo, *fdots;  // fdots: [3][n_dchunk] FIRE dot partials
+  int n_dchunk;    // chunks of the FIRE dot products: d ceil(N / kDotChunk)
   const int* run;  // status word that turns this configuration's kernels into no-ops when non-zero, or null
 };
 
@@ -314,7 +315,18 @@ struct Ctx {
   bool tc_requested = false;      // fixed point on the tensor cores (d = 1, 2, 3)
   int64_t tc_chunk_req = 0;        // particles per chunk on that path (0: as device memory allows)
   TcPlan tc;
+  // particle shard: evaluations sum and force only particles [shard_p0, shard_p0 + shard_n) of the N (shard_n = 0:
+  // every particle, the ordinary context); the exchange with the other shards goes through the caller (shard.cu)
+  int64_t shard_p0 = 0, shard_n = 0;
 };
+
+// first particle and particle count a context's evaluations cover (its shard, or all N)
+inline int64_t part_p0(const Ctx* c) { return c->shard_n > 0 ? c->shard_p0 : 0; }
+inline int64_t part_n(const Ctx* c) { return c->shard_n > 0 ? c->shard_n : c->N; }
+// FIRE dot products are summed per chunk of kDotChunk particles of one axis, so that a shard boundary on a multiple
+// of it leaves every chunk's partial sum to one shard (the totals then agree bit for bit with the unsharded sums)
+constexpr int64_t kDotChunk = 2048;
+inline int64_t dot_chunks(int d, int64_t N) { return (int64_t)d * ((N + kDotChunk - 1) / kDotChunk); }
 
 // Launch with programmatic dependent launch: the kernel's CTAs may be made resident while the previous kernel on
 // the stream is still finishing, and each waits (grid_dep_wait, its first statement) until that kernel has
@@ -394,6 +406,12 @@ int64_t tc_table_blocks(const Ctx* c, int ch);
 void tc_prep_items(const Ctx* c, int cfg, int ch, std::vector<TwItem>& prep);
 void tc_gemm_items(const Ctx* c, int cfg, int ch, int64_t pieces, std::vector<TcItem>& dens, std::vector<TcItem>& force);
 cudaError_t tc_launch_density(const EngineView& v, cudaStream_t st, Prof* prof);
+// the two halves of tc_launch_density: the GEMM phases (into the exact tile accumulators), then the finish
+cudaError_t tc_launch_density_gemms(const EngineView& v, cudaStream_t st, Prof* prof);
+cudaError_t tc_launch_dens_finish(const EngineView& v, cudaStream_t st, Prof* prof);
+// the exact density tile accumulators of a tensor-core context: device pointer and int64 words
+long long* tc_acc_ptr(const Ctx* c);
+int64_t tc_acc_words(const Ctx* c);
 cudaError_t tc_launch_force(const EngineView& v, cudaStream_t st, Prof* prof);
 cudaError_t tc_launch_force_finish(const EngineView& v, cudaStream_t st, Prof* prof);
 
@@ -411,6 +429,15 @@ void fire_free(Ctx* c);
 ssh_status fire_begin(Ctx* c, const ssh_min_params* p);
 ssh_status fire_steps(Ctx* c, int prec, int64_t nsteps);
 ssh_status fire_state(Ctx* c, ssh_min_result* r, int* dev_status);
+// the pieces of one FIRE step that a sharded run interleaves with its exchanges (shard.cu): the minimiser's
+// engine for prec; the dot-product partials of every chunk into out ([3][n_dchunk]); the FIRE controls from summed
+// partials, then the move; the acceptance and the undo; a stage start from the results already in place
+cudaError_t fire_engine_for(Ctx* c, int prec, Engine** out);
+cudaError_t fire_dots_partials(const Engine* e, double* out, cudaStream_t st);
+cudaError_t fire_control_move(const Engine* e, const double* tot, cudaStream_t st);
+cudaError_t fire_accept_restore(const Engine* e, cudaStream_t st);
+ssh_status fire_begin_from_results(Ctx* c, const ssh_min_params* p);
+bool fire_begun(const Ctx* c);  // a FIRE run has begun on this context
 
 // zero fields of pin take the context's defaults; validates the result
 ssh_status complete_params(const ssh_ctx* h, const ssh_min_params* pin, ssh_min_params* out);

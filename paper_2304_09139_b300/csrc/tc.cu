@@ -1258,11 +1258,13 @@ cudaError_t tc_setup(Ctx* c) {
   // particles per chunk.  The digit tensor, the density B digits, the Q2.126 a_j(n1) and the tables hold one
   // chunk; the density sums run over the chunks into the same exact accumulators and the force rows of a chunk
   // are its own particles, so the results do not depend on the chunking.  By default every particle is one
-  // chunk when these buffers fit in 70% of the free device memory.
+  // chunk when these buffers fit in 70% of the free device memory.  The chunks cover the context's particles:
+  // all N, or its shard.
   {
+    const int64_t Np = part_n(c);
     const double bpp = (double)kDigits * t.NPg * 16 + (double)t.CTd * kStageB / kStepK + (double)W1 * sizeof(fxc) +
                        (double)d * t.ntab * sizeof(qent);  // bytes per particle of the chunk buffers
-    const int64_t Nr = (c->N + kTileM - 1) / kTileM * kTileM;
+    const int64_t Nr = (Np + kTileM - 1) / kTileM * kTileM;
     int64_t Nc = Nr;
     if (c->tc_chunk_req > 0) {
       Nc = c->tc_chunk_req;
@@ -1270,14 +1272,14 @@ cudaError_t tc_setup(Ctx* c) {
       size_t fr = 0, tot = 0;
       if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && bpp * (double)Nr > 0.7 * (double)fr) {
         const int64_t nch = (int64_t)std::ceil(bpp * (double)Nr / (0.7 * (double)fr));
-        Nc = (c->N + nch - 1) / nch;
+        Nc = (Np + nch - 1) / nch;
       }
     }
-    const int64_t Nmin = (c->N + kMaxTcPhases - 1) / kMaxTcPhases;  // at most kMaxTcPhases chunks
+    const int64_t Nmin = (Np + kMaxTcPhases - 1) / kMaxTcPhases;  // at most kMaxTcPhases chunks
     Nc = std::max(Nc, Nmin);
     Nc = std::min((Nc + kTileM - 1) / kTileM * kTileM, Nr);
     t.Nc = Nc;
-    t.nchunk = (int)((c->N + Nc - 1) / Nc);
+    t.nchunk = (int)((Np + Nc - 1) / Nc);
   }
   t.KS = t.Nc / kStepK;
   t.PT = (int)(t.Nc / kTileM);
@@ -1368,8 +1370,8 @@ void tc_fill_cfgdev(const Ctx* c, CfgDev* g) {
   g->tc_KS = t.KS;
   g->tc_NJ = t.NJ;
   g->tc_NPg = t.NPg;
-  g->tc_j0 = 0;  // chunk 0 (tc_chunk_cfgdev for the others)
-  g->tc_n = std::min<int64_t>(c->N, t.Nc);
+  g->tc_j0 = part_p0(c);  // chunk 0 (tc_chunk_cfgdev for the others)
+  g->tc_n = std::min<int64_t>(part_n(c), t.Nc);
   g->tc_nbuf = t.Nc;
   g->tc_wT = (uint8_t*)t.wT.p;
   g->tc_aB = (uint8_t*)t.aB.p;
@@ -1392,10 +1394,13 @@ void tc_fill_cfgdev(const Ctx* c, CfgDev* g) {
 
 int tc_chunks(const Ctx* c) { return c->tc.on ? c->tc.nchunk : 0; }
 
-static int64_t chunk_len(const Ctx* c, int ch) { return std::min<int64_t>(c->tc.Nc, c->N - (int64_t)ch * c->tc.Nc); }
+long long* tc_acc_ptr(const Ctx* c) { return c->tc.on ? reinterpret_cast<long long*>(c->tc.acc.p) : nullptr; }
+int64_t tc_acc_words(const Ctx* c) { return c->tc.on ? (int64_t)c->tc.tiles.size() * 3 * kTileN * kTileM : 0; }
+
+static int64_t chunk_len(const Ctx* c, int ch) { return std::min<int64_t>(c->tc.Nc, part_n(c) - (int64_t)ch * c->tc.Nc); }
 
 void tc_chunk_cfgdev(const Ctx* c, int ch, CfgDev* g) {
-  g->tc_j0 = (int64_t)ch * c->tc.Nc;
+  g->tc_j0 = part_p0(c) + (int64_t)ch * c->tc.Nc;
   g->tc_n = chunk_len(c, ch);
 }
 
@@ -1507,6 +1512,12 @@ static cudaError_t launch_tables_prep(const EngineView& v, int tab_off, int tab_
 
 // chunk by chunk: tables, preparation, density GEMM (into the exact tile accumulators); then the finish
 cudaError_t tc_launch_density(const EngineView& v, cudaStream_t st, Prof* prof) {
+  const cudaError_t le = tc_launch_density_gemms(v, st, prof);
+  if (le != cudaSuccess) return le;
+  return tc_launch_dens_finish(v, st, prof);
+}
+
+cudaError_t tc_launch_density_gemms(const EngineView& v, cudaStream_t st, Prof* prof) {
   if (v.ntc_list == 0) return cudaSuccess;
   for (int ph = 0; ph < v.ntc_phase; ph++) {
     const TcPhase& P = v.tc_ph[ph];
@@ -1520,6 +1531,11 @@ cudaError_t tc_launch_density(const EngineView& v, cudaStream_t st, Prof* prof) 
       prof_end(prof, st);
     }
   }
+  return cudaGetLastError();
+}
+
+cudaError_t tc_launch_dens_finish(const EngineView& v, cudaStream_t st, Prof* prof) {
+  if (v.ntc_list == 0) return cudaSuccess;
   prof_begin(prof, st, kKTcFinish);
   const cudaError_t le =
       launch_pdl(k_tc_dens_finish, dim3((unsigned)v.ntc_bm_fin), dim3(kFinThreads), 0, st, v.cfgs, v.tc_bm_fin);

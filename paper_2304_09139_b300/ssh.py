@@ -134,6 +134,13 @@ def load():
             _sig(lib, "ssh_prof_read", c_int, [c_vp, c_int, P(c_d), P(c_i64)])
             _sig(lib, "ssh_set_wait_limit", c_int, [c_int, c_i64])
             _sig(lib, "ssh_pipe_rate", c_int, [c_int, c_int, P(c_d), P(c_d)])
+            _sig(lib, "ssh_shard_words", c_int, [c_vp, P(c_i64), P(c_i64)])
+            _sig(lib, "ssh_shard_density", c_int, [c_vp, c_vp])
+            _sig(lib, "ssh_shard_finish", c_int, [c_vp, c_vp, c_int])
+            _sig(lib, "ssh_shard_fire_begin", c_int, [c_vp, P(MinParams)])
+            _sig(lib, "ssh_shard_step_dots", c_int, [c_vp, c_vp])
+            _sig(lib, "ssh_shard_step_move", c_int, [c_vp, c_vp, c_vp])
+            _sig(lib, "ssh_shard_step_finish", c_int, [c_vp, c_vp])
             _sig(lib, "ssh_ntilde_noalloc", c_int, [c_int, c_i64, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp,
                                                    c_vp])
             _sig(lib, "ssh_min_defaults", c_int, [c_vp, P(MinParams)])
@@ -274,14 +281,16 @@ class Context:
     """One configuration (d, N, L, chi | K) resident on the GPU.  Wraps ssh_create / ssh_destroy."""
 
     def __init__(self, d: int, N: int, L: float, chi: float = 0.0, K: float = 0.0, device: int = 0,
-                 fx_impl: int = 0, tc_chunk: int = 0, kset=None, _handle=None):
-        """kset: an explicit [M, d] wavevector list (ssh_create_kset) in place of chi / K."""
+                 fx_impl: int = 0, tc_chunk: int = 0, kset=None, shard=None, _handle=None):
+        """kset: an explicit [M, d] wavevector list (ssh_create_kset) in place of chi / K.  shard: (first, count), a
+        particle shard of the configuration (ssh_opts.shard_first / shard_count; evaluate with the shard_* methods)."""
         lib = load()
         self._lib = lib
         self._owned = _handle is None
         self._h = c_vp()
         if _handle is None:
-            opts = (c_int * 8)(device, fx_impl, tc_chunk, 0, 0, 0, 0, 0)  # ssh_opts
+            sf, sn = shard if shard is not None else (0, 0)
+            opts = (c_int * 8)(device, fx_impl, tc_chunk, sf, sn, 0, 0, 0)  # ssh_opts
             if kset is not None:
                 n = np.ascontiguousarray(kset, dtype=np.int32).reshape(-1, d)
                 _check(lib.ssh_create_kset(d, N, L, n.shape[0], n.ctypes.data_as(P(c_i32)), ctypes.cast(opts, c_vp),
@@ -338,6 +347,34 @@ class Context:
         out = np.zeros(nbins, dtype=np.uint64)
         _check(self._lib.ssh_pair_histogram(self._h, n_ref, r_max, nbins, out.ctypes.data_as(P(ctypes.c_uint64))))
         return out
+
+    # ---- particle shards (ssh_shard_*): device buffers are passed as raw pointers (e.g. torch data_ptr())
+    def shard_words(self) -> tuple[int, int]:
+        """(int64 words of the density exchange, binary64 words of the dot-product exchange)."""
+        a, b = c_i64(), c_i64()
+        _check(self._lib.ssh_shard_words(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def shard_density(self, dens_out: int):
+        _check(self._lib.ssh_shard_density(self._h, dens_out))
+
+    def shard_finish(self, dens_total: int, want_force: bool = True):
+        _check(self._lib.ssh_shard_finish(self._h, dens_total, 1 if want_force else 0))
+
+    def shard_fire_begin(self, params: MinParams | None = None, **kw):
+        p = params if params is not None else self.min_defaults()
+        for k, v in kw.items():
+            setattr(p, k, v)
+        _check(self._lib.ssh_shard_fire_begin(self._h, ctypes.byref(p)))
+
+    def shard_step_dots(self, dots_out: int):
+        _check(self._lib.ssh_shard_step_dots(self._h, dots_out))
+
+    def shard_step_move(self, dots_total: int, dens_out: int):
+        _check(self._lib.ssh_shard_step_move(self._h, dots_total, dens_out))
+
+    def shard_step_finish(self, dens_total: int):
+        _check(self._lib.ssh_shard_step_finish(self._h, dens_total))
 
     @property
     def tc_chunks(self) -> tuple[int, int]:
