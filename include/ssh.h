@@ -119,6 +119,30 @@ ssh_status ssh_set_weights(ssh_ctx* ctx, const double* w);
  * counts: nbins host uint64.  Synchronous.  Errors: SSH_EINVAL, SSH_ECUDA. */
 ssh_status ssh_pair_histogram(ssh_ctx* ctx, int64_t n_ref, double r_max, int nbins, uint64_t* counts);
 
+/* g_2(r) from pair counts (the supplement's Fig. S1b), host arithmetic only (no context, no GPU): g2[b] =
+ * counts[b] / (n_ref (N - 1) / L^d x v_d ((b + 1)^d - b^d) w^d), w = r_max / nbins, v_d the volume of the unit
+ * ball: each shell's count over the count an ideal gas of the same density gives there.  r_mid[b] = (b + 1/2) w
+ * (may be NULL).  counts, r_mid, g2: nbins host values.  Errors: SSH_EINVAL. */
+ssh_status ssh_g2(int d, int64_t N, double L, int64_t n_ref, double r_max, int nbins, const uint64_t* counts,
+                  double* r_mid, double* g2);
+
+/* Shell averages of S(k) = |n~(k)|^2 / N (Eq. structurefactor; the supplement's Fig. S1a shows S(k) on a linear
+ * scale) and the order metric tau of Eq. tau, from the context's last evaluation, in double-double on the GPU.
+ * Shells: edges E_b = ceil(b^2 n2max / nbins^2) (exact integers); shell b < nbins - 1 holds the wavevectors with
+ * E_b <= |n|^2 < E_(b+1), the last E_(nbins-1) <= |n|^2 <= n2max, i.e. |k| = 2 pi |n| / L in
+ * [b, b + 1) x 2 pi sqrt(n2max) / (L nbins).  counts[b] (int64) is the shell's population, mean[2b], mean[2b+1] the
+ * dd mean of S over it (0 when empty), k_mid[b] (may be NULL) the shell's middle |k|.  tau (dd, 2 doubles): the
+ * integral of [S(k) - 1]^2 over k, divided by (2 pi D)^d rho^2 with D = 1 / K and rho = N / L^d, taken as the
+ * lattice sum over every wavevector of the context and its mirror -k (cells (2 pi / L)^d):
+ * tau = 2 (K L)^d / N^2 sum_k [S(k) - 1]^2.  The paper's tau is an ensemble integral in the thermodynamic limit;
+ * over one configuration's wavevectors this is a finite-size estimate (a K-mode context with a cutoff beyond the
+ * exclusion region carries more of the integral).  Each shell and tau are summed in a fixed order, so repeated
+ * calls return the same bits.  1 <= nbins <= 65536; n2max = 0 takes the largest |n|^2 of the set and K = 0 its
+ * largest |k|.  Synchronous.  Errors: SSH_EINVAL (no
+ * evaluation yet, a particle-shard context, arguments), SSH_ECUDA. */
+ssh_status ssh_structure_factor(ssh_ctx* ctx, int nbins, int64_t n2max, double K, int64_t* counts, double* mean,
+                                double* tau, double* k_mid);
+
 /* Particle chunks of the tensor-core path (ssh_opts.tc_chunk): their number and the particles per chunk; both 0
  * when the context uses the integer pipes.  Either pointer may be NULL. */
 ssh_status ssh_get_tc_chunks(const ssh_ctx* ctx, int* nchunk, int64_t* chunk);

@@ -71,6 +71,11 @@ def _load():
             lib.oracle_fire.restype = ctypes.c_int
             lib.oracle_fire.argtypes = [ctypes.c_int, i64, d, P(d), P(d), i64, P(i32), P(FireParams), P(i64),
                                         P(d), P(d), ctypes.c_int]
+            lib.oracle_structure_factor.restype = ctypes.c_int
+            lib.oracle_structure_factor.argtypes = [ctypes.c_int, i64, d, P(d), P(d), i64, P(i32), ctypes.c_int, i64,
+                                                    d, P(i64), P(d), P(d), ctypes.c_int]
+            lib.oracle_g2.restype = ctypes.c_int
+            lib.oracle_g2.argtypes = [ctypes.c_int, i64, d, i64, d, ctypes.c_int, P(ctypes.c_uint64), P(d), P(d)]
             lib.oracle_num_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -164,6 +169,39 @@ def pair_histogram(s_hi, L: float, n_ref: int, r_max: float, nbins: int) -> np.n
         b = np.searchsorted(Eu, r2, side="right") - 1
         counts += np.bincount(b, minlength=nbins)[:nbins]
     return counts.astype(np.uint64)
+
+
+def structure_factor(s_hi, s_lo, n, L: float, nbins: int, n2max: int, K: float, nthreads: int = 0):
+    """Shell averages of S(k) (Eq. structurefactor) over nbins shells of |n| up to sqrt(n2max), and the truncated
+    order metric tau of Eq. tau over every wavevector of n and its mirror, with D = 1 / K; binary128 from the
+    particles' own n~.  Shell b holds E_b <= |n|^2 < E_(b+1), E_b = ceil(b^2 n2max / nbins^2) (the last shell
+    includes n2max).  Returns (counts int64 [nbins], mean S as [nbins, 2] (hi, lo), tau as (hi, lo))."""
+    n = np.ascontiguousarray(n, dtype=np.int32)
+    d = n.shape[1]
+    s_hi, s_lo = _pos(s_hi, s_lo, d)
+    counts = np.zeros(nbins, dtype=np.int64)
+    mean = np.zeros((nbins, 2))
+    tau = np.zeros(2)
+    rc = _load().oracle_structure_factor(d, s_hi.shape[0], L, _dp(s_hi), _dp(s_lo), n.shape[0], _ip(n), nbins,
+                                         int(n2max), K, counts.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                         _dp(mean), _dp(tau), nthreads)
+    if rc != 0:
+        raise RuntimeError(f"oracle_structure_factor rc={rc}")
+    return counts, mean, tau
+
+
+def g2(counts, d: int, N: int, L: float, n_ref: int, r_max: float):
+    """g_2(r) from pair counts (the supplement's Fig. S1b): each shell's count over an ideal gas's expectation,
+    n_ref (N - 1) / L^d x the shell's volume.  Returns (shell centres, g_2)."""
+    c = np.ascontiguousarray(counts, dtype=np.uint64)
+    nb = len(c)
+    r = np.zeros(nb)
+    g = np.zeros(nb)
+    rc = _load().oracle_g2(d, N, L, n_ref, r_max, nb, c.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), _dp(r),
+                           _dp(g))
+    if rc != 0:
+        raise RuntimeError(f"oracle_g2 rc={rc}")
+    return r, g
 
 
 def _pos(s_hi, s_lo, d):

@@ -285,6 +285,88 @@ int oracle_phi_grad(int d, int64_t N, double L, const double *s_hi, const double
   return oracle_phi_grad_w(d, N, L, s_hi, s_lo, M, n, NULL, phi, smax, F_out, C_out, S_out, nthreads);
 }
 
+/* ---------------------------------------------------------------- post-processing (Eq. tau; Fig. S1) */
+
+/* Shell averages of S(k) = |n~(k)|^2 / N (Eq. structurefactor) and the truncated order metric of Eq. tau, from
+ * the particles' own n~ (binary128 throughout).
+ *   Shells: with integers nbins >= 1 and n2max >= 1, edge E_b = ceil(b^2 n2max / nbins^2) (b = 0..nbins, exact
+ *   integer arithmetic); shell b < nbins - 1 holds the wavevectors with E_b <= |n|^2 < E_(b+1), the last shell
+ *   E_(nbins-1) <= |n|^2 <= n2max.  So shell b covers |n| in [b R / nbins, (b + 1) R / nbins), R^2 = n2max, and
+ *   |k| = 2 pi |n| / L.  Wavevectors beyond n2max are in no shell.  counts[b] is the shell's population and
+ *   mean_out[2b], mean_out[2b+1] the (hi, lo) pair of its mean S (0 for an empty shell).
+ *   tau: the integral over k of [S(k) - 1]^2 taken as the lattice sum over every wavevector of the set and its
+ *   mirror -k, each cell of volume (2 pi / L)^d, divided by (2 pi D)^d rho^2 with D = 1 / K and rho = N / L^d:
+ *   tau = 2 (K L)^d / N^2 sum_k [S(k) - 1]^2.  The sum runs in index order. */
+int oracle_structure_factor(int d, int64_t N, double L, const double *s_hi, const double *s_lo, int64_t M,
+                            const int32_t *n, int nbins, int64_t n2max, double K, int64_t *counts, double *mean_out,
+                            double *tau_out, int nthreads) {
+  if (d < 1 || d > 4 || N < 1 || M < 0 || !(L > 0) || nbins < 1 || n2max < 1 || !(K > 0)) return -1;
+  set_threads(nthreads);
+  q_t *C = (q_t *)malloc(sizeof(q_t) * (size_t)(M > 0 ? M : 1));
+  q_t *S = (q_t *)malloc(sizeof(q_t) * (size_t)(M > 0 ? M : 1));
+  q_t *sum = (q_t *)calloc((size_t)nbins, sizeof(q_t));
+  int64_t *E = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nbins + 1));
+  ntilde_q(d, N, s_hi, s_lo, M, n, C, S);
+  const unsigned __int128 den = (unsigned __int128)nbins * (unsigned __int128)nbins;
+  for (int b = 0; b <= nbins; b++) {
+    const unsigned __int128 num = (unsigned __int128)b * (unsigned __int128)b * (unsigned __int128)n2max;
+    E[b] = (int64_t)((num + den - 1) / den);
+  }
+  for (int b = 0; b < nbins; b++) counts[b] = 0;
+  q_t t2 = 0;
+  for (int64_t k = 0; k < M; k++) {
+    int64_t m = 0;
+    for (int a = 0; a < d; a++) m += (int64_t)n[k * d + a] * (int64_t)n[k * d + a];
+    const q_t sk = (C[k] * C[k] + S[k] * S[k]) / (q_t)N;
+    t2 += (sk - 1) * (sk - 1);
+    if (m > n2max) continue;
+    int b = 0;
+    while (b + 1 < nbins && m >= E[b + 1]) b++;   /* linear search: the oracle is not fast, only plain */
+    counts[b]++;
+    sum[b] += sk;
+  }
+  for (int b = 0; b < nbins; b++) {
+    const q_t mean = counts[b] > 0 ? sum[b] / (q_t)counts[b] : 0;
+    q_to_dd(mean, &mean_out[2 * b], &mean_out[2 * b + 1]);
+  }
+  q_t kl = 1;
+  for (int a = 0; a < d; a++) kl *= (q_t)K * (q_t)L;
+  q_to_dd(2 * kl * t2 / ((q_t)N * (q_t)N), &tau_out[0], &tau_out[1]);
+  free(C);
+  free(S);
+  free(sum);
+  free(E);
+  return 0;
+}
+
+/* g_2(r) from pair counts (the supplement's Fig. S1b): counts[b] of ordered pairs (i < n_ref, j != i) at distances
+ * in [b w, (b + 1) w), w = r_max / nbins, divided by the count an ideal gas of the same density gives in that shell,
+ * n_ref (N - 1) / L^d times the shell's volume v_d ((b + 1)^d - b^d) w^d, v_d = pi^(d/2) / Gamma(d/2 + 1) the volume
+ * of the unit ball (2, pi, 4 pi / 3, pi^2 / 2 for d = 1..4).  r_out[b] = (b + 1/2) w. */
+int oracle_g2(int d, int64_t N, double L, int64_t n_ref, double r_max, int nbins, const uint64_t *counts,
+              double *r_out, double *g_out) {
+  if (d < 1 || d > 4 || N < 2 || !(L > 0) || n_ref < 1 || !(r_max > 0) || nbins < 1) return -1;
+  const q_t vd[5] = {0, 2, M_PIq, 4 * M_PIq / 3, M_PIq * M_PIq / 2};
+  const q_t w = (q_t)r_max / (q_t)nbins;
+  q_t ld = 1, wd = 1;
+  for (int a = 0; a < d; a++) {
+    ld *= (q_t)L;
+    wd *= w;
+  }
+  const q_t dens = (q_t)n_ref * (q_t)(N - 1) / ld;
+  for (int b = 0; b < nbins; b++) {
+    q_t lo = 1, hi = 1;
+    for (int a = 0; a < d; a++) {
+      lo *= (q_t)b;
+      hi *= (q_t)(b + 1);
+    }
+    const q_t ideal = dens * vd[d] * (hi - lo) * wd;
+    r_out[b] = (double)(((q_t)b + 0.5Q) * w);
+    g_out[b] = (double)((q_t)counts[b] / ideal);
+  }
+  return 0;
+}
+
 /* ---------------------------------------------------------------- FIRE (Bitzek et al. 2006) */
 
 /*

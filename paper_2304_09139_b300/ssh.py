@@ -118,6 +118,8 @@ def load():
             _sig(lib, "ssh_set_weights", c_int, [c_vp, P(c_d)])
             _sig(lib, "ssh_get_positions", c_int, [c_vp, P(c_d), P(c_d)])
             _sig(lib, "ssh_pair_histogram", c_int, [c_vp, c_i64, c_d, c_int, P(ctypes.c_uint64)])
+            _sig(lib, "ssh_g2", c_int, [c_int, c_i64, c_d, c_i64, c_d, c_int, P(ctypes.c_uint64), P(c_d), P(c_d)])
+            _sig(lib, "ssh_structure_factor", c_int, [c_vp, c_int, c_i64, c_d, P(c_i64), P(c_d), P(c_d), P(c_d)])
             _sig(lib, "ssh_create_kset", c_int, [c_int, c_i64, c_d, c_i64, P(c_i32), c_vp, P(c_vp)])
             _sig(lib, "ssh_kset_build_region", c_int, [c_int, c_i64, c_d, c_d, c_d, P(c_i32), c_i64, P(c_i32), P(c_i64)])
             _sig(lib, "ssh_kset_build", c_int, [c_int, c_i64, c_d, c_d, c_d, c_i64, P(c_i32), P(c_i64)])
@@ -209,43 +211,13 @@ def kset_region(d: int, N: int, L: float, axis_weights, chi: float = 0.0, K: flo
 
 
 def g2(counts, d: int, N: int, L: float, n_ref: int, r_max: float):
-    """g_2(r) from pair_histogram counts: (bin centres, g_2), each bin's count over the count an ideal gas of the
-    same density would give in that shell, n_ref (N - 1) / L^d x shell volume."""
-    nb = len(counts)
-    edges = np.arange(nb + 1) * (r_max / nb)
-    vd = math.pi ** (d / 2) / math.gamma(d / 2 + 1)
-    shell = vd * (edges[1:] ** d - edges[:-1] ** d)
-    return 0.5 * (edges[1:] + edges[:-1]), np.asarray(counts, dtype=np.float64) / (n_ref * (N - 1) / L ** d * shell)
-
-
-def structure_factor_radial(n, C, S, L: float, N: int, nbins: int, k_max: float | None = None):
-    """S(k) = |n~(k)|^2 / N (Eq. structurefactor) averaged over shells of |k| = 2 pi |n| / L: (bin centres, mean
-    S, vectors per bin).  n, C, S as from Context.kset() / ntilde() (C, S as (hi, lo) pairs); a context built in
-    K mode with a cutoff beyond the exclusion region gives S(k) beyond it."""
-    kk = 2 * math.pi / L * np.sqrt((np.asarray(n, dtype=np.float64) ** 2).sum(1))
-    Cv, Sv = np.asarray(C)[..., 0] + np.asarray(C)[..., 1], np.asarray(S)[..., 0] + np.asarray(S)[..., 1]
-    sk = (Cv ** 2 + Sv ** 2) / N
-    top = kk.max() if k_max is None else k_max
-    b = np.minimum((kk / top * nbins).astype(np.int64), nbins - 1)
-    keep = kk <= top
-    cnt = np.bincount(b[keep], minlength=nbins)
-    tot = np.bincount(b[keep], weights=sk[keep], minlength=nbins)
-    with np.errstate(invalid="ignore", divide="ignore"):
-        mean = tot / cnt
-    return (np.arange(nbins) + 0.5) * top / nbins, mean, cnt
-
-
-def tau_estimate(n, C, S, L: float, N: int, K: float) -> float:
-    """The order metric of Eq. tau from one configuration, truncated to the context's wavevectors:
-    (1 / ((2 pi D)^d rho^2)) sum over k of [S(k) - 1]^2 (2 pi / L)^d, over both k and -k, with D = 1 / K and
-    rho = N / L^d.  The paper's tau is an ensemble, thermodynamic-limit integral; this finite lattice sum is
-    for qualitative comparison only."""
-    n = np.asarray(n)
-    d = n.shape[1]
-    Cv, Sv = np.asarray(C)[..., 0] + np.asarray(C)[..., 1], np.asarray(S)[..., 0] + np.asarray(S)[..., 1]
-    sk = (Cv ** 2 + Sv ** 2) / N
-    rho = N / L ** d
-    return float(2 * ((sk - 1.0) ** 2).sum() * (2 * math.pi / L) ** d / ((2 * math.pi / K) ** d * rho ** 2))
+    """g_2(r) from pair_histogram counts (ssh_g2): (bin centres, g_2), each bin's count over the count an ideal gas
+    of the same density gives in that shell."""
+    c = np.ascontiguousarray(counts, dtype=np.uint64)
+    r = np.zeros(len(c))
+    g = np.zeros(len(c))
+    _check(load().ssh_g2(d, N, L, n_ref, r_max, len(c), c.ctypes.data_as(P(ctypes.c_uint64)), _dp(r), _dp(g)))
+    return r, g
 
 
 def ntilde_noalloc(d: int, N: int, M: int, s_hi_ptr: int, s_lo_ptr: int | None, n_ptr: int, C_hi_ptr: int,
@@ -347,6 +319,20 @@ class Context:
         out = np.zeros(nbins, dtype=np.uint64)
         _check(self._lib.ssh_pair_histogram(self._h, n_ref, r_max, nbins, out.ctypes.data_as(P(ctypes.c_uint64))))
         return out
+
+    def structure_factor(self, nbins: int, n2max: int | None = None, K: float | None = None) -> dict:
+        """Shell averages of S(k) and the order metric tau (Eq. tau) from the last evaluation
+        (ssh_structure_factor): shells of |n| up to sqrt(n2max) (default: the largest |n|^2 of the set), tau with
+        D = 1 / K (default: the largest |k| of the set).  Returns counts [nbins], mean [nbins, 2] (dd), tau (hi,
+        lo) and k_mid [nbins]."""
+        counts = np.zeros(nbins, dtype=np.int64)
+        mean = np.zeros((nbins, 2))
+        tau = np.zeros(2)
+        k_mid = np.zeros(nbins)
+        _check(self._lib.ssh_structure_factor(self._h, nbins, int(n2max or 0), float(K or 0.0),
+                                              counts.ctypes.data_as(P(c_i64)),
+                                              _dp(mean), _dp(tau), _dp(k_mid)))
+        return {"counts": counts, "mean": mean, "tau": tau, "k_mid": k_mid}
 
     # ---- particle shards (ssh_shard_*): device buffers are passed as raw pointers (e.g. torch data_ptr())
     def shard_words(self) -> tuple[int, int]:

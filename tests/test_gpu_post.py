@@ -90,11 +90,71 @@ def test_structure_factor_beyond_the_exclusion_region(built, oracle_mod):
     mine = np.array([tuple(v) in inner for v in n])
     assert mine.sum() == len(inner) and sk[mine].max() <= 1.01e-36
     assert 0.2 < sk[kk > 1.5 * kmax].mean() < 5.0
-    kb, sb, cnt = ssh.structure_factor_radial(n, C, S, cfg.L, cfg.N, 20)
-    assert cnt.sum() == len(n) and np.all(np.isfinite(sb[cnt > 0]))
-    assert math.isfinite(ssh.tau_estimate(n, C, S, cfg.L, cfg.N, kmax))
+    sf = wide.structure_factor(20, K=kmax)
+    assert sf["counts"].sum() == len(n) and np.all(np.isfinite(sf["mean"][sf["counts"] > 0]))
+    assert math.isfinite(sf["tau"][0]) and sf["tau"][0] > 0
     # the oracle agrees on S(k) of the wide set
     ref = oracle_mod.phi_grad(hi, lo, n, cfg.L, want_force=False, want_cs=True, nthreads=NTHREADS)
     assert np.all(np.abs((C[:, 0] - ref["C"][:, 0]) + (C[:, 1] - ref["C"][:, 1])) <= 1e-28 * cfg.N)
     wide.close()
+    ctx.close()
+
+
+SF_CASES = [
+    # (label, d, N, L, K cutoff in units of 2 pi / L, nbins, n2max (0: the set's largest), tau's K, seed)
+    ("d2", 2, 1500, 1500 ** 0.5, 14.3, 9, 0, 1.0, 31),
+    ("d3_partial", 3, 700, 700 ** (1 / 3), 5.2, 5, 20, 0.8, 32),
+    ("d1", 1, 900, 900.0, 300.5, 17, 0, 2.0, 33),
+    ("d4", 4, 300, 300 ** 0.25, 2.7, 4, 0, 1.5, 34),
+]
+
+
+@pytest.mark.parametrize("case", SF_CASES, ids=[c[0] for c in SF_CASES])
+@pytest.mark.parametrize("prec", ["fx", "dd"])
+def test_structure_factor_against_oracle(built, oracle_mod, case, prec):
+    """Shell means of S(k) and tau (Eq. tau) from the GPU's evaluation against the oracle's binary128 values from
+    its own n~ at the same positions.  Shell counts are exact integer decisions and must agree exactly.  The GPU's
+    C, S are within 1e-28 N of the oracle's, so S(k) = |n~|^2 / N is within 1e-28 (4 sqrt(N S) + 1) and so is every
+    shell mean (bound by the shell's largest S); tau moves by at most 2 (K L)^d / N^2 sum_k 2 |S - 1| dS."""
+    label, d, N, L, kc, nb, n2max, Kt, seed = case
+    s = synth.positions(seed, N, d)
+    ctx = ssh.Context(d, N, L, K=2 * math.pi / L * kc)
+    ctx.set_positions_frac(s)
+    ctx.energy_grad(ssh.FX if prec == "fx" else ssh.DD)
+    n = ctx.kset()
+    sf = ctx.structure_factor(nb, n2max or None, Kt)
+    sf2 = ctx.structure_factor(nb, n2max or None, Kt)
+    assert all(np.array_equal(sf[k], sf2[k]) for k in sf), "repeated calls give the same bits"
+    top = int((n.astype(np.int64) ** 2).sum(1).max()) if n2max == 0 else n2max
+    counts, mean, tau = oracle_mod.structure_factor(s, None, n, L, nb, top, Kt, nthreads=NTHREADS)
+    assert np.array_equal(sf["counts"], counts)
+    ref = oracle_mod.phi_grad(s, None, n, L, want_force=False, want_cs=True, nthreads=NTHREADS)
+    sk = ((ref["C"][:, 0] + ref["C"][:, 1]) ** 2 + (ref["S"][:, 0] + ref["S"][:, 1]) ** 2) / N
+    dsk = 1e-28 * (4 * np.sqrt(N * sk) + 1) + 1e-30 * sk
+    n2 = (n.astype(np.int64) ** 2).sum(1)
+    E = [-(-(b * b * top) // (nb * nb)) for b in range(nb + 1)]
+    for b in range(nb):
+        sel = (n2 >= E[b]) & ((n2 < E[b + 1]) if b < nb - 1 else (n2 <= top))
+        got = sf["mean"][b, 0] + sf["mean"][b, 1]
+        want = mean[b, 0] + mean[b, 1]
+        if not sel.any():
+            assert got == 0.0 and want == 0.0
+            continue
+        assert abs((sf["mean"][b, 0] - mean[b, 0]) + (sf["mean"][b, 1] - mean[b, 1])) <= dsk[sel].max(), (b, got, want)
+    scale = 2 * (Kt * L) ** d / N ** 2
+    tol = scale * (2 * np.abs(sk - 1) * dsk + dsk ** 2).sum() + 1e-30 * (tau[0] + 1e-300)
+    assert abs((sf["tau"][0] - tau[0]) + (sf["tau"][1] - tau[1])) <= tol, (sf["tau"], tau)
+    assert np.allclose(sf["k_mid"], (np.arange(nb) + 0.5) * 2 * math.pi / L * math.sqrt(top) / nb, rtol=1e-14)
+    ctx.close()
+
+
+def test_structure_factor_rejects_bad_arguments(built):
+    ctx = ssh.Context(2, 200, 200 ** 0.5, chi=0.3)
+    ctx.set_positions_frac(synth.positions(5, 200, 2))
+    with pytest.raises(ssh.SshError):
+        ctx.structure_factor(4)            # no evaluation yet
+    ctx.energy_grad(ssh.FX)
+    for args in ((0,), (70000,), (4, -1), (4, 0, -1.0)):
+        with pytest.raises(ssh.SshError):
+            ctx.structure_factor(*args)
     ctx.close()

@@ -419,3 +419,74 @@ def test_force_at_single_particle_is_zero(oracle_mod):
     C, S = oracle_mod.ntilde(s, None, n)
     F = oracle_mod.force_at(s, None, n, 7.0, C, S)
     assert np.all(np.abs(dd(F)) <= 1e-30 * len(n) * 4)
+
+
+# ------------------------------------------------------------------ post-processing (Eq. tau; the supplement's Fig. S1)
+
+def test_structure_factor_shell_counts_match_jacobi(oracle_mod):
+    """Shell populations: shell b holds the half-space vectors with E_b <= |n|^2 < E_(b+1), E_b = ceil(b^2 R^2 /
+    nbins^2); in d = 2 a value m >= 1 of |n|^2 has r_2(m) / 2 such vectors (Jacobi's two-square theorem)."""
+    L, n2max, nb = 30.0, 400, 7
+    n = oracle_mod.kset(2, 5000, L, K=2 * math.pi / L * math.sqrt(n2max + 30))
+    s = synth.positions(71, 9, 2)
+    counts, _, _ = oracle_mod.structure_factor(s, None, n, L, nb, n2max, 1.0)
+    E = [-(-(b * b * n2max) // (nb * nb)) for b in range(nb + 1)]
+    want = [sum(jacobi_r2(m) // 2 for m in range(max(E[b], 1), E[b + 1] if b < nb - 1 else n2max + 1))
+            for b in range(nb)]
+    assert counts.tolist() == want
+
+
+def test_structure_factor_closed_forms(oracle_mod):
+    """N = 1: S(k) = 1 for every k, so every shell's mean is 1 and tau (Eq. tau) vanishes.  A q x q lattice with
+    every |n_a| < q: n~(k) = 0, S = 0, and tau = 2 (K L)^d M / N^2 (the integral of [0 - 1]^2 over 2 M cells of volume
+    (2 pi / L)^d, divided by (2 pi / K)^d rho^2)."""
+    L, K = 7.0, 1.3
+    n = oracle_mod.kset(2, 1000, L, K=2 * math.pi / L * 5.5)
+    n2max = int((n.astype(np.int64) ** 2).sum(1).max())
+    counts, mean, tau = oracle_mod.structure_factor(np.array([[0.3141, 0.2718]]), None, n, L, 6, n2max, K)
+    full = counts > 0
+    assert counts.sum() == len(n) and full.sum() >= 4 and np.all(mean[~full] == 0)   # |n| < R / 6 holds no vector
+    assert np.all(np.abs(mean[full, 0] - 1.0) + np.abs(mean[full, 1]) <= 1e-30)
+    assert abs(tau[0]) + abs(tau[1]) <= 1e-50
+    q = 8
+    g = np.stack(np.meshgrid(np.arange(q), np.arange(q), indexing="ij"), -1).reshape(-1, 2) / q
+    counts, mean, tau = oracle_mod.structure_factor(g, None, n, L, 6, n2max, K)
+    assert np.all(np.abs(mean[:, 0]) <= 1e-30)
+    want = mpmath.mpf(2) * (mpmath.mpf(K) * mpmath.mpf(L)) ** 2 * len(n) / q ** 4
+    assert abs(mp_dd(tau) - want) <= 1e-30 * want
+
+
+def test_structure_factor_two_particles(oracle_mod):
+    """N = 2: |n~(k)|^2 = 2 + 2 cos(2 pi n.(s_1 - s_2)), so S(k) = 1 + cos(2 pi n.(s_1 - s_2)) (a closed form
+    evaluated here in mpmath); the shell means and tau = 2 (K L)^d / 4 sum_k cos^2 follow, in every dimension."""
+    for d, L, K, nb in ((1, 5.0, 2.0, 4), (2, 6.0, 1.1, 5), (3, 4.0, 0.7, 3)):
+        n = oracle_mod.kset(d, 400, L, K=2 * math.pi / L * 4.2)
+        s = synth.positions(80 + d, 2, d)
+        n2 = (n.astype(np.int64) ** 2).sum(1)
+        n2max = int(n2.max()) - 1          # the outermost shell left out of the shells, kept in tau
+        counts, mean, tau = oracle_mod.structure_factor(s, None, n, L, nb, n2max, K)
+        ds = [mpmath.mpf(float(s[0, a])) - mpmath.mpf(float(s[1, a])) for a in range(d)]
+        sk = [1 + mpmath.cos(2 * mpmath.pi * sum(int(v[a]) * ds[a] for a in range(d))) for v in n]
+        E = [-(-(b * b * n2max) // (nb * nb)) for b in range(nb + 1)]
+        for b in range(nb):
+            top = E[b + 1] if b < nb - 1 else n2max + 1
+            sel = [sk[i] for i in range(len(n)) if E[b] <= n2[i] < top]
+            assert counts[b] == len(sel)
+            if sel:
+                assert abs(mp_dd(mean[b]) - sum(sel) / len(sel)) <= 1e-30
+        want = mpmath.mpf(2) * (mpmath.mpf(K) * mpmath.mpf(L)) ** d / 4 * sum((x - 1) ** 2 for x in sk)
+        assert abs(mp_dd(tau) - want) <= 1e-30 * want
+
+
+def test_g2_of_uniform_points_is_one(oracle_mod):
+    """An ideal gas has g_2 = 1 at every r: uniform random points (pair counts from the exact histogram) give
+    shell values near 1 in d = 1, 2, 3, which fixes the unit-ball volume and the density factor of the
+    normalisation (a slip in either moves every shell by a constant factor)."""
+    for d, N, nb in ((1, 4000, 8), (2, 3000, 8), (3, 3000, 6)):
+        L = N ** (1 / d)
+        s = synth.positions(90 + d, N, d)
+        counts = oracle_mod.pair_histogram(s, L, 600, 0.45 * L, nb)
+        r, g = oracle_mod.g2(counts, d, N, L, 600, 0.45 * L)
+        assert np.allclose(r, (np.arange(nb) + 0.5) * 0.45 * L / nb)
+        assert abs(g[1:].mean() - 1.0) < 0.02, (d, g)
+        assert np.all(np.abs(g[1:] - 1.0) < 0.15), (d, g)
