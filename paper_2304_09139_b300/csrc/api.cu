@@ -284,6 +284,16 @@ ssh_status ssh_get_tc_chunks(const ssh_ctx* h, int* nchunk, int64_t* chunk) {
   return SSH_OK;
 }
 
+ssh_status ssh_get_tc_plan(const ssh_ctx* h, int* row_tiles, int* col_tiles, int* tiles, int* transposed) {
+  if (!h) { set_error("ssh_get_tc_plan: null context"); return SSH_EINVAL; }
+  const ssh::TcPlan& t = h->c.tc;
+  if (row_tiles) *row_tiles = t.on ? t.RT : 0;
+  if (col_tiles) *col_tiles = t.on ? t.CTd : 0;
+  if (tiles) *tiles = t.on ? (int)t.tiles.size() : 0;
+  if (transposed) *transposed = t.on ? t.tr : 0;
+  return SSH_OK;
+}
+
 ssh_status ssh_get_kset(const ssh_ctx* h, int64_t* M, int32_t* n) {
   if (!h) { set_error("ssh_get_kset: NULL context"); return SSH_EINVAL; }
   if (M) *M = h->c.M;

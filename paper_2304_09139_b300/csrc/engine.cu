@@ -215,6 +215,10 @@ cudaError_t engine_build(Engine* e, const std::vector<Ctx*>& members, const std:
       std::stable_sort(tcf.begin() + P.force_off, tcf.end(), [&](const TcItem& a, const TcItem& b) {
         return bundle[{a.cfg, a.a}] > bundle[{b.cfg, b.a}];
       });
+      // the last items of the queue decide when the launch ends: the final two items per SM go largest first, so the
+      // launch ends on the shortest ones
+      const size_t tail = std::min<size_t>(tcf.size() - P.force_off, 2 * (size_t)e->sm_count);
+      std::stable_sort(tcf.end() - tail, tcf.end(), by_size);
     } else {
       std::stable_sort(tcf.begin() + P.force_off, tcf.end(), by_size);
     }

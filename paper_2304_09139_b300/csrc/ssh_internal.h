@@ -88,6 +88,9 @@ struct CfgDev {
   // tensor-core fixed-point path (tc.cu); tc = 0 when the configuration uses the integer-pipe kernels
   int tc, tc_R1, tc_nP, tc_RT, tc_CTd, tc_PT, tc_KSf, tc_CTf, tc_bexp, tc_nblk, tc_gs, tc_ts, tc_ntab;
   int tc_d, tc_lift;   // the path's number of axes (2 or 3); d = 1 on two lifted axes: n = 2^tc_lift n1 + n2
+  // two-axis path: the last row tile's canonical p (those >= tc_trP0) run as one transposed density tile, rows
+  // (n1, cos / sin) of a_j(n1) for n1 < tc_trN1 from local row tc_trRow0 of that row tile, columns (p, cos / sin)
+  int tc_tr, tc_trP0, tc_trRow0, tc_trN1;
   int tc_Rax[3];       // per axis: powers 0..tc_Rax[a] in the tables
   int64_t tc_KS, tc_NJ, tc_NPg;  // density K-steps; particle groups and row groups of the digit tensor (a chunk)
   int64_t tc_j0, tc_n, tc_nbuf;  // this chunk: first particle, particles, particle stride of the chunk buffers
@@ -258,7 +261,12 @@ struct TcPlan {
   int64_t Nc = 0;                // particles per chunk (the buffers below hold one chunk), a multiple of 128
   int nchunk = 1;                // chunks of N, evaluated one after another
   int64_t KS = 0;                // density K-steps (16 particles each) of a full chunk
-  int RT = 0, CTd = 0;           // density row tiles (128 rows (p, cos/sin)), column tiles (32 columns (n1, cos/sin))
+  int RT = 0, CTd = 0;           // density row tiles (128 rows (p, cos/sin)), column tiles (32 columns (n1, cos/sin);
+                                 // with tr, one more: the transposed tile's B operand, w_j(p) of the last row tile)
+  // transposed remainder tile (two-axis path): the last row tile holds at most 16 canonical p, whose members have
+  // n1 < trN1; their density is one tile with rows (n1, cos / sin) of a_j(n1), written into that row tile of the digit
+  // tensor from local row trRow0 (past every K row the force reads), and columns (p, cos / sin) of w_j(p)
+  int tr = 0, trP0 = 0, trRow0 = 0, trN1 = 0;
   int PT = 0, KSf = 0, CTf = 0;  // force particle tiles (of a chunk), K-steps (16 rows (p, cos/sin)), column tiles (16/d n1, all axes)
   int64_t NJ = 0, NPg = 0;       // digit tensor: particle groups (of a chunk) and row groups of 8
   int bexp = 0;                  // 2^bexp > |n_a| (a >= 2): scale of the weighted force coefficients

@@ -267,8 +267,10 @@ __device__ __forceinline__ qent qconj(const qent& z) {
 // 16-byte row (8 bf16) per digit slice, slice s holding digit 14 - s.  Digit i < 14 is d = u - 64 with u the
 // bits 7i..7i+6 of Y; the bf16 of 192 + d = 128 + u is 0x4300 | u (exponent 2^7, mantissa u), so one packed
 // bf16 subtraction of 192 gives two digits exactly.  The top digit, the signed bits 98..127 (it may be 64), is
-// converted through fp32.
-__device__ __forceinline__ void put_digit_rows(uint8_t* base, size_t slice_stride, const uint4 (&Y)[8]) {
+// converted through fp32.  With base2 set, every row is also stored at base2 (slices slice_stride2 apart): the digits
+// are formed once.
+__device__ __forceinline__ void put_digit_rows(uint8_t* base, size_t slice_stride, const uint4 (&Y)[8],
+                                               uint8_t* base2 = nullptr, size_t slice_stride2 = 0) {
   {
     uint32_t f[8];
 #pragma unroll
@@ -283,6 +285,7 @@ __device__ __forceinline__ void put_digit_rows(uint8_t* base, size_t slice_strid
     row.z = __byte_perm(f[4], f[5], 0x7632);
     row.w = __byte_perm(f[6], f[7], 0x7632);
     *reinterpret_cast<uint4*>(base) = row;
+    if (base2) *reinterpret_cast<uint4*>(base2) = row;
   }
   const __nv_bfloat162 b192 = __halves2bfloat162(__ushort_as_bfloat16((unsigned short)0x4340),
                                                  __ushort_as_bfloat16((unsigned short)0x4340));
@@ -300,7 +303,9 @@ __device__ __forceinline__ void put_digit_rows(uint8_t* base, size_t slice_strid
       const __nv_bfloat162 r = __hsub2(*reinterpret_cast<const __nv_bfloat162*>(&t), b192);
       wv[pr] = *reinterpret_cast<const uint32_t*>(&r);
     }
-    *reinterpret_cast<uint4*>(base + (size_t)s * slice_stride) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+    const uint4 row = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+    *reinterpret_cast<uint4*>(base + (size_t)s * slice_stride) = row;
+    if (base2) *reinterpret_cast<uint4*>(base2 + (size_t)s * slice_stride2) = row;
   }
 }
 
@@ -485,7 +490,19 @@ __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restri
       uint8_t* base = kind == 0
           ? c.tc_aB + ((int64_t)(r >> 5) * c.tc_KS + (jg >> 4)) * kStageB + slice_off(r & 31, (int)(jg & 15))
           : c.tc_wT + ((size_t)(r >> 3) * (size_t)c.tc_NJ + (size_t)(jg >> 3)) * 128 + (r & 7) * 16;
-      put_digit_rows(base, kind == 0 ? (size_t)kSliceB : wstride, Y);
+      // the transposed remainder tile: a_j(n1) also as digit-tensor rows, w_j(p) of the last row tile also as the
+      // columns of its B operand (the last density column tile)
+      uint8_t* b2 = nullptr;
+      if (c.tc_tr && (kind == 0 ? e < c.tc_trN1 : e >= c.tc_trP0)) {
+        if (kind == 0) {
+          const int rt = kTileM * (c.tc_RT - 1) + c.tc_trRow0 + r;
+          b2 = c.tc_wT + ((size_t)(rt >> 3) * (size_t)c.tc_NJ + (size_t)(jg >> 3)) * 128 + (rt & 7) * 16;
+        } else {
+          const int col = 2 * (e - c.tc_trP0) + h;
+          b2 = c.tc_aB + ((int64_t)(c.tc_CTd - 1) * c.tc_KS + (jg >> 4)) * kStageB + slice_off(col, (int)(jg & 15));
+        }
+      }
+      put_digit_rows(base, kind == 0 ? (size_t)kSliceB : wstride, Y, b2, kind == 0 ? wstride : (size_t)kSliceB);
     }
   }
 }
@@ -506,7 +523,6 @@ __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restri
 __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __restrict__ cfgs,
                                                               const TcItem* __restrict__ items, int n_items,
                                                               int* __restrict__ queue) {
-  grid_dep_wait();
   extern __shared__ __align__(128) uint8_t smem_raw[];
   // tensor-map destinations must be 128-byte aligned
   uint8_t* smem = reinterpret_cast<uint8_t*>(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
@@ -535,6 +551,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  // the set-up above touches no global memory, so it overlaps the end of the previous kernel; the operands, the
+  // queue and the accumulators are used only after that kernel has completed
+  grid_dep_wait();
   const uint32_t tbase = tmem_base_sh;
   volatile int* abort_flag = &abort_sh;
   const long long wlim = g_tc_wait_limit;  // waits on work; the drains below always use kWaitLimit
@@ -850,6 +869,7 @@ __global__ void __launch_bounds__(kFinThreads) k_tc_dens_finish(const CfgDev* __
   const int64_t idx = ((int64_t)m.blk * kFinThreads + threadIdx.x) >> 1;
   const int neg = threadIdx.x & 1;
   int k = -1, ti = -1, rr = 0, cc = 0;
+  bool tr = false;
   long long P[4][3];  // [2 x + y]: x the cos / sin of w (row), y of a (column)
   long long* acc = nullptr;
   if (idx < (int64_t)W1 * c.tc_nP) {
@@ -857,17 +877,22 @@ __global__ void __launch_bounds__(kFinThreads) k_tc_dens_finish(const CfgDev* __
     const int kp = c.tc_em[idx * 2 + 0], km = c.tc_em[idx * 2 + 1];  // em is [p][n1][2]
     k = neg ? km : kp;
     const int r = 2 * p, col = 2 * n1;
-    ti = (kp >= 0 || km >= 0) ? c.tc_tilemap[(r >> 7) * c.tc_CTd + (col >> 5)] : -1;
+    // the transposed remainder tile holds P_xy(p, n1) at row trRow0 + 2 n1 + y, column 2 (p - trP0) + x
+    tr = c.tc_tr && p >= c.tc_trP0;
+    ti = (kp >= 0 || km >= 0)
+             ? c.tc_tilemap[tr ? (c.tc_RT - 1) * c.tc_CTd + (c.tc_CTd - 1) : (r >> 7) * c.tc_CTd + (col >> 5)]
+             : -1;
     if (ti >= 0) {
-      rr = r & 127;
-      cc = col & 31;
+      rr = tr ? c.tc_trRow0 + col : r & 127;
+      cc = tr ? 2 * (p - c.tc_trP0) : col & 31;
       acc = c.tc_acc + (size_t)ti * (3 * kTileN * kTileM);
 #pragma unroll
       for (int x = 0; x < 2; x++)
 #pragma unroll
         for (int y = 0; y < 2; y++)
 #pragma unroll
-          for (int g = 0; g < 3; g++) P[2 * x + y][g] = acc[((size_t)g * kTileN + cc + y) * kTileM + rr + x];
+          for (int g = 0; g < 3; g++)
+            P[2 * x + y][g] = acc[((size_t)g * kTileN + cc + (tr ? x : y)) * kTileM + rr + (tr ? y : x)];
     }
   }
   __syncwarp();
@@ -877,7 +902,7 @@ __global__ void __launch_bounds__(kFinThreads) k_tc_dens_finish(const CfgDev* __
 #pragma unroll
       for (int y = 0; y < 2; y++)
 #pragma unroll
-        for (int g = 0; g < 3; g++) acc[((size_t)g * kTileN + cc + y) * kTileM + rr + x] = 0;
+        for (int g = 0; g < 3; g++) acc[((size_t)g * kTileN + cc + (tr ? x : y)) * kTileM + rr + (tr ? y : x)] = 0;
   }
   if (ti >= 0 && k >= 0) {
     // n~(n1, p)  = (P_cc - P_ss) + i (P_cs + P_sc);  n~(n1, -p) = (P_cc + P_ss) + i (P_cs - P_sc)
@@ -1228,6 +1253,36 @@ cudaError_t tc_setup(Ctx* c) {
   const int npt = 16 / d;  // force column tile: n1 in [npt ct, npt ct + npt), every axis of each (2 d columns per n1)
   t.CTf = (W1 + npt - 1) / npt;
   t.NPg = (int64_t)t.RT * (kTileM / 8);
+  // Transposed remainder tile (two axes).  The last row tile holds rows (p, cos / sin) of the canonical p >= p0
+  // only, often a small fraction of its 128 rows, yet it is paired with every column tile its members reach.  When
+  // those p fit 32 columns and their n1 fit the rows the force never reads (from the K-step boundary past 2 nP), one
+  // tile with the roles swapped covers them all: rows (n1, cos / sin) of a_j(n1), columns (p, cos / sin) of w_j(p).
+  t.tr = 0;
+  if (d == 2 && t.RT >= 2) {
+    const int p0 = (kTileM / 2) * (t.RT - 1);
+    const int row0 = (2 * nP + kStepK - 1) / kStepK * kStepK - kTileM * (t.RT - 1);
+    int n1max = -1;
+    std::vector<char> reach(t.CTd, 0);
+    for (int64_t k = 0; k < M; k++) {
+      int n1, n2, n3;
+      sub_vec(*c, lift, k, n1, n2, n3);
+      const bool can = canonical(n2, n3);
+      const int p = pid[(size_t)((can ? n3 : -n3) + Rp) * span + ((can ? n2 : -n2) + Rp)];
+      if (p >= p0) {
+        n1max = std::max(n1max, n1);
+        reach[(2 * n1) >> 5] = 1;
+      }
+    }
+    int used = 0;
+    for (char r : reach) used += r;
+    if (2 * (nP - p0) <= kTileN && row0 + 2 * (n1max + 1) <= kTileM && used >= 2) {
+      t.tr = 1;
+      t.trP0 = p0;
+      t.trRow0 = row0;
+      t.trN1 = n1max + 1;
+      t.CTd += 1;
+    }
+  }
   t.bexp = 0;
   while ((1 << t.bexp) <= std::max(R2, R3)) t.bexp++;
   // emit map: k = (n1, p) -> [p][n1][0], k = (n1, -p) -> [p][n1][1]
@@ -1240,7 +1295,10 @@ cudaError_t tc_setup(Ctx* c) {
     const bool can = canonical(n2, n3);
     const int p = pid[(size_t)((can ? n3 : -n3) + Rp) * span + ((can ? n2 : -n2) + Rp)];
     t.em[((size_t)p * W1 + n1) * 2 + (can ? 0 : 1)] = (int32_t)k;
-    t.tilemap[(size_t)((2 * p) >> 7) * t.CTd + ((2 * n1) >> 5)] = 1;
+    if (t.tr && p >= t.trP0)
+      t.tilemap[(size_t)(t.RT - 1) * t.CTd + (t.CTd - 1)] = 1;
+    else
+      t.tilemap[(size_t)((2 * p) >> 7) * t.CTd + ((2 * n1) >> 5)] = 1;
     pmax_ct[n1 / npt] = std::max(pmax_ct[n1 / npt], p);
   }
   for (int i = 0; i < t.RT * t.CTd; i++)
@@ -1358,6 +1416,10 @@ void tc_fill_cfgdev(const Ctx* c, CfgDev* g) {
   if (!t.on) return;
   g->tc_d = t.d;
   g->tc_lift = t.lift;
+  g->tc_tr = t.tr;
+  g->tc_trP0 = t.trP0;
+  g->tc_trRow0 = t.trRow0;
+  g->tc_trN1 = t.trN1;
   g->tc_R1 = t.R1;
   g->tc_nP = t.nP;
   for (int a = 0; a < 3; a++) g->tc_Rax[a] = t.Rax[a];

@@ -115,6 +115,7 @@ def load():
             _sig(lib, "ssh_get_kset", c_int, [c_vp, P(c_i64), P(c_i32)])
             _sig(lib, "ssh_get_fx_impl", c_int, [c_vp, P(c_int)])
             _sig(lib, "ssh_get_tc_chunks", c_int, [c_vp, P(c_int), P(c_i64)])
+            _sig(lib, "ssh_get_tc_plan", c_int, [c_vp, P(c_int), P(c_int), P(c_int), P(c_int)])
             _sig(lib, "ssh_set_weights", c_int, [c_vp, P(c_d)])
             _sig(lib, "ssh_get_positions", c_int, [c_vp, P(c_d), P(c_d)])
             _sig(lib, "ssh_pair_histogram", c_int, [c_vp, c_i64, c_d, c_int, P(ctypes.c_uint64)])
@@ -368,6 +369,13 @@ class Context:
         n, c = c_int(), c_i64()
         _check(self._lib.ssh_get_tc_chunks(self._h, ctypes.byref(n), ctypes.byref(c)))
         return n.value, c.value
+
+    @property
+    def tc_plan(self) -> dict:
+        """The tensor-core density tile plan (ssh_get_tc_plan): row tiles, column tiles, tiles in use, transposed."""
+        v = [c_int() for _ in range(4)]
+        _check(self._lib.ssh_get_tc_plan(self._h, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("row_tiles", "col_tiles", "tiles", "transposed"), (x.value for x in v)))
 
     def kset(self) -> np.ndarray:
         out = np.zeros((max(self.M, 1), self.d), dtype=np.int32)

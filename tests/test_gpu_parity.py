@@ -84,6 +84,10 @@ CASES = [
     # |n| <= 17.5: n1 in [0, 17] (two column tiles of the tensor-core density), about 480 canonical (n2, n3)
     # (eight row tiles), 1500 particles (a ragged last particle tile)
     ("d3_wide_kmode", 3, 1500, 1500 ** (1 / 3), 0.0, 2 * math.pi * 17.5 / 1500 ** (1 / 3), 15),
+    # |n| <= 66.5: 67 canonical n2, the last row tile's three (n2 >= 64, n1 <= 18) run as the transposed tile
+    ("d2_transposed", 2, 900, 30.0, 0.0, 2 * math.pi * 66.5 / 30.0, 17),
+    # |n| <= 79.5: the transposed tile at its limits, 16 p in its 32 columns and n1 <= 47 filling its rows to 128
+    ("d2_transposed_full", 2, 600, 25.0, 0.0, 2 * math.pi * 79.5 / 25.0, 18),
 ]
 
 
@@ -423,3 +427,22 @@ def test_region_parity(built, oracle_mod, case):
         for prec in precs:
             check_parity(ctx, s, None, L, prec, ref, n, label=f"{label}/{ssh.PREC_NAMES[prec]}/impl{impl}")
         ctx.close()
+
+
+@pytest.mark.parametrize("label, d, N, L, chi, K, want", [
+    # the d = 2, N = 10^4, chi = 0.45 workload: 76 canonical n2 in two row tiles; the last one's 12 (n1 <= 40) run
+    # transposed, so its three (row tile, column tile) pairs become one tile
+    ("medium_d2", 2, 10_000, 100.0, 0.45, 0.0, {"row_tiles": 2, "col_tiles": 6, "tiles": 6, "transposed": 1}),
+    ("d2_transposed", 2, 900, 30.0, 0.0, 2 * math.pi * 66.5 / 30.0, {"row_tiles": 2, "tiles": 6, "transposed": 1}),
+    ("d2_transposed_full", 2, 600, 25.0, 0.0, 2 * math.pi * 79.5 / 25.0, {"row_tiles": 2, "transposed": 1}),
+    # one row tile: nothing to transpose
+    ("small_d2", 2, 100, 1.0, 0.30, 0.0, {"row_tiles": 1, "transposed": 0}),
+    # |n| <= 80.5: 81 canonical n2, 17 in the last row tile, more than its 32 columns hold
+    ("d2_no_transpose", 2, 600, 25.0, 0.0, 2 * math.pi * 80.5 / 25.0, {"row_tiles": 2, "transposed": 0}),
+    ("d3", 3, 300, 300 ** (1 / 3), 0.40, 0.0, {"transposed": 0}),
+])
+def test_density_tile_plan(built, label, d, N, L, chi, K, want):
+    """The density tile plan of the tensor-core path: which sets run their last row tile transposed."""
+    with ssh.Context(d, N, L, chi=chi, K=K, fx_impl=ssh.FX_TENSOR) as ctx:
+        plan = ctx.tc_plan
+        assert all(plan[k] == v for k, v in want.items()), (label, plan)
