@@ -234,3 +234,36 @@ def test_anisotropic_region_quench_converges(built, oracle_mod):
     sm, _ = oracle_smax(oracle_mod, ctx, hi, lo)
     assert sm <= 1.01e-36, (sm, r)
     ctx.close()
+
+
+@pytest.mark.parametrize("d,N,chi,seed", [(2, 2000, 0.45, 41), (3, 1000, 0.40, 42)], ids=["d2", "d3"])
+def test_staged_fp64_dd_error_per_stage(built, oracle_mod, d, N, chi, seed):
+    """The paper's own ladder in its own arithmetic: an FP64 descent to S_max <= 1e-24, then the double-double
+    polish to 1e-36, as two single-stage minimisations (FIRE restarts at every stage).  At the end of each stage
+    that stage's arithmetic, evaluated at the stage's final positions, is compared with the binary128 oracle on
+    every wavevector: within 1e-13 N (FP64) and 1e-28 N (dd) per component of n~, and the final state's oracle
+    S_max at or below the target."""
+    L = N ** (1 / d)
+    ctx = ssh.Context(d, N, L, chi=chi)
+    n = ctx.kset()
+    ctx.set_positions_frac(synth.positions(seed, N, d))
+
+    def stage_error(prec):
+        ctx.energy_grad(prec, want_force=False)
+        C, S = ctx.ntilde()
+        hi, lo = ctx.positions_frac()
+        ref = oracle_mod.phi_grad(hi, lo, n, L, want_force=False, want_cs=True, nthreads=NTHREADS)
+        dC = np.abs((C[:, 0] - ref["C"][:, 0]) + (C[:, 1] - ref["C"][:, 1]))
+        dS = np.abs((S[:, 0] - ref["S"][:, 0]) + (S[:, 1] - ref["S"][:, 1]))
+        return max(dC.max(), dS.max()) / N, ref["smax"][0] + ref["smax"][1]
+
+    r1 = ctx.minimize(stages=[ssh.FP64], smax_target=1e-24, max_steps=40000, max_seconds=120)
+    assert r1["status"] in (0, 5), r1          # at the stage floor, or stalled near it
+    e1, _ = stage_error(ssh.FP64)
+    assert e1 <= 1e-13, e1
+    r2 = ctx.minimize(stages=[ssh.DD], max_steps=40000, max_seconds=240)
+    assert r2["status"] == 0, r2
+    e2, sm2 = stage_error(ssh.DD)
+    assert e2 <= 1e-28, e2
+    assert sm2 <= 1.01e-36, sm2
+    ctx.close()
