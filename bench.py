@@ -102,10 +102,10 @@ WORKLOAD = WORKLOADS["d2-n10000"]
 # the kernel's family of sources hashes to the value recorded with them; otherwise the traffic is reported as null.
 NCU_TRAFFIC = {("d2-n10000", "fx", "force"): ("2d22c6704b91", 35_869_696 + 1_536),
                ("d2-n10000", "fx", "ntilde"): ("2d22c6704b91", 36_569_600 + 13_568),
-               ("d2-n10000", "fx-tensor", "tc_force"): ("d7bda9a5ac2c", 74_688_512 + 2_547_712),
-               ("d2-n10000", "fx-tensor", "tc_dens"): ("d7bda9a5ac2c", 126_249_216 + 4_840_960),
-               ("d3-n32768", "fx-tensor", "tc_force"): ("d7bda9a5ac2c", 2_292_177_000 + 20_520_000),
-               ("d3-n32768", "fx-tensor", "tc_dens"): ("d7bda9a5ac2c", 3_008_816_000 + 8_002_000)}
+               ("d2-n10000", "fx-tensor", "tc_force"): ("b284e7325135", 74_685_696 + 2_521_856),
+               ("d2-n10000", "fx-tensor", "tc_dens"): ("b284e7325135", 135_649_024 + 5_326_080),
+               ("d3-n32768", "fx-tensor", "tc_force"): ("b284e7325135", 3_585_672_000 + 26_525_000),
+               ("d3-n32768", "fx-tensor", "tc_dens"): ("b284e7325135", 3_008_942_000 + 8_470_000)}
 
 
 # The sources each family of kernels is built from: the integer fixed-point and dd kernels, and the tensor-core
@@ -141,6 +141,7 @@ def parse():
                     help="skip the FP64 -> dd and all-dd quenches of the d=2 N=100 and N=10^4 workloads (about 4 min)")
     ap.add_argument("--dd-seconds", type=float, default=300.0, help="wall limit of each dd-ladder quench")
     ap.add_argument("--no-floor", action="store_true", help="skip the quenches to the paper's 1e-50 floor")
+    ap.add_argument("--no-gemm-counters", action="store_true", help="skip the GEMM cycle-counter block")
     ap.add_argument("--minimize-seconds", type=float, default=150.0)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the d=3, N=32768 block")
@@ -392,6 +393,44 @@ def dd_ladder_block(ssh, synth, dev, stream, max_seconds=300.0):
                                                       if b["configs_per_hour"] > 0 else None)
         blk["stage_error_note"] = ("max |n~ - n~_oracle| / N over 256 sampled wavevectors at the end of each stage, in "
                                    "that stage's arithmetic (bounds: 1e-13 FP64, 1e-28 dd)")
+        out[tag] = blk
+    return out
+
+
+def gemm_counters_block(ssh, synth, dev, stream):
+    """Where the tensor-core GEMMs' time goes (ssh_gemm_counters: a counting instance of the kernel records, per CTA,
+    clock64 cycles in each wait and phase): one evaluation of the d=2 N=10^4 and d=3 N=32768 workloads after three
+    warm ones.  Fractions are of the mean CTA time; cycles per K-step divide the MMA thread's time outside its waits
+    by its K-steps.  The counting instance spills a few registers, so its times run slightly above production."""
+    f = {n: i for i, n in enumerate(ssh.GEMM_COUNTER_FIELDS)}
+    out = {}
+    for tag, cfg in (("d2_N10000", synth.MEDIUM_D2), ("d3_N32768", synth.LARGE_D3)):
+        c = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi, device=dev)
+        c.set_stream(stream.cuda_stream)
+        c.set_positions_frac(synth.positions(cfg.seed, cfg.N, cfg.d))
+        ssh.gemm_counters(True, dev)
+        try:
+            for _ in range(4):
+                c.eval(ssh.FX)
+            c.sync()
+            rec = ssh.gemm_counters_read(dev).astype(np.float64)
+        finally:
+            ssh.gemm_counters(False, dev)
+            c.close()
+        blk = {}
+        for kind, name in ((0, "density"), (1, "force")):
+            r = rec[kind][rec[kind][:, f["cycles"]] > 0]
+            tot = r[:, f["cycles"]].mean()
+            waits = r[:, [f["mma_wait_operands"], f["mma_wait_accumulator"], f["mma_wait_item"]]].sum(1)
+            blk[name] = {"ctas": int(len(r)), "cta_cycles_mean": tot, "cta_cycles_max": r[:, f["cycles"]].max(),
+                         "span_us": (r[:, f["t1_ns"]].max() - r[:, f["t0_ns"]].min()) / 1e3,
+                         "end_spread_us": (r[:, f["t1_ns"]].max() - r[:, f["t1_ns"]].min()) / 1e3,
+                         "items_per_cta": r[:, f["items"]].mean(), "ksteps_per_cta": r[:, f["ksteps"]].mean(),
+                         "mma_cycles_per_kstep": ((r[:, f["mma_thread_cycles"]] - waits) / r[:, f["ksteps"]]).mean(),
+                         **{k: r[:, f[k]].mean() / tot for k in ("mma_wait_operands", "mma_wait_accumulator",
+                                                                  "mma_wait_item", "producer_wait_stage",
+                                                                  "epilogue_wait_accumulator", "epilogue_readout",
+                                                                  "epilogue_math")}}
         out[tag] = blk
     return out
 
@@ -953,6 +992,8 @@ def main():
         line["serving"] = serving_block(ssh, synth, dev, window_s=args.serve_seconds, method=args.serve_method)
         line["p50_s"] = line["serving"]["p50_s"]
         line["p99_s"] = line["serving"]["p99_s"]
+    if rank == 0 and world == 1 and not args.no_gemm_counters and tensor:
+        line["gemm_counters"] = gemm_counters_block(ssh, synth, dev, stream)
     if rank == 0 and world == 1 and not args.no_floor:
         line["floor"] = floor_block(ssh, synth, dev, stream)
     if rank == 0 and world == 1 and not args.no_dd_ladder:

@@ -57,7 +57,7 @@ static cudaError_t eval_replayed(ssh::Ctx& c, int prec, bool want_force) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaError_t e = cudaStreamIsCapturing(c.stream, &cs);
   if (e != cudaSuccess) return e;
-  if (c.prof.on || cs != cudaStreamCaptureStatusNone) return ssh::eval_phi_grad(&c, prec, want_force);
+  if (c.prof.on || ssh::tc_counters_on() || cs != cudaStreamCaptureStatusNone) return ssh::eval_phi_grad(&c, prec, want_force);
   cudaGraphExec_t& g = c.eval_graph[prec][want_force ? 1 : 0];
   if (!g) {
     cudaGraph_t graph = nullptr;

@@ -422,6 +422,8 @@ long long* tc_acc_ptr(const Ctx* c);
 int64_t tc_acc_words(const Ctx* c);
 cudaError_t tc_launch_force(const EngineView& v, cudaStream_t st, Prof* prof);
 cudaError_t tc_launch_force_finish(const EngineView& v, cudaStream_t st, Prof* prof);
+// the counting instance of the GEMM is in use (ssh_gemm_counters): evaluations launch directly, not from graphs
+bool tc_counters_on();
 
 // kernels.cu
 cudaError_t plan_upload(Ctx* c);

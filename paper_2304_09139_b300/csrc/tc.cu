@@ -73,6 +73,20 @@ __device__ __forceinline__ bool stopped(const CfgDev& c) { return c.run && *c.ru
 // it.  The waits that let copies and MMAs in flight land before a CTA exits always use kWaitLimit.
 __device__ long long g_tc_wait_limit = kWaitLimit;
 
+// Cycle counters of the GEMM (ssh_gemm_counters): one record of kGcFields words per CTA and launch kind (density,
+// force), written by the counting instance of k_tc_gemm only.  The production instance has none of this code.
+constexpr int kGcCtas = 256, kGcFields = 16;
+__device__ unsigned long long g_tc_counters[2][kGcCtas][kGcFields];
+// on for this process between ssh_gemm_counters(.., 1) and (.., 0): GEMM launches use the counting instance
+bool g_counters_on = false;
+enum { kGcCycles = 0, kGcProdWaitStage, kGcMmaWaitOperands, kGcMmaWaitAcc, kGcMmaWaitItem, kGcEpiWaitAcc,
+       kGcEpiRead, kGcEpiMath, kGcItems, kGcKsteps, kGcMmaCycles, kGcT0, kGcT1 };
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // A wait gave up: record `code` in the error word of every configuration with items in this launch, since the
 // items this CTA had claimed or published (and so skips) may belong to any of them.
 __device__ __noinline__ void tc_flag_all(const CfgDev* __restrict__ cfgs, const TcItem* __restrict__ items,
@@ -520,6 +534,7 @@ __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restri
 // Stage and accumulator barrier phases run on across items, so the producer streams the next item's operands
 // while the epilogue finishes the previous item (the accumulator is released as soon as its last level has
 // been read).
+template <bool kCount>
 __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __restrict__ cfgs,
                                                               const TcItem* __restrict__ items, int n_items,
                                                               int* __restrict__ queue) {
@@ -557,6 +572,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
   const uint32_t tbase = tmem_base_sh;
   volatile int* abort_flag = &abort_sh;
   const long long wlim = g_tc_wait_limit;  // waits on work; the drains below always use kWaitLimit
+  // counting instance: cycles spent in each wait and phase (kGc* fields), one record per CTA
+  const long long T0 = kCount ? clock64() : 0;
+  const unsigned long long G0 = kCount ? global_ns() : 0;
+  long long c_prod = 0, c_full = 0, c_acc = 0, c_item = 0, c_items = 0, c_ks = 0, c_eacc = 0, c_eread = 0, c_emath = 0;
 
   if (warp == 0) {
     // ---- producer: one thread streams every item's K-steps through the stages
@@ -588,7 +607,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
         for (int ks = 0; ks < it.nks; ks++, gs++) {
           const int s = (int)(gs % kStages);
           const long long use = gs / kStages;
-          if (use > 0 && !mbar_wait(&bar_empty[s], (uint32_t)((use - 1) & 1), wlim, abort_flag)) {
+          const long long tw0 = kCount ? clock64() : 0;
+          const bool free_stage = use == 0 || mbar_wait(&bar_empty[s], (uint32_t)((use - 1) & 1), wlim, abort_flag);
+          if (kCount) c_prod += clock64() - tw0;
+          if (!free_stage) {
             *abort_flag = 1;
             tc_flag_all(cfgs, items, n_items, 1);
             stop = true;
@@ -619,7 +641,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
       bool stop = false;
       for (long long n = 0; !stop; n++) {
         const int r = (int)(n % kRing);
-        if (!mbar_wait(&bar_item_full[r], (uint32_t)((n / kRing) & 1), wlim, abort_flag)) {
+        const long long ti0 = kCount ? clock64() : 0;
+        const bool have_item = mbar_wait(&bar_item_full[r], (uint32_t)((n / kRing) & 1), wlim, abort_flag);
+        if (kCount) c_item += clock64() - ti0;
+        if (!have_item) {
           *abort_flag = 1;
           tc_flag_all(cfgs, items, n_items, 64);
           break;
@@ -630,6 +655,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
         const TcItem it = items[item];
         const CfgDev& c = cfgs[it.cfg];
         if (stopped(c)) continue;
+        if (kCount) c_items++;
         // density A: K-major, core matrices 128 bytes apart along K and 256 along M; force A: MN-major, 128
         // bytes apart along M (particles) and 2048 along K
         const int mn = it.kind == 0 ? 0 : 1;
@@ -639,13 +665,22 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
           const long long use = gs / kStages;
           const bool first = ks % kChunkSteps == 0;
           const bool last = ks % kChunkSteps == kChunkSteps - 1 || ks == it.nks - 1;
-          if (!mbar_wait(&bar_full[s], (uint32_t)(use & 1), wlim, abort_flag)) {
+          const long long tf0 = kCount ? clock64() : 0;
+          const bool full_stage = mbar_wait(&bar_full[s], (uint32_t)(use & 1), wlim, abort_flag);
+          if (kCount) c_full += clock64() - tf0;
+          if (!full_stage) {
             *abort_flag = 1;
             tc_flag_all(cfgs, items, n_items, 2);
             stop = true;
             break;
           }
-          if (first && gc > 0 && !mbar_wait(&bar_acc_empty, (uint32_t)((gc - 1) & 1), wlim, abort_flag)) {
+          const long long ta0 = kCount ? clock64() : 0;
+          const bool acc_free = !(first && gc > 0) || mbar_wait(&bar_acc_empty, (uint32_t)((gc - 1) & 1), wlim, abort_flag);
+          if (kCount) {
+            c_acc += clock64() - ta0;
+            c_ks++;
+          }
+          if (!acc_free) {
             *abort_flag = 1;
             tc_flag_all(cfgs, items, n_items, 4);
             stop = true;
@@ -716,7 +751,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
       const int nch = (it.nks + kChunkSteps - 1) / kChunkSteps;
       for (int ch = 0; ch < nch; ch++, gc++) {
         // the warp leaves together (tcgen05.ld is warp-collective)
+        const long long te0 = kCount ? clock64() : 0;
         const bool got = mbar_wait(&bar_acc_full, (uint32_t)(gc & 1), wlim, abort_flag);
+        const long long te1 = kCount ? clock64() : 0;
+        if (kCount) c_eacc += te1 - te0;
         if (!__all_sync(0xffffffffu, got)) {
           *abort_flag = 1;
           if (lane == 0) tc_flag_all(cfgs, items, n_items, 16);
@@ -747,6 +785,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&bar_acc_empty);
+            if (kCount) c_eread += clock64() - te1;
           }
           // |x| of level u is at most (u + 1) 2^20 per chunk (u + 1 digit pairs, 256 products of at most 64^2
           // each), twice that for u <= 6: level 0 takes one add; of the others, levels 2, 4, 8, 11, 13 convert on
@@ -768,6 +807,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
         }
       }
       if (stop) break;
+      const long long tp0 = kCount ? clock64() : 0;
       if (it.kind == 0) {
         // level groups of every output, R' = st0 2^70 + st1 2^35 + st2 (value = R' 2^-110), normalised so that
         // st1, st2 lie in [0, 2^35), and added into the tile's accumulator: integer addition, so the K ranges
@@ -832,10 +872,35 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
           }
         }
       }
+      if (kCount) c_emath += clock64() - tp0;
+    }
+  }
+  unsigned long long* rec = nullptr;
+  if (kCount) {
+    // one thread of each role writes its own fields; thread 0 the totals after the CTA's last wait
+    rec = g_tc_counters[items[0].kind == 0 ? 0 : 1][blockIdx.x % kGcCtas];
+    if (warp == 0 && lane == 0) rec[kGcProdWaitStage] = c_prod;
+    if (warp == 1 && lane == 0) {
+      rec[kGcMmaWaitOperands] = c_full;
+      rec[kGcMmaWaitAcc] = c_acc;
+      rec[kGcMmaWaitItem] = c_item;
+      rec[kGcItems] = c_items;
+      rec[kGcKsteps] = c_ks;
+      rec[kGcMmaCycles] = clock64() - T0;
+    }
+    if (warp == 2 && lane == 0) {
+      rec[kGcEpiWaitAcc] = c_eacc;
+      rec[kGcEpiRead] = c_eread;
+      rec[kGcEpiMath] = c_emath;
     }
   }
   tc_fence_before();
   __syncthreads();
+  if (kCount && threadIdx.x == 0) {
+    rec[kGcCycles] = clock64() - T0;
+    rec[kGcT0] = G0;
+    rec[kGcT1] = global_ns();
+  }
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tbase, kTmemCols);
@@ -1079,6 +1144,8 @@ __global__ void __launch_bounds__(128) k_tc_coef(const CfgDev* __restrict__ cfgs
 }
 
 // ------------------------------------------------------------------------------------------------ host side
+
+bool tc_counters_on() { return g_counters_on; }
 
 static cudaError_t tc_dev_alloc(DevBuf* b, size_t bytes, cudaStream_t st) {
   if (bytes == 0) bytes = 16;
@@ -1384,7 +1451,8 @@ cudaError_t tc_setup(Ctx* c) {
   t.on = true;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
+    cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
+    cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
     cudaFuncSetAttribute(k_tc_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPrepSmemMax);
     attr = true;
   }
@@ -1587,7 +1655,8 @@ cudaError_t tc_launch_density_gemms(const EngineView& v, cudaStream_t st, Prof* 
     if (le != cudaSuccess) return le;
     if (P.dens_n > 0) {
       prof_begin(prof, st, kKTcDens);
-      le = launch_pdl(k_tc_gemm, dim3((unsigned)std::min(P.dens_n, v.sm_count)), dim3(kGemmThreads), kGemmSmem, st,
+      le = launch_pdl(g_counters_on ? k_tc_gemm<true> : k_tc_gemm<false>, dim3((unsigned)std::min(P.dens_n, v.sm_count)),
+                      dim3(kGemmThreads), kGemmSmem, st,
                       v.cfgs, v.tc_dens + P.dens_off, P.dens_n, v.counters + 2);
       if (le != cudaSuccess) return le;
       prof_end(prof, st);
@@ -1620,7 +1689,8 @@ cudaError_t tc_launch_force(const EngineView& v, cudaStream_t st, Prof* prof) {
     if (le != cudaSuccess) return le;
     if (P.force_n > 0) {
       prof_begin(prof, st, kKTcForce);
-      le = launch_pdl(k_tc_gemm, dim3((unsigned)std::min(P.force_n, v.sm_count)), dim3(kGemmThreads), kGemmSmem, st,
+      le = launch_pdl(g_counters_on ? k_tc_gemm<true> : k_tc_gemm<false>, dim3((unsigned)std::min(P.force_n, v.sm_count)),
+                      dim3(kGemmThreads), kGemmSmem, st,
                       v.cfgs, v.tc_force + P.force_off, P.force_n, v.counters + 4);
       if (le != cudaSuccess) return le;
       prof_end(prof, st);
@@ -1634,6 +1704,44 @@ cudaError_t tc_launch_force(const EngineView& v, cudaStream_t st, Prof* prof) {
 // The limit of the tensor-core GEMM's waits on work, in clock cycles, on one device (0: the default, about one
 // second at the maximum clock).  A wait that runs out records SSH_ETIMEOUT for the evaluation; this makes that
 // path testable with a limit too short for any real wait.
+extern "C" ssh_status ssh_gemm_counters(int device, int enable) {
+  using namespace ssh;
+  int cur = 0;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e == cudaSuccess && cur != device) e = cudaSetDevice(device);
+  if (e == cudaSuccess && enable) {
+    static unsigned long long zero[2 * kGcCtas * kGcFields];
+    e = cudaMemcpyToSymbol(g_tc_counters, zero, sizeof zero);
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (cur != device) cudaSetDevice(cur);
+  if (e != cudaSuccess) {
+    ssh::set_error(std::string("ssh_gemm_counters: ") + cudaGetErrorString(e));
+    return SSH_ECUDA;
+  }
+  g_counters_on = enable != 0;
+  return SSH_OK;
+}
+
+extern "C" ssh_status ssh_gemm_counters_read(int device, uint64_t* out) {
+  using namespace ssh;
+  if (!out) {
+    ssh::set_error("ssh_gemm_counters_read: NULL output");
+    return SSH_EINVAL;
+  }
+  int cur = 0;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e == cudaSuccess && cur != device) e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbol(out, g_tc_counters, sizeof(g_tc_counters));
+  if (cur != device) cudaSetDevice(cur);
+  if (e != cudaSuccess) {
+    ssh::set_error(std::string("ssh_gemm_counters_read: ") + cudaGetErrorString(e));
+    return SSH_ECUDA;
+  }
+  return SSH_OK;
+}
+
 extern "C" ssh_status ssh_set_wait_limit(int device, int64_t cycles) {
   if (cycles < 0) {
     ssh::set_error("ssh_set_wait_limit: negative limit");

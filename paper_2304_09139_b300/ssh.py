@@ -136,6 +136,8 @@ def load():
             _sig(lib, "ssh_prof_enable", c_int, [c_vp, c_int])
             _sig(lib, "ssh_prof_read", c_int, [c_vp, c_int, P(c_d), P(c_i64)])
             _sig(lib, "ssh_set_wait_limit", c_int, [c_int, c_i64])
+            _sig(lib, "ssh_gemm_counters", c_int, [c_int, c_int])
+            _sig(lib, "ssh_gemm_counters_read", c_int, [c_int, P(ctypes.c_uint64)])
             _sig(lib, "ssh_pipe_rate", c_int, [c_int, c_int, P(c_d), P(c_d)])
             _sig(lib, "ssh_shard_words", c_int, [c_vp, P(c_i64), P(c_i64)])
             _sig(lib, "ssh_shard_density", c_int, [c_vp, c_vp])
@@ -241,6 +243,24 @@ def pipe_rate(kind: str, device: int = 0) -> tuple[float, float]:
 def set_wait_limit(cycles: int, device: int = 0):
     """ssh_set_wait_limit: the tensor-core GEMM's wait limit in clock cycles on `device` (0: the default)."""
     _check(load().ssh_set_wait_limit(device, cycles))
+
+
+GEMM_COUNTER_FIELDS = ("cycles", "producer_wait_stage", "mma_wait_operands", "mma_wait_accumulator", "mma_wait_item",
+                       "epilogue_wait_accumulator", "epilogue_readout", "epilogue_math", "items", "ksteps",
+                       "mma_thread_cycles", "t0_ns", "t1_ns")
+
+
+def gemm_counters(enable: bool, device: int = 0):
+    """ssh_gemm_counters: switch every tensor-core GEMM launch of the process to the counting instance (on) or back."""
+    _check(load().ssh_gemm_counters(device, 1 if enable else 0))
+
+
+def gemm_counters_read(device: int = 0) -> np.ndarray:
+    """ssh_gemm_counters_read: uint64 [2][256][16], [0] the last density launch, [1] the last force launch, a row per
+    CTA; the fields are GEMM_COUNTER_FIELDS."""
+    out = np.zeros((2, 256, 16), dtype=np.uint64)
+    _check(load().ssh_gemm_counters_read(device, out.ctypes.data_as(P(ctypes.c_uint64))))
+    return out
 
 
 def _rows(a, N, d):

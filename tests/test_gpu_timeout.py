@@ -77,3 +77,37 @@ def test_batch_member_reports_a_wait_that_ran_out(built):
         ssh.set_wait_limit(0)
     assert st == ETIMEOUT
     assert all(r["status"] == ETIMEOUT for r in res), res
+
+
+def test_gemm_counters_instance_gives_the_same_bits():
+    """The counting instance of the tensor-core GEMM (ssh_gemm_counters) computes the same integers as the
+    production instance, so Phi, S_max, n~ and F agree bit for bit, with the counters on and after they are off;
+    its records are consistent (every CTA that ran wrote items and K-steps, the MMA thread's waits fit inside its
+    cycles and those inside the CTA's)."""
+    from paper_2304_09139_b300 import _build, ssh, synth
+    _build.build()
+    cfg = synth.MEDIUM_D2
+    with ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi) as ctx:
+        ctx.set_positions_frac(synth.positions(cfg.seed, cfg.N, cfg.d))
+        a = ctx.energy_grad(ssh.FX)
+        Ca, Sa = ctx.ntilde()
+        ssh.gemm_counters(True)
+        try:
+            b = ctx.energy_grad(ssh.FX)
+            Cb, Sb = ctx.ntilde()
+            rec = ssh.gemm_counters_read()
+        finally:
+            ssh.gemm_counters(False)
+        c = ctx.energy_grad(ssh.FX)
+    for x in (b, c):
+        assert np.array_equal(a["phi"], x["phi"]) and np.array_equal(a["smax"], x["smax"])
+        assert np.array_equal(a["F_hi"], x["F_hi"]) and np.array_equal(a["F_lo"], x["F_lo"])
+    assert np.array_equal(Ca, Cb) and np.array_equal(Sa, Sb)
+    f = {n: i for i, n in enumerate(ssh.GEMM_COUNTER_FIELDS)}
+    for kind in (0, 1):
+        r = rec[kind][rec[kind][:, f["cycles"]] > 0].astype(np.int64)
+        assert len(r) > 0
+        assert np.all(r[:, f["ksteps"]] > 0) and np.all(r[:, f["items"]] > 0)
+        waits = r[:, f["mma_wait_operands"]] + r[:, f["mma_wait_accumulator"]] + r[:, f["mma_wait_item"]]
+        assert np.all(waits <= r[:, f["mma_thread_cycles"]]) and np.all(r[:, f["mma_thread_cycles"]] <= r[:, f["cycles"]])
+        assert np.all(r[:, f["t1_ns"]] >= r[:, f["t0_ns"]])
