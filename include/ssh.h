@@ -457,8 +457,8 @@ ssh_status ssh_set_wait_limit(int device, int64_t cycles);
 /* Cycle counters of the tensor-core GEMM, for measuring where its time goes (no counterpart in the paper; a
  * diagnostic of this library).  While enabled (for the whole process), every tensor-core GEMM launch uses a
  * second instance of the kernel that records, per CTA, clock64() cycles spent in each of its waits and phases;
- * the production instance has none of that code.  Evaluations then launch their kernels directly instead of
- * replaying captured graphs.  Enabling clears the records.  ssh_gemm_counters_read copies them out: uint64
+ * the production instance has none of that code.  Evaluations and FIRE steps then launch their kernels directly
+ * instead of replaying captured graphs, and a batch stepper rebuilt meanwhile captures none.  Enabling clears the records.  ssh_gemm_counters_read copies them out: uint64
  * out[2][256][16], [0] = the last density launch, [1] = the last force launch, one row per CTA (CTA index mod
  * 256), fields: 0 CTA cycles, 1 producer waiting for a free stage, 2 MMA thread waiting for operands, 3 MMA thread
  * waiting for the accumulator, 4 MMA thread waiting for an item, 5 epilogue waiting for the accumulator,

@@ -139,7 +139,7 @@ struct Runner {
       cudaGraphExecDestroy(graph);
       graph = nullptr;
     }
-    if (e == cudaSuccess && !act.empty() && !(prof && prof->on)) {
+    if (e == cudaSuccess && !act.empty() && !(prof && prof->on) && !tc_counters_on()) {
       cudaGraph_t g = nullptr;
       e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
       for (int s = 0; s < kGraphSteps && e == cudaSuccess; s++) e = fire_step_engine(&eng, st, nullptr);

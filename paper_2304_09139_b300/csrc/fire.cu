@@ -628,7 +628,9 @@ ssh_status fire_begin(Ctx* c, const ssh_min_params* p) {
 ssh_status fire_steps(Ctx* c, int prec, int64_t nsteps) {
   if (!c->fire || !c->fire->begun) { set_error("ssh_fire_steps: call ssh_fire_begin first"); return SSH_EINVAL; }
   cudaError_t e = cudaSuccess;
-  if (c->prof.on) {  // profiling: direct launches, so every kernel of the step carries its own events
+  // profiling, or the GEMM's counting instance: direct launches, so every kernel of the step carries its own events
+  // and a captured graph keeps no counting instance
+  if (c->prof.on || tc_counters_on()) {
     Engine* E = nullptr;
     e = fire_engine(c, prec, &E);
     for (int64_t i = 0; e == cudaSuccess && i < nsteps; i++) e = fire_step_engine(E, c->stream, &c->prof);

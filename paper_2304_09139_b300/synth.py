@@ -68,6 +68,8 @@ LARGE_D3 = Config(d=3, N=32_768, L=32.0, chi=0.40, seed=3)
 # The paper's own size (d = 2, N = 2 x 10^6, unit density) at its smallest and largest chi: M = 400000 and
 # 1600000 wavevectors.
 PAPER_D2 = Config(d=2, N=2_000_000, L=math.sqrt(2_000_000.0), chi=0.10, seed=6)
+# a tenth of the paper's N at chi = 0.10 (M = 40000): the largest quench that fits a benchmark run
+PAPER_D2_TENTH = Config(d=2, N=200_000, L=math.sqrt(200_000.0), chi=0.10, seed=61)
 PAPER_D2_CHI40 = Config(d=2, N=2_000_000, L=math.sqrt(2_000_000.0), chi=0.40, seed=7)
 
 
