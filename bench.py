@@ -141,6 +141,9 @@ def parse():
                     help="skip the FP64 -> dd and all-dd quenches of the d=2 N=100 and N=10^4 workloads (about 4 min)")
     ap.add_argument("--dd-seconds", type=float, default=300.0, help="wall limit of each dd-ladder quench")
     ap.add_argument("--no-floor", action="store_true", help="skip the quenches to the paper's 1e-50 floor")
+    ap.add_argument("--paper-full-quench", action="store_true",
+                    help="also quench the paper's d=2 N=2x10^6 chi=0.10 system (an hour or more of GPU time)")
+    ap.add_argument("--paper-full-quench-seconds", type=float, default=5400.0)
     ap.add_argument("--no-paper-quench", action="store_true", help="skip the d=2 N=2x10^5 chi=0.10 quenches (about 2 min)")
     ap.add_argument("--no-gemm-counters", action="store_true", help="skip the GEMM cycle-counter block")
     ap.add_argument("--minimize-seconds", type=float, default=150.0)
@@ -460,6 +463,50 @@ def paper_quench_block(ssh, synth, dev, stream, max_seconds=240.0):
                      "oracle_smax_400_sampled_k": float(ref["smax"][0] + ref["smax"][1]),
                      "configs_per_hour": 3600.0 / r["wall_s"] if r["status"] == 0 else 0.0}
     return out
+
+
+def paper_full_quench_block(ssh, synth, dev, stream, max_seconds=5400.0, method_name="lbfgs"):
+    """The paper's own system: d=2, N=2x10^6 at unit density, chi=0.10 (M = 400000), quenched from a uniform random
+    start toward S_max <= 1e-36 in the default fixed point on the tensor cores (about 0.87 s per evaluation), for at
+    most max_seconds.  Progress (steps, S_max, Phi, seconds) goes to stderr about once a minute and into the block;
+    the final state's S(k) is checked by the binary128 oracle on 100 sampled wavevectors (2x10^8 pairs).  Not run by
+    default: it holds the GPU for an hour or more."""
+    import oracle
+    oracle.build()
+    cfg = synth.PAPER_D2
+    c = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi, device=dev)
+    try:
+        c.set_stream(stream.cuda_stream)
+        c.set_positions_frac(synth.positions(cfg.seed, cfg.N, cfg.d))
+        p = c.min_defaults()
+        p.method = ssh.MIN_LBFGS if method_name == "lbfgs" else ssh.MIN_FIRE
+        p.max_steps = 10_000_000
+        c.fire_begin(p)
+        t0 = time.perf_counter()
+        prog, last_print = [], 0.0
+        st = c.fire_state()
+        while st["running"] and time.perf_counter() - t0 < max_seconds:
+            c.fire_steps(ssh.FX, 25)
+            st = c.fire_state()
+            el = time.perf_counter() - t0
+            prog.append([round(el, 1), st["steps"], st["smax"][0], st["phi"][0]])
+            if el - last_print > 60 or not st["running"]:
+                print(f"paper_full_quench {el:.0f} s: {st['steps']} steps, S_max {st['smax'][0]:.3e}, Phi "
+                      f"{st['phi'][0]:.3e}", file=sys.stderr, flush=True)
+                last_print = el
+        wall = time.perf_counter() - t0
+        hi, lo = c.positions_frac()
+        n = c.kset()
+        pick = np.sort(np.random.default_rng(11).choice(len(n), 100, replace=False))
+        ref = oracle.phi_grad(hi, lo, n[pick], cfg.L, want_force=False)
+        return {"workload": f"d=2 N={cfg.N} L={cfg.L:.4f} chi={cfg.chi} M={c.M}, uniform random (SplitMix64 seed "
+                            f"{cfg.seed}), {method_name}, fixed point on the tensor cores",
+                "converged": st["status"] == 0 and not st["running"], "status": st["status"], "steps": st["steps"],
+                "wall_s": wall, "smax": st["smax"][0], "phi": st["phi"][0],
+                "oracle_smax_100_sampled_k": float(ref["smax"][0] + ref["smax"][1]),
+                "progress_every_25_steps": prog[::8] + ([prog[-1]] if prog else [])}
+    finally:
+        c.close()
 
 
 def floor_block(ssh, synth, dev, stream):
@@ -1023,6 +1070,9 @@ def main():
         line["gemm_counters"] = gemm_counters_block(ssh, synth, dev, stream)
     if rank == 0 and world == 1 and not args.no_paper_quench:
         line["paper_quench"] = paper_quench_block(ssh, synth, dev, stream)
+    if rank == 0 and world == 1 and args.paper_full_quench:
+        line["paper_full_quench"] = paper_full_quench_block(ssh, synth, dev, stream,
+                                                            max_seconds=args.paper_full_quench_seconds)
     if rank == 0 and world == 1 and not args.no_floor:
         line["floor"] = floor_block(ssh, synth, dev, stream)
     if rank == 0 and world == 1 and not args.no_dd_ladder:

@@ -463,7 +463,8 @@ ssh_status ssh_set_wait_limit(int device, int64_t cycles);
  * 256), fields: 0 CTA cycles, 1 producer waiting for a free stage, 2 MMA thread waiting for operands, 3 MMA thread
  * waiting for the accumulator, 4 MMA thread waiting for an item, 5 epilogue waiting for the accumulator,
  * 6 epilogue read-out, 7 epilogue arithmetic and atomics, 8 items, 9 K-steps, 10 MMA thread cycles, 11 / 12 start
- * and end (global timer, ns).  Errors: SSH_EINVAL, SSH_ECUDA. */
+ * and end (global timer, ns).  Switch it while no other thread of the process launches evaluations (a server's
+ * worker included): the switch is a plain process-wide flag.  Errors: SSH_EINVAL, SSH_ECUDA. */
 ssh_status ssh_gemm_counters(int device, int enable);
 ssh_status ssh_gemm_counters_read(int device, uint64_t* out);
 ssh_status ssh_prof_read(ssh_ctx* ctx, int n, double* ms, int64_t* launches);
