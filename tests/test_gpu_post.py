@@ -158,3 +158,22 @@ def test_structure_factor_rejects_bad_arguments(built):
         with pytest.raises(ssh.SshError):
             ctx.structure_factor(*args)
     ctx.close()
+
+
+def test_structure_factor_over_an_explicit_wavevector_list(built, oracle_mod):
+    """ssh_structure_factor over a context built from an explicit list in no particular order (ssh_create_kset):
+    the shells follow |n|^2, not the list order, so the counts and means match the oracle's on the same list."""
+    d, N = 2, 800
+    L = N ** 0.5
+    n = oracle_mod.kset(d, N, L, K=2 * math.pi / L * 9.5)
+    n = n[np.random.default_rng(8).permutation(len(n))][: len(n) - 7]   # shuffled, a few dropped
+    s = synth.positions(35, N, d)
+    ctx = ssh.Context(d, N, L, kset=n)
+    ctx.set_positions_frac(s)
+    ctx.energy_grad(ssh.FX)
+    sf = ctx.structure_factor(6, 80, 1.0)
+    counts, mean, tau = oracle_mod.structure_factor(s, None, ctx.kset(), L, 6, 80, 1.0, nthreads=NTHREADS)
+    assert np.array_equal(sf["counts"], counts)
+    assert np.all(np.abs((sf["mean"][:, 0] - mean[:, 0]) + (sf["mean"][:, 1] - mean[:, 1])) <= 1e-26)
+    assert abs((sf["tau"][0] - tau[0]) + (sf["tau"][1] - tau[1])) <= 1e-26 * max(1.0, tau[0])
+    ctx.close()
