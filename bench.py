@@ -141,6 +141,7 @@ def parse():
                     help="skip the FP64 -> dd and all-dd quenches of the d=2 N=100 and N=10^4 workloads (about 4 min)")
     ap.add_argument("--dd-seconds", type=float, default=300.0, help="wall limit of each dd-ladder quench")
     ap.add_argument("--no-floor", action="store_true", help="skip the quenches to the paper's 1e-50 floor")
+    ap.add_argument("--no-d4", action="store_true", help="skip the d=4 block (integer-pipe fixed point)")
     ap.add_argument("--paper-full-quench", action="store_true",
                     help="also quench the paper's d=2 N=2x10^6 chi=0.10 system (an hour or more of GPU time)")
     ap.add_argument("--paper-full-quench-seconds", type=float, default=5400.0)
@@ -509,6 +510,43 @@ def paper_full_quench_block(ssh, synth, dev, stream, max_seconds=5400.0, method_
         c.close()
 
 
+def d4_block(ssh, synth, dev, stream, pipes):
+    """d = 4 (the paper covers d = 1-4) on the integer-pipe fixed point, the path d = 4 takes: N = 4096 points at unit
+    density, chi = 0.30 (M = 4914): per-kernel times of one evaluation against the measured IMAD rate, and quenches
+    to S_max <= 1e-36 with the default ladder (FP64, then fixed point) and with L-BFGS."""
+    N, d, chi, seed = 4096, 4, 0.30, 44
+    L = N ** (1 / d)
+    c = ssh.Context(d, N, L, chi=chi, device=dev)
+    c.set_stream(stream.cuda_stream)
+    c.set_positions_frac(synth.positions(seed, N, d))
+    pairs = c.M * c.N
+    for _ in range(3):
+        c.eval(ssh.FX)
+    c.sync()
+    c.prof_enable(True)
+    for _ in range(5):
+        c.eval(ssh.FX)
+    pr = c.prof_read()
+    c.prof_enable(False)
+    c.close()
+    ms = {k: v[0] / v[1] for k, v in pr.items()}
+    out = {"workload": f"d=4 N={N} L={L:.4f} chi={chi} M={pairs // N}, uniform random (SplitMix64 seed {seed})",
+           "fx_impl": "integer", "eval_ms": sum(ms.values()), "per_kernel_ms": ms,
+           "eval_pairs_per_s": pairs / (sum(ms.values()) * 1e-3),
+           "imad_frac_of_measured": {k: FX_IMAD_PER_PAIR[k] * pairs / (ms[k] * 1e-3) / pipes["imad"]["ops_per_s"]
+                                     for k in FX_IMAD_PER_PAIR if k in ms}}
+    for name, method in (("default", ssh.MIN_FIRE), ("lbfgs", ssh.MIN_LBFGS)):
+        c = ssh.Context(d, N, L, chi=chi, device=dev)
+        c.set_stream(stream.cuda_stream)
+        c.set_positions_frac(synth.positions(seed, N, d))
+        r = c.minimize(max_steps=200000, max_seconds=120.0, method=method)
+        c.close()
+        out[name] = {"converged": r["status"] == 0, "steps": r["steps"], "wall_s": r["wall_s"], "smax": r["smax"][0],
+                     "stage_steps": r["stage_steps"][:r["stages_used"]],
+                     "configs_per_hour": 3600.0 / r["wall_s"] if r["status"] == 0 else 0.0}
+    return out
+
+
 def floor_block(ssh, synth, dev, stream):
     """The paper's accuracy floor (S_max ~ 1e-51 at the end of its quenches): the default fixed-point ladder quenched
     with FIRE and with L-BFGS to S_max <= 1e-50 from the random starts of the d=2 N=100 (chi=0.30) and N=10^4
@@ -601,6 +639,31 @@ def batched_block(ssh, synth, dev, steps=5, warmup=2, count=256):
                         "fixed point, one batched FIRE step (graph replay)"}
 
 
+def serving_summary(done, tickets, sub_t, sub_work, elapsed, window_s):
+    """Latency and load figures of a serving run.  done: ticket -> result (status, steps, t_submit, t_done);
+    tickets: every submitted ticket in order, sub_t its submission time and sub_work its M N (same order) in the run's
+    clock; elapsed: the run's length.  p50 / p99 cover every submitted request, the unfinished ones censored at the
+    end of the run (a lower bound on their latency); the _completed figures cover the finished ones only."""
+    ok = [r for r in done.values() if r["status"] == 0]
+    lat = sorted(r["t_done"] - r["t_submit"] for r in ok)
+    pct = (lambda v, q: float(np.percentile(v, q)) if len(v) else None)
+    cens = sorted([r["t_done"] - r["t_submit"] for r in done.values()] +
+                  [elapsed - sub_t[t] for t in tickets if t not in done])
+    n_sub = len(tickets)
+    work = {t: w for t, w in zip(tickets, sub_work)}
+    return {"submitted": n_sub, "completed": len(done), "converged": len(ok),
+            "completion_fraction": len(done) / n_sub if n_sub else None,
+            "p50_s": pct(cens, 50), "p99_s": pct(cens, 99), "latency": "every submitted request, unfinished ones "
+            "censored at the end of the run (a lower bound)",
+            "p50_completed_s": pct(lat, 50), "p99_completed_s": pct(lat, 99),
+            "configs_per_hour": len(ok) / elapsed * 3600.0, "elapsed_s": elapsed,
+            "offered_requests_per_s": n_sub / window_s, "sustained_requests_per_s": len(done) / elapsed,
+            "offered_pairs_per_s": sum(sub_work) / window_s, "offered_pairs": "sum of M N over the submitted requests "
+            "per second of arrivals (one evaluation of each)",
+            "sustained_pairs_per_s": sum(work[t] * r["steps"] for t, r in done.items()) / elapsed,
+            "sustained_pairs": "sum of M N x steps of the finished requests per second of the run"}
+
+
 def serving_block(ssh, synth, dev, window_s=45.0, drain_s=30.0, count=2000, mean_gap=0.020, method="lbfgs"):
     # The offered load (about 50 requests/s of up to 1.3e9 pairs per step each) exceeds one GPU by far; the
     # server admits the smallest requests first under a cap on pairs per batched step, so the figures below
@@ -643,30 +706,11 @@ def serving_block(ssh, synth, dev, window_s=45.0, drain_s=30.0, count=2000, mean
     elapsed = time.perf_counter() - t0
     st = sv.stats()
     sv.close()
-    ok = [r for r in done.values() if r["status"] == 0]
-    lat = sorted(r["t_done"] - r["t_submit"] for r in ok)
-    pct = (lambda v, q: float(np.percentile(v, q)) if len(v) else None)
-    # every submitted request, the unfinished ones censored at the end of the run (a lower bound on their latency)
-    cens = sorted([r["t_done"] - r["t_submit"] for r in done.values()] +
-                  [elapsed - sub_t[t] for t in tickets if t not in done])
-    n_sub = len(tickets)
-    work = {t: w for t, w in zip(tickets, sub_work)}
-    offered = sum(sub_work) / window_s
-    sustained = sum(work[t] * r["steps"] for t, r in done.items()) / elapsed
-    return {"submitted": n_sub, "completed": len(done), "converged": len(ok), "still_running": st["running"],
-            "still_queued": st["queued"], "completion_fraction": len(done) / n_sub if n_sub else None,
-            "p50_s": pct(cens, 50), "p99_s": pct(cens, 99), "latency": "every submitted request, unfinished ones "
-            "censored at the end of the run (a lower bound)",
-            "p50_completed_s": pct(lat, 50), "p99_completed_s": pct(lat, 99),
-            "configs_per_hour": len(ok) / elapsed * 3600.0, "elapsed_s": elapsed,
-            "offered_requests_per_s": n_sub / window_s, "sustained_requests_per_s": len(done) / elapsed,
-            "offered_pairs_per_s": offered, "offered_pairs": "sum of M N over the submitted requests per second of "
-            "arrivals (one evaluation of each)",
-            "sustained_pairs_per_s": sustained, "sustained_pairs": "sum of M N x steps of the finished requests per "
-            "second of the run",
-            "minimiser": method,
-            "workload": f"Poisson arrivals mean {1 / mean_gap:.0f}/s for {window_s:.0f} s (+{drain_s:.0f} s drain), "
-                        "d in {1,2,3}, N log-uniform [64, 32768], chi U[0.10, 0.49]"}
+    out = serving_summary(done, tickets, sub_t, sub_work, elapsed, window_s)
+    out.update({"still_running": st["running"], "still_queued": st["queued"], "minimiser": method,
+                "workload": f"Poisson arrivals mean {1 / mean_gap:.0f}/s for {window_s:.0f} s (+{drain_s:.0f} s drain), "
+                            "d in {1,2,3}, N log-uniform [64, 32768], chi U[0.10, 0.49]"})
+    return out
 
 
 def run_reference(args):
@@ -1073,6 +1117,8 @@ def main():
     if rank == 0 and world == 1 and args.paper_full_quench:
         line["paper_full_quench"] = paper_full_quench_block(ssh, synth, dev, stream,
                                                             max_seconds=args.paper_full_quench_seconds)
+    if rank == 0 and world == 1 and not args.no_d4:
+        line["d4"] = d4_block(ssh, synth, dev, stream, pipes)
     if rank == 0 and world == 1 and not args.no_floor:
         line["floor"] = floor_block(ssh, synth, dev, stream)
     if rank == 0 and world == 1 and not args.no_dd_ladder:

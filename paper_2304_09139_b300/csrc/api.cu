@@ -363,10 +363,19 @@ static ssh_status stage_and_upload(ssh_ctx* h, const double* s_hi, const double*
   // the previous upload from the staging buffer must have landed before it is rewritten
   SSH_CUDA(cudaEventSynchronize(h->stage_done), "upload positions");
   if (!physical && frac_all_plain(s_hi, s_lo, (int64_t)d * N)) {
-    // every value is its own fraction: the staging is a transposed copy with zero low words
-    for (int64_t j = 0; j < N; j++)
-      for (int a = 0; a < d; a++) hs[a * N + j] = s_hi[j * d + a];
-    memset(ls, 0, sizeof(double) * d * N);
+    // every value is its own fraction: the staging is a transposed copy, and the low words are zeroed on the
+    // device instead of being copied
+    for (int a = 0; a < d; a++) {
+      double* o = hs + (size_t)a * N;
+      const double* in = s_hi + a;
+      for (int64_t j = 0; j < N; j++) o[j] = in[j * d];
+    }
+    SSH_CUDA(cudaMemcpyAsync(c.s_hi.p, hs, sizeof(double) * d * N, cudaMemcpyHostToDevice, c.stream), "upload positions");
+    SSH_CUDA(cudaMemsetAsync(c.s_lo.p, 0, sizeof(double) * d * N, c.stream), "upload positions");
+    SSH_CUDA(cudaEventRecord(h->stage_done, c.stream), "upload positions");
+    c.have_positions = true;
+    c.have_result = false;
+    return SSH_OK;
   } else {
     dd Ld = dd_make(c.L);
     for (int64_t j = 0; j < N; j++) {

@@ -59,3 +59,24 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
         steps, warmup = 2, 1
     assert bench.run_reference(A()) == 0
     assert not called
+
+
+def test_serving_summary_censors_unfinished_requests():
+    """The serving figures: p50 / p99 over every submitted request, an unfinished one counted at the end of the run
+    (its latency is at least that), the completed-only figures beside them, and the offered and sustained load."""
+    import bench
+    done = {1: {"status": 0, "steps": 10, "t_submit": 0.0, "t_done": 1.0},
+            2: {"status": 0, "steps": 20, "t_submit": 1.0, "t_done": 4.0},
+            3: {"status": 5, "steps": 5, "t_submit": 2.0, "t_done": 2.5}}
+    tickets = [1, 2, 3, 4, 5]
+    sub_t = {1: 0.0, 2: 1.0, 3: 2.0, 4: 3.0, 5: 9.0}
+    sub_work = [100, 200, 300, 400, 500]
+    out = bench.serving_summary(done, tickets, sub_t, sub_work, elapsed=10.0, window_s=5.0)
+    # latencies 1, 3, 0.5 (finished) and 10 - 3 = 7, 10 - 9 = 1 (censored)
+    assert out["submitted"] == 5 and out["completed"] == 3 and out["converged"] == 2
+    assert out["p50_s"] == 1.0 and abs(out["p99_s"] - (3 + 0.96 * 4)) < 1e-12
+    assert out["p50_completed_s"] == 2.0            # the converged ones: 1 and 3
+    assert out["completion_fraction"] == 0.6
+    assert out["offered_pairs_per_s"] == 1500 / 5.0
+    assert out["sustained_pairs_per_s"] == (100 * 10 + 200 * 20 + 300 * 5) / 10.0
+    assert out["configs_per_hour"] == 2 / 10.0 * 3600.0
