@@ -713,11 +713,23 @@ def serving_block(ssh, synth, dev, window_s=45.0, drain_s=30.0, count=2000, mean
     return out
 
 
+def arm_config(w, M, world):
+    """The config of both arms' lines (the same dict, so that the two lines describe one workload): the workload and
+    its sizes, the L2 policy of the GPU arm's timed steps, the parallelism."""
+    return {"workload": f"d={w['d']} N={w['N']} L={w['L']} chi={w['chi']} M={M}, uniform random (SplitMix64 seed "
+                        f"{w['seed']}+rank)",
+            "l2": "flushed between timed steps (256 MiB write, outside the step events)",
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
     rank, world, local = dist_info()
     if rank != 0:
         return 0
     w = WORKLOADS[args.workload]
+    import oracle
+    oracle.build()
+    M_full = oracle.chi_to_m(w["d"], w["N"], w["chi"])
     times, pairs = [], None
     for i in range(args.warmup + args.steps):
         rate, Ms, cores = cpu_sample(w["N"], w["d"], w["L"], w["chi"], w["seed"])
@@ -731,7 +743,8 @@ def run_reference(args):
             "unit": "pairs/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": tot / len(times) * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "binary128", "data": "synthetic",
-            "config": {"workload": f"d=2 N={w['N']} L={w['L']} chi={w['chi']} uniform random seed {w['seed']}"},
+            "config": arm_config(w, M_full, world),
+            "step": "one binary128 oracle Phi + force over the sample on the host cores",
             "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -1073,11 +1086,8 @@ def main():
                        "fp64": "f64"}[args.prec]),
             "fx_impl": ("tensor" if tensor else "integer") if prec == ssh.FX else None,
             "data": "synthetic",
-            "config": {"workload": f"d={w['d']} N={w['N']} L={w['L']} chi={w['chi']} M={ctx.M}, uniform random "
-                                   f"(SplitMix64 seed {w['seed']}+rank), one device FIRE step (Phi + force + "
-                                   f"update + acceptance) per step",
-                       "l2": "flushed between timed steps (256 MiB write, outside the step events)",
-                       "parallelism": f"replicas x{world}"},
+            "config": arm_config(w, ctx.M, world),
+            "step": "one device FIRE step: Phi + force + update + acceptance",
             "roofline": roof, "gpu_launches": launches, "wall_s": t_wall,
             "e2e": {"value": pairs * world / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": clk.summary(), "variants_pairs_per_s": variants, "pipe_rates": pipes}

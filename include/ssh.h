@@ -147,7 +147,8 @@ ssh_status ssh_structure_factor(ssh_ctx* ctx, int nbins, int64_t n2max, double K
  * when the context uses the integer pipes.  Either pointer may be NULL. */
 ssh_status ssh_get_tc_chunks(const ssh_ctx* ctx, int* nchunk, int64_t* chunk);
 
-/* The tensor-core path's density tile plan: row tiles (128 rows (p, cos / sin)), column tiles (32 columns), density
+/* The tensor-core path's density tile plan (a diagnostic of this library; no counterpart in the paper): row tiles
+ * (128 rows (p, cos / sin)), column tiles (32 columns), density
  * tiles in use, and whether the last row tile's wavevectors run as one transposed tile (two-axis sets whose last
  * row tile holds at most 16 canonical p: rows (n1, cos / sin), columns (p, cos / sin); column tiles then counts its
  * B operand).  All 0 on the integer pipes.  Any pointer may be NULL. */
