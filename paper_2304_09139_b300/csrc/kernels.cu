@@ -535,7 +535,8 @@ __global__ void __launch_bounds__(kForceThreads) k_force(const CfgDev* __restric
 // i.e. +-X s +- Y c with (X, Y) = (C, S) for even q and (S, C) for odd q: two unsigned products of the
 // sign-magnitude coefficients.  Negations are one's complements whose missing units are counted (cntA for
 // A = sum w, cntB for B = sum A) and added exactly at the end of the column.
-__global__ void __launch_bounds__(kForceThreads) k_force_fx(const CfgDev* __restrict__ cfgs, const FItem* __restrict__ items,
+// at most 96 registers, so that five CTAs fit an SM (the persistent launch runs five per SM)
+__global__ void __launch_bounds__(kForceThreads, 5) k_force_fx(const CfgDev* __restrict__ cfgs, const FItem* __restrict__ items,
                                                             int n_items, int* __restrict__ queue) {
   __shared__ int s_item;
   for (;;) {

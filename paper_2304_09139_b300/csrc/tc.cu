@@ -42,6 +42,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
@@ -77,8 +78,9 @@ __device__ long long g_tc_wait_limit = kWaitLimit;
 // force), written by the counting instance of k_tc_gemm only.  The production instance has none of this code.
 constexpr int kGcCtas = 256, kGcFields = 16;
 __device__ unsigned long long g_tc_counters[2][kGcCtas][kGcFields];
-// on for this process between ssh_gemm_counters(.., 1) and (.., 0): GEMM launches use the counting instance
-bool g_counters_on = false;
+// on for this process between ssh_gemm_counters(.., 1) and (.., 0): GEMM launches use the counting instance (an
+// atomic, since a server's worker thread may launch while another thread switches it)
+std::atomic<bool> g_counters_on{false};
 enum { kGcCycles = 0, kGcProdWaitStage, kGcMmaWaitOperands, kGcMmaWaitAcc, kGcMmaWaitItem, kGcEpiWaitAcc,
        kGcEpiRead, kGcEpiMath, kGcItems, kGcKsteps, kGcMmaCycles, kGcT0, kGcT1 };
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -325,9 +327,8 @@ __device__ __forceinline__ void put_digit_rows(uint8_t* base, size_t slice_strid
 
 // The product z b of two first-quadrant phasors -> (re, im) as round(x 2^104) + balanced-digit offset, and as
 // signed Q2.126.  The three products of qmul give (re, im), im >= 0 (clamped at 0 as there); the product is
-// i^(q1 + q2) (re + i im), turned without renormalising to the first quadrant, and each component is rounded to
-// 2^-104 on its magnitude with the sign applied after: the same bits as rounding the renormalised non-negative
-// pair (qmul) and then turning it.
+// i^(q1 + q2) (re + i im), turned without renormalising to the first quadrant, and each signed component is
+// rounded to the nearest multiple of 2^-104 (ties upward; error at most 2^-105).
 __device__ __forceinline__ void qmul_out(const qent& z, const qent& b, uint4& yre, uint4& yim, fxc* q126) {
   const q128 p1 = umulhi(z.c, b.c), p2 = umulhi(z.s, b.s), p3 = umulhi(z.cs, b.cs);
   const q128 re = q128_sub(p1, p2);
@@ -342,11 +343,8 @@ __device__ __forceinline__ void qmul_out(const qent& z, const qent& b, uint4& yr
     case 2: xr = -R; xi = -I; break;
     default: xr = I; xi = -R; break;
   }
-  const auto rnd = [](__int128 x) -> __int128 {
-    const unsigned __int128 m = (unsigned __int128)(x < 0 ? -x : x);
-    const __int128 r = (__int128)((m + ((unsigned __int128)1 << 21)) >> 22);
-    return x < 0 ? -r : r;
-  };
+  // to the nearest multiple of 2^-104 (ties upward): an add and an arithmetic shift
+  const auto rnd = [](__int128 x) -> __int128 { return (x + ((__int128)1 << 21)) >> 22; };
   const __int128 bias = digit_bias();
   const unsigned __int128 ur = (unsigned __int128)(rnd(xr) + bias), ui = (unsigned __int128)(rnd(xi) + bias);
   yre = make_uint4((uint32_t)ur, (uint32_t)(ur >> 32), (uint32_t)(ur >> 64), (uint32_t)(ur >> 96));
@@ -938,8 +936,10 @@ __global__ void __launch_bounds__(kFinThreads) k_tc_dens_finish(const CfgDev* __
   long long P[4][3];  // [2 x + y]: x the cos / sin of w (row), y of a (column)
   long long* acc = nullptr;
   if (idx < (int64_t)W1 * c.tc_nP) {
-    const int n1 = (int)(idx % W1), p = (int)(idx / W1);
-    const int kp = c.tc_em[idx * 2 + 0], km = c.tc_em[idx * 2 + 1];  // em is [p][n1][2]
+    // p fastest: a warp's lanes read consecutive accumulator rows (p, cos / sin), contiguous in memory
+    const int p = (int)(idx % c.tc_nP), n1 = (int)(idx / c.tc_nP);
+    const int64_t ei = (int64_t)p * W1 + n1;  // em is [p][n1][2]
+    const int kp = c.tc_em[ei * 2 + 0], km = c.tc_em[ei * 2 + 1];
     k = neg ? km : kp;
     const int r = 2 * p, col = 2 * n1;
     // the transposed remainder tile holds P_xy(p, n1) at row trRow0 + 2 n1 + y, column 2 (p - trP0) + x
