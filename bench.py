@@ -100,12 +100,14 @@ WORKLOAD = WORKLOADS["d2-n10000"]
 
 # DRAM bytes (read + write) per launch from one ncu capture of this workload (profiles/), valid only while
 # the kernel's family of sources hashes to the value recorded with them; otherwise the traffic is reported as null.
-NCU_TRAFFIC = {("d2-n10000", "fx", "force"): ("2d22c6704b91", 35_869_696 + 1_536),
-               ("d2-n10000", "fx", "ntilde"): ("2d22c6704b91", 36_569_600 + 13_568),
-               ("d2-n10000", "fx-tensor", "tc_force"): ("b284e7325135", 74_685_696 + 2_521_856),
-               ("d2-n10000", "fx-tensor", "tc_dens"): ("b284e7325135", 135_649_024 + 5_326_080),
-               ("d3-n32768", "fx-tensor", "tc_force"): ("b284e7325135", 3_585_672_000 + 26_525_000),
-               ("d3-n32768", "fx-tensor", "tc_dens"): ("b284e7325135", 3_008_942_000 + 8_470_000)}
+NCU_TRAFFIC = {("d2-n10000", "fx", "force"): ("8c0684b40cfa", 35_871_488 + 24_064),
+               ("d2-n10000", "fx", "ntilde"): ("8c0684b40cfa", 36_564_736 + 7_424),
+               ("d2-n10000", "dd", "force"): ("8c0684b40cfa", 35_895_296 + 0),
+               ("d2-n10000", "dd", "ntilde"): ("8c0684b40cfa", 36_669_184 + 512),
+               ("d2-n10000", "fx-tensor", "tc_force"): ("89d979ba956d", 74_689_792 + 2_654_976),
+               ("d2-n10000", "fx-tensor", "tc_dens"): ("89d979ba956d", 135_645_184 + 5_039_104),
+               ("d3-n32768", "fx-tensor", "tc_force"): ("89d979ba956d", 3_589_898_000 + 26_543_000),
+               ("d3-n32768", "fx-tensor", "tc_dens"): ("89d979ba956d", 3_008_847_000 + 8_463_000)}
 
 
 # The sources each family of kernels is built from: the integer fixed-point and dd kernels, and the tensor-core
