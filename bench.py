@@ -95,7 +95,8 @@ BF16_PEAK = _measured_bf16_peak()
 
 # The headline workload (the default) and the d = 3 one, selectable with --workload.
 WORKLOADS = {"d2-n10000": dict(d=2, N=10_000, L=100.0, chi=0.45, seed=2),
-             "d3-n32768": dict(d=3, N=32_768, L=32.0, chi=0.40, seed=3)}
+             "d3-n32768": dict(d=3, N=32_768, L=32.0, chi=0.40, seed=3),
+             "d4-n4096": dict(d=4, N=4096, L=8.0, chi=0.30, seed=44)}
 WORKLOAD = WORKLOADS["d2-n10000"]
 
 # DRAM bytes (read + write) per launch from one ncu capture of this workload (profiles/), valid only while
@@ -132,9 +133,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--prec", default="fx", choices=["fx", "dd", "fp64"])
     ap.add_argument("--workload", default="d2-n10000", choices=sorted(WORKLOADS),
-                    help="the timed configuration: d=2 N=10^4 chi=0.45 (default) or d=3 N=32768 chi=0.40")
+                    help="the timed configuration: d=2 N=10^4 chi=0.45 (default), d=3 N=32768 chi=0.40 or d=4 N=4096 chi=0.30")
     ap.add_argument("--fx-impl", default="auto", choices=["auto", "integer", "tensor"],
-                    help="fixed-point implementation: integer pipes or exact-digit tensor-core GEMMs (d <= 3)")
+                    help="fixed-point implementation: integer pipes or exact-digit tensor-core GEMMs")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
@@ -143,7 +144,7 @@ def parse():
                     help="skip the FP64 -> dd and all-dd quenches of the d=2 N=100 and N=10^4 workloads (about 4 min)")
     ap.add_argument("--dd-seconds", type=float, default=300.0, help="wall limit of each dd-ladder quench")
     ap.add_argument("--no-floor", action="store_true", help="skip the quenches to the paper's 1e-50 floor")
-    ap.add_argument("--no-d4", action="store_true", help="skip the d=4 block (integer-pipe fixed point)")
+    ap.add_argument("--no-d4", action="store_true", help="skip the d=4 block")
     ap.add_argument("--paper-full-quench", action="store_true",
                     help="also quench the paper's d=2 N=2x10^6 chi=0.10 system (an hour or more of GPU time)")
     ap.add_argument("--paper-full-quench-seconds", type=float, default=5400.0)
@@ -513,30 +514,38 @@ def paper_full_quench_block(ssh, synth, dev, stream, max_seconds=5400.0, method_
 
 
 def d4_block(ssh, synth, dev, stream, pipes):
-    """d = 4 (the paper covers d = 1-4) on the integer-pipe fixed point, the path d = 4 takes: N = 4096 points at unit
-    density, chi = 0.30 (M = 4914): per-kernel times of one evaluation against the measured IMAD rate, and quenches
-    to S_max <= 1e-36 with the default ladder (FP64, then fixed point) and with L-BFGS."""
+    """d = 4 (the paper covers d = 1-4): N = 4096 points at unit density, chi = 0.30 (M = 4914).  Per-kernel times
+    of one fixed-point evaluation on the tensor cores (the default path; GEMM work against the measured bf16 rate)
+    and on the integer pipes (against the measured IMAD rate), and quenches to S_max <= 1e-36 with the default
+    ladder (FP64, then fixed point) and with L-BFGS."""
     N, d, chi, seed = 4096, 4, 0.30, 44
     L = N ** (1 / d)
-    c = ssh.Context(d, N, L, chi=chi, device=dev)
-    c.set_stream(stream.cuda_stream)
-    c.set_positions_frac(synth.positions(seed, N, d))
-    pairs = c.M * c.N
-    for _ in range(3):
-        c.eval(ssh.FX)
-    c.sync()
-    c.prof_enable(True)
-    for _ in range(5):
-        c.eval(ssh.FX)
-    pr = c.prof_read()
-    c.prof_enable(False)
-    c.close()
-    ms = {k: v[0] / v[1] for k, v in pr.items()}
-    out = {"workload": f"d=4 N={N} L={L:.4f} chi={chi} M={pairs // N}, uniform random (SplitMix64 seed {seed})",
-           "fx_impl": "integer", "eval_ms": sum(ms.values()), "per_kernel_ms": ms,
-           "eval_pairs_per_s": pairs / (sum(ms.values()) * 1e-3),
-           "imad_frac_of_measured": {k: FX_IMAD_PER_PAIR[k] * pairs / (ms[k] * 1e-3) / pipes["imad"]["ops_per_s"]
-                                     for k in FX_IMAD_PER_PAIR if k in ms}}
+    out = {"workload": f"d=4 N={N} L={L:.4f} chi={chi}, uniform random (SplitMix64 seed {seed})"}
+    for tag, impl in (("tensor", ssh.FX_TENSOR), ("integer", ssh.FX_INTEGER)):
+        c = ssh.Context(d, N, L, chi=chi, device=dev, fx_impl=impl)
+        c.set_stream(stream.cuda_stream)
+        c.set_positions_frac(synth.positions(seed, N, d))
+        pairs = c.M * c.N
+        used = c.fx_impl
+        for _ in range(3):
+            c.eval(ssh.FX)
+        c.sync()
+        c.prof_enable(True)
+        for _ in range(5):
+            c.eval(ssh.FX)
+        pr = c.prof_read()
+        c.prof_enable(False)
+        c.close()
+        ms = {k: v[0] / v[1] for k, v in pr.items()}
+        r = {"M": pairs // N, "fx_impl": "tensor" if used == ssh.FX_TENSOR else "integer", "eval_ms": sum(ms.values()),
+             "per_kernel_ms": ms, "eval_pairs_per_s": pairs / (sum(ms.values()) * 1e-3)}
+        if used == ssh.FX_TENSOR:
+            r["bf16_frac_of_measured"] = {k: f * pairs / (ms[k] * 1e-3) / BF16_PEAK
+                                          for k, f in tc_flop_per_pair(d).items() if k in ms}
+        else:
+            r["imad_frac_of_measured"] = {k: FX_IMAD_PER_PAIR[k] * pairs / (ms[k] * 1e-3) / pipes["imad"]["ops_per_s"]
+                                          for k in FX_IMAD_PER_PAIR if k in ms}
+        out[tag] = r
     for name, method in (("default", ssh.MIN_FIRE), ("lbfgs", ssh.MIN_LBFGS)):
         c = ssh.Context(d, N, L, chi=chi, device=dev)
         c.set_stream(stream.cuda_stream)

@@ -53,14 +53,17 @@ typedef enum {
 typedef enum { SSH_FP64 = 0, SSH_DD = 1, SSH_FX = 2 } ssh_prec;
 
 /* Implementation of SSH_FX evaluations (same arithmetic class, results agree to the 1e-28 normwise bound):
- *   SSH_FX_AUTO    -- the library's choice: the tensor cores for d <= 3, the integer pipes otherwise
+ *   SSH_FX_AUTO    -- the library's choice: the tensor cores where the set is within their limits, else the
+ *                     integer pipes
  *   SSH_FX_INTEGER -- 128-bit fixed point on the integer pipes, any d
- *   SSH_FX_TENSOR  -- d <= 3 (else SSH_EINVAL): both sums as exact-digit GEMMs on the tensor cores (15
- *                     balanced 7-bit digits per 2^-104 fixed-point value in bf16, fp32 accumulation kept exact by
- *                     bounded read-outs; d = 1 runs on two lifted axes, n = 2^b n_1 + n_2).  A wavevector set
- *                     beyond the path's limits (d = 3 with max |n_2| + max |n_3| above 211, or more than 16384
- *                     distinct (n_2, n_3)), or N above 2^22, runs on the integer pipes; ssh_get_fx_impl reports
- *                     which implementation a context uses. */
+ *   SSH_FX_TENSOR  -- both sums as exact-digit GEMMs on the tensor cores (15 balanced 7-bit digits per 2^-104
+ *                     fixed-point value in bf16, fp32 accumulation kept exact by bounded read-outs; d = 1 runs on
+ *                     two lifted axes, n = 2^b n_1 + n_2).  A wavevector set beyond the path's limits (d = 3 with
+ *                     max |n_2| + max |n_3| above 211; d = 4 with some |n_a| above 64, a >= 2, or with
+ *                     768 (max |n_2| + max |n_3| + max |n_4| + 3) + 4 P above 200 KiB, P the number of
+ *                     distinct canonical (n_2, n_3, n_4); more than 16384 distinct (n_2, .., n_d)), or
+ *                     N above 2^22, runs on the integer pipes; ssh_get_fx_impl reports which implementation a
+ *                     context uses. */
 enum { SSH_FX_AUTO = 0, SSH_FX_INTEGER = 1, SSH_FX_TENSOR = 2 };
 #define SSH_FX_AUTO_TENSOR 1
 
@@ -370,8 +373,7 @@ typedef struct {
                                   (default 2^28, about 10 ms per step); bounds the step time that every
                                   running request shares; a larger request runs only in an empty batch */
   int policy;                  /* 0: smallest M N first (default), 1: first come first served */
-  int fx_impl;                 /* fixed-point implementation of the members (ssh_opts.fx_impl; SSH_FX_TENSOR
-                                  applies to the d <= 3 requests, the others use the integer pipes) */
+  int fx_impl;                 /* fixed-point implementation of the members (ssh_opts.fx_impl) */
 } ssh_server_opts;
 typedef struct {
   int d;

@@ -93,12 +93,7 @@ static ssh_status create_from(int d, int64_t N, double L, ssh::KSet&& ks, const 
   c.device = opts ? opts->device : 0;
   const int fx_impl = opts ? opts->fx_impl : SSH_FX_AUTO;
   if (fx_impl < SSH_FX_AUTO || fx_impl > SSH_FX_TENSOR) { delete h; set_error("ssh_create: bad fx_impl"); return SSH_EINVAL; }
-  if (fx_impl == SSH_FX_TENSOR && d > 3) {
-    delete h;
-    set_error("ssh_create: the tensor-core fixed-point path needs d <= 3");
-    return SSH_EINVAL;
-  }
-  c.tc_requested = fx_impl == SSH_FX_TENSOR || (fx_impl == SSH_FX_AUTO && d <= 3 && SSH_FX_AUTO_TENSOR);
+  c.tc_requested = fx_impl == SSH_FX_TENSOR || (fx_impl == SSH_FX_AUTO && SSH_FX_AUTO_TENSOR);
   c.tc_chunk_req = opts ? opts->tc_chunk : 0;
   if (c.tc_chunk_req < 0) { delete h; set_error("ssh_create: tc_chunk must be >= 0"); return SSH_EINVAL; }
   const int64_t sp0 = opts ? opts->shard_first : 0, spn = opts ? opts->shard_count : 0;
@@ -141,7 +136,7 @@ static ssh_status create_from(int d, int64_t N, double L, ssh::KSet&& ks, const 
   }
   if (c.shard_n > 0 && !c.tc.on) {
     ssh_destroy(h);
-    set_error("ssh_create: a particle shard needs the tensor-core fixed-point path (d <= 3, a set within its limits)");
+    set_error("ssh_create: a particle shard needs the tensor-core fixed-point path (a set within its limits)");
     return SSH_EINVAL;
   }
   *out = h;

@@ -245,7 +245,7 @@ using ssh::set_error;
 
 struct ssh_batch {
   int device = 0;
-  int fx_impl = 0;  // members' ssh_opts.fx_impl (SSH_FX_TENSOR applies to d <= 3 members)
+  int fx_impl = 0;  // members' ssh_opts.fx_impl
   cudaStream_t stream = nullptr;
   std::vector<ssh_ctx*> members;
   std::vector<ssh_min_result> results;
@@ -291,7 +291,7 @@ ssh_status ssh_batch_add(ssh_batch* b, int d, int64_t N, double L, double chi, d
   ssh_opts o;
   memset(&o, 0, sizeof o);
   o.device = b->device;
-  o.fx_impl = (b->fx_impl == SSH_FX_TENSOR && d > 3) ? SSH_FX_INTEGER : b->fx_impl;
+  o.fx_impl = b->fx_impl;
   ssh_ctx* h = nullptr;
   ssh_status s = ssh_create(d, N, L, chi, K, &o, &h);
   if (s != SSH_OK) return s;
@@ -663,7 +663,7 @@ static void server_loop(ssh_server* sv) {
       ssh_opts o;
       memset(&o, 0, sizeof o);
       o.device = sv->o.device;
-      o.fx_impl = (sv->o.fx_impl == SSH_FX_TENSOR && q.d > 3) ? SSH_FX_INTEGER : sv->o.fx_impl;
+      o.fx_impl = sv->o.fx_impl;
       ssh_status s = ssh_create(q.d, q.N, q.L, q.chi, q.K, &o, &m.h);
       if (s == SSH_OK) s = ssh_set_stream(m.h, st);
       if (s == SSH_OK) s = ssh_set_positions_frac(m.h, q.s_hi.data(), q.s_lo.empty() ? nullptr : q.s_lo.data());

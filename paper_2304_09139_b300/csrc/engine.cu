@@ -196,11 +196,18 @@ cudaError_t engine_build(Engine* e, const std::vector<Ctx*>& members, const std:
     P.prep_off = (int)tcp.size();
     P.dens_off = (int)tcd.size();
     P.force_off = (int)tcf.size();
+    // preparation items of the four-axis members last (they run on their own instance of the kernel)
+    for (int four = 0; four < 2; four++)
+      for (int i : tcl)
+        if (tc_chunks(members[i]) > ph && (members[i]->tc.d == 4) == (four == 1)) {
+          const size_t before = tcp.size();
+          tc_prep_items(members[i], ccfg[i][ph], ph, tcp);
+          if (four) P.prep4 += (int)(tcp.size() - before);
+        }
     for (int i : tcl) {
       if (tc_chunks(members[i]) <= ph) continue;
       const int cfg = ccfg[i][ph];
       for (int64_t b = 0; b < tc_table_blocks(members[i], ph); b++) tab_bm[ph].push_back({cfg, (int32_t)b});
-      tc_prep_items(members[i], cfg, ph, tcp);
       const int64_t share = (int64_t)((double)e->sm_count * (double)tc_density_steps(members[i], ph) /
                                       (double)std::max<int64_t>(1, steps) * (double)e->tune.dens_pct / 100.0);
       tc_gemm_items(members[i], cfg, ph, share, tcd, tcf);
@@ -226,10 +233,15 @@ cudaError_t engine_build(Engine* e, const std::vector<Ctx*>& members, const std:
     P.rprep_off = (int)tcp.size();
     for (int i : tcl) {
       if (tc_chunks(members[i]) - 1 <= ph) continue;
-      const int cfg = ccfg[i][ph];
-      for (int64_t b = 0; b < tc_table_blocks(members[i], ph); b++) rtab_bm[ph].push_back({cfg, (int32_t)b});
-      tc_prep_items(members[i], cfg, ph, tcp);
+      for (int64_t b = 0; b < tc_table_blocks(members[i], ph); b++) rtab_bm[ph].push_back({ccfg[i][ph], (int32_t)b});
     }
+    for (int four = 0; four < 2; four++)
+      for (int i : tcl)
+        if (tc_chunks(members[i]) - 1 > ph && (members[i]->tc.d == 4) == (four == 1)) {
+          const size_t before = tcp.size();
+          tc_prep_items(members[i], ccfg[i][ph], ph, tcp);
+          if (four) P.rprep4 += (int)(tcp.size() - before);
+        }
     P.rprep_n = (int)tcp.size() - P.rprep_off;
   }
   cudaError_t err;

@@ -87,11 +87,11 @@ struct CfgDev {
   dd pref, inv_L;
   // tensor-core fixed-point path (tc.cu); tc = 0 when the configuration uses the integer-pipe kernels
   int tc, tc_R1, tc_nP, tc_RT, tc_CTd, tc_PT, tc_KSf, tc_CTf, tc_bexp, tc_nblk, tc_gs, tc_ts, tc_ntab;
-  int tc_d, tc_lift;   // the path's number of axes (2 or 3); d = 1 on two lifted axes: n = 2^tc_lift n1 + n2
+  int tc_d, tc_lift;   // the path's number of axes (2, 3 or 4); d = 1 on two lifted axes: n = 2^tc_lift n1 + n2
   // two-axis path: the last row tile's canonical p (those >= tc_trP0) run as one transposed density tile, rows
   // (n1, cos / sin) of a_j(n1) for n1 < tc_trN1 from local row tc_trRow0 of that row tile, columns (p, cos / sin)
   int tc_tr, tc_trP0, tc_trRow0, tc_trN1;
-  int tc_Rax[3];       // per axis: powers 0..tc_Rax[a] in the tables
+  int tc_Rax[4];       // per axis: powers 0..tc_Rax[a] in the tables
   int64_t tc_KS, tc_NJ, tc_NPg;  // density K-steps; particle groups and row groups of the digit tensor (a chunk)
   int64_t tc_j0, tc_n, tc_nbuf;  // this chunk: first particle, particles, particle stride of the chunk buffers
   uint8_t *tc_wT, *tc_aB, *tc_fB;  // digit tensor of w_j(p); density B (a_j(n1)); force B (coefficients)
@@ -100,7 +100,7 @@ struct CfgDev {
   long long* tc_acc;   // density level groups per tile [tile][3][32][128], summed by integer atomics
   long long* tc_facc;  // force limbs [axis][3][N], summed by integer atomics
   const int32_t* tc_em;       // [p][n1][2]: internal k index of (n1, +-p), or -1
-  const int32_t* tc_pvec;     // [p]: (n2 & 0xffff) | (n3 << 16)
+  const int32_t* tc_pvec;     // [p]: (n2 & 0xffff) | (n3 << 16); four axes: 10-bit fields n2 | n3 << 10 | n4 << 20
   const int32_t* tc_tilemap;  // [RT][CTd] -> tile slot, or -1
   const void* tc_tmap;        // two 128-byte tensor maps of the digit tensor: density box, force box
   int* tc_err;
@@ -138,6 +138,7 @@ constexpr int kMaxTcPhases = 64;  // particle chunks of a tensor-core member, at
 struct TcPhase {
   int tab_off = 0, tab_n = 0, prep_off = 0, prep_n = 0, dens_off = 0, dens_n = 0, force_off = 0, force_n = 0;
   int rtab_off = 0, rtab_n = 0, rprep_off = 0, rprep_n = 0;  // the preparation again, before the force items
+  int prep4 = 0, rprep4 = 0;  // the last items of each preparation range: those of four-axis members
 };
 
 struct EngineView {
@@ -253,11 +254,11 @@ struct Engine {
 // tile plan and buffers of the tensor-core path of one configuration (tc.cu)
 struct TcPlan {
   bool on = false;
-  int d = 0;                     // the path's number of axes: 2 or 3 (d = 1 runs on two lifted axes)
+  int d = 0;                     // the path's number of axes: 2, 3 or 4 (d = 1 runs on two lifted axes)
   int lift = 0;                  // d = 1: n = 2^lift n1 + n2, n2 in [-2^(lift - 1), 2^(lift - 1))
   int R1 = 0;                    // n1 in [0, R1]
-  int Rax[3] = {0, 0, 0};        // largest |n_a| per axis (powers held in the tables)
-  int nP = 0;                    // canonical sub-vectors p = (n2[, n3]) of the half set, sorted by |p|^2
+  int Rax[4] = {0, 0, 0, 0};     // largest |n_a| per axis (powers held in the tables)
+  int nP = 0;                    // canonical sub-vectors p = (n2[, n3[, n4]]) of the half set, sorted by |p|^2
   int64_t Nc = 0;                // particles per chunk (the buffers below hold one chunk), a multiple of 128
   int nchunk = 1;                // chunks of N, evaluated one after another
   int64_t KS = 0;                // density K-steps (16 particles each) of a full chunk
@@ -274,8 +275,9 @@ struct TcPlan {
   std::vector<int32_t> tiles;    // density tiles in use: rt * CTd + ct
   std::vector<int32_t> tilemap;  // [RT * CTd] -> index into tiles, or -1
   std::vector<int32_t> em;       // [nP][R1 + 1][2] internal index of (n1, p) / (n1, -p), or -1
-  std::vector<int32_t> pvec;     // [nP] packed (n2, n3)
+  std::vector<int32_t> pvec;     // [nP] packed (n2, n3) or (n2, n3, n4), as tc_pvec
   std::vector<int32_t> ks_ct;    // force K-steps per column tile
+  int fsplit = 1;                // force K ranges per (particle tile, column tile), at most (see tc_setup)
   int ntab = 0;                  // table entries per (axis, particle)
   size_t prep_smem = 0;          // dynamic shared memory of the preparation kernel
   alignas(64) unsigned char tmap_h[256];  // host copy of the two tensor maps (source of the upload)

@@ -1,16 +1,17 @@
-// tc.cu -- the fixed-point hot path for d = 2 and d = 3 on the tensor cores (Eqs. ntilde and force of
-// arXiv:2304.09139).
+// tc.cu -- the fixed-point hot path for d = 2, 3 and 4 on the tensor cores (Eqs. ntilde and force of
+// arXiv:2304.09139; d = 1 runs on two lifted axes).
 //
-// Write a wavevector as n = (n1, p), p = (n2) or (n2, n3), and the phasor of particle j per factor:
-// a_j(n1) = e^{2 pi i n1 s_j1}, w_j(p) = e^{2 pi i p . (s_j2, s_j3)}.  The collective density is then a matrix
+// Write a wavevector as n = (n1, p), p = (n2), (n2, n3) or (n2, n3, n4), and the phasor of particle j per factor:
+// a_j(n1) = e^{2 pi i n1 s_j1}, w_j(p) = e^{2 pi i p . (s_j2, .., s_jd)}.  The collective density is then a matrix
 // product over the particles, n~(n1, p) = sum_j a_j(n1) w_j(p).  The half set H (first non-zero component > 0)
-// has n1 >= 0; p runs over a half of its plane, P = {p : n3 > 0, or n3 = 0 and n2 >= 0} ("canonical" p), since
-// every k in H is (n1, p) or (n1, -p) with p in P.  As a_j(-n1) = conj(a_j(n1)), the four real products
+// has n1 >= 0; p runs over a half of its space, P = {p : the last non-zero component of p is > 0, or p = 0}
+// ("canonical" p), since every k in H is (n1, p) or (n1, -p) with p in P.  As a_j(-n1) = conj(a_j(n1)), the four real products
 // P_xy(p, n1) = sum_j x_j(p) y_j(n1) (x the cos / sin of w, y of a) give
 //   n~(n1, p)  = (P_cc - P_ss) + i (P_sc + P_cs),
 //   n~(n1, -p) = conj n~(-n1, p) = (P_cc + P_ss) + i (P_cs - P_sc):
 // one real GEMM with rows (p, cos / sin), columns (n1, cos / sin) and K = particles.  For d = 3, w_j(p) is the
-// product b_j(n2) c_j(n3) of the axis-2 and axis-3 powers, formed once per particle and p.
+// product b_j(n2) c_j(n3) of the axis-2 and axis-3 powers, for d = 4 b_j(n2) c_j(n3) e_j(n4), formed once per
+// particle and p.
 //
 // The force F_j = (4 pi / L) sum_k n [C sin th - S cos th] = (4 pi / L) Im sum_k n W_k e^{i th_jk}, W = C - i S,
 // is grouped per n1: G_j(n1) = sum_{p in P} [U(n1, p) cos(2 pi p . s_j) + V(n1, p) sin(2 pi p . s_j)] with
@@ -264,10 +265,24 @@ __device__ __forceinline__ q160 load_q160(const void* p) {
 namespace {
 
 constexpr int kPrepThreads = 256;
-constexpr int kPrepStaged = 16;     // particles per d = 3 w item (their powers b(n2), c(n3) staged in shared memory)
+constexpr int kPrepStaged = 16;     // particles per d >= 3 w item (their axis powers staged in shared memory)
 constexpr int kPrepTable = 128;     // at most this many particles per table item (a(n1); w of d = 1, 2)
 constexpr int kPrepLow = 8;         // e^{2 pi i m s} = A[m / 8] T[m % 8]
 constexpr size_t kPrepSmemMax = 200 * 1024;
+
+// the components of a packed canonical p: (n2 & 0xffff) | n3 << 16 on two or three axes, 10-bit fields
+// n2 | n3 << 10 | n4 << 20 on four (each sign-extended)
+__device__ __forceinline__ void unpack_p(int32_t pv, int d, int& n2, int& n3, int& n4) {
+  if (d == 4) {
+    n2 = (int32_t)((uint32_t)pv << 22) >> 22;
+    n3 = (int32_t)((uint32_t)pv << 12) >> 22;
+    n4 = (int32_t)((uint32_t)pv << 2) >> 22;
+  } else {
+    n2 = (int)(int16_t)(pv & 0xffff);
+    n3 = pv >> 16;
+    n4 = 0;
+  }
+}
 
 // conj of a first-quadrant phasor: conj(i^q (c + i s)) = i^{-q} (c - i s) = i^{3 - q} (s + i c)
 __device__ __forceinline__ qent qconj(const qent& z) {
@@ -397,16 +412,21 @@ __global__ void __launch_bounds__(128) k_tc_tables(const CfgDev* __restrict__ cf
 }
 
 // CTA per item.  Items TwItem {cfg, kind | staged << 8 | groups << 9, first particle}: 8 x groups particles (16
-// for a staged d = 3 w item; a table item enough for 128 (entry, group) lane pairs, at most 128).  Kind 0: a_j(n1), n1 in [0, R1] -> density B digit slices (rows (n1, cos / sin) of
+// for a staged w item of three or four axes; a table item enough for 128 (entry, group) lane pairs, at most 128).
+// Kind 0: a_j(n1), n1 in [0, R1] -> density B digit slices (rows (n1, cos / sin) of
 // K-major 32 x 16 tiles) and the Q2.126 table of the force epilogue.  Kind 1: w_j(p) for the nP canonical p ->
 // the digit tensor.  A lane pair takes one entry and eight consecutive particles: each lane forms four of the
 // products, the pair swaps halves, and lane 0 writes the entry's cos row, lane 1 its sin row, as 16-byte
 // core-matrix rows, so that a warp's store covers whole 128-byte core matrices.  Table items (kind 0, and kind
-// 1 for d = 2) multiply two entries of each particle's tables; d = 3 w items cover 16 particles whose axis-2
-// and axis-3 powers b_j(n2), c_j(n3) (n2, n3 >= 0) are formed first into shared memory, and
-// w = b_j(|n2|) (conjugated for n2 < 0) c_j(n3).
+// 1 for d = 2) multiply two entries of each particle's tables; staged w items cover 16 particles whose axis
+// powers b_j(n2), c_j(n3) (and e_j(n4) on four axes; every exponent >= 0) are formed first into shared memory,
+// and w = b_j(|n2|) (conjugated for n2 < 0) c_j(n3) on three axes, w = b_j(|n2|) c_j(|n3|) e_j(n4) on four (each
+// factor of a negative exponent conjugated).
+// kFour: the instance for members of four axes (their items are launched apart, after the others'), whose w
+// takes a third factor; the other instance is free of that code and of its registers.
+template <bool kFour>
 __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restrict__ cfgs,
-                                                          const TwItem* __restrict__ items) {
+                                                                         const TwItem* __restrict__ items) {
   grid_dep_wait();
   extern __shared__ __align__(16) uint8_t psm[];
   const TwItem it = items[blockIdx.x];
@@ -421,18 +441,21 @@ __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restri
   const __int128 bias = digit_bias();
   const uint4 yzero = make_uint4((uint32_t)bias, (uint32_t)(bias >> 32), (uint32_t)(bias >> 64), (uint32_t)(bias >> 96));
   const qent* tab = reinterpret_cast<const qent*>(c.tc_tab);
-  const int W2 = c.tc_Rax[1] + 1, W23 = W2 + (c.tc_d == 3 ? c.tc_Rax[2] + 1 : 0);
+  // staged powers per particle: axis 2 (W2 of them), axis 3 (W3), axis 4 (W4)
+  const int W2 = c.tc_Rax[1] + 1, W3 = c.tc_d >= 3 ? c.tc_Rax[2] + 1 : 0, W4 = kFour ? c.tc_Rax[3] + 1 : 0;
+  const int W23 = W2 + W3 + W4;
   const int count = kind == 0 ? c.tc_R1 + 1 : c.tc_nP;
-  int32_t* pvs = reinterpret_cast<int32_t*>(psm);  // kind 1: the packed (n2, n3) of every entry
-  qent* Pw = reinterpret_cast<qent*>(psm + (((size_t)c.tc_nP * 4 + 15) & ~(size_t)15));  // [particle][n2, then n3]
+  int32_t* pvs = reinterpret_cast<int32_t*>(psm);  // kind 1: the packed p of every entry
+  // staged: [particle][powers of axis 2, then 3, then 4]
+  qent* Pw = reinterpret_cast<qent*>(psm + (((size_t)c.tc_nP * 4 + 15) & ~(size_t)15));
   if (kind == 1) {
     for (int e = tid; e < count; e += kPrepThreads) pvs[e] = c.tc_pvec[e];
     if (staged) {
       for (int task = tid; task < kPrepStaged * W23; task += kPrepThreads) {
         const int jl = task % kPrepStaged, e = task / kPrepStaged;
         const int64_t j = min(j0 + jl, N - 1);  // entries of particles past N are never read
-        const int axis = e < W2 ? 1 : 2;
-        const int m = e < W2 ? e : e - W2;
+        const int axis = e < W2 ? 1 : (e < W2 + W3 ? 2 : 3);
+        const int m = e < W2 ? e : (e < W2 + W3 ? e - W2 : e - W2 - W3);
         const qent* tj = tab + ((int64_t)axis * c.tc_nbuf + j) * c.tc_ntab;
         Pw[jl * W23 + e] = qmul(tj[kPrepLow + (m >> 3)], tj[m & 7]);
       }
@@ -448,11 +471,9 @@ __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restri
     const int e = valid ? q % count : 0, g = valid ? q / count : 0;
     const int64_t jg = j0 + 8 * g;
     const bool live = valid && jg < Npad;  // digits of particles past the last one are written as zeros
-    int m = e, n2 = 0, n3 = 0;
+    int m = e, n2 = 0, n3 = 0, n4 = 0;
     if (kind == 1) {
-      const int32_t pv = pvs[e];
-      n2 = (int)(int16_t)(pv & 0xffff);
-      n3 = pv >> 16;
+      unpack_p(pvs[e], kFour ? 4 : 2, n2, n3, n4);
       m = n2;  // d = 2: n2 = m >= 0
     }
     uint4 Yr[4], Yi[4];
@@ -468,7 +489,13 @@ __global__ void __launch_bounds__(kPrepThreads) k_tc_prep(const CfgDev* __restri
           const qent* pj = Pw + jl * W23;
           const qent b = pj[n2 < 0 ? -n2 : n2];
           za = n2 < 0 ? qconj(b) : b;
-          zb = pj[W2 + n3];
+          if (kFour) {  // w = b(n2) c(n3) e(n4), n4 >= 0
+            const qent cz = pj[W2 + (n3 < 0 ? -n3 : n3)];
+            za = qmul(za, n3 < 0 ? qconj(cz) : cz);
+            zb = pj[W2 + W3 + n4];
+          } else {
+            zb = pj[W2 + n3];
+          }
         } else {
           const qent* tj = tab + ((int64_t)axis * c.tc_nbuf + j) * c.tc_ntab;
           za = tj[kPrepLow + (m >> 3)];
@@ -833,7 +860,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
         const int64_t j = (int64_t)it.a * kTileM + row;
         const int d = c.tc_d, npt = 16 / d;
         const int gsh = c.tc_gs, tsh = 108 + c.tc_gs - c.tc_ts;
-        __int128 F0 = 0, F1 = 0, F2 = 0;  // per axis, value 2^ts (at most four terms each)
+        __int128 F0 = 0, F1 = 0, F2 = 0, F3 = 0;  // per axis, value 2^ts (at most four terms each)
 #pragma unroll
         for (int v = 0; v < kEpiCols / 2; v++) {
           const int i = (kEpiCols / 2) * hq + v;
@@ -856,13 +883,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
               (q128_to_i128(q128{{p[1], p[2], p[3], p[4]}}) + q128_to_i128(q128{{r2[1], r2[2], r2[3], r2[4]}})) >> tsh;
           if (t == 0) F0 += T * (__int128)n1;
           else if (t == 1) F1 += T;
-          else F2 += T;
+          else if (t == 2) F2 += T;
+          else F3 += T;
         }
         if (j < c.tc_n) {
           // F = L2 2^88 + L1 2^44 + L0 (L0, L1 in [0, 2^44)): the limbs of all column tiles add up exactly
           const unsigned long long m44 = (1ull << 44) - 1;
           for (int t = 0; t < d; t++) {
-            const __int128 F = t == 0 ? F0 : (t == 1 ? F1 : F2);
+            const __int128 F = t == 0 ? F0 : (t == 1 ? F1 : (t == 2 ? F2 : F3));
             unsigned long long* fa = reinterpret_cast<unsigned long long*>(c.tc_facc) + (size_t)t * 3 * c.N + c.tc_j0 + j;
             atomicAdd(fa, (unsigned long long)F & m44);
             atomicAdd(fa + c.N, (unsigned long long)(F >> 44) & m44);
@@ -1120,7 +1148,9 @@ __global__ void __launch_bounds__(128) k_tc_coef(const CfgDev* __restrict__ cfgs
       X1 = q160_shr_round(q160_sub160(Cp, Cm), sh);
     }
   } else {
-    const int n = t == 1 ? (int)(int16_t)(pv & 0xffff) : pv >> 16;
+    int n2, n3, n4;
+    unpack_p(pv, c.tc_d, n2, n3, n4);
+    const int n = t == 1 ? n2 : (t == 2 ? n3 : n4);
     const int sh = 22 + e + c.tc_bexp;
     if (ri == 0) {
       q160 a = Sp;
@@ -1156,7 +1186,7 @@ static cudaError_t tc_dev_alloc(DevBuf* b, size_t bytes, cudaStream_t st) {
 }
 
 // N <= 2^22: the top level group of a density tile accumulates about N 2^40 (int64), and n~ stays inside Q34.126
-bool tc_eligible(const Ctx& c) { return c.d >= 1 && c.d <= 3 && c.N >= 1 && c.N <= (1 << 22) && c.M >= 1; }
+bool tc_eligible(const Ctx& c) { return c.d >= 1 && c.d <= 4 && c.N >= 1 && c.N <= (1 << 22) && c.M >= 1; }
 
 int64_t tc_coef_blocks(const Ctx& c) {
   if (!c.tc.on) return 0;
@@ -1188,12 +1218,14 @@ EncodeTiledFn encode_tiled() {
   return fn;
 }
 
-// (n1, p) of internal wavevector k: p = (n2, n3) of axes 2..d (n3 = 0 for d = 2).  For d = 1 the single index
-// n > 0 is split as n = 2^lift n1 + n2 with n2 in [-2^(lift - 1), 2^(lift - 1)): the phase n s is n1 (2^lift s)
-// + n2 s, a wavevector of two lifted axes, and n > 0 exactly when (n1, n2) lies in the two-axis half set.
-inline void sub_vec(const Ctx& c, int lift, int64_t k, int& n1, int& n2, int& n3) {
+// (n1, p) of internal wavevector k: p = (n2, n3, n4) of axes 2..d (the components past d are 0).  For d = 1 the
+// single index n > 0 is split as n = 2^lift n1 + n2 with n2 in [-2^(lift - 1), 2^(lift - 1)): the phase n s is
+// n1 (2^lift s) + n2 s, a wavevector of two lifted axes, and n > 0 exactly when (n1, n2) lies in the two-axis half
+// set.
+inline void sub_vec(const Ctx& c, int lift, int64_t k, int& n1, int& n2, int& n3, int& n4) {
   const int32_t* n = &c.ks.n_int[(size_t)k * c.d];
   n3 = 0;
+  n4 = 0;
   if (c.d == 1) {
     const int64_t B = (int64_t)1 << lift;
     n1 = (int)((n[0] + B / 2) >> lift);
@@ -1202,7 +1234,8 @@ inline void sub_vec(const Ctx& c, int lift, int64_t k, int& n1, int& n2, int& n3
   }
   n1 = n[0];
   n2 = n[1];
-  n3 = c.d == 3 ? n[2] : 0;
+  if (c.d >= 3) n3 = n[2];
+  if (c.d == 4) n4 = n[3];
 }
 
 // d = 1: the split 2^lift minimising the padded work of both GEMMs (rows (n2, cos / sin) in tiles of 128 and
@@ -1218,8 +1251,8 @@ int choose_lift(const Ctx& c) {
     std::vector<char> seen(B / 2 + 1, 0);
     int64_t nP = 0, R1 = 0;
     for (int64_t k = 0; k < c.M; k++) {
-      int n1, n2, n3;
-      sub_vec(c, lift, k, n1, n2, n3);
+      int n1, n2, n3, n4;
+      sub_vec(c, lift, k, n1, n2, n3, n4);
       R1 = std::max<int64_t>(R1, n1);
       const int a = std::abs(n2);
       if (!seen[a]) {
@@ -1237,7 +1270,12 @@ int choose_lift(const Ctx& c) {
   }
   return best;
 }
-inline bool canonical(int n2, int n3) { return n3 > 0 || (n3 == 0 && n2 >= 0); }
+// the canonical half of the sub-vectors: the last non-zero component of p = (n2, n3, n4) is positive, or p = 0
+inline bool canonical(int n2, int n3, int n4) { return n4 > 0 || (n4 == 0 && (n3 > 0 || (n3 == 0 && n2 >= 0))); }
+
+struct PVec {
+  int n2, n3, n4;
+};
 
 }  // namespace
 
@@ -1256,46 +1294,62 @@ cudaError_t tc_setup(Ctx* c) {
   const int d = c->d == 1 ? 2 : c->d;  // the path's number of axes (d = 1 runs on two lifted axes)
   const int lift = c->d == 1 ? choose_lift(*c) : 0;
   const int64_t M = c->M;
-  // canonical sub-vectors present in the set, sorted by |p|^2 (then n3, n2): a prefix of the list is a disk
+  // canonical sub-vectors present in the set, sorted by |p|^2 (then n4, n3, n2): a prefix of the list is a ball
   int R1 = 0, Rp = 0;
   for (int64_t k = 0; k < M; k++) {
-    int n1, n2, n3;
-    sub_vec(*c, lift, k, n1, n2, n3);
+    int n1, n2, n3, n4;
+    sub_vec(*c, lift, k, n1, n2, n3, n4);
     R1 = std::max(R1, n1);
-    Rp = std::max(Rp, std::max(std::abs(n2), std::abs(n3)));
+    Rp = std::max(Rp, std::max(std::abs(n2), std::max(std::abs(n3), std::abs(n4))));
   }
-  const int span = 2 * Rp + 1;
-  std::vector<int32_t> pid((size_t)span * span, -1);
-  std::vector<std::pair<int, int>> plist;
-  for (int64_t k = 0; k < M; k++) {
-    int n1, n2, n3;
-    sub_vec(*c, lift, k, n1, n2, n3);
-    if (!canonical(n2, n3)) {
+  // four axes: the packed p has 10-bit fields, and the dense index map below has (2 Rp + 1)^3 entries
+  if (d == 4 && Rp > 64) return cudaSuccess;
+  // dense index map over the box |n_a| <= Rp of the axes in use
+  const int64_t s2 = 2 * Rp + 1, s3 = d >= 3 ? s2 : 1, o3 = d >= 3 ? Rp : 0, o4 = d == 4 ? Rp : 0;
+  const int64_t span4 = d == 4 ? s2 : 1;
+  std::vector<int32_t> pid((size_t)(s2 * s3 * span4), -1);
+  auto pslot = [&](int n2, int n3, int n4) -> int32_t& {
+    return pid[(size_t)(((n4 + o4) * s3 + (n3 + o3)) * s2 + (n2 + Rp))];
+  };
+  // the canonical p of wavevector k (flipping the sign of p when k is (n1, -p)) and whether it was canonical
+  auto pcan = [&](int& n2, int& n3, int& n4) {
+    const bool can = canonical(n2, n3, n4);
+    if (!can) {
       n2 = -n2;
       n3 = -n3;
+      n4 = -n4;
     }
-    int32_t& slot = pid[(size_t)(n3 + Rp) * span + (n2 + Rp)];
+    return can;
+  };
+  std::vector<PVec> plist;
+  for (int64_t k = 0; k < M; k++) {
+    int n1, n2, n3, n4;
+    sub_vec(*c, lift, k, n1, n2, n3, n4);
+    pcan(n2, n3, n4);
+    int32_t& slot = pslot(n2, n3, n4);
     if (slot < 0) {
       slot = 0;
-      plist.push_back({n2, n3});
+      plist.push_back({n2, n3, n4});
     }
   }
-  std::sort(plist.begin(), plist.end(), [](const std::pair<int, int>& a, const std::pair<int, int>& b) {
-    const int ra = a.first * a.first + a.second * a.second, rb = b.first * b.first + b.second * b.second;
+  std::sort(plist.begin(), plist.end(), [](const PVec& a, const PVec& b) {
+    const int ra = a.n2 * a.n2 + a.n3 * a.n3 + a.n4 * a.n4, rb = b.n2 * b.n2 + b.n3 * b.n3 + b.n4 * b.n4;
     if (ra != rb) return ra < rb;
-    if (a.second != b.second) return a.second < b.second;
-    return a.first < b.first;
+    if (a.n4 != b.n4) return a.n4 < b.n4;
+    if (a.n3 != b.n3) return a.n3 < b.n3;
+    return a.n2 < b.n2;
   });
   const int nP = (int)plist.size();
-  int R2 = 0, R3 = 0;
+  int R2 = 0, R3 = 0, R4 = 0;
   for (int i = 0; i < nP; i++) {
-    pid[(size_t)(plist[i].second + Rp) * span + (plist[i].first + Rp)] = i;
-    R2 = std::max(R2, std::abs(plist[i].first));
-    R3 = std::max(R3, plist[i].second);
+    pslot(plist[i].n2, plist[i].n3, plist[i].n4) = i;
+    R2 = std::max(R2, std::abs(plist[i].n2));
+    R3 = std::max(R3, std::abs(plist[i].n3));
+    R4 = std::max(R4, plist[i].n4);
   }
   // limits: the prep kernel's shared memory, the force epilogue scales
-  const size_t prep_smem =
-      (((size_t)nP * 4 + 15) & ~(size_t)15) + (d == 3 ? (size_t)kPrepStaged * (R2 + 1 + R3 + 1) * sizeof(qent) : 0);
+  const size_t prep_smem = (((size_t)nP * 4 + 15) & ~(size_t)15) +
+                           (d >= 3 ? (size_t)kPrepStaged * (R2 + 1 + R3 + 1 + (d == 4 ? R4 + 1 : 0)) * sizeof(qent) : 0);
   int lg = 0;
   while ((1ll << lg) < 2ll * nP) lg++;
   int lf = 0;
@@ -1306,13 +1360,18 @@ cudaError_t tc_setup(Ctx* c) {
   t.R1 = R1;
   t.Rax[0] = R1;
   t.Rax[1] = R2;
-  t.Rax[2] = d == 3 ? R3 : 0;
+  t.Rax[2] = d >= 3 ? R3 : 0;
+  t.Rax[3] = d == 4 ? R4 : 0;
   t.nP = nP;
   t.gs = 16 - lg;  // G~ (|.| <= 2 nP) held as R' 2^gs below 2^126
   t.ts = 126 - lf;  // partial sums of four n1 terms weighted by n1 <= R1, value 2^ts, below 2^126
   t.prep_smem = prep_smem;
   t.pvec.resize(nP);
-  for (int i = 0; i < nP; i++) t.pvec[i] = (int32_t)((uint32_t)(plist[i].first & 0xffff) | ((uint32_t)plist[i].second << 16));
+  for (int i = 0; i < nP; i++) {
+    const PVec& v = plist[i];
+    t.pvec[i] = d == 4 ? (int32_t)(((uint32_t)v.n2 & 0x3ffu) | (((uint32_t)v.n3 & 0x3ffu) << 10) | ((uint32_t)v.n4 << 20))
+                       : (int32_t)(((uint32_t)v.n2 & 0xffffu) | ((uint32_t)v.n3 << 16));
+  }
   const int W1 = R1 + 1;
   t.RT = (2 * nP + kTileM - 1) / kTileM;
   t.CTd = (2 * W1 + kTileN - 1) / kTileN;
@@ -1331,10 +1390,10 @@ cudaError_t tc_setup(Ctx* c) {
     int n1max = -1;
     std::vector<char> reach(t.CTd, 0);
     for (int64_t k = 0; k < M; k++) {
-      int n1, n2, n3;
-      sub_vec(*c, lift, k, n1, n2, n3);
-      const bool can = canonical(n2, n3);
-      const int p = pid[(size_t)((can ? n3 : -n3) + Rp) * span + ((can ? n2 : -n2) + Rp)];
+      int n1, n2, n3, n4;
+      sub_vec(*c, lift, k, n1, n2, n3, n4);
+      pcan(n2, n3, n4);
+      const int p = pslot(n2, n3, n4);
       if (p >= p0) {
         n1max = std::max(n1max, n1);
         reach[(2 * n1) >> 5] = 1;
@@ -1351,16 +1410,16 @@ cudaError_t tc_setup(Ctx* c) {
     }
   }
   t.bexp = 0;
-  while ((1 << t.bexp) <= std::max(R2, R3)) t.bexp++;
+  while ((1 << t.bexp) <= std::max(R2, std::max(R3, R4))) t.bexp++;
   // emit map: k = (n1, p) -> [p][n1][0], k = (n1, -p) -> [p][n1][1]
   t.em.assign((size_t)nP * W1 * 2, -1);
   t.tilemap.assign((size_t)t.RT * t.CTd, -1);
   std::vector<int> pmax_ct(t.CTf, -1);
   for (int64_t k = 0; k < M; k++) {
-    int n1, n2, n3;
-    sub_vec(*c, lift, k, n1, n2, n3);
-    const bool can = canonical(n2, n3);
-    const int p = pid[(size_t)((can ? n3 : -n3) + Rp) * span + ((can ? n2 : -n2) + Rp)];
+    int n1, n2, n3, n4;
+    sub_vec(*c, lift, k, n1, n2, n3, n4);
+    const bool can = pcan(n2, n3, n4);
+    const int p = pslot(n2, n3, n4);
     t.em[((size_t)p * W1 + n1) * 2 + (can ? 0 : 1)] = (int32_t)k;
     if (t.tr && p >= t.trP0)
       t.tilemap[(size_t)(t.RT - 1) * t.CTd + (t.CTd - 1)] = 1;
@@ -1377,9 +1436,19 @@ cudaError_t tc_setup(Ctx* c) {
   // (p is sorted by |p|: the range of a tile of large n1 is a small disk)
   t.ks_ct.resize(t.CTf);
   for (int ct = 0; ct < t.CTf; ct++) t.ks_ct[ct] = pmax_ct[ct] < 0 ? 0 : (2 * (pmax_ct[ct] + 1) + kStepK - 1) / kStepK;
+  // split force K: when the (particle tile, column tile) items of the whole configuration are fewer than the SMs,
+  // each column tile's K range is cut into up to fsplit pieces of at least one read-out chunk (their force limbs add
+  // up by integer atomics).  The split follows from N and the set alone, not from a chunk, a shard or a batch, so
+  // that the truncation of each piece's a_j(n1) G product, and with it every bit of F, is the same in all of them.
+  {
+    int used = 0;
+    for (int ct = 0; ct < t.CTf; ct++) used += t.ks_ct[ct] > 0;
+    const int64_t items = (c->N + kTileM - 1) / kTileM * std::max(1, used);
+    t.fsplit = (int)std::max<int64_t>(1, std::min<int64_t>(8, std::max(1, c->sm_count) / items));
+  }
   const int nt = (int)t.tiles.size();
 
-  t.ntab = kPrepLow + std::max(R1, std::max(R2, R3)) / kPrepLow + 1;
+  t.ntab = kPrepLow + std::max(std::max(R1, R4), std::max(R2, R3)) / kPrepLow + 1;
   // particles per chunk.  The digit tensor, the density B digits, the Q2.126 a_j(n1) and the tables hold one
   // chunk; the density sums run over the chunks into the same exact accumulators and the force rows of a chunk
   // are its own particles, so the results do not depend on the chunking.  By default every particle is one
@@ -1453,7 +1522,8 @@ cudaError_t tc_setup(Ctx* c) {
   if (!attr) {
     cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
     cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem);
-    cudaFuncSetAttribute(k_tc_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPrepSmemMax);
+    cudaFuncSetAttribute(k_tc_prep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPrepSmemMax);
+    cudaFuncSetAttribute(k_tc_prep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPrepSmemMax);
     attr = true;
   }
   return cudaGetLastError();
@@ -1490,7 +1560,7 @@ void tc_fill_cfgdev(const Ctx* c, CfgDev* g) {
   g->tc_trN1 = t.trN1;
   g->tc_R1 = t.R1;
   g->tc_nP = t.nP;
-  for (int a = 0; a < 3; a++) g->tc_Rax[a] = t.Rax[a];
+  for (int a = 0; a < 4; a++) g->tc_Rax[a] = t.Rax[a];
   g->tc_RT = t.RT;
   g->tc_CTd = t.CTd;
   g->tc_PT = t.PT;
@@ -1542,8 +1612,8 @@ int64_t tc_density_steps(const Ctx* c, int ch) {
 // blocks (128 threads) of the tables kernel for one chunk: two threads per (axis, particle)
 int64_t tc_table_blocks(const Ctx* c, int ch) { return (2 * (int64_t)c->tc.d * chunk_len(c, ch) + 127) / 128; }
 
-// preparation items of one chunk (cfg: its descriptor in the engine), the heavier w items first.  d = 3 w items
-// cover 16 particles (their powers fill shared memory); a table item covers enough groups of 8 particles for 128
+// preparation items of one chunk (cfg: its descriptor in the engine), the heavier w items first.  w items of
+// three or four axes cover 16 particles (their powers fill shared memory); a table item covers enough groups of 8 particles for 128
 // (entry, group) lane pairs, at most 128 particles.  They reach the chunk's last K-step boundary, so that stale
 // digits of an earlier, longer chunk never enter the density sums.
 void tc_prep_items(const Ctx* c, int cfg, int ch, std::vector<TwItem>& prep) {
@@ -1551,7 +1621,7 @@ void tc_prep_items(const Ctx* c, int cfg, int ch, std::vector<TwItem>& prep) {
   const int64_t npad = (chunk_len(c, ch) + kStepK - 1) / kStepK * kStepK;
   for (int kind = 1; kind >= 0; kind--) {
     const int count = kind == 0 ? t.R1 + 1 : t.nP;
-    const bool staged = kind == 1 && t.d == 3;
+    const bool staged = kind == 1 && t.d >= 3;
     int ng = staged ? kPrepStaged / 8 : 1;
     if (!staged)
       while (ng < kPrepTable / 8 && ng * count < kPrepThreads / 2) ng *= 2;
@@ -1606,8 +1676,14 @@ void tc_gemm_items(const Ctx* c, int cfg, int ch, int64_t pieces, std::vector<Tc
   // read the particle tile's digits from L2 once they are in
   const int PT = (int)((n + kTileM - 1) / kTileM);
   for (int pt = 0; pt < PT; pt++)
-    for (int ct = 0; ct < t.CTf; ct++)
-      if (t.ks_ct[ct] > 0) force.push_back({cfg, 1, pt, ct, 0, t.ks_ct[ct], ct, 0});
+    for (int ct = 0; ct < t.CTf; ct++) {
+      const int ks = t.ks_ct[ct];
+      const int sp = std::max(1, std::min(t.fsplit, ks / kChunkSteps));  // pieces of at least one read-out chunk
+      for (int i = 0; i < sp; i++) {
+        const int k0 = (int)((int64_t)ks * i / sp), k1 = (int)((int64_t)ks * (i + 1) / sp);
+        if (k1 > k0) force.push_back({cfg, 1, pt, ct, k0, k1 - k0, ct, 0});
+      }
+    }
 }
 
 size_t tc_gemm_smem() { return kGemmSmem; }
@@ -1621,7 +1697,9 @@ cudaError_t tc_launch_force_finish(const EngineView& v, cudaStream_t st, Prof* p
   return cudaGetLastError();
 }
 
-static cudaError_t launch_tables_prep(const EngineView& v, int tab_off, int tab_n, int prep_off, int prep_n,
+// prep4: the last items of the range, those of four-axis members (their own kernel instance); one profiler record
+// covers both launches
+static cudaError_t launch_tables_prep(const EngineView& v, int tab_off, int tab_n, int prep_off, int prep_n, int prep4,
                                       cudaStream_t st, Prof* prof) {
   if (tab_n > 0) {
     prof_begin(prof, st, kKTcTables);
@@ -1632,9 +1710,16 @@ static cudaError_t launch_tables_prep(const EngineView& v, int tab_off, int tab_
   }
   if (prep_n > 0) {
     prof_begin(prof, st, kKTcPrep);
-    const cudaError_t le =
-        launch_pdl(k_tc_prep, dim3((unsigned)prep_n), dim3(kPrepThreads), v.tc_prep_smem, st, v.cfgs, v.tc_prep + prep_off);
-    if (le != cudaSuccess) return le;
+    if (prep_n > prep4) {
+      const cudaError_t le = launch_pdl(k_tc_prep<false>, dim3((unsigned)(prep_n - prep4)), dim3(kPrepThreads),
+                                        v.tc_prep_smem, st, v.cfgs, v.tc_prep + prep_off);
+      if (le != cudaSuccess) return le;
+    }
+    if (prep4 > 0) {
+      const cudaError_t le = launch_pdl(k_tc_prep<true>, dim3((unsigned)prep4), dim3(kPrepThreads), v.tc_prep_smem, st,
+                                        v.cfgs, v.tc_prep + prep_off + (prep_n - prep4));
+      if (le != cudaSuccess) return le;
+    }
     prof_end(prof, st);
   }
   return cudaSuccess;
@@ -1651,7 +1736,7 @@ cudaError_t tc_launch_density_gemms(const EngineView& v, cudaStream_t st, Prof* 
   if (v.ntc_list == 0) return cudaSuccess;
   for (int ph = 0; ph < v.ntc_phase; ph++) {
     const TcPhase& P = v.tc_ph[ph];
-    cudaError_t le = launch_tables_prep(v, P.tab_off, P.tab_n, P.prep_off, P.prep_n, st, prof);
+    cudaError_t le = launch_tables_prep(v, P.tab_off, P.tab_n, P.prep_off, P.prep_n, P.prep4, st, prof);
     if (le != cudaSuccess) return le;
     if (P.dens_n > 0) {
       prof_begin(prof, st, kKTcDens);
@@ -1685,7 +1770,7 @@ cudaError_t tc_launch_force(const EngineView& v, cudaStream_t st, Prof* prof) {
   prof_end(prof, st);
   for (int ph = v.ntc_phase - 1; ph >= 0; ph--) {
     const TcPhase& P = v.tc_ph[ph];
-    le = launch_tables_prep(v, P.rtab_off, P.rtab_n, P.rprep_off, P.rprep_n, st, prof);
+    le = launch_tables_prep(v, P.rtab_off, P.rtab_n, P.rprep_off, P.rprep_n, P.rprep4, st, prof);
     if (le != cudaSuccess) return le;
     if (P.force_n > 0) {
       prof_begin(prof, st, kKTcForce);

@@ -57,8 +57,8 @@ def test_batched_evaluation_equals_single(built, impl):
 
 
 def test_tensor_members_equal_single(built):
-    """A batch whose d = 1, 2, 3 members run on the tensor cores and whose d = 4 member runs on the integer pipes:
-    every member bit-identical to a lone context of the same implementation, in an evaluation and a quench."""
+    """A batch of d = 1..4 members on the tensor cores: every member bit-identical to a lone context, in an
+    evaluation and a quench."""
     cfgs = small_mix(6, 46, dims=(1, 2, 3)) + [synth.Config(d=2, N=2000, L=2000 ** 0.5, chi=0.45, seed=11),
                                               synth.Config(d=4, N=120, L=120 ** 0.25, chi=0.3, seed=12)]
     b = ssh.Batch(fx_impl=ssh.FX_TENSOR)
@@ -66,7 +66,7 @@ def test_tensor_members_equal_single(built):
         b.add(c.d, c.N, c.L, synth.positions(c.seed, c.N, c.d), chi=c.chi)
     b.eval(ssh.FX)
     for i, c in enumerate(cfgs):
-        impl = ssh.FX_TENSOR if c.d <= 3 else ssh.FX_INTEGER
+        impl = ssh.FX_TENSOR
         assert b.member(i).fx_impl == impl
         rb = b.member(i).results()
         with ssh.Context(c.d, c.N, c.L, chi=c.chi, fx_impl=impl) as ctx:

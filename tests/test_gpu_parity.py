@@ -76,6 +76,12 @@ CASES = [
     ("d3", 3, 300, 300 ** (1 / 3), 0.40, 0.0, 9),
     ("d3_kmode", 3, 150, 4.0, 0.0, 2 * math.pi * 3.3 / 4.0, 10),
     ("d4", 4, 120, 120 ** 0.25, 0.3, 0.0, 11),
+    # four axes: about 150 canonical (n2, n3, n4) (three density row tiles), n1 in [0, 4] (two force column tiles
+    # of 4 n1 x 4 axes), 700 particles (a ragged last particle tile)
+    ("d4_tiles", 4, 700, 700 ** 0.25, 0.30, 0.0, 19),
+    # |n| <= 7.5: about 880 canonical p (fourteen row tiles) and force K ranges of up to seven read-out chunks
+    ("d4_wide_kmode", 4, 800, 800 ** 0.25, 0.0, 2 * math.pi * 7.5 / 800 ** 0.25, 20),
+    ("fullbits_d4", 4, 300, 300 ** 0.25, 0.30, 0.0, -21),
     ("wide_d2", 2, 2000, 2000 ** 0.5, 0.45, 0.0, 12),
     # positions with full-mantissa bits and low words on every axis (as after minimiser moves); synthetic
     # draws are multiples of 2^-53, which makes every phase reduction exact and hides rounding in it
@@ -92,10 +98,8 @@ CASES = [
 
 
 def impls(d):
-    """(fx_impl, precisions to check) per context: d <= 3 runs the fixed point through both implementations."""
-    if d <= 3:
-        return [(ssh.FX_INTEGER, PRECS), (ssh.FX_TENSOR, [ssh.FX])]
-    return [(ssh.FX_AUTO, PRECS)]
+    """(fx_impl, precisions to check) per context: the fixed point runs through both implementations."""
+    return [(ssh.FX_INTEGER, PRECS), (ssh.FX_TENSOR, [ssh.FX])]
 
 
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
@@ -260,14 +264,19 @@ def test_fx_impl_selection(built):
     with ssh.Context(2, 64, 8.0, chi=0.3, fx_impl=ssh.FX_INTEGER) as c:
         assert c.fx_impl == ssh.FX_INTEGER
     with ssh.Context(3, 64, 4.0, chi=0.3) as c:
-        assert c.fx_impl == ssh.FX_TENSOR        # the tensor-core path covers d = 1, 2 and 3
+        assert c.fx_impl == ssh.FX_TENSOR        # the tensor-core path covers d = 1..4
     with ssh.Context(1, 64, 64.0, chi=0.3) as c:
         assert c.fx_impl == ssh.FX_TENSOR        # d = 1 on two lifted axes
     with ssh.Context(4, 64, 64 ** 0.25, chi=0.3) as c:
+        assert c.fx_impl == ssh.FX_TENSOR
+    with ssh.Context(4, 64, 64 ** 0.25, chi=0.3, fx_impl=ssh.FX_INTEGER) as c:
         assert c.fx_impl == ssh.FX_INTEGER
-    with pytest.raises(ssh.SshError) as e:
-        ssh.Context(4, 64, 64 ** 0.25, chi=0.3, fx_impl=ssh.FX_TENSOR)
-    assert e.value.status == 1
+    # four axes with a component beyond 64 (the packed sub-vector's limit): the integer pipes serve the set
+    far = np.array([[1, 0, 0, 0], [0, 1, 0, 0], [0, 0, 0, 65], [2, -1, 3, 1]], dtype=np.int32)
+    with ssh.Context(4, 64, 64 ** 0.25, kset=far, fx_impl=ssh.FX_TENSOR) as c:
+        assert c.fx_impl == ssh.FX_INTEGER
+    with ssh.Context(4, 64, 64 ** 0.25, kset=far[[0, 1, 3]], fx_impl=ssh.FX_TENSOR) as c:
+        assert c.fx_impl == ssh.FX_TENSOR
     with pytest.raises(ssh.SshError):
         ssh.Context(2, 64, 8.0, chi=0.3, fx_impl=7)
 
@@ -314,11 +323,12 @@ def test_positions_wrap_exact(built):
 
 
 @pytest.mark.parametrize("d,N,L,chi,chunk", [(2, 10_000, 100.0, 0.45, 2048), (3, 3000, 3000 ** (1 / 3), 0.30, 1024),
-                                              (1, 5000, 5000.0, 0.30, 1280)])
+                                              (1, 5000, 5000.0, 0.30, 1280), (4, 3000, 3000 ** 0.25, 0.30, 1024)])
 def test_chunked_equals_unchunked(built, d, N, L, chi, chunk):
     """Particle chunks on the tensor-core path (ssh_opts.tc_chunk; the last chunk ragged, not a whole number of
     K-steps): the sums are exact integers, so n~, Phi, S_max and F are bit-identical to one chunk, and so is a
-    FIRE segment."""
+    FIRE segment.  At d = 3 and d = 4 these sizes also split the force K ranges (fewer particle-tile items than
+    SMs), the same split in every chunk."""
     s = synth.positions(77 + d, N, d)
     out = {}
     for ch in (0, chunk):
