@@ -224,6 +224,128 @@ __device__ __forceinline__ void i192_add_double_126(i192& a, double x) {
 // 2^e as a double (normal range)
 __device__ __forceinline__ double pow2(int e) { return __longlong_as_double((long long)(1023 + e) << 52); }
 
+// 320-bit unsigned integer, five little-endian 64-bit words: exact sums of |n~|^2 in units of 2^-220
+struct u320 {
+  unsigned long long w[5];
+};
+__device__ __forceinline__ void u320_zero(u320& a) {
+#pragma unroll
+  for (int i = 0; i < 5; i++) a.w[i] = 0ull;
+}
+__device__ __forceinline__ void u320_add(u320& a, const u320& b) {
+  unsigned long long cy = 0;
+#pragma unroll
+  for (int i = 0; i < 5; i++) {
+    const unsigned __int128 t = (unsigned __int128)a.w[i] + b.w[i] + cy;
+    a.w[i] = (unsigned long long)t;
+    cy = (unsigned long long)(t >> 64);
+  }
+}
+// a += v 2^(64 i) (the sum stays below 2^320)
+__device__ __forceinline__ void u320_add_at(u320& a, int i, unsigned __int128 v) {
+  unsigned long long add[5] = {0ull, 0ull, 0ull, 0ull, 0ull};
+  add[i] = (unsigned long long)v;
+  if (i + 1 < 5) add[i + 1] = (unsigned long long)(v >> 64);
+  u320 b;
+#pragma unroll
+  for (int k = 0; k < 5; k++) b.w[k] = add[k];
+  u320_add(a, b);
+}
+// x^2 of a 192-bit two's-complement integer with |x| < 2^159
+__device__ __forceinline__ u320 u320_sq(const i192& x) {
+  unsigned long long a0 = x.w[0], a1 = x.w[1], a2 = x.w[2];
+  if ((long long)a2 < 0) {  // |x|
+    a0 = ~a0;
+    a1 = ~a1;
+    a2 = ~a2;
+    a0 += 1ull;
+    const unsigned long long c0 = a0 == 0ull ? 1ull : 0ull;
+    a1 += c0;
+    a2 += (c0 && a1 == 0ull) ? 1ull : 0ull;
+  }
+  // x^2 = a0^2 + 2 a0 a1 2^64 + (a1^2 + 2 a0 a2) 2^128 + 2 a1 a2 2^192 + a2^2 2^256
+  u320 r;
+  u320_zero(r);
+  const unsigned __int128 p01 = (unsigned __int128)a0 * a1, p02 = (unsigned __int128)a0 * a2,
+                          p12 = (unsigned __int128)a1 * a2;
+  u320_add_at(r, 0, (unsigned __int128)a0 * a0);
+  u320_add_at(r, 1, p01);
+  u320_add_at(r, 1, p01);
+  u320_add_at(r, 2, (unsigned __int128)a1 * a1);
+  u320_add_at(r, 2, p02);
+  u320_add_at(r, 2, p02);
+  u320_add_at(r, 3, p12);
+  u320_add_at(r, 3, p12);
+  r.w[4] += a2 * a2;
+  return r;
+}
+// word q of a little-endian array of n words (0 outside), by selects: no indexed access to registers
+template <int n>
+__device__ __forceinline__ unsigned long long word_at(const unsigned long long (&w)[n], int q) {
+  unsigned long long v = 0ull;
+#pragma unroll
+  for (int k = 0; k < n; k++) v = k == q ? w[k] : v;
+  return v;
+}
+// 64 bits of x from bit b up (b may be negative: zeros shifted in below bit 0)
+__device__ __forceinline__ unsigned long long u320_bits(const u320& x, int b) {
+  if (b <= -64) return 0ull;
+  if (b < 0) return x.w[0] << (-b);
+  const int q = b >> 6, r = b & 63;
+  const unsigned long long lo = word_at(x.w, q), hi = word_at(x.w, q + 1);
+  return r ? (lo >> r) | (hi << (64 - r)) : lo;
+}
+// x 2^-S as a double-double from the top 106 bits of x (the bits below are dropped: relative error < 2^-105);
+// S - 320 >= -1022 keeps both words normal
+__device__ __forceinline__ dd u320_to_dd(const u320& x, int S) {
+  int t = 0;
+#pragma unroll
+  for (int k = 1; k < 5; k++) t = x.w[k] != 0ull ? k : t;
+  const unsigned long long top = word_at(x.w, t);
+  if (top == 0ull) return dd_make(0.0);
+  const int lead = 64 * t + 63 - __clzll((long long)top);
+  const unsigned long long m53 = (1ull << 53) - 1;
+  const unsigned long long h = u320_bits(x, lead - 52) & m53, l = u320_bits(x, lead - 105) & m53;
+  return fast_two_sum((double)h * pow2(lead - 52 - S), (double)l * pow2(lead - 105 - S));
+}
+// round(x w) for a weight 0 <= w <= 1024 (round half up; x w < 2^320)
+__device__ __forceinline__ u320 u320_mul_weight(const u320& x, double w) {
+  u320 r;
+  u320_zero(r);
+  if (!(w > 0.0)) return r;
+  int ex;
+  const double fr = frexp(w, &ex);                                  // w = fr 2^ex, 1/2 <= fr < 1
+  const unsigned long long m = (unsigned long long)ldexp(fr, 53);  // exact: w = m 2^(ex - 53)
+  unsigned long long y[6];
+  unsigned long long cy = 0;
+#pragma unroll
+  for (int i = 0; i < 5; i++) {
+    const unsigned __int128 t = (unsigned __int128)x.w[i] * m + cy;
+    y[i] = (unsigned long long)t;
+    cy = (unsigned long long)(t >> 64);
+  }
+  y[5] = cy;
+  const int sh = 53 - ex;  // >= 42
+  if (sh >= 6 * 64) return r;
+  {  // + 2^(sh - 1)
+    const int q = (sh - 1) >> 6;
+    unsigned long long c = 0ull;
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+      const unsigned long long o = y[i], a = (i == q ? 1ull << ((sh - 1) & 63) : 0ull) + c;
+      y[i] = o + a;
+      c = y[i] < o ? 1ull : 0ull;
+    }
+  }
+  const int q = sh >> 6, b = sh & 63;
+#pragma unroll
+  for (int i = 0; i < 5; i++) {
+    const unsigned long long lo = word_at(y, i + q), hi = word_at(y, i + q + 1);
+    r.w[i] = b ? (lo >> b) | (hi << (64 - b)) : lo;
+  }
+  return r;
+}
+
 // X 2^-S of a 192-bit integer with |X| < 2^150, as a double-double.  X = h 2^106 + m 2^53 + l with l, m in
 // [0, 2^53) and h signed are each exact in binary64; the two-sum of the top two pieces is exact, and the last
 // piece lies below the unit of the result's low word.
@@ -372,10 +494,11 @@ __device__ __forceinline__ void qmul_out(const qent& z, const qent& b, uint4& yr
 
 }  // namespace
 
-// Two threads per (particle, axis), in two halves of the grid so that every warp runs one of the two chains:
+// Two threads per (particle, axis), in two halves of the grid so that every warp runs one of the two tables:
 // half 0 the tables T[k] = e^{2 pi i k s} (k < 8), half 1 the tables A[b] = e^{2 pi i 8 b s} (b <= Rax / 8), as
-// first-quadrant phasors.  Each chain starts from an exact-phase evaluation (e^{2 pi i s}, e^{2 pi i 8 s}) and
-// multiplies on (each product at most 8 units of 2^-126 low, so the error of a power grows linearly in its
+// first-quadrant phasors.  Each table starts from an exact-phase evaluation z (e^{2 pi i s}, e^{2 pi i 8 s}) and
+// runs as two interleaved chains of step z^2, the even and the odd powers, which halves the dependent multiplies
+// of the thread (each product at most 8 units of 2^-126 low, so the error of a power grows linearly in its
 // exponent: far below the 2^-104 digits).
 // Block map over the tensor-core members' chunks; layout tc_tab[(axis nbuf + j) tc_ntab + (k | 8 + b)], j within
 // the chunk.
@@ -398,16 +521,20 @@ __global__ void __launch_bounds__(128) k_tc_tables(const CfgDev* __restrict__ cf
   if (c.tc_lift && axis == 0) u = turn_times(u, 1 << c.tc_lift);
   qent* tab = reinterpret_cast<qent*>(c.tc_tab) + ((int64_t)axis * c.tc_nbuf + j) * c.tc_ntab + (h == 0 ? 0 : kPrepLow);
   // e^0 = 1 exactly (the exact-phase evaluation returns (2^126, 0) at t = 0): c = 1 in Q1.127, s = 0, quadrant 0
-  qent x;
-  x.c = q128_zero();
-  x.c.w[3] = 0x80000000u;
-  x.s = q128_zero();
-  x.cs = x.c;
+  qent xe;
+  xe.c = q128_zero();
+  xe.c.w[3] = 0x80000000u;
+  xe.s = q128_zero();
+  xe.cs = xe.c;
   const qent e = to_quadrant(phasor_turn(h == 0 ? u : turn_times(u, kPrepLow)));
+  const qent e2 = qmul(e, e);
+  qent xo = e;
 #pragma unroll 1
-  for (int k = 0; k < cnt; k++) {
-    tab[k] = x;
-    if (k + 1 < cnt) x = qmul(x, e);
+  for (int k = 0; k < cnt; k += 2) {  // xe = z^k, xo = z^(k + 1)
+    tab[k] = xe;
+    if (k + 1 < cnt) tab[k + 1] = xo;
+    if (k + 2 < cnt) xe = qmul(xe, e2);
+    if (k + 3 < cnt) xo = qmul(xo, e2);
   }
 }
 
@@ -944,37 +1071,120 @@ __global__ void __launch_bounds__(kGemmThreads, 1) k_tc_gemm(const CfgDev* __res
 
 // ------------------------------------------------------------------------------------------------ finish
 
-// block map over the tensor-core members (tc_nblk blocks each), 64 threads, a lane pair per (n1, p), n1 fastest:
+namespace {
+
+// per-block partials of the tensor-core density reduction, in the space of one RedPart: Phi as an exact integer
+// (units of 2^-220, so every order of summation gives the same bits), max |n~|^2 as dd, max |C|, |S|
+struct TcRed {
+  u320 phi;
+  double a2_hi, a2_lo, cmax;
+};
+static_assert(sizeof(TcRed) == sizeof(RedPart), "the tensor-core partials reuse the partial buffer");
+
+__device__ __forceinline__ void tc_red_combine(TcRed& a, const TcRed& b) {
+  u320_add(a.phi, b.phi);
+  if (dd_gt(dd_make(b.a2_hi, b.a2_lo), dd_make(a.a2_hi, a.a2_lo))) {
+    a.a2_hi = b.a2_hi;
+    a.a2_lo = b.a2_lo;
+  }
+  a.cmax = fmax(a.cmax, b.cmax);
+}
+
+// fixed-order warp tree: lane 0 ends with the combination of lanes 0..31
+__device__ __forceinline__ void tc_red_warp(TcRed& v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    TcRed o;
+#pragma unroll
+    for (int i = 0; i < 5; i++) o.phi.w[i] = __shfl_down_sync(0xffffffffu, v.phi.w[i], off);
+    o.a2_hi = __shfl_down_sync(0xffffffffu, v.a2_hi, off);
+    o.a2_lo = __shfl_down_sync(0xffffffffu, v.a2_lo, off);
+    o.cmax = __shfl_down_sync(0xffffffffu, v.cmax, off);
+    if (lane < off) tc_red_combine(v, o);
+  }
+}
+
+// The scalars of one evaluation from its nb block partials (one block of kFinThreads threads, the same order
+// whichever block runs it): Phi, S_max = max |n~|^2 / N, max |C|, |S| and the scale e (2^e > 2 max |C|, |S|).
+// The partials are read through L2 (the caller's fence and ticket make every block's write visible).
+__device__ __forceinline__ void tc_finalize(const TcRed* blk, int nb, int64_t N, double* scal,
+                                            TcRed (&sh)[kFinThreads / 32]) {
+  auto load = [&](int i) {
+    const unsigned long long* p = reinterpret_cast<const unsigned long long*>(blk + i);
+    TcRed r;
+#pragma unroll
+    for (int k = 0; k < 5; k++) r.phi.w[k] = __ldcg(p + k);
+    const double* q = reinterpret_cast<const double*>(p + 5);
+    r.a2_hi = __ldcg(q + 0);
+    r.a2_lo = __ldcg(q + 1);
+    r.cmax = __ldcg(q + 2);
+    return r;
+  };
+  TcRed v;
+  u320_zero(v.phi);
+  v.a2_hi = v.a2_lo = v.cmax = 0.0;
+  if ((int)threadIdx.x < nb) v = load(threadIdx.x);
+  for (int i = threadIdx.x + kFinThreads; i < nb; i += kFinThreads) tc_red_combine(v, load(i));
+  tc_red_warp(v);
+  __syncthreads();  // sh holds the caller's partials
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    v = sh[0];
+#pragma unroll
+    for (int w = 1; w < kFinThreads / 32; w++) tc_red_combine(v, sh[w]);
+    const dd phi = u320_to_dd(v.phi, 220);
+    scal[kScPhiHi] = phi.hi;
+    scal[kScPhiLo] = phi.lo;
+    const dd sm = N > 0 ? dd_div(dd_make(v.a2_hi, v.a2_lo), dd_make((double)N)) : dd_make(0.0);
+    scal[kScSmaxHi] = sm.hi;
+    scal[kScSmaxLo] = sm.lo;
+    scal[kScCmax] = v.cmax;
+    scal[kScScaleExp] = v.cmax > 0 ? (double)(ilogb(v.cmax) + 2) : 0.0;
+    scal[kScA2MaxHi] = v.a2_hi;
+    scal[kScA2MaxLo] = v.a2_lo;
+  }
+}
+
+}  // namespace
+
+// block map over the tensor-core members (tc_nblk blocks each), 64 threads, a lane pair per (n1, p), p fastest:
 // the even lane n~(n1, p), the odd lane n~(n1, -p), from the four real products of the tile accumulator (which the
 // even lane clears for the next evaluation once both have read it), as exact Q34.126 values (for the force
-// coefficients) and as dd (C, S), with the block's Phi / max |n~|^2 / max |C|, |S| partials; the last block to
-// finish reduces the partials to Phi, S_max and the scale.
+// coefficients) and as dd (C, S), with the block's partials: Phi as an exact integer sum of v~ |n~|^2 (|n~|^2 =
+// C^2 + S^2 formed exactly, in integer arithmetic rather than on the scarce FP64 pipe), max |n~|^2 and
+// max |C|, |S|; the last block to finish reduces the partials to Phi, S_max and the scale.
 __global__ void __launch_bounds__(kFinThreads) k_tc_dens_finish(const CfgDev* __restrict__ cfgs,
                                                                 const BlockMap* __restrict__ bm) {
   grid_dep_wait();
   const BlockMap m = bm[blockIdx.x];
   const CfgDev& c = cfgs[m.cfg];
   if (stopped(c)) return;  // uniform per block
-  RedPart v = {0, 0, 0, 0, 0, 0, 0, 0};
+  TcRed v;
+  u320_zero(v.phi);
+  v.a2_hi = v.a2_lo = v.cmax = 0.0;
   const int W1 = c.tc_R1 + 1;
   const int64_t idx = ((int64_t)m.blk * kFinThreads + threadIdx.x) >> 1;
   const int neg = threadIdx.x & 1;
   int k = -1, ti = -1, rr = 0, cc = 0;
   bool tr = false;
+  double w = 1.0;
   long long P[4][3];  // [2 x + y]: x the cos / sin of w (row), y of a (column)
   long long* acc = nullptr;
   if (idx < (int64_t)W1 * c.tc_nP) {
     // p fastest: a warp's lanes read consecutive accumulator rows (p, cos / sin), contiguous in memory
     const int p = (int)(idx % c.tc_nP), n1 = (int)(idx / c.tc_nP);
     const int64_t ei = (int64_t)p * W1 + n1;  // em is [p][n1][2]
-    const int kp = c.tc_em[ei * 2 + 0], km = c.tc_em[ei * 2 + 1];
-    k = neg ? km : kp;
     const int r = 2 * p, col = 2 * n1;
     // the transposed remainder tile holds P_xy(p, n1) at row trRow0 + 2 n1 + y, column 2 (p - trP0) + x
     tr = c.tc_tr && p >= c.tc_trP0;
-    ti = (kp >= 0 || km >= 0)
-             ? c.tc_tilemap[tr ? (c.tc_RT - 1) * c.tc_CTd + (c.tc_CTd - 1) : (r >> 7) * c.tc_CTd + (col >> 5)]
-             : -1;
+    // the emit map and the tile map are read together (the tile map entry is in range for every (p, n1))
+    const int kp = c.tc_em[ei * 2 + 0], km = c.tc_em[ei * 2 + 1];
+    const int tm = c.tc_tilemap[tr ? (c.tc_RT - 1) * c.tc_CTd + (c.tc_CTd - 1) : (r >> 7) * c.tc_CTd + (col >> 5)];
+    k = neg ? km : kp;
+    if (k >= 0) w = c.wk[k];
+    ti = (kp >= 0 || km >= 0) ? tm : -1;
     if (ti >= 0) {
       rr = tr ? c.tc_trRow0 + col : r & 127;
       cc = tr ? 2 * (p - c.tc_trP0) : col & 31;
@@ -1016,7 +1226,6 @@ __global__ void __launch_bounds__(kFinThreads) k_tc_dens_finish(const CfgDev* __
     c.S_lo[k] = sd.lo;
     // the force coefficients take the weighted value v~(k) n~(k): exact for weight 1, else v~ n~ in dd (relative
     // error 2^-105) rounded to Q34.126
-    const double w = c.wk[k];
     FxAcc o;
     if (w == 1.0) {
       o.re = i192_to_q160_shl(C, 16);  // value 2^-110 -> Q34.126
@@ -1034,24 +1243,25 @@ __global__ void __launch_bounds__(kFinThreads) k_tc_dens_finish(const CfgDev* __
       o.im = i192_to_q160_shl(Y, 0);
     }
     part[k] = o;
-    const dd a2 = dd_add(dd_sqr(cd), dd_sqr(sd));
-    const dd wa2 = w == 1.0 ? a2 : dd_mul_d(a2, w);
-    v.phi_hi = wa2.hi;
-    v.phi_lo = wa2.lo;
-    v.a2max_hi = a2.hi;
-    v.a2max_lo = a2.lo;
+    // |n~|^2 = (C^2 + S^2) 2^-220 exactly; Phi takes v~ |n~|^2 (rounded to 2^-220 for weights other than 1)
+    u320 a2 = u320_sq(C);
+    u320_add(a2, u320_sq(S));
+    const dd a2d = u320_to_dd(a2, 220);
+    v.phi = w == 1.0 ? a2 : u320_mul_weight(a2, w);
+    v.a2_hi = a2d.hi;
+    v.a2_lo = a2d.lo;
     v.cmax = w * fmax(fabs(cd.hi), fabs(sd.hi));
   }
-  red_warp(v);
-  __shared__ RedPart sh[kFinThreads / 32];
+  tc_red_warp(v);
+  __shared__ TcRed sh[kFinThreads / 32];
   __shared__ int last;
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
-    RedPart a = sh[0];
+    TcRed a = sh[0];
 #pragma unroll
-    for (int w = 1; w < kFinThreads / 32; w++) red_combine(a, sh[w]);
-    reinterpret_cast<RedPart*>(c.blk)[m.blk] = a;
+    for (int i = 1; i < kFinThreads / 32; i++) tc_red_combine(a, sh[i]);
+    reinterpret_cast<TcRed*>(c.blk)[m.blk] = a;
     // the block that finishes last reduces every block's partial (tc_err[1] counts finished blocks)
     __threadfence();
     last = atomicAdd(c.tc_err + 1, 1) == c.tc_nblk - 1;
@@ -1059,7 +1269,7 @@ __global__ void __launch_bounds__(kFinThreads) k_tc_dens_finish(const CfgDev* __
   __syncthreads();
   if (last) {
     __threadfence();
-    finalize_block<kFinThreads>(reinterpret_cast<const RedPart*>(c.blk), c.tc_nblk, c.N, c.scal, sh);
+    tc_finalize(reinterpret_cast<const TcRed*>(c.blk), c.tc_nblk, c.N, c.scal, sh);
     if (threadIdx.x == 0) c.tc_err[1] = 0;  // for the next evaluation
   }
 }
