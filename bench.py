@@ -536,7 +536,7 @@ def d4_block(ssh, synth, dev, stream, pipes):
         pr = c.prof_read()
         c.prof_enable(False)
         c.close()
-        ms = {k: v[0] / v[1] for k, v in pr.items()}
+        ms = {k: v[0] / 5 for k, v in pr.items()}  # per evaluation (the two finishes share one record name)
         r = {"M": pairs // N, "fx_impl": "tensor" if used == ssh.FX_TENSOR else "integer", "eval_ms": sum(ms.values()),
              "per_kernel_ms": ms, "eval_pairs_per_s": pairs / (sum(ms.values()) * 1e-3)}
         if used == ssh.FX_TENSOR:
@@ -884,7 +884,8 @@ def large_d3_block(ssh, synth, dev, stream, flush, steps=5, warmup=3, max_second
     prof = ctx.prof_read()
     ctx.prof_enable(False)
     out["step"] = {"ms": ms, "pairs_per_s": pairs / (ms * 1e-3),
-                   "per_kernel_ms": {k: v[0] / v[1] for k, v in prof.items()}}
+                   "per_kernel_ms": {k: v[0] / v[1] for k, v in prof.items()},
+                   "per_step_ms": {k: v[0] / steps for k, v in prof.items()}}
     if ctx.fx_impl == ssh.FX_TENSOR:
         fl = tc_flop_per_pair(cfg.d)
         out["step"]["tensor_frac_of_measured_bf16_peak"] = {
@@ -1040,7 +1041,11 @@ def main():
                                 if what == "bf16" else
                                 f"ssh_pipe_rate {'imad' if what == 'IMAD' else 'fp64_fma'} measured in this run, "
                                 f"of measured"),
-                "per_kernel_ms": {k: v[0] / v[1] for k, v in prof.items()}}
+                "per_kernel_ms": {k: v[0] / v[1] for k, v in prof.items()},
+                # per step: "fire" and "tc_finish" are two records a step (FIRE before and after the
+                # evaluation; the density and the force finish)
+                "per_step_ms": {k: v[0] / args.steps for k, v in prof.items()},
+                "records_per_step": {k: v[1] // args.steps for k, v in prof.items()}}
         tr = NCU_TRAFFIC.get((args.workload, "fx-tensor" if tensor else args.prec, dom_name))
         if tr and tr[0] == kernel_source_hash("tc" if tensor else "fx"):
             roof["traffic"] = tr[1]

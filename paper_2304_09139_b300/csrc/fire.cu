@@ -68,6 +68,10 @@ __device__ void dots_chunk(const CfgDev& c, int64_t q, double (*sh)[kFireThreads
 // The FIRE controls of a step from the chunk partials part[3][nq], summed by one warp (lane-strided in chunk order,
 // then a fixed shuffle tree): mixing, velocity reset, dt and alpha (Bitzek et al. 2006).
 __device__ void dots_control(FireState* fs, const double* part, int64_t nq, int lane) {
+  // the state the rules read, loaded before the sums so that the loads overlap (one latency, not a chain)
+  const double alpha = fs->alpha, dt = fs->dt, f_inc = fs->f_inc, dt_max = fs->dt_max, f_alpha = fs->f_alpha,
+               f_dec = fs->f_dec, alpha_start = fs->alpha_start;
+  const long long n_pos = fs->n_pos, n_min = fs->n_min;
   double P = 0, f2 = 0, v2 = 0;
   for (int64_t b = lane; b < nq; b += 32) {
     P += part[b];
@@ -84,19 +88,19 @@ __device__ void dots_control(FireState* fs, const double* part, int64_t nq, int 
   fs->dots_ticket = 0;  // for the next step
   if (P > 0) {
     fs->zero_v = 0;
-    fs->cv = 1.0 - fs->alpha;
-    fs->cf = f2 > 0 ? fs->alpha * sqrt(v2) / sqrt(f2) : 0.0;
-    if (fs->n_pos > fs->n_min) {
-      fs->dt = fmin(fs->dt * fs->f_inc, fs->dt_max);
-      fs->alpha *= fs->f_alpha;
+    fs->cv = 1.0 - alpha;
+    fs->cf = f2 > 0 ? alpha * sqrt(v2) / sqrt(f2) : 0.0;
+    if (n_pos > n_min) {
+      fs->dt = fmin(dt * f_inc, dt_max);
+      fs->alpha = alpha * f_alpha;
     }
-    fs->n_pos++;
+    fs->n_pos = n_pos + 1;
   } else {
     fs->zero_v = 1;
     fs->cv = 0;
     fs->cf = 0;
-    fs->dt *= fs->f_dec;
-    fs->alpha = fs->alpha_start;
+    fs->dt = dt * f_dec;
+    fs->alpha = alpha_start;
     fs->n_pos = 0;
   }
 }
@@ -187,11 +191,18 @@ __global__ void k_fire_accept(const CfgDev* __restrict__ cfgs, const int* __rest
   const CfgDev& c = cfgs[all[i]];
   FireState* fs = fstate(c);
   if (fs->status || fs->method != kMethodFire) return;
-  dd phi = dd_make(c.scal[kScPhiHi], c.scal[kScPhiLo]);
-  dd smx = dd_make(c.scal[kScSmaxHi], c.scal[kScSmaxLo]);
-  fs->step++;
-  fs->stage_step++;
-  if (tc_failed(c)) {  // incomplete sums: undo the step and stop the run
+  // every input is loaded up front, so that the loads overlap (one latency, not a chain of them)
+  const dd phi = dd_make(c.scal[kScPhiHi], c.scal[kScPhiLo]);
+  const dd smx = dd_make(c.scal[kScSmaxHi], c.scal[kScSmaxLo]);
+  const long long step = fs->step + 1, stage_step = fs->stage_step + 1, max_steps = fs->max_steps,
+                  best_step0 = fs->best_step, stall_window = fs->stall_window;
+  const dd phi_acc = dd_make(fs->phi_hi, fs->phi_lo);
+  const double smax_hi0 = fs->smax_hi, smax_lo0 = fs->smax_lo, phi_tol = fs->phi_tol, target = fs->target,
+               best_smax0 = fs->best_smax, stage_floor = fs->stage_floor;
+  const bool failed = tc_failed(c);
+  fs->step = step;
+  fs->stage_step = stage_step;
+  if (failed) {  // incomplete sums: undo the step and stop the run
     fs->status = kFsDevErr;
     fs->rejected_now = 1;
     return;
@@ -202,33 +213,38 @@ __global__ void k_fire_accept(const CfgDev* __restrict__ cfgs, const int* __rest
     return;
   }
   // uphill beyond the evaluation's own error bound: reject (FIRE's uphill reset, with dt halved)
-  const dd phi_acc = dd_make(fs->phi_hi, fs->phi_lo);
-  const double margin = fs->phi_tol * sqrt(fmax(phi_acc.hi, 0.0));
+  const double margin = phi_tol * sqrt(fmax(phi_acc.hi, 0.0));
+  double sm;
   if (dd_gt(phi, dd_add_d(phi_acc, margin))) {
+    const double dt = fs->dt, f_dec = fs->f_dec, alpha_start = fs->alpha_start;
+    const long long rejected = fs->rejected;
     fs->rejected_now = 1;
-    fs->rejected++;
-    fs->dt *= fs->f_dec;
-    fs->alpha = fs->alpha_start;
+    fs->rejected = rejected + 1;
+    fs->dt = dt * f_dec;
+    fs->alpha = alpha_start;
     fs->n_pos = 0;
+    sm = smax_hi0 + smax_lo0;
   } else {
     fs->rejected_now = 0;
     fs->phi_hi = phi.hi;
     fs->phi_lo = phi.lo;
     fs->smax_hi = smx.hi;
     fs->smax_lo = smx.lo;
+    sm = smx.hi + smx.lo;
   }
-  double sm = fs->smax_hi + fs->smax_lo;
-  if (sm <= fs->target) {
+  if (sm <= target) {
     fs->status = kFsConverged;
-  } else if (fs->step >= fs->max_steps) {
+  } else if (step >= max_steps) {
     fs->status = kFsMaxSteps;
   } else {
-    if (sm < 0.5 * fs->best_smax) {
+    long long best_step = best_step0;
+    if (sm < 0.5 * best_smax0) {
       fs->best_smax = sm;
-      fs->best_step = fs->stage_step;
+      fs->best_step = stage_step;
+      best_step = stage_step;
     }
-    if (fs->stage_floor > 0 && sm <= fs->stage_floor) fs->status = kFsStageDone;
-    else if (fs->stage_step - fs->best_step > fs->stall_window) fs->status = kFsStageDone;
+    if (stage_floor > 0 && sm <= stage_floor) fs->status = kFsStageDone;
+    else if (stage_step - best_step > stall_window) fs->status = kFsStageDone;
   }
 }
 
