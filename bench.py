@@ -105,10 +105,12 @@ NCU_TRAFFIC = {("d2-n10000", "fx", "force"): ("8c0684b40cfa", 35_871_488 + 24_06
                ("d2-n10000", "fx", "ntilde"): ("8c0684b40cfa", 36_564_736 + 7_424),
                ("d2-n10000", "dd", "force"): ("8c0684b40cfa", 35_895_296 + 0),
                ("d2-n10000", "dd", "ntilde"): ("8c0684b40cfa", 36_669_184 + 512),
-               ("d2-n10000", "fx-tensor", "tc_force"): ("89d979ba956d", 74_689_792 + 2_654_976),
-               ("d2-n10000", "fx-tensor", "tc_dens"): ("89d979ba956d", 135_645_184 + 5_039_104),
-               ("d3-n32768", "fx-tensor", "tc_force"): ("89d979ba956d", 3_589_898_000 + 26_543_000),
-               ("d3-n32768", "fx-tensor", "tc_dens"): ("89d979ba956d", 3_008_847_000 + 8_463_000)}
+               ("d2-n10000", "fx-tensor", "tc_force"): ("44444e97309e", 74_682_624 + 2_351_104),
+               ("d2-n10000", "fx-tensor", "tc_dens"): ("44444e97309e", 135_644_928 + 5_040_640),
+               ("d3-n32768", "fx-tensor", "tc_force"): ("44444e97309e", 3_583_391_488 + 26_191_104),
+               ("d3-n32768", "fx-tensor", "tc_dens"): ("44444e97309e", 3_008_975_360 + 8_591_872),
+               ("d4-n4096", "fx-tensor", "tc_force"): ("44444e97309e", 191_571_968 + 4_759_296),
+               ("d4-n4096", "fx-tensor", "tc_dens"): ("44444e97309e", 178_693_888 + 4_872_448)}
 
 
 # The sources each family of kernels is built from: the integer fixed-point and dd kernels, and the tensor-core
