@@ -65,6 +65,8 @@ class Config:
 SMALL_D2 = Config(d=2, N=100, L=1.0, chi=0.30, seed=1)
 MEDIUM_D2 = Config(d=2, N=10_000, L=100.0, chi=0.45, seed=2)
 LARGE_D3 = Config(d=3, N=32_768, L=32.0, chi=0.40, seed=3)
+# four axes at unit density: N = 4096 in a box of side 8, M = 4914
+MEDIUM_D4 = Config(d=4, N=4096, L=8.0, chi=0.30, seed=44)
 # The paper's own size (d = 2, N = 2 x 10^6, unit density) at its smallest and largest chi: M = 400000 and
 # 1600000 wavevectors.
 PAPER_D2 = Config(d=2, N=2_000_000, L=math.sqrt(2_000_000.0), chi=0.10, seed=6)

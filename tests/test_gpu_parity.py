@@ -145,6 +145,26 @@ def test_parity_medium_d2_full(built, oracle_mod):
         ctx.close()
 
 
+def test_parity_medium_d4_full(built, oracle_mod):
+    """The d=4, N=4096, chi=0.30 workload (M = 4914) at full size, in the launch configuration of its bench step
+    (on the tensor cores: 11 density row tiles, the force K ranges split in two): every output of both fixed-point
+    implementations and the dd path against the binary128 oracle."""
+    cfg = synth.MEDIUM_D4
+    s = synth.positions(cfg.seed, cfg.N, cfg.d)
+    ref = None
+    for impl, precs in impls(cfg.d):
+        ctx = ssh.Context(cfg.d, cfg.N, cfg.L, chi=cfg.chi, fx_impl=impl)
+        assert ctx.fx_impl == impl
+        n = ctx.kset()
+        if ref is None:
+            assert np.array_equal(n, oracle_mod.kset(cfg.d, cfg.N, cfg.L, chi=cfg.chi))
+            ref = oracle_mod.phi_grad(s, None, n, cfg.L, want_cs=True, nthreads=NTHREADS)
+        ctx.set_positions_frac(s)
+        for prec in precs:
+            check_parity(ctx, s, None, cfg.L, prec, ref, n, label=f"medium_d4/{ssh.PREC_NAMES[prec]}/impl{impl}")
+        ctx.close()
+
+
 def test_parity_large_d3_full(built, oracle_mod):
     """The d=3, N=32768, chi=0.40 workload (M = 39320) at full size, in the launch configuration of a plain
     evaluation: every n~(k) against the binary128 oracle (each a full sum over the particles), and F on 64 sampled
