@@ -126,7 +126,7 @@ static ssh_status create_from(int d, int64_t N, double L, ssh::KSet&& ks, const 
   c.own_stream = true;
   cudaDeviceGetAttribute(&c.sm_count, cudaDevAttrMultiProcessorCount, c.device);
   e = ssh::plan_upload(&c);
-  if (e == cudaSuccess) e = cudaMallocHost(&h->h_stage, sizeof(double) * 2 * (size_t)d * N);
+  if (e == cudaSuccess) e = cudaMallocHost(&h->h_stage, sizeof(double) * (2 * (size_t)d * N + ssh::kPackTail));
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->stage_done, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
   if (e != cudaSuccess) {
@@ -225,6 +225,7 @@ void ssh_destroy(ssh_ctx* h) {
   for (ssh::DevBuf* b : {&c.s_hi, &c.s_lo, &c.rows, &c.slots, &c.blocks, &c.grows, &c.cols, &c.fsplit, &c.tab, &c.part,
                          &c.C_hi, &c.C_lo, &c.S_hi, &c.S_lo, &c.wk, &c.coef, &c.blk, &c.scal, &c.fpart, &c.F_hi, &c.F_lo})
     free_buf(*b);
+  free_buf(h->d_pack);
   if (h->h_stage) cudaFreeHost(h->h_stage);
   if (h->stage_done) cudaEventDestroy(h->stage_done);
   for (ssh::ProfRec& r : c.prof.pending) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
@@ -464,47 +465,69 @@ ssh_status ssh_eval(ssh_ctx* h, int prec, int want_force) {
   return SSH_OK;
 }
 
+// The results of an evaluation in one block for a single download: F_hi and F_lo turned from the device's
+// axis-major [a][j] to the caller's [j][a] (nd = d N values each, or none), then the scalars and the status words
+// {any non-finite F_hi, the tensor-core status}.  The caller zeroes the first status word before the launch.
+__global__ void k_pack_results(const double* __restrict__ F_hi, const double* __restrict__ F_lo,
+                               const double* __restrict__ scal, const int* __restrict__ tc_err, int64_t N, int d,
+                               int64_t nd, double* __restrict__ out) {
+  double* tail = out + 2 * nd;
+  int* status = reinterpret_cast<int*>(tail + ssh::kScCount);
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nd) {
+    const int64_t j = i / d;
+    const int a = (int)(i - j * d);
+    const double fh = F_hi[a * N + j];
+    out[i] = fh;
+    out[nd + i] = F_lo[a * N + j];
+    if (!isfinite(fh)) status[0] = 1;
+  }
+  if (i < ssh::kScCount) tail[i] = scal[i];
+  if (i == 0) status[1] = tc_err ? *tc_err : 0;
+}
+
 ssh_status ssh_get_results(ssh_ctx* h, double phi[2], double smax[2], double* F_hi, double* F_lo) {
   if (!h) { set_error("ssh_get_results: NULL context"); return SSH_EINVAL; }
   ssh::Ctx& c = h->c;
   if (!c.have_result) { set_error("ssh_get_results: no evaluation yet"); return SSH_EINVAL; }
   if ((F_hi || F_lo) && !c.last_force) { set_error("ssh_get_results: last evaluation had no force"); return SSH_EINVAL; }
   cudaSetDevice(c.device);
-  double sc[ssh::kScCount];
-  SSH_CUDA(cudaMemcpyAsync(sc, c.scal.p, sizeof(sc), cudaMemcpyDeviceToHost, c.stream), "download scalars");
   const int64_t N = c.N;
   const int d = c.d;
-  double* hs = h->h_stage;
-  double* ls = h->h_stage + (size_t)d * N;
-  if (F_hi || F_lo) {
-    SSH_CUDA(cudaMemcpyAsync(hs, c.F_hi.p, sizeof(double) * d * N, cudaMemcpyDeviceToHost, c.stream), "download force");
-    SSH_CUDA(cudaMemcpyAsync(ls, c.F_lo.p, sizeof(double) * d * N, cudaMemcpyDeviceToHost, c.stream), "download force");
+  const int64_t nd = (F_hi || F_lo) ? (int64_t)d * N : 0;
+  const size_t full = sizeof(double) * (2 * (size_t)d * N + ssh::kPackTail);
+  if (!h->d_pack.p) {
+    SSH_CUDA(cudaMalloc(&h->d_pack.p, full), "ssh_get_results: results buffer");
+    h->d_pack.bytes = full;
   }
-  int tc_err = 0;
-  if (c.tc.on)
-    SSH_CUDA(cudaMemcpyAsync(&tc_err, c.tc.err.p, sizeof(int), cudaMemcpyDeviceToHost, c.stream), "download status");
+  // one kernel packs the force (in the caller's layout), the scalars and the status words; one copy brings them
+  double* dp = reinterpret_cast<double*>(h->d_pack.p);
+  SSH_CUDA(cudaMemsetAsync(dp + 2 * nd + ssh::kScCount, 0, sizeof(int), c.stream), "ssh_get_results");
+  const int64_t work = std::max<int64_t>(nd, ssh::kScCount);
+  k_pack_results<<<(unsigned)((work + 255) / 256), 256, 0, c.stream>>>(
+      (const double*)c.F_hi.p, (const double*)c.F_lo.p, (const double*)c.scal.p, c.tc.on ? (const int*)c.tc.err.p : nullptr,
+      N, d, nd, dp);
+  SSH_CUDA(cudaGetLastError(), "ssh_get_results: pack");
+  double* hp = h->h_stage;
+  SSH_CUDA(cudaMemcpyAsync(hp, dp, sizeof(double) * (2 * nd + ssh::kPackTail), cudaMemcpyDeviceToHost, c.stream),
+           "download results");
   SSH_CUDA(cudaStreamSynchronize(c.stream), "ssh_get_results");
-  if (tc_err != 0) {
+  const double* sc = hp + 2 * nd;
+  int status[2];
+  memcpy(status, sc + ssh::kScCount, sizeof status);
+  if (status[1] != 0) {
     // a bounded wait inside a tensor-core kernel gave up: the results of that evaluation are not valid
     cudaMemsetAsync(c.tc.err.p, 0, sizeof(int), c.stream);
-    set_error("tensor-core kernel: a bounded wait gave up (status " + std::to_string(tc_err) + ")");
+    set_error("tensor-core kernel: a bounded wait gave up (status " + std::to_string(status[1]) + ")");
     return SSH_ETIMEOUT;
   }
   if (phi) { phi[0] = sc[ssh::kScPhiHi]; phi[1] = sc[ssh::kScPhiLo]; }
   if (smax) { smax[0] = sc[ssh::kScSmaxHi]; smax[1] = sc[ssh::kScSmaxLo]; }
   bool bad = !isfinite(sc[ssh::kScPhiHi]) || !isfinite(sc[ssh::kScSmaxHi]);
-  if (F_hi || F_lo) {
-    uint64_t nonfinite = 0;  // branch-free: an all-ones exponent is an infinity or a NaN
-    for (int64_t j = 0; j < N; j++)
-      for (int a = 0; a < d; a++) {
-        const double fh = hs[a * N + j];
-        uint64_t u;
-        memcpy(&u, &fh, sizeof u);
-        nonfinite |= (uint64_t)(((u >> 52) & 0x7ff) == 0x7ff);
-        if (F_hi) F_hi[j * d + a] = fh;
-        if (F_lo) F_lo[j * d + a] = ls[a * N + j];
-      }
-    bad = bad || nonfinite != 0;
+  if (nd) {
+    if (F_hi) memcpy(F_hi, hp, sizeof(double) * nd);
+    if (F_lo) memcpy(F_lo, hp + nd, sizeof(double) * nd);
+    bad = bad || status[0] != 0;
   }
   if (bad) { set_error("non-finite energy, S_max or force"); return SSH_ENAN; }
   return SSH_OK;

@@ -392,6 +392,7 @@ cudaError_t fire_stage_init_engine(const Engine* e, const std::vector<int>& idx,
 
 // device scalar block written by k_finalize (doubles)
 enum { kScPhiHi = 0, kScPhiLo, kScSmaxHi, kScSmaxLo, kScCmax, kScScaleExp, kScA2MaxHi, kScA2MaxLo, kScCount = 16 };
+constexpr int kPackTail = kScCount + 1;  // packed results: the scalars, then int {non-finite force, tc status}
 
 // lbfgs.cu (the L-BFGS minimiser's step kernels)
 cudaError_t lbfgs_pre(const Engine* e, cudaStream_t st);
@@ -462,6 +463,9 @@ size_t device_footprint(const Ctx& c);
 // the public handle: one configuration plus its pinned host staging
 struct ssh_ctx {
   ssh::Ctx c;
-  double* h_stage = nullptr;  // pinned staging for positions and forces: 2 * d * N doubles
+  // pinned staging for positions and results: 2 d N doubles, then the packed results' tail (the scalars and two
+  // status words, kPackTail doubles)
+  double* h_stage = nullptr;
   cudaEvent_t stage_done = nullptr;  // recorded after the last upload from h_stage
+  ssh::DevBuf d_pack;               // the packed results on the device, laid out as h_stage (allocated on first use)
 };
