@@ -1081,7 +1081,7 @@ def main():
                 ctx.eval(p)
             ctx.sync()
             variants[name] = pairs / ((time.perf_counter() - t0) / reps)
-        if prec == ssh.FX and w["d"] in (2, 3):
+        if prec == ssh.FX:
             # the other fixed-point implementation on the same positions
             other = ssh.FX_INTEGER if tensor else ssh.FX_TENSOR
             with ssh.Context(w["d"], w["N"], w["L"], chi=w["chi"], device=dev, fx_impl=other) as c2:

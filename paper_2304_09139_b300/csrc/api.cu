@@ -465,24 +465,25 @@ ssh_status ssh_eval(ssh_ctx* h, int prec, int want_force) {
   return SSH_OK;
 }
 
-// The results of an evaluation in one block for a single download: F_hi and F_lo turned from the device's
-// axis-major [a][j] to the caller's [j][a] (nd = d N values each, or none), then the scalars and the status words
-// {any non-finite F_hi, the tensor-core status}.  The caller zeroes the first status word before the launch.
+// The results of an evaluation in one block for a single download: the scalars and the status words {any
+// non-finite F_hi, the tensor-core status} first, then F_hi and F_lo turned from the device's axis-major [a][j] to
+// the caller's [j][a] (nd = d N values each, or none).  The first status word is only ever set here; the host
+// clears it after a call that found it set.
 __global__ void k_pack_results(const double* __restrict__ F_hi, const double* __restrict__ F_lo,
                                const double* __restrict__ scal, const int* __restrict__ tc_err, int64_t N, int d,
                                int64_t nd, double* __restrict__ out) {
-  double* tail = out + 2 * nd;
-  int* status = reinterpret_cast<int*>(tail + ssh::kScCount);
+  int* status = reinterpret_cast<int*>(out + ssh::kScCount);
+  double* f = out + ssh::kPackTail;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < nd) {
     const int64_t j = i / d;
     const int a = (int)(i - j * d);
     const double fh = F_hi[a * N + j];
-    out[i] = fh;
-    out[nd + i] = F_lo[a * N + j];
+    f[i] = fh;
+    f[nd + i] = F_lo[a * N + j];
     if (!isfinite(fh)) status[0] = 1;
   }
-  if (i < ssh::kScCount) tail[i] = scal[i];
+  if (i < ssh::kScCount) out[i] = scal[i];
   if (i == 0) status[1] = tc_err ? *tc_err : 0;
 }
 
@@ -499,22 +500,23 @@ ssh_status ssh_get_results(ssh_ctx* h, double phi[2], double smax[2], double* F_
   if (!h->d_pack.p) {
     SSH_CUDA(cudaMalloc(&h->d_pack.p, full), "ssh_get_results: results buffer");
     h->d_pack.bytes = full;
+    SSH_CUDA(cudaMemsetAsync(h->d_pack.p, 0, sizeof(double) * ssh::kPackTail, c.stream), "ssh_get_results");
   }
-  // one kernel packs the force (in the caller's layout), the scalars and the status words; one copy brings them
+  // one kernel packs the scalars, the status words and the force (in the caller's layout); one copy brings them
   double* dp = reinterpret_cast<double*>(h->d_pack.p);
-  SSH_CUDA(cudaMemsetAsync(dp + 2 * nd + ssh::kScCount, 0, sizeof(int), c.stream), "ssh_get_results");
   const int64_t work = std::max<int64_t>(nd, ssh::kScCount);
   k_pack_results<<<(unsigned)((work + 255) / 256), 256, 0, c.stream>>>(
       (const double*)c.F_hi.p, (const double*)c.F_lo.p, (const double*)c.scal.p, c.tc.on ? (const int*)c.tc.err.p : nullptr,
       N, d, nd, dp);
   SSH_CUDA(cudaGetLastError(), "ssh_get_results: pack");
   double* hp = h->h_stage;
-  SSH_CUDA(cudaMemcpyAsync(hp, dp, sizeof(double) * (2 * nd + ssh::kPackTail), cudaMemcpyDeviceToHost, c.stream),
+  SSH_CUDA(cudaMemcpyAsync(hp, dp, sizeof(double) * (ssh::kPackTail + 2 * nd), cudaMemcpyDeviceToHost, c.stream),
            "download results");
   SSH_CUDA(cudaStreamSynchronize(c.stream), "ssh_get_results");
-  const double* sc = hp + 2 * nd;
+  const double* sc = hp;
   int status[2];
   memcpy(status, sc + ssh::kScCount, sizeof status);
+  if (status[0] != 0) cudaMemsetAsync(dp + ssh::kScCount, 0, sizeof(int), c.stream);  // for the next call
   if (status[1] != 0) {
     // a bounded wait inside a tensor-core kernel gave up: the results of that evaluation are not valid
     cudaMemsetAsync(c.tc.err.p, 0, sizeof(int), c.stream);
@@ -525,8 +527,8 @@ ssh_status ssh_get_results(ssh_ctx* h, double phi[2], double smax[2], double* F_
   if (smax) { smax[0] = sc[ssh::kScSmaxHi]; smax[1] = sc[ssh::kScSmaxLo]; }
   bool bad = !isfinite(sc[ssh::kScPhiHi]) || !isfinite(sc[ssh::kScSmaxHi]);
   if (nd) {
-    if (F_hi) memcpy(F_hi, hp, sizeof(double) * nd);
-    if (F_lo) memcpy(F_lo, hp + nd, sizeof(double) * nd);
+    if (F_hi) memcpy(F_hi, hp + ssh::kPackTail, sizeof(double) * nd);
+    if (F_lo) memcpy(F_lo, hp + ssh::kPackTail + nd, sizeof(double) * nd);
     bad = bad || status[0] != 0;
   }
   if (bad) { set_error("non-finite energy, S_max or force"); return SSH_ENAN; }
