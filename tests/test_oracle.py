@@ -37,6 +37,14 @@ def jacobi_r2(q):
     return 4 * (d1 - d3)
 
 
+def jacobi_r4(q):
+    """Number of integer (a, b, c, e) with a^2 + b^2 + c^2 + e^2 = q: 8 times the sum of the divisors of q that are
+    not multiples of 4 (Jacobi's four-square theorem)."""
+    if q == 0:
+        return 1
+    return 8 * sum(t for t in range(1, q + 1) if q % t == 0 and t % 4 != 0)
+
+
 def brute_half_ball(d, r2max):
     R = int(math.isqrt(r2max))
     grid = np.stack(np.meshgrid(*([np.arange(-R, R + 1)] * d), indexing="ij"), -1).reshape(-1, d)
@@ -54,6 +62,16 @@ def test_kset_2d_shell_counts_match_jacobi(oracle_mod, r2max):
     for q in range(1, r2max + 1):
         assert (n2 == q).sum() * 2 == jacobi_r2(q), q   # inversion pairs: half of the shell is independent
     assert len(n) == (sum(jacobi_r2(q) for q in range(0, r2max + 1)) - 1) // 2
+
+
+@pytest.mark.parametrize("r2max", [1, 3, 7, 12, 30])
+def test_kset_4d_shell_counts_match_jacobi(oracle_mod, r2max):
+    K = 2 * math.pi * math.sqrt(r2max)  # L = 1 so |n| <= sqrt(r2max), boundary inclusive
+    n = oracle_mod.kset(4, 10, 1.0, K=K)
+    n2 = (n.astype(np.int64) ** 2).sum(1)
+    for q in range(1, r2max + 1):
+        assert (n2 == q).sum() * 2 == jacobi_r4(q), q   # inversion pairs: half of the shell is independent
+    assert len(n) == (sum(jacobi_r4(q) for q in range(0, r2max + 1)) - 1) // 2
 
 
 @pytest.mark.parametrize("d,r2max", [(1, 16), (2, 30), (3, 12), (3, 27), (4, 6)])
