@@ -532,13 +532,14 @@ def d4_block(ssh, synth, dev, stream, pipes):
         for _ in range(3):
             c.eval(ssh.FX)
         c.sync()
+        reps = 5
         c.prof_enable(True)
-        for _ in range(5):
+        for _ in range(reps):
             c.eval(ssh.FX)
         pr = c.prof_read()
         c.prof_enable(False)
         c.close()
-        ms = {k: v[0] / 5 for k, v in pr.items()}  # per evaluation (the two finishes share one record name)
+        ms = {k: v[0] / reps for k, v in pr.items()}  # per evaluation (the two finishes share one record name)
         r = {"M": pairs // N, "fx_impl": "tensor" if used == ssh.FX_TENSOR else "integer", "eval_ms": sum(ms.values()),
              "per_kernel_ms": ms, "eval_pairs_per_s": pairs / (sum(ms.values()) * 1e-3)}
         if used == ssh.FX_TENSOR:
